@@ -1,0 +1,353 @@
+"""Benchmark of the Matching Pursuit decoder on GB300.
+
+One step = one complete decode (every MP iteration until ||r|| <= eps ||y||
+or T) of one signal of the plain FP32 workload N=4096, M=16384, K=256
+(256 MiB dictionary, larger than L2, so every iteration streams it from HBM).
+Inputs are resident in HBM before the timed region.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank decodes its own signals with its own copy
+of the dictionary (independent problems, no collective on the data path);
+the time is the max over ranks and ``value`` counts the recoveries of all
+ranks (weak scaling).
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MP recoveries/s & HBM GB/s vs peak, batched low-prec vs plain FP32; p99 latency"
+WORKLOAD = "plain_fp32_N4096_M16384_K256"
+KERNEL_SOURCES = ["paper_0809_1833_gb300/csrc/mp_plain.cu", "paper_0809_1833_gb300/csrc/mp_device.cuh"]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_record():
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "plain_stream_N4096_M16384_K256.traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------- problem
+
+def make_problem(n_signals, seed=0):
+    from paper_0809_1833_gb300 import workloads as W
+    w = W.WORKLOADS[WORKLOAD]
+    psi = W.gaussian_dictionary(w["N"], w["M"], seed)
+    sigs = [W.make_plain(w["N"], w["M"], w["K"], seed=seed + 1000 * i + 1, eps=w["eps"], T=w["T"], psi=psi)
+            for i in range(n_signals)]
+    Y = np.stack([s.y[0] for s in sigs])
+    return w, psi, Y, sigs
+
+
+def cpu_baseline(psi, y, eps, T, full_iters, budget_s=15.0):
+    """Time the FP64 oracle on the host cores on the first iterations of one
+    decode; extrapolate to recoveries/s with the full decode's iteration
+    count."""
+    from oracle import mp_oracle as orc
+    # one iteration to size the sample
+    t0 = time.perf_counter()
+    orc.mp(psi, y, eps, 1, record=False)
+    t1 = time.perf_counter() - t0
+    n = int(max(3, min(full_iters, budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    out = orc.mp(psi, y, eps, n, record=False)
+    dt = time.perf_counter() - t0
+    per_iter = dt / max(out["iters"], 1)
+    cores = os.cpu_count()
+    return {"value": 1.0 / (per_iter * full_iters), "unit": "recoveries/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {out['iters']} of {full_iters} iterations of one decode of {WORKLOAD} "
+                      f"(FP64 numpy, {dt:.1f} s); recoveries/s = 1/(s per iteration x {full_iters})",
+            "s_per_iteration": per_iter}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w, psi, Y, sigs = make_problem(1)
+    from oracle import mp_oracle as orc
+    # iteration count of the full decode of this signal, from one untimed
+    # full oracle run; each timed step is a bounded prefix of it
+    full_iters = orc.mp(psi, Y[0], w["eps"], w["T"], record=False)["iters"]
+    sample_iters = 20
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        orc.mp(psi, Y[0], w["eps"], sample_iters, record=False)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    per_iter = sum(times) / (len(times) * sample_iters)
+    v = 1.0 / (per_iter * full_iters)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "recoveries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "N": w["N"], "M": w["M"], "K": w["K"],
+                                            "eps": w["eps"], "T": w["T"]},
+            "cpu_baseline": {"value": v, "unit": "recoveries/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"each step = {sample_iters} FP64 oracle iterations of one decode; "
+                                       f"recoveries/s = 1/(s per iteration x {full_iters})"},
+            "e2e": {"value": v, "unit": "recoveries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0809_1833_gb300 import binding as B
+
+    n_sig = 4
+    w, psi_np, Y_np, sigs = make_problem(n_sig, seed=rank * 7919)
+    N, M = w["N"], w["M"]
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    psi = torch.from_numpy(psi_np).to(dev)
+    plan = B.mp_plan_create(N, M, psi.data_ptr(), prec_mask=0, stream=sptr)
+    del psi
+    Y = torch.from_numpy(Y_np).to(dev)
+    X = torch.empty((n_sig, M), dtype=torch.float32, device=dev)
+    mode = B.mp_plan_query(plan, B.MP_Q_PLAIN_MODE)
+
+    def step(i):
+        b = i % n_sig
+        B.mp_recover(plan, Y[b].data_ptr(), X[b].data_ptr(), w["eps"], w["T"], None, False, sptr)
+
+    # iterations per signal (device-side counts) for the algorithmic bytes
+    iters = []
+    for b in range(n_sig):
+        _, r = B.mp_recover(plan, Y[b].data_ptr(), X[b].data_ptr(), w["eps"], w["T"], None, True, sptr)
+        iters.append(r.iters)
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = B.mp_plan_query(plan, B.MP_Q_KERNEL_LAUNCHES)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step(i)
+        ev[i][1].record(stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = B.mp_plan_query(plan, B.MP_Q_KERNEL_LAUNCHES) - l0
+    clk = clocks.stop()
+    elapsed_ms = start.elapsed_time(end)
+    per_launch_ms = [a.elapsed_time(b) for a, b in ev]
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    total_recoveries = args.steps * world
+    value = total_recoveries / (elapsed_ms / 1e3)
+
+    # roofline of the persistent kernel: algorithmic bytes = 4 N M per iteration
+    step_iters = [iters[i % n_sig] for i in range(args.steps)]
+    alg_bytes = [4.0 * N * M * it for it in step_iters]
+    achieved = sum(alg_bytes) / (sum(per_launch_ms) / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    tr = traffic_record()
+    traffic = None
+    if tr is not None:
+        traffic = tr["dram_bytes_per_iteration"] * (sum(step_iters) / len(step_iters))
+
+    # end to end through the host-buffer entry point
+    y_host = [np.ascontiguousarray(Y_np[b]) for b in range(n_sig)]
+    x_host = np.empty(M, dtype=np.float32)
+    for i in range(2):
+        B.mp_recover_host(plan, y_host[i % n_sig], x_host, w["eps"], w["T"])
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        B.mp_recover_host(plan, y_host[i % n_sig], x_host, w["eps"], w["T"])
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": total_recoveries / e2e_s, "unit": "recoveries/s", "h2d_bytes_per_step": 4 * N,
+           "d2h_bytes_per_step": 4 * M + 56}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "recoveries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "M": M, "K": w["K"], "eps": w["eps"], "T": w["T"],
+                   "signals": n_sig, "iterations_per_decode": iters, "plain_mode": int(mode),
+                   "l2": "inputs exceed L2: the 256 MiB dictionary is streamed from HBM every iteration",
+                   "parallelism": f"dp{world} (independent signals)"},
+        "hbm_gbs": achieved,
+        "us_per_iteration": 1e3 * sum(per_launch_ms) / sum(step_iters),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "mp_plain_kernel<3> (grid streaming)",
+                     "algorithmic_bytes_per_launch": sum(alg_bytes) / len(alg_bytes)},
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(psi_np, Y_np[0], w["eps"], w["T"], iters[0], args.cpu_budget)
+    B.mp_plan_destroy(plan)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_profile_case(iters):
+    """Small case for ncu: the full-size dictionary, one decode capped at
+    ``iters`` iterations (one launch of the streaming kernel)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0809_1833_gb300 import binding as B
+    w, psi_np, Y_np, _ = make_problem(1)
+    s = torch.cuda.current_stream().cuda_stream
+    psi = torch.from_numpy(psi_np).cuda()
+    plan = B.mp_plan_create(w["N"], w["M"], psi.data_ptr(), stream=s)
+    del psi
+    y = torch.from_numpy(Y_np[0]).cuda()
+    x = torch.empty(w["M"], dtype=torch.float32, device="cuda")
+    _, r = B.mp_recover(plan, y.data_ptr(), x.data_ptr(), w["eps"], iters, None, True, s)
+    print(json.dumps({"profile_case": WORKLOAD, "iterations": r.iters,
+                      "dram_bytes_algorithmic_per_iteration": 4 * w["N"] * w["M"]}))
+    B.mp_plan_destroy(plan)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--profile", type=int, default=0,
+                    help="profiling case: one decode capped at this many iterations, then exit")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.profile:
+        run_profile_case(args.profile)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * mpgb.h — C ABI of the GB300 (sm_103a) Matching Pursuit decoder.
+ *
+ * The library recovers a sparse x in R^M from y = Psi x (Sec. 2, Eq. 2),
+ * Psi an N x M dictionary with unit-L2 columns (Eq. 4), by the Matching
+ * Pursuit iteration of Sec. 3 (Eqs. 8-12):
+ *
+ *     r <- y, x~ <- 0, t <- 0
+ *     while ||r||_2 > eps ||y||_2 and t < T:
+ *         i <- argmax_m |<r, psi_m>|     (smallest index on ties, Sec. 4)
+ *         x~_i <- x~_i + <r, psi_i>
+ *         r <- r - <r, psi_i> psi_i
+ *         t <- t + 1
+ *
+ * Conventions shared by every entry point:
+ *  - Indices are 0-based.  All sizes are element counts.
+ *  - "device pointer" means memory of the current CUDA device (for example a
+ *    torch tensor's data_ptr()); "host pointer" means ordinary CPU memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device-pointer entry points are stream-ordered: they enqueue
+ *    work and return; buffers must stay valid until the stream reaches it.
+ *  - Errors are returned as mp_status codes, never thrown or aborted; a
+ *    human-readable reason for the last failure on the calling thread is
+ *    given by mp_last_error_message().
+ *  - The loop test is evaluated in the squared form
+ *        e > eps^2 * e0,  e = sum_n r_n^2,  e0 = sum_n y_n^2
+ *    with e and e0 accumulated in FP64 on the device.  In exact arithmetic
+ *    it is Sec. 3's test ||r|| > eps ||y||.
+ *  - A plan is not thread-safe: calls on one plan must be serialised by the
+ *    caller (one host thread, one stream at a time).  Different plans are
+ *    independent.
+ */
+#ifndef MPGB_H
+#define MPGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MPGB_API __attribute__((visibility("default")))
+#else
+#define MPGB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Status codes, precisions, layouts                                   */
+/* ------------------------------------------------------------------ */
+
+typedef enum {
+    MP_OK = 0,
+    MP_PENDING = 1,            /* server: request not finished yet            */
+    MP_ERR_INVALID = -1,       /* bad argument or size, or non-unit atom      */
+    MP_ERR_NOMEM = -2,         /* device or host allocation failed            */
+    MP_ERR_BUSY = -3,          /* server: over its HBM or queue budget        */
+    MP_ERR_TIMEOUT = -4,       /* a device-side wait ran past its limit       */
+    MP_ERR_NONFINITE = -5,     /* non-finite input (y or Psi)                 */
+    MP_ERR_CUDA = -6,          /* a CUDA runtime call failed                  */
+    MP_ERR_UNSUPPORTED = -7,   /* size or precision this build cannot run     */
+    MP_ERR_NOT_FOUND = -8      /* server: unknown ticket or dictionary        */
+} mp_status;
+
+typedef enum {
+    MP_PREC_FP32 = 0,          /* FP32 correlations (CUDA cores)                    */
+    MP_PREC_BF16 = 1,          /* BF16 correlations on tcgen05, FP32 top-8 rescore  */
+    MP_PREC_FP8E4M3 = 2        /* FP8-E4M3 per-atom-scaled correlations, FP32 rescore */
+} mp_precision;
+
+typedef enum {
+    MP_LAYOUT_ATOM_MAJOR = 0,  /* M rows of N floats: row m is psi_m (column m of Psi) */
+    MP_LAYOUT_ROW_MAJOR = 1    /* Psi itself, N rows of M floats                       */
+} mp_layout;
+
+typedef enum {
+    MP_STOP_CONVERGED = 0,     /* ||r|| <= eps ||y||                          */
+    MP_STOP_MAX_ITERS = 1,     /* t reached T                                 */
+    MP_STOP_ZERO_Y = 2         /* y == 0                                      */
+} mp_stop_reason;
+
+typedef struct mp_plan_s* mp_plan_t;
+typedef struct mp_server_s* mp_server_t;
+
+/* Dictionary description for mp_plan_create. */
+typedef struct {
+    int N;                     /* measurement length, rows of Psi (>= 1)             */
+    int M;                     /* number of atoms, columns of Psi (>= 1)             */
+    int layout;                /* mp_layout of the psi pointer                       */
+    unsigned prec_mask;        /* bit (1u << p) builds the copy for precision p;     */
+                               /* FP32 is always built                               */
+    int normalize;             /* nonzero: scale atoms to unit norm (Eq. 4);         */
+                               /* zero: reject atoms with | ||psi_m|| - 1 | > 1e-5   */
+    int reserved;              /* must be 0                                          */
+} mp_plan_desc;
+
+/* Stopping parameters of Sec. 3's loop (eps, T). */
+typedef struct {
+    double eps;                /* relative residual target, >= 0                     */
+    int max_iters;             /* T, >= 0                                            */
+    int reserved;              /* must be 0                                          */
+} mp_stop;
+
+/* Per-signal result. */
+typedef struct {
+    int iters;                 /* t at exit: number of completed updates             */
+    int stop_reason;           /* mp_stop_reason                                     */
+    int status;                /* mp_status of this signal                           */
+    int reserved;
+    double rel_residual;       /* ||r|| / ||y|| at exit (0 when y == 0)               */
+    double energy_audit_max;   /* max_k |e_k - (e_{k-1} - c_k^2)| / e_0, where c_k is */
+                               /* the committed coefficient (energy conservation,     */
+                               /* Eq. 11 with Eq. 4)                                  */
+} mp_result;
+
+/* Optional per-iteration trace, device pointers (any may be NULL).
+ * Entry k (k < capacity) records step k: the selected atom, the
+ * coefficient added to x~ (Eq. 10) and the FP64 energy after the step.
+ * `residual` (N floats) receives the final residual r. */
+typedef struct {
+    int* atoms;
+    float* coefs;
+    double* energies;
+    float* residual;
+    int capacity;
+    int reserved;
+} mp_trace;
+
+/* Plan options for mp_plan_set_option. */
+typedef enum {
+    MP_OPT_PLAIN_MODE = 1,     /* 0 auto, 1 one-cluster resident, 2 grid resident,   */
+                               /* 3 grid streaming (TMA ring)                        */
+    MP_OPT_WATCHDOG_NS = 2,    /* limit of every device-side wait, ns (default 2e9)  */
+    MP_OPT_DEBUG_SKIP_ARRIVE = 3, /* grid modes: this CTA never arrives at the first */
+                               /* grid barrier (watchdog test), -1 = off             */
+    MP_OPT_GRID_CTAS = 4,      /* grid modes: CTA count (0 = one per SM)             */
+    MP_OPT_BATCH_TILE_N = 5    /* batched: atoms per GEMM tile (0 = autotuned)       */
+} mp_option;
+
+/* Read-only plan properties for mp_plan_query. */
+typedef enum {
+    MP_Q_PLAIN_MODE = 1,       /* mode the next mp_recover will use (1, 2 or 3)      */
+    MP_Q_PLAIN_CTAS = 2,       /* CTAs it will launch                                */
+    MP_Q_PLAIN_THREADS = 3,    /* threads per CTA                                    */
+    MP_Q_PLAIN_SMEM = 4,       /* dynamic shared memory per CTA, bytes               */
+    MP_Q_PLAIN_STAGE_ATOMS = 5,/* streaming mode: atoms per ring stage               */
+    MP_Q_PLAIN_STAGES = 6,     /* streaming mode: ring depth                         */
+    MP_Q_LD_FP32 = 7,          /* padded row length of the FP32 atom copy, floats    */
+    MP_Q_DEVICE_BYTES = 8,     /* device memory owned by the plan, bytes             */
+    MP_Q_KERNEL_LAUNCHES = 9   /* kernels this library launched for the plan so far  */
+} mp_query;
+
+/* ------------------------------------------------------------------ */
+/* Errors                                                              */
+/* ------------------------------------------------------------------ */
+
+/* Static string naming a status code.  Never NULL. */
+MPGB_API const char* mp_status_string(mp_status s);
+
+/* Reason for the most recent failure on the calling thread ("" if none).
+ * The pointer stays valid until the thread's next mpgb call. */
+MPGB_API const char* mp_last_error_message(void);
+
+/* ------------------------------------------------------------------ */
+/* Plans (Sec. 2: the dictionary shared by encoder and decoder)        */
+/* ------------------------------------------------------------------ */
+
+/* Create a plan for one dictionary.
+ *  out    : receives the plan handle (set to NULL on failure).
+ *  desc   : sizes, layout of `psi`, copies to build, normalisation policy.
+ *  psi    : device pointer to N*M floats in desc->layout; it is copied, the
+ *           caller keeps ownership and may free it after return.
+ *  stream : stream on which the copy and checks run; the call synchronises
+ *           it before returning.
+ * The plan owns an FP32 atom-major copy padded to a multiple of 32 floats
+ * per atom, plus the BF16 copy and/or the FP8-E4M3 copy with per-atom FP32
+ * scale max|psi_m|/448 that prec_mask asks for.
+ * Errors: MP_ERR_INVALID (sizes, layout, reserved field, non-unit atom
+ * without normalize, zero atom with normalize), MP_ERR_NONFINITE (a
+ * non-finite entry), MP_ERR_NOMEM, MP_ERR_CUDA. */
+MPGB_API mp_status mp_plan_create(mp_plan_t* out, const mp_plan_desc* desc, const float* psi,
+                         void* stream);
+
+/* Release a plan and everything it owns (synchronises the device first).
+ * NULL is accepted and ignored. */
+MPGB_API mp_status mp_plan_destroy(mp_plan_t plan);
+
+/* Set an mp_option.  MP_ERR_INVALID for an unknown option or value. */
+MPGB_API mp_status mp_plan_set_option(mp_plan_t plan, int option, long long value);
+
+/* Read an mp_query value into *value.  MP_ERR_INVALID if unknown. */
+MPGB_API mp_status mp_plan_query(mp_plan_t plan, int what, long long* value);
+
+/* ------------------------------------------------------------------ */
+/* Single-signal decode, FP32 (Sec. 3, Eqs. 8-12)                      */
+/* ------------------------------------------------------------------ */
+
+/* Decode one signal with the persistent FP32 kernel: correlations, the
+ * argmax, the x~ and r updates and the FP64 stop test all run in one
+ * launch with no host round-trip per iteration.
+ *  y        : device pointer, N floats (read only).
+ *  x        : device pointer, M floats; overwritten with x~ (zeroed first).
+ *  stop     : eps and T.
+ *  trace    : optional per-step record (NULL for none).
+ *  host_out : if non-NULL, the call synchronises `stream` and fills it;
+ *             the return value then reflects device-side errors too
+ *             (MP_ERR_TIMEOUT, MP_ERR_NONFINITE for non-finite y).
+ *             If NULL the call returns after enqueueing; fetch the result
+ *             later with mp_plan_last_result.
+ * Errors: MP_ERR_INVALID (NULL pointers, eps < 0, T < 0),
+ * MP_ERR_UNSUPPORTED (N too large for the on-chip residual), MP_ERR_CUDA. */
+MPGB_API mp_status mp_recover(mp_plan_t plan, const float* y, float* x, const mp_stop* stop,
+                     const mp_trace* trace, mp_result* host_out, void* stream);
+
+/* Synchronise the stream of the plan's last mp_recover and return its
+ * result (and its device-side status as the return value). */
+MPGB_API mp_status mp_plan_last_result(mp_plan_t plan, mp_result* out);
+
+/* mp_recover with HOST buffers: copies y to the device, decodes, copies x~
+ * back, and fills *out.  Blocking.  y_host: N floats; x_host: M floats.
+ * Uses plan-owned device and pinned staging buffers. */
+MPGB_API mp_status mp_recover_host(mp_plan_t plan, const float* y_host, float* x_host,
+                          const mp_stop* stop, mp_result* out);
+
+/* ------------------------------------------------------------------ */
+/* Batched decode of B signals sharing the plan's dictionary           */
+/* ------------------------------------------------------------------ */
+
+/* Decode B independent signals.  Each step computes the correlations of
+ * every still-active signal as one GEMM C = R Psi (tcgen05, BF16 or FP8
+ * operands, FP32 accumulation) that keeps only the top-8 |c| per signal,
+ * rescores those 8 atoms in FP32 from the FP32 atoms and commits the best
+ * (ties to the smallest index), updates x~ and r in FP32 and evaluates the
+ * FP64 stop test per signal.  Signals stop independently; finished ones
+ * leave the GEMM.
+ *  prec     : MP_PREC_BF16 or MP_PREC_FP8E4M3 (the plan must hold that
+ *             copy) or MP_PREC_FP32 (runs mp_recover per signal).
+ *  Y        : device pointer, B x N floats, row b is y_b.
+ *  X        : device pointer, B x M floats, row b receives x~_b.
+ *  stops    : n_stops entries, 1 (shared) or B (per signal).
+ *  host_out : B results (required); the call synchronises `stream`.
+ * Errors: MP_ERR_INVALID, MP_ERR_UNSUPPORTED (precision not built),
+ * MP_ERR_NOMEM, MP_ERR_CUDA, MP_ERR_TIMEOUT. */
+MPGB_API mp_status mp_recover_batched(mp_plan_t plan, int prec, const float* Y, float* X, int B,
+                             const mp_stop* stops, int n_stops, mp_result* host_out,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPGB_H */

@@ -106,20 +106,25 @@ def follow(psi_atoms, y, atoms):
 
     At each step the coefficient is the FP64 <r, psi_i> of the imposed atom,
     and the returned ``ratio[k]`` is |<r, psi_{atoms[k]}>| / max_m |<r, psi_m>|
-    before step k: 1.0 where the imposed atom is an MP choice.
-    Returns dict(ratio, x, r).
+    before step k: 1.0 where the imposed atom is an MP choice.  ``cmax[k]``
+    and ``rnorm[k]`` are max_m |<r, psi_m>| and ||r|| before step k.
+    Returns dict(ratio, cmax, rnorm, x, r).
     """
     P = np.array(psi_atoms, dtype=np.float64, copy=True)
     r = np.array(y, dtype=np.float64, copy=True).reshape(-1)
     x = np.zeros(P.shape[0], dtype=np.float64)
     ratio = np.empty(len(atoms), dtype=np.float64)
+    cmaxs = np.empty(len(atoms), dtype=np.float64)
+    rnorm = np.empty(len(atoms), dtype=np.float64)
     for k, i in enumerate(np.asarray(atoms, dtype=np.int64)):
         c = P @ r
         cmax = float(np.max(np.abs(c)))
         ratio[k] = abs(float(c[i])) / cmax if cmax > 0 else 1.0
+        cmaxs[k] = cmax
+        rnorm[k] = float(np.sqrt(np.dot(r, r)))
         x[i] += float(c[i])
         r -= float(c[i]) * P[i]
-    return dict(ratio=ratio, x=x, r=r)
+    return dict(ratio=ratio, cmax=cmaxs, rnorm=rnorm, x=x, r=r)
 
 
 def reconstruction_error(x_rec, x_true):

@@ -1,0 +1,211 @@
+"""Thin ctypes binding of ``libmpgb.so`` (declared in ``include/mpgb.h``).
+
+Functions keep the C names and only marshal arguments: pointers are passed
+as integers (``tensor.data_ptr()`` for device memory), streams as
+``torch.cuda.Stream.cuda_stream`` integers.  Every step of the decode runs
+in the library's CUDA kernels; there is no Python or CPU fallback, and
+``lib()`` raises if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libmpgb.so")
+
+# status codes
+MP_OK = 0
+MP_PENDING = 1
+MP_ERR_INVALID = -1
+MP_ERR_NOMEM = -2
+MP_ERR_BUSY = -3
+MP_ERR_TIMEOUT = -4
+MP_ERR_NONFINITE = -5
+MP_ERR_CUDA = -6
+MP_ERR_UNSUPPORTED = -7
+MP_ERR_NOT_FOUND = -8
+
+MP_PREC_FP32, MP_PREC_BF16, MP_PREC_FP8E4M3 = 0, 1, 2
+MP_LAYOUT_ATOM_MAJOR, MP_LAYOUT_ROW_MAJOR = 0, 1
+MP_STOP_CONVERGED, MP_STOP_MAX_ITERS, MP_STOP_ZERO_Y = 0, 1, 2
+
+MP_OPT_PLAIN_MODE = 1
+MP_OPT_WATCHDOG_NS = 2
+MP_OPT_DEBUG_SKIP_ARRIVE = 3
+MP_OPT_GRID_CTAS = 4
+MP_OPT_BATCH_TILE_N = 5
+
+MP_Q_PLAIN_MODE = 1
+MP_Q_PLAIN_CTAS = 2
+MP_Q_PLAIN_THREADS = 3
+MP_Q_PLAIN_SMEM = 4
+MP_Q_PLAIN_STAGE_ATOMS = 5
+MP_Q_PLAIN_STAGES = 6
+MP_Q_LD_FP32 = 7
+MP_Q_DEVICE_BYTES = 8
+MP_Q_KERNEL_LAUNCHES = 9
+
+
+class mp_plan_desc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("layout", ctypes.c_int),
+                ("prec_mask", ctypes.c_uint), ("normalize", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class mp_stop(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("max_iters", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class mp_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("stop_reason", ctypes.c_int), ("status", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("energy_audit_max", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class mp_trace(ctypes.Structure):
+    _fields_ = [("atoms", ctypes.c_void_p), ("coefs", ctypes.c_void_p), ("energies", ctypes.c_void_p),
+                ("residual", ctypes.c_void_p), ("capacity", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class MpError(RuntimeError):
+    def __init__(self, status, where, message):
+        super().__init__(f"{where}: {status_name(status)}: {message}")
+        self.status = status
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+# name -> (restype, argtypes); the same list is the set of exported symbols
+# the header declares.
+SIGNATURES = {
+    "mp_status_string": (ctypes.c_char_p, [_I]),
+    "mp_last_error_message": (ctypes.c_char_p, []),
+    "mp_plan_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(mp_plan_desc), _P, _P]),
+    "mp_plan_destroy": (_I, [_P]),
+    "mp_plan_set_option": (_I, [_P, _I, ctypes.c_longlong]),
+    "mp_plan_query": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong)]),
+    "mp_recover": (_I, [_P, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_trace),
+                        ctypes.POINTER(mp_result), _P]),
+    "mp_plan_last_result": (_I, [_P, ctypes.POINTER(mp_result)]),
+    "mp_recover_host": (_I, [_P, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_result)]),
+    "mp_recover_batched": (_I, [_P, _I, _P, _P, _I, ctypes.POINTER(mp_stop), _I,
+                                ctypes.POINTER(mp_result), _P]),
+}
+
+_LIB = None
+
+
+def lib():
+    """Load libmpgb.so (built by ``build.build()``); raises if it is missing."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def status_name(s):
+    return lib().mp_status_string(int(s)).decode()
+
+
+def last_error():
+    return lib().mp_last_error_message().decode()
+
+
+def check(status, where):
+    if status < 0:
+        raise MpError(status, where, last_error())
+    return status
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    return int(getattr(stream, "cuda_stream", stream)) or None
+
+
+# ---------------------------------------------------------------- wrappers
+
+def mp_plan_create(N, M, psi_ptr, layout=MP_LAYOUT_ATOM_MAJOR, prec_mask=0, normalize=False,
+                   stream=None):
+    """Returns a plan handle (int); raises MpError on failure."""
+    d = mp_plan_desc(int(N), int(M), int(layout), int(prec_mask), 1 if normalize else 0, 0)
+    h = ctypes.c_void_p()
+    check(lib().mp_plan_create(ctypes.byref(h), ctypes.byref(d), ctypes.c_void_p(int(psi_ptr)),
+                               _stream(stream)), "mp_plan_create")
+    return h.value
+
+
+def mp_plan_destroy(plan):
+    return check(lib().mp_plan_destroy(plan), "mp_plan_destroy")
+
+
+def mp_plan_set_option(plan, option, value):
+    return check(lib().mp_plan_set_option(plan, int(option), int(value)), "mp_plan_set_option")
+
+
+def mp_plan_query(plan, what):
+    v = ctypes.c_longlong()
+    check(lib().mp_plan_query(plan, int(what), ctypes.byref(v)), "mp_plan_query")
+    return v.value
+
+
+def make_trace(atoms_ptr=0, coefs_ptr=0, energies_ptr=0, capacity=0, residual_ptr=0):
+    return mp_trace(atoms_ptr or None, coefs_ptr or None, energies_ptr or None, residual_ptr or None,
+                    int(capacity), 0)
+
+
+def mp_recover(plan, y_ptr, x_ptr, eps, max_iters, trace=None, sync=True, stream=None,
+               raise_on_error=True):
+    """Decode one signal (device pointers).  With ``sync`` returns
+    (status, mp_result); otherwise (status, None) right after enqueueing."""
+    st = mp_stop(float(eps), int(max_iters), 0)
+    res = mp_result()
+    s = lib().mp_recover(plan, ctypes.c_void_p(int(y_ptr)), ctypes.c_void_p(int(x_ptr)), ctypes.byref(st),
+                         ctypes.byref(trace) if trace is not None else None,
+                         ctypes.byref(res) if sync else None, _stream(stream))
+    if raise_on_error:
+        check(s, "mp_recover")
+    return s, (res if sync else None)
+
+
+def mp_plan_last_result(plan, raise_on_error=True):
+    res = mp_result()
+    s = lib().mp_plan_last_result(plan, ctypes.byref(res))
+    if raise_on_error:
+        check(s, "mp_plan_last_result")
+    return s, res
+
+
+def mp_recover_host(plan, y_host, x_host, eps, max_iters, raise_on_error=True):
+    """Host-buffer decode: y_host / x_host are contiguous float32 numpy arrays."""
+    st = mp_stop(float(eps), int(max_iters), 0)
+    res = mp_result()
+    s = lib().mp_recover_host(plan, ctypes.c_void_p(y_host.ctypes.data), ctypes.c_void_p(x_host.ctypes.data),
+                              ctypes.byref(st), ctypes.byref(res))
+    if raise_on_error:
+        check(s, "mp_recover_host")
+    return s, res
+
+
+def mp_recover_batched(plan, prec, Y_ptr, X_ptr, B, stops, stream=None, raise_on_error=True):
+    """Batched decode; ``stops`` is one (eps, T) pair or a list of B pairs.
+    Returns (status, list of mp_result)."""
+    if isinstance(stops, tuple):
+        stops = [stops]
+    arr = (mp_stop * len(stops))(*[mp_stop(float(e), int(t), 0) for e, t in stops])
+    res = (mp_result * max(int(B), 1))()
+    s = lib().mp_recover_batched(plan, int(prec), ctypes.c_void_p(int(Y_ptr)), ctypes.c_void_p(int(X_ptr)),
+                                 int(B), arr, len(stops), res, _stream(stream))
+    if raise_on_error:
+        check(s, "mp_recover_batched")
+    return s, list(res)[:int(B)]

@@ -1,0 +1,111 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/mpgb.h"
+
+namespace mpgb {
+
+// Thread-local error text behind mp_last_error_message().
+void set_error(const std::string& msg);
+void clear_error();
+mp_status fail(mp_status s, const std::string& msg);
+mp_status cuda_fail(cudaError_t e, const char* what);
+
+#define MP_CUDA_TRY(expr)                                          \
+    do {                                                           \
+        cudaError_t _e = (expr);                                   \
+        if (_e != cudaSuccess) return ::mpgb::cuda_fail(_e, #expr); \
+    } while (0)
+
+// Device-side result of one plain decode, written by the kernel.
+struct PlainDevResult {
+    int iters;
+    int stop_reason;
+    int status;            // mp_status of the decode (set by the kernel)
+    int pad;
+    double e0;
+    double e;
+    double audit_max;
+};
+
+// Scratch of the plain kernel: the argmax key slots and the arrival
+// counter of the grid barrier, an error word, and the result.
+struct PlainWorkspace {
+    unsigned long long keys[4];
+    unsigned long long count;
+    int err;
+    int pad;
+    PlainDevResult res;
+};
+
+// Launch shape of the plain kernel, derived from (N, M) and the device.
+struct PlainConfig {
+    int mode = 0;          // 1 cluster-resident, 2 grid-resident, 3 grid-stream
+    int ctas = 0;          // grid size (= cluster size in mode 1)
+    int threads = 0;
+    int smem = 0;          // dynamic shared memory bytes
+    int stage_atoms = 0;   // mode 3
+    int stages = 0;        // mode 3
+    int off_data = 0;      // byte offsets inside dynamic smem
+    int off_sh = 0;
+};
+
+struct BatchEngine;        // batched decode state (mp_batched.cu)
+
+struct PlanImpl {
+    int N = 0, M = 0;
+    int ldN = 0;           // FP32 atom stride (floats), multiple of 32
+    int ldK16 = 0;         // BF16 atom stride (elements), multiple of 64
+    int ldK8 = 0;          // FP8 atom stride (bytes), multiple of 128
+    unsigned prec_mask = 0;
+    int device = 0;
+    int sm_count = 0;
+    int max_smem_optin = 0;
+    size_t device_bytes = 0;
+
+    float* psi32 = nullptr;
+    void* psi16 = nullptr;          // __nv_bfloat16
+    void* psi8 = nullptr;           // __nv_fp8_e4m3
+    float* scale8 = nullptr;        // per-atom FP8 scale
+
+    PlainWorkspace* ws = nullptr;   // device
+    PlainWorkspace* ws_host = nullptr;  // pinned mirror
+    cudaStream_t last_stream = nullptr;
+    bool have_pending = false;
+
+    // staging for mp_recover_host
+    float* y_stage = nullptr;       // device N
+    float* x_stage = nullptr;       // device M
+    float* h_y = nullptr;           // pinned N
+    float* h_x = nullptr;           // pinned M
+    cudaStream_t own_stream = nullptr;
+
+    // options
+    int forced_mode = 0;
+    long long watchdog_ns = 2000000000LL;
+    int skip_cta = -1;
+    int grid_ctas = 0;
+    int batch_tile_n = 0;
+
+    long long launches = 0;
+    BatchEngine* batch = nullptr;
+};
+
+// Plain-kernel helpers (mp_plain.cu).
+mp_status plain_configure(PlanImpl* p, PlainConfig* cfg);
+mp_status plain_launch(PlanImpl* p, const float* y, float* x, const mp_stop* stop,
+                       const mp_trace* trace, PlainWorkspace* ws, cudaStream_t st);
+mp_status plain_result_to_host(const PlanImpl* p, const PlainWorkspace* h, mp_result* out);
+
+// Batched engine teardown (mp_batched.cu).
+void batch_destroy(BatchEngine* b);
+
+}  // namespace mpgb
+
+struct mp_plan_s {
+    mpgb::PlanImpl impl;
+};

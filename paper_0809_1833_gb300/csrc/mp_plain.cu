@@ -1,0 +1,655 @@
+// Persistent FP32 Matching Pursuit kernel (Sec. 3, Eqs. 8-12): one launch
+// runs every iteration of one decode on the device.
+//
+// Each CTA owns a contiguous slice of atoms and keeps a full copy of the
+// residual r in shared memory.  Per iteration:
+//   1. correlate  c_m = <r, psi_m> for the CTA's atoms       (Eq. 9)
+//   2. select     the CTA's best packed key (|c|, -m, sign)  (Eq. 9, Sec. 4 ties)
+//   3. exchange   the grid-wide max key (cluster DSMEM atomics + hardware
+//                 cluster barrier, or global atomics + a bounded grid barrier)
+//   4. update     every CTA applies r -= c psi_m* to its own copy of r
+//                 (identical arithmetic in every CTA, so all copies stay
+//                 bit-identical) and reduces e = sum r^2 in FP64   (Eq. 11)
+//   5. CTA 0 adds c to x~_m*                                  (Eq. 10)
+//   6. every CTA evaluates the same stop test e <= eps^2 e0 or t = T.
+//
+// Launch shapes (chosen per plan from N, M and shared-memory capacity):
+//   mode 1  one cluster of up to 16 CTAs, the whole dictionary resident in
+//           the cluster's shared memory (small dictionaries: latency bound)
+//   mode 2  one CTA per SM, the dictionary resident across the grid
+//   mode 3  one CTA per SM; a producer warp streams the CTA's atoms from HBM
+//           through a ring of shared-memory stages with 1-D bulk copies and
+//           mbarriers, running ahead across iteration boundaries so that the
+//           exchange/update bubble overlaps the next pass's loads.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "mp_device.cuh"
+#include "mp_internal.h"
+
+namespace mpgb {
+
+constexpr int kMaxWarps = 32;
+constexpr int kMaxStages = 64;
+constexpr int kResidentThreads = 256;
+
+struct PlainShared {
+    unsigned long long keys[4];          // mode 1: key slots (rank 0's copy is used)
+    unsigned long long wkey[kMaxWarps];  // per compute warp best key
+    double wsum[kMaxWarps];              // per compute warp energy partial
+    unsigned long long key;              // selected key broadcast
+    int abort;
+    int done;
+    uint64_t full[kMaxStages];           // mode 3 ring barriers
+    uint64_t empty[kMaxStages];
+};
+
+struct PlainArgs {
+    const float* psi;      // M x ldN atom-major, zero padded
+    const float* y;        // N
+    float* x;              // M
+    int N, ldN, M, T;
+    double eps2;
+    int stage_atoms, stages;
+    int off_sh, off_data;
+    PlainWorkspace* ws;
+    int* tr_atoms;
+    float* tr_coefs;
+    double* tr_energy;
+    float* tr_resid;
+    int tr_cap;
+    unsigned long long watchdog_ns;
+    int skip_cta;
+};
+
+// ------------------------------------------------------------------ dots
+// Canonical per-atom summation order (every mode and group size gives the
+// same bits): lane l accumulates components x,y,z,w of segment elements
+// 4l..4l+3 of each 128-float segment in four FMA chains, combines them as
+// (x+y)+(z+w), then a butterfly sum across the warp.
+MP_DEV float dot1(const float* __restrict__ p, const float* __restrict__ r, int ldN, int lane) {
+    float ax = 0.f, ay = 0.f, az = 0.f, aw = 0.f;
+#pragma unroll 4
+    for (int off = lane * 4; off < ldN; off += 128) {
+        const float4 q = *reinterpret_cast<const float4*>(r + off);
+        const float4 v = *reinterpret_cast<const float4*>(p + off);
+        ax = fmaf(v.x, q.x, ax);
+        ay = fmaf(v.y, q.y, ay);
+        az = fmaf(v.z, q.z, az);
+        aw = fmaf(v.w, q.w, aw);
+    }
+    return warp_sum_f32((ax + ay) + (az + aw));
+}
+
+MP_DEV void dot4(const float* __restrict__ p, const float* __restrict__ r, int ldN, int lane,
+                 float out[4]) {
+    float a[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i][0] = a[i][1] = a[i][2] = a[i][3] = 0.f;
+#pragma unroll 2
+    for (int off = lane * 4; off < ldN; off += 128) {
+        const float4 q = *reinterpret_cast<const float4*>(r + off);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 v = *reinterpret_cast<const float4*>(p + static_cast<size_t>(i) * ldN + off);
+            a[i][0] = fmaf(v.x, q.x, a[i][0]);
+            a[i][1] = fmaf(v.y, q.y, a[i][1]);
+            a[i][2] = fmaf(v.z, q.z, a[i][2]);
+            a[i][3] = fmaf(v.w, q.w, a[i][3]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[i] = warp_sum_f32((a[i][0] + a[i][1]) + (a[i][2] + a[i][3]));
+}
+
+// Scan `n` consecutive atoms at p (first index m0) and fold into `best`.
+MP_DEV unsigned long long scan_atoms(const float* __restrict__ p, const float* __restrict__ r,
+                                     int ldN, int n, int m0, int lane, unsigned long long best) {
+    int q = 0;
+    for (; q + 4 <= n; q += 4) {
+        float c[4];
+        dot4(p + static_cast<size_t>(q) * ldN, r, ldN, lane, c);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) best = umax64(best, pack_key(c[i], m0 + q + i));
+    }
+    for (; q < n; ++q) best = umax64(best, pack_key(dot1(p + static_cast<size_t>(q) * ldN, r, ldN, lane), m0 + q));
+    return best;
+}
+
+// ------------------------------------------------------------------ grid barrier
+// Arrive with the CTA's key, wait (bounded) for all G CTAs, read the max.
+MP_DEV bool grid_exchange(const PlainArgs& a, int cta, int G, int t, unsigned long long k,
+                          unsigned long long* out) {
+    PlainWorkspace* ws = a.ws;
+    atomicMax(&ws->keys[t % 3], k);
+    if (!(cta == a.skip_cta && t == 0)) red_release_add_u64(&ws->count, 1ull);
+    const unsigned long long target = static_cast<unsigned long long>(t + 1) * G;
+    if (ld_acquire_u64(&ws->count) < target) {
+        const uint64_t deadline = globaltimer_ns() + a.watchdog_ns;
+        while (ld_acquire_u64(&ws->count) < target) {
+            if (ld_volatile_i32(&ws->err) != 0 || globaltimer_ns() > deadline) {
+                atomicCAS(&ws->err, 0, static_cast<int>(MP_ERR_TIMEOUT));
+                return false;
+            }
+        }
+    }
+    *out = ld_relaxed_u64(&ws->keys[t % 3]);
+    // slot (t+2)%3 was last read at iteration t-1, before every CTA arrived
+    // at this barrier; it is next written at iteration t+2, after the next one.
+    if (cta == 0) st_relaxed_u64(&ws->keys[(t + 2) % 3], 0ull);
+    return true;
+}
+
+// ------------------------------------------------------------------ producer
+MP_DEV void plain_producer(const PlainArgs& a, PlainShared* sh, float* ring, int a0, int na) {
+    const int A = a.stage_atoms, D = a.stages, ldN = a.ldN;
+    const int S = (na + A - 1) / A;
+    if (S == 0) return;
+    const size_t stage_floats = static_cast<size_t>(A) * ldN;
+    const uint64_t pol = policy_evict_first();
+    volatile int* vdone = &sh->done;
+    long long seq = 0;
+    while (true) {
+        const int slot = static_cast<int>(seq % D);
+        if (seq >= D) {
+            const uint32_t par = static_cast<uint32_t>(((seq / D) - 1) & 1);
+            bool ok = mbar_try_wait(&sh->empty[slot], par);
+            uint64_t deadline = 0;
+            while (!ok) {
+                if (*vdone) break;
+                const uint64_t now = globaltimer_ns();
+                if (deadline == 0) {
+                    deadline = now + a.watchdog_ns;
+                } else if (now > deadline) {
+                    atomicCAS(&a.ws->err, 0, static_cast<int>(MP_ERR_TIMEOUT));
+                    *reinterpret_cast<volatile int*>(&sh->abort) = 1;
+                    break;
+                }
+                ok = mbar_try_wait(&sh->empty[slot], par);
+            }
+            if (!ok) break;
+        }
+        if (*vdone) break;
+        const int j = static_cast<int>(seq % S);
+        const int atom0 = a0 + j * A;
+        const int nat = min(A, na - j * A);
+        const uint32_t bytes = static_cast<uint32_t>(nat) * ldN * 4u;
+        mbar_arrive_expect_tx(&sh->full[slot], bytes);
+        bulk_g2s_evict_first(ring + slot * stage_floats, a.psi + static_cast<size_t>(atom0) * ldN,
+                             bytes, &sh->full[slot], pol);
+        ++seq;
+    }
+    // Wait for every copy still in flight before the CTA may exit: the only
+    // outstanding copy of slot k is the last one issued into it.
+    const long long issued = seq;
+    for (int k = 0; k < D && k < issued; ++k) {
+        const long long last = issued - 1 - ((issued - 1 - k) % D);
+        mbar_wait_bounded(&sh->full[k], static_cast<uint32_t>((last / D) & 1), a.watchdog_ns);
+    }
+}
+
+// ------------------------------------------------------------------ kernel
+template <int MODE>
+__global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const PlainArgs a) {
+    constexpr bool STREAM = MODE == 3;
+    constexpr bool CLUSTER = MODE == 1;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* r = reinterpret_cast<float*>(smem);
+    PlainShared* sh = reinterpret_cast<PlainShared*>(smem + a.off_sh);
+    float* data = reinterpret_cast<float*>(smem + a.off_data);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncw = STREAM ? static_cast<int>(blockDim.x >> 5) - 1 : static_cast<int>(blockDim.x >> 5);
+    const int nct = ncw * 32;
+    const int cw = STREAM ? warp - 1 : warp;
+    const int ct = cw * 32 + lane;
+    const int cta = CLUSTER ? static_cast<int>(cluster_ctarank()) : static_cast<int>(blockIdx.x);
+    const int G = CLUSTER ? static_cast<int>(cluster_nctarank()) : static_cast<int>(gridDim.x);
+    const int ldN = a.ldN;
+    const int base = a.M / G, rem = a.M % G;
+    const int a0 = cta * base + min(cta, rem);
+    const int na = base + (cta < rem ? 1 : 0);
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 4; ++i) sh->keys[i] = 0ull;
+        sh->abort = 0;
+        sh->done = 0;
+        if (STREAM) {
+            for (int s = 0; s < a.stages; ++s) {
+                mbar_init(&sh->full[s], 1);
+                mbar_init(&sh->empty[s], 1);
+            }
+            fence_mbar_init();
+        }
+    }
+    __syncthreads();
+    if (CLUSTER) cluster_sync_all();  // rank 0's key slots are zero before any remote max
+
+    if (STREAM && warp == 0) {
+        if (lane == 0) plain_producer(a, sh, data, a0, na);
+        return;
+    }
+
+    // ---- Eq. 8: r <- y (zero padded), x~ <- 0 (own slice), resident atoms
+    for (int i = ct; i < ldN; i += nct) r[i] = i < a.N ? a.y[i] : 0.f;
+    for (int i = ct; i < na; i += nct) a.x[a0 + i] = 0.f;
+    if (!STREAM) {
+        const float4* src = reinterpret_cast<const float4*>(a.psi + static_cast<size_t>(a0) * ldN);
+        float4* dst = reinterpret_cast<float4*>(data);
+        const int n4 = na * (ldN / 4);
+        for (int i = ct; i < n4; i += nct) dst[i] = __ldg(src + i);
+    }
+    named_bar_sync(1, nct);
+
+    float4* r4 = reinterpret_cast<float4*>(r);
+    const int n4r = ldN / 4;
+    double acc = 0.0;
+    for (int k = ct; k < n4r; k += nct) {
+        const float4 v = r4[k];
+        acc = fma(static_cast<double>(v.x), static_cast<double>(v.x), acc);
+        acc = fma(static_cast<double>(v.y), static_cast<double>(v.y), acc);
+        acc = fma(static_cast<double>(v.z), static_cast<double>(v.z), acc);
+        acc = fma(static_cast<double>(v.w), static_cast<double>(v.w), acc);
+    }
+    acc = warp_sum_f64(acc);
+    if (lane == 0) sh->wsum[cw] = acc;
+    named_bar_sync(1, nct);
+    double e = 0.0;
+    for (int w = 0; w < ncw; ++w) e += sh->wsum[w];
+    const double e0 = e;
+    const double thr2 = a.eps2 * e0;
+    const bool finite0 = isfinite(e0);
+
+    int t = 0;
+    double audit = 0.0;
+    bool aborted = false;
+    const int A = a.stage_atoms, D = a.stages;
+    while (finite0 && e > thr2 && t < a.T) {
+        // ---- Eq. 9: correlations of this CTA's atoms, best packed key
+        unsigned long long best = 0ull;
+        if (!STREAM) {
+            for (int j = 4 * cw; j < na; j += 4 * ncw)
+                best = scan_atoms(data + static_cast<size_t>(j) * ldN, r, ldN, min(4, na - j), a0 + j,
+                                  lane, best);
+        } else {
+            const int S = (na + A - 1) / A;
+            const long long seq0 = static_cast<long long>(t) * S;
+            int j = static_cast<int>(((cw - seq0) % ncw + ncw) % ncw);
+            for (; j < S; j += ncw) {
+                const long long seq = seq0 + j;
+                const int slot = static_cast<int>(seq % D);
+                if (!mbar_wait_bounded(&sh->full[slot], static_cast<uint32_t>((seq / D) & 1),
+                                       a.watchdog_ns)) {
+                    if (lane == 0) {
+                        atomicCAS(&a.ws->err, 0, static_cast<int>(MP_ERR_TIMEOUT));
+                        *reinterpret_cast<volatile int*>(&sh->abort) = 1;
+                    }
+                    break;
+                }
+                const float* st = data + static_cast<size_t>(slot) * A * ldN;
+                best = scan_atoms(st, r, ldN, min(A, na - j * A), a0 + j * A, lane, best);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh->empty[slot]);
+            }
+        }
+        // ---- CTA max, then grid max
+        if (lane == 0) sh->wkey[cw] = best;
+        named_bar_sync(1, nct);
+        if (ct == 0) {
+            unsigned long long k = 0ull;
+            for (int w = 0; w < ncw; ++w) k = umax64(k, sh->wkey[w]);
+            if (CLUSTER) {
+                dsmem_max_u64(mapa_shared(smem_u32(&sh->keys[t % 3]), 0), k);
+            } else {
+                unsigned long long g = 0ull;
+                if (!grid_exchange(a, cta, G, t, k, &g)) *reinterpret_cast<volatile int*>(&sh->abort) = 1;
+                sh->key = g;
+            }
+        }
+        if (CLUSTER) {
+            cluster_sync_all();
+            if (ct == 0) {
+                sh->key = dsmem_ld_u64(mapa_shared(smem_u32(&sh->keys[t % 3]), 0));
+                if (cta == 0) sh->keys[(t + 2) % 3] = 0ull;
+            }
+        }
+        named_bar_sync(1, nct);
+        if (*reinterpret_cast<volatile int*>(&sh->abort)) {
+            aborted = true;
+            break;
+        }
+        const unsigned long long key = sh->key;
+        const int m = key_index(key);
+        const float c = key_coef(key);
+
+        // ---- Eq. 11: r <- r - c psi_m, and e = sum r^2 in FP64
+        const float4* pm = reinterpret_cast<const float4*>(a.psi + static_cast<size_t>(m) * ldN);
+        acc = 0.0;
+        for (int k = ct; k < n4r; k += nct) {
+            const float4 pv = __ldg(pm + k);
+            float4 v = r4[k];
+            v.x = fmaf(-c, pv.x, v.x);
+            v.y = fmaf(-c, pv.y, v.y);
+            v.z = fmaf(-c, pv.z, v.z);
+            v.w = fmaf(-c, pv.w, v.w);
+            r4[k] = v;
+            acc = fma(static_cast<double>(v.x), static_cast<double>(v.x), acc);
+            acc = fma(static_cast<double>(v.y), static_cast<double>(v.y), acc);
+            acc = fma(static_cast<double>(v.z), static_cast<double>(v.z), acc);
+            acc = fma(static_cast<double>(v.w), static_cast<double>(v.w), acc);
+        }
+        acc = warp_sum_f64(acc);
+        if (lane == 0) sh->wsum[cw] = acc;
+        named_bar_sync(1, nct);
+        double e_new = 0.0;
+        for (int w = 0; w < ncw; ++w) e_new += sh->wsum[w];
+
+        // ---- Eq. 10 and bookkeeping (one thread of CTA 0)
+        if (cta == 0 && ct == 0) {
+            a.x[m] += c;
+            if (t < a.tr_cap) {
+                if (a.tr_atoms) a.tr_atoms[t] = m;
+                if (a.tr_coefs) a.tr_coefs[t] = c;
+                if (a.tr_energy) a.tr_energy[t] = e_new;
+            }
+            const double cc = static_cast<double>(c);
+            audit = fmax(audit, fabs(e_new - (e - cc * cc)) / e0);
+        }
+        e = e_new;
+        ++t;  // Eq. 12
+    }
+
+    if (STREAM && ct == 0) *reinterpret_cast<volatile int*>(&sh->done) = 1;
+    if (cta == 0 && a.tr_resid)
+        for (int i = ct; i < a.N; i += nct) a.tr_resid[i] = r[i];
+    if (cta == 0 && ct == 0) {
+        PlainDevResult& res = a.ws->res;
+        res.iters = t;
+        res.e0 = e0;
+        res.e = e;
+        res.audit_max = audit;
+        res.stop_reason = e0 == 0.0 ? MP_STOP_ZERO_Y : (e <= thr2 ? MP_STOP_CONVERGED : MP_STOP_MAX_ITERS);
+        res.status = !finite0 ? MP_ERR_NONFINITE : (aborted ? MP_ERR_TIMEOUT : MP_OK);
+    }
+    if (CLUSTER) cluster_sync_all();  // keep rank 0's key slots alive until all are done
+}
+
+// ------------------------------------------------------------------ host side
+static int round_up_i(int v, int m) { return (v + m - 1) / m * m; }
+
+template <int MODE>
+static cudaError_t prepare_kernel_attrs(int max_smem) {
+    static int done_smem = -1;
+    cudaError_t e = cudaSuccess;
+    if (done_smem != max_smem) {
+        e = cudaFuncSetAttribute(mp_plain_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        if (e == cudaSuccess && MODE == 1)
+            e = cudaFuncSetAttribute(mp_plain_kernel<MODE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess) done_smem = max_smem;
+    }
+    return e;
+}
+
+static int max_cluster_size(int smem, int threads, int max_smem) {
+    static int cached[2] = {-1, -1};  // [smem key, result]
+    if (cached[0] == smem) return cached[1];
+    int best = 0;
+    if (prepare_kernel_attrs<1>(max_smem) == cudaSuccess) {
+        for (int c : {16, 8}) {
+            cudaLaunchConfig_t lc = {};
+            lc.gridDim = dim3(c);
+            lc.blockDim = dim3(threads);
+            lc.dynamicSmemBytes = smem;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = c;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            lc.attrs = at;
+            lc.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, mp_plain_kernel<1>, &lc) == cudaSuccess && n > 0) {
+                best = c;
+                break;
+            }
+            cudaGetLastError();
+        }
+    }
+    cached[0] = smem;
+    cached[1] = best;
+    return best;
+}
+
+mp_status plain_configure(PlanImpl* p, PlainConfig* cfg) {
+    *cfg = PlainConfig();
+    const long long atom_bytes = static_cast<long long>(p->ldN) * 4;
+    const int r_bytes = round_up_i(p->ldN * 4, 128);
+    const int sh_bytes = round_up_i(static_cast<int>(sizeof(PlainShared)), 128);
+    cfg->off_sh = r_bytes;
+    cfg->off_data = r_bytes + sh_bytes;
+    const long long budget = static_cast<long long>(p->max_smem_optin) - cfg->off_data;
+    if (budget < atom_bytes)
+        return fail(MP_ERR_UNSUPPORTED, "plain decode: N=" + std::to_string(p->N) +
+                                            " is too large for the shared-memory residual");
+    const int M = p->M;
+    int G = p->grid_ctas > 0 ? std::min(p->grid_ctas, p->sm_count) : p->sm_count;
+    G = std::max(1, std::min(G, M));
+
+    auto cluster_ok = [&](int* C_out) {
+        int C = 1;
+        while (C * 2 <= std::min(16, M)) C *= 2;
+        const long long apc = (M + C - 1) / C;
+        const long long smem = cfg->off_data + apc * atom_bytes;
+        if (smem > p->max_smem_optin) return false;
+        const int cmax = max_cluster_size(static_cast<int>(smem), kResidentThreads, p->max_smem_optin);
+        if (cmax == 0) return false;
+        if (C > cmax) {
+            C = cmax;
+            if (cfg->off_data + static_cast<long long>((M + C - 1) / C) * atom_bytes > p->max_smem_optin)
+                return false;
+        }
+        *C_out = C;
+        return true;
+    };
+    auto gridres_ok = [&]() {
+        const long long apc = (M + G - 1) / G;
+        return cfg->off_data + apc * atom_bytes <= p->max_smem_optin;
+    };
+
+    int mode = p->forced_mode;
+    int C = 0;
+    if (mode == 0) {
+        if (cluster_ok(&C)) mode = 1;
+        else if (gridres_ok()) mode = 2;
+        else mode = 3;
+    } else if (mode == 1 && !cluster_ok(&C)) {
+        return fail(MP_ERR_UNSUPPORTED, "plain decode: dictionary does not fit one cluster");
+    } else if (mode == 2 && !gridres_ok()) {
+        return fail(MP_ERR_UNSUPPORTED, "plain decode: dictionary does not fit the grid's shared memory");
+    }
+    cfg->mode = mode;
+    if (mode == 1) {
+        cfg->ctas = C;
+        cfg->threads = kResidentThreads;
+        cfg->smem = static_cast<int>(cfg->off_data + static_cast<long long>((M + C - 1) / C) * atom_bytes);
+        return MP_OK;
+    }
+    if (mode == 2) {
+        cfg->ctas = G;
+        cfg->threads = kResidentThreads;
+        cfg->smem = static_cast<int>(cfg->off_data + static_cast<long long>((M + G - 1) / G) * atom_bytes);
+        return MP_OK;
+    }
+    // mode 3: choose compute warps W, atoms per stage A, ring depth D (a multiple of W)
+    const long long apc = (M + G - 1) / G;
+    long long A = std::max<long long>(1, 16384 / atom_bytes);
+    A = std::min(A, apc);
+    const long long stage_bytes = A * atom_bytes;
+    for (int W : {4, 2, 1}) {
+        long long D = std::min<long long>(kMaxStages, budget / stage_bytes);
+        D -= D % W;
+        if (D >= std::max(W, 2)) {
+            cfg->ctas = G;
+            cfg->threads = 32 * (1 + W);
+            cfg->stage_atoms = static_cast<int>(A);
+            cfg->stages = static_cast<int>(D);
+            cfg->smem = static_cast<int>(cfg->off_data + D * stage_bytes);
+            return MP_OK;
+        }
+    }
+    return fail(MP_ERR_UNSUPPORTED, "plain decode: N=" + std::to_string(p->N) +
+                                        " leaves no room for a two-stage ring");
+}
+
+mp_status plain_launch(PlanImpl* p, const float* y, float* x, const mp_stop* stop, const mp_trace* trace,
+                       PlainWorkspace* ws, cudaStream_t st) {
+    PlainConfig cfg;
+    mp_status s = plain_configure(p, &cfg);
+    if (s != MP_OK) return s;
+    PlainArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = p->psi32;
+    a.y = y;
+    a.x = x;
+    a.N = p->N;
+    a.ldN = p->ldN;
+    a.M = p->M;
+    a.T = stop->max_iters;
+    a.eps2 = stop->eps * stop->eps;
+    a.stage_atoms = cfg.stage_atoms;
+    a.stages = cfg.stages;
+    a.off_sh = cfg.off_sh;
+    a.off_data = cfg.off_data;
+    a.ws = ws;
+    if (trace) {
+        a.tr_atoms = trace->atoms;
+        a.tr_coefs = trace->coefs;
+        a.tr_energy = trace->energies;
+        a.tr_resid = trace->residual;
+        a.tr_cap = std::max(0, trace->capacity);
+    }
+    a.watchdog_ns = static_cast<unsigned long long>(p->watchdog_ns);
+    a.skip_cta = cfg.mode == 1 ? -1 : p->skip_cta;
+
+    MP_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(PlainWorkspace), st));
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(cfg.ctas);
+    lc.blockDim = dim3(cfg.threads);
+    lc.dynamicSmemBytes = cfg.smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    if (cfg.mode == 1) {
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cfg.ctas;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+    } else {
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+    }
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    cudaError_t e;
+    switch (cfg.mode) {
+        case 1:
+            MP_CUDA_TRY(prepare_kernel_attrs<1>(p->max_smem_optin));
+            e = cudaLaunchKernelEx(&lc, mp_plain_kernel<1>, a);
+            break;
+        case 2:
+            MP_CUDA_TRY(prepare_kernel_attrs<2>(p->max_smem_optin));
+            e = cudaLaunchKernelEx(&lc, mp_plain_kernel<2>, a);
+            break;
+        default:
+            MP_CUDA_TRY(prepare_kernel_attrs<3>(p->max_smem_optin));
+            e = cudaLaunchKernelEx(&lc, mp_plain_kernel<3>, a);
+            break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "plain decode launch");
+    p->launches++;
+    return MP_OK;
+}
+
+mp_status plain_result_to_host(const PlanImpl*, const PlainWorkspace* h, mp_result* out) {
+    const PlainDevResult& r = h->res;
+    std::memset(out, 0, sizeof(*out));
+    out->iters = r.iters;
+    out->stop_reason = r.stop_reason;
+    mp_status s = static_cast<mp_status>(r.status);
+    if (s == MP_OK && h->err != 0) s = static_cast<mp_status>(h->err);
+    out->status = s;
+    out->rel_residual = r.e0 > 0.0 ? std::sqrt(r.e / r.e0) : 0.0;
+    out->energy_audit_max = r.audit_max;
+    if (s == MP_ERR_TIMEOUT) set_error("a device-side wait exceeded the watchdog limit");
+    if (s == MP_ERR_NONFINITE) set_error("y has a non-finite entry");
+    return s;
+}
+
+static mp_status check_stop(const mp_stop* stop) {
+    if (!stop) return fail(MP_ERR_INVALID, "stop is NULL");
+    if (!(stop->eps >= 0.0) || !std::isfinite(stop->eps)) return fail(MP_ERR_INVALID, "eps must be finite and >= 0");
+    if (stop->max_iters < 0) return fail(MP_ERR_INVALID, "max_iters must be >= 0");
+    if (stop->reserved != 0) return fail(MP_ERR_INVALID, "stop.reserved must be 0");
+    return MP_OK;
+}
+
+}  // namespace mpgb
+
+using namespace mpgb;
+
+extern "C" {
+
+mp_status mp_recover(mp_plan_t plan, const float* y, float* x, const mp_stop* stop, const mp_trace* trace,
+                     mp_result* host_out, void* stream) {
+    clear_error();
+    if (!plan || !y || !x) return fail(MP_ERR_INVALID, "mp_recover: NULL plan, y or x");
+    mp_status s = check_stop(stop);
+    if (s != MP_OK) return s;
+    PlanImpl* p = &plan->impl;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    s = plain_launch(p, y, x, stop, trace, p->ws, st);
+    if (s != MP_OK) return s;
+    p->last_stream = st;
+    p->have_pending = true;
+    if (!host_out) return MP_OK;
+    return mp_plan_last_result(plan, host_out);
+}
+
+mp_status mp_plan_last_result(mp_plan_t plan, mp_result* out) {
+    if (!plan || !out) return fail(MP_ERR_INVALID, "mp_plan_last_result: NULL argument");
+    PlanImpl* p = &plan->impl;
+    if (!p->have_pending) return fail(MP_ERR_INVALID, "mp_plan_last_result: no decode was issued");
+    MP_CUDA_TRY(cudaMemcpyAsync(p->ws_host, p->ws, sizeof(PlainWorkspace), cudaMemcpyDeviceToHost, p->last_stream));
+    MP_CUDA_TRY(cudaStreamSynchronize(p->last_stream));
+    return plain_result_to_host(p, p->ws_host, out);
+}
+
+mp_status mp_recover_host(mp_plan_t plan, const float* y_host, float* x_host, const mp_stop* stop,
+                          mp_result* out) {
+    clear_error();
+    if (!plan || !y_host || !x_host || !out) return fail(MP_ERR_INVALID, "mp_recover_host: NULL argument");
+    mp_status s = check_stop(stop);
+    if (s != MP_OK) return s;
+    PlanImpl* p = &plan->impl;
+    if (!p->own_stream) MP_CUDA_TRY(cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking));
+    if (!p->y_stage) {
+        MP_CUDA_TRY(cudaMalloc(&p->y_stage, sizeof(float) * p->N));
+        MP_CUDA_TRY(cudaMalloc(&p->x_stage, sizeof(float) * p->M));
+        MP_CUDA_TRY(cudaMallocHost(&p->h_y, sizeof(float) * p->N));
+        MP_CUDA_TRY(cudaMallocHost(&p->h_x, sizeof(float) * p->M));
+    }
+    cudaStream_t st = p->own_stream;
+    std::memcpy(p->h_y, y_host, sizeof(float) * p->N);
+    MP_CUDA_TRY(cudaMemcpyAsync(p->y_stage, p->h_y, sizeof(float) * p->N, cudaMemcpyHostToDevice, st));
+    s = plain_launch(p, p->y_stage, p->x_stage, stop, nullptr, p->ws, st);
+    if (s != MP_OK) return s;
+    p->last_stream = st;
+    p->have_pending = true;
+    MP_CUDA_TRY(cudaMemcpyAsync(p->h_x, p->x_stage, sizeof(float) * p->M, cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaMemcpyAsync(p->ws_host, p->ws, sizeof(PlainWorkspace), cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaStreamSynchronize(st));
+    std::memcpy(x_host, p->h_x, sizeof(float) * p->M);
+    return plain_result_to_host(p, p->ws_host, out);
+}
+
+}  // extern "C"

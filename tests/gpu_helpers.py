@@ -1,0 +1,127 @@
+"""Helpers for the GPU parity tests: run the CUDA path through the C ABI and
+compare it with the FP64 oracle by the comparison rule for MP results.
+
+Comparison rule (several MP paths are correct at a near tie, so only what is
+unique is compared exactly):
+  (i)   the selected-atom sequence equals the oracle's on the prefix up to
+        the first step whose oracle top-two gap is <= 1e-5 relative (the
+        whole sequence when there is no such step);
+  (ii)  x~ is within ``x_tol`` relative L2 of the oracle's x~;
+  (iii) replaying the GPU's sequence in FP64, every selected atom is an MP
+        choice up to the FP32 error: ratio_k >= 1 - tol_k, with
+        tol_k = max(1e-5, (2 ||delta|| + 2 N 2^-24 ||r_k||) / max|c_k|) where
+        delta = y - Psi x~_gpu - r_gpu is the accumulated FP32 drift
+        (measured in FP64) and N 2^-24 ||r_k|| bounds one FP32 dot product's
+        rounding for unit atoms.
+"""
+import numpy as np
+
+GAP_TIE = 1e-5
+
+
+def torch_mod():
+    import torch
+    return torch
+
+
+def cur_stream():
+    torch = torch_mod()
+    return torch.cuda.current_stream().cuda_stream
+
+
+class GpuPlan:
+    """A plan over a numpy atom-major dictionary, created through the C ABI."""
+
+    def __init__(self, psi, prec_mask=0, mode=0, layout_row_major=False, normalize=False):
+        from paper_0809_1833_gb300 import binding as B
+        torch = torch_mod()
+        self.B = B
+        M, N = psi.shape
+        self.N, self.M = N, M
+        src = np.ascontiguousarray(psi.T if layout_row_major else psi, dtype=np.float32)
+        d = torch.from_numpy(src).cuda()
+        self.plan = B.mp_plan_create(N, M, d.data_ptr(),
+                                     B.MP_LAYOUT_ROW_MAJOR if layout_row_major else B.MP_LAYOUT_ATOM_MAJOR,
+                                     prec_mask, normalize, cur_stream())
+        del d
+        if mode:
+            B.mp_plan_set_option(self.plan, B.MP_OPT_PLAIN_MODE, mode)
+
+    def set(self, opt, val):
+        self.B.mp_plan_set_option(self.plan, opt, val)
+
+    def query(self, what):
+        return self.B.mp_plan_query(self.plan, what)
+
+    def decode(self, y, eps, T, trace_cap=None, raise_on_error=True):
+        """Decode one signal; returns dict(status, result, x, atoms, coefs, energies, r)."""
+        torch = torch_mod()
+        B = self.B
+        yd = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32)).cuda()
+        x = torch.full((self.M,), float("nan"), dtype=torch.float32, device="cuda")
+        cap = min(int(T), 200000) if trace_cap is None else int(trace_cap)
+        cap = max(cap, 1)
+        atoms = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+        coefs = torch.zeros(cap, dtype=torch.float32, device="cuda")
+        en = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        r = torch.full((self.N,), float("nan"), dtype=torch.float32, device="cuda")
+        tr = B.make_trace(atoms.data_ptr(), coefs.data_ptr(), en.data_ptr(), cap, r.data_ptr())
+        s, res = B.mp_recover(self.plan, yd.data_ptr(), x.data_ptr(), eps, T, tr, True, cur_stream(),
+                              raise_on_error=raise_on_error)
+        torch.cuda.synchronize()
+        n = min(res.iters, cap)
+        return dict(status=s, result=res, x=x.cpu().numpy(), atoms=atoms.cpu().numpy()[:n],
+                    coefs=coefs.cpu().numpy()[:n], energies=en.cpu().numpy()[:n], r=r.cpu().numpy())
+
+    def close(self):
+        if self.plan:
+            self.B.mp_plan_destroy(self.plan)
+            self.plan = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def first_near_tie(gaps):
+    idx = np.nonzero(np.asarray(gaps) <= GAP_TIE)[0]
+    return int(idx[0]) if idx.size else None
+
+
+def compare_to_oracle(psi, y, eps, T, gpu, ora=None, x_tol=1e-4, check_follow=True):
+    """Apply rules (i)-(iii); returns a dict of diagnostics, asserts on failure."""
+    from oracle import mp_oracle as orc
+    if ora is None:
+        ora = orc.mp(psi, y, eps, T)
+    res = gpu["result"]
+    ga = np.asarray(gpu["atoms"], dtype=np.int64)
+    oa = ora["atoms"]
+    tie = first_near_tie(ora["gaps"])
+    lim = len(oa) if tie is None else tie
+    n = min(lim, len(ga))
+    div = next((k for k in range(min(len(ga), len(oa))) if ga[k] != oa[k]), None)
+    assert np.array_equal(ga[:n], oa[:n]), f"atom sequence diverges at {div} before first near-tie {tie}"
+    if tie is None and div is None:
+        if res.iters != ora["iters"]:
+            # only legitimate when the stop test sits at the rounding level
+            e_last = ora["energies"][min(res.iters, ora["iters"]) - 1] if ora["iters"] else ora["e0"]
+            thr2 = eps * eps * ora["e0"]
+            assert abs(e_last - thr2) <= 1e-3 * thr2, (res.iters, ora["iters"])
+    nx = np.linalg.norm(ora["x"])
+    xerr = np.linalg.norm(gpu["x"].astype(np.float64) - ora["x"]) / (nx if nx > 0 else 1.0)
+    assert xerr <= x_tol, f"x relative L2 error {xerr:.3e} > {x_tol}"
+    out = dict(first_divergence=div, first_near_tie=tie, x_rel_err=xerr, iters=res.iters,
+               oracle_iters=ora["iters"])
+    if check_follow and len(ga):
+        f = orc.follow(psi, y, ga)
+        P = np.asarray(psi, dtype=np.float64)
+        recon = gpu["x"].astype(np.float64) @ P
+        delta = np.linalg.norm(y.astype(np.float64) - recon - gpu["r"].astype(np.float64))
+        N = P.shape[1]
+        tol = np.maximum(1e-5, (2 * delta + 2 * N * 2.0 ** -24 * f["rnorm"]) / np.maximum(f["cmax"], 1e-300))
+        bad = np.nonzero(f["ratio"] < 1 - tol)[0]
+        assert bad.size == 0, f"follow ratio below bound at steps {bad[:5]}: {f['ratio'][bad[:5]]}"
+        out.update(min_ratio=float(f["ratio"].min()), drift=float(delta))
+    return out

@@ -1,0 +1,76 @@
+"""CPU checks of the C ABI: the library builds, loads without a GPU, and
+exports every function include/mpgb.h declares (no compute calls)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mpgb.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"MPGB_API\s+[\w\s\*]+?\b(mp_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_0809_1833_gb300 import build
+    return build.build()
+
+
+def test_header_declares_api():
+    names = declared_functions()
+    for must in ("mp_plan_create", "mp_plan_destroy", "mp_recover", "mp_recover_batched",
+                 "mp_status_string", "mp_last_error_message"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT\s+(mp_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    # nothing undeclared leaks out
+    assert exported <= set(declared_functions()), exported - set(declared_functions())
+
+
+def test_loads_without_gpu_and_binding_covers_header(libpath):
+    L = ctypes.CDLL(libpath)
+    for n in declared_functions():
+        assert hasattr(L, n)
+    from paper_0809_1833_gb300 import binding as B
+    assert set(B.SIGNATURES) == set(declared_functions())
+
+
+def test_status_strings(libpath):
+    from paper_0809_1833_gb300 import binding as B
+    assert B.status_name(B.MP_OK) == "MP_OK"
+    assert B.status_name(B.MP_ERR_TIMEOUT) == "MP_ERR_TIMEOUT"
+    assert B.status_name(12345) == "MP_UNKNOWN_STATUS"
+
+
+def test_null_arguments_rejected_on_host(libpath):
+    """Argument checks happen before any CUDA call."""
+    from paper_0809_1833_gb300 import binding as B
+    L = B.lib()
+    assert L.mp_plan_create(None, None, None, None) == B.MP_ERR_INVALID
+    h = ctypes.c_void_p()
+    d = B.mp_plan_desc(0, 5, 0, 0, 0, 0)
+    assert L.mp_plan_create(ctypes.byref(h), ctypes.byref(d), ctypes.c_void_p(16), None) == B.MP_ERR_INVALID
+    assert "N and M" in B.last_error()
+    d = B.mp_plan_desc(4, 5, 7, 0, 0, 0)
+    assert L.mp_plan_create(ctypes.byref(h), ctypes.byref(d), ctypes.c_void_p(16), None) == B.MP_ERR_INVALID
+    assert L.mp_recover(None, None, None, None, None, None, None) == B.MP_ERR_INVALID
+    assert L.mp_plan_destroy(None) == B.MP_OK
+
+
+def test_header_compiles_as_c(tmp_path):
+    c = tmp_path / "t.c"
+    c.write_text('#include "mpgb.h"\nint main(void){mp_result r; (void)r; return (int)sizeof(mp_plan_desc) == 0;}\n')
+    p = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        "-c", str(c), "-o", str(tmp_path / "t.o")], capture_output=True, text=True)
+    assert p.returncode == 0, p.stderr
