@@ -107,19 +107,11 @@ MP_DEV uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
     return r;
 }
-MP_DEV void dsmem_max_u64(uint32_t cluster_addr, uint64_t v) {
-    asm volatile("red.relaxed.cluster.shared::cluster.max.u64 [%0], %1;" ::"r"(cluster_addr), "l"(v)
-                 : "memory");
-}
 MP_DEV uint64_t dsmem_ld_u64(uint32_t cluster_addr) {
     uint64_t v;
     asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(cluster_addr) : "memory");
     return v;
 }
-MP_DEV void dsmem_st_u64(uint32_t cluster_addr, uint64_t v) {
-    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(cluster_addr), "l"(v) : "memory");
-}
-
 // ---------------------------------------------------------------- global atomics
 MP_DEV void red_release_add_u64(unsigned long long* p, unsigned long long v) {
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");

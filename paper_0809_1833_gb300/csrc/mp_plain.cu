@@ -5,8 +5,9 @@
 // residual r in shared memory.  Per iteration:
 //   1. correlate  c_m = <r, psi_m> for the CTA's atoms       (Eq. 9)
 //   2. select     the CTA's best packed key (|c|, -m, sign)  (Eq. 9, Sec. 4 ties)
-//   3. exchange   the grid-wide max key (cluster DSMEM atomics + hardware
-//                 cluster barrier, or global atomics + a bounded grid barrier)
+//   3. exchange   the grid-wide max key (a hardware cluster barrier, then one
+//                 warp reads every CTA's key over DSMEM; or global atomics and
+//                 a bounded grid barrier)
 //   4. update     every CTA applies r -= c psi_m* to its own copy of r
 //                 (identical arithmetic in every CTA, so all copies stay
 //                 bit-identical) and reduces e = sum r^2 in FP64   (Eq. 11)
@@ -35,7 +36,7 @@ constexpr int kMaxStages = 64;
 constexpr int kResidentThreads = 256;
 
 struct PlainShared {
-    unsigned long long keys[4];          // mode 1: key slots (rank 0's copy is used)
+    unsigned long long keys[2];          // mode 1: this CTA's key, two-slot ring
     unsigned long long wkey[kMaxWarps];  // per compute warp best key
     double wsum[kMaxWarps];              // per compute warp energy partial
     unsigned long long key;              // selected key broadcast
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
     const int na = base + (cta < rem ? 1 : 0);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 4; ++i) sh->keys[i] = 0ull;
+        sh->keys[0] = sh->keys[1] = 0ull;
         sh->abort = 0;
         sh->done = 0;
         if (STREAM) {
@@ -224,7 +225,6 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
         }
     }
     __syncthreads();
-    if (CLUSTER) cluster_sync_all();  // rank 0's key slots are zero before any remote max
 
     if (STREAM && warp == 0) {
         if (lane == 0) plain_producer(a, sh, data, a0, na);
@@ -300,7 +300,10 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
             unsigned long long k = 0ull;
             for (int w = 0; w < ncw; ++w) k = umax64(k, sh->wkey[w]);
             if (CLUSTER) {
-                dsmem_max_u64(mapa_shared(smem_u32(&sh->keys[t % 3]), 0), k);
+                // own slot of a two-slot ring: peers read slot t&1 after this
+                // iteration's cluster barrier and before arriving at the next
+                // one; this CTA rewrites it only at iteration t+2
+                sh->keys[t & 1] = k;
             } else {
                 unsigned long long g = 0ull;
                 if (!grid_exchange(a, cta, G, t, k, &g)) *reinterpret_cast<volatile int*>(&sh->abort) = 1;
@@ -309,9 +312,13 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
         }
         if (CLUSTER) {
             cluster_sync_all();
-            if (ct == 0) {
-                sh->key = dsmem_ld_u64(mapa_shared(smem_u32(&sh->keys[t % 3]), 0));
-                if (cta == 0) sh->keys[(t + 2) % 3] = 0ull;
+            if (cw == 0) {
+                // lane k reads CTA k's key over DSMEM; the warp max is the
+                // cluster's key (the same value in every CTA)
+                unsigned long long v = 0ull;
+                if (lane < G) v = dsmem_ld_u64(mapa_shared(smem_u32(&sh->keys[t & 1]), lane));
+                v = warp_max_u64(v);
+                if (lane == 0) sh->key = v;
             }
         }
         named_bar_sync(1, nct);
@@ -372,7 +379,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
         res.stop_reason = e0 == 0.0 ? MP_STOP_ZERO_Y : (e <= thr2 ? MP_STOP_CONVERGED : MP_STOP_MAX_ITERS);
         res.status = !finite0 ? MP_ERR_NONFINITE : (aborted ? MP_ERR_TIMEOUT : MP_OK);
     }
-    if (CLUSTER) cluster_sync_all();  // keep rank 0's key slots alive until all are done
+    if (CLUSTER) cluster_sync_all();  // peers may still read this CTA's key slot
 }
 
 // ------------------------------------------------------------------ host side

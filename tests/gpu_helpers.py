@@ -2,21 +2,35 @@
 compare it with the FP64 oracle by the comparison rule for MP results.
 
 Comparison rule (several MP paths are correct at a near tie, so only what is
-unique is compared exactly):
+unique is compared exactly).  With tol_k the FP32 error bound of step k,
+
+    tol_k = max(1e-5, (2 Delta + 2 gamma_d ||r_k||) / max_m |c_m,k|),
+
+where Delta = ||r_gpu - r_replay|| is the drift between the GPU's final FP32
+residual and an FP64 replay of the GPU's own atom sequence, and
+gamma_d ||r_k|| (gamma_d = d 2^-24, d the depth of the kernel's summation
+tree) bounds one FP32 dot product's rounding for a unit atom:
   (i)   the selected-atom sequence equals the oracle's on the prefix up to
-        the first step whose oracle top-two gap is <= 1e-5 relative (the
-        whole sequence when there is no such step);
+        the first step whose oracle top-two gap is <= tol_k (the whole
+        sequence when there is no such step).  The floor 1e-5 is the
+        literal near-tie threshold; above it the FP32 rounding itself can
+        decide the order of two correlations, and either atom is an MP step;
   (ii)  x~ is within ``x_tol`` relative L2 of the oracle's x~;
   (iii) replaying the GPU's sequence in FP64, every selected atom is an MP
-        choice up to the FP32 error: ratio_k >= 1 - tol_k, with
-        tol_k = max(1e-5, (2 ||delta|| + 2 N 2^-24 ||r_k||) / max|c_k|) where
-        delta = y - Psi x~_gpu - r_gpu is the accumulated FP32 drift
-        (measured in FP64) and N 2^-24 ||r_k|| bounds one FP32 dot product's
-        rounding for unit atoms.
+        choice up to the FP32 error: ratio_k >= 1 - tol_k.
 """
 import numpy as np
 
 GAP_TIE = 1e-5
+U32 = 2.0 ** -24
+
+
+def summation_depth(N):
+    """Depth of the FP32 summation tree of one correlation: one FMA chain
+    per lane over the 128-float segments, two combining adds, and a 5-level
+    warp butterfly."""
+    ld = (N + 31) // 32 * 32
+    return (ld + 127) // 128 + 7
 
 
 def torch_mod():
@@ -91,37 +105,52 @@ def first_near_tie(gaps):
 
 
 def compare_to_oracle(psi, y, eps, T, gpu, ora=None, x_tol=1e-4, check_follow=True):
-    """Apply rules (i)-(iii); returns a dict of diagnostics, asserts on failure."""
+    """Apply rules (i)-(iii); returns a dict of diagnostics, asserts on failure.
+    ``check_follow=False`` skips the FP64 replay when the whole sequence and
+    the iteration count already match the oracle literally."""
     from oracle import mp_oracle as orc
     if ora is None:
         ora = orc.mp(psi, y, eps, T)
     res = gpu["result"]
     ga = np.asarray(gpu["atoms"], dtype=np.int64)
     oa = ora["atoms"]
-    tie = first_near_tie(ora["gaps"])
+    N = np.asarray(psi).shape[1]
+    div = next((k for k in range(min(len(ga), len(oa))) if ga[k] != oa[k]), None)
+    literal = div is None and len(ga) == len(oa)
+    out = dict(first_divergence=div, iters=res.iters, oracle_iters=ora["iters"])
+    Delta = 0.0
+    f = None
+    if (check_follow or not literal) and len(ga):
+        f = orc.follow(psi, y, ga)
+        Delta = float(np.linalg.norm(gpu["r"].astype(np.float64) - f["r"]))
+        out["drift"] = Delta
+    gamma = summation_depth(N) * U32
+    if len(oa):
+        rk = np.sqrt(np.concatenate([[ora["e0"]], ora["energies"][:-1]]))
+        tol = np.maximum(GAP_TIE, (2 * Delta + 2 * gamma * rk) / np.maximum(np.abs(ora["coefs"]), 1e-300))
+        ties = np.nonzero(ora["gaps"] <= tol)[0]
+        tie = int(ties[0]) if ties.size else None
+    else:
+        tie = None
+    out["first_near_tie"] = tie
     lim = len(oa) if tie is None else tie
     n = min(lim, len(ga))
-    div = next((k for k in range(min(len(ga), len(oa))) if ga[k] != oa[k]), None)
     assert np.array_equal(ga[:n], oa[:n]), f"atom sequence diverges at {div} before first near-tie {tie}"
-    if tie is None and div is None:
-        if res.iters != ora["iters"]:
-            # only legitimate when the stop test sits at the rounding level
-            e_last = ora["energies"][min(res.iters, ora["iters"]) - 1] if ora["iters"] else ora["e0"]
-            thr2 = eps * eps * ora["e0"]
-            assert abs(e_last - thr2) <= 1e-3 * thr2, (res.iters, ora["iters"])
+    if div is None and tie is None and res.iters != ora["iters"]:
+        # only legitimate when the stop test sits at the rounding level:
+        # the GPU's FP32 energy differs from the FP64 one by ~2 ||r|| Delta
+        k = min(res.iters, ora["iters"])
+        e_k = ora["energies"][k - 1] if k else ora["e0"]
+        thr2 = eps * eps * ora["e0"]
+        slack = 4 * np.sqrt(e_k) * Delta + 4 * gamma * e_k + 1e-9 * thr2
+        assert abs(e_k - thr2) <= slack, (res.iters, ora["iters"], e_k, thr2, slack)
     nx = np.linalg.norm(ora["x"])
     xerr = np.linalg.norm(gpu["x"].astype(np.float64) - ora["x"]) / (nx if nx > 0 else 1.0)
     assert xerr <= x_tol, f"x relative L2 error {xerr:.3e} > {x_tol}"
-    out = dict(first_divergence=div, first_near_tie=tie, x_rel_err=xerr, iters=res.iters,
-               oracle_iters=ora["iters"])
-    if check_follow and len(ga):
-        f = orc.follow(psi, y, ga)
-        P = np.asarray(psi, dtype=np.float64)
-        recon = gpu["x"].astype(np.float64) @ P
-        delta = np.linalg.norm(y.astype(np.float64) - recon - gpu["r"].astype(np.float64))
-        N = P.shape[1]
-        tol = np.maximum(1e-5, (2 * delta + 2 * N * 2.0 ** -24 * f["rnorm"]) / np.maximum(f["cmax"], 1e-300))
-        bad = np.nonzero(f["ratio"] < 1 - tol)[0]
+    out["x_rel_err"] = xerr
+    if f is not None:
+        tolf = np.maximum(GAP_TIE, (2 * Delta + 2 * gamma * f["rnorm"]) / np.maximum(f["cmax"], 1e-300))
+        bad = np.nonzero(f["ratio"] < 1 - tolf)[0]
         assert bad.size == 0, f"follow ratio below bound at steps {bad[:5]}: {f['ratio'][bad[:5]]}"
-        out.update(min_ratio=float(f["ratio"].min()), drift=float(delta))
+        out["min_ratio"] = float(f["ratio"].min())
     return out
