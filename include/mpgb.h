@@ -135,7 +135,9 @@ typedef enum {
     MP_OPT_DEBUG_SKIP_ARRIVE = 3, /* grid modes: this CTA never arrives at the first */
                                /* grid barrier (watchdog test), -1 = off             */
     MP_OPT_GRID_CTAS = 4,      /* grid modes: CTA count (0 = one per SM)             */
-    MP_OPT_BATCH_TILE_N = 5    /* batched: atoms per GEMM tile (0 = autotuned)       */
+    MP_OPT_BATCH_TILE_N = 5,   /* batched: atoms per GEMM tile (0 = autotuned)       */
+    MP_OPT_PLAIN_PREFETCH = 6  /* grid streaming: stages pulled into L2 ahead of the */
+                               /* shared-memory ring (0 = off, default 16)           */
 } mp_option;
 
 /* Read-only plan properties for mp_plan_query. */
@@ -239,12 +241,25 @@ MPGB_API mp_status mp_recover_host(mp_plan_t plan, const float* y_host, float* x
  *  Y        : device pointer, B x N floats, row b is y_b.
  *  X        : device pointer, B x M floats, row b receives x~_b.
  *  stops    : n_stops entries, 1 (shared) or B (per signal).
+ *  trace    : optional; each array holds B rows of `capacity` entries
+ *             (row b records signal b's steps; `residual` is ignored).
  *  host_out : B results (required); the call synchronises `stream`.
+ * The plan keeps the batch state (residuals, quantised GEMM operand, slot
+ * table, candidate buffer) between calls and grows it to the largest B.
  * Errors: MP_ERR_INVALID, MP_ERR_UNSUPPORTED (precision not built),
- * MP_ERR_NOMEM, MP_ERR_CUDA, MP_ERR_TIMEOUT. */
+ * MP_ERR_NOMEM, MP_ERR_CUDA, MP_ERR_TIMEOUT, MP_ERR_NONFINITE (a signal). */
 MPGB_API mp_status mp_recover_batched(mp_plan_t plan, int prec, const float* Y, float* X, int B,
-                             const mp_stop* stops, int n_stops, mp_result* host_out,
-                             void* stream);
+                             const mp_stop* stops, int n_stops, const mp_trace* trace,
+                             mp_result* host_out, void* stream);
+
+/* Diagnostic: the tensor-core correlations of the batched path, written out
+ * in full.  R (device, B x N floats) is quantised as the batched step does
+ * (BF16, or E4M3 with per-row scale max|r|/448) and C (device, B x M floats)
+ * receives the FP32-accumulated correlations of R with the plan's BF16 or
+ * FP8 atoms, rescaled by the FP8 per-atom and per-row scales.  Synchronises
+ * `stream`.  For tests of the GEMM; the decode paths never write C. */
+MPGB_API mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B, float* C,
+                                void* stream);
 
 #ifdef __cplusplus
 }

@@ -35,6 +35,7 @@ MP_OPT_WATCHDOG_NS = 2
 MP_OPT_DEBUG_SKIP_ARRIVE = 3
 MP_OPT_GRID_CTAS = 4
 MP_OPT_BATCH_TILE_N = 5
+MP_OPT_PLAIN_PREFETCH = 6
 
 MP_Q_PLAIN_MODE = 1
 MP_Q_PLAIN_CTAS = 2
@@ -92,7 +93,8 @@ SIGNATURES = {
     "mp_plan_last_result": (_I, [_P, ctypes.POINTER(mp_result)]),
     "mp_recover_host": (_I, [_P, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_result)]),
     "mp_recover_batched": (_I, [_P, _I, _P, _P, _I, ctypes.POINTER(mp_stop), _I,
-                                ctypes.POINTER(mp_result), _P]),
+                                ctypes.POINTER(mp_trace), ctypes.POINTER(mp_result), _P]),
+    "mp_debug_correlations": (_I, [_P, _I, _P, _I, _P, _P]),
 }
 
 _LIB = None
@@ -197,7 +199,7 @@ def mp_recover_host(plan, y_host, x_host, eps, max_iters, raise_on_error=True):
     return s, res
 
 
-def mp_recover_batched(plan, prec, Y_ptr, X_ptr, B, stops, stream=None, raise_on_error=True):
+def mp_recover_batched(plan, prec, Y_ptr, X_ptr, B, stops, trace=None, stream=None, raise_on_error=True):
     """Batched decode; ``stops`` is one (eps, T) pair or a list of B pairs.
     Returns (status, list of mp_result)."""
     if isinstance(stops, tuple):
@@ -205,7 +207,15 @@ def mp_recover_batched(plan, prec, Y_ptr, X_ptr, B, stops, stream=None, raise_on
     arr = (mp_stop * len(stops))(*[mp_stop(float(e), int(t), 0) for e, t in stops])
     res = (mp_result * max(int(B), 1))()
     s = lib().mp_recover_batched(plan, int(prec), ctypes.c_void_p(int(Y_ptr)), ctypes.c_void_p(int(X_ptr)),
-                                 int(B), arr, len(stops), res, _stream(stream))
+                                 int(B), arr, len(stops), ctypes.byref(trace) if trace is not None else None,
+                                 res, _stream(stream))
     if raise_on_error:
         check(s, "mp_recover_batched")
     return s, list(res)[:int(B)]
+
+
+def mp_debug_correlations(plan, prec, R_ptr, B, C_ptr, stream=None):
+    """Tensor-core correlations of B residuals (diagnostic)."""
+    return check(lib().mp_debug_correlations(plan, int(prec), ctypes.c_void_p(int(R_ptr)), int(B),
+                                             ctypes.c_void_p(int(C_ptr)), _stream(stream)),
+                 "mp_debug_correlations")

@@ -76,6 +76,11 @@ MP_DEV void bulk_g2s_evict_first(void* dst, const void* src, uint32_t bytes, uin
         "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
 }
+// Fire-and-forget prefetch of [src, src+bytes) into L2 (16-byte aligned,
+// bytes a multiple of 16).
+MP_DEV void prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 MP_DEV uint64_t policy_evict_first() {
     uint64_t p;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));

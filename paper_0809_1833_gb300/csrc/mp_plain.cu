@@ -27,6 +27,7 @@
 #include <cstring>
 
 #include "mp_device.cuh"
+#include "mp_dot.cuh"
 #include "mp_internal.h"
 
 namespace mpgb {
@@ -53,6 +54,7 @@ struct PlainArgs {
     int N, ldN, M, T;
     double eps2;
     int stage_atoms, stages;
+    int prefetch;          // mode 3: L2 prefetch distance in stages (0 = off)
     int off_sh, off_data;
     PlainWorkspace* ws;
     int* tr_atoms;
@@ -65,45 +67,6 @@ struct PlainArgs {
 };
 
 // ------------------------------------------------------------------ dots
-// Canonical per-atom summation order (every mode and group size gives the
-// same bits): lane l accumulates components x,y,z,w of segment elements
-// 4l..4l+3 of each 128-float segment in four FMA chains, combines them as
-// (x+y)+(z+w), then a butterfly sum across the warp.
-MP_DEV float dot1(const float* __restrict__ p, const float* __restrict__ r, int ldN, int lane) {
-    float ax = 0.f, ay = 0.f, az = 0.f, aw = 0.f;
-#pragma unroll 4
-    for (int off = lane * 4; off < ldN; off += 128) {
-        const float4 q = *reinterpret_cast<const float4*>(r + off);
-        const float4 v = *reinterpret_cast<const float4*>(p + off);
-        ax = fmaf(v.x, q.x, ax);
-        ay = fmaf(v.y, q.y, ay);
-        az = fmaf(v.z, q.z, az);
-        aw = fmaf(v.w, q.w, aw);
-    }
-    return warp_sum_f32((ax + ay) + (az + aw));
-}
-
-MP_DEV void dot4(const float* __restrict__ p, const float* __restrict__ r, int ldN, int lane,
-                 float out[4]) {
-    float a[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) a[i][0] = a[i][1] = a[i][2] = a[i][3] = 0.f;
-#pragma unroll 2
-    for (int off = lane * 4; off < ldN; off += 128) {
-        const float4 q = *reinterpret_cast<const float4*>(r + off);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float4 v = *reinterpret_cast<const float4*>(p + static_cast<size_t>(i) * ldN + off);
-            a[i][0] = fmaf(v.x, q.x, a[i][0]);
-            a[i][1] = fmaf(v.y, q.y, a[i][1]);
-            a[i][2] = fmaf(v.z, q.z, a[i][2]);
-            a[i][3] = fmaf(v.w, q.w, a[i][3]);
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) out[i] = warp_sum_f32((a[i][0] + a[i][1]) + (a[i][2] + a[i][3]));
-}
-
 // Scan `n` consecutive atoms at p (first index m0) and fold into `best`.
 MP_DEV unsigned long long scan_atoms(const float* __restrict__ p, const float* __restrict__ r,
                                      int ldN, int n, int m0, int lane, unsigned long long best) {
@@ -179,6 +142,14 @@ MP_DEV void plain_producer(const PlainArgs& a, PlainShared* sh, float* ring, int
         mbar_arrive_expect_tx(&sh->full[slot], bytes);
         bulk_g2s_evict_first(ring + slot * stage_floats, a.psi + static_cast<size_t>(atom0) * ldN,
                              bytes, &sh->full[slot], pol);
+        // L2 as a deeper window than the shared-memory ring: pull the stage
+        // `prefetch` positions ahead into L2 now, so HBM keeps streaming
+        // while the ring is full during the per-iteration exchange.
+        if (a.prefetch > 0) {
+            const int jp = static_cast<int>((seq + a.prefetch) % S);
+            const int np = min(A, na - jp * A);
+            prefetch_l2(a.psi + static_cast<size_t>(a0 + jp * A) * ldN, static_cast<uint32_t>(np) * ldN * 4u);
+        }
         ++seq;
     }
     // Wait for every copy still in flight before the CTA may exit: the only
@@ -306,6 +277,9 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
                 sh->keys[t & 1] = k;
             } else {
                 unsigned long long g = 0ull;
+                // the grid's winner is one of the CTAs' local bests: start
+                // pulling this one into L2 for the residual update
+                if (k != 0ull) prefetch_l2(a.psi + static_cast<size_t>(key_index(k)) * ldN, ldN * 4u);
                 if (!grid_exchange(a, cta, G, t, k, &g)) *reinterpret_cast<volatile int*>(&sh->abort) = 1;
                 sh->key = g;
             }
@@ -526,6 +500,7 @@ mp_status plain_launch(PlanImpl* p, const float* y, float* x, const mp_stop* sto
     a.eps2 = stop->eps * stop->eps;
     a.stage_atoms = cfg.stage_atoms;
     a.stages = cfg.stages;
+    a.prefetch = cfg.mode == 3 ? p->prefetch_stages : 0;
     a.off_sh = cfg.off_sh;
     a.off_data = cfg.off_data;
     a.ws = ws;

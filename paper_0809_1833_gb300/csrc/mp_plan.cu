@@ -273,6 +273,10 @@ mp_status mp_plan_set_option(mp_plan_t plan, int option, long long value) {
             if (value < 0) return fail(MP_ERR_INVALID, "grid CTA count must be >= 0");
             p->grid_ctas = static_cast<int>(value);
             return MP_OK;
+        case MP_OPT_PLAIN_PREFETCH:
+            if (value < 0 || value > 256) return fail(MP_ERR_INVALID, "prefetch distance must be 0..256");
+            p->prefetch_stages = static_cast<int>(value);
+            return MP_OK;
         case MP_OPT_BATCH_TILE_N:
             if (value != 0 && value != 128 && value != 256)
                 return fail(MP_ERR_INVALID, "batch tile must be 0, 128 or 256");

@@ -1,0 +1,141 @@
+"""Batched decode (mp_recover_batched) on the tensor cores.
+
+* The tcgen05 GEMM is checked element by element (mp_debug_correlations)
+  against an FP64 product of the same quantised operands.
+* The batched MP result is compared with the FP32 persistent kernel: the
+  rescore uses the same FP32 correlation order, so whenever the FP32 argmax
+  is among the 8 low-precision candidates the batched path reproduces the
+  plain path bit for bit; and every signal meets the oracle rule.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import GpuPlan, compare_to_oracle, cur_stream
+from oracle import mp_oracle as orc
+from paper_0809_1833_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def B():
+    from paper_0809_1833_gb300 import binding
+    return binding
+
+
+def torch():
+    import torch as t
+    return t
+
+
+def bf16_round(a):
+    T = torch()
+    return T.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(T.bfloat16).to(T.float32).numpy()
+
+
+def e4m3_rows(a):
+    """Per-row E4M3 quantisation as the library defines it: scale
+    s = max|row| / 448 (FP32), codes = RNE_e4m3(row * (448 / max|row|))."""
+    T = torch()
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    amax = np.max(np.abs(a), axis=1).astype(np.float32)
+    inv = np.where(amax > 0, np.float32(448.0) / np.where(amax > 0, amax, 1), np.float32(1)).astype(np.float32)
+    q = T.from_numpy((a * inv[:, None]).astype(np.float32)).to(T.float8_e4m3fn).to(T.float32).numpy()
+    s = np.where(amax > 0, amax / np.float32(448.0), np.float32(1)).astype(np.float32)
+    return q.astype(np.float64), s.astype(np.float64)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("shape", [(256, 1000, 200), (100, 300, 5), (2048, 1024, 130)],
+                         ids=lambda s: f"N{s[0]}_M{s[1]}_B{s[2]}")
+def test_tensor_core_correlations(prec, shape):
+    T = torch()
+    N, M, Bn = shape
+    psi = W.gaussian_dictionary(N, M, seed=3)
+    rng = np.random.default_rng([N, M, Bn])
+    R = rng.standard_normal((Bn, N)).astype(np.float32)
+    p = B().MP_PREC_BF16 if prec == "bf16" else B().MP_PREC_FP8E4M3
+    with GpuPlan(psi, prec_mask=1 << p) as pl:
+        Rd = T.from_numpy(R).cuda()
+        C = T.full((Bn, M), float("nan"), dtype=T.float32, device="cuda")
+        B().mp_debug_correlations(pl.plan, p, Rd.data_ptr(), Bn, C.data_ptr(), cur_stream())
+        C = C.cpu().numpy().astype(np.float64)
+    if prec == "bf16":
+        A = bf16_round(R).astype(np.float64)
+        P = bf16_round(psi).astype(np.float64)
+        ref = A @ P.T
+        mag = np.abs(A) @ np.abs(P).T
+    else:
+        qa, sa = e4m3_rows(R)
+        qp, sp = e4m3_rows(psi)
+        ref = (qa @ qp.T) * sa[:, None] * sp[None, :]
+        mag = (np.abs(qa) @ np.abs(qp).T) * sa[:, None] * sp[None, :]
+    # FP32 accumulation of exact products: |err| <= K 2^-24 sum|products| (+ scaling)
+    tol = (N + 8) * 2.0 ** -24 * mag + 1e-30
+    err = np.abs(C - ref)
+    assert np.all(np.isfinite(C))
+    assert np.all(err <= tol), f"max err/tol {np.max(err / tol):.3g}"
+
+
+def run_batched(pl, prec, Y, stops, cap=4096):
+    T = torch()
+    Bn, N = Y.shape
+    Yd = T.from_numpy(np.ascontiguousarray(Y, dtype=np.float32)).cuda()
+    X = T.full((Bn, pl.M), float("nan"), dtype=T.float32, device="cuda")
+    atoms = T.full((Bn, cap), -1, dtype=T.int32, device="cuda")
+    coefs = T.zeros((Bn, cap), dtype=T.float32, device="cuda")
+    tr = B().make_trace(atoms.data_ptr(), coefs.data_ptr(), 0, cap)
+    s, res = B().mp_recover_batched(pl.plan, prec, Yd.data_ptr(), X.data_ptr(), Bn, stops, tr, cur_stream(),
+                                    raise_on_error=False)
+    T.cuda.synchronize()
+    return s, res, X.cpu().numpy(), atoms.cpu().numpy(), coefs.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_batched_matches_plain_and_oracle(prec):
+    prob = W.make_batched(256, 1024, 300, 2, 16, seed=5, eps=1e-5, T=3000)
+    p = B().MP_PREC_BF16 if prec == "bf16" else B().MP_PREC_FP8E4M3
+    with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
+        s, res, X, atoms, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
+        assert s == 0
+        n_same = 0
+        for b in range(prob.B):
+            r = res[b]
+            assert r.status == 0 and r.stop_reason == B().MP_STOP_CONVERGED
+            plain = pl.decode(prob.y[b], prob.eps, prob.T)
+            if (r.iters == plain["result"].iters and np.array_equal(atoms[b, :r.iters], plain["atoms"])):
+                assert np.array_equal(X[b], plain["x"]), b
+                n_same += 1
+            out = dict(result=r, x=X[b], atoms=atoms[b, :r.iters], r=plain["r"])
+            if b % 10 == 0:   # full oracle rule on a sample of the signals
+                ora = orc.mp(prob.psi, prob.y[b], prob.eps, prob.T)
+                compare_to_oracle(prob.psi, prob.y[b], prob.eps, prob.T, out, ora=ora, check_follow=False)
+                assert orc.support_score(X[b], prob.supports[b]) == 1.0
+        # the 8-candidate rescore recovers the FP32 choice at (nearly) every step
+        assert n_same >= prob.B - 3, n_same
+
+
+def test_batched_edge_cases():
+    psi = W.gaussian_dictionary(64, 300, seed=2)
+    prob = W.make_batched(64, 300, 6, 1, 3, seed=2, psi=psi, eps=1e-5, T=500)
+    Y = prob.y.copy()
+    Y[1] = 0.0                  # y = 0
+    Y[3, 7] = np.nan            # non-finite signal
+    stops = [(1e-5, 500), (1e-5, 500), (1e-5, 0), (1e-5, 500), (2.0, 500), (0.0, 9)]
+    p = B().MP_PREC_BF16
+    with GpuPlan(psi, prec_mask=1 << p) as pl:
+        s, res, X, atoms, _ = run_batched(pl, p, Y, stops)
+        assert s == B().MP_ERR_NONFINITE
+        assert res[1].iters == 0 and res[1].stop_reason == B().MP_STOP_ZERO_Y and not np.any(X[1])
+        assert res[2].iters == 0 and res[2].stop_reason == B().MP_STOP_MAX_ITERS and not np.any(X[2])
+        assert res[3].status == B().MP_ERR_NONFINITE and res[3].iters == 0
+        assert res[4].iters == 0 and res[4].stop_reason == B().MP_STOP_CONVERGED
+        assert res[5].iters == 9 and res[5].stop_reason == B().MP_STOP_MAX_ITERS
+        for b in (0, 5):
+            ora = orc.mp(psi, Y[b], stops[b][0], stops[b][1])
+            assert list(atoms[b, :res[b].iters]) == list(ora["atoms"])
+        # a second call on the same plan (state reuse), B = 1
+        s, res1, X1, _, _ = run_batched(pl, p, prob.y[:1], (1e-5, 500))
+        assert s == 0 and res1[0].iters == res[0].iters and np.array_equal(X1[0], X[0])
+        # precision that the plan does not hold
+        s, _, _, _, _ = run_batched(pl, B().MP_PREC_FP8E4M3, prob.y[:1], (1e-5, 500))
+        assert s == B().MP_ERR_UNSUPPORTED
