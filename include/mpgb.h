@@ -137,7 +137,7 @@ typedef enum {
     MP_OPT_GRID_CTAS = 4,      /* grid modes: CTA count (0 = one per SM)             */
     MP_OPT_BATCH_TILE_N = 5,   /* batched: atoms per GEMM tile (0 = autotuned)       */
     MP_OPT_PLAIN_PREFETCH = 6  /* grid streaming: stages pulled into L2 ahead of the */
-                               /* shared-memory ring (0 = off, default 16)           */
+                               /* shared-memory ring (0 = off, the default)          */
 } mp_option;
 
 /* Read-only plan properties for mp_plan_query. */

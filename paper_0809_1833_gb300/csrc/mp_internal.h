@@ -90,7 +90,7 @@ struct PlanImpl {
     int skip_cta = -1;
     int grid_ctas = 0;
     int batch_tile_n = 0;
-    int prefetch_stages = 16;       // plain streaming: L2 prefetch distance
+    int prefetch_stages = 0;        // plain streaming: L2 prefetch distance (measured slower; off)
 
     long long launches = 0;
     BatchEngine* batch = nullptr;
