@@ -95,6 +95,7 @@ SIGNATURES = {
     "mp_recover_batched": (_I, [_P, _I, _P, _P, _I, ctypes.POINTER(mp_stop), _I,
                                 ctypes.POINTER(mp_trace), ctypes.POINTER(mp_result), _P]),
     "mp_debug_correlations": (_I, [_P, _I, _P, _I, _P, _P]),
+    "mp_recover_noalloc": (_I, [_P, _I, _I, _I, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_result), _P]),
 }
 
 _LIB = None
@@ -212,6 +213,14 @@ def mp_recover_batched(plan, prec, Y_ptr, X_ptr, B, stops, trace=None, stream=No
     if raise_on_error:
         check(s, "mp_recover_batched")
     return s, list(res)[:int(B)]
+
+
+def mp_recover_noalloc(psi_ptr, N, M, ld, y_ptr, x_ptr, stop, result, stream=None):
+    """Allocation-free decode (include/mpgb_noalloc.h): ``stop`` is an
+    mp_stop, ``result`` an mp_result filled in place; returns the status."""
+    return lib().mp_recover_noalloc(ctypes.c_void_p(int(psi_ptr)), int(N), int(M), int(ld),
+                                    ctypes.c_void_p(int(y_ptr)), ctypes.c_void_p(int(x_ptr)), ctypes.byref(stop),
+                                    ctypes.byref(result), _stream(stream))
 
 
 def mp_debug_correlations(plan, prec, R_ptr, B, C_ptr, stream=None):

@@ -8,12 +8,16 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "mpgb.h")
+INCLUDE = os.path.join(ROOT, "include")
 
 
 def declared_functions():
-    src = open(HEADER).read()
-    return sorted(set(re.findall(r"MPGB_API\s+[\w\s\*]+?\b(mp_\w+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(INCLUDE)):
+        if h.endswith(".h"):
+            src = open(os.path.join(INCLUDE, h)).read()
+            names |= set(re.findall(r"MPGB_API\s+[\w\s\*]+?\b(mp_\w+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -70,7 +74,8 @@ def test_null_arguments_rejected_on_host(libpath):
 
 def test_header_compiles_as_c(tmp_path):
     c = tmp_path / "t.c"
-    c.write_text('#include "mpgb.h"\nint main(void){mp_result r; (void)r; return (int)sizeof(mp_plan_desc) == 0;}\n')
+    incs = "".join(f'#include "{h}"\n' for h in sorted(os.listdir(INCLUDE)) if h.endswith(".h"))
+    c.write_text(incs + "int main(void){mp_result r; (void)r; return (int)sizeof(mp_plan_desc) == 0;}\n")
     p = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
                         "-c", str(c), "-o", str(tmp_path / "t.o")], capture_output=True, text=True)
     assert p.returncode == 0, p.stderr
