@@ -302,10 +302,77 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(psi_np, Y_np[0], w["eps"], w["T"], iters[0], args.cpu_budget)
     B.mp_plan_destroy(plan)
+    if rank == 0 and not args.no_batched:
+        # batched low-precision form vs the plain FP32 kernel on the same signals
+        line["batched"] = [batched_measure("bf16"), batched_measure("fp8", n_plain=4)]
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+BATCHED = {"bf16": "batched_bf16_N2048_M8192_B1024", "fp8": "batched_fp8_N8192_M32768_B256"}
+
+
+def batched_measure(prec_name, reps=3, n_plain=16, profile=False):
+    """Batched low-precision decode of a whole batched workload vs the plain
+    FP32 kernel on the same signals (the first ``n_plain`` of them)."""
+    import torch
+    from oracle import mp_oracle as orc
+    from paper_0809_1833_gb300 import binding as B
+    from paper_0809_1833_gb300 import workloads as W
+    name = BATCHED[prec_name]
+    w = W.WORKLOADS[name]
+    prob = W.make_workload(name, seed=0)
+    prec = B.MP_PREC_BF16 if prec_name == "bf16" else B.MP_PREC_FP8E4M3
+    s = torch.cuda.current_stream().cuda_stream
+    d = torch.from_numpy(prob.psi).cuda()
+    plan = B.mp_plan_create(prob.N, prob.M, d.data_ptr(), prec_mask=1 << prec, stream=s)
+    del d
+    Y = torch.from_numpy(prob.y).cuda()
+    X = torch.empty((prob.B, prob.M), device="cuda")
+    stop = (w["eps"], w["T"])
+    B.mp_recover_batched(plan, prec, Y.data_ptr(), X.data_ptr(), prob.B, stop, None, s)   # builds the graph
+    if profile:
+        torch.cuda.synchronize()
+        B.mp_recover_batched(plan, prec, Y.data_ptr(), X.data_ptr(), prob.B, stop, None, s)
+        B.mp_plan_destroy(plan)
+        return {"profile_case": name}
+    times = []
+    l0 = B.mp_plan_query(plan, B.MP_Q_KERNEL_LAUNCHES)
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        _, res = B.mp_recover_batched(plan, prec, Y.data_ptr(), X.data_ptr(), prob.B, stop, None, s)
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b) / 1e3)
+    launches = (B.mp_plan_query(plan, B.MP_Q_KERNEL_LAUNCHES) - l0) // reps
+    tb = statistics.median(times)
+    iters = np.array([r.iters for r in res])
+    Xh = X.cpu().numpy()
+    supp_b = [orc.support_score(Xh[i], prob.supports[i]) for i in range(prob.B)]
+    xs = torch.empty(prob.M, device="cuda")
+    tp, supp_p = 0.0, []
+    for i in range(n_plain):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        B.mp_recover(plan, Y[i].data_ptr(), xs.data_ptr(), w["eps"], w["T"], None, False, s)
+        b.record()
+        torch.cuda.synchronize()
+        tp += a.elapsed_time(b) / 1e3
+        supp_p.append(orc.support_score(xs.cpu().numpy(), prob.supports[i]))
+    B.mp_plan_destroy(plan)
+    flops = 2.0 * prob.N * prob.M * float(iters.sum())
+    rec_b, rec_p = prob.B / tb, n_plain / tp
+    return {"workload": name, "precision": prec_name, "signals": prob.B, "recoveries_per_s": rec_b,
+            "ms_per_batch": 1e3 * tb, "plain_fp32_recoveries_per_s": rec_p, "speedup_vs_plain": rec_b / rec_p,
+            "plain_sample": f"first {n_plain} signals through mp_recover",
+            "support_score_mean": float(np.mean(supp_b)), "support_score_min": float(np.min(supp_b)),
+            "plain_support_score_mean": float(np.mean(supp_p)),
+            "iterations_total": int(iters.sum()), "iterations_max": int(iters.max()),
+            "effective_tflops": flops / tb / 1e12, "gpu_launches_per_batch": int(launches)}
 
 
 def run_profile_case(iters):
@@ -338,10 +405,17 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling case: one decode capped at this many iterations, then exit")
+    ap.add_argument("--profile-batched", choices=["bf16", "fp8"], default=None,
+                    help="profiling case: one batched decode of that workload, then exit")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    if args.profile:
+    if args.profile_batched:
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps(batched_measure(args.profile_batched, profile=True)))
+    elif args.profile:
         run_profile_case(args.profile)
     elif args.impl == "reference":
         run_reference(args)
