@@ -305,6 +305,8 @@ def run_ours(args):
     if rank == 0 and not args.no_batched:
         # batched low-precision form vs the plain FP32 kernel on the same signals
         line["batched"] = [batched_measure("bf16"), batched_measure("fp8", n_plain=4)]
+    if rank == 0 and args.served_duration > 0:
+        line["served"] = served_measure(args.served_rate, args.served_duration)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -375,6 +377,86 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False):
             "effective_tflops": flops / tb / 1e12, "gpu_launches_per_batch": int(launches)}
 
 
+def served_measure(rate=2000.0, duration=10.0, pool=48, seed=0, max_slots=256):
+    """Poisson arrivals over the four resident dictionaries of the served
+    workload; every request is submitted at its arrival time through the
+    server's C ABI and polled until done.  Reports offered / completed rates,
+    rejections and latency percentiles (server clock: submit -> result
+    ready; client clock: submit -> successful poll)."""
+    import torch
+    from paper_0809_1833_gb300 import binding as B
+    from paper_0809_1833_gb300 import workloads as W
+    wl = W.WORKLOADS["served_4dict_poisson2000"]
+    dicts = wl["dicts"]
+    prec = B.MP_PREC_BF16
+    s = torch.cuda.current_stream().cuda_stream
+    plans, pools = [], []
+    for di, (N, M) in enumerate(dicts):
+        psi = W.gaussian_dictionary(N, M, seed + 10 + di)
+        d = torch.from_numpy(psi).cuda()
+        plans.append(B.mp_plan_create(N, M, d.data_ptr(), prec_mask=1 << prec, stream=s))
+        del d
+        g = np.random.default_rng([seed, 50 + di])
+        ys = []
+        for k in range(pool):
+            K = int(g.integers(4, N // 16 + 1))
+            x, _ = W.sparse_signal(M, K, g, wl["values"])
+            ys.append(np.ascontiguousarray(W.encode(psi, x)))
+        pools.append(ys)
+    srv = B.mp_server_create(96 << 30, max_slots, 1 << 20)
+    ids = [B.mp_server_add_dictionary(srv, p, prec) for p in plans]
+    slots = [B.mp_server_dictionary_slots(srv, i) for i in ids]
+    arr, dsel, _ = W.served_requests(dicts, rate, duration, seed)
+    # warm-up: one request per dictionary
+    for di in range(len(dicts)):
+        _, t = B.mp_server_submit(srv, ids[di], pools[di][0], wl["eps"], wl["T"])
+        while B.mp_server_poll(srv, t)[0] == B.MP_PENDING:
+            time.sleep(0.001)
+    B.mp_server_reset_stats(srv)
+    pending, lat, rejected, n_sub = {}, [], 0, 0
+    t0 = time.perf_counter()
+    i, n = 0, len(arr)
+    while i < n or pending:
+        now = time.perf_counter() - t0
+        while i < n and arr[i] <= now:
+            di = int(dsel[i])
+            st, t = B.mp_server_submit(srv, ids[di], pools[di][i % pool], wl["eps"], wl["T"])
+            if st == 0:
+                pending[t] = now
+                n_sub += 1
+            else:
+                rejected += 1
+            i += 1
+        done = []
+        for t, ts in pending.items():
+            st, _ = B.mp_server_poll(srv, t)
+            if st == B.MP_OK:
+                done.append(t)
+                lat.append(time.perf_counter() - t0 - ts)
+            if len(done) >= 256:
+                break
+        for t in done:
+            del pending[t]
+        if now > duration + 120:
+            break
+        if not done and (i >= n or arr[i] > now + 5e-4):
+            time.sleep(2e-4)
+    wall = time.perf_counter() - t0
+    stt = B.mp_server_get_stats(srv)
+    B.mp_server_destroy(srv)
+    for p in plans:
+        B.mp_plan_destroy(p)
+    lat = np.array(lat)
+    return {"workload": "served_4dict_poisson2000", "dictionaries": [list(d) for d in dicts], "precision": "bf16",
+            "slots_per_dictionary": slots, "offered_rps": rate, "duration_s": duration, "requests": int(n),
+            "submitted": int(n_sub), "rejected": int(rejected), "rejected_pct": 100.0 * rejected / max(n, 1),
+            "completed": int(stt.completed), "completed_rps": float(stt.completed) / wall, "wall_s": wall,
+            "server_p50_ms": 1e3 * stt.latency_p50_s, "server_p99_ms": 1e3 * stt.latency_p99_s,
+            "client_p50_ms": 1e3 * float(np.percentile(lat, 50)) if lat.size else None,
+            "client_p99_ms": 1e3 * float(np.percentile(lat, 99)) if lat.size else None,
+            "signal_pool": f"{pool} distinct seeded signals per dictionary, K ~ U{{4..N/16}}, reused across requests"}
+
+
 def run_profile_case(iters):
     """Small case for ncu: the full-size dictionary, one decode capped at
     ``iters`` iterations (one launch of the streaming kernel)."""
@@ -408,7 +490,16 @@ def main():
     ap.add_argument("--profile-batched", choices=["bf16", "fp8"], default=None,
                     help="profiling case: one batched decode of that workload, then exit")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--served-duration", type=float, default=10.0,
+                    help="seconds of Poisson arrivals for the served measurement (0 = skip)")
+    ap.add_argument("--served-rate", type=float, default=2000.0)
+    ap.add_argument("--served-only", action="store_true", help="run only the served measurement")
     args = ap.parse_args()
+    if args.served_only:
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps(served_measure(args.served_rate, args.served_duration)))
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.profile_batched:

@@ -71,6 +71,17 @@ class mp_trace(ctypes.Structure):
                 ("residual", ctypes.c_void_p), ("capacity", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
+class mp_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("rejected", ctypes.c_longlong), ("admitted", ctypes.c_longlong),
+                ("completed", ctypes.c_longlong), ("queued", ctypes.c_longlong), ("active", ctypes.c_longlong),
+                ("latency_p50_s", ctypes.c_double), ("latency_p99_s", ctypes.c_double),
+                ("latency_mean_s", ctypes.c_double), ("latency_max_s", ctypes.c_double),
+                ("hbm_bytes", ctypes.c_size_t), ("chunks", ctypes.c_longlong), ("retired", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class MpError(RuntimeError):
     def __init__(self, status, where, message):
         super().__init__(f"{where}: {status_name(status)}: {message}")
@@ -96,6 +107,14 @@ SIGNATURES = {
                                 ctypes.POINTER(mp_trace), ctypes.POINTER(mp_result), _P]),
     "mp_debug_correlations": (_I, [_P, _I, _P, _I, _P, _P]),
     "mp_recover_noalloc": (_I, [_P, _I, _I, _I, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_result), _P]),
+    "mp_server_create": (_I, [ctypes.POINTER(_P), ctypes.c_size_t, _I, _I]),
+    "mp_server_add_dictionary": (_I, [_P, _P, _I, ctypes.POINTER(_I)]),
+    "mp_server_dictionary_slots": (_I, [_P, _I, ctypes.POINTER(_I)]),
+    "mp_server_submit": (_I, [_P, _I, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(ctypes.c_uint64)]),
+    "mp_server_poll": (_I, [_P, ctypes.c_uint64, _P, ctypes.POINTER(mp_result)]),
+    "mp_server_get_stats": (_I, [_P, ctypes.POINTER(mp_server_stats)]),
+    "mp_server_reset_stats": (_I, [_P]),
+    "mp_server_destroy": (_I, [_P]),
 }
 
 _LIB = None
@@ -228,3 +247,55 @@ def mp_debug_correlations(plan, prec, R_ptr, B, C_ptr, stream=None):
     return check(lib().mp_debug_correlations(plan, int(prec), ctypes.c_void_p(int(R_ptr)), int(B),
                                              ctypes.c_void_p(int(C_ptr)), _stream(stream)),
                  "mp_debug_correlations")
+
+
+# ---------------------------------------------------------------- server (include/mpgb_server.h)
+
+def mp_server_create(hbm_budget_bytes, max_slots, max_queue):
+    h = ctypes.c_void_p()
+    check(lib().mp_server_create(ctypes.byref(h), int(hbm_budget_bytes), int(max_slots), int(max_queue)),
+          "mp_server_create")
+    return h.value
+
+
+def mp_server_add_dictionary(srv, plan, prec):
+    d = ctypes.c_int()
+    check(lib().mp_server_add_dictionary(srv, plan, int(prec), ctypes.byref(d)), "mp_server_add_dictionary")
+    return d.value
+
+
+def mp_server_dictionary_slots(srv, dict_id):
+    n = ctypes.c_int()
+    check(lib().mp_server_dictionary_slots(srv, int(dict_id), ctypes.byref(n)), "mp_server_dictionary_slots")
+    return n.value
+
+
+def mp_server_submit(srv, dict_id, y_host, eps, max_iters):
+    """Returns (status, ticket); y_host is a contiguous float32 numpy array."""
+    st = mp_stop(float(eps), int(max_iters), 0)
+    t = ctypes.c_uint64()
+    s = lib().mp_server_submit(srv, int(dict_id), ctypes.c_void_p(y_host.ctypes.data), ctypes.byref(st),
+                               ctypes.byref(t))
+    return s, t.value
+
+
+def mp_server_poll(srv, ticket, x_host=None):
+    """Returns (status, mp_result or None); fills x_host (float32, M) when done."""
+    res = mp_result()
+    s = lib().mp_server_poll(srv, ctypes.c_uint64(ticket),
+                             ctypes.c_void_p(x_host.ctypes.data) if x_host is not None else None, ctypes.byref(res))
+    return s, (res if s == MP_OK else None)
+
+
+def mp_server_get_stats(srv):
+    out = mp_server_stats()
+    check(lib().mp_server_get_stats(srv, ctypes.byref(out)), "mp_server_get_stats")
+    return out
+
+
+def mp_server_reset_stats(srv):
+    return check(lib().mp_server_reset_stats(srv), "mp_server_reset_stats")
+
+
+def mp_server_destroy(srv):
+    return check(lib().mp_server_destroy(srv), "mp_server_destroy")

@@ -1,0 +1,122 @@
+// Definitions shared by the batched decode (mp_batched.cu), its correlation
+// GEMM (mp_corr.cu) and the request server (mp_server.cu).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mp_internal.h"
+
+namespace mpgb {
+
+constexpr int kBM = 128;            // signals per GEMM tile = TMEM lanes = UMMA M
+constexpr int kRowBytes = 128;      // bytes of K per operand row per stage (one swizzle row)
+constexpr int kMaxStages = 8;       // GEMM shared-memory pipeline depth, upper bound
+constexpr int kSmemOptin = 232448;  // shared memory a CTA may opt into on sm_103a
+
+// Pipeline depth for a tile width: as many A+B stages as fit, at most 8.
+constexpr int corr_stages(int TN) {
+    return (kSmemOptin - 2048) / (kBM * kRowBytes + TN * kRowBytes) < kMaxStages
+               ? (kSmemOptin - 2048) / (kBM * kRowBytes + TN * kRowBytes)
+               : kMaxStages;
+}
+constexpr int kTop = 8;             // low-precision candidates kept per signal and atom tile
+constexpr int kGemmThreads = 192;   // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+
+// Arguments of the correlation GEMM.
+struct CorrArgs {
+    const int* n_act;       // active rows this step (rows 0..n_act-1 of the A operand)
+    int TN;                 // atoms per tile (128 or 256)
+    int n_at;               // atom tiles
+    int M;
+    int nk;                 // K blocks of 128 bytes
+    int fp8;
+    int tmem_cols;
+    int stages;             // pipeline depth, corr_stages(TN)
+    const float* colscale;  // FP8 per-atom scale
+    uint2* cand;            // [row][n_at][8] = (score bits, atom), sorted by score
+    unsigned long long watchdog_ns;
+    int* err;
+    float* dump;            // diagnostic: full correlation rows (row * M + m), or NULL
+    const float* rscale;    // diagnostic FP8: per-row scale of the quantised residual
+};
+
+int corr_smem_bytes(int TN);
+cudaError_t corr_prepare();
+cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CorrArgs& a, int grid,
+                             cudaStream_t st);
+
+// ------------------------------------------------------------------ batch engine
+// Per-signal state of a slot.
+struct SlotState {
+    double e0, e, thr2, audit;
+    int t, T, status, stop_reason;
+};
+
+// Outputs the kernels write, read through one device pointer so a captured
+// graph does not depend on the caller's buffers.
+struct BatchIO {
+    float* X;              // slot s row at X + s * ldx
+    long long ldx;
+    int* tr_atoms;         // slot s row at tr_atoms + s * tr_cap (optional)
+    float* tr_coefs;
+    double* tr_energy;
+    int tr_cap;
+    int pad;
+};
+
+// Device state of `cap` decode slots over one dictionary at one precision:
+// FP32 residuals, the quantised GEMM operand (one row per active signal),
+// the active-row table, candidates, slot states, and the step graph.
+struct BatchEngine {
+    int cap = 0;            // slots (= GEMM rows available)
+    int cap_pad = 0;        // rows of the GEMM operand (multiple of 128)
+    int prec = -1;
+    int TN = 0;
+    int n_at = 0;
+    int ldq = 0;            // operand row: elements (BF16) or bytes (FP8)
+    float* R32 = nullptr;
+    void* Rq = nullptr;
+    SlotState* st = nullptr;
+    int* act = nullptr;
+    int* counters = nullptr;   // [0] active rows, [1] rows just admitted, [2] finished count
+    int* done = nullptr;
+    int* holes = nullptr;
+    int* surv = nullptr;
+    uint2* cand = nullptr;
+    double* eps2 = nullptr;
+    int* T = nullptr;
+    int* err = nullptr;
+    BatchIO* io = nullptr;
+    float* rscale = nullptr;
+    int* fin_list = nullptr;   // slots that stopped since the last retire
+    SlotState* h_st = nullptr;
+    int* h_cnt = nullptr;
+    double* h_eps2 = nullptr;
+    int* h_T = nullptr;
+    BatchIO* h_io = nullptr;
+    int* h_err = nullptr;
+    CUtensorMap tmA, tmB;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    bool graph_retire = false;
+    cudaStream_t cap_stream = nullptr;
+    size_t bytes = 0;
+};
+
+// Bytes of device memory one slot costs (residual, operand row, candidates,
+// state, an output row of M floats when the engine owns X).
+size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x);
+mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int cap);
+void engine_free(BatchEngine* e);
+// Admit n signals: rows Y (device, n x N), into slots `slots_dev` (device,
+// NULL = 0..n-1), with per-signal eps^2 and T already in e->eps2 / e->T.
+// Signals that need no iteration are reported in fin_list at once.
+cudaError_t engine_admit(PlanImpl* p, BatchEngine* e, const float* Y, int n, const int* slots_dev, cudaStream_t st);
+// Capture `steps` steps (and, if `retire`, a copy of the finished slots'
+// results to host-mapped memory) as the engine's graph.
+mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire, float* out_x_dev,
+                             SlotState* out_state_dev, int* out_list_dev, int* out_count_dev);
+
+}  // namespace mpgb

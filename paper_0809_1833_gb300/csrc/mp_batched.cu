@@ -3,19 +3,21 @@
 // that is still active.
 //
 // One step is three kernels:
-//   corr_top8   C = Rq * Psiq^T on the tensor cores (tcgen05, BF16 or FP8-E4M3
-//               operands, FP32 accumulation in TMEM); the epilogue keeps, per
-//               signal and per tile of atoms, the 8 largest |c| (FP8: times the
-//               atom's scale), so C is never written to memory.
-//   select      per signal: merge the per-tile candidates into the top 8,
-//               rescore those 8 atoms in FP32 from the FP32 atoms
+//   corr_top8   (mp_corr.cu) C = Rq * Psiq^T on the tensor cores; per signal
+//               and per atom tile the 8 largest |c| (FP8: times the atom scale).
+//   select      per signal: merge the sorted per-tile candidate lists into the
+//               top 8, rescore those atoms in FP32 from the FP32 atoms
 //               (<r, psi_m>, Eq. 9), commit the best (ties to the smallest
-//               index), x~_m += c (Eq. 10), r -= c psi_m in FP32 (Eq. 11),
-//               e = sum r^2 in FP64, t += 1 (Eq. 12), stop test.
-//   compact     order-preserving compaction of the still-active signals and
-//               requantisation of their residuals into the GEMM operand.
-// Signals stop independently; finished signals leave the GEMM.  The steps
-// are captured in a CUDA graph and replayed until no signal is active.
+//               index): x~_m += c (Eq. 10), r -= c psi_m in FP32 (Eq. 11),
+//               e = sum r^2 in FP64, t += 1 (Eq. 12), stop test; and write the
+//               requantised residual back into the signal's GEMM row.
+//   fixup       remove the signals that stopped from the active rows: each
+//               hole below the new row count is filled with a surviving row
+//               from above it (work proportional to the signals that stopped).
+//               A signal's arithmetic does not depend on its row, so results
+//               are the same alone and in any batch.
+// Signals stop independently; the steps are captured in a CUDA graph and
+// replayed until no signal is active.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -25,265 +27,16 @@
 #include <cstring>
 #include <vector>
 
+#include "mp_batch.cuh"
 #include "mp_device.cuh"
 #include "mp_dot.cuh"
 #include "mp_internal.h"
-#include "mp_tcgen05.cuh"
 
 namespace mpgb {
 
-constexpr int kBM = 128;            // signals per tile = TMEM lanes = UMMA M
-constexpr int kRowBytes = 128;      // bytes of K per operand row per stage (one swizzle row)
-constexpr int kStages = 4;
-constexpr int kTop = 8;
-constexpr int kGemmThreads = 192;   // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int kSelThreads = 256;
-constexpr int kStepsPerGraph = 16;  // even: the active-list parity returns to 0
-
-struct SlotState {
-    double e0, e, thr2, audit;
-    int t, T, status, stop_reason;
-};
-
-// Per-call outputs, read by the kernels through one device pointer so the
-// captured graph does not depend on the caller's buffers.
-struct BatchIO {
-    float* X;              // row b at X + b * ldx
-    long long ldx;
-    int* tr_atoms;         // row b at tr_atoms + b * tr_cap (optional)
-    float* tr_coefs;
-    double* tr_energy;
-    int tr_cap;
-    int pad;
-};
-
-// ------------------------------------------------------------------ GEMM + top-8
-struct CorrArgs {
-    const int* n_act;       // active rows this step
-    int TN;                 // atoms per tile
-    int n_at;               // atom tiles
-    int M;
-    int nk;                 // K blocks of 128 bytes
-    int fp8;
-    int tmem_cols;
-    const float* colscale;  // FP8 per-atom scale
-    uint2* cand;            // [row][n_at][8] = (score bits, atom)
-    unsigned long long watchdog_ns;
-    int* err;
-    float* dump;            // diagnostic: full correlation rows (row * M + m), or NULL
-    const float* rscale;    // diagnostic FP8: per-row scale of the quantised residual
-};
-
-struct CorrShared {
-    uint64_t full[kStages];
-    uint64_t empty[kStages];
-    uint64_t tfull[2];
-    uint64_t tempty[2];
-    uint64_t drain;
-    uint32_t tmem_base;
-    int abort;
-};
-
-MP_DEV void corr_timeout(int* err, CorrShared* sh) {
-    atomicCAS(err, 0, static_cast<int>(MP_ERR_TIMEOUT));
-    *reinterpret_cast<volatile int*>(&sh->abort) = 1;
-}
-
-__global__ void __launch_bounds__(kGemmThreads, 1)
-    corr_top8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     const CorrArgs a) {
-    extern __shared__ uint8_t smem_raw[];
-    // operand tiles need 1024-byte alignment for the 128-byte swizzle atoms
-    const uint32_t base_u32 = smem_u32(smem_raw);
-    uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
-    const int TN = a.TN;
-    const uint32_t a_bytes = kBM * kRowBytes;
-    const uint32_t b_bytes = static_cast<uint32_t>(TN) * kRowBytes;
-    uint8_t* tilesA = smem;
-    uint8_t* tilesB = smem + kStages * a_bytes;
-    CorrShared* sh = reinterpret_cast<CorrShared*>(tilesB + kStages * b_bytes);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_act = *a.n_act;
-    const int n_rt = (n_act + kBM - 1) / kBM;
-    const int n_tiles = n_rt * a.n_at;
-    if (static_cast<int>(blockIdx.x) >= n_tiles) return;   // uniform across the CTA
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&sh->full[s], 1);
-            mbar_init(&sh->empty[s], 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&sh->tfull[b], 1);
-            mbar_init(&sh->tempty[b], 4 * 32);
-        }
-        mbar_init(&sh->drain, 1);
-        sh->abort = 0;
-        fence_mbar_init();
-        tma_prefetch_desc(&tmA);
-        tma_prefetch_desc(&tmB);
-    }
-    if (warp == 1) tmem_alloc(&sh->tmem_base, static_cast<uint32_t>(a.tmem_cols));
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = sh->tmem_base;
-    const uint64_t lim = a.watchdog_ns;
-
-    if (warp == 0) {
-        // ---------------- TMA producer (one thread)
-        if (lane == 0) {
-            long long g = 0;
-            const int kelems = a.fp8 ? kRowBytes : kRowBytes / 2;
-            bool stop = false;
-            for (int tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x) {
-                const int rt = tile % n_rt, at = tile / n_rt;
-                for (int kb = 0; kb < a.nk; ++kb) {
-                    const int s = static_cast<int>(g % kStages);
-                    const long long use = g / kStages;
-                    if (use > 0 && !mbar_wait_bounded(&sh->empty[s], static_cast<uint32_t>((use - 1) & 1), lim)) {
-                        corr_timeout(a.err, sh);
-                        stop = true;
-                        break;
-                    }
-                    if (*reinterpret_cast<volatile int*>(&sh->abort)) {
-                        stop = true;
-                        break;
-                    }
-                    mbar_arrive_expect_tx(&sh->full[s], a_bytes + b_bytes);
-                    tma_load_2d(tilesA + s * a_bytes, &tmA, kb * kelems, rt * kBM, &sh->full[s]);
-                    tma_load_2d(tilesB + s * b_bytes, &tmB, kb * kelems, at * TN, &sh->full[s]);
-                    ++g;
-                }
-            }
-            // every issued load lands before the CTA may exit: the only load
-            // that can be in flight in stage s is the last one issued to it
-            for (int s = 0; s < kStages && s < g; ++s) {
-                const long long last = g - 1 - ((g - 1 - s) % kStages);
-                mbar_wait_bounded(&sh->full[s], static_cast<uint32_t>((last / kStages) & 1), lim);
-            }
-        }
-    } else if (warp == 1) {
-        // ---------------- MMA issuer (one thread)
-        if (lane == 0) {
-            const uint32_t idesc = make_idesc(kBM, TN, a.fp8 ? 0u : 1u);
-            long long g = 0;
-            int li = 0;
-            bool ok = true;
-            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++li) {
-                const int buf = li & 1, useb = li >> 1;
-                if (useb > 0 && !mbar_wait_bounded(&sh->tempty[buf], static_cast<uint32_t>((useb - 1) & 1), lim)) {
-                    corr_timeout(a.err, sh);
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t d = tmem + static_cast<uint32_t>(buf * TN);
-                for (int kb = 0; kb < a.nk; ++kb, ++g) {
-                    const int s = static_cast<int>(g % kStages);
-                    if (!mbar_wait_bounded(&sh->full[s], static_cast<uint32_t>((g / kStages) & 1), lim) ||
-                        *reinterpret_cast<volatile int*>(&sh->abort)) {
-                        corr_timeout(a.err, sh);
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t sa = smem_u32(tilesA + s * a_bytes);
-                    const uint32_t sb = smem_u32(tilesB + s * b_bytes);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        // 32 bytes of K per instruction: 16 BF16 or 32 E4M3 values
-                        const uint64_t ad = sw128_kmajor_desc(sa + 32u * k);
-                        const uint64_t bd = sw128_kmajor_desc(sb + 32u * k);
-                        const uint32_t acc = (kb | k) ? 1u : 0u;
-                        if (a.fp8) mma_fp8(d, ad, bd, idesc, acc);
-                        else mma_bf16(d, ad, bd, idesc, acc);
-                    }
-                    mma_commit(&sh->empty[s]);   // stage reusable once these MMAs finish
-                }
-                if (ok) mma_commit(&sh->tfull[buf]);
-            }
-            // no MMA may still write TMEM when it is freed: this commit
-            // arrives once every MMA issued above has completed
-            mma_commit(&sh->drain);
-            mbar_wait_bounded(&sh->drain, 0u, lim);
-        }
-    } else {
-        // ---------------- epilogue: one TMEM lane (= one signal row) per thread
-        const int q = warp & 3;               // TMEM lane quadrant this warp may access
-        int li = 0;
-        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++li) {
-            const int rt = tile % n_rt, at = tile / n_rt;
-            const int buf = li & 1, useb = li >> 1;
-            bool ok = mbar_wait_bounded(&sh->tfull[buf], static_cast<uint32_t>(useb & 1), lim) &&
-                      !*reinterpret_cast<volatile int*>(&sh->abort);
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) {
-                if (lane == 0) corr_timeout(a.err, sh);
-                break;
-            }
-            tc_fence_after();
-            const int row = rt * kBM + q * 32 + lane;
-            float ts[kTop];
-            int ti[kTop];
-#pragma unroll
-            for (int k = 0; k < kTop; ++k) {
-                ts[k] = -1.f;
-                ti[k] = 0x7fffffff;
-            }
-            const int m0 = at * TN;
-            for (int c = 0; c < TN / 32; ++c) {
-                float v[32];
-                tmem_ld_32cols(tmem + (static_cast<uint32_t>(q * 32) << 16) +
-                                   static_cast<uint32_t>(buf * TN + c * 32),
-                               v);
-                if (a.dump && row < n_act) {
-                    const float rsc = a.fp8 ? a.rscale[row] : 1.f;
-                    for (int j = 0; j < 32; ++j) {
-                        const int m = m0 + c * 32 + j;
-                        if (m < a.M) a.dump[static_cast<size_t>(row) * a.M + m] = v[j] * (a.fp8 ? a.colscale[m] * rsc : 1.f);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int m = m0 + c * 32 + j;
-                    if (m >= a.M) continue;
-                    float s = fabsf(v[j]);
-                    if (a.fp8) s *= __ldg(a.colscale + m);
-                    // strict: an equal score keeps the earlier (smaller) atom
-                    if (s > ts[kTop - 1]) {
-                        ts[kTop - 1] = s;
-                        ti[kTop - 1] = m;
-#pragma unroll
-                        for (int k = kTop - 1; k > 0; --k) {
-                            if (ts[k] > ts[k - 1]) {
-                                const float f = ts[k];
-                                ts[k] = ts[k - 1];
-                                ts[k - 1] = f;
-                                const int ii = ti[k];
-                                ti[k] = ti[k - 1];
-                                ti[k - 1] = ii;
-                            }
-                        }
-                    }
-                }
-            }
-            tc_fence_before();
-            mbar_arrive(&sh->tempty[buf]);
-            if (row < n_act) {
-                uint2* o = a.cand + (static_cast<size_t>(row) * a.n_at + at) * kTop;
-#pragma unroll
-                for (int k = 0; k < kTop; ++k) o[k] = make_uint2(__float_as_uint(ts[k]), static_cast<uint32_t>(ti[k]));
-            }
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        tmem_dealloc(tmem, static_cast<uint32_t>(a.tmem_cols));
-    }
-}
+constexpr int kFixThreads = 1024;
+constexpr int kStepsPerGraph = 16;
 
 // ------------------------------------------------------------------ block helpers
 MP_DEV double block_sum_f64(double v, double* red) {
@@ -296,72 +49,117 @@ MP_DEV double block_sum_f64(double v, double* red) {
     for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s += red[w];
     return s;
 }
-MP_DEV unsigned long long block_max_u64(unsigned long long v, unsigned long long* red) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    v = warp_max_u64(v);
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    unsigned long long m = 0ull;
-    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) m = umax64(m, red[w]);
-    return m;
-}
-MP_DEV int block_sum_i32(int v, int* red) {
+MP_DEV float block_max_f32(float v, float* red) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     __syncthreads();
     if (lane == 0) red[warp] = v;
     __syncthreads();
-    int s = 0;
-    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s += red[w];
-    return s;
+    float m = 0.f;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    return m;
+}
+// Exclusive prefix of `flag` over the block's threads in thread order;
+// *total receives the block sum.  red: 32 ints.
+MP_DEV int block_scan_flag(int flag, int* red, int* total) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned b = __ballot_sync(0xffffffffu, flag);
+    const int in_warp = __popc(b & ((1u << lane) - 1u));
+    __syncthreads();
+    if (lane == 0) red[warp] = __popc(b);
+    __syncthreads();
+    int before = 0, tot = 0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
+        if (w < warp) before += red[w];
+        tot += red[w];
+    }
+    *total = tot;
+    return before + in_warp;
 }
 
-// ------------------------------------------------------------------ init
-struct InitArgs {
-    const float* Y;         // B x N
-    int B, N, ldN, M;
-    float* R32;             // slot b row at R32 + b * ldN
+// Quantise one residual row (ldN floats) into a GEMM operand row of ldq
+// elements (BF16) or bytes (E4M3, per-row scale max|r| / 448).  Whole block.
+// Returns the row scale (1 for BF16).
+MP_DEV float block_quantize(const float* r, int ldN, void* dst, int ldq, int fp8, float* red) {
+    if (!fp8) {
+        __nv_bfloat16* q = static_cast<__nv_bfloat16*>(dst);
+        for (int n = threadIdx.x; n < ldq; n += blockDim.x) q[n] = __float2bfloat16_rn(n < ldN ? r[n] : 0.f);
+        return 1.f;
+    }
+    float mx = 0.f;
+    for (int n = threadIdx.x; n < ldN; n += blockDim.x) mx = fmaxf(mx, fabsf(r[n]));
+    const float amax = block_max_f32(mx, red);
+    const float inv = amax > 0.f ? 448.f / amax : 1.f;
+    __nv_fp8_storage_t* q = static_cast<__nv_fp8_storage_t*>(dst);
+    for (int n = threadIdx.x; n < ldq; n += blockDim.x)
+        q[n] = __nv_cvt_float_to_fp8(n < ldN ? r[n] * inv : 0.f, __NV_SATFINITE, __NV_E4M3);
+    return amax > 0.f ? amax / 448.f : 1.f;
+}
+
+// ------------------------------------------------------------------ admission (Eq. 8)
+// New signal k takes slot slots[k] (k when slots == NULL) and GEMM row
+// *n_act + k; signals that need no iteration are marked done and leave at
+// the next fixup.  *n_extra = n_new tells the fixup how many rows were added.
+struct AdmitArgs {
+    const float* Y;         // n_new x N
+    int n_new, N, ldN, M;
+    const int* slots;
+    const double* eps2;     // per new signal
+    const int* T;
+    float* R32;
     const BatchIO* io;
-    const double* eps2;     // per slot
-    const int* T;           // per slot
     SlotState* st;
-    int* act;               // list written here (all slots, in order)
-    int* n_act;
+    void* Rq;
+    int ldq, fp8;
+    float* rscale;          // optional: FP8 row scales (diagnostic)
+    int* act;
     int* done;
+    const int* n_act;
+    int* n_extra;
+    int* fin_count;         // signals that need no iteration are reported here
+    int* fin_list;
 };
 
-__global__ void __launch_bounds__(kSelThreads) batch_init_kernel(const InitArgs a) {
-    __shared__ double red[kSelThreads / 32];
-    const int b = blockIdx.x;
-    const float* y = a.Y + static_cast<size_t>(b) * a.N;
-    float* r = a.R32 + static_cast<size_t>(b) * a.ldN;
+__global__ void __launch_bounds__(kSelThreads) admit_kernel(const AdmitArgs a) {
+    __shared__ double redd[kSelThreads / 32];
+    __shared__ float redf[kSelThreads / 32];
+    const int k = blockIdx.x;
+    const int slot = a.slots ? a.slots[k] : k;
+    const int row = *a.n_act + k;
+    const float* y = a.Y + static_cast<size_t>(k) * a.N;
+    float* r = a.R32 + static_cast<size_t>(slot) * a.ldN;
     double acc = 0.0;
     for (int n = threadIdx.x; n < a.ldN; n += blockDim.x) {
         const float v = n < a.N ? y[n] : 0.f;
         r[n] = v;
         acc = fma(static_cast<double>(v), static_cast<double>(v), acc);
     }
-    float* x = a.io->X + static_cast<size_t>(b) * a.io->ldx;
-    for (int m = threadIdx.x; m < a.M; m += blockDim.x) x[m] = 0.f;
-    const double e0 = block_sum_f64(acc, red);
+    if (a.io->X) {
+        float* x = a.io->X + static_cast<size_t>(slot) * a.io->ldx;
+        for (int m = threadIdx.x; m < a.M; m += blockDim.x) x[m] = 0.f;
+    }
+    const double e0 = block_sum_f64(acc, redd);   // also orders the r writes before the quantise
+    const float sc = block_quantize(r, a.ldN, static_cast<char*>(a.Rq) + static_cast<size_t>(row) * a.ldq * (a.fp8 ? 1 : 2),
+                                    a.ldq, a.fp8, redf);
     if (threadIdx.x == 0) {
         SlotState s;
         s.e0 = e0;
         s.e = e0;
-        s.thr2 = a.eps2[b] * e0;
+        s.thr2 = a.eps2[k] * e0;
         s.audit = 0.0;
         s.t = 0;
-        s.T = a.T[b];
+        s.T = a.T[k];
         const bool finite = isfinite(e0);
         s.status = finite ? MP_OK : MP_ERR_NONFINITE;
         const bool run = finite && e0 > s.thr2 && s.T > 0;
         s.stop_reason = e0 == 0.0 ? MP_STOP_ZERO_Y : (e0 <= s.thr2 ? MP_STOP_CONVERGED : MP_STOP_MAX_ITERS);
-        a.st[b] = s;
-        a.act[b] = b;
-        a.done[b] = run ? 0 : 1;
-        if (b == 0) *a.n_act = a.B;
+        a.st[slot] = s;
+        a.act[row] = slot;
+        a.done[row] = run ? 0 : 1;
+        if (a.rscale) a.rscale[row] = sc;
+        if (!run && a.fin_list) a.fin_list[atomicAdd(a.fin_count, 1)] = slot;
+        if (k == 0) *a.n_extra = a.n_new;
     }
 }
 
@@ -369,7 +167,7 @@ __global__ void __launch_bounds__(kSelThreads) batch_init_kernel(const InitArgs 
 struct SelArgs {
     const int* n_act;
     const int* act;
-    int* done;              // by position in the active list
+    int* done;              // by row
     const uint2* cand;
     int n_at;
     const float* psi32;
@@ -377,13 +175,17 @@ struct SelArgs {
     float* R32;
     const BatchIO* io;
     SlotState* st;
+    void* Rq;
+    int ldq, fp8;
+    int* fin_count;         // optional: slots that stopped this step are appended here
+    int* fin_list;
 };
 
 __global__ void __launch_bounds__(kSelThreads) select_update_kernel(const SelArgs a) {
     extern __shared__ float4 r_sh4[];
     float* r = reinterpret_cast<float*>(r_sh4);
-    __shared__ unsigned long long redk[kSelThreads / 32];
     __shared__ double redd[kSelThreads / 32];
+    __shared__ float redf[kSelThreads / 32];
     __shared__ int top[kTop];
     __shared__ unsigned long long rkey[kTop];
     const int i = blockIdx.x;
@@ -391,25 +193,44 @@ __global__ void __launch_bounds__(kSelThreads) select_update_kernel(const SelArg
     const int slot = a.act[i];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* rs4 = reinterpret_cast<float4*>(r);
-    const float4* rg4 = reinterpret_cast<const float4*>(a.R32 + static_cast<size_t>(slot) * a.ldN);
+    float4* rg4 = reinterpret_cast<float4*>(a.R32 + static_cast<size_t>(slot) * a.ldN);
     const int n4 = a.ldN / 4;
     for (int k = threadIdx.x; k < n4; k += blockDim.x) rs4[k] = rg4[k];
 
-    // merge: 8 rounds, each the largest (score, -atom) key below the previous
-    const int nc = a.n_at * kTop;
-    const uint2* cd = a.cand + static_cast<size_t>(i) * nc;
-    unsigned long long prev = ~0ull;
-    for (int round = 0; round < kTop; ++round) {
-        unsigned long long best = 0ull;
-        for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-            const uint2 c = cd[k];
-            if (c.y >= static_cast<uint32_t>(a.M)) continue;
-            const unsigned long long key = (static_cast<unsigned long long>(c.x) << 32) | (0xffffffffu - c.y);
-            if (key < prev && key > best) best = key;
+    if (warp == 0) {
+        // merge the sorted per-tile lists: keys (score bits, ~atom) order by
+        // score, then by the smaller atom.  Each lane first keeps the best 8
+        // of its tiles, then 8 rounds of a warp max pop the global best 8.
+        unsigned long long lk[kTop];
+#pragma unroll
+        for (int k = 0; k < kTop; ++k) lk[k] = 0ull;
+        const uint2* cd = a.cand + static_cast<size_t>(i) * a.n_at * kTop;
+        for (int t = lane; t < a.n_at; t += 32) {
+            for (int k = 0; k < kTop; ++k) {
+                const uint2 c = cd[t * kTop + k];
+                if (c.y >= static_cast<uint32_t>(a.M)) break;
+                const unsigned long long key = (static_cast<unsigned long long>(c.x) << 32) | (0xffffffffu - c.y);
+                if (key <= lk[kTop - 1]) break;   // the tile's list is sorted: nothing better follows
+                lk[kTop - 1] = key;
+#pragma unroll
+                for (int j = kTop - 1; j > 0; --j) {
+                    if (lk[j] > lk[j - 1]) {
+                        const unsigned long long f = lk[j];
+                        lk[j] = lk[j - 1];
+                        lk[j - 1] = f;
+                    }
+                }
+            }
         }
-        best = block_max_u64(best, redk);
-        if (threadIdx.x == 0) top[round] = best ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(best)) : -1;
-        prev = best ? best : 0ull;
+        for (int round = 0; round < kTop; ++round) {
+            const unsigned long long m = warp_max_u64(lk[0]);
+            if (m != 0ull && lk[0] == m) {
+#pragma unroll
+                for (int j = 0; j < kTop - 1; ++j) lk[j] = lk[j + 1];
+                lk[kTop - 1] = 0ull;
+            }
+            if (lane == 0) top[round] = m ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(m)) : -1;
+        }
     }
     __syncthreads();
     // rescore the candidates in FP32 from the FP32 atoms (Eq. 9)
@@ -422,10 +243,8 @@ __global__ void __launch_bounds__(kSelThreads) select_update_kernel(const SelArg
     __syncthreads();
     unsigned long long kbest = 0ull;
     for (int w = 0; w < kTop; ++w) kbest = umax64(kbest, rkey[w]);
-    const int m = key_index(kbest);
-    const float c = key_coef(kbest);
     SlotState s = a.st[slot];
-    if (kbest == 0ull) {   // no candidate: nothing to select
+    if (kbest == 0ull) {   // no candidate: nothing can be selected
         if (threadIdx.x == 0) {
             s.status = MP_ERR_INVALID;
             a.st[slot] = s;
@@ -433,9 +252,11 @@ __global__ void __launch_bounds__(kSelThreads) select_update_kernel(const SelArg
         }
         return;
     }
-    // Eq. 11 in FP32 and the FP64 energy
+    const int m = key_index(kbest);
+    const float c = key_coef(kbest);
+    // Eq. 11 in FP32, the FP64 energy, and (BF16) the requantised row
     const float4* pm = reinterpret_cast<const float4*>(a.psi32 + static_cast<size_t>(m) * a.ldN);
-    float4* rw4 = reinterpret_cast<float4*>(a.R32 + static_cast<size_t>(slot) * a.ldN);
+    char* qrow = static_cast<char*>(a.Rq) + static_cast<size_t>(i) * a.ldq * (a.fp8 ? 1 : 2);
     double acc = 0.0;
     for (int k = threadIdx.x; k < n4; k += blockDim.x) {
         const float4 p = __ldg(pm + k);
@@ -444,13 +265,20 @@ __global__ void __launch_bounds__(kSelThreads) select_update_kernel(const SelArg
         v.y = fmaf(-c, p.y, v.y);
         v.z = fmaf(-c, p.z, v.z);
         v.w = fmaf(-c, p.w, v.w);
-        rw4[k] = v;
+        rg4[k] = v;
+        rs4[k] = v;
         acc = fma(static_cast<double>(v.x), static_cast<double>(v.x), acc);
         acc = fma(static_cast<double>(v.y), static_cast<double>(v.y), acc);
         acc = fma(static_cast<double>(v.z), static_cast<double>(v.z), acc);
         acc = fma(static_cast<double>(v.w), static_cast<double>(v.w), acc);
+        if (!a.fp8) {
+            __nv_bfloat162* q2 = reinterpret_cast<__nv_bfloat162*>(qrow) + 2 * k;
+            q2[0] = __floats2bfloat162_rn(v.x, v.y);
+            q2[1] = __floats2bfloat162_rn(v.z, v.w);
+        }
     }
-    const double e = block_sum_f64(acc, redd);
+    const double e = block_sum_f64(acc, redd);   // also orders the smem r writes
+    if (a.fp8) block_quantize(r, a.ldN, qrow, a.ldq, 1, redf);
     if (threadIdx.x == 0) {
         const BatchIO& io = *a.io;
         io.X[static_cast<size_t>(slot) * io.ldx + m] += c;   // Eq. 10
@@ -466,62 +294,100 @@ __global__ void __launch_bounds__(kSelThreads) select_update_kernel(const SelArg
         if (stop) s.stop_reason = conv ? MP_STOP_CONVERGED : MP_STOP_MAX_ITERS;
         a.st[slot] = s;
         a.done[i] = stop ? 1 : 0;
+        if (stop && a.fin_list) a.fin_list[atomicAdd(a.fin_count, 1)] = slot;
     }
 }
 
-// ------------------------------------------------------------------ compact / requantise
-struct CompactArgs {
-    const int* n_old;
-    const int* act_old;
-    const int* done;
-    int* n_new;
-    int* act_new;
-    const float* R32;
-    int ldN, N;
-    void* Rq;               // BF16 (ldq elements per row) or E4M3 (ldq bytes per row)
-    int ldq;
-    int fp8;
-    float* rscale;          // FP8: per-row scale written here (optional)
+// ------------------------------------------------------------------ fixup (one CTA)
+// Rows 0..n-1 with n = *n_act + *n_extra; rows with done set leave.  Holes
+// below the new count n' are filled, in order, with the surviving rows at or
+// above n' (moving the slot id and the quantised GEMM row).
+struct FixupArgs {
+    int* n_act;
+    int* n_extra;
+    int* act;
+    int* done;
+    char* Rq;
+    int ldq_bytes;
+    int* holes;             // scratch, capacity rows
+    int* surv;
 };
 
-__global__ void __launch_bounds__(kSelThreads) compact_requant_kernel(const CompactArgs a) {
-    __shared__ int redi[kSelThreads / 32];
-    __shared__ float redf[kSelThreads / 32];
-    const int i = blockIdx.x;
-    const int n_old = *a.n_old;
-    if (i == 0) {
-        int cnt = 0;
-        for (int k = threadIdx.x; k < n_old; k += blockDim.x) cnt += a.done[k] ? 0 : 1;
-        cnt = block_sum_i32(cnt, redi);
-        if (threadIdx.x == 0) *a.n_new = cnt;
+__global__ void __launch_bounds__(kFixThreads) fixup_kernel(const FixupArgs a) {
+    __shared__ int red[32];
+    const int n = *a.n_act + *a.n_extra;
+    int tot = 0, cnt = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int p = base + threadIdx.x;
+        int t;
+        block_scan_flag(p < n && a.done[p], red, &t);
+        cnt += t;
     }
-    if (i >= n_old || a.done[i]) return;
-    int before = 0;
-    for (int k = threadIdx.x; k < i; k += blockDim.x) before += a.done[k] ? 0 : 1;
-    before = block_sum_i32(before, redi);
-    const int slot = a.act_old[i];
-    if (threadIdx.x == 0) a.act_new[before] = slot;
-    const float* r = a.R32 + static_cast<size_t>(slot) * a.ldN;
-    if (!a.fp8) {
-        __nv_bfloat16* q = static_cast<__nv_bfloat16*>(a.Rq) + static_cast<size_t>(before) * a.ldq;
-        for (int n = threadIdx.x; n < a.ldq; n += blockDim.x) q[n] = __float2bfloat16_rn(n < a.ldN ? r[n] : 0.f);
-    } else {
-        // per-signal scale max|r| / 448 maps r onto the E4M3 range; one
-        // positive factor per row leaves the row's ranking unchanged
-        float mx = 0.f;
-        for (int n = threadIdx.x; n < a.ldN; n += blockDim.x) mx = fmaxf(mx, fabsf(r[n]));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if ((threadIdx.x & 31) == 0) redf[threadIdx.x >> 5] = mx;
-        __syncthreads();
-        float amax = 0.f;
-        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) amax = fmaxf(amax, redf[w]);
-        const float inv = amax > 0.f ? 448.f / amax : 1.f;
-        if (a.rscale && threadIdx.x == 0) a.rscale[before] = amax > 0.f ? amax / 448.f : 1.f;
-        __nv_fp8_storage_t* q = static_cast<__nv_fp8_storage_t*>(a.Rq) + static_cast<size_t>(before) * a.ldq;
-        for (int n = threadIdx.x; n < a.ldq; n += blockDim.x)
-            q[n] = __nv_cvt_float_to_fp8(n < a.ldN ? r[n] * inv : 0.f, __NV_SATFINITE, __NV_E4M3);
+    const int n_new = n - cnt;
+    int nh = 0;
+    for (int base = 0; base < n_new; base += blockDim.x) {
+        const int p = base + threadIdx.x;
+        const int f = p < n_new && a.done[p];
+        const int rk = block_scan_flag(f, red, &tot);
+        if (f) a.holes[nh + rk] = p;
+        nh += tot;
     }
+    int ns = 0;
+    for (int base = n_new; base < n; base += blockDim.x) {
+        const int q = base + threadIdx.x;
+        const int f = q < n && !a.done[q];
+        const int rk = block_scan_flag(f, red, &tot);
+        if (f) a.surv[ns + rk] = q;
+        ns += tot;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = warp; k < nh; k += blockDim.x >> 5) {
+        const int p = a.holes[k], q = a.surv[k];
+        if (lane == 0) a.act[p] = a.act[q];
+        const uint4* src = reinterpret_cast<const uint4*>(a.Rq + static_cast<size_t>(q) * a.ldq_bytes);
+        uint4* dst = reinterpret_cast<uint4*>(a.Rq + static_cast<size_t>(p) * a.ldq_bytes);
+        for (int o = lane; o < a.ldq_bytes / 16; o += 32) dst[o] = src[o];
+    }
+    // every remaining row is active: clear the flags (a filled hole still
+    // holds its old flag, and admission can run another fixup before the
+    // next select rewrites them)
+    for (int k = threadIdx.x; k < n_new; k += blockDim.x) a.done[k] = 0;
+    if (threadIdx.x == 0) {
+        *a.n_act = n_new;
+        *a.n_extra = 0;
+    }
+}
+
+// ------------------------------------------------------------------ retire
+// Copy the results of the slots that stopped since the last retire (x~ row
+// and state, by slot) and their list to the caller's buffers (host-mapped
+// memory in the server), so the host learns about them without a copy.
+struct RetireArgs {
+    const int* fin_count;
+    const int* fin_list;
+    const SlotState* st;
+    const BatchIO* io;
+    int M;
+    float* out_x;           // slot s at out_x + s * M
+    SlotState* out_state;   // by slot
+    int* out_list;
+    int* out_count;
+};
+
+__global__ void __launch_bounds__(kSelThreads) retire_kernel(const RetireArgs a) {
+    const int n = *a.fin_count;
+    const int k = blockIdx.x;
+    if (k == 0 && threadIdx.x == 0) *a.out_count = n;
+    if (k >= n) return;
+    const int slot = a.fin_list[k];
+    if (threadIdx.x == 0) {
+        a.out_list[k] = slot;
+        a.out_state[slot] = a.st[slot];
+    }
+    const float* x = a.io->X + static_cast<size_t>(slot) * a.io->ldx;
+    float* o = a.out_x + static_cast<size_t>(slot) * a.M;
+    for (int m = threadIdx.x; m < a.M; m += blockDim.x) o[m] = x[m];
 }
 
 // ------------------------------------------------------------------ host engine
@@ -542,9 +408,9 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// rows x row_bytes matrix (row stride = row_bytes), box of box_rows rows x 128 bytes
-static mp_status make_map(CUtensorMap* map, void* base, bool fp8, long long rows, long long row_elems,
-                          int box_rows) {
+// rows x row_elems matrix (row stride row_elems elements); box = box_rows
+// rows x 128 bytes, 128-byte swizzle (the UMMA K-major layout)
+static mp_status make_map(CUtensorMap* map, void* base, bool fp8, long long rows, long long row_elems, int box_rows) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(MP_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     const int esize = fp8 ? 1 : 2;
@@ -552,66 +418,22 @@ static mp_status make_map(CUtensorMap* map, void* base, bool fp8, long long rows
     cuuint64_t strides[1] = {static_cast<cuuint64_t>(row_elems * esize)};
     cuuint32_t box[2] = {static_cast<cuuint32_t>(kRowBytes / esize), static_cast<cuuint32_t>(box_rows)};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims,
-                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+    CUresult r = enc(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides,
+                     box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(MP_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
     return MP_OK;
 }
 
-struct BatchEngine {
-    int cap = 0;            // slots
-    int cap_pad = 0;        // rows of the GEMM operand (multiple of 128)
-    int prec = -1;
-    int TN = 0;
-    int n_at = 0;
-    float* R32 = nullptr;
-    void* Rq = nullptr;
-    SlotState* st = nullptr;
-    int* act = nullptr;     // 2 x cap
-    int* n_act = nullptr;   // 2
-    int* done = nullptr;
-    uint2* cand = nullptr;
-    double* eps2 = nullptr;
-    int* T = nullptr;
-    int* err = nullptr;
-    BatchIO* io = nullptr;
-    float* rscale = nullptr;   // diagnostic FP8 row scales
-    // pinned host mirrors
-    SlotState* h_st = nullptr;
-    int* h_nact = nullptr;
-    double* h_eps2 = nullptr;
-    int* h_T = nullptr;
-    BatchIO* h_io = nullptr;
-    int* h_err = nullptr;
-    CUtensorMap tmA, tmB;
-    cudaGraphExec_t graph = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    size_t bytes = 0;
-};
-
-static void engine_free(BatchEngine* e) {
+void engine_free(BatchEngine* e) {
     if (!e) return;
     if (e->graph) cudaGraphExecDestroy(e->graph);
     if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
-    cudaFree(e->R32);
-    cudaFree(e->Rq);
-    cudaFree(e->st);
-    cudaFree(e->act);
-    cudaFree(e->n_act);
-    cudaFree(e->done);
-    cudaFree(e->cand);
-    cudaFree(e->eps2);
-    cudaFree(e->T);
-    cudaFree(e->err);
-    cudaFree(e->io);
-    cudaFree(e->rscale);
-    cudaFreeHost(e->h_st);
-    cudaFreeHost(e->h_nact);
-    cudaFreeHost(e->h_eps2);
-    cudaFreeHost(e->h_T);
-    cudaFreeHost(e->h_io);
-    cudaFreeHost(e->h_err);
+    void* dev[] = {e->R32, e->Rq, e->st, e->act, e->counters, e->done, e->holes, e->surv, e->cand,
+                   e->eps2, e->T, e->err, e->io, e->rscale, e->fin_list};
+    for (void* p : dev) cudaFree(p);
+    void* host[] = {e->h_st, e->h_cnt, e->h_eps2, e->h_T, e->h_io, e->h_err};
+    for (void* p : host) cudaFreeHost(p);
     *e = BatchEngine();
 }
 
@@ -620,17 +442,24 @@ void batch_destroy(BatchEngine* b) {
     delete b;
 }
 
-static int gemm_smem_bytes(int TN) {
-    return 1024 + kStages * (kBM * kRowBytes + TN * kRowBytes) + static_cast<int>(sizeof(CorrShared));
+size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x) {
+    const bool fp8 = prec == MP_PREC_FP8E4M3;
+    const size_t TN = p->batch_tile_n ? p->batch_tile_n : 256;
+    const size_t n_at = (p->M + TN - 1) / TN;
+    return sizeof(float) * p->ldN + (fp8 ? p->ldK8 : 2 * p->ldK16) + sizeof(uint2) * n_at * kTop +
+           sizeof(SlotState) + 6 * sizeof(int) + sizeof(double) + sizeof(float) + (with_x ? sizeof(float) * p->M : 0);
 }
 
-// (Re)build the engine for `cap` slots at precision `prec`.
 static mp_status engine_prepare(PlanImpl* p, int prec, int cap) {
     BatchEngine* e = p->batch;
     const int TN = p->batch_tile_n ? p->batch_tile_n : 256;
     if (e && e->prec == prec && e->cap >= cap && e->TN == TN) return MP_OK;
     if (!e) e = p->batch = new BatchEngine();
-    const int newcap = std::max(cap, e->cap);
+    return engine_alloc(e, p, prec, std::max(cap, e->cap));
+}
+
+mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap) {
+    const int TN = p->batch_tile_n ? p->batch_tile_n : 256;
     engine_free(e);
     e->cap = newcap;
     e->cap_pad = (newcap + kBM - 1) / kBM * kBM;
@@ -638,39 +467,44 @@ static mp_status engine_prepare(PlanImpl* p, int prec, int cap) {
     e->TN = TN;
     e->n_at = (p->M + TN - 1) / TN;
     const bool fp8 = prec == MP_PREC_FP8E4M3;
-    const int ldq = fp8 ? p->ldK8 : p->ldK16;
-    const size_t qbytes = static_cast<size_t>(e->cap_pad) * ldq * (fp8 ? 1 : 2);
-    auto A = [&](void** ptr, size_t b) {
-        e->bytes += b;
-        return cudaMalloc(ptr, b);
-    };
+    e->ldq = fp8 ? p->ldK8 : p->ldK16;
+    const size_t qbytes = static_cast<size_t>(e->cap_pad) * e->ldq * (fp8 ? 1 : 2);
+    const size_t C = static_cast<size_t>(e->cap);
     cudaError_t r = cudaSuccess;
-    if (r == cudaSuccess) r = A(reinterpret_cast<void**>(&e->R32), sizeof(float) * e->cap * static_cast<size_t>(p->ldN));
-    if (r == cudaSuccess) r = A(&e->Rq, qbytes);
-    if (r == cudaSuccess) r = A(reinterpret_cast<void**>(&e->st), sizeof(SlotState) * e->cap);
-    if (r == cudaSuccess) r = A(reinterpret_cast<void**>(&e->act), sizeof(int) * 2 * e->cap);
-    if (r == cudaSuccess) r = A(reinterpret_cast<void**>(&e->n_act), sizeof(int) * 2);
-    if (r == cudaSuccess) r = A(reinterpret_cast<void**>(&e->done), sizeof(int) * e->cap);
-    if (r == cudaSuccess)
-        r = A(reinterpret_cast<void**>(&e->cand), sizeof(uint2) * static_cast<size_t>(e->cap) * e->n_at * kTop);
-    if (r == cudaSuccess) r = A(reinterpret_cast<void**>(&e->eps2), sizeof(double) * e->cap);
-    if (r == cudaSuccess) r = A(reinterpret_cast<void**>(&e->T), sizeof(int) * e->cap);
-    if (r == cudaSuccess) r = A(reinterpret_cast<void**>(&e->err), sizeof(int));
-    if (r == cudaSuccess) r = A(reinterpret_cast<void**>(&e->io), sizeof(BatchIO));
-    if (r == cudaSuccess) r = A(reinterpret_cast<void**>(&e->rscale), sizeof(float) * e->cap);
-    if (r == cudaSuccess) r = cudaMallocHost(&e->h_st, sizeof(SlotState) * e->cap);
-    if (r == cudaSuccess) r = cudaMallocHost(&e->h_nact, sizeof(int) * 2);
-    if (r == cudaSuccess) r = cudaMallocHost(&e->h_eps2, sizeof(double) * e->cap);
-    if (r == cudaSuccess) r = cudaMallocHost(&e->h_T, sizeof(int) * e->cap);
+    auto A = [&](auto** ptr, size_t b) {
+        if (r != cudaSuccess) return;
+        e->bytes += b;
+        r = cudaMalloc(reinterpret_cast<void**>(ptr), b);
+    };
+    A(&e->R32, sizeof(float) * C * p->ldN);
+    A(reinterpret_cast<char**>(&e->Rq), qbytes);
+    A(&e->st, sizeof(SlotState) * C);
+    A(&e->act, sizeof(int) * C);
+    A(&e->counters, sizeof(int) * 4);
+    A(&e->done, sizeof(int) * C);
+    A(&e->holes, sizeof(int) * C);
+    A(&e->surv, sizeof(int) * C);
+    A(&e->cand, sizeof(uint2) * C * e->n_at * kTop);
+    A(&e->eps2, sizeof(double) * C);
+    A(&e->T, sizeof(int) * C);
+    A(&e->err, sizeof(int));
+    A(&e->io, sizeof(BatchIO));
+    A(&e->rscale, sizeof(float) * C);
+    A(&e->fin_list, sizeof(int) * C);
+    if (r == cudaSuccess) r = cudaMallocHost(&e->h_st, sizeof(SlotState) * C);
+    if (r == cudaSuccess) r = cudaMallocHost(&e->h_cnt, sizeof(int) * 4);
+    if (r == cudaSuccess) r = cudaMallocHost(&e->h_eps2, sizeof(double) * C);
+    if (r == cudaSuccess) r = cudaMallocHost(&e->h_T, sizeof(int) * C);
     if (r == cudaSuccess) r = cudaMallocHost(&e->h_io, sizeof(BatchIO));
     if (r == cudaSuccess) r = cudaMallocHost(&e->h_err, sizeof(int));
     if (r == cudaSuccess) r = cudaMemset(e->Rq, 0, qbytes);
+    if (r == cudaSuccess) r = cudaMemset(e->counters, 0, sizeof(int) * 4);
     if (r != cudaSuccess) {
         engine_free(e);
         return cuda_fail(r, "batched engine allocation");
     }
-    mp_status s = make_map(&e->tmA, e->Rq, fp8, e->cap_pad, ldq, kBM);
-    if (s == MP_OK) s = make_map(&e->tmB, fp8 ? p->psi8 : p->psi16, fp8, p->M, ldq, TN);
+    mp_status s = make_map(&e->tmA, e->Rq, fp8, e->cap_pad, e->ldq, kBM);
+    if (s == MP_OK) s = make_map(&e->tmB, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, TN);
     if (s != MP_OK) {
         engine_free(e);
         return s;
@@ -678,35 +512,50 @@ static mp_status engine_prepare(PlanImpl* p, int prec, int cap) {
     return MP_OK;
 }
 
-// Launch one step (GEMM, select, compact) with active-list parity `par`.
-static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int par, cudaStream_t st) {
+static CorrArgs corr_args(PlanImpl* p, BatchEngine* e) {
     const bool fp8 = e->prec == MP_PREC_FP8E4M3;
-    int* act_cur = e->act + par * e->cap;
-    int* act_new = e->act + (1 - par) * e->cap;
-    const int* n_cur = e->n_act + par;
-    int* n_new = e->n_act + (1 - par);
     CorrArgs ca;
-    ca.n_act = n_cur;
+    std::memset(&ca, 0, sizeof(ca));
+    ca.n_act = e->counters;
     ca.TN = e->TN;
     ca.n_at = e->n_at;
     ca.M = p->M;
     ca.nk = (fp8 ? p->ldK8 : p->ldK16 * 2) / kRowBytes;
     ca.fp8 = fp8 ? 1 : 0;
     ca.tmem_cols = 2 * e->TN >= 512 ? 512 : (2 * e->TN >= 256 ? 256 : 128);
+    ca.stages = corr_stages(e->TN);
     ca.colscale = p->scale8;
     ca.cand = e->cand;
     ca.watchdog_ns = static_cast<unsigned long long>(p->watchdog_ns);
     ca.err = e->err;
-    ca.dump = nullptr;
-    ca.rscale = nullptr;
+    return ca;
+}
+
+static cudaError_t launch_fixup(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
+    FixupArgs fa;
+    fa.n_act = e->counters;
+    fa.n_extra = e->counters + 1;
+    fa.act = e->act;
+    fa.done = e->done;
+    fa.Rq = static_cast<char*>(e->Rq);
+    fa.ldq_bytes = e->ldq * (e->prec == MP_PREC_FP8E4M3 ? 1 : 2);
+    fa.holes = e->holes;
+    fa.surv = e->surv;
+    fixup_kernel<<<1, kFixThreads, 0, st>>>(fa);
+    p->launches++;
+    return cudaGetLastError();
+}
+
+// One step: GEMM + top-8, select/rescore/update, fixup.
+static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
+    int* fin_count = e->counters + 2;
+    int* fin_list = e->fin_list;
     const int max_tiles = (e->cap_pad / kBM) * e->n_at;
-    const int grid = std::max(1, std::min(max_tiles, p->sm_count));
-    corr_top8_kernel<<<grid, kGemmThreads, gemm_smem_bytes(e->TN), st>>>(e->tmA, e->tmB, ca);
-    cudaError_t r = cudaGetLastError();
+    cudaError_t r = launch_corr_top8(e->tmA, e->tmB, corr_args(p, e), std::min(max_tiles, p->sm_count), st);
     if (r != cudaSuccess) return r;
     SelArgs sa;
-    sa.n_act = n_cur;
-    sa.act = act_cur;
+    sa.n_act = e->counters;
+    sa.act = e->act;
     sa.done = e->done;
     sa.cand = e->cand;
     sa.n_at = e->n_at;
@@ -717,39 +566,45 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int par, cudaStream_
     sa.R32 = e->R32;
     sa.io = e->io;
     sa.st = e->st;
+    sa.Rq = e->Rq;
+    sa.ldq = e->ldq;
+    sa.fp8 = e->prec == MP_PREC_FP8E4M3 ? 1 : 0;
+    sa.fin_count = fin_count;
+    sa.fin_list = fin_list;
     select_update_kernel<<<e->cap, kSelThreads, p->ldN * sizeof(float), st>>>(sa);
     if ((r = cudaGetLastError()) != cudaSuccess) return r;
-    CompactArgs cp;
-    cp.n_old = n_cur;
-    cp.act_old = act_cur;
-    cp.done = e->done;
-    cp.n_new = n_new;
-    cp.act_new = act_new;
-    cp.R32 = e->R32;
-    cp.ldN = p->ldN;
-    cp.N = p->N;
-    cp.Rq = e->Rq;
-    cp.ldq = fp8 ? p->ldK8 : p->ldK16;
-    cp.fp8 = fp8 ? 1 : 0;
-    cp.rscale = nullptr;
-    compact_requant_kernel<<<e->cap, kSelThreads, 0, st>>>(cp);
-    return cudaGetLastError();
+    return launch_fixup(p, e, st);
 }
 
-static mp_status build_graph(PlanImpl* p, BatchEngine* e) {
-    if (e->graph) return MP_OK;
-    if (!e->cap_stream) MP_CUDA_TRY(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
-    static bool attr = false;
-    if (!attr) {
-        MP_CUDA_TRY(cudaFuncSetAttribute(corr_top8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         gemm_smem_bytes(256)));
-        attr = true;
+mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire, float* out_x, SlotState* out_state,
+                             int* out_list, int* out_count) {
+    if (e->graph && e->graph_steps == steps && e->graph_retire == retire) return MP_OK;
+    if (e->graph) {
+        cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
     }
-    MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     std::max(p->ldN * 4, 48 * 1024)));
+    if (!e->cap_stream) MP_CUDA_TRY(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
+    MP_CUDA_TRY(corr_prepare());
+    if (p->ldN * 4 > 48 * 1024)
+        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, p->ldN * 4));
     MP_CUDA_TRY(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t r = cudaSuccess;
-    for (int s = 0; s < kStepsPerGraph && r == cudaSuccess; ++s) r = launch_step(p, e, s & 1, e->cap_stream);
+    for (int s = 0; s < steps && r == cudaSuccess; ++s) r = launch_step(p, e, e->cap_stream);
+    if (retire && r == cudaSuccess) {
+        RetireArgs ra;
+        ra.fin_count = e->counters + 2;
+        ra.fin_list = e->fin_list;
+        ra.st = e->st;
+        ra.io = e->io;
+        ra.M = p->M;
+        ra.out_x = out_x;
+        ra.out_state = out_state;
+        ra.out_list = out_list;
+        ra.out_count = out_count;
+        retire_kernel<<<e->cap, kSelThreads, 0, e->cap_stream>>>(ra);
+        r = cudaGetLastError();
+        if (r == cudaSuccess) r = cudaMemsetAsync(e->counters + 2, 0, sizeof(int), e->cap_stream);
+    }
     cudaGraph_t g = nullptr;
     cudaError_t r2 = cudaStreamEndCapture(e->cap_stream, &g);
     if (r != cudaSuccess) {
@@ -760,16 +615,52 @@ static mp_status build_graph(PlanImpl* p, BatchEngine* e) {
     r = cudaGraphInstantiate(&e->graph, g, 0);
     cudaGraphDestroy(g);
     if (r != cudaSuccess) return cuda_fail(r, "cudaGraphInstantiate");
+    e->graph_steps = steps;
+    e->graph_retire = retire;
     return MP_OK;
 }
 
-static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, long long ldx, int B,
-                             const mp_stop* stops, int n_stops, const mp_trace* trace, mp_result* out,
-                             cudaStream_t st) {
+static AdmitArgs admit_args(PlanImpl* p, BatchEngine* e, const float* Y, int n_new, const int* slots) {
+    AdmitArgs aa;
+    aa.Y = Y;
+    aa.n_new = n_new;
+    aa.N = p->N;
+    aa.ldN = p->ldN;
+    aa.M = p->M;
+    aa.slots = slots;
+    aa.eps2 = e->eps2;
+    aa.T = e->T;
+    aa.R32 = e->R32;
+    aa.io = e->io;
+    aa.st = e->st;
+    aa.Rq = e->Rq;
+    aa.ldq = e->ldq;
+    aa.fp8 = e->prec == MP_PREC_FP8E4M3 ? 1 : 0;
+    aa.rscale = nullptr;
+    aa.act = e->act;
+    aa.done = e->done;
+    aa.n_act = e->counters;
+    aa.n_extra = e->counters + 1;
+    aa.fin_count = e->counters + 2;
+    aa.fin_list = e->fin_list;
+    return aa;
+}
+
+cudaError_t engine_admit(PlanImpl* p, BatchEngine* e, const float* Y, int n, const int* slots_dev, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    admit_kernel<<<n, kSelThreads, 0, st>>>(admit_args(p, e, Y, n, slots_dev));
+    cudaError_t r = cudaGetLastError();
+    if (r != cudaSuccess) return r;
+    p->launches++;
+    return launch_fixup(p, e, st);
+}
+
+static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, long long ldx, int B, const mp_stop* stops,
+                             int n_stops, const mp_trace* trace, mp_result* out, cudaStream_t st) {
     mp_status s = engine_prepare(p, prec, B);
     if (s != MP_OK) return s;
     BatchEngine* e = p->batch;
-    s = build_graph(p, e);
+    s = engine_build_graph(p, e, kStepsPerGraph, false, nullptr, nullptr, nullptr, nullptr);
     if (s != MP_OK) return s;
     int maxT = 0;
     for (int b = 0; b < B; ++b) {
@@ -793,47 +684,16 @@ static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, lo
     MP_CUDA_TRY(cudaMemcpyAsync(e->T, e->h_T, sizeof(int) * B, cudaMemcpyHostToDevice, st));
     MP_CUDA_TRY(cudaMemcpyAsync(e->io, e->h_io, sizeof(BatchIO), cudaMemcpyHostToDevice, st));
     MP_CUDA_TRY(cudaMemsetAsync(e->err, 0, sizeof(int), st));
-    InitArgs ia;
-    ia.Y = Y;
-    ia.B = B;
-    ia.N = p->N;
-    ia.ldN = p->ldN;
-    ia.M = p->M;
-    ia.R32 = e->R32;
-    ia.io = e->io;
-    ia.eps2 = e->eps2;
-    ia.T = e->T;
-    ia.st = e->st;
-    ia.act = e->act + e->cap;      // list 1, compacted into list 0 below
-    ia.n_act = e->n_act + 1;
-    ia.done = e->done;
-    batch_init_kernel<<<B, kSelThreads, 0, st>>>(ia);
-    MP_CUDA_TRY(cudaGetLastError());
-    // slots beyond B never enter the list; compact list 1 into list 0
-    CompactArgs cp;
-    cp.n_old = e->n_act + 1;
-    cp.act_old = e->act + e->cap;
-    cp.done = e->done;
-    cp.n_new = e->n_act;
-    cp.act_new = e->act;
-    cp.R32 = e->R32;
-    cp.ldN = p->ldN;
-    cp.N = p->N;
-    cp.Rq = e->Rq;
-    const bool fp8 = prec == MP_PREC_FP8E4M3;
-    cp.ldq = fp8 ? p->ldK8 : p->ldK16;
-    cp.fp8 = fp8 ? 1 : 0;
-    cp.rscale = nullptr;
-    compact_requant_kernel<<<B, kSelThreads, 0, st>>>(cp);
-    MP_CUDA_TRY(cudaGetLastError());
-    p->launches += 2;
+    MP_CUDA_TRY(cudaMemsetAsync(e->counters, 0, sizeof(int) * 4, st));
+    // signal b -> slot b, GEMM row b; then drop those that need no iteration
+    MP_CUDA_TRY(engine_admit(p, e, Y, B, nullptr, st));
     // replay the captured steps until no signal is active (each step moves
-    // every active signal by one iteration, so maxT + 1 steps always suffice)
-    const long long max_replays = (static_cast<long long>(maxT) + kStepsPerGraph) / kStepsPerGraph + 1;
+    // every active signal by one iteration, so maxT steps always suffice)
+    const long long max_replays = (static_cast<long long>(maxT) + kStepsPerGraph - 1) / kStepsPerGraph + 1;
     for (long long k = 0; k < max_replays; ++k) {
-        MP_CUDA_TRY(cudaMemcpyAsync(e->h_nact, e->n_act, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MP_CUDA_TRY(cudaMemcpyAsync(e->h_cnt, e->counters, sizeof(int), cudaMemcpyDeviceToHost, st));
         MP_CUDA_TRY(cudaStreamSynchronize(st));
-        if (*e->h_nact == 0) break;
+        if (e->h_cnt[0] == 0) break;
         MP_CUDA_TRY(cudaGraphLaunch(e->graph, st));
         p->launches += 3 * kStepsPerGraph;
     }
@@ -894,35 +754,14 @@ mp_status mp_recover_batched(mp_plan_t plan, int prec, const float* Y, float* X,
                 tb.residual = nullptr;
                 tp = &tb;
             }
-            mp_status s = mp_recover(plan, Y + static_cast<size_t>(b) * p->N, X + static_cast<size_t>(b) * p->M, sb,
-                                     tp, &host_out[b], stream);
+            mp_status s = mp_recover(plan, Y + static_cast<size_t>(b) * p->N, X + static_cast<size_t>(b) * p->M, sb, tp,
+                                     &host_out[b], stream);
             if (s < 0 && worst == MP_OK) worst = s;
         }
         return worst;
     }
     return batched_run(p, prec, Y, X, p->M, B, stops, n_stops, trace, host_out, st);
 }
-
-}  // extern "C"
-
-namespace mpgb {
-
-// Diagnostic: load B residuals as active rows 0..B-1 (slot b = row b).
-__global__ void debug_load_kernel(const float* R, int B, int N, int ldN, float* R32, int* act, int* n_act,
-                                  int* done) {
-    const int b = blockIdx.x;
-    for (int n = threadIdx.x; n < ldN; n += blockDim.x)
-        R32[static_cast<size_t>(b) * ldN + n] = n < N ? R[static_cast<size_t>(b) * N + n] : 0.f;
-    if (threadIdx.x == 0) {
-        act[b] = b;
-        done[b] = 0;
-        if (b == 0) *n_act = B;
-    }
-}
-
-}  // namespace mpgb
-
-extern "C" {
 
 mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B, float* C, void* stream) {
     clear_error();
@@ -936,44 +775,31 @@ mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B,
     mp_status s = engine_prepare(p, prec, B);
     if (s != MP_OK) return s;
     BatchEngine* e = p->batch;
-    MP_CUDA_TRY(cudaFuncSetAttribute(corr_top8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     gemm_smem_bytes(256)));
+    MP_CUDA_TRY(corr_prepare());
+    for (int b = 0; b < B; ++b) {
+        e->h_eps2[b] = 0.0;
+        e->h_T[b] = 1;
+    }
+    BatchIO io;
+    std::memset(&io, 0, sizeof(io));
+    *e->h_io = io;
+    MP_CUDA_TRY(cudaMemcpyAsync(e->eps2, e->h_eps2, sizeof(double) * B, cudaMemcpyHostToDevice, st));
+    MP_CUDA_TRY(cudaMemcpyAsync(e->T, e->h_T, sizeof(int) * B, cudaMemcpyHostToDevice, st));
+    MP_CUDA_TRY(cudaMemcpyAsync(e->io, e->h_io, sizeof(BatchIO), cudaMemcpyHostToDevice, st));
     MP_CUDA_TRY(cudaMemsetAsync(e->err, 0, sizeof(int), st));
-    debug_load_kernel<<<B, 256, 0, st>>>(R, B, p->N, p->ldN, e->R32, e->act + e->cap, e->n_act + 1, e->done);
-    const bool fp8 = prec == MP_PREC_FP8E4M3;
-    CompactArgs cp;
-    cp.n_old = e->n_act + 1;
-    cp.act_old = e->act + e->cap;
-    cp.done = e->done;
-    cp.n_new = e->n_act;
-    cp.act_new = e->act;
-    cp.R32 = e->R32;
-    cp.ldN = p->ldN;
-    cp.N = p->N;
-    cp.Rq = e->Rq;
-    cp.ldq = fp8 ? p->ldK8 : p->ldK16;
-    cp.fp8 = fp8 ? 1 : 0;
-    cp.rscale = e->rscale;
-    compact_requant_kernel<<<B, kSelThreads, 0, st>>>(cp);
-    CorrArgs ca;
-    ca.n_act = e->n_act;
-    ca.TN = e->TN;
-    ca.n_at = e->n_at;
-    ca.M = p->M;
-    ca.nk = (fp8 ? p->ldK8 : p->ldK16 * 2) / kRowBytes;
-    ca.fp8 = fp8 ? 1 : 0;
-    ca.tmem_cols = 2 * e->TN >= 512 ? 512 : (2 * e->TN >= 256 ? 256 : 128);
-    ca.colscale = p->scale8;
-    ca.cand = e->cand;
-    ca.watchdog_ns = static_cast<unsigned long long>(p->watchdog_ns);
-    ca.err = e->err;
+    MP_CUDA_TRY(cudaMemsetAsync(e->counters, 0, sizeof(int) * 4, st));
+    // rows 0..B-1 hold R (quantised); the row count is set directly so that
+    // zero rows are kept too
+    AdmitArgs aa = admit_args(p, e, R, B, nullptr);
+    aa.rscale = e->rscale;
+    admit_kernel<<<B, kSelThreads, 0, st>>>(aa);
+    MP_CUDA_TRY(cudaMemcpyAsync(e->counters, &B, sizeof(int), cudaMemcpyHostToDevice, st));
+    CorrArgs ca = corr_args(p, e);
     ca.dump = C;
     ca.rscale = e->rscale;
     const int tiles = ((B + kBM - 1) / kBM) * e->n_at;
-    corr_top8_kernel<<<std::max(1, std::min(tiles, p->sm_count)), kGemmThreads, gemm_smem_bytes(e->TN), st>>>(
-        e->tmA, e->tmB, ca);
-    MP_CUDA_TRY(cudaGetLastError());
-    p->launches += 3;
+    MP_CUDA_TRY(launch_corr_top8(e->tmA, e->tmB, ca, std::min(tiles, p->sm_count), st));
+    p->launches += 2;
     MP_CUDA_TRY(cudaMemcpyAsync(e->h_err, e->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaStreamSynchronize(st));
     if (*e->h_err) return fail(static_cast<mp_status>(*e->h_err), "mp_debug_correlations: device wait timed out");

@@ -1,0 +1,248 @@
+// Batched correlation GEMM with a segmented top-8 epilogue (Sec. 3 Eq. 9 for
+// many signals at once): C = Rq * Psiq^T on the tcgen05 tensor cores, BF16
+// (kind::f16) or FP8-E4M3 (kind::f8f6f4) operands staged by TMA with
+// 128-byte swizzling, FP32 accumulators in TMEM, and per signal row the 8
+// largest |c| of each atom tile kept in registers and written out, so the
+// correlation matrix itself is never stored.
+#include <cuda.h>
+
+#include <algorithm>
+
+#include "mp_batch.cuh"
+#include "mp_device.cuh"
+#include "mp_tcgen05.cuh"
+
+namespace mpgb {
+
+struct CorrShared {
+    uint64_t full[kMaxStages];
+    uint64_t empty[kMaxStages];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+MP_DEV void corr_timeout(int* err, CorrShared* sh) {
+    atomicCAS(err, 0, static_cast<int>(MP_ERR_TIMEOUT));
+    *reinterpret_cast<volatile int*>(&sh->abort) = 1;
+}
+
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    corr_top8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const CorrArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    // operand tiles need 1024-byte alignment for the 128-byte swizzle atoms
+    const uint32_t base_u32 = smem_u32(smem_raw);
+    uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
+    const int TN = a.TN;
+    const uint32_t a_bytes = kBM * kRowBytes;
+    const uint32_t b_bytes = static_cast<uint32_t>(TN) * kRowBytes;
+    uint8_t* tilesA = smem;
+    uint8_t* tilesB = smem + a.stages * a_bytes;
+    CorrShared* sh = reinterpret_cast<CorrShared*>(tilesB + a.stages * b_bytes);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_act = *a.n_act;
+    const int n_rt = (n_act + kBM - 1) / kBM;
+    const int n_tiles = n_rt * a.n_at;
+    if (static_cast<int>(blockIdx.x) >= n_tiles) return;   // uniform across the CTA
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(&sh->full[s], 1);
+            mbar_init(&sh->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sh->tfull[b], 1);
+            mbar_init(&sh->tempty[b], 4 * 32);
+        }
+        mbar_init(&sh->drain, 1);
+        sh->abort = 0;
+        fence_mbar_init();
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    if (warp == 1) tmem_alloc(&sh->tmem_base, static_cast<uint32_t>(a.tmem_cols));
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+    const uint64_t lim = a.watchdog_ns;
+
+    if (warp == 0) {
+        // ---------------- TMA producer (one thread)
+        if (lane == 0) {
+            long long g = 0;
+            const int kelems = a.fp8 ? kRowBytes : kRowBytes / 2;
+            bool stop = false;
+            for (int tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x) {
+                const int rt = tile % n_rt, at = tile / n_rt;
+                for (int kb = 0; kb < a.nk; ++kb) {
+                    const int s = static_cast<int>(g % a.stages);
+                    const long long use = g / a.stages;
+                    if (use > 0 && !mbar_wait_bounded(&sh->empty[s], static_cast<uint32_t>((use - 1) & 1), lim)) {
+                        corr_timeout(a.err, sh);
+                        stop = true;
+                        break;
+                    }
+                    if (*reinterpret_cast<volatile int*>(&sh->abort)) {
+                        stop = true;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&sh->full[s], a_bytes + b_bytes);
+                    tma_load_2d(tilesA + s * a_bytes, &tmA, kb * kelems, rt * kBM, &sh->full[s]);
+                    tma_load_2d(tilesB + s * b_bytes, &tmB, kb * kelems, at * TN, &sh->full[s]);
+                    ++g;
+                }
+            }
+            // every issued load lands before the CTA may exit: the only load
+            // that can be in flight in stage s is the last one issued to it
+            for (int s = 0; s < a.stages && s < g; ++s) {
+                const long long last = g - 1 - ((g - 1 - s) % a.stages);
+                mbar_wait_bounded(&sh->full[s], static_cast<uint32_t>((last / a.stages) & 1), lim);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (one thread)
+        if (lane == 0) {
+            const uint32_t idesc = make_idesc(kBM, TN, a.fp8 ? 0u : 1u);
+            long long g = 0;
+            int li = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++li) {
+                const int buf = li & 1, useb = li >> 1;
+                if (useb > 0 && !mbar_wait_bounded(&sh->tempty[buf], static_cast<uint32_t>((useb - 1) & 1), lim)) {
+                    corr_timeout(a.err, sh);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + static_cast<uint32_t>(buf * TN);
+                for (int kb = 0; kb < a.nk; ++kb, ++g) {
+                    const int s = static_cast<int>(g % a.stages);
+                    if (!mbar_wait_bounded(&sh->full[s], static_cast<uint32_t>((g / a.stages) & 1), lim) ||
+                        *reinterpret_cast<volatile int*>(&sh->abort)) {
+                        corr_timeout(a.err, sh);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(tilesA + s * a_bytes);
+                    const uint32_t sb = smem_u32(tilesB + s * b_bytes);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        // 32 bytes of K per instruction: 16 BF16 or 32 E4M3 values
+                        const uint64_t ad = sw128_kmajor_desc(sa + 32u * k);
+                        const uint64_t bd = sw128_kmajor_desc(sb + 32u * k);
+                        const uint32_t acc = (kb | k) ? 1u : 0u;
+                        if (a.fp8) mma_fp8(d, ad, bd, idesc, acc);
+                        else mma_bf16(d, ad, bd, idesc, acc);
+                    }
+                    mma_commit(&sh->empty[s]);   // stage reusable once these MMAs finish
+                }
+                if (ok) mma_commit(&sh->tfull[buf]);
+            }
+            // no MMA may still write TMEM when it is freed: this commit
+            // arrives once every MMA issued above has completed
+            mma_commit(&sh->drain);
+            mbar_wait_bounded(&sh->drain, 0u, lim);
+        }
+    } else {
+        // ---------------- epilogue: one TMEM lane (= one signal row) per thread
+        const int q = warp & 3;               // TMEM lane quadrant this warp may access
+        int li = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++li) {
+            const int rt = tile % n_rt, at = tile / n_rt;
+            const int buf = li & 1, useb = li >> 1;
+            bool ok = mbar_wait_bounded(&sh->tfull[buf], static_cast<uint32_t>(useb & 1), lim) &&
+                      !*reinterpret_cast<volatile int*>(&sh->abort);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) corr_timeout(a.err, sh);
+                break;
+            }
+            tc_fence_after();
+            const int row = rt * kBM + q * 32 + lane;
+            float ts[kTop];
+            int ti[kTop];
+#pragma unroll
+            for (int k = 0; k < kTop; ++k) {
+                ts[k] = -1.f;
+                ti[k] = 0x7fffffff;
+            }
+            const int m0 = at * TN;
+            for (int c = 0; c < TN / 32; ++c) {
+                float v[32];
+                tmem_ld_32cols(tmem + (static_cast<uint32_t>(q * 32) << 16) +
+                                   static_cast<uint32_t>(buf * TN + c * 32),
+                               v);
+                if (a.dump && row < n_act) {
+                    const float rsc = a.fp8 ? a.rscale[row] : 1.f;
+                    for (int j = 0; j < 32; ++j) {
+                        const int m = m0 + c * 32 + j;
+                        if (m < a.M) a.dump[static_cast<size_t>(row) * a.M + m] = v[j] * (a.fp8 ? a.colscale[m] * rsc : 1.f);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int m = m0 + c * 32 + j;
+                    if (m >= a.M) continue;
+                    float s = fabsf(v[j]);
+                    if (a.fp8) s *= __ldg(a.colscale + m);
+                    // strict: an equal score keeps the earlier (smaller) atom
+                    if (s > ts[kTop - 1]) {
+                        ts[kTop - 1] = s;
+                        ti[kTop - 1] = m;
+#pragma unroll
+                        for (int k = kTop - 1; k > 0; --k) {
+                            if (ts[k] > ts[k - 1]) {
+                                const float f = ts[k];
+                                ts[k] = ts[k - 1];
+                                ts[k - 1] = f;
+                                const int ii = ti[k];
+                                ti[k] = ti[k - 1];
+                                ti[k - 1] = ii;
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&sh->tempty[buf]);
+            if (row < n_act) {
+                uint2* o = a.cand + (static_cast<size_t>(row) * a.n_at + at) * kTop;
+#pragma unroll
+                for (int k = 0; k < kTop; ++k) o[k] = make_uint2(__float_as_uint(ts[k]), static_cast<uint32_t>(ti[k]));
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, static_cast<uint32_t>(a.tmem_cols));
+    }
+}
+
+
+int corr_smem_bytes(int TN) {
+    return 1024 + corr_stages(TN) * (kBM * kRowBytes + TN * kRowBytes) + static_cast<int>(sizeof(CorrShared));
+}
+
+cudaError_t corr_prepare() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(corr_top8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         std::max(corr_smem_bytes(128), corr_smem_bytes(256)));
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CorrArgs& a, int grid,
+                             cudaStream_t st) {
+    corr_top8_kernel<<<std::max(grid, 1), kGemmThreads, corr_smem_bytes(a.TN), st>>>(tmA, tmB, a);
+    return cudaGetLastError();
+}
+
+}  // namespace mpgb
