@@ -136,8 +136,14 @@ typedef enum {
                                /* grid barrier (watchdog test), -1 = off             */
     MP_OPT_GRID_CTAS = 4,      /* grid modes: CTA count (0 = one per SM)             */
     MP_OPT_BATCH_TILE_N = 5,   /* batched: atoms per GEMM tile (0 = autotuned)       */
-    MP_OPT_PLAIN_PREFETCH = 6  /* grid streaming: stages pulled into L2 ahead of the */
+    MP_OPT_PLAIN_PREFETCH = 6, /* grid streaming: stages pulled into L2 ahead of the */
                                /* shared-memory ring (0 = off, the default)          */
+    MP_OPT_BATCH_CLUSTER = 7,  /* batched GEMM: CTAs per cluster sharing one atom    */
+                               /* tile by TMA multicast: 1, 2, 4 (0 = auto)          */
+    MP_OPT_PLAIN_STAGE_BYTES = 8, /* grid streaming: target bytes per ring stage     */
+                               /* (whole atoms, at least one; default 16384)         */
+    MP_OPT_PLAIN_EVICT_FIRST = 9  /* grid streaming: 1 = evict-first L2 hint on the  */
+                               /* streamed atoms (default), 0 = no hint              */
 } mp_option;
 
 /* Read-only plan properties for mp_plan_query. */

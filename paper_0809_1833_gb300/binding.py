@@ -36,6 +36,9 @@ MP_OPT_DEBUG_SKIP_ARRIVE = 3
 MP_OPT_GRID_CTAS = 4
 MP_OPT_BATCH_TILE_N = 5
 MP_OPT_PLAIN_PREFETCH = 6
+MP_OPT_BATCH_CLUSTER = 7
+MP_OPT_PLAIN_STAGE_BYTES = 8
+MP_OPT_PLAIN_EVICT_FIRST = 9
 
 MP_Q_PLAIN_MODE = 1
 MP_Q_PLAIN_CTAS = 2

@@ -44,8 +44,12 @@ struct CorrArgs {
 
 int corr_smem_bytes(int TN);
 cudaError_t corr_prepare();
-cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CorrArgs& a, int grid,
-                             cudaStream_t st);
+int corr_max_clusters(int CL, int TN);
+// Launch with clusters of CL (1, 2 or 4) CTAs along the signal rows; tmB's
+// box is TN/CL atom rows.  max_row_tiles bounds the row tiles any step of
+// this launch can see (it sizes the grid).
+cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CorrArgs& a, int max_row_tiles,
+                             int CL, cudaStream_t st);
 
 // ------------------------------------------------------------------ batch engine
 // Per-signal state of a slot.
@@ -74,6 +78,7 @@ struct BatchEngine {
     int cap_pad = 0;        // rows of the GEMM operand (multiple of 128)
     int prec = -1;
     int TN = 0;
+    int CL = 1;             // GEMM cluster size along signal rows
     int n_at = 0;
     int ldq = 0;            // operand row: elements (BF16) or bytes (FP8)
     float* R32 = nullptr;

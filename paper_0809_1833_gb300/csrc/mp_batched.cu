@@ -450,10 +450,18 @@ size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x) {
            sizeof(SlotState) + 6 * sizeof(int) + sizeof(double) + sizeof(float) + (with_x ? sizeof(float) * p->M : 0);
 }
 
+// GEMM cluster size: the option, else the largest of 4, 2, 1 not exceeding
+// the engine's row tiles (a cluster's CTAs share one atom tile).
+static int choose_cluster(const PlanImpl* p, int cap) {
+    if (p->batch_cluster) return p->batch_cluster;
+    const int rt = (cap + kBM - 1) / kBM;
+    return rt >= 4 ? 4 : (rt >= 2 ? 2 : 1);
+}
+
 static mp_status engine_prepare(PlanImpl* p, int prec, int cap) {
     BatchEngine* e = p->batch;
     const int TN = p->batch_tile_n ? p->batch_tile_n : 256;
-    if (e && e->prec == prec && e->cap >= cap && e->TN == TN) return MP_OK;
+    if (e && e->prec == prec && e->cap >= cap && e->TN == TN && e->CL == choose_cluster(p, e->cap)) return MP_OK;
     if (!e) e = p->batch = new BatchEngine();
     return engine_alloc(e, p, prec, std::max(cap, e->cap));
 }
@@ -465,6 +473,7 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap) {
     e->cap_pad = (newcap + kBM - 1) / kBM * kBM;
     e->prec = prec;
     e->TN = TN;
+    e->CL = choose_cluster(p, newcap);
     e->n_at = (p->M + TN - 1) / TN;
     const bool fp8 = prec == MP_PREC_FP8E4M3;
     e->ldq = fp8 ? p->ldK8 : p->ldK16;
@@ -504,7 +513,8 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap) {
         return cuda_fail(r, "batched engine allocation");
     }
     mp_status s = make_map(&e->tmA, e->Rq, fp8, e->cap_pad, e->ldq, kBM);
-    if (s == MP_OK) s = make_map(&e->tmB, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, TN);
+    // each CTA of a GEMM cluster loads TN / CL atom rows and multicasts them
+    if (s == MP_OK) s = make_map(&e->tmB, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, TN / e->CL);
     if (s != MP_OK) {
         engine_free(e);
         return s;
@@ -550,8 +560,7 @@ static cudaError_t launch_fixup(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
 static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
     int* fin_count = e->counters + 2;
     int* fin_list = e->fin_list;
-    const int max_tiles = (e->cap_pad / kBM) * e->n_at;
-    cudaError_t r = launch_corr_top8(e->tmA, e->tmB, corr_args(p, e), std::min(max_tiles, p->sm_count), st);
+    cudaError_t r = launch_corr_top8(e->tmA, e->tmB, corr_args(p, e), e->cap_pad / kBM, e->CL, st);
     if (r != cudaSuccess) return r;
     SelArgs sa;
     sa.n_act = e->counters;
@@ -797,8 +806,7 @@ mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B,
     CorrArgs ca = corr_args(p, e);
     ca.dump = C;
     ca.rscale = e->rscale;
-    const int tiles = ((B + kBM - 1) / kBM) * e->n_at;
-    MP_CUDA_TRY(launch_corr_top8(e->tmA, e->tmB, ca, std::min(tiles, p->sm_count), st));
+    MP_CUDA_TRY(launch_corr_top8(e->tmA, e->tmB, ca, (B + kBM - 1) / kBM, e->CL, st));
     p->launches += 2;
     MP_CUDA_TRY(cudaMemcpyAsync(e->h_err, e->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaStreamSynchronize(st));

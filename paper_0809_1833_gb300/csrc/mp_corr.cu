@@ -4,6 +4,13 @@
 // 128-byte swizzling, FP32 accumulators in TMEM, and per signal row the 8
 // largest |c| of each atom tile kept in registers and written out, so the
 // correlation matrix itself is never stored.
+//
+// Operand reuse: a cluster of CL CTAs takes CL consecutive 128-signal row
+// tiles of one atom tile.  Each CTA loads its own rows of R, but only 1/CL of
+// the atom tile, and multicasts that slice to every CTA of the cluster; a
+// stage is refilled only after all CL CTAs released it (their MMA commits are
+// multicast to every CTA's "empty" barrier).  The atom operand, the larger
+// one, then crosses from L2 once per cluster instead of once per CTA.
 #include <cuda.h>
 
 #include <algorithm>
@@ -29,30 +36,38 @@ MP_DEV void corr_timeout(int* err, CorrShared* sh) {
     *reinterpret_cast<volatile int*>(&sh->abort) = 1;
 }
 
+template <int CL>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     corr_top8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const CorrArgs a) {
     extern __shared__ uint8_t smem_raw[];
     // operand tiles need 1024-byte alignment for the 128-byte swizzle atoms
+    // (the same offset in every CTA, as multicast writes the same offsets)
     const uint32_t base_u32 = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
     const int TN = a.TN;
     const uint32_t a_bytes = kBM * kRowBytes;
     const uint32_t b_bytes = static_cast<uint32_t>(TN) * kRowBytes;
+    const uint32_t slice_bytes = b_bytes / CL;   // this CTA's share of the atom tile
     uint8_t* tilesA = smem;
     uint8_t* tilesB = smem + a.stages * a_bytes;
     CorrShared* sh = reinterpret_cast<CorrShared*>(tilesB + a.stages * b_bytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = CL > 1 ? static_cast<int>(cluster_ctarank()) : 0;     // rank in the cluster
+    const int cid = static_cast<int>(blockIdx.x) / CL;
+    const int n_clusters = static_cast<int>(gridDim.x) / CL;
     const int n_act = *a.n_act;
     const int n_rt = (n_act + kBM - 1) / kBM;
-    const int n_tiles = n_rt * a.n_at;
-    if (static_cast<int>(blockIdx.x) >= n_tiles) return;   // uniform across the CTA
+    const int n_rg = (n_rt + CL - 1) / CL;         // groups of CL row tiles
+    const int n_ct = n_rg * a.n_at;                 // cluster tiles
+    if (cid >= n_ct) return;                        // uniform across the cluster
+    const uint16_t all = static_cast<uint16_t>((1u << CL) - 1u);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
             mbar_init(&sh->full[s], 1);
-            mbar_init(&sh->empty[s], 1);
+            mbar_init(&sh->empty[s], CL);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sh->tfull[b], 1);
@@ -67,6 +82,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     if (warp == 1) tmem_alloc(&sh->tmem_base, static_cast<uint32_t>(a.tmem_cols));
     tc_fence_before();
     __syncthreads();
+    if (CL > 1) cluster_sync_all();   // every CTA's barriers exist before any multicast
     tc_fence_after();
     const uint32_t tmem = sh->tmem_base;
     const uint64_t lim = a.watchdog_ns;
@@ -77,11 +93,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             long long g = 0;
             const int kelems = a.fp8 ? kRowBytes : kRowBytes / 2;
             bool stop = false;
-            for (int tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x) {
-                const int rt = tile % n_rt, at = tile / n_rt;
+            for (int ct = cid; ct < n_ct && !stop; ct += n_clusters) {
+                const int rt = (ct % n_rg) * CL + q, at = ct / n_rg;
                 for (int kb = 0; kb < a.nk; ++kb) {
                     const int s = static_cast<int>(g % a.stages);
                     const long long use = g / a.stages;
+                    // all CL CTAs released the stage's previous use
                     if (use > 0 && !mbar_wait_bounded(&sh->empty[s], static_cast<uint32_t>((use - 1) & 1), lim)) {
                         corr_timeout(a.err, sh);
                         stop = true;
@@ -93,15 +110,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     }
                     mbar_arrive_expect_tx(&sh->full[s], a_bytes + b_bytes);
                     tma_load_2d(tilesA + s * a_bytes, &tmA, kb * kelems, rt * kBM, &sh->full[s]);
-                    tma_load_2d(tilesB + s * b_bytes, &tmB, kb * kelems, at * TN, &sh->full[s]);
+                    if (CL == 1)
+                        tma_load_2d(tilesB + s * b_bytes, &tmB, kb * kelems, at * TN, &sh->full[s]);
+                    else
+                        tma_load_2d_multicast(tilesB + s * b_bytes + q * slice_bytes, &tmB, kb * kelems,
+                                              at * TN + q * (TN / CL), &sh->full[s], all);
                     ++g;
                 }
             }
-            // every issued load lands before the CTA may exit: the only load
-            // that can be in flight in stage s is the last one issued to it
+            // before the CTA may exit: its own loads have landed (the only one
+            // that can be in flight in stage s is the last one issued to it),
+            // and every CTA of the cluster released the stages' last uses, so
+            // no peer still writes into this CTA or arrives on its barriers
             for (int s = 0; s < a.stages && s < g; ++s) {
                 const long long last = g - 1 - ((g - 1 - s) % a.stages);
                 mbar_wait_bounded(&sh->full[s], static_cast<uint32_t>((last / a.stages) & 1), lim);
+                mbar_wait_bounded(&sh->empty[s], static_cast<uint32_t>((last / a.stages) & 1), lim);
             }
         }
     } else if (warp == 1) {
@@ -111,7 +135,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             long long g = 0;
             int li = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++li) {
+            for (int ct = cid; ct < n_ct && ok; ct += n_clusters, ++li) {
                 const int buf = li & 1, useb = li >> 1;
                 if (useb > 0 && !mbar_wait_bounded(&sh->tempty[buf], static_cast<uint32_t>((useb - 1) & 1), lim)) {
                     corr_timeout(a.err, sh);
@@ -139,7 +163,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                         if (a.fp8) mma_fp8(d, ad, bd, idesc, acc);
                         else mma_bf16(d, ad, bd, idesc, acc);
                     }
-                    mma_commit(&sh->empty[s]);   // stage reusable once these MMAs finish
+                    // stage reusable once these MMAs finish (in every CTA that
+                    // will refill it with a multicast)
+                    if (CL == 1) mma_commit(&sh->empty[s]);
+                    else mma_commit_multicast(&sh->empty[s], all);
                 }
                 if (ok) mma_commit(&sh->tfull[buf]);
             }
@@ -150,10 +177,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
     } else {
         // ---------------- epilogue: one TMEM lane (= one signal row) per thread
-        const int q = warp & 3;               // TMEM lane quadrant this warp may access
+        const int quad = warp & 3;            // TMEM lane quadrant this warp may access
         int li = 0;
-        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++li) {
-            const int rt = tile % n_rt, at = tile / n_rt;
+        for (int ct = cid; ct < n_ct; ct += n_clusters, ++li) {
+            const int rt = (ct % n_rg) * CL + q, at = ct / n_rg;
             const int buf = li & 1, useb = li >> 1;
             bool ok = mbar_wait_bounded(&sh->tfull[buf], static_cast<uint32_t>(useb & 1), lim) &&
                       !*reinterpret_cast<volatile int*>(&sh->abort);
@@ -163,7 +190,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 break;
             }
             tc_fence_after();
-            const int row = rt * kBM + q * 32 + lane;
+            const int row = rt * kBM + quad * 32 + lane;
             float ts[kTop];
             int ti[kTop];
 #pragma unroll
@@ -174,7 +201,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             const int m0 = at * TN;
             for (int c = 0; c < TN / 32; ++c) {
                 float v[32];
-                tmem_ld_32cols(tmem + (static_cast<uint32_t>(q * 32) << 16) +
+                tmem_ld_32cols(tmem + (static_cast<uint32_t>(quad * 32) << 16) +
                                    static_cast<uint32_t>(buf * TN + c * 32),
                                v);
                 if (a.dump && row < n_act) {
@@ -223,26 +250,84 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         tc_fence_after();
         tmem_dealloc(tmem, static_cast<uint32_t>(a.tmem_cols));
     }
+    if (CL > 1) cluster_sync_all();   // no CTA leaves while a peer may still address it
 }
-
 
 int corr_smem_bytes(int TN) {
     return 1024 + corr_stages(TN) * (kBM * kRowBytes + TN * kRowBytes) + static_cast<int>(sizeof(CorrShared));
 }
 
+template <int CL>
+static cudaError_t set_attrs() {
+    cudaError_t e = cudaFuncSetAttribute(corr_top8_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         std::max(corr_smem_bytes(128), corr_smem_bytes(256)));
+    return e;
+}
+
 cudaError_t corr_prepare() {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(corr_top8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         std::max(corr_smem_bytes(128), corr_smem_bytes(256)));
+    cudaError_t e = set_attrs<1>();
+    if (e == cudaSuccess) e = set_attrs<2>();
+    if (e == cudaSuccess) e = set_attrs<4>();
     if (e == cudaSuccess) done = true;
     return e;
 }
 
-cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CorrArgs& a, int grid,
-                             cudaStream_t st) {
-    corr_top8_kernel<<<std::max(grid, 1), kGemmThreads, corr_smem_bytes(a.TN), st>>>(tmA, tmB, a);
-    return cudaGetLastError();
+// Largest number of CL-CTA clusters that can be resident at once.
+int corr_max_clusters(int CL, int TN) {
+    static int cache[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
+    const int ci = CL == 1 ? 0 : (CL == 2 ? 1 : 2), ti = TN == 256 ? 1 : 0;
+    if (cache[ci][ti] >= 0) return cache[ci][ti];
+    int sm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+    int n = sm / CL;
+    if (CL > 1 && corr_prepare() == cudaSuccess) {
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(CL);
+        lc.blockDim = dim3(kGemmThreads);
+        lc.dynamicSmemBytes = corr_smem_bytes(TN);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = CL;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        int k = 0;
+        cudaError_t e = CL == 2 ? cudaOccupancyMaxActiveClusters(&k, corr_top8_kernel<2>, &lc)
+                                : cudaOccupancyMaxActiveClusters(&k, corr_top8_kernel<4>, &lc);
+        if (e == cudaSuccess && k > 0) n = std::min(n, k);
+        cudaGetLastError();
+    }
+    cache[ci][ti] = n;
+    return n;
+}
+
+cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CorrArgs& a, int max_row_tiles,
+                             int CL, cudaStream_t st) {
+    // enough clusters for the largest tile count this launch can see
+    const int max_ct = ((max_row_tiles + CL - 1) / CL) * a.n_at;
+    const int clusters = std::max(1, std::min(max_ct, corr_max_clusters(CL, a.TN)));
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(clusters * CL);
+    lc.blockDim = dim3(kGemmThreads);
+    lc.dynamicSmemBytes = corr_smem_bytes(a.TN);
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    switch (CL) {
+        case 1: return cudaLaunchKernelEx(&lc, corr_top8_kernel<1>, tmA, tmB, a);
+        case 2: return cudaLaunchKernelEx(&lc, corr_top8_kernel<2>, tmA, tmB, a);
+        case 4: return cudaLaunchKernelEx(&lc, corr_top8_kernel<4>, tmA, tmB, a);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace mpgb

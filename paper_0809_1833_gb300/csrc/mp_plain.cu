@@ -55,6 +55,7 @@ struct PlainArgs {
     double eps2;
     int stage_atoms, stages;
     int prefetch;          // mode 3: L2 prefetch distance in stages (0 = off)
+    int evict_first;       // mode 3: evict-first L2 hint on the streamed atoms
     int off_sh, off_data;
     PlainWorkspace* ws;
     int* tr_atoms;
@@ -140,8 +141,11 @@ MP_DEV void plain_producer(const PlainArgs& a, PlainShared* sh, float* ring, int
         const int nat = min(A, na - j * A);
         const uint32_t bytes = static_cast<uint32_t>(nat) * ldN * 4u;
         mbar_arrive_expect_tx(&sh->full[slot], bytes);
-        bulk_g2s_evict_first(ring + slot * stage_floats, a.psi + static_cast<size_t>(atom0) * ldN,
-                             bytes, &sh->full[slot], pol);
+        if (a.evict_first)
+            bulk_g2s_evict_first(ring + slot * stage_floats, a.psi + static_cast<size_t>(atom0) * ldN, bytes,
+                                 &sh->full[slot], pol);
+        else
+            bulk_g2s(ring + slot * stage_floats, a.psi + static_cast<size_t>(atom0) * ldN, bytes, &sh->full[slot]);
         // L2 as a deeper window than the shared-memory ring: pull the stage
         // `prefetch` positions ahead into L2 now, so HBM keeps streaming
         // while the ring is full during the per-iteration exchange.
@@ -464,7 +468,7 @@ mp_status plain_configure(PlanImpl* p, PlainConfig* cfg) {
     }
     // mode 3: choose compute warps W, atoms per stage A, ring depth D (a multiple of W)
     const long long apc = (M + G - 1) / G;
-    long long A = std::max<long long>(1, 16384 / atom_bytes);
+    long long A = std::max<long long>(1, p->stage_bytes / atom_bytes);
     A = std::min(A, apc);
     const long long stage_bytes = A * atom_bytes;
     for (int W : {4, 2, 1}) {
@@ -501,6 +505,7 @@ mp_status plain_launch(PlanImpl* p, const float* y, float* x, const mp_stop* sto
     a.stage_atoms = cfg.stage_atoms;
     a.stages = cfg.stages;
     a.prefetch = cfg.mode == 3 ? p->prefetch_stages : 0;
+    a.evict_first = p->evict_first;
     a.off_sh = cfg.off_sh;
     a.off_data = cfg.off_data;
     a.ws = ws;

@@ -277,6 +277,18 @@ mp_status mp_plan_set_option(mp_plan_t plan, int option, long long value) {
             if (value < 0 || value > 256) return fail(MP_ERR_INVALID, "prefetch distance must be 0..256");
             p->prefetch_stages = static_cast<int>(value);
             return MP_OK;
+        case MP_OPT_PLAIN_STAGE_BYTES:
+            if (value < 16 || value > (1 << 20)) return fail(MP_ERR_INVALID, "stage bytes must be 16..1 MiB");
+            p->stage_bytes = static_cast<int>(value);
+            return MP_OK;
+        case MP_OPT_PLAIN_EVICT_FIRST:
+            p->evict_first = value ? 1 : 0;
+            return MP_OK;
+        case MP_OPT_BATCH_CLUSTER:
+            if (value != 0 && value != 1 && value != 2 && value != 4)
+                return fail(MP_ERR_INVALID, "batch cluster size must be 0, 1, 2 or 4");
+            p->batch_cluster = static_cast<int>(value);
+            return MP_OK;
         case MP_OPT_BATCH_TILE_N:
             if (value != 0 && value != 128 && value != 256)
                 return fail(MP_ERR_INVALID, "batch tile must be 0, 128 or 256");

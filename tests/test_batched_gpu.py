@@ -44,10 +44,14 @@ def e4m3_rows(a):
     return q.astype(np.float64), s.astype(np.float64)
 
 
+@pytest.mark.parametrize("cluster", [1, 2, 4])
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
-@pytest.mark.parametrize("shape", [(256, 1000, 200), (100, 300, 5), (2048, 1024, 130)],
+@pytest.mark.parametrize("shape", [(256, 1000, 200), (100, 300, 5), (2048, 1024, 130), (192, 777, 600)],
                          ids=lambda s: f"N{s[0]}_M{s[1]}_B{s[2]}")
-def test_tensor_core_correlations(prec, shape):
+def test_tensor_core_correlations(prec, shape, cluster):
+    """Every cluster size (atom tile shared by TMA multicast across 1, 2 or
+    4 CTAs) gives the exact quantised product, including row tiles beyond
+    the batch and a ragged last atom tile."""
     T = torch()
     N, M, Bn = shape
     psi = W.gaussian_dictionary(N, M, seed=3)
@@ -55,6 +59,7 @@ def test_tensor_core_correlations(prec, shape):
     R = rng.standard_normal((Bn, N)).astype(np.float32)
     p = B().MP_PREC_BF16 if prec == "bf16" else B().MP_PREC_FP8E4M3
     with GpuPlan(psi, prec_mask=1 << p) as pl:
+        pl.set(B().MP_OPT_BATCH_CLUSTER, cluster)
         Rd = T.from_numpy(R).cuda()
         C = T.full((Bn, M), float("nan"), dtype=T.float32, device="cuda")
         B().mp_debug_correlations(pl.plan, p, Rd.data_ptr(), Bn, C.data_ptr(), cur_stream())
@@ -90,11 +95,13 @@ def run_batched(pl, prec, Y, stops, cap=4096):
     return s, res, X.cpu().numpy(), atoms.cpu().numpy(), coefs.cpu().numpy()
 
 
+@pytest.mark.parametrize("cluster", [1, 4])
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
-def test_batched_matches_plain_and_oracle(prec):
+def test_batched_matches_plain_and_oracle(prec, cluster):
     prob = W.make_batched(256, 1024, 300, 2, 16, seed=5, eps=1e-5, T=3000)
     p = B().MP_PREC_BF16 if prec == "bf16" else B().MP_PREC_FP8E4M3
     with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
+        pl.set(B().MP_OPT_BATCH_CLUSTER, cluster)
         s, res, X, atoms, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
         assert s == 0
         n_same = 0
