@@ -141,7 +141,7 @@ typedef enum {
     MP_OPT_BATCH_CLUSTER = 7,  /* batched GEMM: CTAs per cluster sharing one atom    */
                                /* tile by TMA multicast: 1, 2, 4 (0 = auto)          */
     MP_OPT_PLAIN_STAGE_BYTES = 8, /* grid streaming: target bytes per ring stage     */
-                               /* (whole atoms, at least one; default 16384)         */
+                               /* (whole atoms, at least one; default 32768)         */
     MP_OPT_PLAIN_EVICT_FIRST = 9  /* grid streaming: 1 = evict-first L2 hint on the  */
                                /* streamed atoms (default), 0 = no hint              */
 } mp_option;

@@ -21,8 +21,9 @@ constexpr int corr_stages(int TN) {
                ? (kSmemOptin - 2048) / (kBM * kRowBytes + TN * kRowBytes)
                : kMaxStages;
 }
-constexpr int kTop = 8;             // low-precision candidates kept per signal and atom tile
-constexpr int kGemmThreads = 192;   // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kTop = 8;             // low-precision candidates kept per signal and list
+constexpr int kEpiGroups = 4;       // epilogue warp groups: each scans 1/4 of a tile's atoms
+constexpr int kGemmThreads = 32 * (2 + 4 * kEpiGroups);   // warp 0 TMA, warp 1 MMA, then epilogue
 
 // Arguments of the correlation GEMM.
 struct CorrArgs {
@@ -35,7 +36,7 @@ struct CorrArgs {
     int tmem_cols;
     int stages;             // pipeline depth, corr_stages(TN)
     const float* colscale;  // FP8 per-atom scale
-    uint2* cand;            // [row][n_at][8] = (score bits, atom), sorted by score
+    uint2* cand;            // [row][n_at * kEpiGroups][8] = (score bits, atom), each list sorted
     unsigned long long watchdog_ns;
     int* err;
     float* dump;            // diagnostic: full correlation rows (row * M + m), or NULL

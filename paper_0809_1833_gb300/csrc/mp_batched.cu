@@ -446,7 +446,7 @@ size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x) {
     const bool fp8 = prec == MP_PREC_FP8E4M3;
     const size_t TN = p->batch_tile_n ? p->batch_tile_n : 256;
     const size_t n_at = (p->M + TN - 1) / TN;
-    return sizeof(float) * p->ldN + (fp8 ? p->ldK8 : 2 * p->ldK16) + sizeof(uint2) * n_at * kTop +
+    return sizeof(float) * p->ldN + (fp8 ? p->ldK8 : 2 * p->ldK16) + sizeof(uint2) * n_at * kEpiGroups * kTop +
            sizeof(SlotState) + 6 * sizeof(int) + sizeof(double) + sizeof(float) + (with_x ? sizeof(float) * p->M : 0);
 }
 
@@ -493,7 +493,7 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap) {
     A(&e->done, sizeof(int) * C);
     A(&e->holes, sizeof(int) * C);
     A(&e->surv, sizeof(int) * C);
-    A(&e->cand, sizeof(uint2) * C * e->n_at * kTop);
+    A(&e->cand, sizeof(uint2) * C * e->n_at * kEpiGroups * kTop);
     A(&e->eps2, sizeof(double) * C);
     A(&e->T, sizeof(int) * C);
     A(&e->err, sizeof(int));
@@ -567,7 +567,7 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
     sa.act = e->act;
     sa.done = e->done;
     sa.cand = e->cand;
-    sa.n_at = e->n_at;
+    sa.n_at = e->n_at * kEpiGroups;   // sorted candidate lists per signal
     sa.psi32 = p->psi32;
     sa.ldN = p->ldN;
     sa.N = p->N;

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sh->tfull[b], 1);
-            mbar_init(&sh->tempty[b], 4 * 32);
+            mbar_init(&sh->tempty[b], 4 * 32 * kEpiGroups);
         }
         mbar_init(&sh->drain, 1);
         sh->abort = 0;
@@ -176,8 +176,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             mbar_wait_bounded(&sh->drain, 0u, lim);
         }
     } else {
-        // ---------------- epilogue: one TMEM lane (= one signal row) per thread
-        const int quad = warp & 3;            // TMEM lane quadrant this warp may access
+        // ---------------- epilogue: kEpiGroups threads per signal row; a warp
+        // reads the TMEM lane quadrant warp % 4 (the quadrant a warp may
+        // access), and warp group grp scans atom columns [grp, grp+1) * TN/kEpiGroups
+        const int quad = warp & 3;
+        const int grp = (warp - 2) >> 2;
+        const int cols = TN / kEpiGroups;
         int li = 0;
         for (int ct = cid; ct < n_ct; ct += n_clusters, ++li) {
             const int rt = (ct % n_rg) * CL + q, at = ct / n_rg;
@@ -198,11 +202,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 ts[k] = -1.f;
                 ti[k] = 0x7fffffff;
             }
-            const int m0 = at * TN;
-            for (int c = 0; c < TN / 32; ++c) {
+            const int m0 = at * TN + grp * cols;
+            for (int c = 0; c < cols / 32; ++c) {
                 float v[32];
                 tmem_ld_32cols(tmem + (static_cast<uint32_t>(quad * 32) << 16) +
-                                   static_cast<uint32_t>(buf * TN + c * 32),
+                                   static_cast<uint32_t>(buf * TN + grp * cols + c * 32),
                                v);
                 if (a.dump && row < n_act) {
                     const float rsc = a.fp8 ? a.rscale[row] : 1.f;
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             tc_fence_before();
             mbar_arrive(&sh->tempty[buf]);
             if (row < n_act) {
-                uint2* o = a.cand + (static_cast<size_t>(row) * a.n_at + at) * kTop;
+                uint2* o = a.cand + ((static_cast<size_t>(row) * a.n_at + at) * kEpiGroups + grp) * kTop;
 #pragma unroll
                 for (int k = 0; k < kTop; ++k) o[k] = make_uint2(__float_as_uint(ts[k]), static_cast<uint32_t>(ti[k]));
             }

@@ -92,7 +92,7 @@ struct PlanImpl {
     int batch_tile_n = 0;
     int batch_cluster = 0;          // batched GEMM cluster size (0 = auto)
     int prefetch_stages = 0;        // plain streaming: L2 prefetch distance (measured slower; off)
-    int stage_bytes = 16384;        // plain streaming: target bytes per ring stage
+    int stage_bytes = 32768;        // plain streaming: target bytes per ring stage
     int evict_first = 1;            // plain streaming: L2 evict-first hint on the stream
 
     long long launches = 0;

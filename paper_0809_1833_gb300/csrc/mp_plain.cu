@@ -248,14 +248,15 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
                 best = scan_atoms(data + static_cast<size_t>(j) * ldN, r, ldN, min(4, na - j), a0 + j,
                                   lane, best);
         } else {
+            // slot s belongs to warp s % ncw, which consumes the slot's uses
+            // in order (so it never waits two phases ahead on a barrier)
             const int S = (na + A - 1) / A;
             const long long seq0 = static_cast<long long>(t) * S;
-            int j = static_cast<int>(((cw - seq0) % ncw + ncw) % ncw);
-            for (; j < S; j += ncw) {
-                const long long seq = seq0 + j;
-                const int slot = static_cast<int>(seq % D);
-                if (!mbar_wait_bounded(&sh->full[slot], static_cast<uint32_t>((seq / D) & 1),
-                                       a.watchdog_ns)) {
+            int slot = static_cast<int>(seq0 % D);
+            uint32_t par = static_cast<uint32_t>((seq0 / D) & 1);
+            for (int j = 0; j < S; ++j, slot = slot + 1 == D ? (par ^= 1u, 0) : slot + 1) {
+                if (slot % ncw != cw) continue;
+                if (!mbar_wait_bounded(&sh->full[slot], par, a.watchdog_ns)) {
                     if (lane == 0) {
                         atomicCAS(&a.ws->err, 0, static_cast<int>(MP_ERR_TIMEOUT));
                         *reinterpret_cast<volatile int*>(&sh->abort) = 1;
@@ -471,20 +472,19 @@ mp_status plain_configure(PlanImpl* p, PlainConfig* cfg) {
     long long A = std::max<long long>(1, p->stage_bytes / atom_bytes);
     A = std::min(A, apc);
     const long long stage_bytes = A * atom_bytes;
-    for (int W : {4, 2, 1}) {
-        long long D = std::min<long long>(kMaxStages, budget / stage_bytes);
-        D -= D % W;
-        if (D >= std::max(W, 2)) {
-            cfg->ctas = G;
-            cfg->threads = 32 * (1 + W);
-            cfg->stage_atoms = static_cast<int>(A);
-            cfg->stages = static_cast<int>(D);
-            cfg->smem = static_cast<int>(cfg->off_data + D * stage_bytes);
-            return MP_OK;
-        }
-    }
-    return fail(MP_ERR_UNSUPPORTED, "plain decode: N=" + std::to_string(p->N) +
-                                        " leaves no room for a two-stage ring");
+    // as deep a ring as fits; up to 4 consumer warps, each owning the slots
+    // s with s % W == its index (D need not be a multiple of W)
+    const long long D = std::min<long long>(kMaxStages, budget / stage_bytes);
+    if (D < 2)
+        return fail(MP_ERR_UNSUPPORTED, "plain decode: N=" + std::to_string(p->N) +
+                                            " leaves no room for a two-stage ring");
+    const int W = static_cast<int>(std::min<long long>(4, D));
+    cfg->ctas = G;
+    cfg->threads = 32 * (1 + W);
+    cfg->stage_atoms = static_cast<int>(A);
+    cfg->stages = static_cast<int>(D);
+    cfg->smem = static_cast<int>(cfg->off_data + D * stage_bytes);
+    return MP_OK;
 }
 
 mp_status plain_launch(PlanImpl* p, const float* y, float* x, const mp_stop* stop, const mp_trace* trace,
