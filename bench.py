@@ -139,11 +139,16 @@ def cpu_baseline(psi, y, eps, T, full_iters, budget_s=15.0):
     decode; extrapolate to recoveries/s with the full decode's iteration
     count."""
     from oracle import mp_oracle as orc
-    # one iteration to size the sample
+    # size the sample from a short run (21 minus 1 iterations, so the
+    # oracle's one-off FP64 copy of the dictionary cancels), then time a run
+    # of about budget_s seconds
     t0 = time.perf_counter()
     orc.mp(psi, y, eps, 1, record=False)
-    t1 = time.perf_counter() - t0
-    n = int(max(3, min(full_iters, budget_s / max(t1, 1e-6))))
+    t1 = time.perf_counter()
+    orc.mp(psi, y, eps, 21, record=False)
+    t2 = time.perf_counter()
+    est = max(((t2 - t1) - (t1 - t0)) / 20.0, 1e-6)
+    n = int(max(3, min(full_iters, budget_s / est)))
     t0 = time.perf_counter()
     out = orc.mp(psi, y, eps, n, record=False)
     dt = time.perf_counter() - t0
