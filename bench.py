@@ -207,8 +207,9 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_0809_1833_gb300 import binding as B
 
+    from paper_0809_1833_gb300 import dp
     n_sig = 4
-    w, psi_np, Y_np, sigs = make_problem(n_sig, seed=rank * 7919)
+    w, psi_np, Y_np, sigs = make_problem(n_sig, seed=dp.rank_seed(0, rank))
     N, M = w["N"], w["M"]
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
@@ -251,14 +252,11 @@ def run_ours(args):
         dist.barrier()
     launches = B.mp_plan_query(plan, B.MP_Q_KERNEL_LAUNCHES) - l0
     clk = clocks.stop()
-    elapsed_ms = start.elapsed_time(end)
     per_launch_ms = [a.elapsed_time(b) for a, b in ev]
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    total_recoveries = args.steps * world
-    value = total_recoveries / (elapsed_ms / 1e3)
+    # max time over ranks, recoveries summed over ranks (no data-path collective)
+    elapsed_s, total_recoveries = dp.aggregate(start.elapsed_time(end) / 1e3, args.steps, dev)
+    elapsed_ms = 1e3 * elapsed_s
+    value = total_recoveries / elapsed_s
 
     # roofline of the persistent kernel: algorithmic bytes = 4 N M per iteration
     step_iters = [iters[i % n_sig] for i in range(args.steps)]
@@ -280,12 +278,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     for i in range(args.steps):
         B.mp_recover_host(plan, y_host[i % n_sig], x_host, w["eps"], w["T"])
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": total_recoveries / e2e_s, "unit": "recoveries/s", "h2d_bytes_per_step": 4 * N,
+    e2e_s, e2e_total = dp.aggregate(time.perf_counter() - t0, args.steps, dev)
+    e2e = {"value": e2e_total / e2e_s, "unit": "recoveries/s", "h2d_bytes_per_step": 4 * N,
            "d2h_bytes_per_step": 4 * M + 56}
 
     line = {
@@ -308,6 +302,7 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(psi_np, Y_np[0], w["eps"], w["T"], iters[0], args.cpu_budget)
     B.mp_plan_destroy(plan)
     if rank == 0 and not args.no_batched:
+        line["plain_small"] = plain_small_measure()
         # batched low-precision form vs the plain FP32 kernel on the same signals
         line["batched"] = [batched_measure("bf16"), batched_measure("fp8", n_plain=4)]
     if rank == 0 and args.served_duration > 0:
@@ -319,6 +314,41 @@ def run_ours(args):
 
 
 BATCHED = {"bf16": "batched_bf16_N2048_M8192_B1024", "fp8": "batched_fp8_N8192_M32768_B256"}
+
+
+def plain_small_measure(reps=20):
+    """The 1 MiB plain workload (N=256, M=1024, K=16): the dictionary sits in
+    shared memory, so an iteration costs the exchange, not the stream.
+    Times every launch shape that can hold it."""
+    import torch
+    from paper_0809_1833_gb300 import binding as B
+    from paper_0809_1833_gb300 import workloads as W
+    name = "plain_fp32_N256_M1024_K16"
+    w = W.WORKLOADS[name]
+    prob = W.make_workload(name, seed=0)
+    s = torch.cuda.current_stream().cuda_stream
+    d = torch.from_numpy(prob.psi).cuda()
+    plan = B.mp_plan_create(prob.N, prob.M, d.data_ptr(), stream=s)
+    y = torch.from_numpy(prob.y[0]).cuda()
+    x = torch.empty(prob.M, device="cuda")
+    out = {"workload": name, "auto_mode": B.mp_plan_query(plan, B.MP_Q_PLAIN_MODE), "shapes": {}}
+    for mode, label in ((1, "cluster_resident"), (2, "grid_resident"), (3, "grid_stream")):
+        B.mp_plan_set_option(plan, B.MP_OPT_PLAIN_MODE, mode)
+        if B.mp_plan_query(plan, B.MP_Q_PLAIN_MODE) != mode:
+            continue
+        _, r = B.mp_recover(plan, y.data_ptr(), x.data_ptr(), w["eps"], w["T"], None, True, s)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            B.mp_recover(plan, y.data_ptr(), x.data_ptr(), w["eps"], w["T"], None, False, s)
+        b.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 1e3 / reps
+        out["shapes"][label] = {"ctas": B.mp_plan_query(plan, B.MP_Q_PLAIN_CTAS), "iterations": r.iters,
+                                "us_per_iteration": 1e6 * t / r.iters, "recoveries_per_s": 1.0 / t,
+                                "dictionary_GBps_from_smem": 4.0 * prob.N * prob.M * r.iters / t / 1e9}
+    B.mp_plan_destroy(plan)
+    return out
 
 
 def batched_measure(prec_name, reps=3, n_plain=16, profile=False):
@@ -346,6 +376,8 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False):
         B.mp_plan_destroy(plan)
         return {"profile_case": name}
     times = []
+    shape = {"atoms_per_tile": B.mp_plan_query(plan, B.MP_Q_BATCH_TILE_N),
+             "cluster_ctas": B.mp_plan_query(plan, B.MP_Q_BATCH_CLUSTER), "chosen_by": "autotuner"}
     l0 = B.mp_plan_query(plan, B.MP_Q_KERNEL_LAUNCHES)
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -379,7 +411,7 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False):
             "support_score_mean": float(np.mean(supp_b)), "support_score_min": float(np.min(supp_b)),
             "plain_support_score_mean": float(np.mean(supp_p)),
             "iterations_total": int(iters.sum()), "iterations_max": int(iters.max()),
-            "effective_tflops": flops / tb / 1e12, "gpu_launches_per_batch": int(launches)}
+            "effective_tflops": flops / tb / 1e12, "gpu_launches_per_batch": int(launches), "gemm_shape": shape}
 
 
 def served_measure(rate=2000.0, duration=10.0, pool=48, seed=0, max_slots=256):

@@ -142,8 +142,10 @@ typedef enum {
                                /* tile by TMA multicast: 1, 2, 4 (0 = auto)          */
     MP_OPT_PLAIN_STAGE_BYTES = 8, /* grid streaming: target bytes per ring stage     */
                                /* (whole atoms, at least one; default 32768)         */
-    MP_OPT_PLAIN_EVICT_FIRST = 9  /* grid streaming: 1 = evict-first L2 hint on the  */
+    MP_OPT_PLAIN_EVICT_FIRST = 9, /* grid streaming: 1 = evict-first L2 hint on the  */
                                /* streamed atoms (default), 0 = no hint              */
+    MP_OPT_BATCH_AUTOTUNE = 10 /* batched: 1 = time the GEMM tile shapes on the first */
+                               /* batch of each size bucket (default), 0 = heuristic */
 } mp_option;
 
 /* Read-only plan properties for mp_plan_query. */
@@ -156,7 +158,9 @@ typedef enum {
     MP_Q_PLAIN_STAGES = 6,     /* streaming mode: ring depth                         */
     MP_Q_LD_FP32 = 7,          /* padded row length of the FP32 atom copy, floats    */
     MP_Q_DEVICE_BYTES = 8,     /* device memory owned by the plan, bytes             */
-    MP_Q_KERNEL_LAUNCHES = 9   /* kernels this library launched for the plan so far  */
+    MP_Q_KERNEL_LAUNCHES = 9,  /* kernels this library launched for the plan so far  */
+    MP_Q_BATCH_TILE_N = 10,    /* atoms per GEMM tile of the current batch state     */
+    MP_Q_BATCH_CLUSTER = 11    /* GEMM cluster size of the current batch state       */
 } mp_query;
 
 /* ------------------------------------------------------------------ */
@@ -257,6 +261,16 @@ MPGB_API mp_status mp_recover_host(mp_plan_t plan, const float* y_host, float* x
 MPGB_API mp_status mp_recover_batched(mp_plan_t plan, int prec, const float* Y, float* X, int B,
                              const mp_stop* stops, int n_stops, const mp_trace* trace,
                              mp_result* host_out, void* stream);
+
+/* Autotuner of the batched correlation GEMM: times each tile shape (128 or
+ * 256 atoms per tile; 1, 2 or 4 CTAs sharing an atom tile by multicast) on
+ * B synthetic rows at precision `prec`, keeps the fastest for B's size
+ * bucket (the next power of two, at least 128) and returns it.  With the
+ * default MP_OPT_BATCH_AUTOTUNE = 1, mp_recover_batched runs the same
+ * timing on its own first batch of a new bucket.  Options MP_OPT_BATCH_TILE_N
+ * / MP_OPT_BATCH_CLUSTER, when set, override the result.  Synchronises the
+ * legacy default stream.  tile_n, cluster: may be NULL. */
+MPGB_API mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* cluster);
 
 /* Diagnostic: the tensor-core correlations of the batched path, written out
  * in full.  R (device, B x N floats) is quantised as the batched step does

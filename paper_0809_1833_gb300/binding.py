@@ -39,6 +39,9 @@ MP_OPT_PLAIN_PREFETCH = 6
 MP_OPT_BATCH_CLUSTER = 7
 MP_OPT_PLAIN_STAGE_BYTES = 8
 MP_OPT_PLAIN_EVICT_FIRST = 9
+MP_OPT_BATCH_AUTOTUNE = 10
+MP_Q_BATCH_TILE_N = 10
+MP_Q_BATCH_CLUSTER = 11
 
 MP_Q_PLAIN_MODE = 1
 MP_Q_PLAIN_CTAS = 2
@@ -109,6 +112,7 @@ SIGNATURES = {
     "mp_recover_batched": (_I, [_P, _I, _P, _P, _I, ctypes.POINTER(mp_stop), _I,
                                 ctypes.POINTER(mp_trace), ctypes.POINTER(mp_result), _P]),
     "mp_debug_correlations": (_I, [_P, _I, _P, _I, _P, _P]),
+    "mp_plan_autotune": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "mp_recover_noalloc": (_I, [_P, _I, _I, _I, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_result), _P]),
     "mp_server_create": (_I, [ctypes.POINTER(_P), ctypes.c_size_t, _I, _I]),
     "mp_server_add_dictionary": (_I, [_P, _P, _I, ctypes.POINTER(_I)]),
@@ -235,6 +239,13 @@ def mp_recover_batched(plan, prec, Y_ptr, X_ptr, B, stops, trace=None, stream=No
     if raise_on_error:
         check(s, "mp_recover_batched")
     return s, list(res)[:int(B)]
+
+
+def mp_plan_autotune(plan, prec, B):
+    """Returns the (atoms per tile, cluster size) the autotuner picked."""
+    tn, cl = ctypes.c_int(), ctypes.c_int()
+    check(lib().mp_plan_autotune(plan, int(prec), int(B), ctypes.byref(tn), ctypes.byref(cl)), "mp_plan_autotune")
+    return tn.value, cl.value
 
 
 def mp_recover_noalloc(psi_ptr, N, M, ld, y_ptr, x_ptr, stop, result, stream=None):

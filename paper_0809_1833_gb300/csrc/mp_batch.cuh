@@ -114,7 +114,7 @@ struct BatchEngine {
 // Bytes of device memory one slot costs (residual, operand row, candidates,
 // state, an output row of M floats when the engine owns X).
 size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x);
-mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int cap);
+mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int cap, int tile_n, int cluster);
 void engine_free(BatchEngine* e);
 // Admit n signals: rows Y (device, n x N), into slots `slots_dev` (device,
 // NULL = 0..n-1), with per-signal eps^2 and T already in e->eps2 / e->T.

@@ -444,36 +444,42 @@ void batch_destroy(BatchEngine* b) {
 
 size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x) {
     const bool fp8 = prec == MP_PREC_FP8E4M3;
-    const size_t TN = p->batch_tile_n ? p->batch_tile_n : 256;
+    const size_t TN = 128;   // the narrowest tile the shape choice may pick (most candidate lists)
     const size_t n_at = (p->M + TN - 1) / TN;
     return sizeof(float) * p->ldN + (fp8 ? p->ldK8 : 2 * p->ldK16) + sizeof(uint2) * n_at * kEpiGroups * kTop +
            sizeof(SlotState) + 6 * sizeof(int) + sizeof(double) + sizeof(float) + (with_x ? sizeof(float) * p->M : 0);
 }
 
-// GEMM cluster size: the option, else the largest of 4, 2, 1 not exceeding
-// the engine's row tiles (a cluster's CTAs share one atom tile).
-static int choose_cluster(const PlanImpl* p, int cap) {
-    if (p->batch_cluster) return p->batch_cluster;
-    const int rt = (cap + kBM - 1) / kBM;
-    return rt >= 4 ? 4 : (rt >= 2 ? 2 : 1);
+mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_t st, int* tn_out, int* cl_out);
+
+mp_status batch_shape(PlanImpl* p, int prec, int B, const float* R, cudaStream_t st, int* tile_n, int* cluster) {
+    const int rt = (B + kBM - 1) / kBM;
+    int tn = 256, cl = rt >= 4 ? 4 : (rt >= 2 ? 2 : 1);
+    if (p->batch_autotune && !p->batch_tile_n && !p->batch_cluster) {
+        mp_status s = autotune(p, prec, B, R, st, &tn, &cl);
+        if (s != MP_OK) return s;
+    }
+    if (p->batch_tile_n) tn = p->batch_tile_n;
+    if (p->batch_cluster) cl = p->batch_cluster;
+    *tile_n = tn;
+    *cluster = cl;
+    return MP_OK;
 }
 
-static mp_status engine_prepare(PlanImpl* p, int prec, int cap) {
+static mp_status engine_prepare(PlanImpl* p, int prec, int cap, int TN, int CL) {
     BatchEngine* e = p->batch;
-    const int TN = p->batch_tile_n ? p->batch_tile_n : 256;
-    if (e && e->prec == prec && e->cap >= cap && e->TN == TN && e->CL == choose_cluster(p, e->cap)) return MP_OK;
+    if (e && e->prec == prec && e->cap >= cap && e->TN == TN && e->CL == CL) return MP_OK;
     if (!e) e = p->batch = new BatchEngine();
-    return engine_alloc(e, p, prec, std::max(cap, e->cap));
+    return engine_alloc(e, p, prec, std::max(cap, e->cap), TN, CL);
 }
 
-mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap) {
-    const int TN = p->batch_tile_n ? p->batch_tile_n : 256;
+mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, int TN, int CL) {
     engine_free(e);
     e->cap = newcap;
     e->cap_pad = (newcap + kBM - 1) / kBM * kBM;
     e->prec = prec;
     e->TN = TN;
-    e->CL = choose_cluster(p, newcap);
+    e->CL = CL;
     e->n_at = (p->M + TN - 1) / TN;
     const bool fp8 = prec == MP_PREC_FP8E4M3;
     e->ldq = fp8 ? p->ldK8 : p->ldK16;
@@ -666,7 +672,10 @@ cudaError_t engine_admit(PlanImpl* p, BatchEngine* e, const float* Y, int n, con
 
 static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, long long ldx, int B, const mp_stop* stops,
                              int n_stops, const mp_trace* trace, mp_result* out, cudaStream_t st) {
-    mp_status s = engine_prepare(p, prec, B);
+    int TN = 256, CL = 1;
+    mp_status s = batch_shape(p, prec, B, Y, st, &TN, &CL);
+    if (s != MP_OK) return s;
+    s = engine_prepare(p, prec, B, TN, CL);
     if (s != MP_OK) return s;
     BatchEngine* e = p->batch;
     s = engine_build_graph(p, e, kStepsPerGraph, false, nullptr, nullptr, nullptr, nullptr);
@@ -781,7 +790,10 @@ mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B,
     if (!(p->prec_mask & (1u << prec)))
         return fail(MP_ERR_UNSUPPORTED, "mp_debug_correlations: the plan holds no copy for this precision");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    mp_status s = engine_prepare(p, prec, B);
+    int TN = 256, CL = 1;
+    mp_status s = batch_shape(p, prec, B, R, st, &TN, &CL);
+    if (s != MP_OK) return s;
+    s = engine_prepare(p, prec, B, TN, CL);
     if (s != MP_OK) return s;
     BatchEngine* e = p->batch;
     MP_CUDA_TRY(corr_prepare());
@@ -811,6 +823,133 @@ mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B,
     MP_CUDA_TRY(cudaMemcpyAsync(e->h_err, e->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaStreamSynchronize(st));
     if (*e->h_err) return fail(static_cast<mp_status>(*e->h_err), "mp_debug_correlations: device wait timed out");
+    return MP_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ autotuner
+namespace mpgb {
+
+// Deterministic pseudo-random rows in [-1, 1) (splitmix-style hash of the
+// element index): stand-in residuals for timing the GEMM.
+__global__ void fill_rows_kernel(float* R, int B, int N, unsigned seed) {
+    const size_t n = static_cast<size_t>(B) * N;
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        unsigned long long z = (i + 1) * 0x9E3779B97F4A7C15ull + seed;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        R[i] = static_cast<float>(static_cast<double>(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+    }
+}
+
+static int batch_bucket(int B) {
+    int b = 128;
+    while (b < B) b *= 2;
+    return b;
+}
+
+// Time the correlation GEMM for B active rows with tile width TN and cluster
+// size CL; returns microseconds per launch (or a negative value on failure).
+static double time_gemm(PlanImpl* p, int prec, int B, int TN, int CL, const float* R, cudaStream_t st) {
+    BatchEngine e;
+    double us = -1.0;
+    if (engine_alloc(&e, p, prec, B, TN, CL) == MP_OK && corr_prepare() == cudaSuccess) {
+        for (int b = 0; b < B; ++b) {
+            e.h_eps2[b] = 0.0;
+            e.h_T[b] = 1;
+        }
+        BatchIO io;
+        std::memset(&io, 0, sizeof(io));
+        *e.h_io = io;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaError_t r = cudaMemcpyAsync(e.eps2, e.h_eps2, sizeof(double) * B, cudaMemcpyHostToDevice, st);
+        if (r == cudaSuccess) r = cudaMemcpyAsync(e.T, e.h_T, sizeof(int) * B, cudaMemcpyHostToDevice, st);
+        if (r == cudaSuccess) r = cudaMemcpyAsync(e.io, e.h_io, sizeof(BatchIO), cudaMemcpyHostToDevice, st);
+        if (r == cudaSuccess) r = cudaMemsetAsync(e.counters, 0, sizeof(int) * 4, st);
+        if (r == cudaSuccess) {
+            admit_kernel<<<B, kSelThreads, 0, st>>>(admit_args(p, &e, R, B, nullptr));
+            r = cudaGetLastError();
+        }
+        if (r == cudaSuccess) r = cudaMemcpyAsync(e.counters, &B, sizeof(int), cudaMemcpyHostToDevice, st);
+        if (r == cudaSuccess) r = cudaEventCreate(&e0);
+        if (r == cudaSuccess) r = cudaEventCreate(&e1);
+        const CorrArgs ca = corr_args(p, &e);
+        const int rt = (B + kBM - 1) / kBM;
+        for (int it = 0; it < 2 && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, ca, rt, e.CL, st);
+        if (r == cudaSuccess) r = cudaEventRecord(e0, st);
+        const int reps = 5;
+        for (int it = 0; it < reps && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, ca, rt, e.CL, st);
+        if (r == cudaSuccess) r = cudaEventRecord(e1, st);
+        if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (r == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) us = 1e3 * ms / reps;
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        p->launches += 2 + reps + 1;
+    }
+    engine_free(&e);
+    return us;
+}
+
+mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_t st, int* tn_out, int* cl_out) {
+    const int bucket = batch_bucket(B);
+    for (const TuneEntry& t : p->tuned)
+        if (t.prec == prec && t.bucket == bucket) {
+            *tn_out = t.tile_n;
+            *cl_out = t.cluster;
+            return MP_OK;
+        }
+    float* R = nullptr;
+    if (!R_dev) {
+        MP_CUDA_TRY(cudaMallocAsync(&R, sizeof(float) * static_cast<size_t>(B) * p->N, st));
+        fill_rows_kernel<<<256, 256, 0, st>>>(R, B, p->N, 12345u);
+        MP_CUDA_TRY(cudaGetLastError());
+        p->launches++;
+    }
+    double best = -1.0;
+    int best_tn = 256, best_cl = 1;
+    const int rt = (B + kBM - 1) / kBM;
+    for (int tn : {256, 128}) {
+        for (int cl : {1, 2, 4}) {
+            if (cl > 1 && cl > rt) continue;
+            const double us = time_gemm(p, prec, B, tn, cl, R_dev ? R_dev : R, st);
+            if (us > 0.0 && (best < 0.0 || us < best)) {
+                best = us;
+                best_tn = tn;
+                best_cl = cl;
+            }
+        }
+    }
+    if (R) cudaFreeAsync(R, st);
+    if (best < 0.0) return fail(MP_ERR_CUDA, "autotune: no tile shape could be timed");
+    p->tuned.push_back(TuneEntry{prec, bucket, best_tn, best_cl, best});
+    *tn_out = best_tn;
+    *cl_out = best_cl;
+    return MP_OK;
+}
+
+}  // namespace mpgb
+
+extern "C" {
+
+mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* cluster) {
+    clear_error();
+    if (!plan || B < 1) return fail(MP_ERR_INVALID, "mp_plan_autotune: bad argument");
+    PlanImpl* p = &plan->impl;
+    if (prec != MP_PREC_BF16 && prec != MP_PREC_FP8E4M3)
+        return fail(MP_ERR_INVALID, "mp_plan_autotune: precision must be BF16 or FP8");
+    if (!(p->prec_mask & (1u << prec)))
+        return fail(MP_ERR_UNSUPPORTED, "mp_plan_autotune: the plan holds no copy for this precision");
+    int tn = 0, cl = 0;
+    mp_status s = autotune(p, prec, B, nullptr, nullptr, &tn, &cl);
+    if (s != MP_OK) return s;
+    if (tile_n) *tile_n = tn;
+    if (cluster) *cluster = cl;
     return MP_OK;
 }
 

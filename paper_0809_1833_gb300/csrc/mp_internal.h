@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/mpgb.h"
 
@@ -56,6 +57,15 @@ struct PlainConfig {
 
 struct BatchEngine;        // batched decode state (mp_batched.cu)
 
+// Autotuned batched-GEMM shape for one (precision, batch-size bucket).
+struct TuneEntry {
+    int prec;
+    int bucket;
+    int tile_n;
+    int cluster;
+    double us;             // measured GEMM time per launch
+};
+
 struct PlanImpl {
     int N = 0, M = 0;
     int ldN = 0;           // FP32 atom stride (floats), multiple of 32
@@ -91,6 +101,8 @@ struct PlanImpl {
     int grid_ctas = 0;
     int batch_tile_n = 0;
     int batch_cluster = 0;          // batched GEMM cluster size (0 = auto)
+    int batch_autotune = 1;         // time the GEMM shapes on first use of a batch size
+    std::vector<TuneEntry> tuned;
     int prefetch_stages = 0;        // plain streaming: L2 prefetch distance (measured slower; off)
     int stage_bytes = 32768;        // plain streaming: target bytes per ring stage
     int evict_first = 1;            // plain streaming: L2 evict-first hint on the stream
@@ -107,6 +119,10 @@ mp_status plain_result_to_host(const PlanImpl* p, const PlainWorkspace* h, mp_re
 
 // Batched engine teardown (mp_batched.cu).
 void batch_destroy(BatchEngine* b);
+// GEMM shape (atoms per tile, cluster size) for a batch of B signals: the
+// plan's options if set, else the autotuned choice (timed now on first use
+// of the batch-size bucket, on rows R when given), else a heuristic.
+mp_status batch_shape(PlanImpl* p, int prec, int B, const float* R, cudaStream_t st, int* tile_n, int* cluster);
 
 }  // namespace mpgb
 

@@ -9,6 +9,7 @@
 #include <new>
 #include <vector>
 
+#include "mp_batch.cuh"
 #include "mp_device.cuh"
 #include "mp_internal.h"
 
@@ -284,6 +285,9 @@ mp_status mp_plan_set_option(mp_plan_t plan, int option, long long value) {
         case MP_OPT_PLAIN_EVICT_FIRST:
             p->evict_first = value ? 1 : 0;
             return MP_OK;
+        case MP_OPT_BATCH_AUTOTUNE:
+            p->batch_autotune = value ? 1 : 0;
+            return MP_OK;
         case MP_OPT_BATCH_CLUSTER:
             if (value != 0 && value != 1 && value != 2 && value != 4)
                 return fail(MP_ERR_INVALID, "batch cluster size must be 0, 1, 2 or 4");
@@ -314,6 +318,8 @@ mp_status mp_plan_query(mp_plan_t plan, int what, long long* value) {
         case MP_Q_LD_FP32: *value = p->ldN; return MP_OK;
         case MP_Q_DEVICE_BYTES: *value = static_cast<long long>(p->device_bytes); return MP_OK;
         case MP_Q_KERNEL_LAUNCHES: *value = p->launches; return MP_OK;
+        case MP_Q_BATCH_TILE_N: *value = p->batch ? p->batch->TN : 0; return MP_OK;
+        case MP_Q_BATCH_CLUSTER: *value = p->batch ? p->batch->CL : 0; return MP_OK;
     }
     return fail(MP_ERR_INVALID, "unknown query " + std::to_string(what));
 }

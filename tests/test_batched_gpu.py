@@ -121,6 +121,25 @@ def test_batched_matches_plain_and_oracle(prec, cluster):
         assert n_same >= prob.B - 3, n_same
 
 
+def test_autotuner_picks_a_valid_shape_and_results_do_not_depend_on_it():
+    prob = W.make_batched(256, 2048, 260, 2, 12, seed=6, eps=1e-5, T=2000)
+    p = B().MP_PREC_BF16
+    with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
+        tn, cl = B().mp_plan_autotune(pl.plan, p, prob.B)
+        assert tn in (128, 256) and cl in (1, 2, 4)
+        assert B().mp_plan_autotune(pl.plan, p, prob.B) == (tn, cl)      # cached per size bucket
+        s, res, X, _, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
+        assert s == 0
+        assert (pl.query(B().MP_Q_BATCH_TILE_N), pl.query(B().MP_Q_BATCH_CLUSTER)) == (tn, cl)
+        other = (128 if tn == 256 else 256, 1)
+        pl.set(B().MP_OPT_BATCH_TILE_N, other[0])
+        pl.set(B().MP_OPT_BATCH_CLUSTER, other[1])
+        s2, res2, X2, _, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
+        assert (pl.query(B().MP_Q_BATCH_TILE_N), pl.query(B().MP_Q_BATCH_CLUSTER)) == other
+    assert s2 == 0 and np.array_equal(X, X2)
+    assert [r.iters for r in res] == [r.iters for r in res2]
+
+
 def test_batched_edge_cases():
     psi = W.gaussian_dictionary(64, 300, seed=2)
     prob = W.make_batched(64, 300, 6, 1, 3, seed=2, psi=psi, eps=1e-5, T=500)
