@@ -309,11 +309,21 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
         const int m = key_index(key);
         const float c = key_coef(key);
 
-        // ---- Eq. 11: r <- r - c psi_m, and e = sum r^2 in FP64
+        // ---- Eq. 11: r <- r - c psi_m, and e = sum r^2 in FP64.  In the
+        // cluster shape psi_m is resident in its owner CTA's shared memory
+        // and is read from there over DSMEM; otherwise from global memory.
         const float4* pm = reinterpret_cast<const float4*>(a.psi + static_cast<size_t>(m) * ldN);
+        uint32_t pm_cluster = 0;
+        if (CLUSTER) {
+            // owner of atom m under the slice split above
+            const int big = rem * (base + 1);
+            const int own = m < big ? m / (base + 1) : rem + (m - big) / base;
+            const int own_a0 = own * base + min(own, rem);
+            pm_cluster = mapa_shared(smem_u32(data + static_cast<size_t>(m - own_a0) * ldN), static_cast<uint32_t>(own));
+        }
         acc = 0.0;
         for (int k = ct; k < n4r; k += nct) {
-            const float4 pv = __ldg(pm + k);
+            const float4 pv = CLUSTER ? dsmem_ld_f32x4(pm_cluster + 16u * k) : __ldg(pm + k);
             float4 v = r4[k];
             v.x = fmaf(-c, pv.x, v.x);
             v.y = fmaf(-c, pv.y, v.y);
@@ -333,7 +343,9 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
 
         // ---- Eq. 10 and bookkeeping (one thread of CTA 0)
         if (cta == 0 && ct == 0) {
-            a.x[m] += c;
+            // fire-and-forget: same-address reductions from one thread apply
+            // in program order, so x~_m accumulates exactly as x~_m += c would
+            red_add_f32(a.x + m, c);
             if (t < a.tr_cap) {
                 if (a.tr_atoms) a.tr_atoms[t] = m;
                 if (a.tr_coefs) a.tr_coefs[t] = c;
