@@ -514,6 +514,84 @@ def run_profile_case(iters):
     B.mp_plan_destroy(plan)
 
 
+PAPER_TIMING_SIZES = [1000, 3000, 5000, 7000, 9000, 11000, 13000, 15000]
+
+
+def paper_timing_sweep(sizes, reps=3, cpu_budget_s=4.0):
+    """Sec. 4's CPU-vs-GPU sweep: M = 1000..15000, N = M/2, K = 0.07M,
+    Bernoulli Psi, eps = 1e-7, T = N; one decode per size and precision
+    (the FP32 decode on the FP32 dictionary, the FP64 decode on the same
+    dictionary drawn in FP64), timed with CUDA events after a warm-up decode.
+    The CPU column is the FP64 oracle on the host cores, timed over a bounded
+    prefix of the decode and scaled by the GPU FP64 run's iteration count.
+    One JSON line per size."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0809_1833_gb300 import binding as B
+    from paper_0809_1833_gb300 import workloads as W
+    from oracle import mp_oracle as orc
+    st = torch.cuda.current_stream()
+    sh = st.cuda_stream
+    for M in sizes:
+        row = {"M": M}
+        for prec in ("fp32", "fp64"):
+            prob = W.paper_timing_problem(M, seed=0, fp64=prec == "fp64")
+            N, T, eps = prob.N, prob.T, prob.eps
+            row.update(N=N, K=len(prob.supports[0]), T=T, eps=eps)
+            dt = torch.float64 if prec == "fp64" else torch.float32
+            psi = torch.from_numpy(prob.psi).cuda()
+            if prec == "fp64":
+                plan = B.mp_plan_create_f64(N, M, psi.data_ptr(), stream=sh)
+                rec, mode_q = B.mp_recover_f64, B.MP_Q_PLAIN64_MODE
+            else:
+                plan = B.mp_plan_create(N, M, psi.data_ptr(), stream=sh)
+                rec, mode_q = B.mp_recover, B.MP_Q_PLAIN_MODE
+            del psi
+            y = torch.from_numpy(prob.y[0]).cuda()
+            x = torch.empty(M, dtype=dt, device="cuda")
+            rec(plan, y.data_ptr(), x.data_ptr(), eps, T, None, True, sh)
+            times = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                rec(plan, y.data_ptr(), x.data_ptr(), eps, T, None, False, sh)
+                e1.record(st)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            _, r = B.mp_plan_last_result(plan)
+            xh = x.cpu().numpy().astype(np.float64)
+            xt = prob.x_true[0]
+            ms = statistics.median(times)
+            row[prec] = {"ms_per_decode": ms, "iterations": r.iters, "stop_reason": r.stop_reason,
+                         "rel_residual": r.rel_residual, "mode": B.mp_plan_query(plan, mode_q),
+                         "us_per_iteration": 1e3 * ms / max(r.iters, 1),
+                         "dictionary_gbs": (prob.psi.itemsize * N * M * r.iters) / (ms * 1e6),
+                         "E_pct": 100.0 * float(np.sum((xh - xt) ** 2) / np.sum(xt ** 2))}
+            B.mp_plan_destroy(plan)
+            if prec == "fp64":
+                # CPU leg: the FP64 oracle over a bounded prefix of the same decode
+                t0 = time.perf_counter()
+                orc.mp(prob.psi, prob.y[0], eps, 1, record=False)
+                t1 = time.perf_counter()
+                n = 2
+                while True:
+                    t2 = time.perf_counter()
+                    o = orc.mp(prob.psi, prob.y[0], eps, n, record=False)
+                    t3 = time.perf_counter()
+                    if (t3 - t2) > cpu_budget_s / 4 or n >= r.iters:
+                        break
+                    n *= 4
+                per_iter = max((t3 - t2) - (t1 - t0), 1e-9) / max(o["iters"] - 1, 1)
+                row["cpu_fp64_oracle"] = {"ms_per_decode_est": 1e3 * per_iter * r.iters,
+                                          "ms_per_iteration": 1e3 * per_iter, "iterations_timed": o["iters"],
+                                          "cores": os.cpu_count()}
+        c = row["cpu_fp64_oracle"]["ms_per_decode_est"]
+        row["speedup_vs_cpu_oracle"] = {"fp32": c / row["fp32"]["ms_per_decode"],
+                                        "fp64": c / row["fp64"]["ms_per_decode"]}
+        print(json.dumps({"paper_timing": row}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -531,7 +609,13 @@ def main():
                     help="seconds of Poisson arrivals for the served measurement (0 = skip)")
     ap.add_argument("--served-rate", type=float, default=2000.0)
     ap.add_argument("--served-only", action="store_true", help="run only the served measurement")
+    ap.add_argument("--paper-timing", nargs="*", type=int, default=None,
+                    help="run only Sec. 4's CPU-vs-GPU size sweep (FP32 and FP64) at these M "
+                         f"(default {PAPER_TIMING_SIZES})")
     args = ap.parse_args()
+    if args.paper_timing is not None:
+        paper_timing_sweep(args.paper_timing or PAPER_TIMING_SIZES)
+        return
     if args.served_only:
         import __graft_entry__
         __graft_entry__.build()

@@ -66,7 +66,9 @@ typedef enum {
 typedef enum {
     MP_PREC_FP32 = 0,          /* FP32 correlations (CUDA cores)                    */
     MP_PREC_BF16 = 1,          /* BF16 correlations on tcgen05, FP32 top-8 rescore  */
-    MP_PREC_FP8E4M3 = 2        /* FP8-E4M3 per-atom-scaled correlations, FP32 rescore */
+    MP_PREC_FP8E4M3 = 2,       /* FP8-E4M3 per-atom-scaled correlations, FP32 rescore */
+    MP_PREC_FP64 = 3           /* FP64 atoms, residual and correlations (CUDA cores): */
+                               /* the double-precision decode of Sec. 5              */
 } mp_precision;
 
 typedef enum {
@@ -127,6 +129,16 @@ typedef struct {
     int reserved;
 } mp_trace;
 
+/* The same trace for mp_recover_f64: coefficients and residual in FP64. */
+typedef struct {
+    int* atoms;
+    double* coefs;
+    double* energies;
+    double* residual;
+    int capacity;
+    int reserved;
+} mp_trace_f64;
+
 /* Plan options for mp_plan_set_option. */
 typedef enum {
     MP_OPT_PLAIN_MODE = 1,     /* 0 auto, 1 one-cluster resident, 2 grid resident,   */
@@ -160,7 +172,9 @@ typedef enum {
     MP_Q_DEVICE_BYTES = 8,     /* device memory owned by the plan, bytes             */
     MP_Q_KERNEL_LAUNCHES = 9,  /* kernels this library launched for the plan so far  */
     MP_Q_BATCH_TILE_N = 10,    /* atoms per GEMM tile of the current batch state     */
-    MP_Q_BATCH_CLUSTER = 11    /* GEMM cluster size of the current batch state       */
+    MP_Q_BATCH_CLUSTER = 11,   /* GEMM cluster size of the current batch state       */
+    MP_Q_PLAIN64_MODE = 12,    /* mode the next mp_recover_f64 will use (0: none)    */
+    MP_Q_PLAIN64_STAGES = 13   /* its streaming ring depth                           */
 } mp_query;
 
 /* ------------------------------------------------------------------ */
@@ -193,6 +207,18 @@ MPGB_API const char* mp_last_error_message(void);
  * non-finite entry), MP_ERR_NOMEM, MP_ERR_CUDA. */
 MPGB_API mp_status mp_plan_create(mp_plan_t* out, const mp_plan_desc* desc, const float* psi,
                          void* stream);
+
+/* Create a plan from an FP64 dictionary (the paper's double-precision runs
+ * draw Psi in FP64, Eq. 13).  Same contract as mp_plan_create, with psi a
+ * device pointer to N*M doubles.  prec_mask must include MP_PREC_FP64; the
+ * FP64 copy holds the input atoms (scaled to unit norm in FP64 when
+ * desc->normalize), and the FP32 copy (always built) and any BF16/FP8 copy
+ * are those atoms rounded to FP32 first.  The norm check of Eq. 4 runs on
+ * the FP64 atoms.  A plan created by mp_plan_create with MP_PREC_FP64 in
+ * prec_mask instead widens its FP32 atoms exactly, so both decodes read the
+ * same dictionary. */
+MPGB_API mp_status mp_plan_create_f64(mp_plan_t* out, const mp_plan_desc* desc, const double* psi,
+                             void* stream);
 
 /* Release a plan and everything it owns (synchronises the device first).
  * NULL is accepted and ignored. */
@@ -228,6 +254,18 @@ MPGB_API mp_status mp_recover(mp_plan_t plan, const float* y, float* x, const mp
 /* Synchronise the stream of the plan's last mp_recover and return its
  * result (and its device-side status as the return value). */
 MPGB_API mp_status mp_plan_last_result(mp_plan_t plan, mp_result* out);
+
+/* The same decode entirely in FP64 (Sec. 3, Eqs. 8-12 in double precision,
+ * the precision of the paper's reference CPU code): FP64 atoms, residual,
+ * correlations, argmax (ties to the smallest index, compared on all 64 bits
+ * of |c|) and x~.  Launch shapes as for mp_recover with 8-byte elements.
+ *  y : device pointer, N doubles.  x : device pointer, M doubles.
+ *  trace, host_out, stream : as for mp_recover (mp_trace_f64 records FP64
+ *  coefficients and residual).
+ * Errors: as mp_recover, plus MP_ERR_UNSUPPORTED when the plan holds no
+ * FP64 copy (prec_mask without MP_PREC_FP64). */
+MPGB_API mp_status mp_recover_f64(mp_plan_t plan, const double* y, double* x, const mp_stop* stop,
+                         const mp_trace_f64* trace, mp_result* host_out, void* stream);
 
 /* mp_recover with HOST buffers: copies y to the device, decodes, copies x~
  * back, and fills *out.  Blocking.  y_host: N floats; x_host: M floats.

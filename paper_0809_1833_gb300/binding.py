@@ -26,7 +26,7 @@ MP_ERR_CUDA = -6
 MP_ERR_UNSUPPORTED = -7
 MP_ERR_NOT_FOUND = -8
 
-MP_PREC_FP32, MP_PREC_BF16, MP_PREC_FP8E4M3 = 0, 1, 2
+MP_PREC_FP32, MP_PREC_BF16, MP_PREC_FP8E4M3, MP_PREC_FP64 = 0, 1, 2, 3
 MP_LAYOUT_ATOM_MAJOR, MP_LAYOUT_ROW_MAJOR = 0, 1
 MP_STOP_CONVERGED, MP_STOP_MAX_ITERS, MP_STOP_ZERO_Y = 0, 1, 2
 
@@ -52,6 +52,8 @@ MP_Q_PLAIN_STAGES = 6
 MP_Q_LD_FP32 = 7
 MP_Q_DEVICE_BYTES = 8
 MP_Q_KERNEL_LAUNCHES = 9
+MP_Q_PLAIN64_MODE = 12
+MP_Q_PLAIN64_STAGES = 13
 
 
 class mp_plan_desc(ctypes.Structure):
@@ -75,6 +77,10 @@ class mp_result(ctypes.Structure):
 class mp_trace(ctypes.Structure):
     _fields_ = [("atoms", ctypes.c_void_p), ("coefs", ctypes.c_void_p), ("energies", ctypes.c_void_p),
                 ("residual", ctypes.c_void_p), ("capacity", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class mp_trace_f64(ctypes.Structure):
+    _fields_ = mp_trace._fields_
 
 
 class mp_server_stats(ctypes.Structure):
@@ -107,6 +113,9 @@ SIGNATURES = {
     "mp_plan_query": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong)]),
     "mp_recover": (_I, [_P, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_trace),
                         ctypes.POINTER(mp_result), _P]),
+    "mp_plan_create_f64": (_I, [ctypes.POINTER(_P), ctypes.POINTER(mp_plan_desc), _P, _P]),
+    "mp_recover_f64": (_I, [_P, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_trace_f64),
+                            ctypes.POINTER(mp_result), _P]),
     "mp_plan_last_result": (_I, [_P, ctypes.POINTER(mp_result)]),
     "mp_recover_host": (_I, [_P, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_result)]),
     "mp_recover_batched": (_I, [_P, _I, _P, _P, _I, ctypes.POINTER(mp_stop), _I,
@@ -174,6 +183,16 @@ def mp_plan_create(N, M, psi_ptr, layout=MP_LAYOUT_ATOM_MAJOR, prec_mask=0, norm
     return h.value
 
 
+def mp_plan_create_f64(N, M, psi_ptr, layout=MP_LAYOUT_ATOM_MAJOR, prec_mask=1 << MP_PREC_FP64,
+                       normalize=False, stream=None):
+    """Plan from an FP64 dictionary (device pointer to N*M doubles)."""
+    d = mp_plan_desc(int(N), int(M), int(layout), int(prec_mask), 1 if normalize else 0, 0)
+    h = ctypes.c_void_p()
+    check(lib().mp_plan_create_f64(ctypes.byref(h), ctypes.byref(d), ctypes.c_void_p(int(psi_ptr)),
+                                   _stream(stream)), "mp_plan_create_f64")
+    return h.value
+
+
 def mp_plan_destroy(plan):
     return check(lib().mp_plan_destroy(plan), "mp_plan_destroy")
 
@@ -204,6 +223,24 @@ def mp_recover(plan, y_ptr, x_ptr, eps, max_iters, trace=None, sync=True, stream
                          ctypes.byref(res) if sync else None, _stream(stream))
     if raise_on_error:
         check(s, "mp_recover")
+    return s, (res if sync else None)
+
+
+def make_trace_f64(atoms_ptr=0, coefs_ptr=0, energies_ptr=0, capacity=0, residual_ptr=0):
+    return mp_trace_f64(atoms_ptr or None, coefs_ptr or None, energies_ptr or None, residual_ptr or None,
+                        int(capacity), 0)
+
+
+def mp_recover_f64(plan, y_ptr, x_ptr, eps, max_iters, trace=None, sync=True, stream=None,
+                   raise_on_error=True):
+    """FP64 decode of one signal (device pointers to doubles); returns as mp_recover."""
+    st = mp_stop(float(eps), int(max_iters), 0)
+    res = mp_result()
+    s = lib().mp_recover_f64(plan, ctypes.c_void_p(int(y_ptr)), ctypes.c_void_p(int(x_ptr)), ctypes.byref(st),
+                             ctypes.byref(trace) if trace is not None else None,
+                             ctypes.byref(res) if sync else None, _stream(stream))
+    if raise_on_error:
+        check(s, "mp_recover_f64")
     return s, (res if sync else None)
 
 

@@ -751,6 +751,8 @@ mp_status mp_recover_batched(mp_plan_t plan, int prec, const float* Y, float* X,
         if (!(stops[i].eps >= 0.0) || !std::isfinite(stops[i].eps) || stops[i].max_iters < 0 || stops[i].reserved)
             return fail(MP_ERR_INVALID, "mp_recover_batched: bad stop entry " + std::to_string(i));
     PlanImpl* p = &plan->impl;
+    if (prec == MP_PREC_FP64)
+        return fail(MP_ERR_UNSUPPORTED, "mp_recover_batched: FP64 decodes run one signal at a time (mp_recover_f64)");
     if (prec != MP_PREC_FP32 && prec != MP_PREC_BF16 && prec != MP_PREC_FP8E4M3)
         return fail(MP_ERR_INVALID, "mp_recover_batched: unknown precision");
     if (!(p->prec_mask & (1u << prec)))

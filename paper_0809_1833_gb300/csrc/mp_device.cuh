@@ -120,8 +120,16 @@ MP_DEV float4 dsmem_ld_f32x4(uint32_t cluster_addr) {
                  : "memory");
     return v;
 }
-MP_DEV void red_add_f32(float* p, float v) {
+MP_DEV double2 dsmem_ld_f64x2(uint32_t cluster_addr) {
+    double2 v;
+    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(cluster_addr) : "memory");
+    return v;
+}
+MP_DEV void red_add(float* p, float v) {
     asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+MP_DEV void red_add(double* p, double v) {
+    asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
 MP_DEV uint64_t dsmem_ld_u64(uint32_t cluster_addr) {
     uint64_t v;
@@ -170,6 +178,26 @@ MP_DEV unsigned long long umax64(unsigned long long a, unsigned long long b) {
     return a > b ? a : b;
 }
 
+// The same order for FP64 correlations, with |c| kept to all 63 bits: the
+// magnitude in the high word, (index, sign) packed as above in the low word,
+// compared as one 128-bit unsigned number.
+struct Key128 {
+    unsigned long long hi, lo;
+};
+MP_DEV Key128 pack_key(double c, int idx) {
+    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(c));
+    Key128 k;
+    k.hi = bits & 0x7fffffffffffffffull;
+    k.lo = (static_cast<unsigned long long>(0x7fffffffu - static_cast<uint32_t>(idx)) << 1) | (bits >> 63);
+    return k;
+}
+MP_DEV int key_index(Key128 k) { return static_cast<int>(0x7fffffffu - static_cast<uint32_t>(k.lo >> 1)); }
+MP_DEV double key_coef(Key128 k) {
+    return __longlong_as_double(static_cast<long long>(k.hi | ((k.lo & 1ull) << 63)));
+}
+MP_DEV Key128 kmax(Key128 a, Key128 b) { return (a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo)) ? a : b; }
+MP_DEV unsigned long long kmax(unsigned long long a, unsigned long long b) { return umax64(a, b); }
+
 // ---------------------------------------------------------------- reductions
 // Butterfly sums: every lane ends with the same bits (each step adds the
 // same two operands on both partner lanes).
@@ -188,5 +216,16 @@ MP_DEV unsigned long long warp_max_u64(unsigned long long v) {
     for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
+MP_DEV Key128 warp_max_key(Key128 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Key128 w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = kmax(v, w);
+    }
+    return v;
+}
+MP_DEV unsigned long long warp_max_key(unsigned long long v) { return warp_max_u64(v); }
 
 }  // namespace mpgb

@@ -81,6 +81,8 @@ struct PlanImpl {
     void* psi16 = nullptr;          // __nv_bfloat16
     void* psi8 = nullptr;           // __nv_fp8_e4m3
     float* scale8 = nullptr;        // per-atom FP8 scale
+    double* psi64 = nullptr;        // FP64 atom-major copy, stride ldN
+    void* slots64 = nullptr;        // FP64 grid exchange slots (2 x sm_count keys)
 
     PlainWorkspace* ws = nullptr;   // device
     PlainWorkspace* ws_host = nullptr;  // pinned mirror
@@ -116,6 +118,10 @@ mp_status plain_configure(PlanImpl* p, PlainConfig* cfg);
 mp_status plain_launch(PlanImpl* p, const float* y, float* x, const mp_stop* stop,
                        const mp_trace* trace, PlainWorkspace* ws, cudaStream_t st);
 mp_status plain_result_to_host(const PlanImpl* p, const PlainWorkspace* h, mp_result* out);
+// The FP64 decode (the same kernel instantiated for double).
+mp_status plain_configure64(PlanImpl* p, PlainConfig* cfg);
+mp_status plain_launch64(PlanImpl* p, const double* y, double* x, const mp_stop* stop,
+                         const mp_trace_f64* trace, PlainWorkspace* ws, cudaStream_t st);
 
 // Batched engine teardown (mp_batched.cu).
 void batch_destroy(BatchEngine* b);

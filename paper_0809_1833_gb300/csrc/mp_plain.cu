@@ -36,62 +36,110 @@ constexpr int kMaxWarps = 32;
 constexpr int kMaxStages = 64;
 constexpr int kResidentThreads = 256;
 
+// Per-precision types: the argmax key and the 16-byte vector the residual
+// and the atoms are read in.
+template <typename T>
+struct PlainTraits;
+template <>
+struct PlainTraits<float> {
+    using Key = unsigned long long;
+    using V = float4;
+};
+template <>
+struct PlainTraits<double> {
+    using Key = Key128;
+    using V = double2;
+};
+
+template <typename T>
 struct PlainShared {
-    unsigned long long keys[2];          // mode 1: this CTA's key, two-slot ring
-    unsigned long long wkey[kMaxWarps];  // per compute warp best key
+    using Key = typename PlainTraits<T>::Key;
+    Key keys[2];                         // mode 1: this CTA's key, two-slot ring
+    Key wkey[kMaxWarps];                 // per compute warp best key
     double wsum[kMaxWarps];              // per compute warp energy partial
-    unsigned long long key;              // selected key broadcast
+    Key key;                             // selected key broadcast
     int abort;
     int done;
     uint64_t full[kMaxStages];           // mode 3 ring barriers
     uint64_t empty[kMaxStages];
 };
 
+template <typename T>
 struct PlainArgs {
-    const float* psi;      // M x ldN atom-major, zero padded
-    const float* y;        // N
-    float* x;              // M
-    int N, ldN, M, T;
+    const T* psi;          // M x ldN atom-major, zero padded
+    const T* y;            // N
+    T* x;                  // M
+    int N, ldN, M, T_max;
     double eps2;
     int stage_atoms, stages;
     int prefetch;          // mode 3: L2 prefetch distance in stages (0 = off)
     int evict_first;       // mode 3: evict-first L2 hint on the streamed atoms
     int off_sh, off_data;
     PlainWorkspace* ws;
+    Key128* slots;         // FP64 grid exchange: two rings of one key per CTA
     int* tr_atoms;
-    float* tr_coefs;
+    T* tr_coefs;
     double* tr_energy;
-    float* tr_resid;
+    T* tr_resid;
     int tr_cap;
     unsigned long long watchdog_ns;
     int skip_cta;
 };
 
+// ------------------------------------------------------------------ vectors
+MP_DEV double sq_acc(const float4 v, double acc) {
+    acc = fma(static_cast<double>(v.x), static_cast<double>(v.x), acc);
+    acc = fma(static_cast<double>(v.y), static_cast<double>(v.y), acc);
+    acc = fma(static_cast<double>(v.z), static_cast<double>(v.z), acc);
+    acc = fma(static_cast<double>(v.w), static_cast<double>(v.w), acc);
+    return acc;
+}
+MP_DEV double sq_acc(const double2 v, double acc) {
+    acc = fma(v.x, v.x, acc);
+    acc = fma(v.y, v.y, acc);
+    return acc;
+}
+// v - c p, elementwise
+MP_DEV float4 sub_scaled(float c, const float4 p, float4 v) {
+    v.x = fmaf(-c, p.x, v.x);
+    v.y = fmaf(-c, p.y, v.y);
+    v.z = fmaf(-c, p.z, v.z);
+    v.w = fmaf(-c, p.w, v.w);
+    return v;
+}
+MP_DEV double2 sub_scaled(double c, const double2 p, double2 v) {
+    v.x = fma(-c, p.x, v.x);
+    v.y = fma(-c, p.y, v.y);
+    return v;
+}
+MP_DEV void dsmem_ld(uint32_t addr, float4* v) { *v = dsmem_ld_f32x4(addr); }
+MP_DEV void dsmem_ld(uint32_t addr, double2* v) { *v = dsmem_ld_f64x2(addr); }
+MP_DEV void dsmem_ld(uint32_t addr, unsigned long long* k) { *k = dsmem_ld_u64(addr); }
+MP_DEV void dsmem_ld(uint32_t addr, Key128* k) {
+    k->hi = dsmem_ld_u64(addr);
+    k->lo = dsmem_ld_u64(addr + 8u);
+}
+
 // ------------------------------------------------------------------ dots
 // Scan `n` consecutive atoms at p (first index m0) and fold into `best`.
-MP_DEV unsigned long long scan_atoms(const float* __restrict__ p, const float* __restrict__ r,
-                                     int ldN, int n, int m0, int lane, unsigned long long best) {
+template <typename T, typename Key>
+MP_DEV Key scan_atoms(const T* __restrict__ p, const T* __restrict__ r, int ldN, int n, int m0, int lane, Key best) {
     int q = 0;
     for (; q + 4 <= n; q += 4) {
-        float c[4];
+        T c[4];
         dot4(p + static_cast<size_t>(q) * ldN, r, ldN, lane, c);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) best = umax64(best, pack_key(c[i], m0 + q + i));
+        for (int i = 0; i < 4; ++i) best = kmax(best, pack_key(c[i], m0 + q + i));
     }
-    for (; q < n; ++q) best = umax64(best, pack_key(dot1(p + static_cast<size_t>(q) * ldN, r, ldN, lane), m0 + q));
+    for (; q < n; ++q) best = kmax(best, pack_key(dot1(p + static_cast<size_t>(q) * ldN, r, ldN, lane), m0 + q));
     return best;
 }
 
 // ------------------------------------------------------------------ grid barrier
-// Arrive with the CTA's key, wait (bounded) for all G CTAs, read the max.
-MP_DEV bool grid_exchange(const PlainArgs& a, int cta, int G, int t, unsigned long long k,
-                          unsigned long long* out) {
-    PlainWorkspace* ws = a.ws;
-    atomicMax(&ws->keys[t % 3], k);
-    if (!(cta == a.skip_cta && t == 0)) red_release_add_u64(&ws->count, 1ull);
-    const unsigned long long target = static_cast<unsigned long long>(t + 1) * G;
+// Wait (bounded) until all G CTAs arrived at barrier t.
+MP_DEV bool grid_wait(PlainWorkspace* ws, unsigned long long target, unsigned long long limit_ns) {
     if (ld_acquire_u64(&ws->count) < target) {
-        const uint64_t deadline = globaltimer_ns() + a.watchdog_ns;
+        const uint64_t deadline = globaltimer_ns() + limit_ns;
         while (ld_acquire_u64(&ws->count) < target) {
             if (ld_volatile_i32(&ws->err) != 0 || globaltimer_ns() > deadline) {
                 atomicCAS(&ws->err, 0, static_cast<int>(MP_ERR_TIMEOUT));
@@ -99,6 +147,17 @@ MP_DEV bool grid_exchange(const PlainArgs& a, int cta, int G, int t, unsigned lo
             }
         }
     }
+    return true;
+}
+
+// FP32 (one thread): fold the CTA's key into the iteration's slot with a
+// 64-bit atomic max, arrive, wait, read the max.
+MP_DEV bool grid_exchange(const PlainArgs<float>& a, int cta, int G, int t, unsigned long long k,
+                          unsigned long long* out) {
+    PlainWorkspace* ws = a.ws;
+    atomicMax(&ws->keys[t % 3], k);
+    if (!(cta == a.skip_cta && t == 0)) red_release_add_u64(&ws->count, 1ull);
+    if (!grid_wait(ws, static_cast<unsigned long long>(t + 1) * G, a.watchdog_ns)) return false;
     *out = ld_relaxed_u64(&ws->keys[t % 3]);
     // slot (t+2)%3 was last read at iteration t-1, before every CTA arrived
     // at this barrier; it is next written at iteration t+2, after the next one.
@@ -106,12 +165,41 @@ MP_DEV bool grid_exchange(const PlainArgs& a, int cta, int G, int t, unsigned lo
     return true;
 }
 
+// FP64 (one warp): the 128-bit key has no atomic max, so each CTA writes its
+// key to its own slot of ring t&1, arrives, and after the barrier every lane
+// reads a share of the G slots; a warp max gives the grid's key.  Ring t&1
+// is rewritten at iteration t+2, after barrier t+1, which every CTA reaches
+// only after finishing its reads of iteration t.
+MP_DEV bool grid_exchange(const PlainArgs<double>& a, int cta, int G, int t, Key128 k, int lane, Key128* out) {
+    PlainWorkspace* ws = a.ws;
+    Key128* ring = a.slots + (t & 1) * G;
+    if (lane == 0) {
+        st_relaxed_u64(&ring[cta].hi, k.hi);
+        st_relaxed_u64(&ring[cta].lo, k.lo);
+        if (!(cta == a.skip_cta && t == 0)) red_release_add_u64(&ws->count, 1ull);
+    }
+    __syncwarp();
+    const bool ok = __all_sync(0xffffffffu, grid_wait(ws, static_cast<unsigned long long>(t + 1) * G,
+                                                      a.watchdog_ns));
+    if (!ok) return false;
+    Key128 best = {0ull, 0ull};
+    for (int i = lane; i < G; i += 32) {
+        Key128 v;
+        v.hi = ld_relaxed_u64(&ring[i].hi);
+        v.lo = ld_relaxed_u64(&ring[i].lo);
+        best = kmax(best, v);
+    }
+    *out = warp_max_key(best);
+    return true;
+}
+
 // ------------------------------------------------------------------ producer
-MP_DEV void plain_producer(const PlainArgs& a, PlainShared* sh, float* ring, int a0, int na) {
+template <typename T>
+MP_DEV void plain_producer(const PlainArgs<T>& a, PlainShared<T>* sh, T* ring, int a0, int na) {
     const int A = a.stage_atoms, D = a.stages, ldN = a.ldN;
     const int S = (na + A - 1) / A;
     if (S == 0) return;
-    const size_t stage_floats = static_cast<size_t>(A) * ldN;
+    const size_t stage_elems = static_cast<size_t>(A) * ldN;
     const uint64_t pol = policy_evict_first();
     volatile int* vdone = &sh->done;
     long long seq = 0;
@@ -139,20 +227,21 @@ MP_DEV void plain_producer(const PlainArgs& a, PlainShared* sh, float* ring, int
         const int j = static_cast<int>(seq % S);
         const int atom0 = a0 + j * A;
         const int nat = min(A, na - j * A);
-        const uint32_t bytes = static_cast<uint32_t>(nat) * ldN * 4u;
+        const uint32_t bytes = static_cast<uint32_t>(nat) * ldN * static_cast<uint32_t>(sizeof(T));
         mbar_arrive_expect_tx(&sh->full[slot], bytes);
         if (a.evict_first)
-            bulk_g2s_evict_first(ring + slot * stage_floats, a.psi + static_cast<size_t>(atom0) * ldN, bytes,
+            bulk_g2s_evict_first(ring + slot * stage_elems, a.psi + static_cast<size_t>(atom0) * ldN, bytes,
                                  &sh->full[slot], pol);
         else
-            bulk_g2s(ring + slot * stage_floats, a.psi + static_cast<size_t>(atom0) * ldN, bytes, &sh->full[slot]);
+            bulk_g2s(ring + slot * stage_elems, a.psi + static_cast<size_t>(atom0) * ldN, bytes, &sh->full[slot]);
         // L2 as a deeper window than the shared-memory ring: pull the stage
         // `prefetch` positions ahead into L2 now, so HBM keeps streaming
         // while the ring is full during the per-iteration exchange.
         if (a.prefetch > 0) {
             const int jp = static_cast<int>((seq + a.prefetch) % S);
             const int np = min(A, na - jp * A);
-            prefetch_l2(a.psi + static_cast<size_t>(a0 + jp * A) * ldN, static_cast<uint32_t>(np) * ldN * 4u);
+            prefetch_l2(a.psi + static_cast<size_t>(a0 + jp * A) * ldN,
+                        static_cast<uint32_t>(np) * ldN * static_cast<uint32_t>(sizeof(T)));
         }
         ++seq;
     }
@@ -166,14 +255,20 @@ MP_DEV void plain_producer(const PlainArgs& a, PlainShared* sh, float* ring, int
 }
 
 // ------------------------------------------------------------------ kernel
-template <int MODE>
-__global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const PlainArgs a) {
+// T = float: the FP32 decode; T = double: the same iteration in FP64 (the
+// paper's double-precision runs).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const PlainArgs<T> a) {
+    using Key = typename PlainTraits<T>::Key;
+    using V = typename PlainTraits<T>::V;
     constexpr bool STREAM = MODE == 3;
     constexpr bool CLUSTER = MODE == 1;
+    constexpr bool FP64 = sizeof(T) == 8;
+    constexpr int kV = 16 / sizeof(T);
     extern __shared__ __align__(128) unsigned char smem[];
-    float* r = reinterpret_cast<float*>(smem);
-    PlainShared* sh = reinterpret_cast<PlainShared*>(smem + a.off_sh);
-    float* data = reinterpret_cast<float*>(smem + a.off_data);
+    T* r = reinterpret_cast<T*>(smem);
+    PlainShared<T>* sh = reinterpret_cast<PlainShared<T>*>(smem + a.off_sh);
+    T* data = reinterpret_cast<T*>(smem + a.off_data);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ncw = STREAM ? static_cast<int>(blockDim.x >> 5) - 1 : static_cast<int>(blockDim.x >> 5);
@@ -186,9 +281,10 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
     const int base = a.M / G, rem = a.M % G;
     const int a0 = cta * base + min(cta, rem);
     const int na = base + (cta < rem ? 1 : 0);
+    const Key kzero = {};
 
     if (threadIdx.x == 0) {
-        sh->keys[0] = sh->keys[1] = 0ull;
+        sh->keys[0] = sh->keys[1] = kzero;
         sh->abort = 0;
         sh->done = 0;
         if (STREAM) {
@@ -207,26 +303,20 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
     }
 
     // ---- Eq. 8: r <- y (zero padded), x~ <- 0 (own slice), resident atoms
-    for (int i = ct; i < ldN; i += nct) r[i] = i < a.N ? a.y[i] : 0.f;
-    for (int i = ct; i < na; i += nct) a.x[a0 + i] = 0.f;
+    for (int i = ct; i < ldN; i += nct) r[i] = i < a.N ? a.y[i] : T(0);
+    for (int i = ct; i < na; i += nct) a.x[a0 + i] = T(0);
     if (!STREAM) {
         const float4* src = reinterpret_cast<const float4*>(a.psi + static_cast<size_t>(a0) * ldN);
         float4* dst = reinterpret_cast<float4*>(data);
-        const int n4 = na * (ldN / 4);
-        for (int i = ct; i < n4; i += nct) dst[i] = __ldg(src + i);
+        const int n16 = na * (ldN / kV);
+        for (int i = ct; i < n16; i += nct) dst[i] = __ldg(src + i);
     }
     named_bar_sync(1, nct);
 
-    float4* r4 = reinterpret_cast<float4*>(r);
-    const int n4r = ldN / 4;
+    V* rv = reinterpret_cast<V*>(r);
+    const int nvr = ldN / kV;
     double acc = 0.0;
-    for (int k = ct; k < n4r; k += nct) {
-        const float4 v = r4[k];
-        acc = fma(static_cast<double>(v.x), static_cast<double>(v.x), acc);
-        acc = fma(static_cast<double>(v.y), static_cast<double>(v.y), acc);
-        acc = fma(static_cast<double>(v.z), static_cast<double>(v.z), acc);
-        acc = fma(static_cast<double>(v.w), static_cast<double>(v.w), acc);
-    }
+    for (int k = ct; k < nvr; k += nct) acc = sq_acc(rv[k], acc);
     acc = warp_sum_f64(acc);
     if (lane == 0) sh->wsum[cw] = acc;
     named_bar_sync(1, nct);
@@ -240,13 +330,12 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
     double audit = 0.0;
     bool aborted = false;
     const int A = a.stage_atoms, D = a.stages;
-    while (finite0 && e > thr2 && t < a.T) {
+    while (finite0 && e > thr2 && t < a.T_max) {
         // ---- Eq. 9: correlations of this CTA's atoms, best packed key
-        unsigned long long best = 0ull;
+        Key best = kzero;
         if (!STREAM) {
             for (int j = 4 * cw; j < na; j += 4 * ncw)
-                best = scan_atoms(data + static_cast<size_t>(j) * ldN, r, ldN, min(4, na - j), a0 + j,
-                                  lane, best);
+                best = scan_atoms(data + static_cast<size_t>(j) * ldN, r, ldN, min(4, na - j), a0 + j, lane, best);
         } else {
             // slot s belongs to warp s % ncw, which consumes the slot's uses
             // in order (so it never waits two phases ahead on a barrier)
@@ -263,7 +352,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
                     }
                     break;
                 }
-                const float* st = data + static_cast<size_t>(slot) * A * ldN;
+                const T* st = data + static_cast<size_t>(slot) * A * ldN;
                 best = scan_atoms(st, r, ldN, min(A, na - j * A), a0 + j * A, lane, best);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh->empty[slot]);
@@ -272,15 +361,19 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
         // ---- CTA max, then grid max
         if (lane == 0) sh->wkey[cw] = best;
         named_bar_sync(1, nct);
-        if (ct == 0) {
-            unsigned long long k = 0ull;
-            for (int w = 0; w < ncw; ++w) k = umax64(k, sh->wkey[w]);
-            if (CLUSTER) {
+        if (CLUSTER) {
+            if (ct == 0) {
+                Key k = kzero;
+                for (int w = 0; w < ncw; ++w) k = kmax(k, sh->wkey[w]);
                 // own slot of a two-slot ring: peers read slot t&1 after this
                 // iteration's cluster barrier and before arriving at the next
                 // one; this CTA rewrites it only at iteration t+2
                 sh->keys[t & 1] = k;
-            } else {
+            }
+        } else if constexpr (!FP64) {
+            if (ct == 0) {
+                unsigned long long k = 0ull;
+                for (int w = 0; w < ncw; ++w) k = umax64(k, sh->wkey[w]);
                 unsigned long long g = 0ull;
                 // the grid's winner is one of the CTAs' local bests: start
                 // pulling this one into L2 for the residual update
@@ -288,15 +381,27 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
                 if (!grid_exchange(a, cta, G, t, k, &g)) *reinterpret_cast<volatile int*>(&sh->abort) = 1;
                 sh->key = g;
             }
+        } else {
+            if (cw == 0) {
+                const Key k = warp_max_key(lane < ncw ? sh->wkey[lane] : kzero);
+                if (lane == 0 && k.hi != 0ull)
+                    prefetch_l2(a.psi + static_cast<size_t>(key_index(k)) * ldN, ldN * 8u);
+                Key g = kzero;
+                const bool ok = grid_exchange(a, cta, G, t, k, lane, &g);
+                if (lane == 0) {
+                    if (!ok) *reinterpret_cast<volatile int*>(&sh->abort) = 1;
+                    sh->key = g;
+                }
+            }
         }
         if (CLUSTER) {
             cluster_sync_all();
             if (cw == 0) {
                 // lane k reads CTA k's key over DSMEM; the warp max is the
                 // cluster's key (the same value in every CTA)
-                unsigned long long v = 0ull;
-                if (lane < G) v = dsmem_ld_u64(mapa_shared(smem_u32(&sh->keys[t & 1]), lane));
-                v = warp_max_u64(v);
+                Key v = kzero;
+                if (lane < G) dsmem_ld(mapa_shared(smem_u32(&sh->keys[t & 1]), lane), &v);
+                v = warp_max_key(v);
                 if (lane == 0) sh->key = v;
             }
         }
@@ -305,14 +410,14 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
             aborted = true;
             break;
         }
-        const unsigned long long key = sh->key;
+        const Key key = sh->key;
         const int m = key_index(key);
-        const float c = key_coef(key);
+        const T c = key_coef(key);
 
         // ---- Eq. 11: r <- r - c psi_m, and e = sum r^2 in FP64.  In the
         // cluster shape psi_m is resident in its owner CTA's shared memory
         // and is read from there over DSMEM; otherwise from global memory.
-        const float4* pm = reinterpret_cast<const float4*>(a.psi + static_cast<size_t>(m) * ldN);
+        const V* pm = reinterpret_cast<const V*>(a.psi + static_cast<size_t>(m) * ldN);
         uint32_t pm_cluster = 0;
         if (CLUSTER) {
             // owner of atom m under the slice split above
@@ -322,18 +427,13 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
             pm_cluster = mapa_shared(smem_u32(data + static_cast<size_t>(m - own_a0) * ldN), static_cast<uint32_t>(own));
         }
         acc = 0.0;
-        for (int k = ct; k < n4r; k += nct) {
-            const float4 pv = CLUSTER ? dsmem_ld_f32x4(pm_cluster + 16u * k) : __ldg(pm + k);
-            float4 v = r4[k];
-            v.x = fmaf(-c, pv.x, v.x);
-            v.y = fmaf(-c, pv.y, v.y);
-            v.z = fmaf(-c, pv.z, v.z);
-            v.w = fmaf(-c, pv.w, v.w);
-            r4[k] = v;
-            acc = fma(static_cast<double>(v.x), static_cast<double>(v.x), acc);
-            acc = fma(static_cast<double>(v.y), static_cast<double>(v.y), acc);
-            acc = fma(static_cast<double>(v.z), static_cast<double>(v.z), acc);
-            acc = fma(static_cast<double>(v.w), static_cast<double>(v.w), acc);
+        for (int k = ct; k < nvr; k += nct) {
+            V pv;
+            if (CLUSTER) dsmem_ld(pm_cluster + 16u * k, &pv);
+            else pv = __ldg(pm + k);
+            const V v = sub_scaled(c, pv, rv[k]);
+            rv[k] = v;
+            acc = sq_acc(v, acc);
         }
         acc = warp_sum_f64(acc);
         if (lane == 0) sh->wsum[cw] = acc;
@@ -345,7 +445,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
         if (cta == 0 && ct == 0) {
             // fire-and-forget: same-address reductions from one thread apply
             // in program order, so x~_m accumulates exactly as x~_m += c would
-            red_add_f32(a.x + m, c);
+            red_add(a.x + m, c);
             if (t < a.tr_cap) {
                 if (a.tr_atoms) a.tr_atoms[t] = m;
                 if (a.tr_coefs) a.tr_coefs[t] = c;
@@ -372,28 +472,28 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
     }
     if (CLUSTER) cluster_sync_all();  // peers may still read this CTA's key slot
 }
-
 // ------------------------------------------------------------------ host side
 static int round_up_i(int v, int m) { return (v + m - 1) / m * m; }
 
-template <int MODE>
+template <typename T, int MODE>
 static cudaError_t prepare_kernel_attrs(int max_smem) {
     static int done_smem = -1;
     cudaError_t e = cudaSuccess;
     if (done_smem != max_smem) {
-        e = cudaFuncSetAttribute(mp_plain_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        e = cudaFuncSetAttribute(mp_plain_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (e == cudaSuccess && MODE == 1)
-            e = cudaFuncSetAttribute(mp_plain_kernel<MODE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            e = cudaFuncSetAttribute(mp_plain_kernel<T, MODE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e == cudaSuccess) done_smem = max_smem;
     }
     return e;
 }
 
+template <typename T>
 static int max_cluster_size(int smem, int threads, int max_smem) {
     static int cached[2] = {-1, -1};  // [smem key, result]
     if (cached[0] == smem) return cached[1];
     int best = 0;
-    if (prepare_kernel_attrs<1>(max_smem) == cudaSuccess) {
+    if (prepare_kernel_attrs<T, 1>(max_smem) == cudaSuccess) {
         for (int c : {16, 8}) {
             cudaLaunchConfig_t lc = {};
             lc.gridDim = dim3(c);
@@ -407,7 +507,7 @@ static int max_cluster_size(int smem, int threads, int max_smem) {
             lc.attrs = at;
             lc.numAttrs = 1;
             int n = 0;
-            if (cudaOccupancyMaxActiveClusters(&n, mp_plain_kernel<1>, &lc) == cudaSuccess && n > 0) {
+            if (cudaOccupancyMaxActiveClusters(&n, mp_plain_kernel<T, 1>, &lc) == cudaSuccess && n > 0) {
                 best = c;
                 break;
             }
@@ -419,11 +519,12 @@ static int max_cluster_size(int smem, int threads, int max_smem) {
     return best;
 }
 
-mp_status plain_configure(PlanImpl* p, PlainConfig* cfg) {
+template <typename T>
+static mp_status plain_configure_t(PlanImpl* p, PlainConfig* cfg) {
     *cfg = PlainConfig();
-    const long long atom_bytes = static_cast<long long>(p->ldN) * 4;
-    const int r_bytes = round_up_i(p->ldN * 4, 128);
-    const int sh_bytes = round_up_i(static_cast<int>(sizeof(PlainShared)), 128);
+    const long long atom_bytes = static_cast<long long>(p->ldN) * sizeof(T);
+    const int r_bytes = round_up_i(p->ldN * static_cast<int>(sizeof(T)), 128);
+    const int sh_bytes = round_up_i(static_cast<int>(sizeof(PlainShared<T>)), 128);
     cfg->off_sh = r_bytes;
     cfg->off_data = r_bytes + sh_bytes;
     const long long budget = static_cast<long long>(p->max_smem_optin) - cfg->off_data;
@@ -440,7 +541,7 @@ mp_status plain_configure(PlanImpl* p, PlainConfig* cfg) {
         const long long apc = (M + C - 1) / C;
         const long long smem = cfg->off_data + apc * atom_bytes;
         if (smem > p->max_smem_optin) return false;
-        const int cmax = max_cluster_size(static_cast<int>(smem), kResidentThreads, p->max_smem_optin);
+        const int cmax = max_cluster_size<T>(static_cast<int>(smem), kResidentThreads, p->max_smem_optin);
         if (cmax == 0) return false;
         if (C > cmax) {
             C = cmax;
@@ -479,7 +580,7 @@ mp_status plain_configure(PlanImpl* p, PlainConfig* cfg) {
         cfg->smem = static_cast<int>(cfg->off_data + static_cast<long long>((M + G - 1) / G) * atom_bytes);
         return MP_OK;
     }
-    // mode 3: choose compute warps W, atoms per stage A, ring depth D (a multiple of W)
+    // mode 3: atoms per stage A, ring depth D, consumer warps W
     const long long apc = (M + G - 1) / G;
     long long A = std::max<long long>(1, p->stage_bytes / atom_bytes);
     A = std::min(A, apc);
@@ -499,20 +600,25 @@ mp_status plain_configure(PlanImpl* p, PlainConfig* cfg) {
     return MP_OK;
 }
 
-mp_status plain_launch(PlanImpl* p, const float* y, float* x, const mp_stop* stop, const mp_trace* trace,
-                       PlainWorkspace* ws, cudaStream_t st) {
+mp_status plain_configure(PlanImpl* p, PlainConfig* cfg) { return plain_configure_t<float>(p, cfg); }
+mp_status plain_configure64(PlanImpl* p, PlainConfig* cfg) { return plain_configure_t<double>(p, cfg); }
+
+template <typename T>
+static mp_status plain_launch_t(PlanImpl* p, const T* psi, const T* y, T* x, const mp_stop* stop, int* tr_atoms,
+                                T* tr_coefs, double* tr_energy, T* tr_resid, int tr_cap, PlainWorkspace* ws,
+                                cudaStream_t st) {
     PlainConfig cfg;
-    mp_status s = plain_configure(p, &cfg);
+    mp_status s = plain_configure_t<T>(p, &cfg);
     if (s != MP_OK) return s;
-    PlainArgs a;
+    PlainArgs<T> a;
     std::memset(&a, 0, sizeof(a));
-    a.psi = p->psi32;
+    a.psi = psi;
     a.y = y;
     a.x = x;
     a.N = p->N;
     a.ldN = p->ldN;
     a.M = p->M;
-    a.T = stop->max_iters;
+    a.T_max = stop->max_iters;
     a.eps2 = stop->eps * stop->eps;
     a.stage_atoms = cfg.stage_atoms;
     a.stages = cfg.stages;
@@ -521,13 +627,12 @@ mp_status plain_launch(PlanImpl* p, const float* y, float* x, const mp_stop* sto
     a.off_sh = cfg.off_sh;
     a.off_data = cfg.off_data;
     a.ws = ws;
-    if (trace) {
-        a.tr_atoms = trace->atoms;
-        a.tr_coefs = trace->coefs;
-        a.tr_energy = trace->energies;
-        a.tr_resid = trace->residual;
-        a.tr_cap = std::max(0, trace->capacity);
-    }
+    a.slots = static_cast<Key128*>(p->slots64);
+    a.tr_atoms = tr_atoms;
+    a.tr_coefs = tr_coefs;
+    a.tr_energy = tr_energy;
+    a.tr_resid = tr_resid;
+    a.tr_cap = std::max(0, tr_cap);
     a.watchdog_ns = static_cast<unsigned long long>(p->watchdog_ns);
     a.skip_cta = cfg.mode == 1 ? -1 : p->skip_cta;
 
@@ -552,21 +657,37 @@ mp_status plain_launch(PlanImpl* p, const float* y, float* x, const mp_stop* sto
     cudaError_t e;
     switch (cfg.mode) {
         case 1:
-            MP_CUDA_TRY(prepare_kernel_attrs<1>(p->max_smem_optin));
-            e = cudaLaunchKernelEx(&lc, mp_plain_kernel<1>, a);
+            MP_CUDA_TRY((prepare_kernel_attrs<T, 1>(p->max_smem_optin)));
+            e = cudaLaunchKernelEx(&lc, mp_plain_kernel<T, 1>, a);
             break;
         case 2:
-            MP_CUDA_TRY(prepare_kernel_attrs<2>(p->max_smem_optin));
-            e = cudaLaunchKernelEx(&lc, mp_plain_kernel<2>, a);
+            MP_CUDA_TRY((prepare_kernel_attrs<T, 2>(p->max_smem_optin)));
+            e = cudaLaunchKernelEx(&lc, mp_plain_kernel<T, 2>, a);
             break;
         default:
-            MP_CUDA_TRY(prepare_kernel_attrs<3>(p->max_smem_optin));
-            e = cudaLaunchKernelEx(&lc, mp_plain_kernel<3>, a);
+            MP_CUDA_TRY((prepare_kernel_attrs<T, 3>(p->max_smem_optin)));
+            e = cudaLaunchKernelEx(&lc, mp_plain_kernel<T, 3>, a);
             break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "plain decode launch");
     p->launches++;
     return MP_OK;
+}
+
+mp_status plain_launch(PlanImpl* p, const float* y, float* x, const mp_stop* stop, const mp_trace* trace,
+                       PlainWorkspace* ws, cudaStream_t st) {
+    if (!trace) return plain_launch_t<float>(p, p->psi32, y, x, stop, nullptr, nullptr, nullptr, nullptr, 0, ws, st);
+    return plain_launch_t<float>(p, p->psi32, y, x, stop, trace->atoms, trace->coefs, trace->energies,
+                                 trace->residual, trace->capacity, ws, st);
+}
+
+mp_status plain_launch64(PlanImpl* p, const double* y, double* x, const mp_stop* stop, const mp_trace_f64* trace,
+                         PlainWorkspace* ws, cudaStream_t st) {
+    if (!p->psi64 || !p->slots64)
+        return fail(MP_ERR_UNSUPPORTED, "the plan holds no FP64 dictionary (prec_mask bit MP_PREC_FP64)");
+    if (!trace) return plain_launch_t<double>(p, p->psi64, y, x, stop, nullptr, nullptr, nullptr, nullptr, 0, ws, st);
+    return plain_launch_t<double>(p, p->psi64, y, x, stop, trace->atoms, trace->coefs, trace->energies,
+                                  trace->residual, trace->capacity, ws, st);
 }
 
 mp_status plain_result_to_host(const PlanImpl*, const PlainWorkspace* h, mp_result* out) {
@@ -607,6 +728,22 @@ mp_status mp_recover(mp_plan_t plan, const float* y, float* x, const mp_stop* st
     PlanImpl* p = &plan->impl;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     s = plain_launch(p, y, x, stop, trace, p->ws, st);
+    if (s != MP_OK) return s;
+    p->last_stream = st;
+    p->have_pending = true;
+    if (!host_out) return MP_OK;
+    return mp_plan_last_result(plan, host_out);
+}
+
+mp_status mp_recover_f64(mp_plan_t plan, const double* y, double* x, const mp_stop* stop,
+                         const mp_trace_f64* trace, mp_result* host_out, void* stream) {
+    clear_error();
+    if (!plan || !y || !x) return fail(MP_ERR_INVALID, "mp_recover_f64: NULL plan, y or x");
+    mp_status s = check_stop(stop);
+    if (s != MP_OK) return s;
+    PlanImpl* p = &plan->impl;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    s = plain_launch64(p, y, x, stop, trace, p->ws, st);
     if (s != MP_OK) return s;
     p->last_stream = st;
     p->have_pending = true;

@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -37,19 +38,23 @@ struct AtomStats {
     int nonfinite;      // any NaN / Inf entry
 };
 
-// One CTA per atom: read psi_m from the caller's layout, reduce its squared
-// norm in FP64, optionally scale it to unit norm, and write the padded FP32
-// row plus the requested low-precision rows.
+// One CTA per atom: read psi_m from the caller's layout (FP32 or FP64),
+// reduce its squared norm in FP64, optionally scale it to unit norm, and
+// write the padded FP32 row plus the requested FP64 and low-precision rows.
+// FP32 input: the FP64 row is the stored FP32 row widened (exact).  FP64
+// input: the FP64 row is the (scaled) input, the FP32 row its rounding.
+template <typename TIn>
 __global__ void __launch_bounds__(256) prep_atoms_kernel(
-    const float* __restrict__ src, int layout, int N, int M, int normalize, float* __restrict__ psi32,
-    int ldN, __nv_bfloat16* __restrict__ psi16, int ldK16, __nv_fp8_storage_t* __restrict__ psi8,
-    int ldK8, float* __restrict__ scale8, AtomStats* __restrict__ stats) {
+    const TIn* __restrict__ src, int layout, int N, int M, int normalize, float* __restrict__ psi32,
+    int ldN, double* __restrict__ psi64, __nv_bfloat16* __restrict__ psi16, int ldK16,
+    __nv_fp8_storage_t* __restrict__ psi8, int ldK8, float* __restrict__ scale8, AtomStats* __restrict__ stats) {
+    constexpr bool kIn64 = sizeof(TIn) == 8;
     const int m = blockIdx.x;
     const int tid = threadIdx.x;
     __shared__ double s_d[8];
     __shared__ float s_f[8];
     __shared__ int s_i[8];
-    auto at = [&](int n) -> float {
+    auto at = [&](int n) -> TIn {
         return layout == MP_LAYOUT_ATOM_MAJOR ? src[static_cast<size_t>(m) * N + n]
                                               : src[static_cast<size_t>(n) * M + m];
     };
@@ -57,8 +62,8 @@ __global__ void __launch_bounds__(256) prep_atoms_kernel(
     double acc = 0.0;
     int bad = 0;
     for (int n = tid; n < N; n += blockDim.x) {
-        const float v = at(n);
-        if (!isfinite(v)) bad = 1;
+        const TIn v = at(n);
+        if (!isfinite(static_cast<double>(v))) bad = 1;
         acc = fma(static_cast<double>(v), static_cast<double>(v), acc);
     }
     acc = warp_sum_f64(acc);
@@ -78,10 +83,21 @@ __global__ void __launch_bounds__(256) prep_atoms_kernel(
     // pass 2: stored FP32 row (zero padded) and its max |entry|
     float mx = 0.f;
     float* row = psi32 + static_cast<size_t>(m) * ldN;
+    double* row64 = psi64 ? psi64 + static_cast<size_t>(m) * ldN : nullptr;
     for (int n = tid; n < ldN; n += blockDim.x) {
         float v = 0.f;
-        if (n < N) v = normalize ? static_cast<float>(static_cast<double>(at(n)) * scale) : at(n);
+        double v64 = 0.0;
+        if (n < N) {
+            if (kIn64) {
+                v64 = normalize ? static_cast<double>(at(n)) * scale : static_cast<double>(at(n));
+                v = static_cast<float>(v64);
+            } else {
+                v = normalize ? static_cast<float>(static_cast<double>(at(n)) * scale) : static_cast<float>(at(n));
+                v64 = static_cast<double>(v);
+            }
+        }
         row[n] = v;
+        if (row64) row64[n] = v64;
         mx = fmaxf(mx, fabsf(v));
     }
 #pragma unroll
@@ -121,6 +137,8 @@ static void plan_free(PlanImpl* p) {
     cudaFree(p->psi16);
     cudaFree(p->psi8);
     cudaFree(p->scale8);
+    cudaFree(p->psi64);
+    cudaFree(p->slots64);
     cudaFree(p->ws);
     cudaFree(p->y_stage);
     cudaFree(p->x_stage);
@@ -154,7 +172,12 @@ const char* mp_status_string(mp_status s) {
 
 const char* mp_last_error_message(void) { return g_last_error.c_str(); }
 
-mp_status mp_plan_create(mp_plan_t* out, const mp_plan_desc* desc, const float* psi, void* stream) {
+}  // extern "C"
+
+namespace mpgb {
+
+template <typename TIn>
+static mp_status plan_create_t(mp_plan_t* out, const mp_plan_desc* desc, const TIn* psi, void* stream) {
     clear_error();
     if (!out) return fail(MP_ERR_INVALID, "mp_plan_create: out is NULL");
     *out = nullptr;
@@ -164,7 +187,9 @@ mp_status mp_plan_create(mp_plan_t* out, const mp_plan_desc* desc, const float* 
     if (desc->layout != MP_LAYOUT_ATOM_MAJOR && desc->layout != MP_LAYOUT_ROW_MAJOR)
         return fail(MP_ERR_INVALID, "mp_plan_create: unknown layout");
     if (desc->reserved != 0) return fail(MP_ERR_INVALID, "mp_plan_create: reserved must be 0");
-    if (desc->prec_mask & ~7u) return fail(MP_ERR_INVALID, "mp_plan_create: unknown precision bit");
+    if (desc->prec_mask & ~15u) return fail(MP_ERR_INVALID, "mp_plan_create: unknown precision bit");
+    if (sizeof(TIn) == 8 && !(desc->prec_mask & (1u << MP_PREC_FP64)))
+        return fail(MP_ERR_INVALID, "mp_plan_create_f64: prec_mask must include MP_PREC_FP64");
     if (static_cast<long long>(desc->N) * desc->M > (1LL << 40))
         return fail(MP_ERR_INVALID, "mp_plan_create: dictionary too large");
 
@@ -204,6 +229,13 @@ mp_status mp_plan_create(mp_plan_t* out, const mp_plan_desc* desc, const float* 
             return bail(cuda_fail(e, "cudaMalloc(scale8)"));
         p->device_bytes += b + p->M * sizeof(float);
     }
+    if (p->prec_mask & (1u << MP_PREC_FP64)) {
+        const size_t b = n32 * sizeof(double);
+        if ((e = cudaMalloc(&p->psi64, b)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(psi64)"));
+        const size_t sb = 2 * static_cast<size_t>(std::max(1, p->sm_count)) * 16;
+        if ((e = cudaMalloc(&p->slots64, sb)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(slots64)"));
+        p->device_bytes += b + sb;
+    }
     if ((e = cudaMalloc(&p->ws, sizeof(PlainWorkspace))) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMalloc(workspace)"));
     if ((e = cudaMallocHost(&p->ws_host, sizeof(PlainWorkspace))) != cudaSuccess)
@@ -212,8 +244,8 @@ mp_status mp_plan_create(mp_plan_t* out, const mp_plan_desc* desc, const float* 
     AtomStats* d_stats = nullptr;
     if ((e = cudaMallocAsync(&d_stats, p->M * sizeof(AtomStats), st)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMallocAsync(stats)"));
-    prep_atoms_kernel<<<p->M, 256, 0, st>>>(
-        psi, desc->layout, p->N, p->M, desc->normalize ? 1 : 0, p->psi32, p->ldN,
+    prep_atoms_kernel<TIn><<<p->M, 256, 0, st>>>(
+        psi, desc->layout, p->N, p->M, desc->normalize ? 1 : 0, p->psi32, p->ldN, p->psi64,
         static_cast<__nv_bfloat16*>(p->psi16), p->ldK16, static_cast<__nv_fp8_storage_t*>(p->psi8),
         p->ldK8, p->scale8, d_stats);
     p->launches++;
@@ -243,6 +275,18 @@ mp_status mp_plan_create(mp_plan_t* out, const mp_plan_desc* desc, const float* 
     plain_configure(p, &cfg);   // validates that a plain launch shape exists (or not)
     *out = plan;
     return MP_OK;
+}
+
+}  // namespace mpgb
+
+extern "C" {
+
+mp_status mp_plan_create(mp_plan_t* out, const mp_plan_desc* desc, const float* psi, void* stream) {
+    return plan_create_t<float>(out, desc, psi, stream);
+}
+
+mp_status mp_plan_create_f64(mp_plan_t* out, const mp_plan_desc* desc, const double* psi, void* stream) {
+    return plan_create_t<double>(out, desc, psi, stream);
 }
 
 mp_status mp_plan_destroy(mp_plan_t plan) {
@@ -320,6 +364,14 @@ mp_status mp_plan_query(mp_plan_t plan, int what, long long* value) {
         case MP_Q_KERNEL_LAUNCHES: *value = p->launches; return MP_OK;
         case MP_Q_BATCH_TILE_N: *value = p->batch ? p->batch->TN : 0; return MP_OK;
         case MP_Q_BATCH_CLUSTER: *value = p->batch ? p->batch->CL : 0; return MP_OK;
+        case MP_Q_PLAIN64_MODE:
+        case MP_Q_PLAIN64_STAGES: {
+            PlainConfig c64;
+            const bool ok = p->psi64 && plain_configure64(p, &c64) == MP_OK;
+            *value = !ok ? 0 : (what == MP_Q_PLAIN64_MODE ? c64.mode : c64.stages);
+            clear_error();
+            return MP_OK;
+        }
     }
     return fail(MP_ERR_INVALID, "unknown query " + std::to_string(what));
 }

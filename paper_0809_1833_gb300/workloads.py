@@ -74,11 +74,13 @@ def gaussian_dictionary(N: int, M: int, seed: int = 0) -> np.ndarray:
     return np.ascontiguousarray(P, dtype=np.float32)
 
 
-def bernoulli_dictionary(N: int, M: int, seed: int = 0) -> np.ndarray:
-    """Atom-major (M, N) float32 dictionary, entries +-1/sqrt(N) (Eq. 13)."""
+def bernoulli_dictionary(N: int, M: int, seed: int = 0, dtype=np.float32) -> np.ndarray:
+    """Atom-major (M, N) dictionary, entries +-1/sqrt(N) (Eq. 13), stored in
+    ``dtype`` (float32, or float64 for the double-precision runs; the signs
+    do not depend on it)."""
     g = _rng(seed, 0)
     s = np.where(g.random((M, N)) < 0.5, -1.0, 1.0)
-    return np.ascontiguousarray(s / math.sqrt(N), dtype=np.float32)
+    return np.ascontiguousarray(s / math.sqrt(N), dtype=dtype)
 
 
 def orthonormal_dictionary(N: int, seed: int = 0) -> np.ndarray:
@@ -112,12 +114,12 @@ def sparse_signal(M: int, K: int, g: np.random.Generator, values: str = "pm12"):
     return x, supp
 
 
-def encode(psi_atoms: np.ndarray, x: np.ndarray) -> np.ndarray:
-    """y = Psi x (Eq. 2) in FP64 from the stored atoms, rounded to FP32."""
+def encode(psi_atoms: np.ndarray, x: np.ndarray, dtype=np.float32) -> np.ndarray:
+    """y = Psi x (Eq. 2) in FP64 from the stored atoms, rounded to ``dtype``."""
     nz = np.nonzero(x)[0]
     P = psi_atoms[nz].astype(np.float64)
     y = x[nz] @ P if nz.size else np.zeros(psi_atoms.shape[1])
-    return y.astype(np.float32)
+    return y.astype(dtype)
 
 
 @dataclass
@@ -183,11 +185,16 @@ def make_workload(name: str, seed: int = 0, B: int | None = None) -> Problem:
     raise ValueError(f"{name} is not a single-dictionary workload")
 
 
-def paper_timing_problem(M: int, seed: int = 0) -> Problem:
+def paper_timing_problem(M: int, seed: int = 0, fp64: bool = False) -> Problem:
     """Sec. 4 timing sweep instance: N=floor(M/2), K=floor(0.07M), Bernoulli
-    dictionary, U[-1,1] values, T=N, eps=1e-7."""
+    dictionary, U[-1,1] values, T=N, eps=1e-7.  ``fp64``: dictionary and y
+    kept in FP64 (the double-precision run; same signs and signal)."""
     N, K = M // 2, int(0.07 * M)
-    return make_plain(N, M, K, seed, 1e-7, N, "uniform11", "bernoulli")
+    if not fp64:
+        return make_plain(N, M, K, seed, 1e-7, N, "uniform11", "bernoulli")
+    psi = bernoulli_dictionary(N, M, seed, np.float64)
+    x, supp = sparse_signal(M, K, _rng(seed, 1), "uniform11")
+    return Problem(psi, encode(psi, x, np.float64)[None, :], x[None, :], [supp], 1e-7, N)
 
 
 def poisson_arrivals(rate: float, duration: float, seed: int = 0) -> np.ndarray:

@@ -23,6 +23,10 @@ import numpy as np
 
 GAP_TIE = 1e-5
 U32 = 2.0 ** -24
+U64 = 2.0 ** -53
+# FP64 near-tie floor: far below any FP32 effect, above FP64 rounding of a
+# correlation of the sizes tested
+GAP_TIE64 = 1e-13
 
 
 def summation_depth(N):
@@ -31,6 +35,14 @@ def summation_depth(N):
     warp butterfly."""
     ld = (N + 31) // 32 * 32
     return (ld + 127) // 128 + 7
+
+
+def summation_depth64(N):
+    """Depth of the FP64 summation tree of one correlation (two FMA chains
+    per lane over 64-double segments, one combining add, the butterfly),
+    plus N for the oracle's own FP64 sum, whose order is not specified."""
+    ld = (N + 31) // 32 * 32
+    return (ld + 63) // 64 + 6 + N
 
 
 def torch_mod():
@@ -46,17 +58,21 @@ def cur_stream():
 class GpuPlan:
     """A plan over a numpy atom-major dictionary, created through the C ABI."""
 
-    def __init__(self, psi, prec_mask=0, mode=0, layout_row_major=False, normalize=False):
+    def __init__(self, psi, prec_mask=0, mode=0, layout_row_major=False, normalize=False, master64=False):
         from paper_0809_1833_gb300 import binding as B
         torch = torch_mod()
         self.B = B
         M, N = psi.shape
         self.N, self.M = N, M
-        src = np.ascontiguousarray(psi.T if layout_row_major else psi, dtype=np.float32)
+        lay = B.MP_LAYOUT_ROW_MAJOR if layout_row_major else B.MP_LAYOUT_ATOM_MAJOR
+        src = np.ascontiguousarray(psi.T if layout_row_major else psi,
+                                   dtype=np.float64 if master64 else np.float32)
         d = torch.from_numpy(src).cuda()
-        self.plan = B.mp_plan_create(N, M, d.data_ptr(),
-                                     B.MP_LAYOUT_ROW_MAJOR if layout_row_major else B.MP_LAYOUT_ATOM_MAJOR,
-                                     prec_mask, normalize, cur_stream())
+        if master64:
+            self.plan = B.mp_plan_create_f64(N, M, d.data_ptr(), lay, prec_mask | (1 << B.MP_PREC_FP64),
+                                             normalize, cur_stream())
+        else:
+            self.plan = B.mp_plan_create(N, M, d.data_ptr(), lay, prec_mask, normalize, cur_stream())
         del d
         if mode:
             B.mp_plan_set_option(self.plan, B.MP_OPT_PLAIN_MODE, mode)
@@ -87,6 +103,26 @@ class GpuPlan:
         return dict(status=s, result=res, x=x.cpu().numpy(), atoms=atoms.cpu().numpy()[:n],
                     coefs=coefs.cpu().numpy()[:n], energies=en.cpu().numpy()[:n], r=r.cpu().numpy())
 
+    def decode64(self, y, eps, T, trace_cap=None, raise_on_error=True):
+        """FP64 decode (mp_recover_f64) of y given in FP64; same dict as decode."""
+        torch = torch_mod()
+        B = self.B
+        yd = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float64)).cuda()
+        x = torch.full((self.M,), float("nan"), dtype=torch.float64, device="cuda")
+        cap = min(int(T), 200000) if trace_cap is None else int(trace_cap)
+        cap = max(cap, 1)
+        atoms = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+        coefs = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        en = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        r = torch.full((self.N,), float("nan"), dtype=torch.float64, device="cuda")
+        tr = B.make_trace_f64(atoms.data_ptr(), coefs.data_ptr(), en.data_ptr(), cap, r.data_ptr())
+        s, res = B.mp_recover_f64(self.plan, yd.data_ptr(), x.data_ptr(), eps, T, tr, True, cur_stream(),
+                                  raise_on_error=raise_on_error)
+        torch.cuda.synchronize()
+        n = min(res.iters, cap)
+        return dict(status=s, result=res, x=x.cpu().numpy(), atoms=atoms.cpu().numpy()[:n],
+                    coefs=coefs.cpu().numpy()[:n], energies=en.cpu().numpy()[:n], r=r.cpu().numpy())
+
     def close(self):
         if self.plan:
             self.B.mp_plan_destroy(self.plan)
@@ -104,10 +140,12 @@ def first_near_tie(gaps):
     return int(idx[0]) if idx.size else None
 
 
-def compare_to_oracle(psi, y, eps, T, gpu, ora=None, x_tol=1e-4, check_follow=True):
+def compare_to_oracle(psi, y, eps, T, gpu, ora=None, x_tol=1e-4, check_follow=True, fp64=False):
     """Apply rules (i)-(iii); returns a dict of diagnostics, asserts on failure.
     ``check_follow=False`` skips the FP64 replay when the whole sequence and
-    the iteration count already match the oracle literally."""
+    the iteration count already match the oracle literally.  ``fp64``: the
+    GPU path computed in FP64, so gamma_d = d 2^-53 (d from
+    summation_depth64) and the near-tie floor is GAP_TIE64."""
     from oracle import mp_oracle as orc
     if ora is None:
         ora = orc.mp(psi, y, eps, T)
@@ -124,10 +162,11 @@ def compare_to_oracle(psi, y, eps, T, gpu, ora=None, x_tol=1e-4, check_follow=Tr
         f = orc.follow(psi, y, ga)
         Delta = float(np.linalg.norm(gpu["r"].astype(np.float64) - f["r"]))
         out["drift"] = Delta
-    gamma = summation_depth(N) * U32
+    gamma = summation_depth64(N) * U64 if fp64 else summation_depth(N) * U32
+    floor = GAP_TIE64 if fp64 else GAP_TIE
     if len(oa):
         rk = np.sqrt(np.concatenate([[ora["e0"]], ora["energies"][:-1]]))
-        tol = np.maximum(GAP_TIE, (2 * Delta + 2 * gamma * rk) / np.maximum(np.abs(ora["coefs"]), 1e-300))
+        tol = np.maximum(floor, (2 * Delta + 2 * gamma * rk) / np.maximum(np.abs(ora["coefs"]), 1e-300))
         ties = np.nonzero(ora["gaps"] <= tol)[0]
         tie = int(ties[0]) if ties.size else None
     else:
@@ -149,7 +188,7 @@ def compare_to_oracle(psi, y, eps, T, gpu, ora=None, x_tol=1e-4, check_follow=Tr
     assert xerr <= x_tol, f"x relative L2 error {xerr:.3e} > {x_tol}"
     out["x_rel_err"] = xerr
     if f is not None:
-        tolf = np.maximum(GAP_TIE, (2 * Delta + 2 * gamma * f["rnorm"]) / np.maximum(f["cmax"], 1e-300))
+        tolf = np.maximum(floor, (2 * Delta + 2 * gamma * f["rnorm"]) / np.maximum(f["cmax"], 1e-300))
         bad = np.nonzero(f["ratio"] < 1 - tolf)[0]
         assert bad.size == 0, f"follow ratio below bound at steps {bad[:5]}: {f['ratio'][bad[:5]]}"
         out["min_ratio"] = float(f["ratio"].min())
