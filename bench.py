@@ -297,12 +297,18 @@ def run_ours(args):
                      "kernel": "mp_plain_kernel<3> (grid streaming)",
                      "algorithmic_bytes_per_launch": sum(alg_bytes) / len(alg_bytes)},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        "paper_context": {"speedup": "GPU vs CPU up to 31x in single and 21x in double precision at M=15000",
+                          "hardware": "GeForce GTX 280 (GT200, 240 stream processors, 1 GB) with CUBLAS "
+                                      "(CUDA 2.0) vs AMD Phenom 9950 (2.6 GHz) with CBLAS (GSL 1.11)",
+                          "workload": "Sec. 4: Bernoulli Psi, N = M/2, K = 0.07M, eps = 1e-7, T = N",
+                          "use": "context only (other workload and hardware); see bench.py --paper-timing"},
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(psi_np, Y_np[0], w["eps"], w["T"], iters[0], args.cpu_budget)
     B.mp_plan_destroy(plan)
     if rank == 0 and not args.no_batched:
         line["plain_small"] = plain_small_measure()
+        line["variants"] = variants_measure()
         # batched low-precision form vs the plain FP32 kernel on the same signals
         line["batched"] = [batched_measure("bf16"), batched_measure("fp8", n_plain=4)]
     if rank == 0 and args.served_duration > 0:
@@ -347,6 +353,58 @@ def plain_small_measure(reps=20):
         out["shapes"][label] = {"ctas": B.mp_plan_query(plan, B.MP_Q_PLAIN_CTAS), "iterations": r.iters,
                                 "us_per_iteration": 1e6 * t / r.iters, "recoveries_per_s": 1.0 / t,
                                 "dictionary_GBps_from_smem": 4.0 * prob.N * prob.M * r.iters / t / 1e9}
+    B.mp_plan_destroy(plan)
+    return out
+
+
+def variants_measure(n_sig=4, gram_period=32):
+    """The benchmark's workload (N=4096, M=16384, K=256) through the two
+    decodes beside direct MP: MP with Gram-updated correlations (period R;
+    not in the paper, same MP iteration with c_m -= c G[m*][m] between direct
+    recomputations) and OMP (the method Sec. 5 names next).  CUDA events per
+    decode; the Gram matrix build is timed once, apart."""
+    import torch
+    from paper_0809_1833_gb300 import binding as B
+    w, psi_np, Y_np, sigs = make_problem(n_sig)
+    st = torch.cuda.current_stream()
+    s = st.cuda_stream
+    d = torch.from_numpy(psi_np).cuda()
+    plan = B.mp_plan_create(w["N"], w["M"], d.data_ptr(), stream=s)
+    del d
+    Y = torch.from_numpy(Y_np).cuda()
+    x = torch.empty(w["M"], dtype=torch.float32, device="cuda")
+    out = {"workload": WORKLOAD, "signals": n_sig}
+
+    def timed(fn):
+        recs = []
+        for i in range(n_sig):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn(plan, Y[i].data_ptr(), x.data_ptr(), w["eps"], w["T"], None, False, s)
+            b.record(st)
+            b.synchronize()
+            _, r = B.mp_plan_last_result(plan)
+            xh = x.cpu().numpy().astype(np.float64)
+            xt = sigs[i].x_true[0]
+            recs.append((a.elapsed_time(b), r.iters, float(np.sum((xh - xt) ** 2) / np.sum(xt ** 2)) * 100))
+        ms = sum(r[0] for r in recs)
+        it = sum(r[1] for r in recs)
+        return {"recoveries_per_s": 1e3 * n_sig / ms, "ms_per_decode": ms / n_sig, "iterations_per_decode": it / n_sig,
+                "us_per_iteration": 1e3 * ms / it, "E_pct_max": max(r[2] for r in recs)}
+
+    B.mp_recover(plan, Y[0].data_ptr(), x.data_ptr(), w["eps"], 2, None, True, s)        # warm-up
+    out["direct_mp"] = timed(B.mp_recover)
+    B.mp_plan_set_option(plan, B.MP_OPT_PLAIN_GRAM, gram_period)
+    t0 = time.perf_counter()
+    B.mp_recover(plan, Y[0].data_ptr(), x.data_ptr(), w["eps"], 0, None, True, s)        # builds G
+    g_s = time.perf_counter() - t0
+    out["gram_mp"] = timed(B.mp_recover)
+    out["gram_mp"].update(period=gram_period, gram_build_s=g_s,
+                          gram_bytes=B.mp_plan_query(plan, B.MP_Q_GRAM_BYTES),
+                          gram_build_tflops=2.0 * w["M"] * w["M"] * w["N"] / g_s / 1e12)
+    B.mp_plan_set_option(plan, B.MP_OPT_PLAIN_GRAM, 0)
+    B.mp_recover_omp(plan, Y[0].data_ptr(), x.data_ptr(), w["eps"], 2, None, True, s)    # scratch
+    out["omp"] = timed(B.mp_recover_omp)
     B.mp_plan_destroy(plan)
     return out
 
@@ -592,6 +650,51 @@ def paper_timing_sweep(sizes, reps=3, cpu_budget_s=4.0):
         print(json.dumps({"paper_timing": row}), flush=True)
 
 
+def phase_diagram(trials=100, prec_name="bf16"):
+    """Sec. 3's reconstruction-error diagram E(sigma, rho) (Eq. 14): M = 1000,
+    sigma = K/M and rho = N/M on a 0.05 grid, ``trials`` signals per cell,
+    eps = 1e-7, T = N.  One batched decode per rho (its 20 x trials signals
+    share that rho's Bernoulli dictionary).  Prints one JSON line: the mean
+    E per cell (rows rho, columns sigma), the fraction of signals with
+    E < 1 %, and the decode time per rho."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0809_1833_gb300 import binding as B
+    from paper_0809_1833_gb300 import workloads as W
+    P = {"bf16": B.MP_PREC_BF16, "fp8": B.MP_PREC_FP8E4M3}[prec_name]
+    st = torch.cuda.current_stream()
+    grid = list(W.PHASE_GRID)
+    E_rows, ok_rows, secs, iters = [], [], [], []
+    for rho in grid:
+        prob = W.phase_diagram_batch(rho, grid, trials)
+        psi = torch.from_numpy(prob.psi).cuda()
+        plan = B.mp_plan_create(prob.N, prob.M, psi.data_ptr(), prec_mask=1 << P, stream=st.cuda_stream)
+        del psi
+        Y = torch.from_numpy(prob.y).cuda()
+        X = torch.empty((prob.B, prob.M), dtype=torch.float32, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s, res = B.mp_recover_batched(plan, P, Y.data_ptr(), X.data_ptr(), prob.B, (prob.eps, prob.T), None,
+                                      st.cuda_stream)
+        e1.record(st)
+        e1.synchronize()
+        B.check(s, "mp_recover_batched")
+        secs.append(e0.elapsed_time(e1) / 1e3)
+        iters.append(int(sum(r.iters for r in res)))
+        xt = prob.x_true
+        E = 100.0 * np.sum((X.cpu().numpy().astype(np.float64) - xt) ** 2, axis=1) / np.sum(xt ** 2, axis=1)
+        E = E.reshape(len(grid), trials)
+        E_rows.append([float(v) for v in E.mean(axis=1)])
+        ok_rows.append([float(v) for v in (E < 1.0).mean(axis=1)])
+        B.mp_plan_destroy(plan)
+    print(json.dumps({"phase_diagram": {"M": W.PHASE_M, "trials": trials, "precision": prec_name,
+                                        "eps": 1e-7, "T": "N", "sigma": grid, "rho": grid,
+                                        "E_pct_mean": E_rows, "frac_E_below_1pct": ok_rows,
+                                        "decode_s_per_rho": secs, "signal_iterations_per_rho": iters,
+                                        "total_decode_s": sum(secs)}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -612,7 +715,13 @@ def main():
     ap.add_argument("--paper-timing", nargs="*", type=int, default=None,
                     help="run only Sec. 4's CPU-vs-GPU size sweep (FP32 and FP64) at these M "
                          f"(default {PAPER_TIMING_SIZES})")
+    ap.add_argument("--phase-diagram", choices=["bf16", "fp8"], default=None,
+                    help="run only Sec. 3's E(sigma, rho) diagram with the batched decode in this precision")
+    ap.add_argument("--trials", type=int, default=100, help="signals per phase-diagram cell")
     args = ap.parse_args()
+    if args.phase_diagram:
+        phase_diagram(args.trials, args.phase_diagram)
+        return
     if args.paper_timing is not None:
         paper_timing_sweep(args.paper_timing or PAPER_TIMING_SIZES)
         return

@@ -79,7 +79,9 @@ typedef enum {
 typedef enum {
     MP_STOP_CONVERGED = 0,     /* ||r|| <= eps ||y||                          */
     MP_STOP_MAX_ITERS = 1,     /* t reached T                                 */
-    MP_STOP_ZERO_Y = 2         /* y == 0                                      */
+    MP_STOP_ZERO_Y = 2,        /* y == 0                                      */
+    MP_STOP_RANK = 3           /* OMP: the selected atom lies in the span of  */
+                               /* the atoms already selected                  */
 } mp_stop_reason;
 
 typedef struct mp_plan_s* mp_plan_t;
@@ -156,13 +158,23 @@ typedef enum {
                                /* (whole atoms, at least one; default 32768)         */
     MP_OPT_PLAIN_EVICT_FIRST = 9, /* grid streaming: 1 = evict-first L2 hint on the  */
                                /* streamed atoms (default), 0 = no hint              */
-    MP_OPT_BATCH_AUTOTUNE = 10 /* batched: 1 = time the GEMM tile shapes on the first */
+    MP_OPT_BATCH_AUTOTUNE = 10,/* batched: 1 = time the GEMM tile shapes on the first */
                                /* batch of each size bucket (default), 0 = heuristic */
+    MP_OPT_PLAIN_GRAM = 11     /* FP32 decode with Gram-updated correlations, period */
+                               /* R >= 1 (0 = off, the default).  Not in the paper:   */
+                               /* from Eqs. 9 and 11, <r - c psi_k, psi_m> =          */
+                               /* c_m - c G[k][m] with G = Psi^T Psi, so step t reads */
+                               /* one row of G (M floats) instead of Psi (N M), and   */
+                               /* every R-th step recomputes c = Psi^T r directly to  */
+                               /* bound the drift of the recurrence.  The plan builds */
+                               /* G (M x M FP32, 4 M^2 bytes) on the first such       */
+                               /* decode.  R = 1 gives the direct decode's bits.      */
 } mp_option;
 
 /* Read-only plan properties for mp_plan_query. */
 typedef enum {
-    MP_Q_PLAIN_MODE = 1,       /* mode the next mp_recover will use (1, 2 or 3)      */
+    MP_Q_PLAIN_MODE = 1,       /* mode the next mp_recover will use (1, 2 or 3; 4 =  */
+                               /* grid with Gram-updated correlations)               */
     MP_Q_PLAIN_CTAS = 2,       /* CTAs it will launch                                */
     MP_Q_PLAIN_THREADS = 3,    /* threads per CTA                                    */
     MP_Q_PLAIN_SMEM = 4,       /* dynamic shared memory per CTA, bytes               */
@@ -174,7 +186,8 @@ typedef enum {
     MP_Q_BATCH_TILE_N = 10,    /* atoms per GEMM tile of the current batch state     */
     MP_Q_BATCH_CLUSTER = 11,   /* GEMM cluster size of the current batch state       */
     MP_Q_PLAIN64_MODE = 12,    /* mode the next mp_recover_f64 will use (0: none)    */
-    MP_Q_PLAIN64_STAGES = 13   /* its streaming ring depth                           */
+    MP_Q_PLAIN64_STAGES = 13,  /* its streaming ring depth                           */
+    MP_Q_GRAM_BYTES = 14       /* device bytes of the Gram matrix (0 until built)     */
 } mp_query;
 
 /* ------------------------------------------------------------------ */
@@ -250,6 +263,26 @@ MPGB_API mp_status mp_plan_query(mp_plan_t plan, int what, long long* value);
  * MP_ERR_UNSUPPORTED (N too large for the on-chip residual), MP_ERR_CUDA. */
 MPGB_API mp_status mp_recover(mp_plan_t plan, const float* y, float* x, const mp_stop* stop,
                      const mp_trace* trace, mp_result* host_out, void* stream);
+
+/* Orthogonal Matching Pursuit, the method Sec. 5 names as the next one to
+ * port: MP's selection (Eq. 9, ties to the smallest index), then x~ on the
+ * selected set S is the least-squares fit argmin ||y - Psi_S z|| and
+ * r = y - Psi_S x~_S (replacing Eqs. 10-11).  One persistent FP32 launch on
+ * the grid shapes (modes 5 and 6 of mp_plan_query's numbering): each step
+ * streams the dictionary for the correlations, orthonormalises the new atom
+ * against the selected ones (classical Gram-Schmidt applied twice, FP32,
+ * norms in FP64), and updates r by its projection on the new direction;
+ * after the loop x~_S solves R x = Q^T y by back substitution on the device.
+ * Stops as mp_recover, plus MP_STOP_RANK when the new atom's component
+ * orthogonal to the selected span is below 1e-4 (or N atoms are selected).
+ *  y, x, stop, trace, host_out, stream : as mp_recover (trace coefs record
+ *  <r, psi_m> at selection; x~ is written after the last step).
+ * Scratch of about 4 (k N + k^2/2) bytes, k = min(T, N), is allocated on
+ * first use and kept by the plan.  Errors: as mp_recover, plus MP_ERR_NOMEM
+ * for the scratch and MP_ERR_UNSUPPORTED when MP_OPT_PLAIN_MODE forces the
+ * one-cluster shape. */
+MPGB_API mp_status mp_recover_omp(mp_plan_t plan, const float* y, float* x, const mp_stop* stop,
+                         const mp_trace* trace, mp_result* host_out, void* stream);
 
 /* Synchronise the stream of the plan's last mp_recover and return its
  * result (and its device-side status as the return value). */

@@ -28,7 +28,7 @@ MP_ERR_NOT_FOUND = -8
 
 MP_PREC_FP32, MP_PREC_BF16, MP_PREC_FP8E4M3, MP_PREC_FP64 = 0, 1, 2, 3
 MP_LAYOUT_ATOM_MAJOR, MP_LAYOUT_ROW_MAJOR = 0, 1
-MP_STOP_CONVERGED, MP_STOP_MAX_ITERS, MP_STOP_ZERO_Y = 0, 1, 2
+MP_STOP_CONVERGED, MP_STOP_MAX_ITERS, MP_STOP_ZERO_Y, MP_STOP_RANK = 0, 1, 2, 3
 
 MP_OPT_PLAIN_MODE = 1
 MP_OPT_WATCHDOG_NS = 2
@@ -40,6 +40,7 @@ MP_OPT_BATCH_CLUSTER = 7
 MP_OPT_PLAIN_STAGE_BYTES = 8
 MP_OPT_PLAIN_EVICT_FIRST = 9
 MP_OPT_BATCH_AUTOTUNE = 10
+MP_OPT_PLAIN_GRAM = 11
 MP_Q_BATCH_TILE_N = 10
 MP_Q_BATCH_CLUSTER = 11
 
@@ -54,6 +55,7 @@ MP_Q_DEVICE_BYTES = 8
 MP_Q_KERNEL_LAUNCHES = 9
 MP_Q_PLAIN64_MODE = 12
 MP_Q_PLAIN64_STAGES = 13
+MP_Q_GRAM_BYTES = 14
 
 
 class mp_plan_desc(ctypes.Structure):
@@ -113,6 +115,8 @@ SIGNATURES = {
     "mp_plan_query": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong)]),
     "mp_recover": (_I, [_P, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_trace),
                         ctypes.POINTER(mp_result), _P]),
+    "mp_recover_omp": (_I, [_P, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_trace),
+                            ctypes.POINTER(mp_result), _P]),
     "mp_plan_create_f64": (_I, [ctypes.POINTER(_P), ctypes.POINTER(mp_plan_desc), _P, _P]),
     "mp_recover_f64": (_I, [_P, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_trace_f64),
                             ctypes.POINTER(mp_result), _P]),
@@ -223,6 +227,19 @@ def mp_recover(plan, y_ptr, x_ptr, eps, max_iters, trace=None, sync=True, stream
                          ctypes.byref(res) if sync else None, _stream(stream))
     if raise_on_error:
         check(s, "mp_recover")
+    return s, (res if sync else None)
+
+
+def mp_recover_omp(plan, y_ptr, x_ptr, eps, max_iters, trace=None, sync=True, stream=None,
+                   raise_on_error=True):
+    """OMP decode of one signal (device pointers); returns as mp_recover."""
+    st = mp_stop(float(eps), int(max_iters), 0)
+    res = mp_result()
+    s = lib().mp_recover_omp(plan, ctypes.c_void_p(int(y_ptr)), ctypes.c_void_p(int(x_ptr)), ctypes.byref(st),
+                             ctypes.byref(trace) if trace is not None else None,
+                             ctypes.byref(res) if sync else None, _stream(stream))
+    if raise_on_error:
+        check(s, "mp_recover_omp")
     return s, (res if sync else None)
 
 

@@ -45,7 +45,7 @@ struct PlainWorkspace {
 
 // Launch shape of the plain kernel, derived from (N, M) and the device.
 struct PlainConfig {
-    int mode = 0;          // 1 cluster-resident, 2 grid-resident, 3 grid-stream
+    int mode = 0;          // 1 cluster-resident, 2 grid-resident, 3 grid-stream, 4 Gram
     int ctas = 0;          // grid size (= cluster size in mode 1)
     int threads = 0;
     int smem = 0;          // dynamic shared memory bytes
@@ -54,6 +54,38 @@ struct PlainConfig {
     int off_data = 0;      // byte offsets inside dynamic smem
     int off_sh = 0;
 };
+
+// OMP decode scratch (mp_plain.cu): basis, packed R, alpha = Q^T y,
+// selected atoms, Gram-Schmidt vectors, per-CTA norm partials, solution.
+struct OmpWorkspace {
+    float* Q = nullptr;
+    float* Rc = nullptr;
+    float* alpha = nullptr;
+    int* sel = nullptr;
+    float* h = nullptr;
+    float* h2 = nullptr;
+    float* w = nullptr;
+    float* w2 = nullptr;
+    double* nrm = nullptr;
+    float* xs = nullptr;
+    int kmax = 0;
+    int G = 0;
+    size_t bytes = 0;
+};
+
+inline void omp_free(OmpWorkspace* o) {
+    cudaFree(o->Q);
+    cudaFree(o->Rc);
+    cudaFree(o->alpha);
+    cudaFree(o->sel);
+    cudaFree(o->h);
+    cudaFree(o->h2);
+    cudaFree(o->w);
+    cudaFree(o->w2);
+    cudaFree(o->nrm);
+    cudaFree(o->xs);
+    *o = OmpWorkspace();
+}
 
 struct BatchEngine;        // batched decode state (mp_batched.cu)
 
@@ -83,6 +115,8 @@ struct PlanImpl {
     float* scale8 = nullptr;        // per-atom FP8 scale
     double* psi64 = nullptr;        // FP64 atom-major copy, stride ldN
     void* slots64 = nullptr;        // FP64 grid exchange slots (2 x sm_count keys)
+    float* gram = nullptr;          // Gram matrix Psi^T Psi (M x ldG), built on demand
+    int ldG = 0;
 
     PlainWorkspace* ws = nullptr;   // device
     PlainWorkspace* ws_host = nullptr;  // pinned mirror
@@ -108,9 +142,11 @@ struct PlanImpl {
     int prefetch_stages = 0;        // plain streaming: L2 prefetch distance (measured slower; off)
     int stage_bytes = 32768;        // plain streaming: target bytes per ring stage
     int evict_first = 1;            // plain streaming: L2 evict-first hint on the stream
+    int gram_period = 0;            // > 0: Gram-updated correlations, direct every R steps
 
     long long launches = 0;
     BatchEngine* batch = nullptr;
+    OmpWorkspace omp;
 };
 
 // Plain-kernel helpers (mp_plain.cu).
@@ -118,6 +154,8 @@ mp_status plain_configure(PlanImpl* p, PlainConfig* cfg);
 mp_status plain_launch(PlanImpl* p, const float* y, float* x, const mp_stop* stop,
                        const mp_trace* trace, PlainWorkspace* ws, cudaStream_t st);
 mp_status plain_result_to_host(const PlanImpl* p, const PlainWorkspace* h, mp_result* out);
+// Gram matrix of the plan's FP32 atoms (mp_gram.cu); builds it once.
+mp_status gram_prepare(PlanImpl* p, cudaStream_t st);
 // The FP64 decode (the same kernel instantiated for double).
 mp_status plain_configure64(PlanImpl* p, PlainConfig* cfg);
 mp_status plain_launch64(PlanImpl* p, const double* y, double* x, const mp_stop* stop,

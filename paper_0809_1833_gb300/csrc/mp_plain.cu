@@ -77,6 +77,24 @@ struct PlainArgs {
     int off_sh, off_data;
     PlainWorkspace* ws;
     Key128* slots;         // FP64 grid exchange: two rings of one key per CTA
+    const T* G;            // mode 4: Gram matrix, row stride ldG
+    int ldG;
+    int gram_period;       // mode 4: direct correlations every gram_period steps
+    // modes 5, 6 (OMP): orthonormal basis Q of the selected atoms (kmax rows
+    // of ldN), R = Q^T Psi_S by packed columns (column k at k(k+1)/2),
+    // alpha = Q^T y, the selected atoms, Gram-Schmidt scratch, per-CTA norm
+    // partials and the solution of R x_S = alpha
+    T* Q;
+    T* Rc;
+    T* alpha;
+    int* sel;
+    T* h;
+    T* h2;
+    T* w;
+    T* w2;
+    double* nrm;
+    T* xs;
+    int kmax;
     int* tr_atoms;
     T* tr_coefs;
     double* tr_energy;
@@ -112,6 +130,8 @@ MP_DEV double2 sub_scaled(double c, const double2 p, double2 v) {
     v.y = fma(-c, p.y, v.y);
     return v;
 }
+MP_DEV float4 scale_vec(const float4 v, float s) { return make_float4(v.x * s, v.y * s, v.z * s, v.w * s); }
+MP_DEV double2 scale_vec(const double2 v, double s) { return make_double2(v.x * s, v.y * s); }
 MP_DEV void dsmem_ld(uint32_t addr, float4* v) { *v = dsmem_ld_f32x4(addr); }
 MP_DEV void dsmem_ld(uint32_t addr, double2* v) { *v = dsmem_ld_f64x2(addr); }
 MP_DEV void dsmem_ld(uint32_t addr, unsigned long long* k) { *k = dsmem_ld_u64(addr); }
@@ -151,13 +171,13 @@ MP_DEV bool grid_wait(PlainWorkspace* ws, unsigned long long target, unsigned lo
 }
 
 // FP32 (one thread): fold the CTA's key into the iteration's slot with a
-// 64-bit atomic max, arrive, wait, read the max.
-MP_DEV bool grid_exchange(const PlainArgs<float>& a, int cta, int G, int t, unsigned long long k,
+// 64-bit atomic max, arrive at grid barrier `bar`, wait, read the max.
+MP_DEV bool grid_exchange(const PlainArgs<float>& a, int cta, int G, int t, int bar, unsigned long long k,
                           unsigned long long* out) {
     PlainWorkspace* ws = a.ws;
     atomicMax(&ws->keys[t % 3], k);
     if (!(cta == a.skip_cta && t == 0)) red_release_add_u64(&ws->count, 1ull);
-    if (!grid_wait(ws, static_cast<unsigned long long>(t + 1) * G, a.watchdog_ns)) return false;
+    if (!grid_wait(ws, static_cast<unsigned long long>(bar + 1) * G, a.watchdog_ns)) return false;
     *out = ld_relaxed_u64(&ws->keys[t % 3]);
     // slot (t+2)%3 was last read at iteration t-1, before every CTA arrived
     // at this barrier; it is next written at iteration t+2, after the next one.
@@ -191,6 +211,35 @@ MP_DEV bool grid_exchange(const PlainArgs<double>& a, int cta, int G, int t, Key
     }
     *out = warp_max_key(best);
     return true;
+}
+
+// Every compute thread of every CTA: grid barrier `bar` (the CTA's writes
+// before it are visible to every CTA after it).  False when the wait ran
+// out (the error word is set; the CTA's abort flag too).
+template <typename T>
+MP_DEV bool cta_grid_sync(const PlainArgs<T>& a, PlainShared<T>* sh, int G, int bar, int ct, int nct) {
+    named_bar_sync(1, nct);
+    if (ct == 0) {
+        red_release_add_u64(&a.ws->count, 1ull);
+        if (!grid_wait(a.ws, static_cast<unsigned long long>(bar + 1) * G, a.watchdog_ns))
+            *reinterpret_cast<volatile int*>(&sh->abort) = 1;
+    }
+    named_bar_sync(1, nct);
+    return *reinterpret_cast<volatile int*>(&sh->abort) == 0;
+}
+
+// <q, r> with q = s w elementwise, in dot1's order (one warp).
+MP_DEV float dot1_scaled(const float* __restrict__ w, float s, const float* __restrict__ r, int ldN, int lane) {
+    float ax = 0.f, ay = 0.f, az = 0.f, aw = 0.f;
+    for (int off = lane * 4; off < ldN; off += 128) {
+        const float4 q = *reinterpret_cast<const float4*>(r + off);
+        const float4 v = *reinterpret_cast<const float4*>(w + off);
+        ax = fmaf(v.x * s, q.x, ax);
+        ay = fmaf(v.y * s, q.y, ay);
+        az = fmaf(v.z * s, q.z, az);
+        aw = fmaf(v.w * s, q.w, aw);
+    }
+    return warp_sum_f32((ax + ay) + (az + aw));
 }
 
 // ------------------------------------------------------------------ producer
@@ -261,9 +310,12 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const PlainArgs<T> a) {
     using Key = typename PlainTraits<T>::Key;
     using V = typename PlainTraits<T>::V;
-    constexpr bool STREAM = MODE == 3;
+    constexpr bool OMP = MODE >= 5;       // 5 grid-resident, 6 grid-streaming
+    constexpr bool STREAM = MODE == 3 || MODE == 6;
     constexpr bool CLUSTER = MODE == 1;
+    constexpr bool GRAM = MODE == 4;
     constexpr bool FP64 = sizeof(T) == 8;
+    constexpr int NB = OMP ? 5 : 1;       // grid barriers per iteration
     constexpr int kV = 16 / sizeof(T);
     extern __shared__ __align__(128) unsigned char smem[];
     T* r = reinterpret_cast<T*>(smem);
@@ -305,7 +357,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
     // ---- Eq. 8: r <- y (zero padded), x~ <- 0 (own slice), resident atoms
     for (int i = ct; i < ldN; i += nct) r[i] = i < a.N ? a.y[i] : T(0);
     for (int i = ct; i < na; i += nct) a.x[a0 + i] = T(0);
-    if (!STREAM) {
+    if (!STREAM && !GRAM) {
         const float4* src = reinterpret_cast<const float4*>(a.psi + static_cast<size_t>(a0) * ldN);
         float4* dst = reinterpret_cast<float4*>(data);
         const int n16 = na * (ldN / kV);
@@ -329,11 +381,40 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
     int t = 0;
     double audit = 0.0;
     bool aborted = false;
+    bool rank_stop = false;   // OMP: the selected atom lies in the span of those selected
     const int A = a.stage_atoms, D = a.stages;
+    int m_prev = 0;        // mode 4: the previous step's atom and coefficient
+    T c_prev = T(0);
     while (finite0 && e > thr2 && t < a.T_max) {
         // ---- Eq. 9: correlations of this CTA's atoms, best packed key
         Key best = kzero;
-        if (!STREAM) {
+        if constexpr (GRAM) {
+            // the CTA's correlations live in shared memory: recomputed from
+            // the atoms (same order as the other shapes) every gram_period
+            // steps, otherwise updated by c_m -= c_prev G[m_prev][m]
+            T* cs = data;
+            if (t % a.gram_period == 0) {
+                for (int j = 4 * cw; j < na; j += 4 * ncw) {
+                    if (j + 4 <= na) {
+                        T c4[4];
+                        dot4(a.psi + static_cast<size_t>(a0 + j) * ldN, r, ldN, lane, c4);
+                        if (lane == 0)
+                            for (int i = 0; i < 4; ++i) cs[j + i] = c4[i];
+                    } else {
+                        for (int q = j; q < na; ++q) {
+                            const T v = dot1(a.psi + static_cast<size_t>(a0 + q) * ldN, r, ldN, lane);
+                            if (lane == 0) cs[q] = v;
+                        }
+                    }
+                }
+            } else {
+                const T* g = a.G + static_cast<size_t>(m_prev) * a.ldG + a0;
+                for (int j = ct; j < na; j += nct) cs[j] = fmaf(-c_prev, __ldg(g + j), cs[j]);
+            }
+            named_bar_sync(1, nct);
+            for (int j = ct; j < na; j += nct) best = kmax(best, pack_key(cs[j], a0 + j));
+            best = warp_max_key(best);
+        } else if (!STREAM) {
             for (int j = 4 * cw; j < na; j += 4 * ncw)
                 best = scan_atoms(data + static_cast<size_t>(j) * ldN, r, ldN, min(4, na - j), a0 + j, lane, best);
         } else {
@@ -378,7 +459,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
                 // the grid's winner is one of the CTAs' local bests: start
                 // pulling this one into L2 for the residual update
                 if (k != 0ull) prefetch_l2(a.psi + static_cast<size_t>(key_index(k)) * ldN, ldN * 4u);
-                if (!grid_exchange(a, cta, G, t, k, &g)) *reinterpret_cast<volatile int*>(&sh->abort) = 1;
+                if (!grid_exchange(a, cta, G, t, t * NB, k, &g)) *reinterpret_cast<volatile int*>(&sh->abort) = 1;
                 sh->key = g;
             }
         } else {
@@ -414,10 +495,99 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
         const int m = key_index(key);
         const T c = key_coef(key);
 
-        // ---- Eq. 11: r <- r - c psi_m, and e = sum r^2 in FP64.  In the
-        // cluster shape psi_m is resident in its owner CTA's shared memory
-        // and is read from there over DSMEM; otherwise from global memory.
-        const V* pm = reinterpret_cast<const V*>(a.psi + static_cast<size_t>(m) * ldN);
+        // ---- OMP: orthonormalise psi_m against the basis Q of the atoms
+        // selected so far (classical Gram-Schmidt, applied twice), then the
+        // residual update below uses the new basis vector q = w2 / ||w2||
+        // and alpha = <r, q>: r - alpha q = y - Psi_S x_S for the least-
+        // squares x_S, which the back substitution after the loop recovers.
+        T step = c;            // coefficient of this step's update
+        T qscale = T(1);       // OMP: 1 / ||w2||
+        if constexpr (OMP) {
+            const int k = t;
+            const int GW = G * ncw, gw = cta * ncw + cw;
+            const int chunk = (ldN / kV + G - 1) / G * kV;
+            const int n0 = min(ldN, cta * chunk), n1 = min(ldN, n0 + chunk);
+            bool ok = k < a.kmax;
+            if (!ok) rank_stop = true;
+            for (int pass = 0; pass < 2 && ok; ++pass) {
+                const T* v = pass == 0 ? a.psi + static_cast<size_t>(m) * ldN : a.w;
+                T* hp = pass == 0 ? a.h : a.h2;
+                T* wo = pass == 0 ? a.w : a.w2;
+                for (int j = gw; j < k; j += GW) {
+                    const T d = dot1(a.Q + static_cast<size_t>(j) * ldN, v, ldN, lane);
+                    if (lane == 0) hp[j] = d;
+                }
+                if (!cta_grid_sync(a, sh, G, t * NB + 1 + 2 * pass, ct, nct)) {
+                    ok = false;
+                    aborted = true;
+                    break;
+                }
+                double nacc = 0.0;
+                for (int n = n0 + ct; n < n1; n += nct) {
+                    T acc = v[n];
+                    for (int j = 0; j < k; ++j) acc = fmaf(-hp[j], a.Q[static_cast<size_t>(j) * ldN + n], acc);
+                    wo[n] = acc;
+                    nacc = fma(static_cast<double>(acc), static_cast<double>(acc), nacc);
+                }
+                if (pass == 1) {
+                    nacc = warp_sum_f64(nacc);
+                    if (lane == 0) sh->wsum[cw] = nacc;
+                    named_bar_sync(1, nct);
+                    if (ct == 0) {
+                        double sum = 0.0;
+                        for (int q = 0; q < ncw; ++q) sum += sh->wsum[q];
+                        a.nrm[cta] = sum;
+                    }
+                }
+                if (!cta_grid_sync(a, sh, G, t * NB + 2 + 2 * pass, ct, nct)) {
+                    ok = false;
+                    aborted = true;
+                    break;
+                }
+            }
+            if (aborted) break;
+            if (ok) {
+                // ||w2||^2 in one fixed order: the same value in every CTA
+                // (broadcast through the last two wsum slots, which no warp
+                // index reaches: at most 8 compute warps)
+                if (ct == 0) {
+                    double sum = 0.0;
+                    for (int q = 0; q < G; ++q) sum += a.nrm[q];
+                    sh->wsum[kMaxWarps - 1] = sum;
+                }
+                named_bar_sync(1, nct);
+                const double nw2 = sh->wsum[kMaxWarps - 1];
+                // unit atoms: a component below 1e-4 is rounding, not a new direction
+                if (!(nw2 > 1e-8)) rank_stop = true;
+                else qscale = static_cast<T>(1.0 / sqrt(nw2));
+                if (!rank_stop) {
+                    if (cw == 0) {
+                        const T al = dot1_scaled(a.w2, qscale, r, ldN, lane);
+                        if (lane == 0) sh->wsum[kMaxWarps - 2] = static_cast<double>(al);
+                    }
+                    named_bar_sync(1, nct);
+                    step = static_cast<T>(sh->wsum[kMaxWarps - 2]);
+                    if (cta == 0) {
+                        // record the basis vector, R's column k and alpha_k
+                        for (int n = ct; n < ldN; n += nct) a.Q[static_cast<size_t>(k) * ldN + n] = a.w2[n] * qscale;
+                        const size_t ck = static_cast<size_t>(k) * (k + 1) / 2;
+                        for (int j = ct; j < k; j += nct) a.Rc[ck + j] = a.h[j] + a.h2[j];
+                        if (ct == 0) {
+                            a.Rc[ck + k] = static_cast<T>(sqrt(nw2));
+                            a.alpha[k] = step;
+                            a.sel[k] = m;
+                        }
+                    }
+                }
+            }
+            if (rank_stop) break;
+        }
+
+        // ---- Eq. 11: r <- r - c psi_m, and e = sum r^2 in FP64 (OMP:
+        // r <- r - alpha q).  In the cluster shape psi_m is resident in its
+        // owner CTA's shared memory and is read from there over DSMEM;
+        // otherwise from global memory.
+        const V* pm = reinterpret_cast<const V*>(OMP ? a.w2 : a.psi + static_cast<size_t>(m) * ldN);
         uint32_t pm_cluster = 0;
         if (CLUSTER) {
             // owner of atom m under the slice split above
@@ -430,8 +600,9 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
         for (int k = ct; k < nvr; k += nct) {
             V pv;
             if (CLUSTER) dsmem_ld(pm_cluster + 16u * k, &pv);
+            else if (OMP) pv = scale_vec(pm[k], qscale);
             else pv = __ldg(pm + k);
-            const V v = sub_scaled(c, pv, rv[k]);
+            const V v = sub_scaled(step, pv, rv[k]);
             rv[k] = v;
             acc = sq_acc(v, acc);
         }
@@ -445,20 +616,39 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
         if (cta == 0 && ct == 0) {
             // fire-and-forget: same-address reductions from one thread apply
             // in program order, so x~_m accumulates exactly as x~_m += c would
-            red_add(a.x + m, c);
+            // (OMP: x~ comes from the back substitution after the loop)
+            if (!OMP) red_add(a.x + m, c);
             if (t < a.tr_cap) {
                 if (a.tr_atoms) a.tr_atoms[t] = m;
                 if (a.tr_coefs) a.tr_coefs[t] = c;
                 if (a.tr_energy) a.tr_energy[t] = e_new;
             }
-            const double cc = static_cast<double>(c);
+            const double cc = static_cast<double>(step);
             audit = fmax(audit, fabs(e_new - (e - cc * cc)) / e0);
         }
         e = e_new;
+        m_prev = m;
+        c_prev = c;
         ++t;  // Eq. 12
     }
 
     if (STREAM && ct == 0) *reinterpret_cast<volatile int*>(&sh->done) = 1;
+    if constexpr (OMP) {
+        // R x_S = alpha by back substitution over R's packed columns, then
+        // x~[sel_i] = x_i (CTA 0; every other CTA zeroed its x~ slice at the
+        // start, before the first grid barrier)
+        if (cta == 0 && !aborted) {
+            for (int i = ct; i < t; i += nct) a.xs[i] = a.alpha[i];
+            named_bar_sync(1, nct);
+            for (int i = t - 1; i >= 0; --i) {
+                const size_t ci = static_cast<size_t>(i) * (i + 1) / 2;
+                const T xi = a.xs[i] / a.Rc[ci + i];
+                for (int j = ct; j < i; j += nct) a.xs[j] = fmaf(-a.Rc[ci + j], xi, a.xs[j]);
+                if (ct == 0) a.x[a.sel[i]] = xi;
+                named_bar_sync(1, nct);
+            }
+        }
+    }
     if (cta == 0 && a.tr_resid)
         for (int i = ct; i < a.N; i += nct) a.tr_resid[i] = r[i];
     if (cta == 0 && ct == 0) {
@@ -467,7 +657,9 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
         res.e0 = e0;
         res.e = e;
         res.audit_max = audit;
-        res.stop_reason = e0 == 0.0 ? MP_STOP_ZERO_Y : (e <= thr2 ? MP_STOP_CONVERGED : MP_STOP_MAX_ITERS);
+        res.stop_reason = e0 == 0.0 ? MP_STOP_ZERO_Y
+                          : rank_stop ? MP_STOP_RANK
+                                      : (e <= thr2 ? MP_STOP_CONVERGED : MP_STOP_MAX_ITERS);
         res.status = !finite0 ? MP_ERR_NONFINITE : (aborted ? MP_ERR_TIMEOUT : MP_OK);
     }
     if (CLUSTER) cluster_sync_all();  // peers may still read this CTA's key slot
@@ -519,8 +711,10 @@ static int max_cluster_size(int smem, int threads, int max_smem) {
     return best;
 }
 
+// omp: the OMP decode (grid shapes only: its Gram-Schmidt phases need grid
+// barriers), reported as mode 5 (grid-resident) or 6 (grid-streaming).
 template <typename T>
-static mp_status plain_configure_t(PlanImpl* p, PlainConfig* cfg) {
+static mp_status plain_configure_t(PlanImpl* p, PlainConfig* cfg, bool omp = false) {
     *cfg = PlainConfig();
     const long long atom_bytes = static_cast<long long>(p->ldN) * sizeof(T);
     const int r_bytes = round_up_i(p->ldN * static_cast<int>(sizeof(T)), 128);
@@ -556,10 +750,22 @@ static mp_status plain_configure_t(PlanImpl* p, PlainConfig* cfg) {
         return cfg->off_data + apc * atom_bytes <= p->max_smem_optin;
     };
 
+    if (sizeof(T) == 4 && p->gram_period > 0 && !omp) {
+        // mode 4: r and the CTA's correlations on chip, atoms and G from HBM
+        const long long apc = (M + G - 1) / G;
+        if (cfg->off_data + apc * static_cast<long long>(sizeof(T)) > p->max_smem_optin)
+            return fail(MP_ERR_UNSUPPORTED, "Gram decode: the correlations do not fit shared memory");
+        cfg->mode = 4;
+        cfg->ctas = G;
+        cfg->threads = kResidentThreads;
+        cfg->smem = static_cast<int>(cfg->off_data + apc * static_cast<long long>(sizeof(T)));
+        return MP_OK;
+    }
     int mode = p->forced_mode;
     int C = 0;
+    if (omp && mode == 1) return fail(MP_ERR_UNSUPPORTED, "OMP decode: no one-cluster launch shape");
     if (mode == 0) {
-        if (cluster_ok(&C)) mode = 1;
+        if (!omp && cluster_ok(&C)) mode = 1;
         else if (gridres_ok()) mode = 2;
         else mode = 3;
     } else if (mode == 1 && !cluster_ok(&C)) {
@@ -575,14 +781,19 @@ static mp_status plain_configure_t(PlanImpl* p, PlainConfig* cfg) {
         return MP_OK;
     }
     if (mode == 2) {
+        cfg->mode = omp ? 5 : 2;
         cfg->ctas = G;
         cfg->threads = kResidentThreads;
         cfg->smem = static_cast<int>(cfg->off_data + static_cast<long long>((M + G - 1) / G) * atom_bytes);
         return MP_OK;
     }
     // mode 3: atoms per stage A, ring depth D, consumer warps W
+    // A: whole atoms per stage, at least stage_bytes when that still leaves
+    // a ring of 4 stages (larger copies stream faster; 4 stages keep 4
+    // consumer warps busy), else at most stage_bytes (and at least one atom)
     const long long apc = (M + G - 1) / G;
-    long long A = std::max<long long>(1, p->stage_bytes / atom_bytes);
+    long long A = std::max<long long>(1, (p->stage_bytes + atom_bytes - 1) / atom_bytes);
+    if (budget / (A * atom_bytes) < 4) A = std::max<long long>(1, p->stage_bytes / atom_bytes);
     A = std::min(A, apc);
     const long long stage_bytes = A * atom_bytes;
     // as deep a ring as fits; up to 4 consumer warps, each owning the slots
@@ -592,6 +803,7 @@ static mp_status plain_configure_t(PlanImpl* p, PlainConfig* cfg) {
         return fail(MP_ERR_UNSUPPORTED, "plain decode: N=" + std::to_string(p->N) +
                                             " leaves no room for a two-stage ring");
     const int W = static_cast<int>(std::min<long long>(4, D));
+    cfg->mode = omp ? 6 : 3;
     cfg->ctas = G;
     cfg->threads = 32 * (1 + W);
     cfg->stage_atoms = static_cast<int>(A);
@@ -606,9 +818,9 @@ mp_status plain_configure64(PlanImpl* p, PlainConfig* cfg) { return plain_config
 template <typename T>
 static mp_status plain_launch_t(PlanImpl* p, const T* psi, const T* y, T* x, const mp_stop* stop, int* tr_atoms,
                                 T* tr_coefs, double* tr_energy, T* tr_resid, int tr_cap, PlainWorkspace* ws,
-                                cudaStream_t st) {
+                                cudaStream_t st, bool omp = false) {
     PlainConfig cfg;
-    mp_status s = plain_configure_t<T>(p, &cfg);
+    mp_status s = plain_configure_t<T>(p, &cfg, omp);
     if (s != MP_OK) return s;
     PlainArgs<T> a;
     std::memset(&a, 0, sizeof(a));
@@ -635,6 +847,25 @@ static mp_status plain_launch_t(PlanImpl* p, const T* psi, const T* y, T* x, con
     a.tr_cap = std::max(0, tr_cap);
     a.watchdog_ns = static_cast<unsigned long long>(p->watchdog_ns);
     a.skip_cta = cfg.mode == 1 ? -1 : p->skip_cta;
+    if (cfg.mode == 4) {
+        a.G = reinterpret_cast<const T*>(p->gram);
+        a.ldG = p->ldG;
+        a.gram_period = p->gram_period;
+    }
+    if (omp) {
+        OmpWorkspace& o = p->omp;
+        a.Q = reinterpret_cast<T*>(o.Q);
+        a.Rc = reinterpret_cast<T*>(o.Rc);
+        a.alpha = reinterpret_cast<T*>(o.alpha);
+        a.sel = o.sel;
+        a.h = reinterpret_cast<T*>(o.h);
+        a.h2 = reinterpret_cast<T*>(o.h2);
+        a.w = reinterpret_cast<T*>(o.w);
+        a.w2 = reinterpret_cast<T*>(o.w2);
+        a.nrm = o.nrm;
+        a.xs = reinterpret_cast<T*>(o.xs);
+        a.kmax = std::min(stop->max_iters, p->N);
+    }
 
     MP_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(PlainWorkspace), st));
     cudaLaunchConfig_t lc = {};
@@ -664,9 +895,25 @@ static mp_status plain_launch_t(PlanImpl* p, const T* psi, const T* y, T* x, con
             MP_CUDA_TRY((prepare_kernel_attrs<T, 2>(p->max_smem_optin)));
             e = cudaLaunchKernelEx(&lc, mp_plain_kernel<T, 2>, a);
             break;
-        default:
+        case 3:
             MP_CUDA_TRY((prepare_kernel_attrs<T, 3>(p->max_smem_optin)));
             e = cudaLaunchKernelEx(&lc, mp_plain_kernel<T, 3>, a);
+            break;
+        default:
+            if constexpr (sizeof(T) == 4) {
+                if (cfg.mode == 4) {
+                    MP_CUDA_TRY((prepare_kernel_attrs<T, 4>(p->max_smem_optin)));
+                    e = cudaLaunchKernelEx(&lc, mp_plain_kernel<T, 4>, a);
+                } else if (cfg.mode == 5) {
+                    MP_CUDA_TRY((prepare_kernel_attrs<T, 5>(p->max_smem_optin)));
+                    e = cudaLaunchKernelEx(&lc, mp_plain_kernel<T, 5>, a);
+                } else {
+                    MP_CUDA_TRY((prepare_kernel_attrs<T, 6>(p->max_smem_optin)));
+                    e = cudaLaunchKernelEx(&lc, mp_plain_kernel<T, 6>, a);
+                }
+            } else {
+                e = cudaErrorInvalidConfiguration;
+            }
             break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "plain decode launch");
@@ -676,9 +923,46 @@ static mp_status plain_launch_t(PlanImpl* p, const T* psi, const T* y, T* x, con
 
 mp_status plain_launch(PlanImpl* p, const float* y, float* x, const mp_stop* stop, const mp_trace* trace,
                        PlainWorkspace* ws, cudaStream_t st) {
+    if (p->gram_period > 0) {
+        const mp_status s = gram_prepare(p, st);
+        if (s != MP_OK) return s;
+    }
     if (!trace) return plain_launch_t<float>(p, p->psi32, y, x, stop, nullptr, nullptr, nullptr, nullptr, 0, ws, st);
     return plain_launch_t<float>(p, p->psi32, y, x, stop, trace->atoms, trace->coefs, trace->energies,
                                  trace->residual, trace->capacity, ws, st);
+}
+
+// OMP scratch for up to kmax selected atoms (grown on demand, kept by the plan).
+static mp_status omp_prepare(PlanImpl* p, int kmax) {
+    OmpWorkspace& o = p->omp;
+    if (o.kmax >= kmax && o.G >= p->sm_count) return MP_OK;
+    omp_free(&o);
+    const size_t ld = static_cast<size_t>(p->ldN), k = static_cast<size_t>(std::max(1, kmax));
+    const size_t G = static_cast<size_t>(std::max(1, p->sm_count));
+    MP_CUDA_TRY(cudaMalloc(&o.Q, k * ld * sizeof(float)));
+    MP_CUDA_TRY(cudaMalloc(&o.Rc, k * (k + 1) / 2 * sizeof(float)));
+    MP_CUDA_TRY(cudaMalloc(&o.alpha, k * sizeof(float)));
+    MP_CUDA_TRY(cudaMalloc(&o.sel, k * sizeof(int)));
+    MP_CUDA_TRY(cudaMalloc(&o.h, k * sizeof(float)));
+    MP_CUDA_TRY(cudaMalloc(&o.h2, k * sizeof(float)));
+    MP_CUDA_TRY(cudaMalloc(&o.w, ld * sizeof(float)));
+    MP_CUDA_TRY(cudaMalloc(&o.w2, ld * sizeof(float)));
+    MP_CUDA_TRY(cudaMalloc(&o.nrm, G * sizeof(double)));
+    MP_CUDA_TRY(cudaMalloc(&o.xs, k * sizeof(float)));
+    o.kmax = static_cast<int>(k);
+    o.G = static_cast<int>(G);
+    o.bytes = (k * ld + k * (k + 1) / 2 + 5 * k + 2 * ld) * sizeof(float) + G * sizeof(double);
+    return MP_OK;
+}
+
+mp_status plain_launch_omp(PlanImpl* p, const float* y, float* x, const mp_stop* stop, const mp_trace* trace,
+                           PlainWorkspace* ws, cudaStream_t st) {
+    const mp_status s = omp_prepare(p, std::min(std::max(stop->max_iters, 1), p->N));
+    if (s != MP_OK) return s;
+    if (!trace)
+        return plain_launch_t<float>(p, p->psi32, y, x, stop, nullptr, nullptr, nullptr, nullptr, 0, ws, st, true);
+    return plain_launch_t<float>(p, p->psi32, y, x, stop, trace->atoms, trace->coefs, trace->energies,
+                                 trace->residual, trace->capacity, ws, st, true);
 }
 
 mp_status plain_launch64(PlanImpl* p, const double* y, double* x, const mp_stop* stop, const mp_trace_f64* trace,
@@ -728,6 +1012,22 @@ mp_status mp_recover(mp_plan_t plan, const float* y, float* x, const mp_stop* st
     PlanImpl* p = &plan->impl;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     s = plain_launch(p, y, x, stop, trace, p->ws, st);
+    if (s != MP_OK) return s;
+    p->last_stream = st;
+    p->have_pending = true;
+    if (!host_out) return MP_OK;
+    return mp_plan_last_result(plan, host_out);
+}
+
+mp_status mp_recover_omp(mp_plan_t plan, const float* y, float* x, const mp_stop* stop, const mp_trace* trace,
+                         mp_result* host_out, void* stream) {
+    clear_error();
+    if (!plan || !y || !x) return fail(MP_ERR_INVALID, "mp_recover_omp: NULL plan, y or x");
+    mp_status s = check_stop(stop);
+    if (s != MP_OK) return s;
+    PlanImpl* p = &plan->impl;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    s = plain_launch_omp(p, y, x, stop, trace, p->ws, st);
     if (s != MP_OK) return s;
     p->last_stream = st;
     p->have_pending = true;

@@ -139,6 +139,8 @@ static void plan_free(PlanImpl* p) {
     cudaFree(p->scale8);
     cudaFree(p->psi64);
     cudaFree(p->slots64);
+    cudaFree(p->gram);
+    omp_free(&p->omp);
     cudaFree(p->ws);
     cudaFree(p->y_stage);
     cudaFree(p->x_stage);
@@ -329,6 +331,10 @@ mp_status mp_plan_set_option(mp_plan_t plan, int option, long long value) {
         case MP_OPT_PLAIN_EVICT_FIRST:
             p->evict_first = value ? 1 : 0;
             return MP_OK;
+        case MP_OPT_PLAIN_GRAM:
+            if (value < 0 || value > (1 << 20)) return fail(MP_ERR_INVALID, "Gram refresh period must be 0..2^20");
+            p->gram_period = static_cast<int>(value);
+            return MP_OK;
         case MP_OPT_BATCH_AUTOTUNE:
             p->batch_autotune = value ? 1 : 0;
             return MP_OK;
@@ -364,6 +370,9 @@ mp_status mp_plan_query(mp_plan_t plan, int what, long long* value) {
         case MP_Q_KERNEL_LAUNCHES: *value = p->launches; return MP_OK;
         case MP_Q_BATCH_TILE_N: *value = p->batch ? p->batch->TN : 0; return MP_OK;
         case MP_Q_BATCH_CLUSTER: *value = p->batch ? p->batch->CL : 0; return MP_OK;
+        case MP_Q_GRAM_BYTES:
+            *value = p->gram ? static_cast<long long>(p->M) * p->ldG * 4 : 0;
+            return MP_OK;
         case MP_Q_PLAIN64_MODE:
         case MP_Q_PLAIN64_STAGES: {
             PlainConfig c64;

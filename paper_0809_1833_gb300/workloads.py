@@ -197,6 +197,31 @@ def paper_timing_problem(M: int, seed: int = 0, fp64: bool = False) -> Problem:
     return Problem(psi, encode(psi, x, np.float64)[None, :], x[None, :], [supp], 1e-7, N)
 
 
+PHASE_M = 1000
+PHASE_GRID = tuple(round(0.05 * i, 2) for i in range(1, 21))     # sigma and rho: 0.05 .. 1.00
+
+
+def phase_diagram_batch(rho: float, sigmas, trials: int, M: int = PHASE_M, seed: int = 0) -> Problem:
+    """Sec. 3's phase-diagram experiment at one rho = N/M: a Bernoulli
+    dictionary (Eq. 13) with N = round(rho M) rows, and ``trials`` signals
+    for each sigma = K/M (K = max(1, round(sigma M)) nonzeros with U[-1,1]
+    values), sigma-major; eps = 1e-7 and T = N as in the paper's run.  The
+    batch shares the dictionary, so one batched decode covers a column of
+    the diagram."""
+    N = max(1, int(round(rho * M)))
+    psi = bernoulli_dictionary(N, M, seed=1000 * seed + N)
+    g = _rng(seed, 10000 + N)
+    Y, X, supps = [], [], []
+    for sg in sigmas:
+        K = max(1, int(round(sg * M)))
+        for _ in range(trials):
+            x, supp = sparse_signal(M, K, g, "uniform11")
+            X.append(x)
+            Y.append(encode(psi, x))
+            supps.append(supp)
+    return Problem(psi, np.stack(Y), np.stack(X), supps, 1e-7, N)
+
+
 def poisson_arrivals(rate: float, duration: float, seed: int = 0) -> np.ndarray:
     """Arrival times (s) of a Poisson process of the given rate."""
     g = _rng(seed, 3)

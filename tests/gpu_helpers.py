@@ -140,12 +140,17 @@ def first_near_tie(gaps):
     return int(idx[0]) if idx.size else None
 
 
-def compare_to_oracle(psi, y, eps, T, gpu, ora=None, x_tol=1e-4, check_follow=True, fp64=False):
+def compare_to_oracle(psi, y, eps, T, gpu, ora=None, x_tol=1e-4, check_follow=True, fp64=False, gram_period=0):
     """Apply rules (i)-(iii); returns a dict of diagnostics, asserts on failure.
     ``check_follow=False`` skips the FP64 replay when the whole sequence and
     the iteration count already match the oracle literally.  ``fp64``: the
     GPU path computed in FP64, so gamma_d = d 2^-53 (d from
-    summation_depth64) and the near-tie floor is GAP_TIE64."""
+    summation_depth64) and the near-tie floor is GAP_TIE64.  ``gram_period``
+    R > 0: the correlations were updated through the Gram matrix for up to
+    R - 1 steps after each direct computation; each update adds at most
+    |c_prev| |G - Psi^T Psi| + 2^-24 |c_m| <= (N + 2) 2^-24 ||r|| of error
+    (G entries are N-term FP32 FMA chains of unit atoms), so gamma_d grows
+    by 2 R (N + 2) 2^-24 (a factor 2 for ||r|| at the refresh vs now)."""
     from oracle import mp_oracle as orc
     if ora is None:
         ora = orc.mp(psi, y, eps, T)
@@ -163,6 +168,8 @@ def compare_to_oracle(psi, y, eps, T, gpu, ora=None, x_tol=1e-4, check_follow=Tr
         Delta = float(np.linalg.norm(gpu["r"].astype(np.float64) - f["r"]))
         out["drift"] = Delta
     gamma = summation_depth64(N) * U64 if fp64 else summation_depth(N) * U32
+    if gram_period > 0:
+        gamma += 2 * gram_period * (N + 2) * U32
     floor = GAP_TIE64 if fp64 else GAP_TIE
     if len(oa):
         rk = np.sqrt(np.concatenate([[ora["e0"]], ora["energies"][:-1]]))
