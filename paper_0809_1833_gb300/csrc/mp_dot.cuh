@@ -49,39 +49,69 @@ MP_DEV void dot4(const float* __restrict__ p, const float* __restrict__ r, int l
 
 namespace mpgb {
 
-// FP64 correlation with its own fixed order: lane l accumulates elements
-// 2l, 2l+1 of each 64-double segment in two FMA chains, adds them, and a
-// butterfly sum across the warp finishes.  p and r 16-byte aligned, ldN a
-// multiple of 2, zero padded past N.
+// FP64 correlation with its own fixed order.  The 64-double segments of
+// the row fall in 4 classes (segment index mod 4); lane l accumulates
+// elements 2l, 2l+1 of the segments of class q in two FMA chains x_q, y_q
+// (increasing segment index), forms p_q = x_q + y_q, combines
+// (p_0 + p_1) + (p_2 + p_3), and a butterfly sum across the warp finishes.
+// The class split lets four warps share one atom (warp q computing p_q)
+// with the same bits as one warp computing all four.  p and r 16-byte
+// aligned, ldN a multiple of 2, zero padded past N.
 MP_DEV double dot1(const double* __restrict__ p, const double* __restrict__ r, int ldN, int lane) {
-    double ax = 0.0, ay = 0.0;
-#pragma unroll 4
-    for (int off = lane * 2; off < ldN; off += 64) {
-        const double2 q = *reinterpret_cast<const double2*>(r + off);
-        const double2 v = *reinterpret_cast<const double2*>(p + off);
-        ax = fma(v.x, q.x, ax);
-        ay = fma(v.y, q.y, ay);
+    double ax[4] = {0.0, 0.0, 0.0, 0.0}, ay[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int base = lane * 2; base < ldN; base += 256) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int off = base + 64 * q;
+            if (off < ldN) {
+                const double2 u = *reinterpret_cast<const double2*>(r + off);
+                const double2 v = *reinterpret_cast<const double2*>(p + off);
+                ax[q] = fma(v.x, u.x, ax[q]);
+                ay[q] = fma(v.y, u.y, ay[q]);
+            }
+        }
     }
-    return warp_sum_f64(ax + ay);
+    return warp_sum_f64(((ax[0] + ay[0]) + (ax[1] + ay[1])) + ((ax[2] + ay[2]) + (ax[3] + ay[3])));
 }
 
 // Four consecutive FP64 atoms (stride ldN), same order per atom as dot1.
 MP_DEV void dot4(const double* __restrict__ p, const double* __restrict__ r, int ldN, int lane, double out[4]) {
-    double a[4][2];
+    double ax[4][4], ay[4][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) a[i][0] = a[i][1] = 0.0;
-#pragma unroll 2
-    for (int off = lane * 2; off < ldN; off += 64) {
-        const double2 q = *reinterpret_cast<const double2*>(r + off);
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const double2 v = *reinterpret_cast<const double2*>(p + static_cast<size_t>(i) * ldN + off);
-            a[i][0] = fma(v.x, q.x, a[i][0]);
-            a[i][1] = fma(v.y, q.y, a[i][1]);
+        for (int q = 0; q < 4; ++q) ax[i][q] = ay[i][q] = 0.0;
+    for (int base = lane * 2; base < ldN; base += 256) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int off = base + 64 * q;
+            if (off < ldN) {
+                const double2 u = *reinterpret_cast<const double2*>(r + off);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const double2 v = *reinterpret_cast<const double2*>(p + static_cast<size_t>(i) * ldN + off);
+                    ax[i][q] = fma(v.x, u.x, ax[i][q]);
+                    ay[i][q] = fma(v.y, u.y, ay[i][q]);
+                }
+            }
         }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) out[i] = warp_sum_f64(a[i][0] + a[i][1]);
+    for (int i = 0; i < 4; ++i)
+        out[i] = warp_sum_f64(((ax[i][0] + ay[i][0]) + (ax[i][1] + ay[i][1])) +
+                              ((ax[i][2] + ay[i][2]) + (ax[i][3] + ay[i][3])));
+}
+
+// One class of dot1's sum: lane l's p_q for the segments of class q.
+MP_DEV double dot_class(const double* __restrict__ p, const double* __restrict__ r, int ldN, int lane, int q) {
+    double ax = 0.0, ay = 0.0;
+    for (int off = lane * 2 + 64 * q; off < ldN; off += 256) {
+        const double2 u = *reinterpret_cast<const double2*>(r + off);
+        const double2 v = *reinterpret_cast<const double2*>(p + off);
+        ax = fma(v.x, u.x, ax);
+        ay = fma(v.y, u.y, ay);
+    }
+    return ax + ay;
 }
 
 }  // namespace mpgb

@@ -53,6 +53,7 @@ struct PlainConfig {
     int stages = 0;        // mode 3
     int off_data = 0;      // byte offsets inside dynamic smem
     int off_sh = 0;
+    int coop = 0;          // FP64 streaming: 4 warps share every stage
 };
 
 // OMP decode scratch (mp_plain.cu): basis, packed R, alpha = Q^T y,
@@ -66,6 +67,7 @@ struct OmpWorkspace {
     float* h2 = nullptr;
     float* w = nullptr;
     float* w2 = nullptr;
+    float* wpart = nullptr;
     double* nrm = nullptr;
     float* xs = nullptr;
     int kmax = 0;
@@ -82,6 +84,7 @@ inline void omp_free(OmpWorkspace* o) {
     cudaFree(o->h2);
     cudaFree(o->w);
     cudaFree(o->w2);
+    cudaFree(o->wpart);
     cudaFree(o->nrm);
     cudaFree(o->xs);
     *o = OmpWorkspace();

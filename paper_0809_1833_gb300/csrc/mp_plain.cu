@@ -35,6 +35,11 @@ namespace mpgb {
 constexpr int kMaxWarps = 32;
 constexpr int kMaxStages = 64;
 constexpr int kResidentThreads = 256;
+// FP64 sums of squares (the energy, OMP's ||w||^2) run as kSumChains FMA
+// chains (chain i takes the elements i, i + kSumChains, ...), then warp sums
+// in warp order: the same bits for every launch shape, whatever its thread
+// count (each shape has at least kSumChains compute threads).
+constexpr int kSumChains = 128;
 
 // Per-precision types: the argmax key and the 16-byte vector the residual
 // and the atoms are read in.
@@ -51,9 +56,21 @@ struct PlainTraits<double> {
     using V = double2;
 };
 
+// FP64 grid streaming with one atom per stage and a ring shallower than the
+// 4 consumer warps: every warp computes its class of each atom's sum (see
+// dot1 for double) into these partials, one warp combines them.
+template <typename T>
+struct CoopPartials {};
+template <>
+struct CoopPartials<double> {
+    double part[2][4][32];
+    int abort[2];
+};
+
 template <typename T>
 struct PlainShared {
     using Key = typename PlainTraits<T>::Key;
+    CoopPartials<T> coop;
     Key keys[2];                         // mode 1: this CTA's key, two-slot ring
     Key wkey[kMaxWarps];                 // per compute warp best key
     double wsum[kMaxWarps];              // per compute warp energy partial
@@ -92,9 +109,11 @@ struct PlainArgs {
     T* h2;
     T* w;
     T* w2;
+    T* wpart;              // 4 x ldN partial sums of the Gram-Schmidt update
     double* nrm;
     T* xs;
     int kmax;
+    int coop;              // FP64 streaming: four warps share every stage (CoopPartials)
     int* tr_atoms;
     T* tr_coefs;
     double* tr_energy;
@@ -337,6 +356,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
 
     if (threadIdx.x == 0) {
         sh->keys[0] = sh->keys[1] = kzero;
+        if constexpr (FP64) sh->coop.abort[0] = sh->coop.abort[1] = 0;
         sh->abort = 0;
         sh->done = 0;
         if (STREAM) {
@@ -368,7 +388,8 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
     V* rv = reinterpret_cast<V*>(r);
     const int nvr = ldN / kV;
     double acc = 0.0;
-    for (int k = ct; k < nvr; k += nct) acc = sq_acc(rv[k], acc);
+    if (ct < kSumChains)
+        for (int k = ct; k < nvr; k += kSumChains) acc = sq_acc(rv[k], acc);
     acc = warp_sum_f64(acc);
     if (lane == 0) sh->wsum[cw] = acc;
     named_bar_sync(1, nct);
@@ -425,6 +446,34 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
             int slot = static_cast<int>(seq0 % D);
             uint32_t par = static_cast<uint32_t>((seq0 / D) & 1);
             for (int j = 0; j < S; ++j, slot = slot + 1 == D ? (par ^= 1u, 0) : slot + 1) {
+                if constexpr (FP64) {
+                    if (a.coop) {
+                        // every warp takes its class of stage j's atom (A = 1).
+                        // Partials and the abort word are double-buffered by
+                        // j's parity: stage j's are written only before
+                        // barrier j and read only after it, and rewritten at
+                        // stage j + 2, after barrier j + 1 -- so every warp
+                        // reads the same abort word and leaves at the same stage
+                        const bool ok = mbar_wait_bounded(&sh->full[slot], par, a.watchdog_ns);
+                        double pq = 0.0;
+                        if (ok) pq = dot_class(data + static_cast<size_t>(slot) * ldN, r, ldN, lane, cw);
+                        else if (lane == 0) {
+                            atomicCAS(&a.ws->err, 0, static_cast<int>(MP_ERR_TIMEOUT));
+                            sh->coop.abort[j & 1] = 1;
+                            *reinterpret_cast<volatile int*>(&sh->abort) = 1;
+                        }
+                        sh->coop.part[j & 1][cw][lane] = pq;
+                        named_bar_sync(2, nct);
+                        if (sh->coop.abort[j & 1]) break;
+                        if (cw == j % ncw) {
+                            const double(&pp)[4][32] = sh->coop.part[j & 1];
+                            const double tot = (pp[0][lane] + pp[1][lane]) + (pp[2][lane] + pp[3][lane]);
+                            best = kmax(best, pack_key(warp_sum_f64(tot), a0 + j));
+                            if (lane == 0) mbar_arrive(&sh->empty[slot]);
+                        }
+                        continue;
+                    }
+                }
                 if (slot % ncw != cw) continue;
                 if (!mbar_wait_bounded(&sh->full[slot], par, a.watchdog_ns)) {
                     if (lane == 0) {
@@ -522,12 +571,29 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
                     aborted = true;
                     break;
                 }
+                // w_n = v_n - sum_j h_j Q[j][n] over the CTA's slice: the
+                // j-sum of each element in 4 fixed quarters (one FMA chain
+                // each, consecutive threads on consecutive n: coalesced rows
+                // of Q), combined as v_n + ((s0 + s1) + (s2 + s3))
+                const int nel = n1 - n0;
+                for (int task = ct; task < 4 * nel; task += nct) {
+                    const int qt = task / nel, n = n0 + task % nel;
+                    const int j0 = (k * qt) / 4, j1 = (k * (qt + 1)) / 4;
+                    T acc = T(0);
+                    for (int j = j0; j < j1; ++j) acc = fmaf(-hp[j], a.Q[static_cast<size_t>(j) * ldN + n], acc);
+                    a.wpart[static_cast<size_t>(qt) * ldN + n] = acc;
+                }
+                named_bar_sync(1, nct);
                 double nacc = 0.0;
                 for (int n = n0 + ct; n < n1; n += nct) {
-                    T acc = v[n];
-                    for (int j = 0; j < k; ++j) acc = fmaf(-hp[j], a.Q[static_cast<size_t>(j) * ldN + n], acc);
-                    wo[n] = acc;
-                    nacc = fma(static_cast<double>(acc), static_cast<double>(acc), nacc);
+                    const T* wp = a.wpart + n;
+                    wo[n] = v[n] + ((wp[0] + wp[ldN]) + (wp[2 * ldN] + wp[3 * ldN]));
+                }
+                if (pass == 1) {
+                    named_bar_sync(1, nct);
+                    if (ct < kSumChains)
+                        for (int n = n0 + ct; n < n1; n += kSumChains)
+                            nacc = fma(static_cast<double>(wo[n]), static_cast<double>(wo[n]), nacc);
                 }
                 if (pass == 1) {
                     nacc = warp_sum_f64(nacc);
@@ -604,7 +670,12 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
             else pv = __ldg(pm + k);
             const V v = sub_scaled(step, pv, rv[k]);
             rv[k] = v;
-            acc = sq_acc(v, acc);
+            if (nct == kSumChains) acc = sq_acc(v, acc);   // the energy chains, fused
+        }
+        if (nct != kSumChains) {
+            named_bar_sync(1, nct);
+            if (ct < kSumChains)
+                for (int k = ct; k < nvr; k += kSumChains) acc = sq_acc(rv[k], acc);
         }
         acc = warp_sum_f64(acc);
         if (lane == 0) sh->wsum[cw] = acc;
@@ -796,13 +867,22 @@ static mp_status plain_configure_t(PlanImpl* p, PlainConfig* cfg, bool omp = fal
     if (budget / (A * atom_bytes) < 4) A = std::max<long long>(1, p->stage_bytes / atom_bytes);
     A = std::min(A, apc);
     const long long stage_bytes = A * atom_bytes;
-    // as deep a ring as fits; up to 4 consumer warps, each owning the slots
-    // s with s % W == its index (D need not be a multiple of W)
-    const long long D = std::min<long long>(kMaxStages, budget / stage_bytes);
+    // as deep a ring as fits; 4 consumer warps (kSumChains threads), each
+    // owning the slots s with s % 4 == its index (D need not be a multiple
+    // of 4; with D < 4 some warps own no slot)
+    long long D = std::min<long long>(kMaxStages, budget / stage_bytes);
     if (D < 2)
         return fail(MP_ERR_UNSUPPORTED, "plain decode: N=" + std::to_string(p->N) +
                                             " leaves no room for a two-stage ring");
-    const int W = static_cast<int>(std::min<long long>(4, D));
+    const int W = kSumChains / 32;
+    // FP64 is bound by the FP64 units, not by HBM: keep all 4 SM sub-
+    // partitions busy -- with one atom per stage and fewer than 4 stages the
+    // 4 warps share every stage; otherwise every warp owns the same number
+    // of slots (FP32 keeps the deepest ring instead)
+    if (sizeof(T) == 8) {
+        if (D < W && A == 1) cfg->coop = 1;
+        else if (D >= W) D -= D % W;
+    }
     cfg->mode = omp ? 6 : 3;
     cfg->ctas = G;
     cfg->threads = 32 * (1 + W);
@@ -847,6 +927,7 @@ static mp_status plain_launch_t(PlanImpl* p, const T* psi, const T* y, T* x, con
     a.tr_cap = std::max(0, tr_cap);
     a.watchdog_ns = static_cast<unsigned long long>(p->watchdog_ns);
     a.skip_cta = cfg.mode == 1 ? -1 : p->skip_cta;
+    a.coop = cfg.coop;
     if (cfg.mode == 4) {
         a.G = reinterpret_cast<const T*>(p->gram);
         a.ldG = p->ldG;
@@ -862,6 +943,7 @@ static mp_status plain_launch_t(PlanImpl* p, const T* psi, const T* y, T* x, con
         a.h2 = reinterpret_cast<T*>(o.h2);
         a.w = reinterpret_cast<T*>(o.w);
         a.w2 = reinterpret_cast<T*>(o.w2);
+        a.wpart = reinterpret_cast<T*>(o.wpart);
         a.nrm = o.nrm;
         a.xs = reinterpret_cast<T*>(o.xs);
         a.kmax = std::min(stop->max_iters, p->N);
@@ -947,11 +1029,12 @@ static mp_status omp_prepare(PlanImpl* p, int kmax) {
     MP_CUDA_TRY(cudaMalloc(&o.h2, k * sizeof(float)));
     MP_CUDA_TRY(cudaMalloc(&o.w, ld * sizeof(float)));
     MP_CUDA_TRY(cudaMalloc(&o.w2, ld * sizeof(float)));
+    MP_CUDA_TRY(cudaMalloc(&o.wpart, 4 * ld * sizeof(float)));
     MP_CUDA_TRY(cudaMalloc(&o.nrm, G * sizeof(double)));
     MP_CUDA_TRY(cudaMalloc(&o.xs, k * sizeof(float)));
     o.kmax = static_cast<int>(k);
     o.G = static_cast<int>(G);
-    o.bytes = (k * ld + k * (k + 1) / 2 + 5 * k + 2 * ld) * sizeof(float) + G * sizeof(double);
+    o.bytes = (k * ld + k * (k + 1) / 2 + 5 * k + 6 * ld) * sizeof(float) + G * sizeof(double);
     return MP_OK;
 }
 

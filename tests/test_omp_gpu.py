@@ -110,8 +110,10 @@ def test_omp_parity_with_oracle(shape, mode):
     assert out["result"].iters <= K + 2
 
 
-def test_omp_modes_agree_bitwise():
-    prob = W.make_plain(200, 900, 12, seed=8, eps=1e-6, T=500)
+@pytest.mark.parametrize("shape", [(200, 900, 12), (1000, 3001, 40)], ids=["N200", "N1000"])
+def test_omp_modes_agree_bitwise(shape):
+    N, M, K = shape
+    prob = W.make_plain(N, M, K, seed=8, eps=1e-6, T=500)
     outs = []
     for mode in (2, 3):
         with GpuPlan(prob.psi, mode=mode) as pl:

@@ -91,6 +91,25 @@ def test_fp64_modes_agree_bitwise():
         assert np.array_equal(o["energies"], outs[0]["energies"])
 
 
+def test_fp64_cooperative_stream_matches_resident_bitwise():
+    """N = 7500 in FP64 (60 KB atoms): the streaming ring holds 2 stages, so
+    the 4 consumer warps share every stage, each summing one class of
+    segments (the FP64 correlation order is defined by those classes).  The
+    grid-resident shape computes the same sums with one warp per atom: the
+    two must agree bit for bit, and both meet the oracle rule."""
+    prob = W.make_plain(7500, 300, 10, seed=13, eps=1e-10, T=3000)
+    y = prob.y[0].astype(np.float64)
+    outs = []
+    for mode in (2, 3):
+        with plan64(prob.psi, mode) as pl:
+            if mode == 3:
+                assert pl.query(B().MP_Q_PLAIN64_STAGES) < 4
+            outs.append(pl.decode64(y, prob.eps, prob.T))
+    for k in ("atoms", "x", "energies", "r"):
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+    compare_to_oracle(prob.psi, y, prob.eps, prob.T, outs[1], x_tol=X_TOL64, fp64=True)
+
+
 def test_fp64_master_paper_timing_instance():
     """Sec. 4's double-precision workload at its smallest size (M = 1000,
     N = 500, K = 70, Bernoulli Psi drawn in FP64, eps = 1e-7, T = N), from an

@@ -68,12 +68,20 @@ def test_parity_with_oracle(shape, mode):
     assert d["x_rel_err"] <= 1e-4
 
 
-def test_modes_agree_bitwise():
-    prob = W.make_plain(300, 1500, 12, seed=9, eps=1e-5, T=3000)
+@pytest.mark.parametrize("shape", [(300, 1500, 12), (1000, 1200, 20)], ids=["N300", "N1000"])
+def test_modes_agree_bitwise(shape):
+    """Every launch shape computes each correlation in one order and the FP64
+    energy in one order (128 chains, whatever the shape's thread count), so
+    atoms, x~ and the energies agree bit for bit."""
+    N, M, K = shape
+    prob = W.make_plain(N, M, K, seed=9, eps=1e-5, T=3000)
     outs = []
     for mode in MODES:
         with GpuPlan(prob.psi, mode=mode) as pl:
+            if pl.query(B().MP_Q_PLAIN_MODE) != mode:
+                continue
             outs.append(pl.decode(prob.y[0], prob.eps, prob.T))
+    assert len(outs) >= 2
     for o in outs[1:]:
         assert np.array_equal(o["atoms"], outs[0]["atoms"])
         assert np.array_equal(o["x"], outs[0]["x"])
