@@ -409,7 +409,7 @@ def variants_measure(n_sig=4, gram_period=32):
     return out
 
 
-def batched_measure(prec_name, reps=3, n_plain=16, profile=False):
+def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=(256, 1)):
     """Batched low-precision decode of a whole batched workload vs the plain
     FP32 kernel on the same signals (the first ``n_plain`` of them)."""
     import torch
@@ -424,6 +424,11 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False):
     d = torch.from_numpy(prob.psi).cuda()
     plan = B.mp_plan_create(prob.N, prob.M, d.data_ptr(), prec_mask=1 << prec, stream=s)
     del d
+    if profile:
+        # under a profiler the autotuner's timings are distorted: pin the
+        # shape it picks in unprofiled runs
+        B.mp_plan_set_option(plan, B.MP_OPT_BATCH_TILE_N, profile_shape[0])
+        B.mp_plan_set_option(plan, B.MP_OPT_BATCH_CLUSTER, profile_shape[1])
     Y = torch.from_numpy(prob.y).cuda()
     X = torch.empty((prob.B, prob.M), device="cuda")
     stop = (w["eps"], w["T"])
@@ -707,6 +712,9 @@ def main():
                     help="profiling case: one decode capped at this many iterations, then exit")
     ap.add_argument("--profile-batched", choices=["bf16", "fp8"], default=None,
                     help="profiling case: one batched decode of that workload, then exit")
+    ap.add_argument("--profile-shape", default="256,1",
+                    help="GEMM atoms per tile and cluster size for --profile-batched (the autotuner's "
+                         "choice in unprofiled runs)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--served-duration", type=float, default=10.0,
                     help="seconds of Poisson arrivals for the served measurement (0 = skip)")
@@ -735,7 +743,8 @@ def main():
     if args.profile_batched:
         import __graft_entry__
         __graft_entry__.build()
-        print(json.dumps(batched_measure(args.profile_batched, profile=True)))
+        shape = tuple(int(v) for v in args.profile_shape.split(","))
+        print(json.dumps(batched_measure(args.profile_batched, profile=True, profile_shape=shape)))
     elif args.profile:
         run_profile_case(args.profile)
     elif args.impl == "reference":

@@ -197,20 +197,24 @@ __global__ void __launch_bounds__(kSelThreads) select_update_kernel(const SelArg
     const int n4 = a.ldN / 4;
     for (int k = threadIdx.x; k < n4; k += blockDim.x) rs4[k] = rg4[k];
 
-    if (warp == 0) {
-        // merge the sorted per-tile lists: keys (score bits, ~atom) order by
-        // score, then by the smaller atom.  Each lane first keeps the best 8
-        // of its tiles, then 8 rounds of a warp max pop the global best 8.
+    // merge the sorted per-tile lists: keys (score bits, ~atom) order by
+    // score, then by the smaller atom.  Thread t keeps the best 8 of lists
+    // t, t + blockDim, ... (each list is sorted, so a list stops at its
+    // first key that does not enter); every warp pops its best 8 (8 rounds
+    // of a warp max) into shared memory, and warp 0 pops the best 8 of
+    // those.  The result is the set of the 8 largest keys, whatever the split.
+    {
+        __shared__ unsigned long long wtop[kSelThreads / 32][kTop];
         unsigned long long lk[kTop];
 #pragma unroll
         for (int k = 0; k < kTop; ++k) lk[k] = 0ull;
         const uint2* cd = a.cand + static_cast<size_t>(i) * a.n_at * kTop;
-        for (int t = lane; t < a.n_at; t += 32) {
+        for (int t = threadIdx.x; t < a.n_at; t += blockDim.x) {
             for (int k = 0; k < kTop; ++k) {
                 const uint2 c = cd[t * kTop + k];
                 if (c.y >= static_cast<uint32_t>(a.M)) break;
                 const unsigned long long key = (static_cast<unsigned long long>(c.x) << 32) | (0xffffffffu - c.y);
-                if (key <= lk[kTop - 1]) break;   // the tile's list is sorted: nothing better follows
+                if (key <= lk[kTop - 1]) break;
                 lk[kTop - 1] = key;
 #pragma unroll
                 for (int j = kTop - 1; j > 0; --j) {
@@ -229,7 +233,21 @@ __global__ void __launch_bounds__(kSelThreads) select_update_kernel(const SelArg
                 for (int j = 0; j < kTop - 1; ++j) lk[j] = lk[j + 1];
                 lk[kTop - 1] = 0ull;
             }
-            if (lane == 0) top[round] = m ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(m)) : -1;
+            if (lane == 0) wtop[warp][round] = m;
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int k = 0; k < kTop; ++k) lk[k] = lane < kSelThreads / 32 ? wtop[lane][k] : 0ull;
+            for (int round = 0; round < kTop; ++round) {
+                const unsigned long long m = warp_max_u64(lk[0]);
+                if (m != 0ull && lk[0] == m) {
+#pragma unroll
+                    for (int j = 0; j < kTop - 1; ++j) lk[j] = lk[j + 1];
+                    lk[kTop - 1] = 0ull;
+                }
+                if (lane == 0) top[round] = m ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(m)) : -1;
+            }
         }
     }
     __syncthreads();

@@ -21,6 +21,39 @@
 
 namespace mpgb {
 
+// ---------------------------------------------------------------- top-8
+// Candidate order: larger score first, equal scores by the smaller atom.
+// A non-negative float's bits order like its value, so (score bits, ~atom)
+// packed in 64 bits orders as one unsigned integer.
+MP_DEV unsigned long long score_key(float s, int m) {
+    return (static_cast<unsigned long long>(__float_as_uint(s)) << 32) | (0xffffffffu - static_cast<uint32_t>(m));
+}
+// after it a >= b
+MP_DEV void cex(unsigned long long& a, unsigned long long& b) {
+    const unsigned long long hi = umax64(a, b);
+    b = a ^ b ^ hi;
+    a = hi;
+}
+// descending sort of 8 keys: Batcher's odd-even merge network (19 exchanges)
+MP_DEV void sort8_desc(unsigned long long (&x)[8]) {
+    cex(x[0], x[1]); cex(x[2], x[3]); cex(x[4], x[5]); cex(x[6], x[7]);
+    cex(x[0], x[2]); cex(x[1], x[3]); cex(x[4], x[6]); cex(x[5], x[7]);
+    cex(x[1], x[2]); cex(x[5], x[6]);
+    cex(x[0], x[4]); cex(x[1], x[5]); cex(x[2], x[6]); cex(x[3], x[7]);
+    cex(x[2], x[4]); cex(x[3], x[5]);
+    cex(x[1], x[2]); cex(x[3], x[4]); cex(x[5], x[6]);
+}
+// t <- the best 8 of (t, c), both sorted descending: the elementwise max
+// of t and reversed c is a bitonic sequence holding them; a bitonic merge
+// network (12 exchanges) sorts it
+MP_DEV void merge_top8(unsigned long long (&t)[8], const unsigned long long (&c)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t[i] = umax64(t[i], c[7 - i]);
+    cex(t[0], t[4]); cex(t[1], t[5]); cex(t[2], t[6]); cex(t[3], t[7]);
+    cex(t[0], t[2]); cex(t[1], t[3]); cex(t[4], t[6]); cex(t[5], t[7]);
+    cex(t[0], t[1]); cex(t[2], t[3]); cex(t[4], t[5]); cex(t[6], t[7]);
+}
+
 struct CorrShared {
     uint64_t full[kMaxStages];
     uint64_t empty[kMaxStages];
@@ -195,13 +228,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             }
             tc_fence_after();
             const int row = rt * kBM + quad * 32 + lane;
-            float ts[kTop];
-            int ti[kTop];
+            // the thread's best 8 as packed keys (score bits, ~atom): larger
+            // score first, then the smaller atom; 0 = empty
+            unsigned long long tk[kTop];
 #pragma unroll
-            for (int k = 0; k < kTop; ++k) {
-                ts[k] = -1.f;
-                ti[k] = 0x7fffffff;
-            }
+            for (int k = 0; k < kTop; ++k) tk[k] = 0ull;
             const int m0 = at * TN + grp * cols;
             for (int c = 0; c < cols / 32; ++c) {
                 float v[32];
@@ -215,28 +246,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                         if (m < a.M) a.dump[static_cast<size_t>(row) * a.M + m] = v[j] * (a.fp8 ? a.colscale[m] * rsc : 1.f);
                     }
                 }
+                // branch-free: sort each group of 8 keys, then keep the best
+                // 8 of (list, group) -- every lane does the same work
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int m = m0 + c * 32 + j;
-                    if (m >= a.M) continue;
-                    float s = fabsf(v[j]);
-                    if (a.fp8) s *= __ldg(a.colscale + m);
-                    // strict: an equal score keeps the earlier (smaller) atom
-                    if (s > ts[kTop - 1]) {
-                        ts[kTop - 1] = s;
-                        ti[kTop - 1] = m;
+                for (int h = 0; h < 4; ++h) {
+                    unsigned long long ck[8];
 #pragma unroll
-                        for (int k = kTop - 1; k > 0; --k) {
-                            if (ts[k] > ts[k - 1]) {
-                                const float f = ts[k];
-                                ts[k] = ts[k - 1];
-                                ts[k - 1] = f;
-                                const int ii = ti[k];
-                                ti[k] = ti[k - 1];
-                                ti[k - 1] = ii;
-                            }
-                        }
+                    for (int j = 0; j < 8; ++j) {
+                        const int m = m0 + c * 32 + h * 8 + j;
+                        float sc = fabsf(v[h * 8 + j]);
+                        if (a.fp8) sc *= m < a.M ? __ldg(a.colscale + m) : 0.f;
+                        ck[j] = (m < a.M && sc <= 3.0e38f) ? score_key(sc, m) : 0ull;
                     }
+                    sort8_desc(ck);
+                    merge_top8(tk, ck);
                 }
             }
             tc_fence_before();
@@ -244,7 +267,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             if (row < n_act) {
                 uint2* o = a.cand + ((static_cast<size_t>(row) * a.n_at + at) * kEpiGroups + grp) * kTop;
 #pragma unroll
-                for (int k = 0; k < kTop; ++k) o[k] = make_uint2(__float_as_uint(ts[k]), static_cast<uint32_t>(ti[k]));
+                for (int k = 0; k < kTop; ++k)
+                    o[k] = make_uint2(static_cast<uint32_t>(tk[k] >> 32), 0xffffffffu - static_cast<uint32_t>(tk[k]));
             }
         }
     }

@@ -543,6 +543,15 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
         const Key key = sh->key;
         const int m = key_index(key);
         const T c = key_coef(key);
+        if constexpr (GRAM) {
+            // the next step reads this CTA's slice of row m of G (from HBM):
+            // start pulling it into L2 now, behind the residual update
+            // (16-byte aligned cover of [a0, a0 + na); rows are padded to 4)
+            if (ct == 0 && na > 0) {
+                const int g0 = a0 & ~3, g1 = (a0 + na + 3) & ~3;
+                prefetch_l2(a.G + static_cast<size_t>(m) * a.ldG + g0, static_cast<uint32_t>(g1 - g0) * 4u);
+            }
+        }
 
         // ---- OMP: orthonormalise psi_m against the basis Q of the atoms
         // selected so far (classical Gram-Schmidt, applied twice), then the
