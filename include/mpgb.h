@@ -187,7 +187,9 @@ typedef enum {
     MP_Q_BATCH_CLUSTER = 11,   /* GEMM cluster size of the current batch state       */
     MP_Q_PLAIN64_MODE = 12,    /* mode the next mp_recover_f64 will use (0: none)    */
     MP_Q_PLAIN64_STAGES = 13,  /* its streaming ring depth                           */
-    MP_Q_GRAM_BYTES = 14       /* device bytes of the Gram matrix (0 until built)     */
+    MP_Q_GRAM_BYTES = 14,      /* device bytes of the Gram matrix (0 until built)     */
+    MP_Q_PLAN_N = 15,          /* N of the plan                                      */
+    MP_Q_PLAN_M = 16           /* M of the plan                                      */
 } mp_query;
 
 /* ------------------------------------------------------------------ */
@@ -351,6 +353,64 @@ MPGB_API mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n
  * `stream`.  For tests of the GEMM; the decode paths never write C. */
 MPGB_API mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B, float* C,
                                 void* stream);
+
+/* ------------------------------------------------------------------ */
+/* One decode with the atoms split across ranks (one GPU each)         */
+/* ------------------------------------------------------------------ */
+
+/* Each rank's plan holds a contiguous shard of Psi: global atoms
+ * [atom_offset, atom_offset + M) (its desc->M), all ranks the same N.  Per
+ * MP iteration (Sec. 3, Eqs. 9-12) a rank computes its shard's best
+ * candidate as a record (mp_shard_step_local), the caller all-gathers the
+ * records of all ranks (one exchange of mp_shard_record_bytes per rank, e.g.
+ * NCCL all-gather), and every rank applies the step (mp_shard_step_apply):
+ * the largest |c| wins, ties to the smallest global atom index (Sec. 4);
+ * every rank updates its copy of r with the winner's atom row carried in
+ * the record, the FP64 energy and the stop test; the owning rank adds c to
+ * its x~ slice (Eq. 10).  All ranks apply identical arithmetic, so their r
+ * copies and states stay bit-identical.  The correlation and energy orders
+ * are the persistent kernel's: with one rank (or with the records of
+ * several shards of one dictionary gathered by hand) the atoms, x~ and
+ * energies equal mp_recover's bit for bit.  The calls are stream-ordered
+ * and never synchronise; once the state says stopped, apply is a no-op, so
+ * the caller may check `stopped` every few iterations. */
+typedef struct {
+    double e0;                 /* ||y||^2                                         */
+    double e;                  /* ||r||^2 after the last step (FP64)              */
+    double thr2;               /* eps^2 e0                                        */
+    double audit;              /* max |e_k - (e_{k-1} - c_k^2)| / e0              */
+    int t;                     /* completed steps                                 */
+    int T;                     /* cap                                             */
+    int stopped;               /* nonzero once the loop test of Eq. 8 fails       */
+    int stop_reason;           /* mp_stop_reason                                  */
+    int status;                /* mp_status (MP_ERR_NONFINITE for non-finite y)   */
+    int reserved;
+} mp_shard_state;
+
+/* Bytes of one rank's record: a 16-byte head (key, global atom, c) followed
+ * by the atom's FP32 row (ld floats, the plan's MP_Q_LD_FP32). 0 for NULL. */
+MPGB_API size_t mp_shard_record_bytes(mp_plan_t plan);
+
+/* r <- y (device, N floats; r has room for MP_Q_LD_FP32 floats), x~ slice
+ * (device, M floats) <- 0, and the state (device) for eps, T.
+ * Errors: MP_ERR_INVALID (NULL, bad stop), MP_ERR_CUDA. */
+MPGB_API mp_status mp_shard_init(mp_plan_t plan, const float* y, float* r, float* x, const mp_stop* stop,
+                        mp_shard_state* state, void* stream);
+
+/* This rank's candidate for the current r: correlations of its shard,
+ * the best packed key, and the winner's row, written to `record` (device,
+ * mp_shard_record_bytes, 16-byte aligned).  atom_offset: global index of the
+ * shard's first atom.  Errors: MP_ERR_INVALID, MP_ERR_CUDA. */
+MPGB_API mp_status mp_shard_step_local(mp_plan_t plan, int atom_offset, const float* r, void* record,
+                              void* stream);
+
+/* Apply one step from the n_records gathered records (device, contiguous,
+ * mp_shard_record_bytes each): update r, x~ (owner only), state, and the
+ * optional trace (atoms, coefs by step; energies and residual unused).
+ * Errors: MP_ERR_INVALID, MP_ERR_CUDA. */
+MPGB_API mp_status mp_shard_step_apply(mp_plan_t plan, int atom_offset, const void* records, int n_records,
+                              float* r, float* x, mp_shard_state* state, const mp_trace* trace,
+                              void* stream);
 
 #ifdef __cplusplus
 }

@@ -56,6 +56,8 @@ MP_Q_KERNEL_LAUNCHES = 9
 MP_Q_PLAIN64_MODE = 12
 MP_Q_PLAIN64_STAGES = 13
 MP_Q_GRAM_BYTES = 14
+MP_Q_PLAN_N = 15
+MP_Q_PLAN_M = 16
 
 
 class mp_plan_desc(ctypes.Structure):
@@ -83,6 +85,12 @@ class mp_trace(ctypes.Structure):
 
 class mp_trace_f64(ctypes.Structure):
     _fields_ = mp_trace._fields_
+
+
+class mp_shard_state(ctypes.Structure):
+    _fields_ = [("e0", ctypes.c_double), ("e", ctypes.c_double), ("thr2", ctypes.c_double),
+                ("audit", ctypes.c_double), ("t", ctypes.c_int), ("T", ctypes.c_int), ("stopped", ctypes.c_int),
+                ("stop_reason", ctypes.c_int), ("status", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class mp_server_stats(ctypes.Structure):
@@ -127,6 +135,10 @@ SIGNATURES = {
     "mp_debug_correlations": (_I, [_P, _I, _P, _I, _P, _P]),
     "mp_plan_autotune": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "mp_recover_noalloc": (_I, [_P, _I, _I, _I, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_result), _P]),
+    "mp_shard_record_bytes": (ctypes.c_size_t, [_P]),
+    "mp_shard_init": (_I, [_P, _P, _P, _P, ctypes.POINTER(mp_stop), _P, _P]),
+    "mp_shard_step_local": (_I, [_P, _I, _P, _P, _P]),
+    "mp_shard_step_apply": (_I, [_P, _I, _P, _I, _P, _P, _P, ctypes.POINTER(mp_trace), _P]),
     "mp_server_create": (_I, [ctypes.POINTER(_P), ctypes.c_size_t, _I, _I]),
     "mp_server_add_dictionary": (_I, [_P, _P, _I, ctypes.POINTER(_I)]),
     "mp_server_dictionary_slots": (_I, [_P, _I, ctypes.POINTER(_I)]),
@@ -318,6 +330,32 @@ def mp_debug_correlations(plan, prec, R_ptr, B, C_ptr, stream=None):
 
 
 # ---------------------------------------------------------------- server (include/mpgb_server.h)
+
+def mp_shard_record_bytes(plan):
+    return int(lib().mp_shard_record_bytes(plan))
+
+
+def mp_shard_init(plan, y_ptr, r_ptr, x_ptr, eps, max_iters, state_ptr, stream=None):
+    st = mp_stop(float(eps), int(max_iters), 0)
+    return check(lib().mp_shard_init(plan, ctypes.c_void_p(int(y_ptr)), ctypes.c_void_p(int(r_ptr)),
+                                      ctypes.c_void_p(int(x_ptr)), ctypes.byref(st),
+                                      ctypes.c_void_p(int(state_ptr)), _stream(stream)), "mp_shard_init")
+
+
+def mp_shard_step_local(plan, atom_offset, r_ptr, record_ptr, stream=None):
+    return check(lib().mp_shard_step_local(plan, int(atom_offset), ctypes.c_void_p(int(r_ptr)),
+                                            ctypes.c_void_p(int(record_ptr)), _stream(stream)),
+                 "mp_shard_step_local")
+
+
+def mp_shard_step_apply(plan, atom_offset, records_ptr, n_records, r_ptr, x_ptr, state_ptr, trace=None,
+                        stream=None):
+    return check(lib().mp_shard_step_apply(plan, int(atom_offset), ctypes.c_void_p(int(records_ptr)),
+                                            int(n_records), ctypes.c_void_p(int(r_ptr)),
+                                            ctypes.c_void_p(int(x_ptr)), ctypes.c_void_p(int(state_ptr)),
+                                            ctypes.byref(trace) if trace is not None else None,
+                                            _stream(stream)), "mp_shard_step_apply")
+
 
 def mp_server_create(hbm_budget_bytes, max_slots, max_queue):
     h = ctypes.c_void_p()

@@ -370,6 +370,8 @@ mp_status mp_plan_query(mp_plan_t plan, int what, long long* value) {
         case MP_Q_KERNEL_LAUNCHES: *value = p->launches; return MP_OK;
         case MP_Q_BATCH_TILE_N: *value = p->batch ? p->batch->TN : 0; return MP_OK;
         case MP_Q_BATCH_CLUSTER: *value = p->batch ? p->batch->CL : 0; return MP_OK;
+        case MP_Q_PLAN_N: *value = p->N; return MP_OK;
+        case MP_Q_PLAN_M: *value = p->M; return MP_OK;
         case MP_Q_GRAM_BYTES:
             *value = p->gram ? static_cast<long long>(p->M) * p->ldG * 4 : 0;
             return MP_OK;
