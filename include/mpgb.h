@@ -160,7 +160,7 @@ typedef enum {
                                /* streamed atoms (default), 0 = no hint              */
     MP_OPT_BATCH_AUTOTUNE = 10,/* batched: 1 = time the GEMM tile shapes on the first */
                                /* batch of each size bucket (default), 0 = heuristic */
-    MP_OPT_PLAIN_GRAM = 11     /* FP32 decode with Gram-updated correlations, period */
+    MP_OPT_PLAIN_GRAM = 11,    /* FP32 decode with Gram-updated correlations, period */
                                /* R >= 1 (0 = off, the default).  Not in the paper:   */
                                /* from Eqs. 9 and 11, <r - c psi_k, psi_m> =          */
                                /* c_m - c G[k][m] with G = Psi^T Psi, so step t reads */
@@ -169,6 +169,10 @@ typedef enum {
                                /* bound the drift of the recurrence.  The plan builds */
                                /* G (M x M FP32, 4 M^2 bytes) on the first such       */
                                /* decode.  R = 1 gives the direct decode's bits.      */
+    MP_OPT_PLAIN_L2_KEEP_BYTES = 12 /* grid streaming: bytes of the dictionary (the    */
+                               /* first atoms of every CTA's slice) loaded with an   */
+                               /* evict-last L2 hint so they stay in L2 from one     */
+                               /* iteration to the next; the rest streams evict-first */
 } mp_option;
 
 /* Read-only plan properties for mp_plan_query. */

@@ -41,6 +41,7 @@ MP_OPT_PLAIN_STAGE_BYTES = 8
 MP_OPT_PLAIN_EVICT_FIRST = 9
 MP_OPT_BATCH_AUTOTUNE = 10
 MP_OPT_PLAIN_GRAM = 11
+MP_OPT_PLAIN_L2_KEEP_BYTES = 12
 MP_Q_BATCH_TILE_N = 10
 MP_Q_BATCH_CLUSTER = 11
 

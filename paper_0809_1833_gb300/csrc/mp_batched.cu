@@ -210,8 +210,18 @@ __global__ void __launch_bounds__(kSelThreads) select_update_kernel(const SelArg
         for (int k = 0; k < kTop; ++k) lk[k] = 0ull;
         const uint2* cd = a.cand + static_cast<size_t>(i) * a.n_at * kTop;
         for (int t = threadIdx.x; t < a.n_at; t += blockDim.x) {
+            // the whole list in one go (64 bytes): no chain of dependent loads
+            uint2 lst[kTop];
+            const uint4* l4 = reinterpret_cast<const uint4*>(cd + static_cast<size_t>(t) * kTop);
+#pragma unroll
+            for (int u = 0; u < kTop / 2; ++u) {
+                const uint4 q = l4[u];
+                lst[2 * u] = make_uint2(q.x, q.y);
+                lst[2 * u + 1] = make_uint2(q.z, q.w);
+            }
+#pragma unroll
             for (int k = 0; k < kTop; ++k) {
-                const uint2 c = cd[t * kTop + k];
+                const uint2 c = lst[k];
                 if (c.y >= static_cast<uint32_t>(a.M)) break;
                 const unsigned long long key = (static_cast<unsigned long long>(c.x) << 32) | (0xffffffffu - c.y);
                 if (key <= lk[kTop - 1]) break;

@@ -67,9 +67,9 @@ MP_DEV void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) 
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
-// Same with an L2 evict-first policy (streamed data read once per pass).
-MP_DEV void bulk_g2s_evict_first(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                 uint64_t policy) {
+// Same with an L2 cache policy (createpolicy: evict-first for data read
+// once per pass, evict-last for data kept resident across passes).
+MP_DEV void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t policy) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], "
         "[%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
@@ -84,6 +84,11 @@ MP_DEV void prefetch_l2(const void* src, uint32_t bytes) {
 MP_DEV uint64_t policy_evict_first() {
     uint64_t p;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+MP_DEV uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
 

@@ -145,6 +145,7 @@ struct PlanImpl {
     int prefetch_stages = 0;        // plain streaming: L2 prefetch distance (measured slower; off)
     int stage_bytes = 32768;        // plain streaming: target bytes per ring stage
     int evict_first = 1;            // plain streaming: L2 evict-first hint on the stream
+    long long l2_keep_bytes = 0;    // plain streaming: dictionary bytes kept resident in L2
     int gram_period = 0;            // > 0: Gram-updated correlations, direct every R steps
 
     long long launches = 0;

@@ -91,6 +91,7 @@ struct PlainArgs {
     int stage_atoms, stages;
     int prefetch;          // mode 3: L2 prefetch distance in stages (0 = off)
     int evict_first;       // mode 3: evict-first L2 hint on the streamed atoms
+    int l2_keep_atoms;     // mode 3: the CTA's first atoms loaded evict-last (kept in L2)
     int off_sh, off_data;
     PlainWorkspace* ws;
     Key128* slots;         // FP64 grid exchange: two rings of one key per CTA
@@ -269,6 +270,7 @@ MP_DEV void plain_producer(const PlainArgs<T>& a, PlainShared<T>* sh, T* ring, i
     if (S == 0) return;
     const size_t stage_elems = static_cast<size_t>(A) * ldN;
     const uint64_t pol = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
     volatile int* vdone = &sh->done;
     long long seq = 0;
     while (true) {
@@ -297,9 +299,14 @@ MP_DEV void plain_producer(const PlainArgs<T>& a, PlainShared<T>* sh, T* ring, i
         const int nat = min(A, na - j * A);
         const uint32_t bytes = static_cast<uint32_t>(nat) * ldN * static_cast<uint32_t>(sizeof(T));
         mbar_arrive_expect_tx(&sh->full[slot], bytes);
-        if (a.evict_first)
-            bulk_g2s_evict_first(ring + slot * stage_elems, a.psi + static_cast<size_t>(atom0) * ldN, bytes,
-                                 &sh->full[slot], pol);
+        // the first l2_keep_atoms atoms of the slice stay in L2 from pass to
+        // pass (evict-last); the rest streams through it (evict-first)
+        if (j * A < a.l2_keep_atoms)
+            bulk_g2s_hint(ring + slot * stage_elems, a.psi + static_cast<size_t>(atom0) * ldN, bytes,
+                          &sh->full[slot], pol_keep);
+        else if (a.evict_first)
+            bulk_g2s_hint(ring + slot * stage_elems, a.psi + static_cast<size_t>(atom0) * ldN, bytes,
+                          &sh->full[slot], pol);
         else
             bulk_g2s(ring + slot * stage_elems, a.psi + static_cast<size_t>(atom0) * ldN, bytes, &sh->full[slot]);
         // L2 as a deeper window than the shared-memory ring: pull the stage
@@ -589,6 +596,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
                     const int qt = task / nel, n = n0 + task % nel;
                     const int j0 = (k * qt) / 4, j1 = (k * (qt + 1)) / 4;
                     T acc = T(0);
+#pragma unroll 8
                     for (int j = j0; j < j1; ++j) acc = fmaf(-hp[j], a.Q[static_cast<size_t>(j) * ldN + n], acc);
                     a.wpart[static_cast<size_t>(qt) * ldN + n] = acc;
                 }
@@ -671,20 +679,19 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
             const int own_a0 = own * base + min(own, rem);
             pm_cluster = mapa_shared(smem_u32(data + static_cast<size_t>(m - own_a0) * ldN), static_cast<uint32_t>(own));
         }
+        // the first kSumChains threads update r and run the energy chains
+        // in the same pass (the other threads of 256-thread shapes idle here)
         acc = 0.0;
-        for (int k = ct; k < nvr; k += nct) {
-            V pv;
-            if (CLUSTER) dsmem_ld(pm_cluster + 16u * k, &pv);
-            else if (OMP) pv = scale_vec(pm[k], qscale);
-            else pv = __ldg(pm + k);
-            const V v = sub_scaled(step, pv, rv[k]);
-            rv[k] = v;
-            if (nct == kSumChains) acc = sq_acc(v, acc);   // the energy chains, fused
-        }
-        if (nct != kSumChains) {
-            named_bar_sync(1, nct);
-            if (ct < kSumChains)
-                for (int k = ct; k < nvr; k += kSumChains) acc = sq_acc(rv[k], acc);
+        if (ct < kSumChains) {
+            for (int k = ct; k < nvr; k += kSumChains) {
+                V pv;
+                if (CLUSTER) dsmem_ld(pm_cluster + 16u * k, &pv);
+                else if (OMP) pv = scale_vec(pm[k], qscale);
+                else pv = __ldg(pm + k);
+                const V v = sub_scaled(step, pv, rv[k]);
+                rv[k] = v;
+                acc = sq_acc(v, acc);
+            }
         }
         acc = warp_sum_f64(acc);
         if (lane == 0) sh->wsum[cw] = acc;
@@ -925,6 +932,11 @@ static mp_status plain_launch_t(PlanImpl* p, const T* psi, const T* y, T* x, con
     a.stages = cfg.stages;
     a.prefetch = cfg.mode == 3 ? p->prefetch_stages : 0;
     a.evict_first = p->evict_first;
+    if (cfg.mode == 3 || cfg.mode == 6) {
+        const long long atom_bytes = static_cast<long long>(p->ldN) * sizeof(T);
+        const long long keep = p->l2_keep_bytes / std::max<long long>(1, atom_bytes * cfg.ctas);
+        a.l2_keep_atoms = static_cast<int>(std::min<long long>(keep, (p->M + cfg.ctas - 1) / cfg.ctas));
+    }
     a.off_sh = cfg.off_sh;
     a.off_data = cfg.off_data;
     a.ws = ws;

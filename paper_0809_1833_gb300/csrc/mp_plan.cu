@@ -328,6 +328,10 @@ mp_status mp_plan_set_option(mp_plan_t plan, int option, long long value) {
             if (value < 16 || value > (1 << 20)) return fail(MP_ERR_INVALID, "stage bytes must be 16..1 MiB");
             p->stage_bytes = static_cast<int>(value);
             return MP_OK;
+        case MP_OPT_PLAIN_L2_KEEP_BYTES:
+            if (value < 0) return fail(MP_ERR_INVALID, "L2 keep bytes must be >= 0");
+            p->l2_keep_bytes = value;
+            return MP_OK;
         case MP_OPT_PLAIN_EVICT_FIRST:
             p->evict_first = value ? 1 : 0;
             return MP_OK;
