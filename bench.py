@@ -311,6 +311,7 @@ def run_ours(args):
         line["variants"] = variants_measure()
         # batched low-precision form vs the plain FP32 kernel on the same signals
         line["batched"] = [batched_measure("bf16"), batched_measure("fp8", n_plain=4)]
+        line["fp8_gemm_peak"] = fp8_gemm_peak()
     if rank == 0 and args.served_duration > 0:
         line["served"] = served_measure(args.served_rate, args.served_duration)
     if rank == 0:
@@ -354,7 +355,45 @@ def plain_small_measure(reps=20):
                                 "us_per_iteration": 1e6 * t / r.iters, "recoveries_per_s": 1.0 / t,
                                 "dictionary_GBps_from_smem": 4.0 * prob.N * prob.M * r.iters / t / 1e9}
     B.mp_plan_destroy(plan)
+    # the per-iteration floor: the same launch shape on 16 atoms, so an
+    # iteration is the cluster exchange and the residual update alone
+    tiny = W.gaussian_dictionary(prob.N, 16, seed=1)
+    d = torch.from_numpy(tiny).cuda()
+    plan = B.mp_plan_create(prob.N, 16, d.data_ptr(), stream=s)
+    B.mp_recover(plan, y.data_ptr(), x.data_ptr(), 0.0, 2000, None, True, s)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(5):
+        B.mp_recover(plan, y.data_ptr(), x.data_ptr(), 0.0, 2000, None, False, s)
+    b.record()
+    torch.cuda.synchronize()
+    out["iteration_floor_us"] = 1e3 * a.elapsed_time(b) / (5 * 2000)
+    out["iteration_floor_shape"] = f"mode {B.mp_plan_query(plan, B.MP_Q_PLAIN_MODE)}, 16 atoms, 2000 iterations"
+    B.mp_plan_destroy(plan)
     return out
+
+
+def fp8_gemm_peak(n=8192, reps=20):
+    """Dense E4M3 GEMM throughput of this GPU through the vendor library
+    (torch._scaled_mm, 8192^3, burst): the denominator for the FP8
+    correlations, which the measured peaks do not include."""
+    import torch
+    try:
+        a = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()
+        one = torch.tensor(1.0, device="cuda")
+        for _ in range(3):
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        e1.record()
+        torch.cuda.synchronize()
+        return {"tflops": 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12,
+                "how": f"torch._scaled_mm E4M3 x E4M3 -> BF16, {n}^3, {reps} launches after 3 warm-up"}
+    except Exception as ex:   # the library may not offer FP8 on this build
+        return {"tflops": None, "how": f"unavailable: {type(ex).__name__}: {ex}"[:200]}
 
 
 def variants_measure(n_sig=4, gram_period=32):

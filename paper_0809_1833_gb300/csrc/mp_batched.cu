@@ -35,6 +35,13 @@
 namespace mpgb {
 
 constexpr int kSelThreads = 256;
+// select/update: 4 warps per signal for rows up to 4096 floats (one wave of
+// CTAs at a full batch of short rows), 8 for longer rows.  The FP64 energy
+// always runs in the persistent kernel's order (128 chains over float4s, then
+// warp sums in warp order), so energies and stop decisions equal the plain
+// decode's bit for bit whenever the selected atoms do.
+constexpr int kSumChains = 128;
+constexpr int kSelectWideLd = 4096;
 constexpr int kFixThreads = 1024;
 constexpr int kStepsPerGraph = 16;
 
@@ -129,15 +136,24 @@ __global__ void __launch_bounds__(kSelThreads) admit_kernel(const AdmitArgs a) {
     const int row = *a.n_act + k;
     const float* y = a.Y + static_cast<size_t>(k) * a.N;
     float* r = a.R32 + static_cast<size_t>(slot) * a.ldN;
-    double acc = 0.0;
-    for (int n = threadIdx.x; n < a.ldN; n += blockDim.x) {
-        const float v = n < a.N ? y[n] : 0.f;
-        r[n] = v;
-        acc = fma(static_cast<double>(v), static_cast<double>(v), acc);
-    }
+    for (int n = threadIdx.x; n < a.ldN; n += blockDim.x) r[n] = n < a.N ? y[n] : 0.f;
     if (a.io->X) {
         float* x = a.io->X + static_cast<size_t>(slot) * a.io->ldx;
         for (int m = threadIdx.x; m < a.M; m += blockDim.x) x[m] = 0.f;
+    }
+    __syncthreads();
+    // e0 in the persistent kernel's order: 128 chains over float4s, warp
+    // sums in warp order (threads 128.. contribute zeros)
+    double acc = 0.0;
+    if (threadIdx.x < kSumChains) {
+        const float4* r4 = reinterpret_cast<const float4*>(r);
+        for (int q = threadIdx.x; q < a.ldN / 4; q += kSumChains) {
+            const float4 v = r4[q];
+            acc = fma(static_cast<double>(v.x), static_cast<double>(v.x), acc);
+            acc = fma(static_cast<double>(v.y), static_cast<double>(v.y), acc);
+            acc = fma(static_cast<double>(v.z), static_cast<double>(v.z), acc);
+            acc = fma(static_cast<double>(v.w), static_cast<double>(v.w), acc);
+        }
     }
     const double e0 = block_sum_f64(acc, redd);   // also orders the r writes before the quantise
     const float sc = block_quantize(r, a.ldN, static_cast<char*>(a.Rq) + static_cast<size_t>(row) * a.ldq * (a.fp8 ? 1 : 2),
@@ -181,11 +197,12 @@ struct SelArgs {
     int* fin_list;
 };
 
-__global__ void __launch_bounds__(kSelThreads) select_update_kernel(const SelArgs a) {
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a) {
     extern __shared__ float4 r_sh4[];
     float* r = reinterpret_cast<float*>(r_sh4);
-    __shared__ double redd[kSelThreads / 32];
-    __shared__ float redf[kSelThreads / 32];
+    __shared__ double redd[THREADS / 32];
+    __shared__ float redf[THREADS / 32];
     __shared__ int top[kTop];
     __shared__ unsigned long long rkey[kTop];
     const int i = blockIdx.x;
@@ -204,7 +221,7 @@ __global__ void __launch_bounds__(kSelThreads) select_update_kernel(const SelArg
     // of a warp max) into shared memory, and warp 0 pops the best 8 of
     // those.  The result is the set of the 8 largest keys, whatever the split.
     {
-        __shared__ unsigned long long wtop[kSelThreads / 32][kTop];
+        __shared__ unsigned long long wtop[THREADS / 32][kTop];
         unsigned long long lk[kTop];
 #pragma unroll
         for (int k = 0; k < kTop; ++k) lk[k] = 0ull;
@@ -248,7 +265,7 @@ __global__ void __launch_bounds__(kSelThreads) select_update_kernel(const SelArg
         __syncthreads();
         if (warp == 0) {
 #pragma unroll
-            for (int k = 0; k < kTop; ++k) lk[k] = lane < kSelThreads / 32 ? wtop[lane][k] : 0ull;
+            for (int k = 0; k < kTop; ++k) lk[k] = lane < THREADS / 32 ? wtop[lane][k] : 0ull;
             for (int round = 0; round < kTop; ++round) {
                 const unsigned long long m = warp_max_u64(lk[0]);
                 if (m != 0ull && lk[0] == m) {
@@ -262,11 +279,11 @@ __global__ void __launch_bounds__(kSelThreads) select_update_kernel(const SelArg
     }
     __syncthreads();
     // rescore the candidates in FP32 from the FP32 atoms (Eq. 9)
-    if (warp < kTop) {
-        const int m = top[warp];
+    for (int cnd = warp; cnd < kTop; cnd += THREADS / 32) {
+        const int m = top[cnd];
         unsigned long long key = 0ull;
         if (m >= 0) key = pack_key(dot1(a.psi32 + static_cast<size_t>(m) * a.ldN, r, a.ldN, lane), m);
-        if (lane == 0) rkey[warp] = key;
+        if (lane == 0) rkey[cnd] = key;
     }
     __syncthreads();
     unsigned long long kbest = 0ull;
@@ -285,8 +302,7 @@ __global__ void __launch_bounds__(kSelThreads) select_update_kernel(const SelArg
     // Eq. 11 in FP32, the FP64 energy, and (BF16) the requantised row
     const float4* pm = reinterpret_cast<const float4*>(a.psi32 + static_cast<size_t>(m) * a.ldN);
     char* qrow = static_cast<char*>(a.Rq) + static_cast<size_t>(i) * a.ldq * (a.fp8 ? 1 : 2);
-    double acc = 0.0;
-    for (int k = threadIdx.x; k < n4; k += blockDim.x) {
+    for (int k = threadIdx.x; k < n4; k += THREADS) {
         const float4 p = __ldg(pm + k);
         float4 v = rs4[k];
         v.x = fmaf(-c, p.x, v.x);
@@ -295,16 +311,22 @@ __global__ void __launch_bounds__(kSelThreads) select_update_kernel(const SelArg
         v.w = fmaf(-c, p.w, v.w);
         rg4[k] = v;
         rs4[k] = v;
-        acc = fma(static_cast<double>(v.x), static_cast<double>(v.x), acc);
-        acc = fma(static_cast<double>(v.y), static_cast<double>(v.y), acc);
-        acc = fma(static_cast<double>(v.z), static_cast<double>(v.z), acc);
-        acc = fma(static_cast<double>(v.w), static_cast<double>(v.w), acc);
         if (!a.fp8) {
             __nv_bfloat162* q2 = reinterpret_cast<__nv_bfloat162*>(qrow) + 2 * k;
             q2[0] = __floats2bfloat162_rn(v.x, v.y);
             q2[1] = __floats2bfloat162_rn(v.z, v.w);
         }
     }
+    if (THREADS != kSumChains) __syncthreads();   // the chains read other threads' updates
+    double acc = 0.0;
+    if (threadIdx.x < kSumChains)
+        for (int k = threadIdx.x; k < n4; k += kSumChains) {
+            const float4 v = rs4[k];
+            acc = fma(static_cast<double>(v.x), static_cast<double>(v.x), acc);
+            acc = fma(static_cast<double>(v.y), static_cast<double>(v.y), acc);
+            acc = fma(static_cast<double>(v.z), static_cast<double>(v.z), acc);
+            acc = fma(static_cast<double>(v.w), static_cast<double>(v.w), acc);
+        }
     const double e = block_sum_f64(acc, redd);   // also orders the smem r writes
     if (a.fp8) block_quantize(r, a.ldN, qrow, a.ldq, 1, redf);
     if (threadIdx.x == 0) {
@@ -614,7 +636,10 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
     sa.fp8 = e->prec == MP_PREC_FP8E4M3 ? 1 : 0;
     sa.fin_count = fin_count;
     sa.fin_list = fin_list;
-    select_update_kernel<<<e->cap, kSelThreads, p->ldN * sizeof(float), st>>>(sa);
+    if (p->ldN <= kSelectWideLd)
+        select_update_kernel<kSumChains><<<e->cap, kSumChains, p->ldN * sizeof(float), st>>>(sa);
+    else
+        select_update_kernel<2 * kSumChains><<<e->cap, 2 * kSumChains, p->ldN * sizeof(float), st>>>(sa);
     if ((r = cudaGetLastError()) != cudaSuccess) return r;
     return launch_fixup(p, e, st);
 }
@@ -628,8 +653,12 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
     }
     if (!e->cap_stream) MP_CUDA_TRY(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
     MP_CUDA_TRY(corr_prepare());
-    if (p->ldN * 4 > 48 * 1024)
-        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, p->ldN * 4));
+    if (p->ldN * 4 > 48 * 1024) {
+        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<kSumChains>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         p->ldN * 4));
+        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, p->ldN * 4));
+    }
     MP_CUDA_TRY(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t r = cudaSuccess;
     for (int s = 0; s < steps && r == cudaSuccess; ++s) r = launch_step(p, e, e->cap_stream);

@@ -88,10 +88,12 @@ def run_batched(pl, prec, Y, stops, cap=4096):
     X = T.full((Bn, pl.M), float("nan"), dtype=T.float32, device="cuda")
     atoms = T.full((Bn, cap), -1, dtype=T.int32, device="cuda")
     coefs = T.zeros((Bn, cap), dtype=T.float32, device="cuda")
-    tr = B().make_trace(atoms.data_ptr(), coefs.data_ptr(), 0, cap)
+    en = T.zeros((Bn, cap), dtype=T.float64, device="cuda")
+    tr = B().make_trace(atoms.data_ptr(), coefs.data_ptr(), en.data_ptr(), cap)
     s, res = B().mp_recover_batched(pl.plan, prec, Yd.data_ptr(), X.data_ptr(), Bn, stops, tr, cur_stream(),
                                     raise_on_error=False)
     T.cuda.synchronize()
+    run_batched.energies = en.cpu().numpy()
     return s, res, X.cpu().numpy(), atoms.cpu().numpy(), coefs.cpu().numpy()
 
 
@@ -110,7 +112,9 @@ def test_batched_matches_plain_and_oracle(prec, cluster):
             assert r.status == 0 and r.stop_reason == B().MP_STOP_CONVERGED
             plain = pl.decode(prob.y[b], prob.eps, prob.T)
             if (r.iters == plain["result"].iters and np.array_equal(atoms[b, :r.iters], plain["atoms"])):
+                # same atoms: the same FP32 update and the same FP64 energy order
                 assert np.array_equal(X[b], plain["x"]), b
+                assert np.array_equal(run_batched.energies[b, :r.iters], plain["energies"]), b
                 n_same += 1
             out = dict(result=r, x=X[b], atoms=atoms[b, :r.iters], r=plain["r"])
             if b % 10 == 0:   # full oracle rule on a sample of the signals
