@@ -392,7 +392,7 @@ def fp8_gemm_peak(n=8192, reps=20):
         torch.cuda.synchronize()
         return {"tflops": 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12,
                 "how": f"torch._scaled_mm E4M3 x E4M3 -> BF16, {n}^3, {reps} launches after 3 warm-up"}
-    except Exception as ex:   # the library may not offer FP8 on this build
+    except Exception as ex:   # the installed torch may not offer FP8 GEMMs
         return {"tflops": None, "how": f"unavailable: {type(ex).__name__}: {ex}"[:200]}
 
 

@@ -59,7 +59,7 @@ typedef enum {
     MP_ERR_TIMEOUT = -4,       /* a device-side wait ran past its limit       */
     MP_ERR_NONFINITE = -5,     /* non-finite input (y or Psi)                 */
     MP_ERR_CUDA = -6,          /* a CUDA runtime call failed                  */
-    MP_ERR_UNSUPPORTED = -7,   /* size or precision this build cannot run     */
+    MP_ERR_UNSUPPORTED = -7,   /* size or precision the library cannot run    */
     MP_ERR_NOT_FOUND = -8      /* server: unknown ticket or dictionary        */
 } mp_status;
 
