@@ -85,6 +85,27 @@ MP_DEV int block_scan_flag(int flag, int* red, int* total) {
     return before + in_warp;
 }
 
+// Exclusive block scan of small non-negative counts (their total < 2^31).
+MP_DEV int block_scan_count(int v, int* red, int* total) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) red[warp] = x;
+    __syncthreads();
+    int before = 0, tot = 0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
+        if (w < warp) before += red[w];
+        tot += red[w];
+    }
+    *total = tot;
+    return before + x - v;
+}
+
 // Quantise one residual row (ldN floats) into a GEMM operand row of ldq
 // elements (BF16) or bytes (E4M3, per-row scale max|r| / 448).  Whole block.
 // Returns the row scale (1 for BF16).
@@ -366,6 +387,39 @@ struct FixupArgs {
 __global__ void __launch_bounds__(kFixThreads) fixup_kernel(const FixupArgs a) {
     __shared__ int red[32];
     const int n = *a.n_act + *a.n_extra;
+    if (n <= static_cast<int>(blockDim.x)) {
+        // one row per thread: the flag stays in a register, one count and one
+        // packed scan (holes in the low half, survivors in the high half)
+        // place every move, and the lists live in shared memory
+        __shared__ int sh_holes[kFixThreads], sh_surv[kFixThreads];
+        const int p = threadIdx.x;
+        const int f = p < n ? a.done[p] : 0;
+        int cnt;
+        block_scan_flag(p < n && f, red, &cnt);
+        const int n_new = n - cnt;
+        const int hole = p < n_new && f;
+        const int sv = p >= n_new && p < n && !f;
+        int tot;
+        const int rk = block_scan_count(hole | (sv << 16), red, &tot);
+        if (hole) sh_holes[rk & 0xffff] = p;
+        if (sv) sh_surv[rk >> 16] = p;
+        __syncthreads();
+        const int nh = tot & 0xffff;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int k = warp; k < nh; k += blockDim.x >> 5) {
+            const int ph = sh_holes[k], q = sh_surv[k];
+            if (lane == 0) a.act[ph] = a.act[q];
+            const uint4* src = reinterpret_cast<const uint4*>(a.Rq + static_cast<size_t>(q) * a.ldq_bytes);
+            uint4* dst = reinterpret_cast<uint4*>(a.Rq + static_cast<size_t>(ph) * a.ldq_bytes);
+            for (int o = lane; o < a.ldq_bytes / 16; o += 32) dst[o] = src[o];
+        }
+        if (p < n_new) a.done[p] = 0;
+        if (threadIdx.x == 0) {
+            *a.n_act = n_new;
+            *a.n_extra = 0;
+        }
+        return;
+    }
     int tot = 0, cnt = 0;
     for (int base = 0; base < n; base += blockDim.x) {
         const int p = base + threadIdx.x;
