@@ -34,7 +34,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MP recoveries/s & HBM GB/s vs peak, batched low-prec vs plain FP32; p99 latency"
 WORKLOAD = "plain_fp32_N4096_M16384_K256"
-KERNEL_SOURCES = ["paper_0809_1833_gb300/csrc/mp_plain.cu", "paper_0809_1833_gb300/csrc/mp_device.cuh"]
+KERNEL_SOURCES = ["paper_0809_1833_gb300/csrc/mp_plain.cu", "paper_0809_1833_gb300/csrc/mp_device.cuh",
+                  "paper_0809_1833_gb300/csrc/mp_dot.cuh"]
 
 
 def kernel_hash():

@@ -180,3 +180,20 @@ def test_large_streamed_workload_full_size():
     assert orc.support_score(out["x"], prob.supports[0]) == 1.0
     # FP32 atom sequence equals FP64's over the whole decode at this size
     assert d["first_divergence"] is None
+
+
+def test_cache_policies_do_not_change_results():
+    """The streaming shape's L2 hints (evict-first stream, an evict-last
+    resident part) and its stage size only move bytes differently: the
+    decode is bit for bit the same."""
+    prob = W.make_plain(512, 6000, 20, seed=12, eps=1e-6, T=3000)
+    outs = []
+    for opts in ({}, {B().MP_OPT_PLAIN_EVICT_FIRST: 0}, {B().MP_OPT_PLAIN_L2_KEEP_BYTES: 4 << 20},
+                 {B().MP_OPT_PLAIN_STAGE_BYTES: 8192}):
+        with GpuPlan(prob.psi, mode=3) as pl:
+            for k, v in opts.items():
+                pl.set(k, v)
+            outs.append(pl.decode(prob.y[0], prob.eps, prob.T))
+    for o in outs[1:]:
+        for k in ("atoms", "x", "energies", "r"):
+            assert np.array_equal(o[k], outs[0][k]), k
