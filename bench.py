@@ -55,6 +55,18 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def tensor_peak():
+    """Dense BF16 tensor throughput, TFLOP/s: the measured burst figure,
+    else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("bf16_tflops"):
+            return float(d["bf16_tflops"])
+    return 1900.0
+
+
 def traffic_record():
     """Per-launch DRAM bytes from the committed ncu summary, if it was taken
     on the current kernel source."""
@@ -313,6 +325,14 @@ def run_ours(args):
         # batched low-precision form vs the plain FP32 kernel on the same signals
         line["batched"] = [batched_measure("bf16"), batched_measure("fp8", n_plain=4)]
         line["fp8_gemm_peak"] = fp8_gemm_peak()
+        # tensor-core fraction of the GEMM: BF16 against the measured burst
+        # peak, FP8 against the vendor library's E4M3 rate measured above
+        bf16_peak = tensor_peak()
+        for bm in line["batched"]:
+            g = bm["gemm_full_batch"]
+            pk = bf16_peak if bm["precision"] == "bf16" else line["fp8_gemm_peak"]["tflops"]
+            g["peak_tflops"] = pk
+            g["frac"] = g["tflops"] / pk if pk else None
     if rank == 0 and args.served_duration > 0:
         line["served"] = served_measure(args.served_rate, args.served_duration)
     if rank == 0:
@@ -449,7 +469,7 @@ def variants_measure(n_sig=4, gram_period=32):
     return out
 
 
-def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=(256, 1)):
+def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=(256, 1, 128)):
     """Batched low-precision decode of a whole batched workload vs the plain
     FP32 kernel on the same signals (the first ``n_plain`` of them)."""
     import torch
@@ -469,6 +489,7 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
         # shape it picks in unprofiled runs
         B.mp_plan_set_option(plan, B.MP_OPT_BATCH_TILE_N, profile_shape[0])
         B.mp_plan_set_option(plan, B.MP_OPT_BATCH_CLUSTER, profile_shape[1])
+        B.mp_plan_set_option(plan, B.MP_OPT_BATCH_TILE_M, profile_shape[2] if len(profile_shape) > 2 else 128)
     Y = torch.from_numpy(prob.y).cuda()
     X = torch.empty((prob.B, prob.M), device="cuda")
     stop = (w["eps"], w["T"])
@@ -479,7 +500,8 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
         B.mp_plan_destroy(plan)
         return {"profile_case": name}
     times = []
-    shape = {"atoms_per_tile": B.mp_plan_query(plan, B.MP_Q_BATCH_TILE_N),
+    shape = {"signals_per_tile": B.mp_plan_query(plan, B.MP_Q_BATCH_TILE_M),
+             "atoms_per_tile": B.mp_plan_query(plan, B.MP_Q_BATCH_TILE_N),
              "cluster_ctas": B.mp_plan_query(plan, B.MP_Q_BATCH_CLUSTER), "chosen_by": "autotuner"}
     l0 = B.mp_plan_query(plan, B.MP_Q_KERNEL_LAUNCHES)
     for _ in range(reps):
@@ -505,6 +527,11 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
         torch.cuda.synchronize()
         tp += a.elapsed_time(b) / 1e3
         supp_p.append(orc.support_score(xs.cpu().numpy(), prob.supports[i]))
+    # the correlation GEMM alone at the batch's shape, full batch (first step)
+    g_us = B.mp_debug_time_gemm(plan, prec, prob.B, reps=20)
+    gemm = {"rows": prob.B, "us_per_launch": g_us, "tflops": 2.0 * prob.N * prob.M * prob.B / g_us / 1e6,
+            "how": "mp_debug_time_gemm: GEMM + top-8 epilogue on the full batch of synthetic rows, CUDA events, "
+                   "mean of 20 launches after 2 warm-up"}
     B.mp_plan_destroy(plan)
     flops = 2.0 * prob.N * prob.M * float(iters.sum())
     rec_b, rec_p = prob.B / tb, n_plain / tp
@@ -514,7 +541,8 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
             "support_score_mean": float(np.mean(supp_b)), "support_score_min": float(np.min(supp_b)),
             "plain_support_score_mean": float(np.mean(supp_p)),
             "iterations_total": int(iters.sum()), "iterations_max": int(iters.max()),
-            "effective_tflops": flops / tb / 1e12, "gpu_launches_per_batch": int(launches), "gemm_shape": shape}
+            "effective_tflops": flops / tb / 1e12, "gpu_launches_per_batch": int(launches), "gemm_shape": shape,
+            "gemm_full_batch": gemm}
 
 
 def served_measure(rate=2000.0, duration=10.0, pool=48, seed=0, max_slots=256):
@@ -752,9 +780,9 @@ def main():
                     help="profiling case: one decode capped at this many iterations, then exit")
     ap.add_argument("--profile-batched", choices=["bf16", "fp8"], default=None,
                     help="profiling case: one batched decode of that workload, then exit")
-    ap.add_argument("--profile-shape", default="256,1",
-                    help="GEMM atoms per tile and cluster size for --profile-batched (the autotuner's "
-                         "choice in unprofiled runs)")
+    ap.add_argument("--profile-shape", default="256,1,128",
+                    help="GEMM atoms per tile, cluster size and signals per tile for --profile-batched "
+                         "(the autotuner's choice in unprofiled runs)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--served-duration", type=float, default=10.0,
                     help="seconds of Poisson arrivals for the served measurement (0 = skip)")

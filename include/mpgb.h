@@ -169,10 +169,13 @@ typedef enum {
                                /* bound the drift of the recurrence.  The plan builds */
                                /* G (M x M FP32, 4 M^2 bytes) on the first such       */
                                /* decode.  R = 1 gives the direct decode's bits.      */
-    MP_OPT_PLAIN_L2_KEEP_BYTES = 12 /* grid streaming: bytes of the dictionary (the    */
+    MP_OPT_PLAIN_L2_KEEP_BYTES = 12, /* grid streaming: bytes of the dictionary (the   */
                                /* first atoms of every CTA's slice) loaded with an   */
                                /* evict-last L2 hint so they stay in L2 from one     */
                                /* iteration to the next; the rest streams evict-first */
+    MP_OPT_BATCH_TILE_M = 13   /* batched GEMM: signals per tile, 128 or 256 (two    */
+                               /* 128-row MMAs sharing each staged atom slice; no    */
+                               /* cluster); 0 = autotuned                            */
 } mp_option;
 
 /* Read-only plan properties for mp_plan_query. */
@@ -193,7 +196,8 @@ typedef enum {
     MP_Q_PLAIN64_STAGES = 13,  /* its streaming ring depth                           */
     MP_Q_GRAM_BYTES = 14,      /* device bytes of the Gram matrix (0 until built)     */
     MP_Q_PLAN_N = 15,          /* N of the plan                                      */
-    MP_Q_PLAN_M = 16           /* M of the plan                                      */
+    MP_Q_PLAN_M = 16,          /* M of the plan                                      */
+    MP_Q_BATCH_TILE_M = 17     /* signals per GEMM tile of the current batch state   */
 } mp_query;
 
 /* ------------------------------------------------------------------ */
@@ -340,14 +344,16 @@ MPGB_API mp_status mp_recover_batched(mp_plan_t plan, int prec, const float* Y, 
                              mp_result* host_out, void* stream);
 
 /* Autotuner of the batched correlation GEMM: times each tile shape (128 or
- * 256 atoms per tile; 1, 2 or 4 CTAs sharing an atom tile by multicast) on
- * B synthetic rows at precision `prec`, keeps the fastest for B's size
- * bucket (the next power of two, at least 128) and returns it.  With the
- * default MP_OPT_BATCH_AUTOTUNE = 1, mp_recover_batched runs the same
- * timing on its own first batch of a new bucket.  Options MP_OPT_BATCH_TILE_N
- * / MP_OPT_BATCH_CLUSTER, when set, override the result.  Synchronises the
- * legacy default stream.  tile_n, cluster: may be NULL. */
-MPGB_API mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* cluster);
+ * 256 signals per tile; 128 or 256 atoms per tile; 1, 2 or 4 CTAs sharing
+ * an atom tile by multicast, 128-signal tiles only) on B synthetic rows at
+ * precision `prec`, keeps the fastest for B's size bucket (the next power
+ * of two, at least 128) and returns it.  With the default
+ * MP_OPT_BATCH_AUTOTUNE = 1, mp_recover_batched runs the same timing on its
+ * own first batch of a new bucket.  Options MP_OPT_BATCH_TILE_N /
+ * MP_OPT_BATCH_CLUSTER / MP_OPT_BATCH_TILE_M, when set, override the
+ * result.  Synchronises the legacy default stream.  tile_n, cluster,
+ * tile_m: may be NULL. */
+MPGB_API mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* cluster, int* tile_m);
 
 /* Diagnostic: the tensor-core correlations of the batched path, written out
  * in full.  R (device, B x N floats) is quantised as the batched step does
@@ -357,6 +363,19 @@ MPGB_API mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n
  * `stream`.  For tests of the GEMM; the decode paths never write C. */
 MPGB_API mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B, float* C,
                                 void* stream);
+
+/* Diagnostic: device time of the batched correlation GEMM (GEMM + top-8
+ * epilogue, one launch per step) on B synthetic rows at precision `prec`:
+ * the autotuner's timing routine, mean of `reps` launches after 2 warm-up
+ * launches, written to *us in microseconds per launch.  Tile shape
+ * (tile_m signals x tile_n atoms, `cluster` CTAs): 128 or 256, 128 or 256,
+ * 1, 2 or 4 (cluster 1 when tile_m = 256); all three 0 = the shape
+ * mp_recover_batched would use for B signals (options, else autotuned).
+ * Allocates its own buffers; synchronises the legacy default stream.
+ * Errors: MP_ERR_INVALID (bad shape or argument), MP_ERR_UNSUPPORTED
+ * (precision not built), MP_ERR_CUDA. */
+MPGB_API mp_status mp_debug_time_gemm(mp_plan_t plan, int prec, int B, int tile_m, int tile_n, int cluster,
+                                      int reps, double* us);
 
 /* ------------------------------------------------------------------ */
 /* One decode with the atoms split across ranks (one GPU each)         */

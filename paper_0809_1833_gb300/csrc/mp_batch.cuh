@@ -10,17 +10,18 @@
 
 namespace mpgb {
 
-constexpr int kBM = 128;            // signals per GEMM tile = TMEM lanes = UMMA M
+constexpr int kBM = 128;            // signals per row block = TMEM lanes = UMMA M
 constexpr int kRowBytes = 128;      // bytes of K per operand row per stage (one swizzle row)
 constexpr int kMaxStages = 8;       // GEMM shared-memory pipeline depth, upper bound
 constexpr int kSmemOptin = 232448;  // shared memory a CTA may opt into on sm_103a
 
-// Pipeline depth for a tile width: as many A+B stages as fit, at most 8.
-constexpr int corr_stages(int TN) {
-    return (kSmemOptin - 2048) / (kBM * kRowBytes + TN * kRowBytes) < kMaxStages
-               ? (kSmemOptin - 2048) / (kBM * kRowBytes + TN * kRowBytes)
+// Pipeline depth for a TM x TN tile: as many A+B stages as fit, at most 8.
+constexpr int corr_stages(int TM, int TN) {
+    return (kSmemOptin - 2048) / (TM * kRowBytes + TN * kRowBytes) < kMaxStages
+               ? (kSmemOptin - 2048) / (TM * kRowBytes + TN * kRowBytes)
                : kMaxStages;
 }
+
 constexpr int kTop = 8;             // low-precision candidates kept per signal and list
 constexpr int kEpiGroups = 4;       // epilogue warp groups: each scans 1/4 of a tile's atoms
 constexpr int kGemmThreads = 32 * (2 + 4 * kEpiGroups);   // warp 0 TMA, warp 1 MMA, then epilogue
@@ -29,12 +30,13 @@ constexpr int kGemmThreads = 32 * (2 + 4 * kEpiGroups);   // warp 0 TMA, warp 1 
 struct CorrArgs {
     const int* n_act;       // active rows this step (rows 0..n_act-1 of the A operand)
     int TN;                 // atoms per tile (128 or 256)
+    int RM;                 // 128-row blocks per tile (1 or 2; 1 when clustered)
     int n_at;               // atom tiles
     int M;
     int nk;                 // K blocks of 128 bytes
     int fp8;
     int tmem_cols;
-    int stages;             // pipeline depth, corr_stages(TN)
+    int stages;             // pipeline depth, corr_stages(128 * RM, TN)
     const float* colscale;  // FP8 per-atom scale
     uint2* cand;            // [row][n_at * kEpiGroups][8] = (score bits, atom), each list sorted
     unsigned long long watchdog_ns;
@@ -43,14 +45,14 @@ struct CorrArgs {
     const float* rscale;    // diagnostic FP8: per-row scale of the quantised residual
 };
 
-int corr_smem_bytes(int TN);
+int corr_smem_bytes(int TM, int TN);
 cudaError_t corr_prepare();
 int corr_max_clusters(int CL, int TN);
 // Launch with clusters of CL (1, 2 or 4) CTAs along the signal rows; tmB's
-// box is TN/CL atom rows.  max_row_tiles bounds the row tiles any step of
-// this launch can see (it sizes the grid).
-cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CorrArgs& a, int max_row_tiles,
-                             int CL, cudaStream_t st);
+// box is TN/CL atom rows, tmA's 128 signal rows.  max_rows bounds the active
+// rows any step of this launch can see (it sizes the grid).
+cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CorrArgs& a, int max_rows, int CL,
+                             cudaStream_t st);
 
 // ------------------------------------------------------------------ batch engine
 // Per-signal state of a slot.
@@ -78,6 +80,7 @@ struct BatchEngine {
     int cap = 0;            // slots (= GEMM rows available)
     int cap_pad = 0;        // rows of the GEMM operand (multiple of 128)
     int prec = -1;
+    int TM = 128;           // signal rows per GEMM tile
     int TN = 0;
     int CL = 1;             // GEMM cluster size along signal rows
     int n_at = 0;
@@ -114,7 +117,7 @@ struct BatchEngine {
 // Bytes of device memory one slot costs (residual, operand row, candidates,
 // state, an output row of M floats when the engine owns X).
 size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x);
-mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int cap, int tile_n, int cluster);
+mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int cap, const GemmShape& shape);
 void engine_free(BatchEngine* e);
 // Admit n signals: rows Y (device, n x N), into slots `slots_dev` (device,
 // NULL = 0..n-1), with per-signal eps^2 and T already in e->eps2 / e->T.

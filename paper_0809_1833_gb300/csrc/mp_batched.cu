@@ -554,36 +554,46 @@ size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x) {
            sizeof(SlotState) + 6 * sizeof(int) + sizeof(double) + sizeof(float) + (with_x ? sizeof(float) * p->M : 0);
 }
 
-mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_t st, int* tn_out, int* cl_out);
+mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_t st, GemmShape* out);
 
-mp_status batch_shape(PlanImpl* p, int prec, int B, const float* R, cudaStream_t st, int* tile_n, int* cluster) {
+mp_status batch_shape(PlanImpl* p, int prec, int B, const float* R, cudaStream_t st, GemmShape* shape) {
     const int rt = (B + kBM - 1) / kBM;
-    int tn = 256, cl = rt >= 4 ? 4 : (rt >= 2 ? 2 : 1);
-    if (p->batch_autotune && !p->batch_tile_n && !p->batch_cluster) {
-        mp_status s = autotune(p, prec, B, R, st, &tn, &cl);
+    GemmShape g;
+    g.tn = 256;
+    g.cl = rt >= 4 ? 4 : (rt >= 2 ? 2 : 1);
+    if (p->batch_autotune && !p->batch_tile_n && !p->batch_cluster && !p->batch_tile_m) {
+        mp_status s = autotune(p, prec, B, R, st, &g);
         if (s != MP_OK) return s;
     }
-    if (p->batch_tile_n) tn = p->batch_tile_n;
-    if (p->batch_cluster) cl = p->batch_cluster;
-    *tile_n = tn;
-    *cluster = cl;
+    if (p->batch_tile_n) g.tn = p->batch_tile_n;
+    if (p->batch_cluster) g.cl = p->batch_cluster;
+    if (p->batch_tile_m) g.tm = p->batch_tile_m;
+    if (g.tm == 256 && g.cl > 1) {
+        if (p->batch_cluster > 1 && p->batch_tile_m == 256)
+            return fail(MP_ERR_INVALID, "batched GEMM: 256-signal tiles run without clusters");
+        if (p->batch_tile_m == 256) g.cl = 1;
+        else g.tm = 128;
+    }
+    *shape = g;
     return MP_OK;
 }
 
-static mp_status engine_prepare(PlanImpl* p, int prec, int cap, int TN, int CL) {
+static mp_status engine_prepare(PlanImpl* p, int prec, int cap, const GemmShape& g) {
     BatchEngine* e = p->batch;
-    if (e && e->prec == prec && e->cap >= cap && e->TN == TN && e->CL == CL) return MP_OK;
+    if (e && e->prec == prec && e->cap >= cap && e->TM == g.tm && e->TN == g.tn && e->CL == g.cl) return MP_OK;
     if (!e) e = p->batch = new BatchEngine();
-    return engine_alloc(e, p, prec, std::max(cap, e->cap), TN, CL);
+    return engine_alloc(e, p, prec, std::max(cap, e->cap), g);
 }
 
-mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, int TN, int CL) {
+mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const GemmShape& g) {
     engine_free(e);
+    const int TN = g.tn;
     e->cap = newcap;
     e->cap_pad = (newcap + kBM - 1) / kBM * kBM;
     e->prec = prec;
+    e->TM = g.tm;
     e->TN = TN;
-    e->CL = CL;
+    e->CL = g.cl;
     e->n_at = (p->M + TN - 1) / TN;
     const bool fp8 = prec == MP_PREC_FP8E4M3;
     e->ldq = fp8 ? p->ldK8 : p->ldK16;
@@ -638,12 +648,17 @@ static CorrArgs corr_args(PlanImpl* p, BatchEngine* e) {
     std::memset(&ca, 0, sizeof(ca));
     ca.n_act = e->counters;
     ca.TN = e->TN;
+    ca.RM = e->TM / kBM;
+    // two accumulator buffers (the epilogue of one tile overlaps the MMAs of
+    // the next) when they fit in TMEM's 512 columns, else one
+    const int nbuf = (ca.RM == 1 || 2 * ca.RM * e->TN <= 512) ? 2 : 1;
     ca.n_at = e->n_at;
     ca.M = p->M;
     ca.nk = (fp8 ? p->ldK8 : p->ldK16 * 2) / kRowBytes;
     ca.fp8 = fp8 ? 1 : 0;
-    ca.tmem_cols = 2 * e->TN >= 512 ? 512 : (2 * e->TN >= 256 ? 256 : 128);
-    ca.stages = corr_stages(e->TN);
+    const int cols = nbuf * ca.RM * e->TN;   // allocations are powers of two >= 32
+    ca.tmem_cols = cols > 256 ? 512 : (cols > 128 ? 256 : 128);
+    ca.stages = corr_stages(e->TM, e->TN);
     ca.colscale = p->scale8;
     ca.cand = e->cand;
     ca.watchdog_ns = static_cast<unsigned long long>(p->watchdog_ns);
@@ -670,7 +685,7 @@ static cudaError_t launch_fixup(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
 static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
     int* fin_count = e->counters + 2;
     int* fin_list = e->fin_list;
-    cudaError_t r = launch_corr_top8(e->tmA, e->tmB, corr_args(p, e), e->cap_pad / kBM, e->CL, st);
+    cudaError_t r = launch_corr_top8(e->tmA, e->tmB, corr_args(p, e), e->cap_pad, e->CL, st);
     if (r != cudaSuccess) return r;
     SelArgs sa;
     sa.n_act = e->counters;
@@ -783,10 +798,10 @@ cudaError_t engine_admit(PlanImpl* p, BatchEngine* e, const float* Y, int n, con
 
 static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, long long ldx, int B, const mp_stop* stops,
                              int n_stops, const mp_trace* trace, mp_result* out, cudaStream_t st) {
-    int TN = 256, CL = 1;
-    mp_status s = batch_shape(p, prec, B, Y, st, &TN, &CL);
+    GemmShape g;
+    mp_status s = batch_shape(p, prec, B, Y, st, &g);
     if (s != MP_OK) return s;
-    s = engine_prepare(p, prec, B, TN, CL);
+    s = engine_prepare(p, prec, B, g);
     if (s != MP_OK) return s;
     BatchEngine* e = p->batch;
     s = engine_build_graph(p, e, kStepsPerGraph, false, nullptr, nullptr, nullptr, nullptr);
@@ -903,10 +918,10 @@ mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B,
     if (!(p->prec_mask & (1u << prec)))
         return fail(MP_ERR_UNSUPPORTED, "mp_debug_correlations: the plan holds no copy for this precision");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int TN = 256, CL = 1;
-    mp_status s = batch_shape(p, prec, B, R, st, &TN, &CL);
+    GemmShape g;
+    mp_status s = batch_shape(p, prec, B, R, st, &g);
     if (s != MP_OK) return s;
-    s = engine_prepare(p, prec, B, TN, CL);
+    s = engine_prepare(p, prec, B, g);
     if (s != MP_OK) return s;
     BatchEngine* e = p->batch;
     MP_CUDA_TRY(corr_prepare());
@@ -931,7 +946,7 @@ mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B,
     CorrArgs ca = corr_args(p, e);
     ca.dump = C;
     ca.rscale = e->rscale;
-    MP_CUDA_TRY(launch_corr_top8(e->tmA, e->tmB, ca, (B + kBM - 1) / kBM, e->CL, st));
+    MP_CUDA_TRY(launch_corr_top8(e->tmA, e->tmB, ca, B, e->CL, st));
     p->launches += 2;
     MP_CUDA_TRY(cudaMemcpyAsync(e->h_err, e->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaStreamSynchronize(st));
@@ -964,12 +979,14 @@ static int batch_bucket(int B) {
     return b;
 }
 
-// Time the correlation GEMM for B active rows with tile width TN and cluster
-// size CL; returns microseconds per launch (or a negative value on failure).
-static double time_gemm(PlanImpl* p, int prec, int B, int TN, int CL, const float* R, cudaStream_t st) {
+// Time the correlation GEMM for B active rows with tile shape g: mean of
+// `reps` launches after 2 warm-up launches; returns microseconds per launch
+// (or a negative value on failure).
+static double time_gemm(PlanImpl* p, int prec, int B, const GemmShape& g, const float* R, cudaStream_t st,
+                        int reps = 5) {
     BatchEngine e;
     double us = -1.0;
-    if (engine_alloc(&e, p, prec, B, TN, CL) == MP_OK && corr_prepare() == cudaSuccess) {
+    if (engine_alloc(&e, p, prec, B, g) == MP_OK && corr_prepare() == cudaSuccess) {
         for (int b = 0; b < B; ++b) {
             e.h_eps2[b] = 0.0;
             e.h_T[b] = 1;
@@ -990,11 +1007,9 @@ static double time_gemm(PlanImpl* p, int prec, int B, int TN, int CL, const floa
         if (r == cudaSuccess) r = cudaEventCreate(&e0);
         if (r == cudaSuccess) r = cudaEventCreate(&e1);
         const CorrArgs ca = corr_args(p, &e);
-        const int rt = (B + kBM - 1) / kBM;
-        for (int it = 0; it < 2 && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, ca, rt, e.CL, st);
+        for (int it = 0; it < 2 && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, ca, B, e.CL, st);
         if (r == cudaSuccess) r = cudaEventRecord(e0, st);
-        const int reps = 5;
-        for (int it = 0; it < reps && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, ca, rt, e.CL, st);
+        for (int it = 0; it < reps && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, ca, B, e.CL, st);
         if (r == cudaSuccess) r = cudaEventRecord(e1, st);
         if (r == cudaSuccess) r = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -1009,12 +1024,11 @@ static double time_gemm(PlanImpl* p, int prec, int B, int TN, int CL, const floa
     return us;
 }
 
-mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_t st, int* tn_out, int* cl_out) {
+mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_t st, GemmShape* out) {
     const int bucket = batch_bucket(B);
     for (const TuneEntry& t : p->tuned)
         if (t.prec == prec && t.bucket == bucket) {
-            *tn_out = t.tile_n;
-            *cl_out = t.cluster;
+            *out = t.shape;
             return MP_OK;
         }
     float* R = nullptr;
@@ -1025,24 +1039,30 @@ mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_
         p->launches++;
     }
     double best = -1.0;
-    int best_tn = 256, best_cl = 1;
+    GemmShape best_g;
     const int rt = (B + kBM - 1) / kBM;
-    for (int tn : {256, 128}) {
-        for (int cl : {1, 2, 4}) {
-            if (cl > 1 && cl > rt) continue;
-            const double us = time_gemm(p, prec, B, tn, cl, R_dev ? R_dev : R, st);
-            if (us > 0.0 && (best < 0.0 || us < best)) {
-                best = us;
-                best_tn = tn;
-                best_cl = cl;
+    for (int tm : {128, 256}) {
+        if (tm == 256 && rt < 2) continue;      // one row block: the same work as 128
+        for (int tn : {256, 128}) {
+            for (int cl : {1, 2, 4}) {
+                if (cl > 1 && (cl > rt || tm != 128)) continue;
+                GemmShape g;
+                g.tm = tm;
+                g.tn = tn;
+                g.cl = cl;
+                const double us = time_gemm(p, prec, B, g, R_dev ? R_dev : R, st);
+                if (us > 0.0 && (best < 0.0 || us < best)) {
+                    best = us;
+                    best_g = g;
+                }
             }
         }
     }
     if (R) cudaFreeAsync(R, st);
     if (best < 0.0) return fail(MP_ERR_CUDA, "autotune: no tile shape could be timed");
-    p->tuned.push_back(TuneEntry{prec, bucket, best_tn, best_cl, best});
-    *tn_out = best_tn;
-    *cl_out = best_cl;
+    cudaStreamSynchronize(st);
+    p->tuned.push_back(TuneEntry{prec, bucket, best_g, best});
+    *out = best_g;
     return MP_OK;
 }
 
@@ -1050,7 +1070,7 @@ mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_
 
 extern "C" {
 
-mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* cluster) {
+mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* cluster, int* tile_m) {
     clear_error();
     if (!plan || B < 1) return fail(MP_ERR_INVALID, "mp_plan_autotune: bad argument");
     PlanImpl* p = &plan->impl;
@@ -1058,11 +1078,45 @@ mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* cl
         return fail(MP_ERR_INVALID, "mp_plan_autotune: precision must be BF16 or FP8");
     if (!(p->prec_mask & (1u << prec)))
         return fail(MP_ERR_UNSUPPORTED, "mp_plan_autotune: the plan holds no copy for this precision");
-    int tn = 0, cl = 0;
-    mp_status s = autotune(p, prec, B, nullptr, nullptr, &tn, &cl);
+    GemmShape g;
+    mp_status s = autotune(p, prec, B, nullptr, nullptr, &g);
     if (s != MP_OK) return s;
-    if (tile_n) *tile_n = tn;
-    if (cluster) *cluster = cl;
+    if (tile_n) *tile_n = g.tn;
+    if (cluster) *cluster = g.cl;
+    if (tile_m) *tile_m = g.tm;
+    return MP_OK;
+}
+
+mp_status mp_debug_time_gemm(mp_plan_t plan, int prec, int B, int tile_m, int tile_n, int cluster, int reps,
+                             double* us) {
+    clear_error();
+    if (!plan || B < 1 || reps < 1 || !us) return fail(MP_ERR_INVALID, "mp_debug_time_gemm: bad argument");
+    PlanImpl* p = &plan->impl;
+    if (prec != MP_PREC_BF16 && prec != MP_PREC_FP8E4M3)
+        return fail(MP_ERR_INVALID, "mp_debug_time_gemm: precision must be BF16 or FP8");
+    if (!(p->prec_mask & (1u << prec)))
+        return fail(MP_ERR_UNSUPPORTED, "mp_debug_time_gemm: the plan holds no copy for this precision");
+    GemmShape g;
+    if (tile_m || tile_n || cluster) {
+        if ((tile_m != 128 && tile_m != 256) || (tile_n != 128 && tile_n != 256) ||
+            (cluster != 1 && cluster != 2 && cluster != 4) || (tile_m == 256 && cluster != 1))
+            return fail(MP_ERR_INVALID, "mp_debug_time_gemm: bad tile shape");
+        g.tm = tile_m;
+        g.tn = tile_n;
+        g.cl = cluster;
+    } else {
+        mp_status s = batch_shape(p, prec, B, nullptr, nullptr, &g);
+        if (s != MP_OK) return s;
+    }
+    float* R = nullptr;
+    MP_CUDA_TRY(cudaMalloc(&R, sizeof(float) * static_cast<size_t>(B) * p->N));
+    fill_rows_kernel<<<256, 256>>>(R, B, p->N, 12345u);
+    p->launches++;
+    cudaError_t r = cudaGetLastError();
+    const double t = r == cudaSuccess ? time_gemm(p, prec, B, g, R, nullptr, reps) : -1.0;
+    cudaFree(R);
+    if (t < 0.0) return fail(MP_ERR_CUDA, "mp_debug_time_gemm: the GEMM could not be timed");
+    *us = t;
     return MP_OK;
 }
 

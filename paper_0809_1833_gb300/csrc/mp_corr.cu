@@ -5,7 +5,10 @@
 // largest |c| of each atom tile kept in registers and written out, so the
 // correlation matrix itself is never stored.
 //
-// Operand reuse: a cluster of CL CTAs takes CL consecutive 128-signal row
+// Operand reuse, within a CTA: a tile of 256 signal rows is two 128-row
+// MMAs per K slice reading the same staged atom slice, so each atom byte
+// brought into the SM feeds 256 rows (and each signal byte TN atoms).
+// Across CTAs: a cluster of CL CTAs takes CL consecutive 128-signal row
 // tiles of one atom tile.  Each CTA loads its own rows of R, but only 1/CL of
 // the atom tile, and multicasts that slice to every CTA of the cluster; a
 // stage is refilled only after all CL CTAs released it (their MMA commits are
@@ -23,19 +26,27 @@ namespace mpgb {
 
 // ---------------------------------------------------------------- top-8
 // Candidate order: larger score first, equal scores by the smaller atom.
-// A non-negative float's bits order like its value, so (score bits, ~atom)
-// packed in 64 bits orders as one unsigned integer.
-MP_DEV unsigned long long score_key(float s, int m) {
-    return (static_cast<unsigned long long>(__float_as_uint(s)) << 32) | (0xffffffffu - static_cast<uint32_t>(m));
+// A non-negative float's bits order like its value, so one 32-bit key
+// holds the score's top 24 bits (sign, exponent, 15 mantissa bits: far
+// finer than the BF16 / FP8 products' own rounding) and, in the low byte,
+// 255 - the atom's column in the tile, plus 0x100 so that no candidate's
+// key is 0 (0 = empty).  Keys order as unsigned integers; a compare-
+// exchange is one max and one min.  The candidates only pick which 8
+// atoms are rescored in FP32, so the truncation never decides a selection
+// by itself.
+MP_DEV uint32_t score_key(float s, int col) {
+    return ((__float_as_uint(s) | 0xffu) - static_cast<uint32_t>(col)) + 0x100u;
 }
+MP_DEV uint32_t key_score_bits(uint32_t k) { return (k - 0x100u) & 0xffffff00u; }
+MP_DEV int key_col(uint32_t k) { return 255 - static_cast<int>(k & 0xffu); }
 // after it a >= b
-MP_DEV void cex(unsigned long long& a, unsigned long long& b) {
-    const unsigned long long hi = umax64(a, b);
-    b = a ^ b ^ hi;
+MP_DEV void cex(uint32_t& a, uint32_t& b) {
+    const uint32_t hi = max(a, b);
+    b = min(a, b);
     a = hi;
 }
 // descending sort of 8 keys: Batcher's odd-even merge network (19 exchanges)
-MP_DEV void sort8_desc(unsigned long long (&x)[8]) {
+MP_DEV void sort8_desc(uint32_t (&x)[8]) {
     cex(x[0], x[1]); cex(x[2], x[3]); cex(x[4], x[5]); cex(x[6], x[7]);
     cex(x[0], x[2]); cex(x[1], x[3]); cex(x[4], x[6]); cex(x[5], x[7]);
     cex(x[1], x[2]); cex(x[5], x[6]);
@@ -46,12 +57,36 @@ MP_DEV void sort8_desc(unsigned long long (&x)[8]) {
 // t <- the best 8 of (t, c), both sorted descending: the elementwise max
 // of t and reversed c is a bitonic sequence holding them; a bitonic merge
 // network (12 exchanges) sorts it
-MP_DEV void merge_top8(unsigned long long (&t)[8], const unsigned long long (&c)[8]) {
+MP_DEV void merge_top8(uint32_t (&t)[8], const uint32_t (&c)[8]) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) t[i] = umax64(t[i], c[7 - i]);
+    for (int i = 0; i < 8; ++i) t[i] = max(t[i], c[7 - i]);
     cex(t[0], t[4]); cex(t[1], t[5]); cex(t[2], t[6]); cex(t[3], t[7]);
     cex(t[0], t[2]); cex(t[1], t[3]); cex(t[4], t[6]); cex(t[5], t[7]);
     cex(t[0], t[1]); cex(t[2], t[3]); cex(t[4], t[5]); cex(t[6], t[7]);
+}
+
+// The MMAs of one 128-byte K slice of a stage: 4 steps of 32 bytes of K
+// (16 BF16 or 32 E4M3 values), each one MMA per row block of the tile, all
+// reading the stage's atom tile.  a0, b0: descriptors of the stage's signal
+// and atom tiles; a step of 32 bytes adds 2 to the start-address field
+// (address >> 4), a row block of 128 rows 1024.  Row block mb accumulates
+// in TMEM columns [mb * TN, (mb + 1) * TN) from d; `first` starts the
+// accumulation (the tile's first slice).
+template <int RM, bool FP8>
+MP_DEV void issue_kblock(uint32_t d, uint64_t a0, uint64_t b0, uint32_t idesc, int nmb, int TN, bool first) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t acc = (first && k == 0) ? 0u : 1u;
+        const uint64_t bd = b0 + static_cast<uint64_t>(2 * k);
+#pragma unroll
+        for (int mb = 0; mb < RM; ++mb) {
+            if (mb >= nmb) break;
+            const uint64_t ad = a0 + static_cast<uint64_t>(2 * k + mb * ((kBM * kRowBytes) >> 4));
+            const uint32_t dm = d + static_cast<uint32_t>(mb * TN);
+            if (FP8) mma_fp8(dm, ad, bd, idesc, acc);
+            else mma_bf16(dm, ad, bd, idesc, acc);
+        }
+    }
 }
 
 struct CorrShared {
@@ -69,7 +104,7 @@ MP_DEV void corr_timeout(int* err, CorrShared* sh) {
     *reinterpret_cast<volatile int*>(&sh->abort) = 1;
 }
 
-template <int CL>
+template <int CL, int RM>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     corr_top8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const CorrArgs a) {
@@ -79,11 +114,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const uint32_t base_u32 = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
     const int TN = a.TN;
-    const uint32_t a_bytes = kBM * kRowBytes;
+    static_assert(RM == 1 || (RM == 2 && CL == 1), "256-row tiles take no cluster");
+    // TMEM accumulator buffers: two unless one tile fills the 512 columns
+    const int nbuf = (RM == 1 || RM * TN * 2 <= 512) ? 2 : 1;
+    const uint32_t a_bytes = kBM * kRowBytes;        // one row block of a stage
+    const uint32_t as_bytes = static_cast<uint32_t>(RM) * a_bytes;
     const uint32_t b_bytes = static_cast<uint32_t>(TN) * kRowBytes;
     const uint32_t slice_bytes = b_bytes / CL;   // this CTA's share of the atom tile
     uint8_t* tilesA = smem;
-    uint8_t* tilesB = smem + a.stages * a_bytes;
+    uint8_t* tilesB = smem + a.stages * as_bytes;
     CorrShared* sh = reinterpret_cast<CorrShared*>(tilesB + a.stages * b_bytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -91,7 +130,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int cid = static_cast<int>(blockIdx.x) / CL;
     const int n_clusters = static_cast<int>(gridDim.x) / CL;
     const int n_act = *a.n_act;
-    const int n_rt = (n_act + kBM - 1) / kBM;
+    const int n_blk = (n_act + kBM - 1) / kBM;     // 128-row blocks holding active rows
+    const int n_rt = (n_blk + RM - 1) / RM;        // row tiles of RM blocks
     const int n_rg = (n_rt + CL - 1) / CL;         // groups of CL row tiles
     const int n_ct = n_rg * a.n_at;                 // cluster tiles
     if (cid >= n_ct) return;                        // uniform across the cluster
@@ -123,16 +163,23 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     if (warp == 0) {
         // ---------------- TMA producer (one thread)
         if (lane == 0) {
+            // ring position: stage s, its use count parity ph, loads issued g
+            // (kept incrementally: a division per K slice would stall this
+            // single thread for hundreds of cycles)
             long long g = 0;
+            int s = 0;
+            uint32_t ph = 0;
             const int kelems = a.fp8 ? kRowBytes : kRowBytes / 2;
             bool stop = false;
             for (int ct = cid; ct < n_ct && !stop; ct += n_clusters) {
                 const int rt = (ct % n_rg) * CL + q, at = ct / n_rg;
+                // row blocks of this tile with active rows (with one block per
+                // tile, a clustered CTA past the last one still loads its
+                // block: its peers need its multicast slice)
+                const int nmb = RM == 1 ? 1 : min(RM, n_blk - rt * RM);
                 for (int kb = 0; kb < a.nk; ++kb) {
-                    const int s = static_cast<int>(g % a.stages);
-                    const long long use = g / a.stages;
                     // all CL CTAs released the stage's previous use
-                    if (use > 0 && !mbar_wait_bounded(&sh->empty[s], static_cast<uint32_t>((use - 1) & 1), lim)) {
+                    if (g >= a.stages && !mbar_wait_bounded(&sh->empty[s], ph ^ 1u, lim)) {
                         corr_timeout(a.err, sh);
                         stop = true;
                         break;
@@ -141,67 +188,80 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                         stop = true;
                         break;
                     }
-                    mbar_arrive_expect_tx(&sh->full[s], a_bytes + b_bytes);
-                    tma_load_2d(tilesA + s * a_bytes, &tmA, kb * kelems, rt * kBM, &sh->full[s]);
+                    mbar_arrive_expect_tx(&sh->full[s], static_cast<uint32_t>(nmb) * a_bytes + b_bytes);
+#pragma unroll
+                    for (int mb = 0; mb < RM; ++mb)
+                        if (mb < nmb)
+                            tma_load_2d(tilesA + s * as_bytes + mb * a_bytes, &tmA, kb * kelems,
+                                        (rt * RM + mb) * kBM, &sh->full[s]);
                     if (CL == 1)
                         tma_load_2d(tilesB + s * b_bytes, &tmB, kb * kelems, at * TN, &sh->full[s]);
                     else
                         tma_load_2d_multicast(tilesB + s * b_bytes + q * slice_bytes, &tmB, kb * kelems,
                                               at * TN + q * (TN / CL), &sh->full[s], all);
                     ++g;
+                    if (++s == a.stages) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                 }
             }
             // before the CTA may exit: its own loads have landed (the only one
             // that can be in flight in stage s is the last one issued to it),
             // and every CTA of the cluster released the stages' last uses, so
             // no peer still writes into this CTA or arrives on its barriers
-            for (int s = 0; s < a.stages && s < g; ++s) {
-                const long long last = g - 1 - ((g - 1 - s) % a.stages);
-                mbar_wait_bounded(&sh->full[s], static_cast<uint32_t>((last / a.stages) & 1), lim);
-                mbar_wait_bounded(&sh->empty[s], static_cast<uint32_t>((last / a.stages) & 1), lim);
+            for (int t = 0; t < a.stages && t < g; ++t) {
+                const long long last = g - 1 - ((g - 1 - t) % a.stages);
+                mbar_wait_bounded(&sh->full[t], static_cast<uint32_t>((last / a.stages) & 1), lim);
+                mbar_wait_bounded(&sh->empty[t], static_cast<uint32_t>((last / a.stages) & 1), lim);
             }
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer (one thread)
         if (lane == 0) {
             const uint32_t idesc = make_idesc(kBM, TN, a.fp8 ? 0u : 1u);
-            long long g = 0;
-            int li = 0;
+            // ring stage s and its phase ph; accumulator buffer buf and its
+            // phase bph (all incremental: no division in the issue loop)
+            int s = 0, buf = 0, li = 0;
+            uint32_t ph = 0, bph = 0;
             bool ok = true;
             for (int ct = cid; ct < n_ct && ok; ct += n_clusters, ++li) {
-                const int buf = li & 1, useb = li >> 1;
-                if (useb > 0 && !mbar_wait_bounded(&sh->tempty[buf], static_cast<uint32_t>((useb - 1) & 1), lim)) {
+                const int rt = (ct % n_rg) * CL + q;
+                const int nmb = RM == 1 ? 1 : min(RM, n_blk - rt * RM);
+                if (li >= nbuf && !mbar_wait_bounded(&sh->tempty[buf], bph ^ 1u, lim)) {
                     corr_timeout(a.err, sh);
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem + static_cast<uint32_t>(buf * TN);
-                for (int kb = 0; kb < a.nk; ++kb, ++g) {
-                    const int s = static_cast<int>(g % a.stages);
-                    if (!mbar_wait_bounded(&sh->full[s], static_cast<uint32_t>((g / a.stages) & 1), lim) ||
-                        *reinterpret_cast<volatile int*>(&sh->abort)) {
+                // row block mb accumulates in columns [mb * TN, (mb + 1) * TN) of the buffer
+                const uint32_t d = tmem + static_cast<uint32_t>(buf * RM * TN);
+                for (int kb = 0; kb < a.nk; ++kb) {
+                    if (!mbar_wait_bounded(&sh->full[s], ph, lim) || *reinterpret_cast<volatile int*>(&sh->abort)) {
                         corr_timeout(a.err, sh);
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = smem_u32(tilesA + s * a_bytes);
-                    const uint32_t sb = smem_u32(tilesB + s * b_bytes);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        // 32 bytes of K per instruction: 16 BF16 or 32 E4M3 values
-                        const uint64_t ad = sw128_kmajor_desc(sa + 32u * k);
-                        const uint64_t bd = sw128_kmajor_desc(sb + 32u * k);
-                        const uint32_t acc = (kb | k) ? 1u : 0u;
-                        if (a.fp8) mma_fp8(d, ad, bd, idesc, acc);
-                        else mma_bf16(d, ad, bd, idesc, acc);
-                    }
+                    // descriptors of the stage's tiles; a step of 32 bytes
+                    // along K adds 2 to the start-address field (address >> 4)
+                    const uint64_t a0 = sw128_kmajor_desc(smem_u32(tilesA + s * as_bytes));
+                    const uint64_t b0 = sw128_kmajor_desc(smem_u32(tilesB + s * b_bytes));
+                    if (a.fp8) issue_kblock<RM, true>(d, a0, b0, idesc, nmb, TN, kb == 0);
+                    else issue_kblock<RM, false>(d, a0, b0, idesc, nmb, TN, kb == 0);
                     // stage reusable once these MMAs finish (in every CTA that
                     // will refill it with a multicast)
                     if (CL == 1) mma_commit(&sh->empty[s]);
                     else mma_commit_multicast(&sh->empty[s], all);
+                    if (++s == a.stages) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                 }
                 if (ok) mma_commit(&sh->tfull[buf]);
+                if (++buf == nbuf) {
+                    buf = 0;
+                    bph ^= 1u;
+                }
             }
             // no MMA may still write TMEM when it is freed: this commit
             // arrives once every MMA issued above has completed
@@ -215,11 +275,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         const int quad = warp & 3;
         const int grp = (warp - 2) >> 2;
         const int cols = TN / kEpiGroups;
-        int li = 0;
-        for (int ct = cid; ct < n_ct; ct += n_clusters, ++li) {
+        int buf = 0;
+        uint32_t bph = 0;
+        for (int ct = cid; ct < n_ct; ct += n_clusters) {
             const int rt = (ct % n_rg) * CL + q, at = ct / n_rg;
-            const int buf = li & 1, useb = li >> 1;
-            bool ok = mbar_wait_bounded(&sh->tfull[buf], static_cast<uint32_t>(useb & 1), lim) &&
+            const int nmb = RM == 1 ? 1 : min(RM, n_blk - rt * RM);
+            bool ok = mbar_wait_bounded(&sh->tfull[buf], bph, lim) &&
                       !*reinterpret_cast<volatile int*>(&sh->abort);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
@@ -227,48 +288,63 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 break;
             }
             tc_fence_after();
-            const int row = rt * kBM + quad * 32 + lane;
-            // the thread's best 8 as packed keys (score bits, ~atom): larger
-            // score first, then the smaller atom; 0 = empty
-            unsigned long long tk[kTop];
 #pragma unroll
-            for (int k = 0; k < kTop; ++k) tk[k] = 0ull;
-            const int m0 = at * TN + grp * cols;
-            for (int c = 0; c < cols / 32; ++c) {
-                float v[32];
-                tmem_ld_32cols(tmem + (static_cast<uint32_t>(quad * 32) << 16) +
-                                   static_cast<uint32_t>(buf * TN + grp * cols + c * 32),
-                               v);
-                if (a.dump && row < n_act) {
-                    const float rsc = a.fp8 ? a.rscale[row] : 1.f;
-                    for (int j = 0; j < 32; ++j) {
-                        const int m = m0 + c * 32 + j;
-                        if (m < a.M) a.dump[static_cast<size_t>(row) * a.M + m] = v[j] * (a.fp8 ? a.colscale[m] * rsc : 1.f);
+            for (int mb = 0; mb < RM; ++mb) {
+                if (mb >= nmb) break;
+                const int row = (rt * RM + mb) * kBM + quad * 32 + lane;
+                // the thread's best 8 as keys (score_key): larger score
+                // first, then the smaller atom; 0 = empty
+                uint32_t tk[kTop];
+#pragma unroll
+                for (int k = 0; k < kTop; ++k) tk[k] = 0u;
+                const int m0 = at * TN + grp * cols;
+                for (int c = 0; c < cols / 32; ++c) {
+                    float v[32];
+                    tmem_ld_32cols(tmem + (static_cast<uint32_t>(quad * 32) << 16) +
+                                       static_cast<uint32_t>((buf * RM + mb) * TN + grp * cols + c * 32),
+                                   v);
+                    if (a.dump && row < n_act) {
+                        const float rsc = a.fp8 ? a.rscale[row] : 1.f;
+                        for (int j = 0; j < 32; ++j) {
+                            const int m = m0 + c * 32 + j;
+                            if (m < a.M)
+                                a.dump[static_cast<size_t>(row) * a.M + m] = v[j] * (a.fp8 ? a.colscale[m] * rsc : 1.f);
+                        }
+                    }
+                    // branch-free: sort each group of 8 keys, then keep the best
+                    // 8 of (list, group) -- every lane does the same work
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        uint32_t ck[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int col = grp * cols + c * 32 + h * 8 + j;   // column in the tile
+                            const int m = m0 + c * 32 + h * 8 + j;
+                            float sc = fabsf(v[h * 8 + j]);
+                            if (a.fp8) sc *= m < a.M ? __ldg(a.colscale + m) : 0.f;
+                            ck[j] = (m < a.M && sc <= 3.0e38f) ? score_key(sc, col) : 0u;
+                        }
+                        sort8_desc(ck);
+                        merge_top8(tk, ck);
                     }
                 }
-                // branch-free: sort each group of 8 keys, then keep the best
-                // 8 of (list, group) -- every lane does the same work
+                if (mb == nmb - 1) {
+                    // the buffer's last columns are in registers: the MMAs may reuse it
+                    tc_fence_before();
+                    mbar_arrive(&sh->tempty[buf]);
+                }
+                if (row < n_act) {
+                    uint2* o = a.cand + ((static_cast<size_t>(row) * a.n_at + at) * kEpiGroups + grp) * kTop;
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    unsigned long long ck[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int m = m0 + c * 32 + h * 8 + j;
-                        float sc = fabsf(v[h * 8 + j]);
-                        if (a.fp8) sc *= m < a.M ? __ldg(a.colscale + m) : 0.f;
-                        ck[j] = (m < a.M && sc <= 3.0e38f) ? score_key(sc, m) : 0ull;
+                    for (int k = 0; k < kTop; ++k) {
+                        const uint32_t m = static_cast<uint32_t>(at * TN + key_col(tk[k]));
+                        o[k] = tk[k] ? make_uint2(key_score_bits(tk[k]), m) : make_uint2(0u, 0xffffffffu);
                     }
-                    sort8_desc(ck);
-                    merge_top8(tk, ck);
                 }
             }
-            tc_fence_before();
-            mbar_arrive(&sh->tempty[buf]);
-            if (row < n_act) {
-                uint2* o = a.cand + ((static_cast<size_t>(row) * a.n_at + at) * kEpiGroups + grp) * kTop;
-#pragma unroll
-                for (int k = 0; k < kTop; ++k)
-                    o[k] = make_uint2(static_cast<uint32_t>(tk[k] >> 32), 0xffffffffu - static_cast<uint32_t>(tk[k]));
+            if (++buf == nbuf) {
+                buf = 0;
+                bph ^= 1u;
             }
         }
     }
@@ -281,23 +357,23 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     if (CL > 1) cluster_sync_all();   // no CTA leaves while a peer may still address it
 }
 
-int corr_smem_bytes(int TN) {
-    return 1024 + corr_stages(TN) * (kBM * kRowBytes + TN * kRowBytes) + static_cast<int>(sizeof(CorrShared));
+int corr_smem_bytes(int TM, int TN) {
+    return 1024 + corr_stages(TM, TN) * (TM * kRowBytes + TN * kRowBytes) + static_cast<int>(sizeof(CorrShared));
 }
 
-template <int CL>
+template <int CL, int RM>
 static cudaError_t set_attrs() {
-    cudaError_t e = cudaFuncSetAttribute(corr_top8_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         std::max(corr_smem_bytes(128), corr_smem_bytes(256)));
-    return e;
+    const int most = std::max(corr_smem_bytes(kBM * RM, 128), corr_smem_bytes(kBM * RM, 256));
+    return cudaFuncSetAttribute(corr_top8_kernel<CL, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
 }
 
 cudaError_t corr_prepare() {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = set_attrs<1>();
-    if (e == cudaSuccess) e = set_attrs<2>();
-    if (e == cudaSuccess) e = set_attrs<4>();
+    cudaError_t e = set_attrs<1, 1>();
+    if (e == cudaSuccess) e = set_attrs<2, 1>();
+    if (e == cudaSuccess) e = set_attrs<4, 1>();
+    if (e == cudaSuccess) e = set_attrs<1, 2>();
     if (e == cudaSuccess) done = true;
     return e;
 }
@@ -315,7 +391,7 @@ int corr_max_clusters(int CL, int TN) {
         cudaLaunchConfig_t lc = {};
         lc.gridDim = dim3(CL);
         lc.blockDim = dim3(kGemmThreads);
-        lc.dynamicSmemBytes = corr_smem_bytes(TN);
+        lc.dynamicSmemBytes = corr_smem_bytes(kBM, TN);
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
         at[0].val.clusterDim.x = CL;
@@ -324,8 +400,8 @@ int corr_max_clusters(int CL, int TN) {
         lc.attrs = at;
         lc.numAttrs = 1;
         int k = 0;
-        cudaError_t e = CL == 2 ? cudaOccupancyMaxActiveClusters(&k, corr_top8_kernel<2>, &lc)
-                                : cudaOccupancyMaxActiveClusters(&k, corr_top8_kernel<4>, &lc);
+        cudaError_t e = CL == 2 ? cudaOccupancyMaxActiveClusters(&k, corr_top8_kernel<2, 1>, &lc)
+                                : cudaOccupancyMaxActiveClusters(&k, corr_top8_kernel<4, 1>, &lc);
         if (e == cudaSuccess && k > 0) n = std::min(n, k);
         cudaGetLastError();
     }
@@ -333,15 +409,20 @@ int corr_max_clusters(int CL, int TN) {
     return n;
 }
 
-cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CorrArgs& a, int max_row_tiles,
-                             int CL, cudaStream_t st) {
+cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CorrArgs& a, int max_rows, int CL,
+                             cudaStream_t st) {
+    const int nbuf = (a.RM == 1 || a.RM * a.TN * 2 <= 512) ? 2 : 1;   // as the kernel computes it
+    if ((CL > 1 && a.RM != 1) || (a.RM != 1 && a.RM != 2) || nbuf * a.RM * a.TN > a.tmem_cols ||
+        a.stages != corr_stages(kBM * a.RM, a.TN))
+        return cudaErrorInvalidValue;
     // enough clusters for the largest tile count this launch can see
-    const int max_ct = ((max_row_tiles + CL - 1) / CL) * a.n_at;
+    const int max_rt = ((max_rows + kBM - 1) / kBM + a.RM - 1) / a.RM;
+    const int max_ct = ((max_rt + CL - 1) / CL) * a.n_at;
     const int clusters = std::max(1, std::min(max_ct, corr_max_clusters(CL, a.TN)));
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(clusters * CL);
     lc.blockDim = dim3(kGemmThreads);
-    lc.dynamicSmemBytes = corr_smem_bytes(a.TN);
+    lc.dynamicSmemBytes = corr_smem_bytes(kBM * a.RM, a.TN);
     lc.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -350,10 +431,11 @@ cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, con
     at[0].val.clusterDim.z = 1;
     lc.attrs = at;
     lc.numAttrs = 1;
+    if (a.RM == 2) return cudaLaunchKernelEx(&lc, corr_top8_kernel<1, 2>, tmA, tmB, a);
     switch (CL) {
-        case 1: return cudaLaunchKernelEx(&lc, corr_top8_kernel<1>, tmA, tmB, a);
-        case 2: return cudaLaunchKernelEx(&lc, corr_top8_kernel<2>, tmA, tmB, a);
-        case 4: return cudaLaunchKernelEx(&lc, corr_top8_kernel<4>, tmA, tmB, a);
+        case 1: return cudaLaunchKernelEx(&lc, corr_top8_kernel<1, 1>, tmA, tmB, a);
+        case 2: return cudaLaunchKernelEx(&lc, corr_top8_kernel<2, 1>, tmA, tmB, a);
+        case 4: return cudaLaunchKernelEx(&lc, corr_top8_kernel<4, 1>, tmA, tmB, a);
     }
     return cudaErrorInvalidValue;
 }

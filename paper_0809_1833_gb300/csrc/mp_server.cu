@@ -277,9 +277,9 @@ mp_status mp_server_add_dictionary(mp_server_t srv, mp_plan_t plan, int prec, in
     d->prec = prec;
     d->cap = cap;
     const int N = p->N, M = p->M;
-    int tn = 256, cl = 1;
-    mp_status st = batch_shape(p, prec, cap, nullptr, nullptr, &tn, &cl);
-    if (st == MP_OK) st = engine_alloc(&d->eng, p, prec, cap, tn, cl);
+    GemmShape g;
+    mp_status st = batch_shape(p, prec, cap, nullptr, nullptr, &g);
+    if (st == MP_OK) st = engine_alloc(&d->eng, p, prec, cap, g);
     cudaError_t e = cudaSuccess;
     if (st == MP_OK) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking);

@@ -44,14 +44,20 @@ def e4m3_rows(a):
     return q.astype(np.float64), s.astype(np.float64)
 
 
-@pytest.mark.parametrize("cluster", [1, 2, 4])
+# (signals per tile, atoms per tile, cluster size)
+TILES = [(128, 256, 1), (128, 256, 2), (128, 256, 4), (128, 128, 1), (256, 256, 1), (256, 128, 1)]
+
+
+@pytest.mark.parametrize("tile", TILES, ids=lambda t: f"TM{t[0]}_TN{t[1]}_CL{t[2]}")
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
 @pytest.mark.parametrize("shape", [(256, 1000, 200), (100, 300, 5), (2048, 1024, 130), (192, 777, 600)],
                          ids=lambda s: f"N{s[0]}_M{s[1]}_B{s[2]}")
-def test_tensor_core_correlations(prec, shape, cluster):
-    """Every cluster size (atom tile shared by TMA multicast across 1, 2 or
-    4 CTAs) gives the exact quantised product, including row tiles beyond
-    the batch and a ragged last atom tile."""
+def test_tensor_core_correlations(prec, shape, tile):
+    """Every tile shape gives the exact quantised product: atom tiles shared
+    by TMA multicast across 1, 2 or 4 CTAs, 256-signal tiles (two MMAs per
+    staged atom slice, one TMEM buffer at 256 atoms) whose second row block
+    is full, partial or absent, row tiles beyond the batch and a ragged last
+    atom tile."""
     T = torch()
     N, M, Bn = shape
     psi = W.gaussian_dictionary(N, M, seed=3)
@@ -59,10 +65,14 @@ def test_tensor_core_correlations(prec, shape, cluster):
     R = rng.standard_normal((Bn, N)).astype(np.float32)
     p = B().MP_PREC_BF16 if prec == "bf16" else B().MP_PREC_FP8E4M3
     with GpuPlan(psi, prec_mask=1 << p) as pl:
-        pl.set(B().MP_OPT_BATCH_CLUSTER, cluster)
+        pl.set(B().MP_OPT_BATCH_TILE_M, tile[0])
+        pl.set(B().MP_OPT_BATCH_TILE_N, tile[1])
+        pl.set(B().MP_OPT_BATCH_CLUSTER, tile[2])
         Rd = T.from_numpy(R).cuda()
         C = T.full((Bn, M), float("nan"), dtype=T.float32, device="cuda")
         B().mp_debug_correlations(pl.plan, p, Rd.data_ptr(), Bn, C.data_ptr(), cur_stream())
+        assert (pl.query(B().MP_Q_BATCH_TILE_M), pl.query(B().MP_Q_BATCH_TILE_N),
+                pl.query(B().MP_Q_BATCH_CLUSTER)) == tile
         C = C.cpu().numpy().astype(np.float64)
     if prec == "bf16":
         A = bf16_round(R).astype(np.float64)
@@ -97,13 +107,14 @@ def run_batched(pl, prec, Y, stops, cap=4096):
     return s, res, X.cpu().numpy(), atoms.cpu().numpy(), coefs.cpu().numpy()
 
 
-@pytest.mark.parametrize("cluster", [1, 4])
+@pytest.mark.parametrize("tile", [(128, 1), (128, 4), (256, 1)], ids=lambda t: f"TM{t[0]}_CL{t[1]}")
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
-def test_batched_matches_plain_and_oracle(prec, cluster):
+def test_batched_matches_plain_and_oracle(prec, tile):
     prob = W.make_batched(256, 1024, 300, 2, 16, seed=5, eps=1e-5, T=3000)
     p = B().MP_PREC_BF16 if prec == "bf16" else B().MP_PREC_FP8E4M3
     with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
-        pl.set(B().MP_OPT_BATCH_CLUSTER, cluster)
+        pl.set(B().MP_OPT_BATCH_TILE_M, tile[0])
+        pl.set(B().MP_OPT_BATCH_CLUSTER, tile[1])
         s, res, X, atoms, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
         assert s == 0
         n_same = 0
@@ -129,17 +140,19 @@ def test_autotuner_picks_a_valid_shape_and_results_do_not_depend_on_it():
     prob = W.make_batched(256, 2048, 260, 2, 12, seed=6, eps=1e-5, T=2000)
     p = B().MP_PREC_BF16
     with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
-        tn, cl = B().mp_plan_autotune(pl.plan, p, prob.B)
-        assert tn in (128, 256) and cl in (1, 2, 4)
-        assert B().mp_plan_autotune(pl.plan, p, prob.B) == (tn, cl)      # cached per size bucket
+        tn, cl, tm = B().mp_plan_autotune(pl.plan, p, prob.B)
+        assert tn in (128, 256) and cl in (1, 2, 4) and tm in (128, 256) and (tm == 128 or cl == 1)
+        assert B().mp_plan_autotune(pl.plan, p, prob.B) == (tn, cl, tm)      # cached per size bucket
         s, res, X, _, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
         assert s == 0
-        assert (pl.query(B().MP_Q_BATCH_TILE_N), pl.query(B().MP_Q_BATCH_CLUSTER)) == (tn, cl)
-        other = (128 if tn == 256 else 256, 1)
+        q = (B().MP_Q_BATCH_TILE_N, B().MP_Q_BATCH_CLUSTER, B().MP_Q_BATCH_TILE_M)
+        assert tuple(pl.query(k) for k in q) == (tn, cl, tm)
+        other = (128 if tn == 256 else 256, 1, 256 if tm == 128 else 128)
         pl.set(B().MP_OPT_BATCH_TILE_N, other[0])
         pl.set(B().MP_OPT_BATCH_CLUSTER, other[1])
+        pl.set(B().MP_OPT_BATCH_TILE_M, other[2])
         s2, res2, X2, _, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
-        assert (pl.query(B().MP_Q_BATCH_TILE_N), pl.query(B().MP_Q_BATCH_CLUSTER)) == other
+        assert tuple(pl.query(k) for k in q) == other
     assert s2 == 0 and np.array_equal(X, X2)
     assert [r.iters for r in res] == [r.iters for r in res2]
 
