@@ -104,61 +104,40 @@ MP_DEV void corr_timeout(int* err, CorrShared* sh) {
     *reinterpret_cast<volatile int*>(&sh->abort) = 1;
 }
 
+// Per-CTA state the three roles share (set up by the kernel).
+struct CorrCtx {
+    uint8_t* tilesA;       // A stages, as_stride bytes apart
+    uint8_t* tilesB;       // B stages
+    CorrShared* sh;
+    uint32_t tmem;
+    uint32_t as_stride;    // bytes of one stage's A region (room for the largest tile)
+    int n_act, n_blk;      // active rows, 128-row blocks holding them
+    int n_rg, n_ct;        // row-tile groups, cluster tiles (for this launch's RM)
+    int cid, n_clusters, q, warp, lane;
+    uint16_t all;          // cluster CTA mask
+    uint64_t lim;          // watchdog, ns
+};
+
+// The producer, MMA and epilogue roles over this CTA's tiles of RM 128-row
+// blocks x TN atoms.
 template <int CL, int RM>
-__global__ void __launch_bounds__(kGemmThreads, 1)
-    corr_top8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     const CorrArgs a) {
-    extern __shared__ uint8_t smem_raw[];
-    // operand tiles need 1024-byte alignment for the 128-byte swizzle atoms
-    // (the same offset in every CTA, as multicast writes the same offsets)
-    const uint32_t base_u32 = smem_u32(smem_raw);
-    uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
-    const int TN = a.TN;
+MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CorrArgs& a, const CorrCtx& x) {
     static_assert(RM == 1 || (RM == 2 && CL == 1), "256-row tiles take no cluster");
+    const int TN = a.TN;
     // TMEM accumulator buffers: two unless one tile fills the 512 columns
     const int nbuf = (RM == 1 || RM * TN * 2 <= 512) ? 2 : 1;
     const uint32_t a_bytes = kBM * kRowBytes;        // one row block of a stage
-    const uint32_t as_bytes = static_cast<uint32_t>(RM) * a_bytes;
+    const uint32_t as_bytes = x.as_stride;
     const uint32_t b_bytes = static_cast<uint32_t>(TN) * kRowBytes;
     const uint32_t slice_bytes = b_bytes / CL;   // this CTA's share of the atom tile
-    uint8_t* tilesA = smem;
-    uint8_t* tilesB = smem + a.stages * as_bytes;
-    CorrShared* sh = reinterpret_cast<CorrShared*>(tilesB + a.stages * b_bytes);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q = CL > 1 ? static_cast<int>(cluster_ctarank()) : 0;     // rank in the cluster
-    const int cid = static_cast<int>(blockIdx.x) / CL;
-    const int n_clusters = static_cast<int>(gridDim.x) / CL;
-    const int n_act = *a.n_act;
-    const int n_blk = (n_act + kBM - 1) / kBM;     // 128-row blocks holding active rows
-    const int n_rt = (n_blk + RM - 1) / RM;        // row tiles of RM blocks
-    const int n_rg = (n_rt + CL - 1) / CL;         // groups of CL row tiles
-    const int n_ct = n_rg * a.n_at;                 // cluster tiles
-    if (cid >= n_ct) return;                        // uniform across the cluster
-    const uint16_t all = static_cast<uint16_t>((1u << CL) - 1u);
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < a.stages; ++s) {
-            mbar_init(&sh->full[s], 1);
-            mbar_init(&sh->empty[s], CL);
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&sh->tfull[b], 1);
-            mbar_init(&sh->tempty[b], 4 * 32 * kEpiGroups);
-        }
-        mbar_init(&sh->drain, 1);
-        sh->abort = 0;
-        fence_mbar_init();
-        tma_prefetch_desc(&tmA);
-        tma_prefetch_desc(&tmB);
-    }
-    if (warp == 1) tmem_alloc(&sh->tmem_base, static_cast<uint32_t>(a.tmem_cols));
-    tc_fence_before();
-    __syncthreads();
-    if (CL > 1) cluster_sync_all();   // every CTA's barriers exist before any multicast
-    tc_fence_after();
-    const uint32_t tmem = sh->tmem_base;
-    const uint64_t lim = a.watchdog_ns;
+    uint8_t* tilesA = x.tilesA;
+    uint8_t* tilesB = x.tilesB;
+    CorrShared* sh = x.sh;
+    const uint32_t tmem = x.tmem;
+    const int n_act = x.n_act, n_blk = x.n_blk, n_rg = x.n_rg, n_ct = x.n_ct;
+    const int cid = x.cid, n_clusters = x.n_clusters, q = x.q, warp = x.warp, lane = x.lane;
+    const uint16_t all = x.all;
+    const uint64_t lim = x.lim;
 
     if (warp == 0) {
         // ---------------- TMA producer (one thread)
@@ -192,12 +171,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 #pragma unroll
                     for (int mb = 0; mb < RM; ++mb)
                         if (mb < nmb)
-                            tma_load_2d(tilesA + s * as_bytes + mb * a_bytes, &tmA, kb * kelems,
+                            tma_load_2d(tilesA + s * as_bytes + mb * a_bytes, tmA, kb * kelems,
                                         (rt * RM + mb) * kBM, &sh->full[s]);
                     if (CL == 1)
-                        tma_load_2d(tilesB + s * b_bytes, &tmB, kb * kelems, at * TN, &sh->full[s]);
+                        tma_load_2d(tilesB + s * b_bytes, tmB, kb * kelems, at * TN, &sh->full[s]);
                     else
-                        tma_load_2d_multicast(tilesB + s * b_bytes + q * slice_bytes, &tmB, kb * kelems,
+                        tma_load_2d_multicast(tilesB + s * b_bytes + q * slice_bytes, tmB, kb * kelems,
                                               at * TN + q * (TN / CL), &sh->full[s], all);
                     ++g;
                     if (++s == a.stages) {
@@ -348,6 +327,73 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             }
         }
     }
+}
+
+// RM = 2: 256-row tiles while the batch has more 128-row tiles than the
+// grid has CTAs, 128-row tiles once it has drained below that (the choice
+// is made per launch from the active row count, the same in every CTA).
+template <int CL, int RM>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    corr_top8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const CorrArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    // operand tiles need 1024-byte alignment for the 128-byte swizzle atoms
+    // (the same offset in every CTA, as multicast writes the same offsets)
+    const uint32_t base_u32 = smem_u32(smem_raw);
+    uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
+    static_assert(RM == 1 || (RM == 2 && CL == 1), "256-row tiles take no cluster");
+    CorrCtx x;
+    x.as_stride = static_cast<uint32_t>(RM) * kBM * kRowBytes;
+    x.tilesA = smem;
+    x.tilesB = smem + a.stages * x.as_stride;
+    CorrShared* sh = reinterpret_cast<CorrShared*>(x.tilesB + a.stages * static_cast<uint32_t>(a.TN) * kRowBytes);
+    x.sh = sh;
+    x.warp = threadIdx.x >> 5;
+    x.lane = threadIdx.x & 31;
+    const int warp = x.warp;
+    x.q = CL > 1 ? static_cast<int>(cluster_ctarank()) : 0;     // rank in the cluster
+    x.cid = static_cast<int>(blockIdx.x) / CL;
+    x.n_clusters = static_cast<int>(gridDim.x) / CL;
+    x.n_act = *a.n_act;
+    x.n_blk = (x.n_act + kBM - 1) / kBM;     // 128-row blocks holding active rows
+    const int rm = (RM == 2 && x.n_blk * a.n_at > static_cast<int>(gridDim.x)) ? 2 : 1;
+    const int n_rt = (x.n_blk + rm - 1) / rm;      // row tiles of rm blocks
+    x.n_rg = (n_rt + CL - 1) / CL;                  // groups of CL row tiles
+    x.n_ct = x.n_rg * a.n_at;                       // cluster tiles
+    if (x.cid >= x.n_ct) return;                    // uniform across the cluster
+    x.all = static_cast<uint16_t>((1u << CL) - 1u);
+    x.lim = a.watchdog_ns;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(&sh->full[s], 1);
+            mbar_init(&sh->empty[s], CL);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sh->tfull[b], 1);
+            mbar_init(&sh->tempty[b], 4 * 32 * kEpiGroups);
+        }
+        mbar_init(&sh->drain, 1);
+        sh->abort = 0;
+        fence_mbar_init();
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    if (warp == 1) tmem_alloc(&sh->tmem_base, static_cast<uint32_t>(a.tmem_cols));
+    tc_fence_before();
+    __syncthreads();
+    if (CL > 1) cluster_sync_all();   // every CTA's barriers exist before any multicast
+    tc_fence_after();
+    x.tmem = sh->tmem_base;
+    const uint32_t tmem = x.tmem;
+
+    if constexpr (RM == 2) {
+        if (rm == 2) corr_roles<CL, 2>(&tmA, &tmB, a, x);
+        else corr_roles<CL, 1>(&tmA, &tmB, a, x);
+    } else {
+        corr_roles<CL, 1>(&tmA, &tmB, a, x);
+    }
+
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
@@ -415,8 +461,10 @@ cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, con
     if ((CL > 1 && a.RM != 1) || (a.RM != 1 && a.RM != 2) || nbuf * a.RM * a.TN > a.tmem_cols ||
         a.stages != corr_stages(kBM * a.RM, a.TN))
         return cudaErrorInvalidValue;
-    // enough clusters for the largest tile count this launch can see
-    const int max_rt = ((max_rows + kBM - 1) / kBM + a.RM - 1) / a.RM;
+    // enough clusters for the largest tile count this launch can see (with
+    // RM = 2 the kernel takes 128-row tiles whenever they fit the grid, so
+    // the grid is sized by those)
+    const int max_rt = (max_rows + kBM - 1) / kBM;
     const int max_ct = ((max_rt + CL - 1) / CL) * a.n_at;
     const int clusters = std::max(1, std::min(max_ct, corr_max_clusters(CL, a.TN)));
     cudaLaunchConfig_t lc = {};

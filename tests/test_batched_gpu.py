@@ -91,6 +91,74 @@ def test_tensor_core_correlations(prec, shape, tile):
     assert np.all(err <= tol), f"max err/tol {np.max(err / tol):.3g}"
 
 
+def n_sms():
+    return torch().cuda.get_device_properties(0).multi_processor_count
+
+
+@pytest.mark.parametrize("tn", [256, 128])
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_tensor_core_correlations_two_block_tiles(prec, tn):
+    """256-signal tiles are taken while the batch has more 128-row tiles
+    than the GPU has SMs: 600 rows x 8192 atoms is past that point, with a
+    last row tile of one block (and, at 128 atoms per tile, CTAs that run
+    two tiles through both accumulator buffers).  Exact quantised product."""
+    T = torch()
+    N, M, Bn = 256, 8192, 600
+    assert -(-Bn // 128) * (M // tn) > n_sms()
+    psi = W.gaussian_dictionary(N, M, seed=4)
+    R = np.random.default_rng(11).standard_normal((Bn, N)).astype(np.float32)
+    p = B().MP_PREC_BF16 if prec == "bf16" else B().MP_PREC_FP8E4M3
+    with GpuPlan(psi, prec_mask=1 << p) as pl:
+        pl.set(B().MP_OPT_BATCH_TILE_M, 256)
+        pl.set(B().MP_OPT_BATCH_TILE_N, tn)
+        pl.set(B().MP_OPT_BATCH_CLUSTER, 1)
+        Rd = T.from_numpy(R).cuda()
+        C = T.full((Bn, M), float("nan"), dtype=T.float32, device="cuda")
+        B().mp_debug_correlations(pl.plan, p, Rd.data_ptr(), Bn, C.data_ptr(), cur_stream())
+        C = C.cpu().numpy().astype(np.float64)
+    if prec == "bf16":
+        A = bf16_round(R).astype(np.float64)
+        P = bf16_round(psi).astype(np.float64)
+        ref, mag = A @ P.T, np.abs(A) @ np.abs(P).T
+    else:
+        qa, sa = e4m3_rows(R)
+        qp, sp = e4m3_rows(psi)
+        ref = (qa @ qp.T) * sa[:, None] * sp[None, :]
+        mag = (np.abs(qa) @ np.abs(qp).T) * sa[:, None] * sp[None, :]
+    tol = (N + 8) * 2.0 ** -24 * mag + 1e-30
+    assert np.all(np.isfinite(C))
+    assert np.all(np.abs(C - ref) <= tol), f"max err/tol {np.max(np.abs(C - ref) / tol):.3g}"
+
+
+def test_batched_decode_switching_tile_rows_equals_128_row_tiles():
+    """A 700-signal decode over 8192 atoms starts on 256-signal tiles and
+    moves to 128-signal tiles as signals finish; the GEMM's products do not
+    depend on the tile, so every signal's atoms, x~ and iteration count
+    equal those of the decode on 128-signal tiles bit for bit."""
+    prob = W.make_batched(256, 8192, 700, 2, 16, seed=8, eps=1e-5, T=3000)
+    assert -(-prob.B // 128) * (8192 // 256) > n_sms()
+    p = B().MP_PREC_BF16
+    out = {}
+    for tm in (256, 128):
+        with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
+            pl.set(B().MP_OPT_BATCH_TILE_M, tm)
+            pl.set(B().MP_OPT_BATCH_TILE_N, 256)
+            pl.set(B().MP_OPT_BATCH_CLUSTER, 1)
+            s, res, X, atoms, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
+            assert s == 0
+            out[tm] = (res, X, atoms)
+            if tm == 256:
+                for b in (0, 350, 699):
+                    r = res[b]
+                    assert r.status == 0 and r.stop_reason == B().MP_STOP_CONVERGED
+                    plain = pl.decode(prob.y[b], prob.eps, prob.T)
+                    o = dict(result=r, x=X[b], atoms=atoms[b, :r.iters], r=plain["r"])
+                    compare_to_oracle(prob.psi, prob.y[b], prob.eps, prob.T, o, check_follow=False)
+    (r2, X2, a2), (r1, X1, a1) = out[256], out[128]
+    assert [r.iters for r in r2] == [r.iters for r in r1]
+    assert np.array_equal(X2, X1) and np.array_equal(a2, a1)
+
+
 def run_batched(pl, prec, Y, stops, cap=4096):
     T = torch()
     Bn, N = Y.shape
