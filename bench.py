@@ -545,6 +545,28 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
             "gemm_full_batch": gemm}
 
 
+def gemm_profile_case(prec_name, shape):
+    """Three launches of the batched workload's correlation GEMM (full batch,
+    synthetic rows) at shape = (atoms per tile, cluster, signals per tile):
+    the case an ncu capture of the GEMM takes (-s 2 -c 1)."""
+    import torch
+    from paper_0809_1833_gb300 import binding as B
+    from paper_0809_1833_gb300 import workloads as W
+    import __graft_entry__
+    __graft_entry__.build()
+    w = W.WORKLOADS[BATCHED[prec_name]]
+    prec = B.MP_PREC_BF16 if prec_name == "bf16" else B.MP_PREC_FP8E4M3
+    psi = W.gaussian_dictionary(w["N"], w["M"], seed=0)
+    d = torch.from_numpy(psi).cuda()
+    plan = B.mp_plan_create(w["N"], w["M"], d.data_ptr(), prec_mask=1 << prec)
+    del d
+    tn, cl, tm = (list(shape) + [128])[:3]
+    us = B.mp_debug_time_gemm(plan, prec, w["B"], (tm, tn, cl), reps=1)
+    B.mp_plan_destroy(plan)
+    return {"profile_case": BATCHED[prec_name], "gemm_shape": [tm, tn, cl], "us": us,
+            "tflops": 2.0 * w["N"] * w["M"] * w["B"] / us / 1e6}
+
+
 def served_measure(rate=2000.0, duration=10.0, pool=48, seed=0, max_slots=256):
     """Poisson arrivals over the four resident dictionaries of the served
     workload; every request is submitted at its arrival time through the
@@ -783,6 +805,9 @@ def main():
     ap.add_argument("--profile-shape", default="256,1,128",
                     help="GEMM atoms per tile, cluster size and signals per tile for --profile-batched "
                          "(the autotuner's choice in unprofiled runs)")
+    ap.add_argument("--profile-gemm", choices=["bf16", "fp8"], default=None,
+                    help="profiling case: the batched workload's correlation GEMM on its full batch of "
+                         "synthetic rows, 3 launches (2 warm-up), at --profile-shape, then exit")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--served-duration", type=float, default=10.0,
                     help="seconds of Poisson arrivals for the served measurement (0 = skip)")
@@ -808,6 +833,10 @@ def main():
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.profile_gemm:
+        shape = tuple(int(v) for v in args.profile_shape.split(","))
+        print(json.dumps(gemm_profile_case(args.profile_gemm, shape)))
+        return
     if args.profile_batched:
         import __graft_entry__
         __graft_entry__.build()

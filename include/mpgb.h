@@ -174,8 +174,9 @@ typedef enum {
                                /* evict-last L2 hint so they stay in L2 from one     */
                                /* iteration to the next; the rest streams evict-first */
     MP_OPT_BATCH_TILE_M = 13   /* batched GEMM: signals per tile, 128 or 256 (two    */
-                               /* 128-row MMAs sharing each staged atom slice; no    */
-                               /* cluster); 0 = autotuned                            */
+                               /* 128-row MMAs sharing each staged atom slice, no    */
+                               /* cluster; taken while the batch has more 128-row    */
+                               /* tiles than the GPU has SMs, 128 after); 0 = auto   */
 } mp_option;
 
 /* Read-only plan properties for mp_plan_query. */
