@@ -15,15 +15,18 @@ constexpr int kRowBytes = 128;      // bytes of K per operand row per stage (one
 constexpr int kMaxStages = 8;       // GEMM shared-memory pipeline depth, upper bound
 constexpr int kSmemOptin = 232448;  // shared memory a CTA may opt into on sm_103a
 
-// Pipeline depth for a TM x TN tile: as many A+B stages as fit, at most 8.
-constexpr int corr_stages(int TM, int TN) {
-    return (kSmemOptin - 2048) / (TM * kRowBytes + TN * kRowBytes) < kMaxStages
-               ? (kSmemOptin - 2048) / (TM * kRowBytes + TN * kRowBytes)
-               : kMaxStages;
-}
-
 constexpr int kTop = 8;             // low-precision candidates kept per signal and list
 constexpr int kEpiGroups = 4;       // epilogue warp groups: each scans 1/4 of a tile's atoms
+// shared memory besides the stages: alignment slack, barriers, and the
+// epilogue's list exchange (3 groups x 8 keys x 128 rows x 4 bytes)
+constexpr int kCorrFixedSmem = 2048 + (kEpiGroups - 1) * kTop * kBM * 4;
+
+// Pipeline depth for a TM x TN tile: as many A+B stages as fit, at most 8.
+constexpr int corr_stages(int TM, int TN) {
+    return (kSmemOptin - kCorrFixedSmem) / (TM * kRowBytes + TN * kRowBytes) < kMaxStages
+               ? (kSmemOptin - kCorrFixedSmem) / (TM * kRowBytes + TN * kRowBytes)
+               : kMaxStages;
+}
 constexpr int kGemmThreads = 32 * (2 + 4 * kEpiGroups);   // warp 0 TMA, warp 1 MMA, then epilogue
 
 // Arguments of the correlation GEMM.
@@ -38,7 +41,7 @@ struct CorrArgs {
     int tmem_cols;
     int stages;             // pipeline depth, corr_stages(128 * RM, TN)
     const float* colscale;  // FP8 per-atom scale
-    uint2* cand;            // [row][n_at * kEpiGroups][8] = (score bits, atom), each list sorted
+    uint2* cand;            // [row][n_at][8] = (score bits, atom), each tile's list sorted
     unsigned long long watchdog_ns;
     int* err;
     float* dump;            // diagnostic: full correlation rows (row * M + m), or NULL

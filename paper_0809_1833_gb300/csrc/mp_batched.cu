@@ -218,6 +218,53 @@ struct SelArgs {
     int* fin_list;
 };
 
+// A candidate entry (score bits, atom) as a key ordering larger scores
+// first, then smaller atoms; 0 for an empty entry (atom >= M).
+MP_DEV unsigned long long cand_key(uint32_t score_bits, uint32_t atom, int M) {
+    return atom < static_cast<uint32_t>(M)
+               ? (static_cast<unsigned long long>(score_bits) << 32) | (0xffffffffu - atom)
+               : 0ull;
+}
+// after it a >= b
+MP_DEV void cex64(unsigned long long& a, unsigned long long& b) {
+    const unsigned long long hi = umax64(a, b);
+    b = a ^ b ^ hi;
+    a = hi;
+}
+// t <- the best 8 of (t, c), both sorted descending: the elementwise max of
+// t and reversed c is a bitonic sequence holding them; a bitonic merge
+// network (12 exchanges) sorts it
+MP_DEV void merge_top8_u64(unsigned long long (&t)[kTop], const unsigned long long (&c)[kTop]) {
+#pragma unroll
+    for (int i = 0; i < kTop; ++i) t[i] = umax64(t[i], c[kTop - 1 - i]);
+    cex64(t[0], t[4]); cex64(t[1], t[5]); cex64(t[2], t[6]); cex64(t[3], t[7]);
+    cex64(t[0], t[2]); cex64(t[1], t[3]); cex64(t[4], t[6]); cex64(t[5], t[7]);
+    cex64(t[0], t[1]); cex64(t[2], t[3]); cex64(t[4], t[5]); cex64(t[6], t[7]);
+}
+// Two FP32 correlations with r at once, each in exactly dot1's order (four
+// chains over the lane's float4s in increasing offset, ((x + y) + (z + w)),
+// then the warp butterfly), so both atoms' loads are in flight together.
+MP_DEV void dot1_pair(const float* __restrict__ p0, const float* __restrict__ p1, const float* __restrict__ r,
+                      int ldN, int lane, float& d0, float& d1) {
+    float ax = 0.f, ay = 0.f, az = 0.f, aw = 0.f, bx = 0.f, by = 0.f, bz = 0.f, bw = 0.f;
+#pragma unroll 4
+    for (int off = lane * 4; off < ldN; off += 128) {
+        const float4 q = *reinterpret_cast<const float4*>(r + off);
+        const float4 v = *reinterpret_cast<const float4*>(p0 + off);
+        const float4 u = *reinterpret_cast<const float4*>(p1 + off);
+        ax = fmaf(v.x, q.x, ax);
+        ay = fmaf(v.y, q.y, ay);
+        az = fmaf(v.z, q.z, az);
+        aw = fmaf(v.w, q.w, aw);
+        bx = fmaf(u.x, q.x, bx);
+        by = fmaf(u.y, q.y, by);
+        bz = fmaf(u.z, q.z, bz);
+        bw = fmaf(u.w, q.w, bw);
+    }
+    d0 = warp_sum_f32((ax + ay) + (az + aw));
+    d1 = warp_sum_f32((bx + by) + (bz + bw));
+}
+
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a) {
     extern __shared__ float4 r_sh4[];
@@ -233,83 +280,88 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
     float4* rs4 = reinterpret_cast<float4*>(r);
     float4* rg4 = reinterpret_cast<float4*>(a.R32 + static_cast<size_t>(slot) * a.ldN);
     const int n4 = a.ldN / 4;
+    SlotState s = a.st[slot];   // loaded now, used after the rescore
     for (int k = threadIdx.x; k < n4; k += blockDim.x) rs4[k] = rg4[k];
 
     // merge the sorted per-tile lists: keys (score bits, ~atom) order by
-    // score, then by the smaller atom.  Thread t keeps the best 8 of lists
-    // t, t + blockDim, ... (each list is sorted, so a list stops at its
-    // first key that does not enter); every warp pops its best 8 (8 rounds
-    // of a warp max) into shared memory, and warp 0 pops the best 8 of
-    // those.  The result is the set of the 8 largest keys, whatever the split.
+    // score, then by the smaller atom.  Thread t folds lists t, t + THREADS,
+    // ... into its sorted best 8 (a bitonic top-8 merge per list); a
+    // butterfly of the same merge gives lane 0 of every warp the warp's best
+    // 8, and warp 0 merges those.  Candidate sets are disjoint at every merge,
+    // so the result is the set of the 8 largest keys, whatever the split.
     {
         __shared__ unsigned long long wtop[THREADS / 32][kTop];
         unsigned long long lk[kTop];
 #pragma unroll
         for (int k = 0; k < kTop; ++k) lk[k] = 0ull;
         const uint2* cd = a.cand + static_cast<size_t>(i) * a.n_at * kTop;
-        for (int t = threadIdx.x; t < a.n_at; t += blockDim.x) {
+        for (int t = threadIdx.x; t < a.n_at; t += THREADS) {
             // the whole list in one go (64 bytes): no chain of dependent loads
-            uint2 lst[kTop];
+            unsigned long long lst[kTop];
             const uint4* l4 = reinterpret_cast<const uint4*>(cd + static_cast<size_t>(t) * kTop);
 #pragma unroll
             for (int u = 0; u < kTop / 2; ++u) {
                 const uint4 q = l4[u];
-                lst[2 * u] = make_uint2(q.x, q.y);
-                lst[2 * u + 1] = make_uint2(q.z, q.w);
+                lst[2 * u] = cand_key(q.x, q.y, a.M);
+                lst[2 * u + 1] = cand_key(q.z, q.w, a.M);
             }
-#pragma unroll
-            for (int k = 0; k < kTop; ++k) {
-                const uint2 c = lst[k];
-                if (c.y >= static_cast<uint32_t>(a.M)) break;
-                const unsigned long long key = (static_cast<unsigned long long>(c.x) << 32) | (0xffffffffu - c.y);
-                if (key <= lk[kTop - 1]) break;
-                lk[kTop - 1] = key;
-#pragma unroll
-                for (int j = kTop - 1; j > 0; --j) {
-                    if (lk[j] > lk[j - 1]) {
-                        const unsigned long long f = lk[j];
-                        lk[j] = lk[j - 1];
-                        lk[j - 1] = f;
-                    }
-                }
-            }
+            merge_top8_u64(lk, lst);
         }
-        for (int round = 0; round < kTop; ++round) {
-            const unsigned long long m = warp_max_u64(lk[0]);
-            if (m != 0ull && lk[0] == m) {
 #pragma unroll
-                for (int j = 0; j < kTop - 1; ++j) lk[j] = lk[j + 1];
-                lk[kTop - 1] = 0ull;
-            }
-            if (lane == 0) wtop[warp][round] = m;
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long other[kTop];
+#pragma unroll
+            for (int k = 0; k < kTop; ++k) other[k] = __shfl_xor_sync(0xffffffffu, lk[k], o);
+            merge_top8_u64(lk, other);
         }
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < kTop; ++k) wtop[warp][k] = lk[k];
         __syncthreads();
         if (warp == 0) {
 #pragma unroll
             for (int k = 0; k < kTop; ++k) lk[k] = lane < THREADS / 32 ? wtop[lane][k] : 0ull;
-            for (int round = 0; round < kTop; ++round) {
-                const unsigned long long m = warp_max_u64(lk[0]);
-                if (m != 0ull && lk[0] == m) {
 #pragma unroll
-                    for (int j = 0; j < kTop - 1; ++j) lk[j] = lk[j + 1];
-                    lk[kTop - 1] = 0ull;
-                }
-                if (lane == 0) top[round] = m ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(m)) : -1;
+            for (int o = 1; o < THREADS / 32; o <<= 1) {
+                unsigned long long other[kTop];
+#pragma unroll
+                for (int k = 0; k < kTop; ++k) other[k] = __shfl_xor_sync(0xffffffffu, lk[k], o);
+                merge_top8_u64(lk, other);
             }
+            if (lane == 0)
+#pragma unroll
+                for (int k = 0; k < kTop; ++k)
+                    top[k] = lk[k] ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(lk[k])) : -1;
         }
     }
     __syncthreads();
-    // rescore the candidates in FP32 from the FP32 atoms (Eq. 9)
-    for (int cnd = warp; cnd < kTop; cnd += THREADS / 32) {
-        const int m = top[cnd];
-        unsigned long long key = 0ull;
-        if (m >= 0) key = pack_key(dot1(a.psi32 + static_cast<size_t>(m) * a.ldN, r, a.ldN, lane), m);
-        if (lane == 0) rkey[cnd] = key;
+    // rescore the candidates in FP32 from the FP32 atoms (Eq. 9), in the
+    // plain kernel's correlation order; a warp takes candidates w and
+    // w + THREADS / 32 together so their loads are in flight at once
+    if constexpr (THREADS / 32 >= kTop) {
+        if (warp < kTop) {
+            const int m0 = top[warp];
+            unsigned long long key = 0ull;
+            if (m0 >= 0) key = pack_key(dot1(a.psi32 + static_cast<size_t>(m0) * a.ldN, r, a.ldN, lane), m0);
+            if (lane == 0) rkey[warp] = key;
+        }
+    } else
+    for (int cnd = warp; cnd < kTop; cnd += 2 * (THREADS / 32)) {
+        const int c2 = cnd + THREADS / 32;
+        const int m0 = top[cnd];
+        const int m1 = c2 < kTop ? top[c2] : -1;
+        const float* p0 = a.psi32 + static_cast<size_t>(m0 < 0 ? 0 : m0) * a.ldN;
+        const float* p1 = m1 < 0 ? p0 : a.psi32 + static_cast<size_t>(m1) * a.ldN;
+        float d0, d1;
+        dot1_pair(p0, p1, r, a.ldN, lane, d0, d1);
+        if (lane == 0) {
+            rkey[cnd] = m0 >= 0 ? pack_key(d0, m0) : 0ull;
+            if (c2 < kTop) rkey[c2] = m1 >= 0 ? pack_key(d1, m1) : 0ull;
+        }
     }
     __syncthreads();
     unsigned long long kbest = 0ull;
     for (int w = 0; w < kTop; ++w) kbest = umax64(kbest, rkey[w]);
-    SlotState s = a.st[slot];
     if (kbest == 0ull) {   // no candidate: nothing can be selected
         if (threadIdx.x == 0) {
             s.status = MP_ERR_INVALID;
@@ -320,6 +372,13 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
     }
     const int m = key_index(kbest);
     const float c = key_coef(kbest);
+    // thread 0 updates x~[m] at the end: fetch the old value now
+    BatchIO io;
+    float xm = 0.f;
+    if (threadIdx.x == 0) {
+        io = *a.io;
+        xm = io.X[static_cast<size_t>(slot) * io.ldx + m];
+    }
     // Eq. 11 in FP32, the FP64 energy, and (BF16) the requantised row
     const float4* pm = reinterpret_cast<const float4*>(a.psi32 + static_cast<size_t>(m) * a.ldN);
     char* qrow = static_cast<char*>(a.Rq) + static_cast<size_t>(i) * a.ldq * (a.fp8 ? 1 : 2);
@@ -351,8 +410,7 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
     const double e = block_sum_f64(acc, redd);   // also orders the smem r writes
     if (a.fp8) block_quantize(r, a.ldN, qrow, a.ldq, 1, redf);
     if (threadIdx.x == 0) {
-        const BatchIO& io = *a.io;
-        io.X[static_cast<size_t>(slot) * io.ldx + m] += c;   // Eq. 10
+        io.X[static_cast<size_t>(slot) * io.ldx + m] = xm + c;   // Eq. 10
         if (io.tr_atoms && s.t < io.tr_cap) io.tr_atoms[static_cast<size_t>(slot) * io.tr_cap + s.t] = m;
         if (io.tr_coefs && s.t < io.tr_cap) io.tr_coefs[static_cast<size_t>(slot) * io.tr_cap + s.t] = c;
         if (io.tr_energy && s.t < io.tr_cap) io.tr_energy[static_cast<size_t>(slot) * io.tr_cap + s.t] = e;
@@ -550,7 +608,7 @@ size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x) {
     const bool fp8 = prec == MP_PREC_FP8E4M3;
     const size_t TN = 128;   // the narrowest tile the shape choice may pick (most candidate lists)
     const size_t n_at = (p->M + TN - 1) / TN;
-    return sizeof(float) * p->ldN + (fp8 ? p->ldK8 : 2 * p->ldK16) + sizeof(uint2) * n_at * kEpiGroups * kTop +
+    return sizeof(float) * p->ldN + (fp8 ? p->ldK8 : 2 * p->ldK16) + sizeof(uint2) * n_at * kTop +
            sizeof(SlotState) + 6 * sizeof(int) + sizeof(double) + sizeof(float) + (with_x ? sizeof(float) * p->M : 0);
 }
 
@@ -613,7 +671,7 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     A(&e->done, sizeof(int) * C);
     A(&e->holes, sizeof(int) * C);
     A(&e->surv, sizeof(int) * C);
-    A(&e->cand, sizeof(uint2) * C * e->n_at * kEpiGroups * kTop);
+    A(&e->cand, sizeof(uint2) * C * e->n_at * kTop);
     A(&e->eps2, sizeof(double) * C);
     A(&e->T, sizeof(int) * C);
     A(&e->err, sizeof(int));
@@ -692,7 +750,7 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
     sa.act = e->act;
     sa.done = e->done;
     sa.cand = e->cand;
-    sa.n_at = e->n_at * kEpiGroups;   // sorted candidate lists per signal
+    sa.n_at = e->n_at;   // sorted candidate lists per signal (one per atom tile)
     sa.psi32 = p->psi32;
     sa.ldN = p->ldN;
     sa.N = p->N;

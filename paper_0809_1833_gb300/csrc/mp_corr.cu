@@ -94,9 +94,13 @@ struct CorrShared {
     uint64_t empty[kMaxStages];
     uint64_t tfull[2];
     uint64_t tempty[2];
+    uint64_t xfull[4];       // per lane quadrant: column groups 1-3 wrote their lists
+    uint64_t xempty[4];      // per lane quadrant: group 0 has read them
     uint64_t drain;
     uint32_t tmem_base;
     int abort;
+    // exchange of the epilogue's per-group lists: [group 1..3][key][row of the block]
+    uint32_t xk[(kEpiGroups - 1) * kTop * kBM];
 };
 
 MP_DEV void corr_timeout(int* err, CorrShared* sh) {
@@ -106,7 +110,7 @@ MP_DEV void corr_timeout(int* err, CorrShared* sh) {
 
 // Per-CTA state the three roles share (set up by the kernel).
 struct CorrCtx {
-    uint8_t* tilesA;       // A stages, as_stride bytes apart
+    uint8_t* tilesA;       // A stages, as_stride bytes apart (1024-byte aligned)
     uint8_t* tilesB;       // B stages
     CorrShared* sh;
     uint32_t tmem;
@@ -250,13 +254,18 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
     } else {
         // ---------------- epilogue: kEpiGroups threads per signal row; a warp
         // reads the TMEM lane quadrant warp % 4 (the quadrant a warp may
-        // access), and warp group grp scans atom columns [grp, grp+1) * TN/kEpiGroups
+        // access), and warp group grp scans atom columns [grp, grp+1) * TN/kEpiGroups.
+        // Groups 1-3 then hand their sorted lists to group 0 through shared
+        // memory (bounded mbarrier waits per quadrant and round), which
+        // merges them into the tile's one list of 8 per row.
         const int quad = warp & 3;
         const int grp = (warp - 2) >> 2;
         const int cols = TN / kEpiGroups;
         int buf = 0;
         uint32_t bph = 0;
-        for (int ct = cid; ct < n_ct; ct += n_clusters) {
+        uint32_t xround = 0;          // exchange rounds of this quadrant so far
+        bool alive = true;
+        for (int ct = cid; ct < n_ct && alive; ct += n_clusters) {
             const int rt = (ct % n_rg) * CL + q, at = ct / n_rg;
             const int nmb = RM == 1 ? 1 : min(RM, n_blk - rt * RM);
             bool ok = mbar_wait_bounded(&sh->tfull[buf], bph, lim) &&
@@ -312,14 +321,45 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
                     tc_fence_before();
                     mbar_arrive(&sh->tempty[buf]);
                 }
-                if (row < n_act) {
-                    uint2* o = a.cand + ((static_cast<size_t>(row) * a.n_at + at) * kEpiGroups + grp) * kTop;
+                const int rr = quad * 32 + lane;      // row within the block
+                if (grp != 0) {
+                    // the slots are free once group 0 read the previous round
+                    bool okx = xround == 0 || mbar_wait_bounded(&sh->xempty[quad], (xround - 1u) & 1u, lim);
+                    okx = __all_sync(0xffffffffu, okx);
+                    if (!okx) {
+                        if (lane == 0) corr_timeout(a.err, sh);
+                        alive = false;
+                        break;
+                    }
 #pragma unroll
-                    for (int k = 0; k < kTop; ++k) {
-                        const uint32_t m = static_cast<uint32_t>(at * TN + key_col(tk[k]));
-                        o[k] = tk[k] ? make_uint2(key_score_bits(tk[k]), m) : make_uint2(0u, 0xffffffffu);
+                    for (int k = 0; k < kTop; ++k) sh->xk[((grp - 1) * kTop + k) * kBM + rr] = tk[k];
+                    mbar_arrive(&sh->xfull[quad]);
+                } else {
+                    bool okx = mbar_wait_bounded(&sh->xfull[quad], xround & 1u, lim);
+                    okx = __all_sync(0xffffffffu, okx);
+                    if (!okx) {
+                        if (lane == 0) corr_timeout(a.err, sh);
+                        alive = false;
+                        break;
+                    }
+#pragma unroll
+                    for (int g = 0; g < kEpiGroups - 1; ++g) {
+                        uint32_t ck[kTop];
+#pragma unroll
+                        for (int k = 0; k < kTop; ++k) ck[k] = sh->xk[(g * kTop + k) * kBM + rr];
+                        merge_top8(tk, ck);
+                    }
+                    mbar_arrive(&sh->xempty[quad]);
+                    if (row < n_act) {
+                        uint2* o = a.cand + (static_cast<size_t>(row) * a.n_at + at) * kTop;
+#pragma unroll
+                        for (int k = 0; k < kTop; ++k) {
+                            const uint32_t m = static_cast<uint32_t>(at * TN + key_col(tk[k]));
+                            o[k] = tk[k] ? make_uint2(key_score_bits(tk[k]), m) : make_uint2(0u, 0xffffffffu);
+                        }
                     }
                 }
+                ++xround;
             }
             if (++buf == nbuf) {
                 buf = 0;
@@ -372,6 +412,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sh->tfull[b], 1);
             mbar_init(&sh->tempty[b], 4 * 32 * kEpiGroups);
+        }
+        for (int b = 0; b < 4; ++b) {
+            mbar_init(&sh->xfull[b], 32 * (kEpiGroups - 1));
+            mbar_init(&sh->xempty[b], 32);
         }
         mbar_init(&sh->drain, 1);
         sh->abort = 0;
