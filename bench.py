@@ -667,6 +667,29 @@ def run_profile_case(iters):
     B.mp_plan_destroy(plan)
 
 
+def run_profile64_case(M, iters):
+    """Small case for ncu: Sec. 4's FP64 timing problem at M (N = M/2), one
+    FP64 decode capped at ``iters`` iterations (one kernel launch)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0809_1833_gb300 import binding as B
+    from paper_0809_1833_gb300 import workloads as W
+    prob = W.paper_timing_problem(M, seed=0, fp64=True)
+    N = prob.psi.shape[1]
+    sh = torch.cuda.current_stream().cuda_stream
+    psi = torch.from_numpy(prob.psi).cuda()
+    plan = B.mp_plan_create_f64(N, M, psi.data_ptr(), stream=sh)
+    del psi
+    y = torch.from_numpy(prob.y[0]).cuda()
+    x = torch.empty(M, dtype=torch.float64, device="cuda")
+    _, r = B.mp_recover_f64(plan, y.data_ptr(), x.data_ptr(), prob.eps, iters, None, True, sh)
+    print(json.dumps({"profile_case": f"paper_timing_fp64_M{M}", "iterations": r.iters,
+                      "mode": B.mp_plan_query(plan, B.MP_Q_PLAIN64_MODE),
+                      "fp64_flops_algorithmic_per_iteration": 2 * N * M}))
+    B.mp_plan_destroy(plan)
+
+
 PAPER_TIMING_SIZES = [1000, 3000, 5000, 7000, 9000, 11000, 13000, 15000]
 
 
@@ -808,6 +831,8 @@ def main():
     ap.add_argument("--profile-gemm", choices=["bf16", "fp8"], default=None,
                     help="profiling case: the batched workload's correlation GEMM on its full batch of "
                          "synthetic rows, 3 launches (2 warm-up), at --profile-shape, then exit")
+    ap.add_argument("--profile64", type=int, nargs=2, metavar=("M", "ITERS"), default=None,
+                    help="profiling case: Sec. 4's FP64 problem at M, one decode capped at ITERS, then exit")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--served-duration", type=float, default=10.0,
                     help="seconds of Poisson arrivals for the served measurement (0 = skip)")
@@ -833,6 +858,9 @@ def main():
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.profile64:
+        run_profile64_case(*args.profile64)
+        return
     if args.profile_gemm:
         shape = tuple(int(v) for v in args.profile_shape.split(","))
         print(json.dumps(gemm_profile_case(args.profile_gemm, shape)))

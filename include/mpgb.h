@@ -198,7 +198,10 @@ typedef enum {
     MP_Q_GRAM_BYTES = 14,      /* device bytes of the Gram matrix (0 until built)     */
     MP_Q_PLAN_N = 15,          /* N of the plan                                      */
     MP_Q_PLAN_M = 16,          /* M of the plan                                      */
-    MP_Q_BATCH_TILE_M = 17     /* signals per GEMM tile of the current batch state   */
+    MP_Q_BATCH_TILE_M = 17,    /* signals per GEMM tile of the current batch state   */
+    MP_Q_PLAIN64_PIECES = 18   /* FP64 streaming with the 4 warps sharing every      */
+                               /* stage: ring stages per atom (an atom streams as    */
+                               /* that many pieces); 0 when warps own whole atoms    */
 } mp_query;
 
 /* ------------------------------------------------------------------ */

@@ -58,6 +58,7 @@ MP_Q_DEVICE_BYTES = 8
 MP_Q_KERNEL_LAUNCHES = 9
 MP_Q_PLAIN64_MODE = 12
 MP_Q_PLAIN64_STAGES = 13
+MP_Q_PLAIN64_PIECES = 18
 MP_Q_GRAM_BYTES = 14
 MP_Q_PLAN_N = 15
 MP_Q_PLAN_M = 16

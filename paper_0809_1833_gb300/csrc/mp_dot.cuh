@@ -102,16 +102,4 @@ MP_DEV void dot4(const double* __restrict__ p, const double* __restrict__ r, int
                               ((ax[i][2] + ay[i][2]) + (ax[i][3] + ay[i][3])));
 }
 
-// One class of dot1's sum: lane l's p_q for the segments of class q.
-MP_DEV double dot_class(const double* __restrict__ p, const double* __restrict__ r, int ldN, int lane, int q) {
-    double ax = 0.0, ay = 0.0;
-    for (int off = lane * 2 + 64 * q; off < ldN; off += 256) {
-        const double2 u = *reinterpret_cast<const double2*>(r + off);
-        const double2 v = *reinterpret_cast<const double2*>(p + off);
-        ax = fma(v.x, u.x, ax);
-        ay = fma(v.y, u.y, ay);
-    }
-    return ax + ay;
-}
-
 }  // namespace mpgb

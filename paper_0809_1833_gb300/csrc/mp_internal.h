@@ -54,6 +54,8 @@ struct PlainConfig {
     int off_data = 0;      // byte offsets inside dynamic smem
     int off_sh = 0;
     int coop = 0;          // FP64 streaming: 4 warps share every stage
+    int pieces = 1;        // coop: stages per atom (pieces of whole 4-segment groups)
+    int piece_elems = 0;   // coop: elements per piece (a multiple of 256), the stage stride
 };
 
 // OMP decode scratch (mp_plain.cu): basis, packed R, alpha = Q^T y,

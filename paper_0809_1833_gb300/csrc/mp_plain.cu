@@ -35,6 +35,10 @@ namespace mpgb {
 constexpr int kMaxWarps = 32;
 constexpr int kMaxStages = 64;
 constexpr int kResidentThreads = 256;
+// FP64 streaming with shared stages: a producer warp and two groups of four
+// consumer warps (two warps per SM sub-partition keep its FP64 pipe fed)
+constexpr int kCoopGroups = 2;
+constexpr int kMaxPlainThreads = 32 * (1 + 4 * kCoopGroups);
 // FP64 sums of squares (the energy, OMP's ||w||^2) run as kSumChains FMA
 // chains (chain i takes the elements i, i + kSumChains, ...), then warp sums
 // in warp order: the same bits for every launch shape, whatever its thread
@@ -56,14 +60,17 @@ struct PlainTraits<double> {
     using V = double2;
 };
 
-// FP64 grid streaming with one atom per stage and a ring shallower than the
-// 4 consumer warps: every warp computes its class of each atom's sum (see
-// dot1 for double) into these partials, one warp combines them.
+// FP64 grid streaming with atoms too large for two ring slots per warp:
+// every warp computes its class of each atom's sum (see dot1 for double)
+// into these partials, kept for a window of kCoopWindow atoms and double-
+// buffered by the window's parity; after the window's barrier each warp
+// combines a quarter of its atoms.
+constexpr int kCoopWindow = 8;
 template <typename T>
 struct CoopPartials {};
 template <>
 struct CoopPartials<double> {
-    double part[2][4][32];
+    double part[2][kCoopWindow][4][32];
     int abort[2];
 };
 
@@ -89,6 +96,8 @@ struct PlainArgs {
     int N, ldN, M, T_max;
     double eps2;
     int stage_atoms, stages;
+    int stage_elems;       // mode 3: elements per ring stage (its stride in the ring)
+    int pieces;            // mode 3: stages per atom (> 1: one atom streams as pieces)
     int prefetch;          // mode 3: L2 prefetch distance in stages (0 = off)
     int evict_first;       // mode 3: evict-first L2 hint on the streamed atoms
     int l2_keep_atoms;     // mode 3: the CTA's first atoms loaded evict-last (kept in L2)
@@ -115,6 +124,7 @@ struct PlainArgs {
     T* xs;
     int kmax;
     int coop;              // FP64 streaming: four warps share every stage (CoopPartials)
+    int piece_elems;       // coop: elements per piece (whole 4-segment groups)
     int* tr_atoms;
     T* tr_coefs;
     double* tr_energy;
@@ -265,18 +275,23 @@ MP_DEV float dot1_scaled(const float* __restrict__ w, float s, const float* __re
 // ------------------------------------------------------------------ producer
 template <typename T>
 MP_DEV void plain_producer(const PlainArgs<T>& a, PlainShared<T>* sh, T* ring, int a0, int na) {
-    const int A = a.stage_atoms, D = a.stages, ldN = a.ldN;
-    const int S = (na + A - 1) / A;
+    const int A = a.stage_atoms, D = a.stages, ldN = a.ldN, np = a.pieces;
+    // stages per pass over the CTA's atoms: A whole atoms each, or (np > 1)
+    // one piece of one atom each
+    const int S = np > 1 ? na * np : (na + A - 1) / A;
     if (S == 0) return;
-    const size_t stage_elems = static_cast<size_t>(A) * ldN;
+    const size_t stage_elems = static_cast<size_t>(a.stage_elems);
     const uint64_t pol = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
     volatile int* vdone = &sh->done;
+    // ring position (slot, parity of its use count) and stage (atom, piece),
+    // kept incrementally: this single thread must not stall on divisions
     long long seq = 0;
+    int slot = 0, j = 0, ja = 0, jp = 0;
+    uint32_t upar = 0;
     while (true) {
-        const int slot = static_cast<int>(seq % D);
         if (seq >= D) {
-            const uint32_t par = static_cast<uint32_t>(((seq / D) - 1) & 1);
+            const uint32_t par = upar ^ 1u;
             bool ok = mbar_try_wait(&sh->empty[slot], par);
             uint64_t deadline = 0;
             while (!ok) {
@@ -294,31 +309,41 @@ MP_DEV void plain_producer(const PlainArgs<T>& a, PlainShared<T>* sh, T* ring, i
             if (!ok) break;
         }
         if (*vdone) break;
-        const int j = static_cast<int>(seq % S);
-        const int atom0 = a0 + j * A;
-        const int nat = min(A, na - j * A);
-        const uint32_t bytes = static_cast<uint32_t>(nat) * ldN * static_cast<uint32_t>(sizeof(T));
+        // this stage: A atoms from atom0, or piece jp of atom ja
+        const int atom0 = np > 1 ? a0 + ja : a0 + j * A;
+        const size_t off = np > 1 ? static_cast<size_t>(jp) * a.piece_elems : 0;
+        const int nel = np > 1 ? min(a.piece_elems, ldN - jp * a.piece_elems) : min(A, na - j * A) * ldN;
+        const uint32_t bytes = static_cast<uint32_t>(nel) * static_cast<uint32_t>(sizeof(T));
+        const T* src = a.psi + static_cast<size_t>(atom0) * ldN + off;
         mbar_arrive_expect_tx(&sh->full[slot], bytes);
         // the first l2_keep_atoms atoms of the slice stay in L2 from pass to
         // pass (evict-last); the rest streams through it (evict-first)
-        if (j * A < a.l2_keep_atoms)
-            bulk_g2s_hint(ring + slot * stage_elems, a.psi + static_cast<size_t>(atom0) * ldN, bytes,
-                          &sh->full[slot], pol_keep);
+        if (atom0 - a0 < a.l2_keep_atoms)
+            bulk_g2s_hint(ring + slot * stage_elems, src, bytes, &sh->full[slot], pol_keep);
         else if (a.evict_first)
-            bulk_g2s_hint(ring + slot * stage_elems, a.psi + static_cast<size_t>(atom0) * ldN, bytes,
-                          &sh->full[slot], pol);
+            bulk_g2s_hint(ring + slot * stage_elems, src, bytes, &sh->full[slot], pol);
         else
-            bulk_g2s(ring + slot * stage_elems, a.psi + static_cast<size_t>(atom0) * ldN, bytes, &sh->full[slot]);
+            bulk_g2s(ring + slot * stage_elems, src, bytes, &sh->full[slot]);
         // L2 as a deeper window than the shared-memory ring: pull the stage
         // `prefetch` positions ahead into L2 now, so HBM keeps streaming
-        // while the ring is full during the per-iteration exchange.
-        if (a.prefetch > 0) {
-            const int jp = static_cast<int>((seq + a.prefetch) % S);
-            const int np = min(A, na - jp * A);
-            prefetch_l2(a.psi + static_cast<size_t>(a0 + jp * A) * ldN,
-                        static_cast<uint32_t>(np) * ldN * static_cast<uint32_t>(sizeof(T)));
+        // while the ring is full during the per-iteration exchange (whole
+        // atoms per stage only)
+        if (a.prefetch > 0 && np == 1) {
+            const int jq = static_cast<int>((seq + a.prefetch) % S);
+            const int nq = min(A, na - jq * A);
+            prefetch_l2(a.psi + static_cast<size_t>(a0 + jq * A) * ldN,
+                        static_cast<uint32_t>(nq) * ldN * static_cast<uint32_t>(sizeof(T)));
         }
         ++seq;
+        if (++slot == D) {
+            slot = 0;
+            upar ^= 1u;
+        }
+        if (++j == S) j = 0;
+        if (np > 1 && ++jp == np) {
+            jp = 0;
+            if (++ja == na) ja = 0;
+        }
     }
     // Wait for every copy still in flight before the CTA may exit: the only
     // outstanding copy of slot k is the last one issued into it.
@@ -333,7 +358,7 @@ MP_DEV void plain_producer(const PlainArgs<T>& a, PlainShared<T>* sh, T* ring, i
 // T = float: the FP32 decode; T = double: the same iteration in FP64 (the
 // paper's double-precision runs).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const PlainArgs<T> a) {
+__global__ void __launch_bounds__(kMaxPlainThreads, 1) mp_plain_kernel(const PlainArgs<T> a) {
     using Key = typename PlainTraits<T>::Key;
     using V = typename PlainTraits<T>::V;
     constexpr bool OMP = MODE >= 5;       // 5 grid-resident, 6 grid-streaming
@@ -369,7 +394,8 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
         if (STREAM) {
             for (int s = 0; s < a.stages; ++s) {
                 mbar_init(&sh->full[s], 1);
-                mbar_init(&sh->empty[s], 1);
+                // shared stages are released by every consumer warp
+                mbar_init(&sh->empty[s], a.coop ? kSumChains / 32 : 1);
             }
             fence_mbar_init();
         }
@@ -446,53 +472,130 @@ __global__ void __launch_bounds__(kResidentThreads, 1) mp_plain_kernel(const Pla
             for (int j = 4 * cw; j < na; j += 4 * ncw)
                 best = scan_atoms(data + static_cast<size_t>(j) * ldN, r, ldN, min(4, na - j), a0 + j, lane, best);
         } else {
-            // slot s belongs to warp s % ncw, which consumes the slot's uses
-            // in order (so it never waits two phases ahead on a barrier)
-            const int S = (na + A - 1) / A;
+            const int np = a.pieces;
+            const int S = np > 1 ? na * np : (na + A - 1) / A;
             const long long seq0 = static_cast<long long>(t) * S;
             int slot = static_cast<int>(seq0 % D);
             uint32_t par = static_cast<uint32_t>((seq0 / D) & 1);
-            for (int j = 0; j < S; ++j, slot = slot + 1 == D ? (par ^= 1u, 0) : slot + 1) {
-                if constexpr (FP64) {
-                    if (a.coop) {
-                        // every warp takes its class of stage j's atom (A = 1).
-                        // Partials and the abort word are double-buffered by
-                        // j's parity: stage j's are written only before
-                        // barrier j and read only after it, and rewritten at
-                        // stage j + 2, after barrier j + 1 -- so every warp
-                        // reads the same abort word and leaves at the same stage
-                        const bool ok = mbar_wait_bounded(&sh->full[slot], par, a.watchdog_ns);
-                        double pq = 0.0;
-                        if (ok) pq = dot_class(data + static_cast<size_t>(slot) * ldN, r, ldN, lane, cw);
-                        else if (lane == 0) {
+            bool shared_stages = false;
+            if constexpr (FP64) {
+                if (a.coop) {
+                    // every warp takes its class of each atom.  An atom
+                    // streams as np stages of whole 4-segment groups; the
+                    // warp's two chains run on across them in dot1's order,
+                    // and the warp releases a stage as soon as its class of
+                    // it is summed.  The lane partials of a window of atoms
+                    // (and the abort word) go to shared memory, double-
+                    // buffered by the window's parity: written only before
+                    // that window's barrier and read only after it,
+                    // rewritten two windows later -- so every warp reads the
+                    // same abort word and leaves at the same window
+                    // With ng = ncw / 4 groups of 4 warps (1 or 2), group g
+                    // takes the atoms in slots s with (s / np) % ng == g:
+                    // the ring holds a multiple of ng np stages, so a slot
+                    // always belongs to the same group, which consumes its
+                    // uses in order.
+                    shared_stages = true;
+                    const int ng = ncw >> 2;
+                    const int cls = cw & 3, grp = cw >> 2;    // class of segments, group
+                    const int spp = a.piece_elems / 64;       // segments per piece, a multiple of 4
+                    const int nseg = (ldN + 63) / 64;
+                    const int nfull = ldN / 64;               // segments with all 64 elements
+                    const double2* r2 = reinterpret_cast<const double2*>(r);
+                    double ax = 0.0, ay = 0.0;
+                    bool failed = false;
+                    int jp = 0, ja = 0, wa = 0, wpar = 0;     // piece, atom, atom in window, window parity
+                    int sgrp = (slot / np) % ng;              // group of the current slot
+                    int sin = slot % np;                      // position of the slot in its group of np
+                    for (int j = 0; j < S; ++j) {
+                        const bool mine = sgrp == grp;
+                        if (mine && !failed) {
+                            const bool ok =
+                                __all_sync(0xffffffffu, mbar_wait_bounded(&sh->full[slot], par, a.watchdog_ns));
+                            if (ok) {
+                                const int s0 = jp * spp, s1 = min(s0 + spp, nseg), s1f = min(s1, nfull);
+                                // st2: the stage's element pairs, the piece's first at 0
+                                const double2* st2 =
+                                    reinterpret_cast<const double2*>(data + static_cast<size_t>(slot) * a.stage_elems);
+                                const int pb = s0 * 32;                   // the piece's first element pair
+                                int sg = s0 + cls;
+#pragma unroll 4
+                                for (; sg < s1f; sg += 4) {
+                                    const int e2 = sg * 32 + lane;    // element pair in the atom
+                                    const double2 u = r2[e2];
+                                    const double2 v = st2[e2 - pb];
+                                    ax = fma(v.x, u.x, ax);
+                                    ay = fma(v.y, u.y, ay);
+                                }
+                                if (sg < s1 && sg * 64 + lane * 2 < ldN) {   // the partial last segment
+                                    const int e2 = sg * 32 + lane;
+                                    const double2 u = r2[e2];
+                                    const double2 v = st2[e2 - pb];
+                                    ax = fma(v.x, u.x, ax);
+                                    ay = fma(v.y, u.y, ay);
+                                }
+                                __syncwarp();
+                                if (lane == 0) mbar_arrive(&sh->empty[slot]);
+                            } else {
+                                failed = true;
+                                if (lane == 0) {
+                                    atomicCAS(&a.ws->err, 0, static_cast<int>(MP_ERR_TIMEOUT));
+                                    sh->coop.abort[wpar] = 1;
+                                    *reinterpret_cast<volatile int*>(&sh->abort) = 1;
+                                }
+                            }
+                        }
+                        if (jp == np - 1) {
+                            if (mine) sh->coop.part[wpar][wa][cls][lane] = failed ? 0.0 : ax + ay;
+                            ax = ay = 0.0;
+                            if (wa == kCoopWindow - 1 || ja == na - 1) {
+                                named_bar_sync(2, nct);
+                                if (sh->coop.abort[wpar]) break;
+                                const int wbase = ja - wa;
+                                for (int k = cw; k <= wa; k += ncw) {
+                                    const double(&pp)[4][32] = sh->coop.part[wpar][k];
+                                    const double tot = (pp[0][lane] + pp[1][lane]) + (pp[2][lane] + pp[3][lane]);
+                                    best = kmax(best, pack_key(warp_sum_f64(tot), a0 + wbase + k));
+                                }
+                                wa = 0;
+                                wpar ^= 1;
+                            } else {
+                                ++wa;
+                            }
+                        }
+                        if (++jp == np) {
+                            jp = 0;
+                            ++ja;
+                        }
+                        if (++slot == D) {
+                            slot = 0;
+                            par ^= 1u;
+                        }
+                        if (++sin == np) {
+                            sin = 0;
+                            if (++sgrp == ng) sgrp = 0;
+                        }
+                    }
+                }
+            }
+            // otherwise slot s belongs to warp s % ncw, which consumes the
+            // slot's uses in order (so it never waits two phases ahead on a
+            // barrier)
+            if (!shared_stages) {
+                for (int j = 0; j < S; ++j, slot = slot + 1 == D ? (par ^= 1u, 0) : slot + 1) {
+                    if (slot % ncw != cw) continue;
+                    if (!mbar_wait_bounded(&sh->full[slot], par, a.watchdog_ns)) {
+                        if (lane == 0) {
                             atomicCAS(&a.ws->err, 0, static_cast<int>(MP_ERR_TIMEOUT));
-                            sh->coop.abort[j & 1] = 1;
                             *reinterpret_cast<volatile int*>(&sh->abort) = 1;
                         }
-                        sh->coop.part[j & 1][cw][lane] = pq;
-                        named_bar_sync(2, nct);
-                        if (sh->coop.abort[j & 1]) break;
-                        if (cw == j % ncw) {
-                            const double(&pp)[4][32] = sh->coop.part[j & 1];
-                            const double tot = (pp[0][lane] + pp[1][lane]) + (pp[2][lane] + pp[3][lane]);
-                            best = kmax(best, pack_key(warp_sum_f64(tot), a0 + j));
-                            if (lane == 0) mbar_arrive(&sh->empty[slot]);
-                        }
-                        continue;
+                        break;
                     }
+                    const T* st = data + static_cast<size_t>(slot) * a.stage_elems;
+                    best = scan_atoms(st, r, ldN, min(A, na - j * A), a0 + j * A, lane, best);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh->empty[slot]);
                 }
-                if (slot % ncw != cw) continue;
-                if (!mbar_wait_bounded(&sh->full[slot], par, a.watchdog_ns)) {
-                    if (lane == 0) {
-                        atomicCAS(&a.ws->err, 0, static_cast<int>(MP_ERR_TIMEOUT));
-                        *reinterpret_cast<volatile int*>(&sh->abort) = 1;
-                    }
-                    break;
-                }
-                const T* st = data + static_cast<size_t>(slot) * A * ldN;
-                best = scan_atoms(st, r, ldN, min(A, na - j * A), a0 + j * A, lane, best);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sh->empty[slot]);
             }
         }
         // ---- CTA max, then grid max
@@ -882,26 +985,52 @@ static mp_status plain_configure_t(PlanImpl* p, PlainConfig* cfg, bool omp = fal
     long long A = std::max<long long>(1, (p->stage_bytes + atom_bytes - 1) / atom_bytes);
     if (budget / (A * atom_bytes) < 4) A = std::max<long long>(1, p->stage_bytes / atom_bytes);
     A = std::min(A, apc);
-    const long long stage_bytes = A * atom_bytes;
+    long long stage_bytes = A * atom_bytes;
     // as deep a ring as fits; 4 consumer warps (kSumChains threads), each
     // owning the slots s with s % 4 == its index (D need not be a multiple
     // of 4; with D < 4 some warps own no slot)
     long long D = std::min<long long>(kMaxStages, budget / stage_bytes);
+    const int W = kSumChains / 32;
+    // FP64 is bound by the FP64 units, not by HBM: keep all 4 SM sub-
+    // partitions' FP64 pipes fed.  For atoms of 16 KB or more, or when the
+    // ring cannot give every warp two whole-atom slots (its next atom
+    // loading while it computes one), 4 warps share every stage, one class
+    // of segments each, an atom streams as pieces of whole 4-segment groups
+    // of about stage_bytes, and two such groups take alternate atoms where
+    // the ring holds an atom for each (a warp fed from shared memory cannot
+    // keep its sub-partition's FP64 pipe busy alone); otherwise every warp
+    // owns the same number of whole-atom slots.  FP32 keeps the deepest ring
+    // of whole atoms.
+    int groups = 1;
+    if (sizeof(T) == 8 && !omp) {
+        if (atom_bytes >= 16384 || budget < 2LL * W * atom_bytes) {
+            const long long nseg = (p->ldN + 63) / 64;
+            long long np = std::max<long long>(1, (atom_bytes + p->stage_bytes - 1) / p->stage_bytes);
+            const long long spp = ((nseg + np - 1) / np + 3) / 4 * 4;
+            np = (nseg + spp - 1) / spp;
+            const long long pe = spp * 64;
+            cfg->coop = 1;
+            cfg->pieces = static_cast<int>(np);
+            cfg->piece_elems = static_cast<int>(pe);
+            A = 1;
+            stage_bytes = pe * static_cast<long long>(sizeof(T));
+            D = std::min<long long>(kMaxStages, budget / stage_bytes);
+            // two groups of 4 warps (two per SM sub-partition) when the ring
+            // holds a whole atom for each, the ring a multiple of 2 atoms
+            if (D >= kCoopGroups * np) {
+                groups = kCoopGroups;
+                D -= D % (kCoopGroups * np);
+            }
+        } else if (D >= W) {
+            D -= D % W;
+        }
+    }
     if (D < 2)
         return fail(MP_ERR_UNSUPPORTED, "plain decode: N=" + std::to_string(p->N) +
                                             " leaves no room for a two-stage ring");
-    const int W = kSumChains / 32;
-    // FP64 is bound by the FP64 units, not by HBM: keep all 4 SM sub-
-    // partitions busy -- with one atom per stage and fewer than 4 stages the
-    // 4 warps share every stage; otherwise every warp owns the same number
-    // of slots (FP32 keeps the deepest ring instead)
-    if (sizeof(T) == 8) {
-        if (D < W && A == 1) cfg->coop = 1;
-        else if (D >= W) D -= D % W;
-    }
     cfg->mode = omp ? 6 : 3;
     cfg->ctas = G;
-    cfg->threads = 32 * (1 + W);
+    cfg->threads = 32 * (1 + W * groups);
     cfg->stage_atoms = static_cast<int>(A);
     cfg->stages = static_cast<int>(D);
     cfg->smem = static_cast<int>(cfg->off_data + D * stage_bytes);
@@ -930,6 +1059,9 @@ static mp_status plain_launch_t(PlanImpl* p, const T* psi, const T* y, T* x, con
     a.eps2 = stop->eps * stop->eps;
     a.stage_atoms = cfg.stage_atoms;
     a.stages = cfg.stages;
+    a.pieces = cfg.coop ? cfg.pieces : 1;
+    a.piece_elems = cfg.coop ? cfg.piece_elems : 0;
+    a.stage_elems = cfg.coop ? cfg.piece_elems : cfg.stage_atoms * p->ldN;
     a.prefetch = cfg.mode == 3 ? p->prefetch_stages : 0;
     a.evict_first = p->evict_first;
     if (cfg.mode == 3 || cfg.mode == 6) {

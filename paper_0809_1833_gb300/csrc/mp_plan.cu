@@ -386,10 +386,14 @@ mp_status mp_plan_query(mp_plan_t plan, int what, long long* value) {
             *value = p->gram ? static_cast<long long>(p->M) * p->ldG * 4 : 0;
             return MP_OK;
         case MP_Q_PLAIN64_MODE:
-        case MP_Q_PLAIN64_STAGES: {
+        case MP_Q_PLAIN64_STAGES:
+        case MP_Q_PLAIN64_PIECES: {
             PlainConfig c64;
             const bool ok = p->psi64 && plain_configure64(p, &c64) == MP_OK;
-            *value = !ok ? 0 : (what == MP_Q_PLAIN64_MODE ? c64.mode : c64.stages);
+            *value = !ok ? 0
+                         : (what == MP_Q_PLAIN64_MODE     ? c64.mode
+                            : what == MP_Q_PLAIN64_STAGES ? c64.stages
+                                                          : (c64.coop ? c64.pieces : 0));
             clear_error();
             return MP_OK;
         }

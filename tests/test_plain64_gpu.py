@@ -91,19 +91,26 @@ def test_fp64_modes_agree_bitwise():
         assert np.array_equal(o["energies"], outs[0]["energies"])
 
 
-def test_fp64_cooperative_stream_matches_resident_bitwise():
-    """N = 7500 in FP64 (60 KB atoms): the streaming ring holds 2 stages, so
-    the 4 consumer warps share every stage, each summing one class of
-    segments (the FP64 correlation order is defined by those classes).  The
+@pytest.mark.parametrize("case", [(3500, 600, 1), (4500, 600, 2), (7500, 300, 2), (9000, 150, 3)],
+                         ids=lambda c: f"N{c[0]}_pieces{c[2]}")
+def test_fp64_cooperative_stream_matches_resident_bitwise(case):
+    """FP64 atoms too large for two ring slots per consumer warp (28, 36,
+    60 and 72 KB): 4 warps share every stage, each summing one class of
+    segments (the FP64 correlation order is defined by those classes),
+    atoms above 32 KB stream as pieces of whole 4-segment groups, the
+    warps' chains running on across the pieces, and where the ring holds
+    two atoms two such groups of warps take alternate atoms.  The
     grid-resident shape computes the same sums with one warp per atom: the
     two must agree bit for bit, and both meet the oracle rule."""
-    prob = W.make_plain(7500, 300, 10, seed=13, eps=1e-10, T=3000)
+    N, M, pieces = case
+    prob = W.make_plain(N, M, 10, seed=13, eps=1e-10, T=3000)
     y = prob.y[0].astype(np.float64)
     outs = []
     for mode in (2, 3):
         with plan64(prob.psi, mode) as pl:
             if mode == 3:
-                assert pl.query(B().MP_Q_PLAIN64_STAGES) < 4
+                assert pl.query(B().MP_Q_PLAIN64_PIECES) == pieces
+                assert pl.query(B().MP_Q_PLAIN64_STAGES) >= 4
             outs.append(pl.decode64(y, prob.eps, prob.T))
     for k in ("atoms", "x", "energies", "r"):
         assert np.array_equal(outs[0][k], outs[1][k]), k
