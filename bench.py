@@ -567,7 +567,7 @@ def gemm_profile_case(prec_name, shape):
             "tflops": 2.0 * w["N"] * w["M"] * w["B"] / us / 1e6}
 
 
-def served_measure(rate=2000.0, duration=10.0, pool=48, seed=0, max_slots=256):
+def served_measure(rate=2000.0, duration=10.0, pool=48, seed=0, max_slots=256, drain_s=120.0):
     """Poisson arrivals over the four resident dictionaries of the served
     workload; every request is submitted at its arrival time through the
     server's C ABI and polled until done.  Reports offered / completed rates,
@@ -627,7 +627,7 @@ def served_measure(rate=2000.0, duration=10.0, pool=48, seed=0, max_slots=256):
                 break
         for t in done:
             del pending[t]
-        if now > duration + 120:
+        if now > duration + drain_s:
             break
         if not done and (i >= n or arr[i] > now + 5e-4):
             time.sleep(2e-4)
@@ -639,12 +639,25 @@ def served_measure(rate=2000.0, duration=10.0, pool=48, seed=0, max_slots=256):
     lat = np.array(lat)
     return {"workload": "served_4dict_poisson2000", "dictionaries": [list(d) for d in dicts], "precision": "bf16",
             "slots_per_dictionary": slots, "offered_rps": rate, "duration_s": duration, "requests": int(n),
+            "submitted_rps": float(n_sub + rejected) / max(min(wall, duration), 1e-9),
+            "unfinished_at_stop": len(pending),
             "submitted": int(n_sub), "rejected": int(rejected), "rejected_pct": 100.0 * rejected / max(n, 1),
             "completed": int(stt.completed), "completed_rps": float(stt.completed) / wall, "wall_s": wall,
             "server_p50_ms": 1e3 * stt.latency_p50_s, "server_p99_ms": 1e3 * stt.latency_p99_s,
             "client_p50_ms": 1e3 * float(np.percentile(lat, 50)) if lat.size else None,
             "client_p99_ms": 1e3 * float(np.percentile(lat, 99)) if lat.size else None,
             "signal_pool": f"{pool} distinct seeded signals per dictionary, K ~ U{{4..N/16}}, reused across requests"}
+
+
+def served_sweep(rates, duration=5.0):
+    """The served workload at increasing Poisson rates (C5's lambda sweep):
+    one JSON line per rate with offered / submitted / completed rates,
+    rejections and latency percentiles; arrivals last `duration` seconds and
+    the backlog then gets at most 10 s to drain."""
+    import __graft_entry__
+    __graft_entry__.build()
+    for r in rates:
+        print(json.dumps({"served_sweep": served_measure(r, duration, drain_s=10.0)}), flush=True)
 
 
 def run_profile_case(iters):
@@ -838,6 +851,9 @@ def main():
                     help="seconds of Poisson arrivals for the served measurement (0 = skip)")
     ap.add_argument("--served-rate", type=float, default=2000.0)
     ap.add_argument("--served-only", action="store_true", help="run only the served measurement")
+    ap.add_argument("--served-sweep", nargs="*", type=float, default=None,
+                    help="run only the served workload at these Poisson rates, req/s "
+                         "(default 1000 2000 3000 4000 6000 8000 12000)")
     ap.add_argument("--paper-timing", nargs="*", type=int, default=None,
                     help="run only Sec. 4's CPU-vs-GPU size sweep (FP32 and FP64) at these M "
                          f"(default {PAPER_TIMING_SIZES})")
@@ -850,6 +866,9 @@ def main():
         return
     if args.paper_timing is not None:
         paper_timing_sweep(args.paper_timing or PAPER_TIMING_SIZES)
+        return
+    if args.served_sweep is not None:
+        served_sweep(args.served_sweep or [1000, 2000, 3000, 4000, 6000, 8000, 12000])
         return
     if args.served_only:
         import __graft_entry__
