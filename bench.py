@@ -517,6 +517,9 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
     iters = np.array([r.iters for r in res])
     Xh = X.cpu().numpy()
     supp_b = [orc.support_score(Xh[i], prob.supports[i]) for i in range(prob.B)]
+    # x~ against the true sparse signal x (every signal; the FP64 oracle's
+    # x~ is compared on a sample by --fp8-error)
+    xerr = np.linalg.norm(Xh.astype(np.float64) - prob.x_true, axis=1) / np.linalg.norm(prob.x_true, axis=1)
     xs = torch.empty(prob.M, device="cuda")
     tp, supp_p = 0.0, []
     for i in range(n_plain):
@@ -540,6 +543,7 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
             "plain_sample": f"first {n_plain} signals through mp_recover",
             "support_score_mean": float(np.mean(supp_b)), "support_score_min": float(np.min(supp_b)),
             "plain_support_score_mean": float(np.mean(supp_p)),
+            "x_rel_err_vs_truth_mean": float(np.mean(xerr)), "x_rel_err_vs_truth_max": float(np.max(xerr)),
             "iterations_total": int(iters.sum()), "iterations_max": int(iters.max()),
             "effective_tflops": flops / tb / 1e12, "gpu_launches_per_batch": int(launches), "gemm_shape": shape,
             "gemm_full_batch": gemm}
@@ -647,6 +651,49 @@ def served_measure(rate=2000.0, duration=10.0, pool=48, seed=0, max_slots=256, d
             "client_p50_ms": 1e3 * float(np.percentile(lat, 50)) if lat.size else None,
             "client_p99_ms": 1e3 * float(np.percentile(lat, 99)) if lat.size else None,
             "signal_pool": f"{pool} distinct seeded signals per dictionary, K ~ U{{4..N/16}}, reused across requests"}
+
+
+def fp8_error(n_sample=2):
+    """The FP8 batched workload (N=8192, M=32768, 256 signals) decoded in one
+    batch; for the first n_sample signals the FP64 oracle's decode of the same
+    y (FP64 throughout) is the reference: relative L2 difference of x~, both
+    iteration counts, and both errors against the true signal.  The oracle
+    takes about half a minute per signal on 16 host cores."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from oracle import mp_oracle as orc
+    from paper_0809_1833_gb300 import binding as B
+    from paper_0809_1833_gb300 import workloads as W
+    name = BATCHED["fp8"]
+    w = W.WORKLOADS[name]
+    prob = W.make_workload(name, seed=0)
+    prec = B.MP_PREC_FP8E4M3
+    s = torch.cuda.current_stream().cuda_stream
+    d = torch.from_numpy(prob.psi).cuda()
+    plan = B.mp_plan_create(prob.N, prob.M, d.data_ptr(), prec_mask=1 << prec, stream=s)
+    del d
+    Y = torch.from_numpy(prob.y).cuda()
+    X = torch.empty((prob.B, prob.M), device="cuda")
+    _, res = B.mp_recover_batched(plan, prec, Y.data_ptr(), X.data_ptr(), prob.B, (w["eps"], w["T"]), None, s)
+    torch.cuda.synchronize()
+    Xh = X.cpu().numpy().astype(np.float64)
+    B.mp_plan_destroy(plan)
+    for i in range(n_sample):
+        t0 = time.perf_counter()
+        o = orc.mp(prob.psi, prob.y[i], w["eps"], w["T"])
+        dt = time.perf_counter() - t0
+        xo = np.asarray(o["x"], dtype=np.float64)
+        nx = np.linalg.norm(prob.x_true[i])
+        print(json.dumps({"fp8_vs_fp64": {
+            "workload": name, "signal": i, "eps": w["eps"],
+            "fp8_iters": int(res[i].iters), "fp64_iters": int(o["iters"]),
+            "x_rel_diff_fp8_vs_fp64": float(np.linalg.norm(Xh[i] - xo) / np.linalg.norm(xo)),
+            "fp8_x_rel_err_vs_truth": float(np.linalg.norm(Xh[i] - prob.x_true[i]) / nx),
+            "fp64_x_rel_err_vs_truth": float(np.linalg.norm(xo - prob.x_true[i]) / nx),
+            "fp8_rel_residual": float(res[i].rel_residual),
+            "fp8_support_score": float(orc.support_score(Xh[i].astype(np.float32), prob.supports[i])),
+            "oracle_s": dt}}), flush=True)
 
 
 def served_sweep(rates, duration=5.0):
@@ -851,6 +898,8 @@ def main():
                     help="seconds of Poisson arrivals for the served measurement (0 = skip)")
     ap.add_argument("--served-rate", type=float, default=2000.0)
     ap.add_argument("--served-only", action="store_true", help="run only the served measurement")
+    ap.add_argument("--fp8-error", type=int, default=None, metavar="S",
+                    help="run only the FP8 workload's decode against the FP64 oracle on S sampled signals")
     ap.add_argument("--served-sweep", nargs="*", type=float, default=None,
                     help="run only the served workload at these Poisson rates, req/s "
                          "(default 1000 2000 3000 4000 6000 8000 12000)")
@@ -866,6 +915,9 @@ def main():
         return
     if args.paper_timing is not None:
         paper_timing_sweep(args.paper_timing or PAPER_TIMING_SIZES)
+        return
+    if args.fp8_error is not None:
+        fp8_error(args.fp8_error)
         return
     if args.served_sweep is not None:
         served_sweep(args.served_sweep or [1000, 2000, 3000, 4000, 6000, 8000, 12000])
