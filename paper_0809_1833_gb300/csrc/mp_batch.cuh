@@ -60,7 +60,7 @@ cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, con
 // ------------------------------------------------------------------ batch engine
 // Per-signal state of a slot.
 struct SlotState {
-    double e0, e, thr2, audit;
+    double e0, e, thr2, audit;   // audit: max |e_t - (e_{t-1} - c^2)| (reported / e0)
     int t, T, status, stop_reason;
 };
 

@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
         if (io.tr_coefs && s.t < io.tr_cap) io.tr_coefs[static_cast<size_t>(slot) * io.tr_cap + s.t] = c;
         if (io.tr_energy && s.t < io.tr_cap) io.tr_energy[static_cast<size_t>(slot) * io.tr_cap + s.t] = e;
         const double cc = static_cast<double>(c);
-        s.audit = fmax(s.audit, fabs(e - (s.e - cc * cc)) / s.e0);
+        s.audit = fmax(s.audit, fabs(e - (s.e - cc * cc)));   // divided by e0 when reported
         s.e = e;
         s.t += 1;   // Eq. 12
         const bool conv = !(e > s.thr2);
@@ -911,7 +911,7 @@ static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, lo
         o.stop_reason = ss.stop_reason;
         o.status = *e->h_err ? *e->h_err : ss.status;
         o.rel_residual = ss.e0 > 0.0 ? std::sqrt(ss.e / ss.e0) : 0.0;
-        o.energy_audit_max = ss.audit;
+        o.energy_audit_max = ss.e0 > 0.0 ? ss.audit / ss.e0 : 0.0;
         if (o.status < 0 && worst == MP_OK) worst = static_cast<mp_status>(o.status);
     }
     if (worst == MP_ERR_TIMEOUT) set_error("a device-side wait in the batched step exceeded the watchdog limit");

@@ -78,7 +78,7 @@ template <typename T>
 struct PlainShared {
     using Key = typename PlainTraits<T>::Key;
     CoopPartials<T> coop;
-    Key keys[2];                         // mode 1: this CTA's key, two-slot ring
+    Key wkeys[2][kMaxWarps];             // mode 1: this CTA's warp keys, two-slot ring
     Key wkey[kMaxWarps];                 // per compute warp best key
     double wsum[kMaxWarps];              // per compute warp energy partial
     Key key;                             // selected key broadcast
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(kMaxPlainThreads, 1) mp_plain_kernel(const Pla
     const Key kzero = {};
 
     if (threadIdx.x == 0) {
-        sh->keys[0] = sh->keys[1] = kzero;
+        for (int w = 0; w < kMaxWarps; ++w) sh->wkeys[0][w] = sh->wkeys[1][w] = kzero;
         if constexpr (FP64) sh->coop.abort[0] = sh->coop.abort[1] = 0;
         sh->abort = 0;
         sh->done = 0;
@@ -426,14 +426,16 @@ __global__ void __launch_bounds__(kMaxPlainThreads, 1) mp_plain_kernel(const Pla
     acc = warp_sum_f64(acc);
     if (lane == 0) sh->wsum[cw] = acc;
     named_bar_sync(1, nct);
+    // warp sums in warp order; only the kSumChains / 32 chain warps carry a
+    // partial (the others hold exact zeros)
     double e = 0.0;
-    for (int w = 0; w < ncw; ++w) e += sh->wsum[w];
+    for (int w = 0; w < kSumChains / 32; ++w) e += sh->wsum[w];
     const double e0 = e;
     const double thr2 = a.eps2 * e0;
     const bool finite0 = isfinite(e0);
 
     int t = 0;
-    double audit = 0.0;
+    double audit = 0.0;    // max |e_t - (e_{t-1} - c^2)|, divided by e0 once at the end
     bool aborted = false;
     bool rank_stop = false;   // OMP: the selected atom lies in the span of those selected
     const int A = a.stage_atoms, D = a.stages;
@@ -599,58 +601,58 @@ __global__ void __launch_bounds__(kMaxPlainThreads, 1) mp_plain_kernel(const Pla
             }
         }
         // ---- CTA max, then grid max
-        if (lane == 0) sh->wkey[cw] = best;
-        named_bar_sync(1, nct);
+        Key key;
         if (CLUSTER) {
-            if (ct == 0) {
-                Key k = kzero;
-                for (int w = 0; w < ncw; ++w) k = kmax(k, sh->wkey[w]);
-                // own slot of a two-slot ring: peers read slot t&1 after this
-                // iteration's cluster barrier and before arriving at the next
-                // one; this CTA rewrites it only at iteration t+2
-                sh->keys[t & 1] = k;
+            // every warp's best goes to its own slot of a two-slot ring; after
+            // the cluster barrier every warp reads all of the cluster's warp
+            // keys over DSMEM (lane l takes entries l, l + 32, ...: CTA
+            // j / ncw, warp j % ncw) and their max is the cluster's key, the
+            // same in every warp of every CTA.  A slot is rewritten only at
+            // iteration t+2, after every warp of the cluster has passed
+            // barrier t+1 and so finished its reads of iteration t
+            if (lane == 0) sh->wkeys[t & 1][cw] = best;
+            cluster_sync_all();
+            Key v = kzero;
+            for (int j = lane; j < G * ncw; j += 32) {
+                Key u;
+                dsmem_ld(mapa_shared(smem_u32(&sh->wkeys[t & 1][j % ncw]), static_cast<uint32_t>(j / ncw)), &u);
+                v = kmax(v, u);
             }
-        } else if constexpr (!FP64) {
-            if (ct == 0) {
-                unsigned long long k = 0ull;
-                for (int w = 0; w < ncw; ++w) k = umax64(k, sh->wkey[w]);
-                unsigned long long g = 0ull;
-                // the grid's winner is one of the CTAs' local bests: start
-                // pulling this one into L2 for the residual update
-                if (k != 0ull) prefetch_l2(a.psi + static_cast<size_t>(key_index(k)) * ldN, ldN * 4u);
-                if (!grid_exchange(a, cta, G, t, t * NB, k, &g)) *reinterpret_cast<volatile int*>(&sh->abort) = 1;
-                sh->key = g;
-            }
+            key = warp_max_key(v);
         } else {
-            if (cw == 0) {
-                const Key k = warp_max_key(lane < ncw ? sh->wkey[lane] : kzero);
-                if (lane == 0 && k.hi != 0ull)
-                    prefetch_l2(a.psi + static_cast<size_t>(key_index(k)) * ldN, ldN * 8u);
-                Key g = kzero;
-                const bool ok = grid_exchange(a, cta, G, t, k, lane, &g);
-                if (lane == 0) {
-                    if (!ok) *reinterpret_cast<volatile int*>(&sh->abort) = 1;
+            if (lane == 0) sh->wkey[cw] = best;
+            named_bar_sync(1, nct);
+            if constexpr (!FP64) {
+                if (ct == 0) {
+                    unsigned long long k = 0ull;
+                    for (int w = 0; w < ncw; ++w) k = umax64(k, sh->wkey[w]);
+                    unsigned long long g = 0ull;
+                    // the grid's winner is one of the CTAs' local bests: start
+                    // pulling this one into L2 for the residual update
+                    if (k != 0ull) prefetch_l2(a.psi + static_cast<size_t>(key_index(k)) * ldN, ldN * 4u);
+                    if (!grid_exchange(a, cta, G, t, t * NB, k, &g)) *reinterpret_cast<volatile int*>(&sh->abort) = 1;
                     sh->key = g;
                 }
+            } else {
+                if (cw == 0) {
+                    const Key k = warp_max_key(lane < ncw ? sh->wkey[lane] : kzero);
+                    if (lane == 0 && k.hi != 0ull)
+                        prefetch_l2(a.psi + static_cast<size_t>(key_index(k)) * ldN, ldN * 8u);
+                    Key g = kzero;
+                    const bool ok = grid_exchange(a, cta, G, t, k, lane, &g);
+                    if (lane == 0) {
+                        if (!ok) *reinterpret_cast<volatile int*>(&sh->abort) = 1;
+                        sh->key = g;
+                    }
+                }
             }
-        }
-        if (CLUSTER) {
-            cluster_sync_all();
-            if (cw == 0) {
-                // lane k reads CTA k's key over DSMEM; the warp max is the
-                // cluster's key (the same value in every CTA)
-                Key v = kzero;
-                if (lane < G) dsmem_ld(mapa_shared(smem_u32(&sh->keys[t & 1]), lane), &v);
-                v = warp_max_key(v);
-                if (lane == 0) sh->key = v;
+            named_bar_sync(1, nct);
+            if (*reinterpret_cast<volatile int*>(&sh->abort)) {
+                aborted = true;
+                break;
             }
+            key = sh->key;
         }
-        named_bar_sync(1, nct);
-        if (*reinterpret_cast<volatile int*>(&sh->abort)) {
-            aborted = true;
-            break;
-        }
-        const Key key = sh->key;
         const int m = key_index(key);
         const T c = key_coef(key);
         if constexpr (GRAM) {
@@ -800,7 +802,7 @@ __global__ void __launch_bounds__(kMaxPlainThreads, 1) mp_plain_kernel(const Pla
         if (lane == 0) sh->wsum[cw] = acc;
         named_bar_sync(1, nct);
         double e_new = 0.0;
-        for (int w = 0; w < ncw; ++w) e_new += sh->wsum[w];
+        for (int w = 0; w < kSumChains / 32; ++w) e_new += sh->wsum[w];
 
         // ---- Eq. 10 and bookkeeping (one thread of CTA 0)
         if (cta == 0 && ct == 0) {
@@ -814,7 +816,10 @@ __global__ void __launch_bounds__(kMaxPlainThreads, 1) mp_plain_kernel(const Pla
                 if (a.tr_energy) a.tr_energy[t] = e_new;
             }
             const double cc = static_cast<double>(step);
-            audit = fmax(audit, fabs(e_new - (e - cc * cc)) / e0);
+            // (e0 > 0 and rounded division is monotonic, so dividing the
+            // maximum once gives the same bits as the maximum of quotients,
+            // without an FP64 division on every iteration's critical path)
+            audit = fmax(audit, fabs(e_new - (e - cc * cc)));
         }
         e = e_new;
         m_prev = m;
@@ -846,7 +851,7 @@ __global__ void __launch_bounds__(kMaxPlainThreads, 1) mp_plain_kernel(const Pla
         res.iters = t;
         res.e0 = e0;
         res.e = e;
-        res.audit_max = audit;
+        res.audit_max = e0 > 0.0 ? audit / e0 : 0.0;
         res.stop_reason = e0 == 0.0 ? MP_STOP_ZERO_Y
                           : rank_stop ? MP_STOP_RANK
                                       : (e <= thr2 ? MP_STOP_CONVERGED : MP_STOP_MAX_ITERS);

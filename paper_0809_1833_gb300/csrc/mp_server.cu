@@ -138,7 +138,7 @@ static void retire(mp_server_s* srv, Dict* d) {
         r->res.stop_reason = s.stop_reason;
         r->res.status = s.status;
         r->res.rel_residual = s.e0 > 0.0 ? std::sqrt(s.e / s.e0) : 0.0;
-        r->res.energy_audit_max = s.audit;
+        r->res.energy_audit_max = s.e0 > 0.0 ? s.audit / s.e0 : 0.0;
         r->done = true;
         r->t_done = now;
         srv->completed++;
