@@ -5,9 +5,9 @@
 // residual r in shared memory.  Per iteration:
 //   1. correlate  c_m = <r, psi_m> for the CTA's atoms       (Eq. 9)
 //   2. select     the CTA's best packed key (|c|, -m, sign)  (Eq. 9, Sec. 4 ties)
-//   3. exchange   the grid-wide max key (a hardware cluster barrier, then one
-//                 warp reads every CTA's key over DSMEM; or global atomics and
-//                 a bounded grid barrier)
+//   3. exchange   the grid-wide max key (a hardware cluster barrier, then every
+//                 warp reads all of the cluster's warp keys over DSMEM; or
+//                 global atomics and a bounded grid barrier)
 //   4. update     every CTA applies r -= c psi_m* to its own copy of r
 //                 (identical arithmetic in every CTA, so all copies stay
 //                 bit-identical) and reduces e = sum r^2 in FP64   (Eq. 11)
@@ -21,7 +21,10 @@
 //   mode 3  one CTA per SM; a producer warp streams the CTA's atoms from HBM
 //           through a ring of shared-memory stages with 1-D bulk copies and
 //           mbarriers, running ahead across iteration boundaries so that the
-//           exchange/update bubble overlaps the next pass's loads.
+//           exchange/update bubble overlaps the next pass's loads.  Consumer
+//           warps own whole-atom slots; in FP64 with large atoms, groups of 4
+//           warps share each stage instead (one class of segments per warp)
+//           and an atom streams as several stages.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
