@@ -278,19 +278,84 @@ MP_DEV float dot1_scaled(const float* __restrict__ w, float s, const float* __re
 // ------------------------------------------------------------------ producer
 template <typename T>
 MP_DEV void plain_producer(const PlainArgs<T>& a, PlainShared<T>* sh, T* ring, int a0, int na) {
-    const int A = a.stage_atoms, D = a.stages, ldN = a.ldN, np = a.pieces;
-    // stages per pass over the CTA's atoms: A whole atoms each, or (np > 1)
-    // one piece of one atom each
-    const int S = np > 1 ? na * np : (na + A - 1) / A;
+    const int A = a.stage_atoms, D = a.stages, ldN = a.ldN;
+    const int S = (na + A - 1) / A;
     if (S == 0) return;
+    const size_t stage_elems = static_cast<size_t>(A) * ldN;
+    const uint64_t pol = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
+    volatile int* vdone = &sh->done;
+    long long seq = 0;
+    while (true) {
+        const int slot = static_cast<int>(seq % D);
+        if (seq >= D) {
+            const uint32_t par = static_cast<uint32_t>(((seq / D) - 1) & 1);
+            bool ok = mbar_try_wait(&sh->empty[slot], par);
+            uint64_t deadline = 0;
+            while (!ok) {
+                if (*vdone) break;
+                const uint64_t now = globaltimer_ns();
+                if (deadline == 0) {
+                    deadline = now + a.watchdog_ns;
+                } else if (now > deadline) {
+                    atomicCAS(&a.ws->err, 0, static_cast<int>(MP_ERR_TIMEOUT));
+                    *reinterpret_cast<volatile int*>(&sh->abort) = 1;
+                    break;
+                }
+                ok = mbar_try_wait(&sh->empty[slot], par);
+            }
+            if (!ok) break;
+        }
+        if (*vdone) break;
+        const int j = static_cast<int>(seq % S);
+        const int atom0 = a0 + j * A;
+        const int nat = min(A, na - j * A);
+        const uint32_t bytes = static_cast<uint32_t>(nat) * ldN * static_cast<uint32_t>(sizeof(T));
+        mbar_arrive_expect_tx(&sh->full[slot], bytes);
+        // the first l2_keep_atoms atoms of the slice stay in L2 from pass to
+        // pass (evict-last); the rest streams through it (evict-first)
+        if (j * A < a.l2_keep_atoms)
+            bulk_g2s_hint(ring + slot * stage_elems, a.psi + static_cast<size_t>(atom0) * ldN, bytes,
+                          &sh->full[slot], pol_keep);
+        else if (a.evict_first)
+            bulk_g2s_hint(ring + slot * stage_elems, a.psi + static_cast<size_t>(atom0) * ldN, bytes,
+                          &sh->full[slot], pol);
+        else
+            bulk_g2s(ring + slot * stage_elems, a.psi + static_cast<size_t>(atom0) * ldN, bytes, &sh->full[slot]);
+        // L2 as a deeper window than the shared-memory ring: pull the stage
+        // `prefetch` positions ahead into L2 now, so HBM keeps streaming
+        // while the ring is full during the per-iteration exchange.
+        if (a.prefetch > 0) {
+            const int jp = static_cast<int>((seq + a.prefetch) % S);
+            const int np = min(A, na - jp * A);
+            prefetch_l2(a.psi + static_cast<size_t>(a0 + jp * A) * ldN,
+                        static_cast<uint32_t>(np) * ldN * static_cast<uint32_t>(sizeof(T)));
+        }
+        ++seq;
+    }
+    // Wait for every copy still in flight before the CTA may exit: the only
+    // outstanding copy of slot k is the last one issued into it.
+    const long long issued = seq;
+    for (int k = 0; k < D && k < issued; ++k) {
+        const long long last = issued - 1 - ((issued - 1 - k) % D);
+        mbar_wait_bounded(&sh->full[k], static_cast<uint32_t>((last / D) & 1), a.watchdog_ns);
+    }
+}
+
+// The same for the FP64 shared-stage shape: stage j of a pass is piece
+// j % np of atom j / np (np >= 1), stages piece_elems elements apart.
+template <typename T>
+MP_DEV void plain_producer_shared(const PlainArgs<T>& a, PlainShared<T>* sh, T* ring, int a0, int na) {
+    const int D = a.stages, ldN = a.ldN, np = a.pieces;
+    if (na == 0) return;
     const size_t stage_elems = static_cast<size_t>(a.stage_elems);
     const uint64_t pol = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
     volatile int* vdone = &sh->done;
     // ring position (slot, parity of its use count) and stage (atom, piece),
-    // kept incrementally: this single thread must not stall on divisions
+    // kept incrementally
     long long seq = 0;
-    int slot = 0, j = 0, ja = 0, jp = 0;
+    int slot = 0, ja = 0, jp = 0;
     uint32_t upar = 0;
     while (true) {
         if (seq >= D) {
@@ -312,10 +377,10 @@ MP_DEV void plain_producer(const PlainArgs<T>& a, PlainShared<T>* sh, T* ring, i
             if (!ok) break;
         }
         if (*vdone) break;
-        // this stage: A atoms from atom0, or piece jp of atom ja
-        const int atom0 = np > 1 ? a0 + ja : a0 + j * A;
-        const size_t off = np > 1 ? static_cast<size_t>(jp) * a.piece_elems : 0;
-        const int nel = np > 1 ? min(a.piece_elems, ldN - jp * a.piece_elems) : min(A, na - j * A) * ldN;
+        // this stage: piece jp of atom ja
+        const int atom0 = a0 + ja;
+        const size_t off = static_cast<size_t>(jp) * a.piece_elems;
+        const int nel = min(a.piece_elems, ldN - jp * a.piece_elems);
         const uint32_t bytes = static_cast<uint32_t>(nel) * static_cast<uint32_t>(sizeof(T));
         const T* src = a.psi + static_cast<size_t>(atom0) * ldN + off;
         mbar_arrive_expect_tx(&sh->full[slot], bytes);
@@ -327,23 +392,12 @@ MP_DEV void plain_producer(const PlainArgs<T>& a, PlainShared<T>* sh, T* ring, i
             bulk_g2s_hint(ring + slot * stage_elems, src, bytes, &sh->full[slot], pol);
         else
             bulk_g2s(ring + slot * stage_elems, src, bytes, &sh->full[slot]);
-        // L2 as a deeper window than the shared-memory ring: pull the stage
-        // `prefetch` positions ahead into L2 now, so HBM keeps streaming
-        // while the ring is full during the per-iteration exchange (whole
-        // atoms per stage only)
-        if (a.prefetch > 0 && np == 1) {
-            const int jq = static_cast<int>((seq + a.prefetch) % S);
-            const int nq = min(A, na - jq * A);
-            prefetch_l2(a.psi + static_cast<size_t>(a0 + jq * A) * ldN,
-                        static_cast<uint32_t>(nq) * ldN * static_cast<uint32_t>(sizeof(T)));
-        }
         ++seq;
         if (++slot == D) {
             slot = 0;
             upar ^= 1u;
         }
-        if (++j == S) j = 0;
-        if (np > 1 && ++jp == np) {
+        if (++jp == np) {
             jp = 0;
             if (++ja == na) ja = 0;
         }
@@ -406,7 +460,10 @@ __global__ void __launch_bounds__(kMaxPlainThreads, 1) mp_plain_kernel(const Pla
     __syncthreads();
 
     if (STREAM && warp == 0) {
-        if (lane == 0) plain_producer(a, sh, data, a0, na);
+        if (lane == 0) {
+            if (a.coop) plain_producer_shared(a, sh, data, a0, na);
+            else plain_producer(a, sh, data, a0, na);
+        }
         return;
     }
 
