@@ -782,8 +782,9 @@ __global__ void __launch_bounds__(kMaxPlainThreads, 1) mp_plain_kernel(const Pla
                     if (lane == 0) sh->wsum[cw] = nacc;
                     named_bar_sync(1, nct);
                     if (ct == 0) {
+                        // the chain warps' sums in warp order (the others hold zeros)
                         double sum = 0.0;
-                        for (int q = 0; q < ncw; ++q) sum += sh->wsum[q];
+                        for (int q = 0; q < kSumChains / 32; ++q) sum += sh->wsum[q];
                         a.nrm[cta] = sum;
                     }
                 }
@@ -795,19 +796,28 @@ __global__ void __launch_bounds__(kMaxPlainThreads, 1) mp_plain_kernel(const Pla
             }
             if (aborted) break;
             if (ok) {
-                // ||w2||^2 in one fixed order: the same value in every CTA
-                // (broadcast through the last two wsum slots, which no warp
-                // index reaches: at most 8 compute warps)
-                if (ct == 0) {
+                // ||w2||^2 in one fixed order, the same value in every CTA:
+                // lane l of warp 0 sums the CTA partials l, l + 32, ... in
+                // turn, then the warp butterfly; lane 0 also takes sqrt and
+                // its reciprocal once for the CTA.  Broadcast through the
+                // last wsum slots, which no warp index reaches (at most 9
+                // warps)
+                if (cw == 0) {
                     double sum = 0.0;
-                    for (int q = 0; q < G; ++q) sum += a.nrm[q];
-                    sh->wsum[kMaxWarps - 1] = sum;
+                    for (int q = lane; q < G; q += 32) sum += a.nrm[q];
+                    sum = warp_sum_f64(sum);
+                    if (lane == 0) {
+                        const double rt = sqrt(sum);
+                        sh->wsum[kMaxWarps - 1] = sum;
+                        sh->wsum[kMaxWarps - 3] = rt;
+                        sh->wsum[kMaxWarps - 4] = 1.0 / rt;
+                    }
                 }
                 named_bar_sync(1, nct);
                 const double nw2 = sh->wsum[kMaxWarps - 1];
                 // unit atoms: a component below 1e-4 is rounding, not a new direction
                 if (!(nw2 > 1e-8)) rank_stop = true;
-                else qscale = static_cast<T>(1.0 / sqrt(nw2));
+                else qscale = static_cast<T>(sh->wsum[kMaxWarps - 4]);
                 if (!rank_stop) {
                     if (cw == 0) {
                         const T al = dot1_scaled(a.w2, qscale, r, ldN, lane);
@@ -821,7 +831,7 @@ __global__ void __launch_bounds__(kMaxPlainThreads, 1) mp_plain_kernel(const Pla
                         const size_t ck = static_cast<size_t>(k) * (k + 1) / 2;
                         for (int j = ct; j < k; j += nct) a.Rc[ck + j] = a.h[j] + a.h2[j];
                         if (ct == 0) {
-                            a.Rc[ck + k] = static_cast<T>(sqrt(nw2));
+                            a.Rc[ck + k] = static_cast<T>(sh->wsum[kMaxWarps - 3]);
                             a.alpha[k] = step;
                             a.sel[k] = m;
                         }
