@@ -218,6 +218,14 @@ struct SelArgs {
     int* fin_list;
 };
 
+// Asynchronous 16-byte global -> shared copies (completed by cp_async_wait_all
+// in the issuing thread, made visible to the block by a barrier after it).
+MP_DEV void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+MP_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+MP_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // A candidate entry (score bits, atom) as a key ordering larger scores
 // first, then smaller atoms; 0 for an empty entry (atom >= M).
 MP_DEV unsigned long long cand_key(uint32_t score_bits, uint32_t atom, int M) {
@@ -281,7 +289,9 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
     float4* rg4 = reinterpret_cast<float4*>(a.R32 + static_cast<size_t>(slot) * a.ldN);
     const int n4 = a.ldN / 4;
     SlotState s = a.st[slot];   // loaded now, used after the rescore
-    for (int k = threadIdx.x; k < n4; k += blockDim.x) rs4[k] = rg4[k];
+    // r streams into shared memory while the candidate lists are merged
+    for (int k = threadIdx.x; k < n4; k += blockDim.x) cp_async16(rs4 + k, rg4 + k);
+    cp_async_commit();
 
     // merge the sorted per-tile lists: keys (score bits, ~atom) order by
     // score, then by the smaller atom.  Thread t folds lists t, t + THREADS,
@@ -334,6 +344,7 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
                     top[k] = lk[k] ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(lk[k])) : -1;
         }
     }
+    cp_async_wait_all();
     __syncthreads();
     // rescore the candidates in FP32 from the FP32 atoms (Eq. 9), in the
     // plain kernel's correlation order; a warp takes candidates w and
