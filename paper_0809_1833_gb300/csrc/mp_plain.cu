@@ -1067,7 +1067,7 @@ static mp_status plain_configure_t(PlanImpl* p, PlainConfig* cfg, bool omp = fal
     long long D = std::min<long long>(kMaxStages, budget / stage_bytes);
     const int W = kSumChains / 32;
     // FP64 is bound by the FP64 units, not by HBM: keep all 4 SM sub-
-    // partitions' FP64 pipes fed.  For atoms of 16 KB or more, or when the
+    // partitions' FP64 pipes fed.  For atoms of 8 KB or more, or when the
     // ring cannot give every warp two whole-atom slots (its next atom
     // loading while it computes one), 4 warps share every stage, one class
     // of segments each, an atom streams as pieces of whole 4-segment groups
@@ -1078,7 +1078,7 @@ static mp_status plain_configure_t(PlanImpl* p, PlainConfig* cfg, bool omp = fal
     // of whole atoms.
     int groups = 1;
     if (sizeof(T) == 8 && !omp) {
-        if (atom_bytes >= 16384 || budget < 2LL * W * atom_bytes) {
+        if (atom_bytes >= 8192 || budget < 2LL * W * atom_bytes) {
             const long long nseg = (p->ldN + 63) / 64;
             long long np = std::max<long long>(1, (atom_bytes + p->stage_bytes - 1) / p->stage_bytes);
             const long long spp = ((nseg + np - 1) / np + 3) / 4 * 4;

@@ -91,11 +91,11 @@ def test_fp64_modes_agree_bitwise():
         assert np.array_equal(o["energies"], outs[0]["energies"])
 
 
-@pytest.mark.parametrize("case", [(3500, 600, 1), (4500, 600, 2), (7500, 300, 2), (9000, 150, 3)],
+@pytest.mark.parametrize("case", [(1500, 600, 1), (3500, 600, 1), (4500, 600, 2), (7500, 300, 2), (9000, 150, 3)],
                          ids=lambda c: f"N{c[0]}_pieces{c[2]}")
 def test_fp64_cooperative_stream_matches_resident_bitwise(case):
-    """FP64 atoms too large for two ring slots per consumer warp (28, 36,
-    60 and 72 KB): 4 warps share every stage, each summing one class of
+    """FP64 atoms of 8 KB and more (12, 28, 36, 60 and 72 KB here): 4 warps
+    share every stage, each summing one class of
     segments (the FP64 correlation order is defined by those classes),
     atoms above 32 KB stream as pieces of whole 4-segment groups, the
     warps' chains running on across the pieces, and where the ring holds
