@@ -250,3 +250,25 @@ def test_batched_edge_cases():
         # precision that the plan does not hold
         s, _, _, _, _ = run_batched(pl, B().MP_PREC_FP8E4M3, prob.y[:1], (1e-5, 500))
         assert s == B().MP_ERR_UNSUPPORTED
+
+
+def test_gemm_timing_diagnostic():
+    """mp_debug_time_gemm times every valid tile shape (and the shape a batch
+    would use) and rejects bad shapes, arguments and precisions the plan does
+    not hold with the documented status codes."""
+    psi = W.gaussian_dictionary(256, 2048, seed=9)
+    p = B().MP_PREC_BF16
+    with GpuPlan(psi, prec_mask=1 << p) as pl:
+        for shape in [(0, 0, 0)] + [t for t in TILES]:
+            us = B().mp_debug_time_gemm(pl.plan, p, 300, shape, reps=3)
+            assert 0.0 < us < 1e6, (shape, us)
+        for bad in [(256, 256, 2), (192, 256, 1), (128, 64, 1), (128, 256, 3)]:
+            with pytest.raises(B().MpError) as ei:
+                B().mp_debug_time_gemm(pl.plan, p, 300, bad, reps=3)
+            assert ei.value.status == B().MP_ERR_INVALID, bad
+        with pytest.raises(B().MpError) as ei:
+            B().mp_debug_time_gemm(pl.plan, p, 0, (0, 0, 0), reps=3)
+        assert ei.value.status == B().MP_ERR_INVALID
+        with pytest.raises(B().MpError) as ei:
+            B().mp_debug_time_gemm(pl.plan, B().MP_PREC_FP8E4M3, 300, (0, 0, 0), reps=3)
+        assert ei.value.status == B().MP_ERR_UNSUPPORTED
