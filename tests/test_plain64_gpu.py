@@ -183,9 +183,15 @@ def test_fp64_needs_the_fp64_copy():
         assert s == B().MP_ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("mode", [2, 3])
-def test_fp64_watchdog_times_out_and_context_survives(mode):
-    prob = W.make_plain(256, 4096, 10, seed=8, eps=1e-9, T=1000)
+@pytest.mark.parametrize("case", [(256, 2), (256, 3), (4500, 3)], ids=lambda c: f"N{c[0]}_mode{c[1]}")
+def test_fp64_watchdog_times_out_and_context_survives(case):
+    """One CTA skips its first grid-barrier arrival: every other CTA's bounded
+    wait expires, the call returns MP_ERR_TIMEOUT and the next call on the
+    same plan decodes normally.  N = 4500 runs the shared-stage shape (two
+    groups of 4 warps, atoms in 2 pieces), whose producer and consumers must
+    leave cleanly too."""
+    N, mode = case
+    prob = W.make_plain(N, 4096 if N <= 256 else 600, 10, seed=8, eps=1e-9, T=1000)
     y = prob.y[0].astype(np.float64)
     with plan64(prob.psi, mode) as pl:
         pl.set(B().MP_OPT_WATCHDOG_NS, 50_000_000)
