@@ -894,6 +894,8 @@ def main():
     ap.add_argument("--profile64", type=int, nargs=2, metavar=("M", "ITERS"), default=None,
                     help="profiling case: Sec. 4's FP64 problem at M, one decode capped at ITERS, then exit")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-only", type=int, default=0, metavar="REPEATS",
+                    help="print only the batched BF16 and FP8 lines, REPEATS times")
     ap.add_argument("--served-duration", type=float, default=10.0,
                     help="seconds of Poisson arrivals for the served measurement (0 = skip)")
     ap.add_argument("--served-rate", type=float, default=2000.0)
@@ -935,6 +937,13 @@ def main():
     if args.profile_gemm:
         shape = tuple(int(v) for v in args.profile_shape.split(","))
         print(json.dumps(gemm_profile_case(args.profile_gemm, shape)))
+        return
+    if args.batched_only:
+        import __graft_entry__
+        __graft_entry__.build()
+        for _ in range(args.batched_only):
+            for prec in ("bf16", "fp8"):
+                print(json.dumps(batched_measure(prec, n_plain=2)))
         return
     if args.profile_batched:
         import __graft_entry__

@@ -46,6 +46,7 @@ struct CorrArgs {
     int* err;
     float* dump;            // diagnostic: full correlation rows (row * M + m), or NULL
     const float* rscale;    // diagnostic FP8: per-row scale of the quantised residual
+    int* zero_next;         // step: the other half's survivor count, set to 0 here (or NULL)
 };
 
 int corr_smem_bytes(int TM, int TN);
@@ -79,6 +80,15 @@ struct BatchIO {
 // Device state of `cap` decode slots over one dictionary at one precision:
 // FP32 residuals, the quantised GEMM operand (one row per active signal),
 // the active-row table, candidates, slot states, and the step graph.
+//
+// The operand and the active-row table have two halves.  A step reads half p
+// (rows 0..counters[p ? 3 : 0]-1) and every signal still running after it
+// takes the next free row of half 1-p with one atomic, writing its slot id
+// and quantised residual there; so the next step's rows are compact without
+// a separate compaction pass.  Step graphs hold an even number of steps, so
+// between graph launches (admission, the host's reads) the current half is 0.
+// The order of rows within a half does not change any signal's result: every
+// row's products, top-8 and update are its own.
 struct BatchEngine {
     int cap = 0;            // slots (= GEMM rows available)
     int cap_pad = 0;        // rows of the GEMM operand (multiple of 128)
@@ -89,10 +99,10 @@ struct BatchEngine {
     int n_at = 0;
     int ldq = 0;            // operand row: elements (BF16) or bytes (FP8)
     float* R32 = nullptr;
-    void* Rq = nullptr;
+    void* Rq = nullptr;        // 2 x cap_pad operand rows (half 0, then half 1)
     SlotState* st = nullptr;
-    int* act = nullptr;
-    int* counters = nullptr;   // [0] active rows, [1] rows just admitted, [2] finished count
+    int* act = nullptr;        // 2 x cap slot ids by row (half 0, then half 1)
+    int* counters = nullptr;   // [0] rows of half 0, [1] rows just admitted, [2] finished count, [3] rows of half 1
     int* done = nullptr;
     int* holes = nullptr;
     int* surv = nullptr;
@@ -109,7 +119,7 @@ struct BatchEngine {
     int* h_T = nullptr;
     BatchIO* h_io = nullptr;
     int* h_err = nullptr;
-    CUtensorMap tmA, tmB;
+    CUtensorMap tmA, tmA1, tmB;   // operand half 0, half 1, atoms
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
     bool graph_retire = false;

@@ -43,7 +43,7 @@ constexpr int kSelThreads = 256;
 constexpr int kSumChains = 128;
 constexpr int kSelectWideLd = 4096;
 constexpr int kFixThreads = 1024;
-constexpr int kStepsPerGraph = 16;
+constexpr int kStepsPerGraph = 16;   // even: every graph starts and ends on operand half 0
 
 // ------------------------------------------------------------------ block helpers
 MP_DEV double block_sum_f64(double v, double* red) {
@@ -202,9 +202,11 @@ __global__ void __launch_bounds__(kSelThreads) admit_kernel(const AdmitArgs a) {
 
 // ------------------------------------------------------------------ select / rescore / update
 struct SelArgs {
-    const int* n_act;
-    const int* act;
-    int* done;              // by row
+    const int* n_act;       // rows of this step's half
+    const int* act;         // this half's slot ids by row
+    int* n_next;            // survivors take rows of the other half:
+    int* act_next;          //   its row count, slot ids
+    void* Rq_next;          //   and quantised operand rows
     const uint2* cand;
     int n_at;
     const float* psi32;
@@ -212,7 +214,6 @@ struct SelArgs {
     float* R32;
     const BatchIO* io;
     SlotState* st;
-    void* Rq;
     int ldq, fp8;
     int* fin_count;         // optional: slots that stopped this step are appended here
     int* fin_list;
@@ -373,11 +374,11 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
     __syncthreads();
     unsigned long long kbest = 0ull;
     for (int w = 0; w < kTop; ++w) kbest = umax64(kbest, rkey[w]);
-    if (kbest == 0ull) {   // no candidate: nothing can be selected
+    if (kbest == 0ull) {   // no candidate: nothing can be selected; the signal leaves
         if (threadIdx.x == 0) {
             s.status = MP_ERR_INVALID;
             a.st[slot] = s;
-            a.done[i] = 1;
+            if (a.fin_list) a.fin_list[atomicAdd(a.fin_count, 1)] = slot;
         }
         return;
     }
@@ -390,9 +391,9 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
         io = *a.io;
         xm = io.X[static_cast<size_t>(slot) * io.ldx + m];
     }
-    // Eq. 11 in FP32, the FP64 energy, and (BF16) the requantised row
+    // Eq. 11 in FP32, the FP64 energy, then the requantised row of a signal
+    // that runs on
     const float4* pm = reinterpret_cast<const float4*>(a.psi32 + static_cast<size_t>(m) * a.ldN);
-    char* qrow = static_cast<char*>(a.Rq) + static_cast<size_t>(i) * a.ldq * (a.fp8 ? 1 : 2);
     for (int k = threadIdx.x; k < n4; k += THREADS) {
         const float4 p = __ldg(pm + k);
         float4 v = rs4[k];
@@ -402,11 +403,6 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
         v.w = fmaf(-c, p.w, v.w);
         rg4[k] = v;
         rs4[k] = v;
-        if (!a.fp8) {
-            __nv_bfloat162* q2 = reinterpret_cast<__nv_bfloat162*>(qrow) + 2 * k;
-            q2[0] = __floats2bfloat162_rn(v.x, v.y);
-            q2[1] = __floats2bfloat162_rn(v.z, v.w);
-        }
     }
     if (THREADS != kSumChains) __syncthreads();   // the chains read other threads' updates
     double acc = 0.0;
@@ -419,7 +415,7 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
             acc = fma(static_cast<double>(v.w), static_cast<double>(v.w), acc);
         }
     const double e = block_sum_f64(acc, redd);   // also orders the smem r writes
-    if (a.fp8) block_quantize(r, a.ldN, qrow, a.ldq, 1, redf);
+    __shared__ int next_row;
     if (threadIdx.x == 0) {
         io.X[static_cast<size_t>(slot) * io.ldx + m] = xm + c;   // Eq. 10
         if (io.tr_atoms && s.t < io.tr_cap) io.tr_atoms[static_cast<size_t>(slot) * io.tr_cap + s.t] = m;
@@ -433,15 +429,39 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
         const bool stop = conv || s.t >= s.T;
         if (stop) s.stop_reason = conv ? MP_STOP_CONVERGED : MP_STOP_MAX_ITERS;
         a.st[slot] = s;
-        a.done[i] = stop ? 1 : 0;
-        if (stop && a.fin_list) a.fin_list[atomicAdd(a.fin_count, 1)] = slot;
+        int row = -1;
+        if (!stop) {
+            row = atomicAdd(a.n_next, 1);
+            a.act_next[row] = slot;
+        } else if (a.fin_list) {
+            a.fin_list[atomicAdd(a.fin_count, 1)] = slot;
+        }
+        next_row = row;
+    }
+    __syncthreads();
+    const int row = next_row;
+    if (row < 0) return;
+    char* qrow = static_cast<char*>(a.Rq_next) + static_cast<size_t>(row) * a.ldq * (a.fp8 ? 1 : 2);
+    if (a.fp8) {
+        block_quantize(r, a.ldN, qrow, a.ldq, 1, redf);
+    } else {
+        // the first ldN elements; the row's zero padding up to ldq is never
+        // written after the operand's allocation
+        for (int k = threadIdx.x; k < n4; k += THREADS) {
+            const float4 v = rs4[k];
+            __nv_bfloat162* q2 = reinterpret_cast<__nv_bfloat162*>(qrow) + 2 * k;
+            q2[0] = __floats2bfloat162_rn(v.x, v.y);
+            q2[1] = __floats2bfloat162_rn(v.z, v.w);
+        }
     }
 }
 
 // ------------------------------------------------------------------ fixup (one CTA)
-// Rows 0..n-1 with n = *n_act + *n_extra; rows with done set leave.  Holes
-// below the new count n' are filled, in order, with the surviving rows at or
-// above n' (moving the slot id and the quantised GEMM row).
+// After an admission, on operand half 0 (between steps the select kernel
+// keeps the rows compact itself).  Rows 0..n-1 with n = *n_act + *n_extra;
+// rows with done set leave.  Holes below the new count n' are filled, in
+// order, with the surviving rows at or above n' (moving the slot id and the
+// quantised GEMM row).
 struct FixupArgs {
     int* n_act;
     int* n_extra;
@@ -523,8 +543,8 @@ __global__ void __launch_bounds__(kFixThreads) fixup_kernel(const FixupArgs a) {
         for (int o = lane; o < a.ldq_bytes / 16; o += 32) dst[o] = src[o];
     }
     // every remaining row is active: clear the flags (a filled hole still
-    // holds its old flag, and admission can run another fixup before the
-    // next select rewrites them)
+    // holds its old flag, and the steps never write them, so the next
+    // admission's fixup reads these rows as running)
     for (int k = threadIdx.x; k < n_new; k += blockDim.x) a.done[k] = 0;
     if (threadIdx.x == 0) {
         *a.n_act = n_new;
@@ -619,8 +639,8 @@ size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x) {
     const bool fp8 = prec == MP_PREC_FP8E4M3;
     const size_t TN = 128;   // the narrowest tile the shape choice may pick (most candidate lists)
     const size_t n_at = (p->M + TN - 1) / TN;
-    return sizeof(float) * p->ldN + (fp8 ? p->ldK8 : 2 * p->ldK16) + sizeof(uint2) * n_at * kTop +
-           sizeof(SlotState) + 6 * sizeof(int) + sizeof(double) + sizeof(float) + (with_x ? sizeof(float) * p->M : 0);
+    return sizeof(float) * p->ldN + 2 * (fp8 ? p->ldK8 : 2 * p->ldK16) + sizeof(uint2) * n_at * kTop +
+           sizeof(SlotState) + 7 * sizeof(int) + sizeof(double) + sizeof(float) + (with_x ? sizeof(float) * p->M : 0);
 }
 
 mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_t st, GemmShape* out);
@@ -675,9 +695,9 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
         r = cudaMalloc(reinterpret_cast<void**>(ptr), b);
     };
     A(&e->R32, sizeof(float) * C * p->ldN);
-    A(reinterpret_cast<char**>(&e->Rq), qbytes);
+    A(reinterpret_cast<char**>(&e->Rq), 2 * qbytes);
     A(&e->st, sizeof(SlotState) * C);
-    A(&e->act, sizeof(int) * C);
+    A(&e->act, 2 * sizeof(int) * C);
     A(&e->counters, sizeof(int) * 4);
     A(&e->done, sizeof(int) * C);
     A(&e->holes, sizeof(int) * C);
@@ -695,13 +715,14 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     if (r == cudaSuccess) r = cudaMallocHost(&e->h_T, sizeof(int) * C);
     if (r == cudaSuccess) r = cudaMallocHost(&e->h_io, sizeof(BatchIO));
     if (r == cudaSuccess) r = cudaMallocHost(&e->h_err, sizeof(int));
-    if (r == cudaSuccess) r = cudaMemset(e->Rq, 0, qbytes);
+    if (r == cudaSuccess) r = cudaMemset(e->Rq, 0, 2 * qbytes);
     if (r == cudaSuccess) r = cudaMemset(e->counters, 0, sizeof(int) * 4);
     if (r != cudaSuccess) {
         engine_free(e);
         return cuda_fail(r, "batched engine allocation");
     }
     mp_status s = make_map(&e->tmA, e->Rq, fp8, e->cap_pad, e->ldq, kBM);
+    if (s == MP_OK) s = make_map(&e->tmA1, static_cast<char*>(e->Rq) + qbytes, fp8, e->cap_pad, e->ldq, kBM);
     // each CTA of a GEMM cluster loads TN / CL atom rows and multicasts them
     if (s == MP_OK) s = make_map(&e->tmB, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, TN / e->CL);
     if (s != MP_OK) {
@@ -750,16 +771,24 @@ static cudaError_t launch_fixup(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// One step: GEMM + top-8, select/rescore/update, fixup.
-static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
+// One step on operand half `half`: GEMM + top-8, then select / rescore /
+// update, which moves the signals that run on into the other half.
+static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, cudaStream_t st) {
     int* fin_count = e->counters + 2;
     int* fin_list = e->fin_list;
-    cudaError_t r = launch_corr_top8(e->tmA, e->tmB, corr_args(p, e), e->cap_pad, e->CL, st);
+    int* cnt[2] = {e->counters, e->counters + 3};
+    const size_t qbytes = static_cast<size_t>(e->cap_pad) * e->ldq * (e->prec == MP_PREC_FP8E4M3 ? 1 : 2);
+    CorrArgs ca = corr_args(p, e);
+    ca.n_act = cnt[half];
+    ca.zero_next = cnt[1 - half];
+    cudaError_t r = launch_corr_top8(half ? e->tmA1 : e->tmA, e->tmB, ca, e->cap_pad, e->CL, st);
     if (r != cudaSuccess) return r;
     SelArgs sa;
-    sa.n_act = e->counters;
-    sa.act = e->act;
-    sa.done = e->done;
+    sa.n_act = cnt[half];
+    sa.act = e->act + static_cast<size_t>(half) * e->cap;
+    sa.n_next = cnt[1 - half];
+    sa.act_next = e->act + static_cast<size_t>(1 - half) * e->cap;
+    sa.Rq_next = static_cast<char*>(e->Rq) + (1 - half) * qbytes;
     sa.cand = e->cand;
     sa.n_at = e->n_at;   // sorted candidate lists per signal (one per atom tile)
     sa.psi32 = p->psi32;
@@ -769,7 +798,6 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
     sa.R32 = e->R32;
     sa.io = e->io;
     sa.st = e->st;
-    sa.Rq = e->Rq;
     sa.ldq = e->ldq;
     sa.fp8 = e->prec == MP_PREC_FP8E4M3 ? 1 : 0;
     sa.fin_count = fin_count;
@@ -778,12 +806,12 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
         select_update_kernel<kSumChains><<<e->cap, kSumChains, p->ldN * sizeof(float), st>>>(sa);
     else
         select_update_kernel<2 * kSumChains><<<e->cap, 2 * kSumChains, p->ldN * sizeof(float), st>>>(sa);
-    if ((r = cudaGetLastError()) != cudaSuccess) return r;
-    return launch_fixup(p, e, st);
+    return cudaGetLastError();
 }
 
 mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire, float* out_x, SlotState* out_state,
                              int* out_list, int* out_count) {
+    if (steps <= 0 || steps % 2) return fail(MP_ERR_INVALID, "batched step graph: an even number of steps");
     if (e->graph && e->graph_steps == steps && e->graph_retire == retire) return MP_OK;
     if (e->graph) {
         cudaGraphExecDestroy(e->graph);
@@ -799,7 +827,7 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
     }
     MP_CUDA_TRY(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t r = cudaSuccess;
-    for (int s = 0; s < steps && r == cudaSuccess; ++s) r = launch_step(p, e, e->cap_stream);
+    for (int s = 0; s < steps && r == cudaSuccess; ++s) r = launch_step(p, e, s & 1, e->cap_stream);
     if (retire && r == cudaSuccess) {
         RetireArgs ra;
         ra.fin_count = e->counters + 2;
@@ -908,7 +936,7 @@ static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, lo
         MP_CUDA_TRY(cudaStreamSynchronize(st));
         if (e->h_cnt[0] == 0) break;
         MP_CUDA_TRY(cudaGraphLaunch(e->graph, st));
-        p->launches += 3 * kStepsPerGraph;
+        p->launches += 2 * kStepsPerGraph;
     }
     MP_CUDA_TRY(cudaMemcpyAsync(e->h_st, e->st, sizeof(SlotState) * B, cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaMemcpyAsync(e->h_err, e->err, sizeof(int), cudaMemcpyDeviceToHost, st));

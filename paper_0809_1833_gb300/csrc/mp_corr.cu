@@ -394,6 +394,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     x.q = CL > 1 ? static_cast<int>(cluster_ctarank()) : 0;     // rank in the cluster
     x.cid = static_cast<int>(blockIdx.x) / CL;
     x.n_clusters = static_cast<int>(gridDim.x) / CL;
+    // the step's select kernel appends its survivors to the other half; its
+    // count was last read by the previous step, which has completed
+    if (a.zero_next && blockIdx.x == 0 && threadIdx.x == 0) *a.zero_next = 0;
     x.n_act = *a.n_act;
     x.n_blk = (x.n_act + kBM - 1) / kBM;     // 128-row blocks holding active rows
     const int rm = (RM == 2 && x.n_blk * a.n_at > static_cast<int>(gridDim.x)) ? 2 : 1;

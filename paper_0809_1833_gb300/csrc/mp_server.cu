@@ -213,7 +213,7 @@ static void scheduler(mp_server_s* srv) {
                     srv->fault.store(static_cast<int>(MP_ERR_CUDA));
                     continue;
                 }
-                d->p->launches += 3 * srv->steps + 2;
+                d->p->launches += 2 * srv->steps + 1;   // the steps' kernels and the retire kernel
                 srv->chunks++;
                 d->inflight = true;
                 busy = true;
