@@ -274,6 +274,38 @@ MP_DEV void dot1_pair(const float* __restrict__ p0, const float* __restrict__ p1
     d1 = warp_sum_f32((bx + by) + (bz + bw));
 }
 
+// One FP32 correlation in exactly dot1's order, with the atom's loads of U
+// consecutive lane steps issued before their FMAs, so that U float4s per
+// lane are in flight at once (a long row is otherwise one L2 round trip per
+// few elements).  The tail steps run one at a time in the same order.
+template <int U>
+MP_DEV float dot1_deep(const float* __restrict__ p, const float* __restrict__ r, int ldN, int lane) {
+    float ax = 0.f, ay = 0.f, az = 0.f, aw = 0.f;
+    int off = lane * 4;
+    for (; off + 128 * (U - 1) < ldN; off += 128 * U) {
+        float4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = __ldg(reinterpret_cast<const float4*>(p + off + 128 * u));
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float4 q = *reinterpret_cast<const float4*>(r + off + 128 * u);
+            ax = fmaf(v[u].x, q.x, ax);
+            ay = fmaf(v[u].y, q.y, ay);
+            az = fmaf(v[u].z, q.z, az);
+            aw = fmaf(v[u].w, q.w, aw);
+        }
+    }
+    for (; off < ldN; off += 128) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p + off));
+        const float4 q = *reinterpret_cast<const float4*>(r + off);
+        ax = fmaf(v.x, q.x, ax);
+        ay = fmaf(v.y, q.y, ay);
+        az = fmaf(v.z, q.z, az);
+        aw = fmaf(v.w, q.w, aw);
+    }
+    return warp_sum_f32((ax + ay) + (az + aw));
+}
+
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a) {
     extern __shared__ float4 r_sh4[];
@@ -354,7 +386,7 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
         if (warp < kTop) {
             const int m0 = top[warp];
             unsigned long long key = 0ull;
-            if (m0 >= 0) key = pack_key(dot1(a.psi32 + static_cast<size_t>(m0) * a.ldN, r, a.ldN, lane), m0);
+            if (m0 >= 0) key = pack_key(dot1_deep<16>(a.psi32 + static_cast<size_t>(m0) * a.ldN, r, a.ldN, lane), m0);
             if (lane == 0) rkey[warp] = key;
         }
     } else
