@@ -47,16 +47,19 @@ struct CorrArgs {
     float* dump;            // diagnostic: full correlation rows (row * M + m), or NULL
     const float* rscale;    // diagnostic FP8: per-row scale of the quantised residual
     int* zero_next;         // step: the other half's survivor count, set to 0 here (or NULL)
+    int half_ok;            // tmBh holds TN/2-row boxes: a launch may take tiles of TN/2 atoms
+    int* n_at_out;          // atom tiles (candidate lists per row) this launch used, or NULL
 };
 
 int corr_smem_bytes(int TM, int TN);
 cudaError_t corr_prepare();
 int corr_max_clusters(int CL, int TN);
 // Launch with clusters of CL (1, 2 or 4) CTAs along the signal rows; tmB's
-// box is TN/CL atom rows, tmA's 128 signal rows.  max_rows bounds the active
-// rows any step of this launch can see (it sizes the grid).
-cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CorrArgs& a, int max_rows, int CL,
-                             cudaStream_t st);
+// box is TN/CL atom rows, tmA's 128 signal rows, tmBh's (when a.half_ok)
+// TN/2 atom rows.  max_rows bounds the active rows any step of this launch
+// can see (it sizes the grid).
+cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmBh, const CorrArgs& a,
+                             int max_rows, int CL, cudaStream_t st);
 
 // ------------------------------------------------------------------ batch engine
 // Per-signal state of a slot.
@@ -102,7 +105,8 @@ struct BatchEngine {
     void* Rq = nullptr;        // 2 x cap_pad operand rows (half 0, then half 1)
     SlotState* st = nullptr;
     int* act = nullptr;        // 2 x cap slot ids by row (half 0, then half 1)
-    int* counters = nullptr;   // [0] rows of half 0, [1] rows just admitted, [2] finished count, [3] rows of half 1
+    int* counters = nullptr;   // [0] rows of half 0, [1] rows just admitted, [2] finished count, [3] rows of half 1,
+                               // [4] candidate lists per row of the last GEMM
     int* done = nullptr;
     int* holes = nullptr;
     int* surv = nullptr;
@@ -119,7 +123,7 @@ struct BatchEngine {
     int* h_T = nullptr;
     BatchIO* h_io = nullptr;
     int* h_err = nullptr;
-    CUtensorMap tmA, tmA1, tmB;   // operand half 0, half 1, atoms
+    CUtensorMap tmA, tmA1, tmB, tmBh;   // operand half 0, half 1, atoms (TN-row and TN/2-row boxes)
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
     bool graph_retire = false;

@@ -208,7 +208,7 @@ struct SelArgs {
     int* act_next;          //   its row count, slot ids
     void* Rq_next;          //   and quantised operand rows
     const uint2* cand;
-    int n_at;
+    const int* n_at;        // sorted candidate lists per row (atom tiles of the step's GEMM)
     const float* psi32;
     int ldN, N, M;
     float* R32;
@@ -337,8 +337,9 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
         unsigned long long lk[kTop];
 #pragma unroll
         for (int k = 0; k < kTop; ++k) lk[k] = 0ull;
-        const uint2* cd = a.cand + static_cast<size_t>(i) * a.n_at * kTop;
-        for (int t = threadIdx.x; t < a.n_at; t += THREADS) {
+        const int n_at = *a.n_at;
+        const uint2* cd = a.cand + static_cast<size_t>(i) * n_at * kTop;
+        for (int t = threadIdx.x; t < n_at; t += THREADS) {
             // the whole list in one go (64 bytes): no chain of dependent loads
             unsigned long long lst[kTop];
             const uint4* l4 = reinterpret_cast<const uint4*>(cd + static_cast<size_t>(t) * kTop);
@@ -730,11 +731,15 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     A(reinterpret_cast<char**>(&e->Rq), 2 * qbytes);
     A(&e->st, sizeof(SlotState) * C);
     A(&e->act, 2 * sizeof(int) * C);
-    A(&e->counters, sizeof(int) * 4);
+    A(&e->counters, sizeof(int) * 8);
     A(&e->done, sizeof(int) * C);
     A(&e->holes, sizeof(int) * C);
     A(&e->surv, sizeof(int) * C);
-    A(&e->cand, sizeof(uint2) * C * e->n_at * kTop);
+    // room for the lists of half-width tiles (taken by the GEMM when few row
+    // blocks are active)
+    const bool half_ok = TN == 256 && e->CL == 1;
+    const size_t n_at_max = half_ok ? (p->M + TN / 2 - 1) / (TN / 2) : e->n_at;
+    A(&e->cand, sizeof(uint2) * C * n_at_max * kTop);
     A(&e->eps2, sizeof(double) * C);
     A(&e->T, sizeof(int) * C);
     A(&e->err, sizeof(int));
@@ -742,13 +747,13 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     A(&e->rscale, sizeof(float) * C);
     A(&e->fin_list, sizeof(int) * C);
     if (r == cudaSuccess) r = cudaMallocHost(&e->h_st, sizeof(SlotState) * C);
-    if (r == cudaSuccess) r = cudaMallocHost(&e->h_cnt, sizeof(int) * 4);
+    if (r == cudaSuccess) r = cudaMallocHost(&e->h_cnt, sizeof(int) * 8);
     if (r == cudaSuccess) r = cudaMallocHost(&e->h_eps2, sizeof(double) * C);
     if (r == cudaSuccess) r = cudaMallocHost(&e->h_T, sizeof(int) * C);
     if (r == cudaSuccess) r = cudaMallocHost(&e->h_io, sizeof(BatchIO));
     if (r == cudaSuccess) r = cudaMallocHost(&e->h_err, sizeof(int));
     if (r == cudaSuccess) r = cudaMemset(e->Rq, 0, 2 * qbytes);
-    if (r == cudaSuccess) r = cudaMemset(e->counters, 0, sizeof(int) * 4);
+    if (r == cudaSuccess) r = cudaMemset(e->counters, 0, sizeof(int) * 8);
     if (r != cudaSuccess) {
         engine_free(e);
         return cuda_fail(r, "batched engine allocation");
@@ -757,6 +762,7 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     if (s == MP_OK) s = make_map(&e->tmA1, static_cast<char*>(e->Rq) + qbytes, fp8, e->cap_pad, e->ldq, kBM);
     // each CTA of a GEMM cluster loads TN / CL atom rows and multicasts them
     if (s == MP_OK) s = make_map(&e->tmB, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, TN / e->CL);
+    if (s == MP_OK) s = make_map(&e->tmBh, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, half_ok ? TN / 2 : TN / e->CL);
     if (s != MP_OK) {
         engine_free(e);
         return s;
@@ -775,6 +781,7 @@ static CorrArgs corr_args(PlanImpl* p, BatchEngine* e) {
     // the next) when they fit in TMEM's 512 columns, else one
     const int nbuf = (ca.RM == 1 || 2 * ca.RM * e->TN <= 512) ? 2 : 1;
     ca.n_at = e->n_at;
+    ca.half_ok = e->TN == 256 && e->CL == 1 ? 1 : 0;
     ca.M = p->M;
     ca.nk = (fp8 ? p->ldK8 : p->ldK16 * 2) / kRowBytes;
     ca.fp8 = fp8 ? 1 : 0;
@@ -813,7 +820,8 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, cudaStream
     CorrArgs ca = corr_args(p, e);
     ca.n_act = cnt[half];
     ca.zero_next = cnt[1 - half];
-    cudaError_t r = launch_corr_top8(half ? e->tmA1 : e->tmA, e->tmB, ca, e->cap_pad, e->CL, st);
+    ca.n_at_out = e->counters + 4;
+    cudaError_t r = launch_corr_top8(half ? e->tmA1 : e->tmA, e->tmB, e->tmBh, ca, e->cap_pad, e->CL, st);
     if (r != cudaSuccess) return r;
     SelArgs sa;
     sa.n_act = cnt[half];
@@ -822,7 +830,7 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, cudaStream
     sa.act_next = e->act + static_cast<size_t>(1 - half) * e->cap;
     sa.Rq_next = static_cast<char*>(e->Rq) + (1 - half) * qbytes;
     sa.cand = e->cand;
-    sa.n_at = e->n_at;   // sorted candidate lists per signal (one per atom tile)
+    sa.n_at = e->counters + 4;   // written by the step's GEMM
     sa.psi32 = p->psi32;
     sa.ldN = p->ldN;
     sa.N = p->N;
@@ -1075,7 +1083,7 @@ mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B,
     CorrArgs ca = corr_args(p, e);
     ca.dump = C;
     ca.rscale = e->rscale;
-    MP_CUDA_TRY(launch_corr_top8(e->tmA, e->tmB, ca, B, e->CL, st));
+    MP_CUDA_TRY(launch_corr_top8(e->tmA, e->tmB, e->tmBh, ca, B, e->CL, st));
     p->launches += 2;
     MP_CUDA_TRY(cudaMemcpyAsync(e->h_err, e->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1136,9 +1144,9 @@ static double time_gemm(PlanImpl* p, int prec, int B, const GemmShape& g, const 
         if (r == cudaSuccess) r = cudaEventCreate(&e0);
         if (r == cudaSuccess) r = cudaEventCreate(&e1);
         const CorrArgs ca = corr_args(p, &e);
-        for (int it = 0; it < 2 && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, ca, B, e.CL, st);
+        for (int it = 0; it < 2 && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, e.tmBh, ca, B, e.CL, st);
         if (r == cudaSuccess) r = cudaEventRecord(e0, st);
-        for (int it = 0; it < reps && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, ca, B, e.CL, st);
+        for (int it = 0; it < reps && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, e.tmBh, ca, B, e.CL, st);
         if (r == cudaSuccess) r = cudaEventRecord(e1, st);
         if (r == cudaSuccess) r = cudaEventSynchronize(e1);
         float ms = 0.f;

@@ -117,6 +117,9 @@ struct CorrCtx {
     uint32_t as_stride;    // bytes of one stage's A region (room for the largest tile)
     int n_act, n_blk;      // active rows, 128-row blocks holding them
     int n_rg, n_ct;        // row-tile groups, cluster tiles (for this launch's RM)
+    int tn, n_at;          // atoms per tile and atom tiles of this launch
+    int stages;            // ring depth for this launch's tile
+    uint32_t b_stride;     // bytes of one stage's B region
     int cid, n_clusters, q, warp, lane;
     uint16_t all;          // cluster CTA mask
     uint64_t lim;          // watchdog, ns
@@ -127,13 +130,15 @@ struct CorrCtx {
 template <int CL, int RM>
 MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CorrArgs& a, const CorrCtx& x) {
     static_assert(RM == 1 || (RM == 2 && CL == 1), "256-row tiles take no cluster");
-    const int TN = a.TN;
+    const int TN = a.TN;      // stage and accumulator strides
+    const int tn = x.tn;      // atoms per tile in this launch: TN, or TN / 2 (one CTA per cluster)
     // TMEM accumulator buffers: two unless one tile fills the 512 columns
     const int nbuf = (RM == 1 || RM * TN * 2 <= 512) ? 2 : 1;
     const uint32_t a_bytes = kBM * kRowBytes;        // one row block of a stage
     const uint32_t as_bytes = x.as_stride;
-    const uint32_t b_bytes = static_cast<uint32_t>(TN) * kRowBytes;
+    const uint32_t b_bytes = x.b_stride;         // one stage's B region (tn atom rows)
     const uint32_t slice_bytes = b_bytes / CL;   // this CTA's share of the atom tile
+    const int stages = x.stages;
     uint8_t* tilesA = x.tilesA;
     uint8_t* tilesB = x.tilesB;
     CorrShared* sh = x.sh;
@@ -162,7 +167,7 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
                 const int nmb = RM == 1 ? 1 : min(RM, n_blk - rt * RM);
                 for (int kb = 0; kb < a.nk; ++kb) {
                     // all CL CTAs released the stage's previous use
-                    if (g >= a.stages && !mbar_wait_bounded(&sh->empty[s], ph ^ 1u, lim)) {
+                    if (g >= stages && !mbar_wait_bounded(&sh->empty[s], ph ^ 1u, lim)) {
                         corr_timeout(a.err, sh);
                         stop = true;
                         break;
@@ -171,19 +176,20 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
                         stop = true;
                         break;
                     }
-                    mbar_arrive_expect_tx(&sh->full[s], static_cast<uint32_t>(nmb) * a_bytes + b_bytes);
+                    mbar_arrive_expect_tx(&sh->full[s], static_cast<uint32_t>(nmb) * a_bytes +
+                                                            static_cast<uint32_t>(tn) * kRowBytes);
 #pragma unroll
                     for (int mb = 0; mb < RM; ++mb)
                         if (mb < nmb)
                             tma_load_2d(tilesA + s * as_bytes + mb * a_bytes, tmA, kb * kelems,
                                         (rt * RM + mb) * kBM, &sh->full[s]);
                     if (CL == 1)
-                        tma_load_2d(tilesB + s * b_bytes, tmB, kb * kelems, at * TN, &sh->full[s]);
+                        tma_load_2d(tilesB + s * b_bytes, tmB, kb * kelems, at * tn, &sh->full[s]);
                     else
                         tma_load_2d_multicast(tilesB + s * b_bytes + q * slice_bytes, tmB, kb * kelems,
                                               at * TN + q * (TN / CL), &sh->full[s], all);
                     ++g;
-                    if (++s == a.stages) {
+                    if (++s == stages) {
                         s = 0;
                         ph ^= 1u;
                     }
@@ -193,16 +199,16 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
             // that can be in flight in stage s is the last one issued to it),
             // and every CTA of the cluster released the stages' last uses, so
             // no peer still writes into this CTA or arrives on its barriers
-            for (int t = 0; t < a.stages && t < g; ++t) {
-                const long long last = g - 1 - ((g - 1 - t) % a.stages);
-                mbar_wait_bounded(&sh->full[t], static_cast<uint32_t>((last / a.stages) & 1), lim);
-                mbar_wait_bounded(&sh->empty[t], static_cast<uint32_t>((last / a.stages) & 1), lim);
+            for (int t = 0; t < stages && t < g; ++t) {
+                const long long last = g - 1 - ((g - 1 - t) % stages);
+                mbar_wait_bounded(&sh->full[t], static_cast<uint32_t>((last / stages) & 1), lim);
+                mbar_wait_bounded(&sh->empty[t], static_cast<uint32_t>((last / stages) & 1), lim);
             }
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer (one thread)
         if (lane == 0) {
-            const uint32_t idesc = make_idesc(kBM, TN, a.fp8 ? 0u : 1u);
+            const uint32_t idesc = make_idesc(kBM, tn, a.fp8 ? 0u : 1u);
             // ring stage s and its phase ph; accumulator buffer buf and its
             // phase bph (all incremental: no division in the issue loop)
             int s = 0, buf = 0, li = 0;
@@ -235,7 +241,7 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
                     // will refill it with a multicast)
                     if (CL == 1) mma_commit(&sh->empty[s]);
                     else mma_commit_multicast(&sh->empty[s], all);
-                    if (++s == a.stages) {
+                    if (++s == stages) {
                         s = 0;
                         ph ^= 1u;
                     }
@@ -260,7 +266,7 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
         // merges them into the tile's one list of 8 per row.
         const int quad = warp & 3;
         const int grp = (warp - 2) >> 2;
-        const int cols = TN / kEpiGroups;
+        const int cols = tn / kEpiGroups;
         int buf = 0;
         uint32_t bph = 0;
         uint32_t xround = 0;          // exchange rounds of this quadrant so far
@@ -285,7 +291,7 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
                 uint32_t tk[kTop];
 #pragma unroll
                 for (int k = 0; k < kTop; ++k) tk[k] = 0u;
-                const int m0 = at * TN + grp * cols;
+                const int m0 = at * tn + grp * cols;
                 for (int c = 0; c < cols / 32; ++c) {
                     float v[32];
                     tmem_ld_32cols(tmem + (static_cast<uint32_t>(quad * 32) << 16) +
@@ -351,10 +357,10 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
                     }
                     mbar_arrive(&sh->xempty[quad]);
                     if (row < n_act) {
-                        uint2* o = a.cand + (static_cast<size_t>(row) * a.n_at + at) * kTop;
+                        uint2* o = a.cand + (static_cast<size_t>(row) * x.n_at + at) * kTop;
 #pragma unroll
                         for (int k = 0; k < kTop; ++k) {
-                            const uint32_t m = static_cast<uint32_t>(at * TN + key_col(tk[k]));
+                            const uint32_t m = static_cast<uint32_t>(at * tn + key_col(tk[k]));
                             o[k] = tk[k] ? make_uint2(key_score_bits(tk[k]), m) : make_uint2(0u, 0xffffffffu);
                         }
                     }
@@ -375,7 +381,7 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
 template <int CL, int RM>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     corr_top8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     const CorrArgs a) {
+                     const __grid_constant__ CUtensorMap tmBh, const CorrArgs a) {
     extern __shared__ uint8_t smem_raw[];
     // operand tiles need 1024-byte alignment for the 128-byte swizzle atoms
     // (the same offset in every CTA, as multicast writes the same offsets)
@@ -383,10 +389,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
     static_assert(RM == 1 || (RM == 2 && CL == 1), "256-row tiles take no cluster");
     CorrCtx x;
-    x.as_stride = static_cast<uint32_t>(RM) * kBM * kRowBytes;
-    x.tilesA = smem;
-    x.tilesB = smem + a.stages * x.as_stride;
-    CorrShared* sh = reinterpret_cast<CorrShared*>(x.tilesB + a.stages * static_cast<uint32_t>(a.TN) * kRowBytes);
+    // the ring the launch allocated (a.stages stages of RM row blocks and TN
+    // atoms), then the barriers and the epilogue's exchange lists
+    const uint32_t ring_bytes = static_cast<uint32_t>(a.stages) * (RM * kBM + a.TN) * kRowBytes;
+    CorrShared* sh = reinterpret_cast<CorrShared*>(smem + ring_bytes);
     x.sh = sh;
     x.warp = threadIdx.x >> 5;
     x.lane = threadIdx.x & 31;
@@ -402,13 +408,36 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int rm = (RM == 2 && x.n_blk * a.n_at > static_cast<int>(gridDim.x)) ? 2 : 1;
     const int n_rt = (x.n_blk + rm - 1) / rm;      // row tiles of rm blocks
     x.n_rg = (n_rt + CL - 1) / CL;                  // groups of CL row tiles
-    x.n_ct = x.n_rg * a.n_at;                       // cluster tiles
+    // with few row blocks the grid has SMs to spare: tiles of TN / 2 atoms
+    // double the tiles and give each SM 2/3 of the bytes of a TN-atom tile,
+    // as long as they all still fit in one wave.  The candidate set each row
+    // ends with is the same (its best 8 keys are in their tiles' lists)
+    x.tn = a.TN;
+    x.n_at = a.n_at;
+    if (CL == 1 && rm == 1 && a.half_ok) {
+        const int n_at_h = (a.M + a.TN / 2 - 1) / (a.TN / 2);
+        if (x.n_blk * n_at_h <= static_cast<int>(gridDim.x)) {
+            x.tn = a.TN / 2;
+            x.n_at = n_at_h;
+        }
+    }
+    if (a.n_at_out && blockIdx.x == 0 && threadIdx.x == 0) *a.n_at_out = x.n_at;
+    // the ring re-cut into stages of this launch's tile (rm row blocks, tn
+    // atoms): a smaller tile gets a deeper ring, so that as many bytes stay
+    // in flight per SM as with the largest one (up to kMaxStages stages).
+    // The same in every CTA of a cluster.  Offsets stay 1024-byte aligned.
+    x.as_stride = static_cast<uint32_t>(rm) * kBM * kRowBytes;
+    x.b_stride = static_cast<uint32_t>(x.tn) * kRowBytes;
+    x.stages = min(kMaxStages, static_cast<int>(ring_bytes / (x.as_stride + x.b_stride)));
+    x.tilesA = smem;
+    x.tilesB = smem + x.stages * x.as_stride;
+    x.n_ct = x.n_rg * x.n_at;                       // cluster tiles
     if (x.cid >= x.n_ct) return;                    // uniform across the cluster
     x.all = static_cast<uint16_t>((1u << CL) - 1u);
     x.lim = a.watchdog_ns;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < a.stages; ++s) {
+        for (int s = 0; s < x.stages; ++s) {
             mbar_init(&sh->full[s], 1);
             mbar_init(&sh->empty[s], CL);
         }
@@ -424,7 +453,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         sh->abort = 0;
         fence_mbar_init();
         tma_prefetch_desc(&tmA);
-        tma_prefetch_desc(&tmB);
+        tma_prefetch_desc(x.tn == a.TN ? &tmB : &tmBh);
     }
     if (warp == 1) tmem_alloc(&sh->tmem_base, static_cast<uint32_t>(a.tmem_cols));
     tc_fence_before();
@@ -434,11 +463,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     x.tmem = sh->tmem_base;
     const uint32_t tmem = x.tmem;
 
+    const CUtensorMap* mb = x.tn == a.TN ? &tmB : &tmBh;
     if constexpr (RM == 2) {
-        if (rm == 2) corr_roles<CL, 2>(&tmA, &tmB, a, x);
-        else corr_roles<CL, 1>(&tmA, &tmB, a, x);
+        if (rm == 2) corr_roles<CL, 2>(&tmA, mb, a, x);
+        else corr_roles<CL, 1>(&tmA, mb, a, x);
     } else {
-        corr_roles<CL, 1>(&tmA, &tmB, a, x);
+        corr_roles<CL, 1>(&tmA, mb, a, x);
     }
 
     tc_fence_before();
@@ -502,17 +532,19 @@ int corr_max_clusters(int CL, int TN) {
     return n;
 }
 
-cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CorrArgs& a, int max_rows, int CL,
-                             cudaStream_t st) {
+cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmBh, const CorrArgs& a,
+                             int max_rows, int CL, cudaStream_t st) {
     const int nbuf = (a.RM == 1 || a.RM * a.TN * 2 <= 512) ? 2 : 1;   // as the kernel computes it
     if ((CL > 1 && a.RM != 1) || (a.RM != 1 && a.RM != 2) || nbuf * a.RM * a.TN > a.tmem_cols ||
-        a.stages != corr_stages(kBM * a.RM, a.TN))
+        a.stages != corr_stages(kBM * a.RM, a.TN) || (a.half_ok && (CL != 1 || a.TN != 256)))
         return cudaErrorInvalidValue;
     // enough clusters for the largest tile count this launch can see (with
     // RM = 2 the kernel takes 128-row tiles whenever they fit the grid, so
     // the grid is sized by those)
     const int max_rt = (max_rows + kBM - 1) / kBM;
-    const int max_ct = ((max_rt + CL - 1) / CL) * a.n_at;
+    int max_ct = ((max_rt + CL - 1) / CL) * a.n_at;
+    if (a.half_ok)   // room for the half-width tiles of one or two row blocks
+        max_ct = std::max(max_ct, std::min(max_rt, 2) * ((a.M + a.TN / 2 - 1) / (a.TN / 2)));
     const int clusters = std::max(1, std::min(max_ct, corr_max_clusters(CL, a.TN)));
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(clusters * CL);
@@ -526,11 +558,11 @@ cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, con
     at[0].val.clusterDim.z = 1;
     lc.attrs = at;
     lc.numAttrs = 1;
-    if (a.RM == 2) return cudaLaunchKernelEx(&lc, corr_top8_kernel<1, 2>, tmA, tmB, a);
+    if (a.RM == 2) return cudaLaunchKernelEx(&lc, corr_top8_kernel<1, 2>, tmA, tmB, tmBh, a);
     switch (CL) {
-        case 1: return cudaLaunchKernelEx(&lc, corr_top8_kernel<1, 1>, tmA, tmB, a);
-        case 2: return cudaLaunchKernelEx(&lc, corr_top8_kernel<2, 1>, tmA, tmB, a);
-        case 4: return cudaLaunchKernelEx(&lc, corr_top8_kernel<4, 1>, tmA, tmB, a);
+        case 1: return cudaLaunchKernelEx(&lc, corr_top8_kernel<1, 1>, tmA, tmB, tmBh, a);
+        case 2: return cudaLaunchKernelEx(&lc, corr_top8_kernel<2, 1>, tmA, tmB, tmBh, a);
+        case 4: return cudaLaunchKernelEx(&lc, corr_top8_kernel<4, 1>, tmA, tmB, tmBh, a);
     }
     return cudaErrorInvalidValue;
 }
