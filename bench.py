@@ -515,6 +515,10 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
     launches = (B.mp_plan_query(plan, B.MP_Q_KERNEL_LAUNCHES) - l0) // reps
     tb = statistics.median(times)
     iters = np.array([r.iters for r in res])
+    # how many steps of the decode ran with at most k signals active
+    active = np.array([(iters > t).sum() for t in range(int(iters.max()))])
+    active_profile = {"steps": int(iters.max()),
+                      "steps_with_at_most": {str(k): int((active <= k).sum()) for k in (128, 256, 384, 512)}}
     Xh = X.cpu().numpy()
     supp_b = [orc.support_score(Xh[i], prob.supports[i]) for i in range(prob.B)]
     # x~ against the true sparse signal x (every signal; the FP64 oracle's
@@ -546,6 +550,7 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
             "x_rel_err_vs_truth_mean": float(np.mean(xerr)), "x_rel_err_vs_truth_max": float(np.max(xerr)),
             "iterations_total": int(iters.sum()), "iterations_max": int(iters.max()),
             "effective_tflops": flops / tb / 1e12, "gpu_launches_per_batch": int(launches), "gemm_shape": shape,
+            "active_rows_profile": active_profile,
             "gemm_full_batch": gemm}
 
 
@@ -569,6 +574,27 @@ def gemm_profile_case(prec_name, shape):
     B.mp_plan_destroy(plan)
     return {"profile_case": BATCHED[prec_name], "gemm_shape": [tm, tn, cl], "us": us,
             "tflops": 2.0 * w["N"] * w["M"] * w["B"] / us / 1e6}
+
+
+def gemm_sweep(prec_name, shape, rows=(64, 128, 256, 384, 512, 768, 1024)):
+    """The batched workload's correlation GEMM alone (GEMM + top-8 epilogue,
+    synthetic rows) at several active-row counts, mean of 50 launches each
+    with CUDA events: how the step's GEMM time falls as a batch drains."""
+    import torch
+    from paper_0809_1833_gb300 import binding as B
+    from paper_0809_1833_gb300 import workloads as W
+    import __graft_entry__
+    __graft_entry__.build()
+    w = W.WORKLOADS[BATCHED[prec_name]]
+    prec = B.MP_PREC_BF16 if prec_name == "bf16" else B.MP_PREC_FP8E4M3
+    psi = W.gaussian_dictionary(w["N"], w["M"], seed=0)
+    d = torch.from_numpy(psi).cuda()
+    plan = B.mp_plan_create(w["N"], w["M"], d.data_ptr(), prec_mask=1 << prec)
+    del d
+    tn, cl, tm = (list(shape) + [128])[:3]
+    us = {str(r): B.mp_debug_time_gemm(plan, prec, r, (tm, tn, cl), reps=50) for r in rows if r <= w["B"]}
+    B.mp_plan_destroy(plan)
+    return {"gemm_sweep": BATCHED[prec_name], "gemm_shape": [tm, tn, cl], "us_by_active_rows": us}
 
 
 def served_measure(rate=2000.0, duration=10.0, pool=48, seed=0, max_slots=256, drain_s=120.0):
@@ -888,6 +914,8 @@ def main():
     ap.add_argument("--profile-shape", default="256,1,128",
                     help="GEMM atoms per tile, cluster size and signals per tile for --profile-batched "
                          "(the autotuner's choice in unprofiled runs)")
+    ap.add_argument("--gemm-sweep", choices=["bf16", "fp8"], default=None,
+                    help="time the batched workload's GEMM alone at several active-row counts (--profile-shape)")
     ap.add_argument("--profile-gemm", choices=["bf16", "fp8"], default=None,
                     help="profiling case: the batched workload's correlation GEMM on its full batch of "
                          "synthetic rows, 3 launches (2 warm-up), at --profile-shape, then exit")
@@ -933,6 +961,10 @@ def main():
         args.warmup = 3
     if args.profile64:
         run_profile64_case(*args.profile64)
+        return
+    if args.gemm_sweep:
+        shape = tuple(int(v) for v in args.profile_shape.split(","))
+        print(json.dumps(gemm_sweep(args.gemm_sweep, shape)))
         return
     if args.profile_gemm:
         shape = tuple(int(v) for v in args.profile_shape.split(","))
