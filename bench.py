@@ -554,10 +554,11 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
             "gemm_full_batch": gemm}
 
 
-def gemm_profile_case(prec_name, shape):
-    """Three launches of the batched workload's correlation GEMM (full batch,
-    synthetic rows) at shape = (atoms per tile, cluster, signals per tile):
-    the case an ncu capture of the GEMM takes (-s 2 -c 1)."""
+def gemm_profile_case(prec_name, shape, rows=None):
+    """Three launches of the batched workload's correlation GEMM (``rows``
+    active synthetic rows, default the full batch) at shape = (atoms per
+    tile, cluster, signals per tile): the case an ncu capture of the GEMM
+    takes (-s 2 -c 1)."""
     import torch
     from paper_0809_1833_gb300 import binding as B
     from paper_0809_1833_gb300 import workloads as W
@@ -570,10 +571,11 @@ def gemm_profile_case(prec_name, shape):
     plan = B.mp_plan_create(w["N"], w["M"], d.data_ptr(), prec_mask=1 << prec)
     del d
     tn, cl, tm = (list(shape) + [128])[:3]
-    us = B.mp_debug_time_gemm(plan, prec, w["B"], (tm, tn, cl), reps=1)
+    rows = rows or w["B"]
+    us = B.mp_debug_time_gemm(plan, prec, rows, (tm, tn, cl), reps=1)
     B.mp_plan_destroy(plan)
-    return {"profile_case": BATCHED[prec_name], "gemm_shape": [tm, tn, cl], "us": us,
-            "tflops": 2.0 * w["N"] * w["M"] * w["B"] / us / 1e6}
+    return {"profile_case": BATCHED[prec_name], "rows": rows, "gemm_shape": [tm, tn, cl], "us": us,
+            "tflops": 2.0 * w["N"] * w["M"] * rows / us / 1e6}
 
 
 def gemm_sweep(prec_name, shape, rows=(64, 128, 256, 384, 512, 768, 1024)):
@@ -914,6 +916,7 @@ def main():
     ap.add_argument("--profile-shape", default="256,1,128",
                     help="GEMM atoms per tile, cluster size and signals per tile for --profile-batched "
                          "(the autotuner's choice in unprofiled runs)")
+    ap.add_argument("--profile-rows", type=int, default=None, help="active rows of the --profile-gemm case")
     ap.add_argument("--gemm-sweep", choices=["bf16", "fp8"], default=None,
                     help="time the batched workload's GEMM alone at several active-row counts (--profile-shape)")
     ap.add_argument("--profile-gemm", choices=["bf16", "fp8"], default=None,
@@ -968,7 +971,7 @@ def main():
         return
     if args.profile_gemm:
         shape = tuple(int(v) for v in args.profile_shape.split(","))
-        print(json.dumps(gemm_profile_case(args.profile_gemm, shape)))
+        print(json.dumps(gemm_profile_case(args.profile_gemm, shape, args.profile_rows)))
         return
     if args.batched_only:
         import __graft_entry__

@@ -2,20 +2,22 @@
 // each step performs one MP iteration (Sec. 3, Eqs. 9-12) for every signal
 // that is still active.
 //
-// One step is three kernels:
+// One step is two kernels:
 //   corr_top8   (mp_corr.cu) C = Rq * Psiq^T on the tensor cores; per signal
 //               and per atom tile the 8 largest |c| (FP8: times the atom scale).
 //   select      per signal: merge the sorted per-tile candidate lists into the
 //               top 8, rescore those atoms in FP32 from the FP32 atoms
 //               (<r, psi_m>, Eq. 9), commit the best (ties to the smallest
 //               index): x~_m += c (Eq. 10), r -= c psi_m in FP32 (Eq. 11),
-//               e = sum r^2 in FP64, t += 1 (Eq. 12), stop test; and write the
-//               requantised residual back into the signal's GEMM row.
-//   fixup       remove the signals that stopped from the active rows: each
-//               hole below the new row count is filled with a surviving row
-//               from above it (work proportional to the signals that stopped).
-//               A signal's arithmetic does not depend on its row, so results
-//               are the same alone and in any batch.
+//               e = sum r^2 in FP64, t += 1 (Eq. 12), stop test; a signal
+//               that runs on takes the next row of the other half of the
+//               double-buffered GEMM operand (one atomic) and writes its
+//               requantised residual there, so the next step's rows are
+//               compact.  A signal's arithmetic does not depend on its row,
+//               so results are the same alone, in any batch and in any row
+//               order.
+// After an admission, fixup (one CTA) drops the newly admitted signals that
+// need no iteration, filling their rows from the tail.
 // Signals stop independently; the steps are captured in a CUDA graph and
 // replayed until no signal is active.
 #include <cuda.h>
@@ -127,8 +129,9 @@ MP_DEV float block_quantize(const float* r, int ldN, void* dst, int ldq, int fp8
 
 // ------------------------------------------------------------------ admission (Eq. 8)
 // New signal k takes slot slots[k] (k when slots == NULL) and GEMM row
-// *n_act + k; signals that need no iteration are marked done and leave at
-// the next fixup.  *n_extra = n_new tells the fixup how many rows were added.
+// *n_act + k of operand half 0; signals that need no iteration are marked
+// done and leave at the fixup that follows.  *n_extra = n_new tells the
+// fixup how many rows were added.
 struct AdmitArgs {
     const float* Y;         // n_new x N
     int n_new, N, ldN, M;
