@@ -128,6 +128,7 @@ struct BatchEngine {
     int graph_steps = 0;
     bool graph_retire = false;
     cudaStream_t cap_stream = nullptr;
+    cudaEvent_t cnt_ready[2] = {nullptr, nullptr};   // active-count reads of alternate replays
     size_t bytes = 0;
 };
 

@@ -658,6 +658,8 @@ void engine_free(BatchEngine* e) {
     if (!e) return;
     if (e->graph) cudaGraphExecDestroy(e->graph);
     if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
+    for (cudaEvent_t ev : e->cnt_ready)
+        if (ev) cudaEventDestroy(ev);
     void* dev[] = {e->R32, e->Rq, e->st, e->act, e->counters, e->done, e->holes, e->surv, e->cand,
                    e->eps2, e->T, e->err, e->io, e->rscale, e->fin_list};
     for (void* p : dev) cudaFree(p);
@@ -972,14 +974,22 @@ static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, lo
     // signal b -> slot b, GEMM row b; then drop those that need no iteration
     MP_CUDA_TRY(engine_admit(p, e, Y, B, nullptr, st));
     // replay the captured steps until no signal is active (each step moves
-    // every active signal by one iteration, so maxT steps always suffice)
+    // every active signal by one iteration, so maxT steps always suffice).
+    // Replay k is queued before the active count after replay k - 1 is
+    // known, so the GPU never waits for the host's read; the replay queued
+    // after the last signal stopped runs empty steps (every CTA exits at once)
+    for (int j = 0; j < 2; ++j)
+        if (!e->cnt_ready[j]) MP_CUDA_TRY(cudaEventCreateWithFlags(&e->cnt_ready[j], cudaEventDisableTiming));
     const long long max_replays = (static_cast<long long>(maxT) + kStepsPerGraph - 1) / kStepsPerGraph + 1;
     for (long long k = 0; k < max_replays; ++k) {
-        MP_CUDA_TRY(cudaMemcpyAsync(e->h_cnt, e->counters, sizeof(int), cudaMemcpyDeviceToHost, st));
-        MP_CUDA_TRY(cudaStreamSynchronize(st));
-        if (e->h_cnt[0] == 0) break;
         MP_CUDA_TRY(cudaGraphLaunch(e->graph, st));
         p->launches += 2 * kStepsPerGraph;
+        MP_CUDA_TRY(cudaMemcpyAsync(e->h_cnt + (k & 1), e->counters, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MP_CUDA_TRY(cudaEventRecord(e->cnt_ready[k & 1], st));
+        if (k > 0) {
+            MP_CUDA_TRY(cudaEventSynchronize(e->cnt_ready[(k - 1) & 1]));
+            if (e->h_cnt[(k - 1) & 1] == 0) break;
+        }
     }
     MP_CUDA_TRY(cudaMemcpyAsync(e->h_st, e->st, sizeof(SlotState) * B, cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaMemcpyAsync(e->h_err, e->err, sizeof(int), cudaMemcpyDeviceToHost, st));
