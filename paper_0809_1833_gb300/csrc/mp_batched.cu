@@ -481,8 +481,9 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
     if (a.fp8) {
         block_quantize(r, a.ldN, qrow, a.ldq, 1, redf);
     } else {
-        // the first ldN elements; the row's zero padding up to ldq is never
-        // written after the operand's allocation
+        // the first ldN elements; the row's padding up to ldq holds zeros (the
+        // operand is zeroed when allocated, and admission and compaction,
+        // which write whole rows, write zeros there)
         for (int k = threadIdx.x; k < n4; k += THREADS) {
             const float4 v = rs4[k];
             __nv_bfloat162* q2 = reinterpret_cast<__nv_bfloat162*>(qrow) + 2 * k;
