@@ -469,7 +469,7 @@ def variants_measure(n_sig=4, gram_period=32):
     return out
 
 
-def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=(256, 1, 128)):
+def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=(256, 256)):
     """Batched low-precision decode of a whole batched workload vs the plain
     FP32 kernel on the same signals (the first ``n_plain`` of them)."""
     import torch
@@ -488,8 +488,7 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
         # under a profiler the autotuner's timings are distorted: pin the
         # shape it picks in unprofiled runs
         B.mp_plan_set_option(plan, B.MP_OPT_BATCH_TILE_N, profile_shape[0])
-        B.mp_plan_set_option(plan, B.MP_OPT_BATCH_CLUSTER, profile_shape[1])
-        B.mp_plan_set_option(plan, B.MP_OPT_BATCH_TILE_M, profile_shape[2] if len(profile_shape) > 2 else 128)
+        B.mp_plan_set_option(plan, B.MP_OPT_BATCH_TILE_M, profile_shape[1] if len(profile_shape) > 1 else 128)
     Y = torch.from_numpy(prob.y).cuda()
     X = torch.empty((prob.B, prob.M), device="cuda")
     stop = (w["eps"], w["T"])
@@ -501,8 +500,7 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
         return {"profile_case": name}
     times = []
     shape = {"signals_per_tile": B.mp_plan_query(plan, B.MP_Q_BATCH_TILE_M),
-             "atoms_per_tile": B.mp_plan_query(plan, B.MP_Q_BATCH_TILE_N),
-             "cluster_ctas": B.mp_plan_query(plan, B.MP_Q_BATCH_CLUSTER), "chosen_by": "autotuner"}
+             "atoms_per_tile": B.mp_plan_query(plan, B.MP_Q_BATCH_TILE_N), "chosen_by": "autotuner"}
     l0 = B.mp_plan_query(plan, B.MP_Q_KERNEL_LAUNCHES)
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -557,8 +555,8 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
 def gemm_profile_case(prec_name, shape, rows=None):
     """Three launches of the batched workload's correlation GEMM (``rows``
     active synthetic rows, default the full batch) at shape = (atoms per
-    tile, cluster, signals per tile): the case an ncu capture of the GEMM
-    takes (-s 2 -c 1)."""
+    tile, signals per tile): the case an ncu capture of the GEMM takes
+    (-s 2 -c 1)."""
     import torch
     from paper_0809_1833_gb300 import binding as B
     from paper_0809_1833_gb300 import workloads as W
@@ -570,11 +568,11 @@ def gemm_profile_case(prec_name, shape, rows=None):
     d = torch.from_numpy(psi).cuda()
     plan = B.mp_plan_create(w["N"], w["M"], d.data_ptr(), prec_mask=1 << prec)
     del d
-    tn, cl, tm = (list(shape) + [128])[:3]
+    tn, tm = (list(shape) + [128])[:2]
     rows = rows or w["B"]
-    us = B.mp_debug_time_gemm(plan, prec, rows, (tm, tn, cl), reps=1)
+    us = B.mp_debug_time_gemm(plan, prec, rows, (tm, tn), reps=1)
     B.mp_plan_destroy(plan)
-    return {"profile_case": BATCHED[prec_name], "rows": rows, "gemm_shape": [tm, tn, cl], "us": us,
+    return {"profile_case": BATCHED[prec_name], "rows": rows, "gemm_shape": [tm, tn], "us": us,
             "tflops": 2.0 * w["N"] * w["M"] * rows / us / 1e6}
 
 
@@ -593,10 +591,10 @@ def gemm_sweep(prec_name, shape, rows=(64, 128, 256, 384, 512, 768, 1024)):
     d = torch.from_numpy(psi).cuda()
     plan = B.mp_plan_create(w["N"], w["M"], d.data_ptr(), prec_mask=1 << prec)
     del d
-    tn, cl, tm = (list(shape) + [128])[:3]
-    us = {str(r): B.mp_debug_time_gemm(plan, prec, r, (tm, tn, cl), reps=50) for r in rows if r <= w["B"]}
+    tn, tm = (list(shape) + [128])[:2]
+    us = {str(r): B.mp_debug_time_gemm(plan, prec, r, (tm, tn), reps=50) for r in rows if r <= w["B"]}
     B.mp_plan_destroy(plan)
-    return {"gemm_sweep": BATCHED[prec_name], "gemm_shape": [tm, tn, cl], "us_by_active_rows": us}
+    return {"gemm_sweep": BATCHED[prec_name], "gemm_shape": [tm, tn], "us_by_active_rows": us}
 
 
 def served_measure(rate=2000.0, duration=10.0, pool=48, seed=0, max_slots=256, drain_s=120.0):
@@ -913,8 +911,8 @@ def main():
                     help="profiling case: one decode capped at this many iterations, then exit")
     ap.add_argument("--profile-batched", choices=["bf16", "fp8"], default=None,
                     help="profiling case: one batched decode of that workload, then exit")
-    ap.add_argument("--profile-shape", default="256,1,128",
-                    help="GEMM atoms per tile, cluster size and signals per tile for --profile-batched "
+    ap.add_argument("--profile-shape", default="256,256",
+                    help="GEMM atoms per tile and signals per tile for --profile-batched "
                          "(the autotuner's choice in unprofiled runs)")
     ap.add_argument("--profile-rows", type=int, default=None, help="active rows of the --profile-gemm case")
     ap.add_argument("--gemm-sweep", choices=["bf16", "fp8"], default=None,

@@ -152,8 +152,7 @@ typedef enum {
     MP_OPT_BATCH_TILE_N = 5,   /* batched: atoms per GEMM tile (0 = autotuned)       */
     MP_OPT_PLAIN_PREFETCH = 6, /* grid streaming: stages pulled into L2 ahead of the */
                                /* shared-memory ring (0 = off, the default)          */
-    MP_OPT_BATCH_CLUSTER = 7,  /* batched GEMM: CTAs per cluster sharing one atom    */
-                               /* tile by TMA multicast: 1, 2, 4 (0 = auto)          */
+                               /* (7: no longer used)                                */
     MP_OPT_PLAIN_STAGE_BYTES = 8, /* grid streaming: target bytes per ring stage     */
                                /* (whole atoms, at least one; default 32768)         */
     MP_OPT_PLAIN_EVICT_FIRST = 9, /* grid streaming: 1 = evict-first L2 hint on the  */
@@ -174,9 +173,9 @@ typedef enum {
                                /* evict-last L2 hint so they stay in L2 from one     */
                                /* iteration to the next; the rest streams evict-first */
     MP_OPT_BATCH_TILE_M = 13   /* batched GEMM: signals per tile, 128 or 256 (two    */
-                               /* 128-row MMAs sharing each staged atom slice, no    */
-                               /* cluster; taken while the batch has more 128-row    */
-                               /* tiles than the GPU has SMs, 128 after); 0 = auto   */
+                               /* 128-row MMAs sharing each staged atom slice;       */
+                               /* taken while the batch has more 128-row tiles than  */
+                               /* the GPU has SMs, 128 after); 0 = auto              */
 } mp_option;
 
 /* Read-only plan properties for mp_plan_query. */
@@ -192,7 +191,7 @@ typedef enum {
     MP_Q_DEVICE_BYTES = 8,     /* device memory owned by the plan, bytes             */
     MP_Q_KERNEL_LAUNCHES = 9,  /* kernels this library launched for the plan so far  */
     MP_Q_BATCH_TILE_N = 10,    /* atoms per GEMM tile of the current batch state     */
-    MP_Q_BATCH_CLUSTER = 11,   /* GEMM cluster size of the current batch state       */
+                               /* (11: no longer used)                               */
     MP_Q_PLAIN64_MODE = 12,    /* mode the next mp_recover_f64 will use (0: none)    */
     MP_Q_PLAIN64_STAGES = 13,  /* its streaming ring depth                           */
     MP_Q_GRAM_BYTES = 14,      /* device bytes of the Gram matrix (0 until built)     */
@@ -348,16 +347,14 @@ MPGB_API mp_status mp_recover_batched(mp_plan_t plan, int prec, const float* Y, 
                              mp_result* host_out, void* stream);
 
 /* Autotuner of the batched correlation GEMM: times each tile shape (128 or
- * 256 signals per tile; 128 or 256 atoms per tile; 1, 2 or 4 CTAs sharing
- * an atom tile by multicast, 128-signal tiles only) on B synthetic rows at
+ * 256 signals per tile; 128 or 256 atoms per tile) on B synthetic rows at
  * precision `prec`, keeps the fastest for B's size bucket (the next power
  * of two, at least 128) and returns it.  With the default
  * MP_OPT_BATCH_AUTOTUNE = 1, mp_recover_batched runs the same timing on its
  * own first batch of a new bucket.  Options MP_OPT_BATCH_TILE_N /
- * MP_OPT_BATCH_CLUSTER / MP_OPT_BATCH_TILE_M, when set, override the
- * result.  Synchronises the legacy default stream.  tile_n, cluster,
- * tile_m: may be NULL. */
-MPGB_API mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* cluster, int* tile_m);
+ * MP_OPT_BATCH_TILE_M, when set, override the result.  Synchronises the
+ * legacy default stream.  tile_n, tile_m: may be NULL. */
+MPGB_API mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* tile_m);
 
 /* Diagnostic: the tensor-core correlations of the batched path, written out
  * in full.  R (device, B x N floats) is quantised as the batched step does
@@ -372,14 +369,13 @@ MPGB_API mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* 
  * epilogue, one launch per step) on B synthetic rows at precision `prec`:
  * the autotuner's timing routine, mean of `reps` launches after 2 warm-up
  * launches, written to *us in microseconds per launch.  Tile shape
- * (tile_m signals x tile_n atoms, `cluster` CTAs): 128 or 256, 128 or 256,
- * 1, 2 or 4 (cluster 1 when tile_m = 256); all three 0 = the shape
+ * (tile_m signals x tile_n atoms): 128 or 256 each; both 0 = the shape
  * mp_recover_batched would use for B signals (options, else autotuned).
  * Allocates its own buffers; synchronises the legacy default stream.
  * Errors: MP_ERR_INVALID (bad shape or argument), MP_ERR_UNSUPPORTED
  * (precision not built), MP_ERR_CUDA. */
-MPGB_API mp_status mp_debug_time_gemm(mp_plan_t plan, int prec, int B, int tile_m, int tile_n, int cluster,
-                                      int reps, double* us);
+MPGB_API mp_status mp_debug_time_gemm(mp_plan_t plan, int prec, int B, int tile_m, int tile_n, int reps,
+                                      double* us);
 
 /* ------------------------------------------------------------------ */
 /* One decode with the atoms split across ranks (one GPU each)         */

@@ -36,7 +36,6 @@ MP_OPT_DEBUG_SKIP_ARRIVE = 3
 MP_OPT_GRID_CTAS = 4
 MP_OPT_BATCH_TILE_N = 5
 MP_OPT_PLAIN_PREFETCH = 6
-MP_OPT_BATCH_CLUSTER = 7
 MP_OPT_PLAIN_STAGE_BYTES = 8
 MP_OPT_PLAIN_EVICT_FIRST = 9
 MP_OPT_BATCH_AUTOTUNE = 10
@@ -44,7 +43,6 @@ MP_OPT_PLAIN_GRAM = 11
 MP_OPT_PLAIN_L2_KEEP_BYTES = 12
 MP_OPT_BATCH_TILE_M = 13
 MP_Q_BATCH_TILE_N = 10
-MP_Q_BATCH_CLUSTER = 11
 MP_Q_BATCH_TILE_M = 17
 
 MP_Q_PLAIN_MODE = 1
@@ -137,8 +135,8 @@ SIGNATURES = {
     "mp_recover_batched": (_I, [_P, _I, _P, _P, _I, ctypes.POINTER(mp_stop), _I,
                                 ctypes.POINTER(mp_trace), ctypes.POINTER(mp_result), _P]),
     "mp_debug_correlations": (_I, [_P, _I, _P, _I, _P, _P]),
-    "mp_debug_time_gemm": (_I, [_P, _I, _I, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_double)]),
-    "mp_plan_autotune": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "mp_debug_time_gemm": (_I, [_P, _I, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_double)]),
+    "mp_plan_autotune": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "mp_recover_noalloc": (_I, [_P, _I, _I, _I, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_result), _P]),
     "mp_shard_record_bytes": (ctypes.c_size_t, [_P]),
     "mp_shard_init": (_I, [_P, _P, _P, _P, ctypes.POINTER(mp_stop), _P, _P]),
@@ -313,12 +311,11 @@ def mp_recover_batched(plan, prec, Y_ptr, X_ptr, B, stops, trace=None, stream=No
 
 
 def mp_plan_autotune(plan, prec, B):
-    """Returns the (atoms per tile, cluster size, signals per tile) the
-    autotuner picked."""
-    tn, cl, tm = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    check(lib().mp_plan_autotune(plan, int(prec), int(B), ctypes.byref(tn), ctypes.byref(cl), ctypes.byref(tm)),
+    """Returns the (atoms per tile, signals per tile) the autotuner picked."""
+    tn, tm = ctypes.c_int(), ctypes.c_int()
+    check(lib().mp_plan_autotune(plan, int(prec), int(B), ctypes.byref(tn), ctypes.byref(tm)),
           "mp_plan_autotune")
-    return tn.value, cl.value, tm.value
+    return tn.value, tm.value
 
 
 def mp_recover_noalloc(psi_ptr, N, M, ld, y_ptr, x_ptr, stop, result, stream=None):
@@ -336,12 +333,12 @@ def mp_debug_correlations(plan, prec, R_ptr, B, C_ptr, stream=None):
                  "mp_debug_correlations")
 
 
-def mp_debug_time_gemm(plan, prec, B, shape=(0, 0, 0), reps=20):
+def mp_debug_time_gemm(plan, prec, B, shape=(0, 0), reps=20):
     """Microseconds per launch of the batched correlation GEMM on B
-    synthetic rows; shape = (signals per tile, atoms per tile, cluster),
-    (0, 0, 0) = the shape a batch of B would use."""
+    synthetic rows; shape = (signals per tile, atoms per tile), (0, 0) =
+    the shape a batch of B would use."""
     us = ctypes.c_double()
-    check(lib().mp_debug_time_gemm(plan, int(prec), int(B), int(shape[0]), int(shape[1]), int(shape[2]), int(reps),
+    check(lib().mp_debug_time_gemm(plan, int(prec), int(B), int(shape[0]), int(shape[1]), int(reps),
                                    ctypes.byref(us)), "mp_debug_time_gemm")
     return us.value
 

@@ -33,7 +33,7 @@ constexpr int kGemmThreads = 32 * (2 + 4 * kEpiGroups);   // warp 0 TMA, warp 1 
 struct CorrArgs {
     const int* n_act;       // active rows this step (rows 0..n_act-1 of the A operand)
     int TN;                 // atoms per tile (128 or 256)
-    int RM;                 // 128-row blocks per tile (1 or 2; 1 when clustered)
+    int RM;                 // 128-row blocks per tile (1 or 2)
     int n_at;               // atom tiles
     int M;
     int nk;                 // K blocks of 128 bytes
@@ -53,13 +53,12 @@ struct CorrArgs {
 
 int corr_smem_bytes(int TM, int TN);
 cudaError_t corr_prepare();
-int corr_max_clusters(int CL, int TN);
-// Launch with clusters of CL (1, 2 or 4) CTAs along the signal rows; tmB's
-// box is TN/CL atom rows, tmA's 128 signal rows, tmBh's (when a.half_ok)
-// TN/2 atom rows.  max_rows bounds the active rows any step of this launch
-// can see (it sizes the grid).
+int corr_max_ctas();
+// Launch: tmA's box is 128 signal rows, tmB's TN atom rows, tmBh's (when
+// a.half_ok) TN/2 atom rows.  max_rows bounds the active rows any step of
+// this launch can see (it sizes the grid).
 cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmBh, const CorrArgs& a,
-                             int max_rows, int CL, cudaStream_t st);
+                             int max_rows, cudaStream_t st);
 
 // ------------------------------------------------------------------ batch engine
 // Per-signal state of a slot.
@@ -98,7 +97,6 @@ struct BatchEngine {
     int prec = -1;
     int TM = 128;           // signal rows per GEMM tile
     int TN = 0;
-    int CL = 1;             // GEMM cluster size along signal rows
     int n_at = 0;
     int ldq = 0;            // operand row: elements (BF16) or bytes (FP8)
     float* R32 = nullptr;

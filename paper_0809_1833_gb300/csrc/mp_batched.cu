@@ -688,27 +688,20 @@ mp_status batch_shape(PlanImpl* p, int prec, int B, const float* R, cudaStream_t
     const int rt = (B + kBM - 1) / kBM;
     GemmShape g;
     g.tn = 256;
-    g.cl = rt >= 4 ? 4 : (rt >= 2 ? 2 : 1);
-    if (p->batch_autotune && !p->batch_tile_n && !p->batch_cluster && !p->batch_tile_m) {
+    g.tm = rt >= 2 ? 256 : 128;
+    if (p->batch_autotune && !p->batch_tile_n && !p->batch_tile_m) {
         mp_status s = autotune(p, prec, B, R, st, &g);
         if (s != MP_OK) return s;
     }
     if (p->batch_tile_n) g.tn = p->batch_tile_n;
-    if (p->batch_cluster) g.cl = p->batch_cluster;
     if (p->batch_tile_m) g.tm = p->batch_tile_m;
-    if (g.tm == 256 && g.cl > 1) {
-        if (p->batch_cluster > 1 && p->batch_tile_m == 256)
-            return fail(MP_ERR_INVALID, "batched GEMM: 256-signal tiles run without clusters");
-        if (p->batch_tile_m == 256) g.cl = 1;
-        else g.tm = 128;
-    }
     *shape = g;
     return MP_OK;
 }
 
 static mp_status engine_prepare(PlanImpl* p, int prec, int cap, const GemmShape& g) {
     BatchEngine* e = p->batch;
-    if (e && e->prec == prec && e->cap >= cap && e->TM == g.tm && e->TN == g.tn && e->CL == g.cl) return MP_OK;
+    if (e && e->prec == prec && e->cap >= cap && e->TM == g.tm && e->TN == g.tn) return MP_OK;
     if (!e) e = p->batch = new BatchEngine();
     return engine_alloc(e, p, prec, std::max(cap, e->cap), g);
 }
@@ -721,7 +714,6 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     e->prec = prec;
     e->TM = g.tm;
     e->TN = TN;
-    e->CL = g.cl;
     e->n_at = (p->M + TN - 1) / TN;
     const bool fp8 = prec == MP_PREC_FP8E4M3;
     e->ldq = fp8 ? p->ldK8 : p->ldK16;
@@ -743,7 +735,7 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     A(&e->surv, sizeof(int) * C);
     // room for the lists of half-width tiles (taken by the GEMM when few row
     // blocks are active)
-    const bool half_ok = TN == 256 && e->CL == 1;
+    const bool half_ok = TN == 256;
     const size_t n_at_max = half_ok ? (p->M + TN / 2 - 1) / (TN / 2) : e->n_at;
     A(&e->cand, sizeof(uint2) * C * n_at_max * kTop);
     A(&e->eps2, sizeof(double) * C);
@@ -766,9 +758,8 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     }
     mp_status s = make_map(&e->tmA, e->Rq, fp8, e->cap_pad, e->ldq, kBM);
     if (s == MP_OK) s = make_map(&e->tmA1, static_cast<char*>(e->Rq) + qbytes, fp8, e->cap_pad, e->ldq, kBM);
-    // each CTA of a GEMM cluster loads TN / CL atom rows and multicasts them
-    if (s == MP_OK) s = make_map(&e->tmB, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, TN / e->CL);
-    if (s == MP_OK) s = make_map(&e->tmBh, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, half_ok ? TN / 2 : TN / e->CL);
+    if (s == MP_OK) s = make_map(&e->tmB, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, TN);
+    if (s == MP_OK) s = make_map(&e->tmBh, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, half_ok ? TN / 2 : TN);
     if (s != MP_OK) {
         engine_free(e);
         return s;
@@ -787,7 +778,7 @@ static CorrArgs corr_args(PlanImpl* p, BatchEngine* e) {
     // the next) when they fit in TMEM's 512 columns, else one
     const int nbuf = (ca.RM == 1 || 2 * ca.RM * e->TN <= 512) ? 2 : 1;
     ca.n_at = e->n_at;
-    ca.half_ok = e->TN == 256 && e->CL == 1 ? 1 : 0;
+    ca.half_ok = e->TN == 256 ? 1 : 0;
     ca.M = p->M;
     ca.nk = (fp8 ? p->ldK8 : p->ldK16 * 2) / kRowBytes;
     ca.fp8 = fp8 ? 1 : 0;
@@ -827,7 +818,7 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, cudaStream
     ca.n_act = cnt[half];
     ca.zero_next = cnt[1 - half];
     ca.n_at_out = e->counters + 4;
-    cudaError_t r = launch_corr_top8(half ? e->tmA1 : e->tmA, e->tmB, e->tmBh, ca, e->cap_pad, e->CL, st);
+    cudaError_t r = launch_corr_top8(half ? e->tmA1 : e->tmA, e->tmB, e->tmBh, ca, e->cap_pad, st);
     if (r != cudaSuccess) return r;
     SelArgs sa;
     sa.n_act = cnt[half];
@@ -1097,7 +1088,7 @@ mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B,
     CorrArgs ca = corr_args(p, e);
     ca.dump = C;
     ca.rscale = e->rscale;
-    MP_CUDA_TRY(launch_corr_top8(e->tmA, e->tmB, e->tmBh, ca, B, e->CL, st));
+    MP_CUDA_TRY(launch_corr_top8(e->tmA, e->tmB, e->tmBh, ca, B, st));
     p->launches += 2;
     MP_CUDA_TRY(cudaMemcpyAsync(e->h_err, e->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1158,9 +1149,9 @@ static double time_gemm(PlanImpl* p, int prec, int B, const GemmShape& g, const 
         if (r == cudaSuccess) r = cudaEventCreate(&e0);
         if (r == cudaSuccess) r = cudaEventCreate(&e1);
         const CorrArgs ca = corr_args(p, &e);
-        for (int it = 0; it < 2 && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, e.tmBh, ca, B, e.CL, st);
+        for (int it = 0; it < 2 && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, e.tmBh, ca, B, st);
         if (r == cudaSuccess) r = cudaEventRecord(e0, st);
-        for (int it = 0; it < reps && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, e.tmBh, ca, B, e.CL, st);
+        for (int it = 0; it < reps && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, e.tmBh, ca, B, st);
         if (r == cudaSuccess) r = cudaEventRecord(e1, st);
         if (r == cudaSuccess) r = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -1195,17 +1186,13 @@ mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_
     for (int tm : {128, 256}) {
         if (tm == 256 && rt < 2) continue;      // one row block: the same work as 128
         for (int tn : {256, 128}) {
-            for (int cl : {1, 2, 4}) {
-                if (cl > 1 && (cl > rt || tm != 128)) continue;
-                GemmShape g;
-                g.tm = tm;
-                g.tn = tn;
-                g.cl = cl;
-                const double us = time_gemm(p, prec, B, g, R_dev ? R_dev : R, st);
-                if (us > 0.0 && (best < 0.0 || us < best)) {
-                    best = us;
-                    best_g = g;
-                }
+            GemmShape g;
+            g.tm = tm;
+            g.tn = tn;
+            const double us = time_gemm(p, prec, B, g, R_dev ? R_dev : R, st);
+            if (us > 0.0 && (best < 0.0 || us < best)) {
+                best = us;
+                best_g = g;
             }
         }
     }
@@ -1221,7 +1208,7 @@ mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_
 
 extern "C" {
 
-mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* cluster, int* tile_m) {
+mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* tile_m) {
     clear_error();
     if (!plan || B < 1) return fail(MP_ERR_INVALID, "mp_plan_autotune: bad argument");
     PlanImpl* p = &plan->impl;
@@ -1233,12 +1220,11 @@ mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* cl
     mp_status s = autotune(p, prec, B, nullptr, nullptr, &g);
     if (s != MP_OK) return s;
     if (tile_n) *tile_n = g.tn;
-    if (cluster) *cluster = g.cl;
     if (tile_m) *tile_m = g.tm;
     return MP_OK;
 }
 
-mp_status mp_debug_time_gemm(mp_plan_t plan, int prec, int B, int tile_m, int tile_n, int cluster, int reps,
+mp_status mp_debug_time_gemm(mp_plan_t plan, int prec, int B, int tile_m, int tile_n, int reps,
                              double* us) {
     clear_error();
     if (!plan || B < 1 || reps < 1 || !us) return fail(MP_ERR_INVALID, "mp_debug_time_gemm: bad argument");
@@ -1248,13 +1234,11 @@ mp_status mp_debug_time_gemm(mp_plan_t plan, int prec, int B, int tile_m, int ti
     if (!(p->prec_mask & (1u << prec)))
         return fail(MP_ERR_UNSUPPORTED, "mp_debug_time_gemm: the plan holds no copy for this precision");
     GemmShape g;
-    if (tile_m || tile_n || cluster) {
-        if ((tile_m != 128 && tile_m != 256) || (tile_n != 128 && tile_n != 256) ||
-            (cluster != 1 && cluster != 2 && cluster != 4) || (tile_m == 256 && cluster != 1))
+    if (tile_m || tile_n) {
+        if ((tile_m != 128 && tile_m != 256) || (tile_n != 128 && tile_n != 256))
             return fail(MP_ERR_INVALID, "mp_debug_time_gemm: bad tile shape");
         g.tm = tile_m;
         g.tn = tile_n;
-        g.cl = cluster;
     } else {
         mp_status s = batch_shape(p, prec, B, nullptr, nullptr, &g);
         if (s != MP_OK) return s;

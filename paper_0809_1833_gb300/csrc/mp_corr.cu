@@ -5,15 +5,10 @@
 // largest |c| of each atom tile kept in registers and written out, so the
 // correlation matrix itself is never stored.
 //
-// Operand reuse, within a CTA: a tile of 256 signal rows is two 128-row
-// MMAs per K slice reading the same staged atom slice, so each atom byte
-// brought into the SM feeds 256 rows (and each signal byte TN atoms).
-// Across CTAs: a cluster of CL CTAs takes CL consecutive 128-signal row
-// tiles of one atom tile.  Each CTA loads its own rows of R, but only 1/CL of
-// the atom tile, and multicasts that slice to every CTA of the cluster; a
-// stage is refilled only after all CL CTAs released it (their MMA commits are
-// multicast to every CTA's "empty" barrier).  The atom operand, the larger
-// one, then crosses from L2 once per cluster instead of once per CTA.
+// Operand reuse: a tile of 256 signal rows is two 128-row MMAs per K slice
+// reading the same staged atom slice, so each atom byte brought into the SM
+// feeds 256 rows (and each signal byte TN atoms).  Every CTA loads its own
+// operand tiles; no shared memory is written by another CTA.
 #include <cuda.h>
 
 #include <algorithm>
@@ -116,36 +111,33 @@ struct CorrCtx {
     uint32_t tmem;
     uint32_t as_stride;    // bytes of one stage's A region (room for the largest tile)
     int n_act, n_blk;      // active rows, 128-row blocks holding them
-    int n_rg, n_ct;        // row-tile groups, cluster tiles (for this launch's RM)
+    int n_rt, n_ct;        // row tiles and tiles (for this launch's RM)
     int tn, n_at;          // atoms per tile and atom tiles of this launch
     int stages;            // ring depth for this launch's tile
     uint32_t b_stride;     // bytes of one stage's B region
-    int cid, n_clusters, q, warp, lane;
-    uint16_t all;          // cluster CTA mask
+    int warp, lane;
     uint64_t lim;          // watchdog, ns
 };
 
 // The producer, MMA and epilogue roles over this CTA's tiles of RM 128-row
 // blocks x TN atoms.
-template <int CL, int RM>
+template <int RM>
 MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CorrArgs& a, const CorrCtx& x) {
-    static_assert(RM == 1 || (RM == 2 && CL == 1), "256-row tiles take no cluster");
     const int TN = a.TN;      // stage and accumulator strides
-    const int tn = x.tn;      // atoms per tile in this launch: TN, or TN / 2 (one CTA per cluster)
+    const int tn = x.tn;      // atoms per tile in this launch: TN, or TN / 2
     // TMEM accumulator buffers: two unless one tile fills the 512 columns
     const int nbuf = (RM == 1 || RM * TN * 2 <= 512) ? 2 : 1;
     const uint32_t a_bytes = kBM * kRowBytes;        // one row block of a stage
     const uint32_t as_bytes = x.as_stride;
     const uint32_t b_bytes = x.b_stride;         // one stage's B region (tn atom rows)
-    const uint32_t slice_bytes = b_bytes / CL;   // this CTA's share of the atom tile
     const int stages = x.stages;
     uint8_t* tilesA = x.tilesA;
     uint8_t* tilesB = x.tilesB;
     CorrShared* sh = x.sh;
     const uint32_t tmem = x.tmem;
-    const int n_act = x.n_act, n_blk = x.n_blk, n_rg = x.n_rg, n_ct = x.n_ct;
-    const int cid = x.cid, n_clusters = x.n_clusters, q = x.q, warp = x.warp, lane = x.lane;
-    const uint16_t all = x.all;
+    const int n_act = x.n_act, n_blk = x.n_blk, n_rt = x.n_rt, n_ct = x.n_ct;
+    const int cid = static_cast<int>(blockIdx.x), n_ctas = static_cast<int>(gridDim.x);
+    const int warp = x.warp, lane = x.lane;
     const uint64_t lim = x.lim;
 
     if (warp == 0) {
@@ -159,14 +151,12 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
             uint32_t ph = 0;
             const int kelems = a.fp8 ? kRowBytes : kRowBytes / 2;
             bool stop = false;
-            for (int ct = cid; ct < n_ct && !stop; ct += n_clusters) {
-                const int rt = (ct % n_rg) * CL + q, at = ct / n_rg;
-                // row blocks of this tile with active rows (with one block per
-                // tile, a clustered CTA past the last one still loads its
-                // block: its peers need its multicast slice)
+            for (int ct = cid; ct < n_ct && !stop; ct += n_ctas) {
+                const int rt = ct % n_rt, at = ct / n_rt;
+                // row blocks of this tile with active rows
                 const int nmb = RM == 1 ? 1 : min(RM, n_blk - rt * RM);
                 for (int kb = 0; kb < a.nk; ++kb) {
-                    // all CL CTAs released the stage's previous use
+                    // the MMAs released the stage's previous use
                     if (g >= stages && !mbar_wait_bounded(&sh->empty[s], ph ^ 1u, lim)) {
                         corr_timeout(a.err, sh);
                         stop = true;
@@ -183,11 +173,7 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
                         if (mb < nmb)
                             tma_load_2d(tilesA + s * as_bytes + mb * a_bytes, tmA, kb * kelems,
                                         (rt * RM + mb) * kBM, &sh->full[s]);
-                    if (CL == 1)
-                        tma_load_2d(tilesB + s * b_bytes, tmB, kb * kelems, at * tn, &sh->full[s]);
-                    else
-                        tma_load_2d_multicast(tilesB + s * b_bytes + q * slice_bytes, tmB, kb * kelems,
-                                              at * TN + q * (TN / CL), &sh->full[s], all);
+                    tma_load_2d(tilesB + s * b_bytes, tmB, kb * kelems, at * tn, &sh->full[s]);
                     ++g;
                     if (++s == stages) {
                         s = 0;
@@ -197,8 +183,7 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
             }
             // before the CTA may exit: its own loads have landed (the only one
             // that can be in flight in stage s is the last one issued to it),
-            // and every CTA of the cluster released the stages' last uses, so
-            // no peer still writes into this CTA or arrives on its barriers
+            // and the MMAs released the stages' last uses
             for (int t = 0; t < stages && t < g; ++t) {
                 const long long last = g - 1 - ((g - 1 - t) % stages);
                 mbar_wait_bounded(&sh->full[t], static_cast<uint32_t>((last / stages) & 1), lim);
@@ -214,8 +199,8 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
             int s = 0, buf = 0, li = 0;
             uint32_t ph = 0, bph = 0;
             bool ok = true;
-            for (int ct = cid; ct < n_ct && ok; ct += n_clusters, ++li) {
-                const int rt = (ct % n_rg) * CL + q;
+            for (int ct = cid; ct < n_ct && ok; ct += n_ctas, ++li) {
+                const int rt = ct % n_rt;
                 const int nmb = RM == 1 ? 1 : min(RM, n_blk - rt * RM);
                 if (li >= nbuf && !mbar_wait_bounded(&sh->tempty[buf], bph ^ 1u, lim)) {
                     corr_timeout(a.err, sh);
@@ -237,10 +222,8 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
                     const uint64_t b0 = sw128_kmajor_desc(smem_u32(tilesB + s * b_bytes));
                     if (a.fp8) issue_kblock<RM, true>(d, a0, b0, idesc, nmb, TN, kb == 0);
                     else issue_kblock<RM, false>(d, a0, b0, idesc, nmb, TN, kb == 0);
-                    // stage reusable once these MMAs finish (in every CTA that
-                    // will refill it with a multicast)
-                    if (CL == 1) mma_commit(&sh->empty[s]);
-                    else mma_commit_multicast(&sh->empty[s], all);
+                    // stage reusable once these MMAs finish
+                    mma_commit(&sh->empty[s]);
                     if (++s == stages) {
                         s = 0;
                         ph ^= 1u;
@@ -271,8 +254,8 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
         uint32_t bph = 0;
         uint32_t xround = 0;          // exchange rounds of this quadrant so far
         bool alive = true;
-        for (int ct = cid; ct < n_ct && alive; ct += n_clusters) {
-            const int rt = (ct % n_rg) * CL + q, at = ct / n_rg;
+        for (int ct = cid; ct < n_ct && alive; ct += n_ctas) {
+            const int rt = ct % n_rt, at = ct / n_rt;
             const int nmb = RM == 1 ? 1 : min(RM, n_blk - rt * RM);
             bool ok = mbar_wait_bounded(&sh->tfull[buf], bph, lim) &&
                       !*reinterpret_cast<volatile int*>(&sh->abort);
@@ -378,16 +361,14 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
 // RM = 2: 256-row tiles while the batch has more 128-row tiles than the
 // grid has CTAs, 128-row tiles once it has drained below that (the choice
 // is made per launch from the active row count, the same in every CTA).
-template <int CL, int RM>
+template <int RM>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     corr_top8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmBh, const CorrArgs a) {
     extern __shared__ uint8_t smem_raw[];
     // operand tiles need 1024-byte alignment for the 128-byte swizzle atoms
-    // (the same offset in every CTA, as multicast writes the same offsets)
     const uint32_t base_u32 = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
-    static_assert(RM == 1 || (RM == 2 && CL == 1), "256-row tiles take no cluster");
     CorrCtx x;
     // the ring the launch allocated (a.stages stages of RM row blocks and TN
     // atoms), then the barriers and the epilogue's exchange lists
@@ -397,24 +378,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     x.warp = threadIdx.x >> 5;
     x.lane = threadIdx.x & 31;
     const int warp = x.warp;
-    x.q = CL > 1 ? static_cast<int>(cluster_ctarank()) : 0;     // rank in the cluster
-    x.cid = static_cast<int>(blockIdx.x) / CL;
-    x.n_clusters = static_cast<int>(gridDim.x) / CL;
     // the step's select kernel appends its survivors to the other half; its
     // count was last read by the previous step, which has completed
     if (a.zero_next && blockIdx.x == 0 && threadIdx.x == 0) *a.zero_next = 0;
     x.n_act = *a.n_act;
     x.n_blk = (x.n_act + kBM - 1) / kBM;     // 128-row blocks holding active rows
     const int rm = (RM == 2 && x.n_blk * a.n_at > static_cast<int>(gridDim.x)) ? 2 : 1;
-    const int n_rt = (x.n_blk + rm - 1) / rm;      // row tiles of rm blocks
-    x.n_rg = (n_rt + CL - 1) / CL;                  // groups of CL row tiles
+    x.n_rt = (x.n_blk + rm - 1) / rm;        // row tiles of rm blocks
     // with few row blocks the grid has SMs to spare: tiles of TN / 2 atoms
     // double the tiles and give each SM 2/3 of the bytes of a TN-atom tile,
     // as long as they all still fit in one wave.  The candidate set each row
     // ends with is the same (its best 8 keys are in their tiles' lists)
     x.tn = a.TN;
     x.n_at = a.n_at;
-    if (CL == 1 && rm == 1 && a.half_ok) {
+    if (rm == 1 && a.half_ok) {
         const int n_at_h = (a.M + a.TN / 2 - 1) / (a.TN / 2);
         if (x.n_blk * n_at_h <= static_cast<int>(gridDim.x)) {
             x.tn = a.TN / 2;
@@ -425,21 +402,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     // the ring re-cut into stages of this launch's tile (rm row blocks, tn
     // atoms): a smaller tile gets a deeper ring, so that as many bytes stay
     // in flight per SM as with the largest one (up to kMaxStages stages).
-    // The same in every CTA of a cluster.  Offsets stay 1024-byte aligned.
+    // Offsets stay 1024-byte aligned.
     x.as_stride = static_cast<uint32_t>(rm) * kBM * kRowBytes;
     x.b_stride = static_cast<uint32_t>(x.tn) * kRowBytes;
     x.stages = min(kMaxStages, static_cast<int>(ring_bytes / (x.as_stride + x.b_stride)));
     x.tilesA = smem;
     x.tilesB = smem + x.stages * x.as_stride;
-    x.n_ct = x.n_rg * x.n_at;                       // cluster tiles
-    if (x.cid >= x.n_ct) return;                    // uniform across the cluster
-    x.all = static_cast<uint16_t>((1u << CL) - 1u);
+    x.n_ct = x.n_rt * x.n_at;                       // tiles
+    if (static_cast<int>(blockIdx.x) >= x.n_ct) return;   // a CTA with no tile
     x.lim = a.watchdog_ns;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < x.stages; ++s) {
             mbar_init(&sh->full[s], 1);
-            mbar_init(&sh->empty[s], CL);
+            mbar_init(&sh->empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sh->tfull[b], 1);
@@ -458,17 +434,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     if (warp == 1) tmem_alloc(&sh->tmem_base, static_cast<uint32_t>(a.tmem_cols));
     tc_fence_before();
     __syncthreads();
-    if (CL > 1) cluster_sync_all();   // every CTA's barriers exist before any multicast
     tc_fence_after();
     x.tmem = sh->tmem_base;
     const uint32_t tmem = x.tmem;
 
     const CUtensorMap* mb = x.tn == a.TN ? &tmB : &tmBh;
     if constexpr (RM == 2) {
-        if (rm == 2) corr_roles<CL, 2>(&tmA, mb, a, x);
-        else corr_roles<CL, 1>(&tmA, mb, a, x);
+        if (rm == 2) corr_roles<2>(&tmA, mb, a, x);
+        else corr_roles<1>(&tmA, mb, a, x);
     } else {
-        corr_roles<CL, 1>(&tmA, mb, a, x);
+        corr_roles<1>(&tmA, mb, a, x);
     }
 
     tc_fence_before();
@@ -477,94 +452,60 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         tc_fence_after();
         tmem_dealloc(tmem, static_cast<uint32_t>(a.tmem_cols));
     }
-    if (CL > 1) cluster_sync_all();   // no CTA leaves while a peer may still address it
 }
 
 int corr_smem_bytes(int TM, int TN) {
     return 1024 + corr_stages(TM, TN) * (TM * kRowBytes + TN * kRowBytes) + static_cast<int>(sizeof(CorrShared));
 }
 
-template <int CL, int RM>
+template <int RM>
 static cudaError_t set_attrs() {
     const int most = std::max(corr_smem_bytes(kBM * RM, 128), corr_smem_bytes(kBM * RM, 256));
-    return cudaFuncSetAttribute(corr_top8_kernel<CL, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    return cudaFuncSetAttribute(corr_top8_kernel<RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
 }
 
 cudaError_t corr_prepare() {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = set_attrs<1, 1>();
-    if (e == cudaSuccess) e = set_attrs<2, 1>();
-    if (e == cudaSuccess) e = set_attrs<4, 1>();
-    if (e == cudaSuccess) e = set_attrs<1, 2>();
+    cudaError_t e = set_attrs<1>();
+    if (e == cudaSuccess) e = set_attrs<2>();
     if (e == cudaSuccess) done = true;
     return e;
 }
 
-// Largest number of CL-CTA clusters that can be resident at once.
-int corr_max_clusters(int CL, int TN) {
-    static int cache[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
-    const int ci = CL == 1 ? 0 : (CL == 2 ? 1 : 2), ti = TN == 256 ? 1 : 0;
-    if (cache[ci][ti] >= 0) return cache[ci][ti];
+// CTAs that can be resident at once (one per SM: each takes most of the
+// SM's shared memory).
+int corr_max_ctas() {
+    static int cache = -1;
+    if (cache >= 0) return cache;
     int sm = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
-    int n = sm / CL;
-    if (CL > 1 && corr_prepare() == cudaSuccess) {
-        cudaLaunchConfig_t lc = {};
-        lc.gridDim = dim3(CL);
-        lc.blockDim = dim3(kGemmThreads);
-        lc.dynamicSmemBytes = corr_smem_bytes(kBM, TN);
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = CL;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        lc.attrs = at;
-        lc.numAttrs = 1;
-        int k = 0;
-        cudaError_t e = CL == 2 ? cudaOccupancyMaxActiveClusters(&k, corr_top8_kernel<2, 1>, &lc)
-                                : cudaOccupancyMaxActiveClusters(&k, corr_top8_kernel<4, 1>, &lc);
-        if (e == cudaSuccess && k > 0) n = std::min(n, k);
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sm < 1) {
         cudaGetLastError();
+        return 1;
     }
-    cache[ci][ti] = n;
-    return n;
+    cache = sm;
+    return cache;
 }
 
 cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmBh, const CorrArgs& a,
-                             int max_rows, int CL, cudaStream_t st) {
+                             int max_rows, cudaStream_t st) {
     const int nbuf = (a.RM == 1 || a.RM * a.TN * 2 <= 512) ? 2 : 1;   // as the kernel computes it
-    if ((CL > 1 && a.RM != 1) || (a.RM != 1 && a.RM != 2) || nbuf * a.RM * a.TN > a.tmem_cols ||
-        a.stages != corr_stages(kBM * a.RM, a.TN) || (a.half_ok && (CL != 1 || a.TN != 256)))
+    if ((a.RM != 1 && a.RM != 2) || nbuf * a.RM * a.TN > a.tmem_cols ||
+        a.stages != corr_stages(kBM * a.RM, a.TN) || (a.half_ok && a.TN != 256))
         return cudaErrorInvalidValue;
-    // enough clusters for the largest tile count this launch can see (with
+    // enough CTAs for the largest tile count this launch can see (with
     // RM = 2 the kernel takes 128-row tiles whenever they fit the grid, so
     // the grid is sized by those)
     const int max_rt = (max_rows + kBM - 1) / kBM;
-    int max_ct = ((max_rt + CL - 1) / CL) * a.n_at;
+    int max_ct = max_rt * a.n_at;
     if (a.half_ok)   // room for the half-width tiles of one or two row blocks
         max_ct = std::max(max_ct, std::min(max_rt, 2) * ((a.M + a.TN / 2 - 1) / (a.TN / 2)));
-    const int clusters = std::max(1, std::min(max_ct, corr_max_clusters(CL, a.TN)));
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3(clusters * CL);
-    lc.blockDim = dim3(kGemmThreads);
-    lc.dynamicSmemBytes = corr_smem_bytes(kBM * a.RM, a.TN);
-    lc.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = CL;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    lc.attrs = at;
-    lc.numAttrs = 1;
-    if (a.RM == 2) return cudaLaunchKernelEx(&lc, corr_top8_kernel<1, 2>, tmA, tmB, tmBh, a);
-    switch (CL) {
-        case 1: return cudaLaunchKernelEx(&lc, corr_top8_kernel<1, 1>, tmA, tmB, tmBh, a);
-        case 2: return cudaLaunchKernelEx(&lc, corr_top8_kernel<2, 1>, tmA, tmB, tmBh, a);
-        case 4: return cudaLaunchKernelEx(&lc, corr_top8_kernel<4, 1>, tmA, tmB, tmBh, a);
-    }
-    return cudaErrorInvalidValue;
+    const int ctas = std::max(1, std::min(max_ct, corr_max_ctas()));
+    const int smem = corr_smem_bytes(kBM * a.RM, a.TN);
+    if (a.RM == 2) corr_top8_kernel<2><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, a);
+    else corr_top8_kernel<1><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, a);
+    return cudaGetLastError();
 }
 
 }  // namespace mpgb

@@ -95,13 +95,10 @@ inline void omp_free(OmpWorkspace* o) {
 struct BatchEngine;        // batched decode state (mp_batched.cu)
 
 // Shape of the batched correlation GEMM's tiles: TM signal rows (128, or
-// 256 = two 128-row MMAs sharing each atom stage), TN atoms (128 or 256),
-// and CL CTAs per cluster sharing an atom tile by multicast (1, 2 or 4;
-// clusters only with TM = 128).
+// 256 = two 128-row MMAs sharing each atom stage) and TN atoms (128 or 256).
 struct GemmShape {
     int tm = 128;
     int tn = 256;
-    int cl = 1;
 };
 
 // Autotuned batched-GEMM shape for one (precision, batch-size bucket).
@@ -151,7 +148,6 @@ struct PlanImpl {
     int grid_ctas = 0;
     int batch_tile_n = 0;
     int batch_tile_m = 0;           // batched GEMM signal rows per tile (0 = auto)
-    int batch_cluster = 0;          // batched GEMM cluster size (0 = auto)
     int batch_autotune = 1;         // time the GEMM shapes on first use of a batch size
     std::vector<TuneEntry> tuned;
     int prefetch_stages = 0;        // plain streaming: L2 prefetch distance (measured slower; off)
@@ -179,11 +175,9 @@ mp_status plain_launch64(PlanImpl* p, const double* y, double* x, const mp_stop*
 
 // Batched engine teardown (mp_batched.cu).
 void batch_destroy(BatchEngine* b);
-// GEMM shape (atoms per tile, cluster size) for a batch of B signals: the
+// GEMM shape (signals and atoms per tile) for a batch of B signals: the
 // plan's options if set, else the autotuned choice (timed now on first use
-// of the batch-size bucket, on rows R when given), else a heuristic.
-// The GEMM shape for a batch of B signals: the explicit options, else the
-// autotuned shape of B's size bucket, else a fixed rule.
+// of the batch-size bucket, on rows R when given), else a fixed rule.
 mp_status batch_shape(PlanImpl* p, int prec, int B, const float* R, cudaStream_t st, GemmShape* shape);
 
 }  // namespace mpgb

@@ -342,11 +342,6 @@ mp_status mp_plan_set_option(mp_plan_t plan, int option, long long value) {
         case MP_OPT_BATCH_AUTOTUNE:
             p->batch_autotune = value ? 1 : 0;
             return MP_OK;
-        case MP_OPT_BATCH_CLUSTER:
-            if (value != 0 && value != 1 && value != 2 && value != 4)
-                return fail(MP_ERR_INVALID, "batch cluster size must be 0, 1, 2 or 4");
-            p->batch_cluster = static_cast<int>(value);
-            return MP_OK;
         case MP_OPT_BATCH_TILE_N:
             if (value != 0 && value != 128 && value != 256)
                 return fail(MP_ERR_INVALID, "batch tile must be 0, 128 or 256");
@@ -378,7 +373,6 @@ mp_status mp_plan_query(mp_plan_t plan, int what, long long* value) {
         case MP_Q_DEVICE_BYTES: *value = static_cast<long long>(p->device_bytes); return MP_OK;
         case MP_Q_KERNEL_LAUNCHES: *value = p->launches; return MP_OK;
         case MP_Q_BATCH_TILE_N: *value = p->batch ? p->batch->TN : 0; return MP_OK;
-        case MP_Q_BATCH_CLUSTER: *value = p->batch ? p->batch->CL : 0; return MP_OK;
         case MP_Q_BATCH_TILE_M: *value = p->batch ? p->batch->TM : 0; return MP_OK;
         case MP_Q_PLAN_N: *value = p->N; return MP_OK;
         case MP_Q_PLAN_M: *value = p->M; return MP_OK;

@@ -18,15 +18,6 @@ MP_DEV void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
-// Same, delivered to the same shared-memory offset (and mbarrier offset) in
-// every CTA of the cluster named by `mask`.
-MP_DEV void tma_load_2d_multicast(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
-        "[%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
-        : "memory");
-}
 MP_DEV void tma_prefetch_desc(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
@@ -95,16 +86,6 @@ MP_DEV void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
                  : "memory");
-}
-
-// Arrive on the same-offset mbarrier of every CTA in `mask` once every
-// tcgen05 op issued so far by this thread is done.
-MP_DEV void mma_commit_multicast(uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(mask)
-        : "memory");
 }
 
 // Warp-wide load of 32 consecutive FP32 columns of this warp's 32 TMEM lanes

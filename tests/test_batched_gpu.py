@@ -44,20 +44,19 @@ def e4m3_rows(a):
     return q.astype(np.float64), s.astype(np.float64)
 
 
-# (signals per tile, atoms per tile, cluster size)
-TILES = [(128, 256, 1), (128, 256, 2), (128, 256, 4), (128, 128, 1), (256, 256, 1), (256, 128, 1)]
+# (signals per tile, atoms per tile)
+TILES = [(128, 256), (128, 128), (256, 256), (256, 128)]
 
 
-@pytest.mark.parametrize("tile", TILES, ids=lambda t: f"TM{t[0]}_TN{t[1]}_CL{t[2]}")
+@pytest.mark.parametrize("tile", TILES, ids=lambda t: f"TM{t[0]}_TN{t[1]}")
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
 @pytest.mark.parametrize("shape", [(256, 1000, 200), (100, 300, 5), (2048, 1024, 130), (192, 777, 600)],
                          ids=lambda s: f"N{s[0]}_M{s[1]}_B{s[2]}")
 def test_tensor_core_correlations(prec, shape, tile):
-    """Every tile shape gives the exact quantised product: atom tiles shared
-    by TMA multicast across 1, 2 or 4 CTAs, 256-signal tiles (two MMAs per
-    staged atom slice, one TMEM buffer at 256 atoms) whose second row block
-    is full, partial or absent, row tiles beyond the batch and a ragged last
-    atom tile."""
+    """Every tile shape gives the exact quantised product: 128- and
+    256-signal tiles (two MMAs per staged atom slice, one TMEM buffer at 256
+    atoms) whose second row block is full, partial or absent, row tiles
+    beyond the batch and a ragged last atom tile."""
     T = torch()
     N, M, Bn = shape
     psi = W.gaussian_dictionary(N, M, seed=3)
@@ -67,12 +66,10 @@ def test_tensor_core_correlations(prec, shape, tile):
     with GpuPlan(psi, prec_mask=1 << p) as pl:
         pl.set(B().MP_OPT_BATCH_TILE_M, tile[0])
         pl.set(B().MP_OPT_BATCH_TILE_N, tile[1])
-        pl.set(B().MP_OPT_BATCH_CLUSTER, tile[2])
         Rd = T.from_numpy(R).cuda()
         C = T.full((Bn, M), float("nan"), dtype=T.float32, device="cuda")
         B().mp_debug_correlations(pl.plan, p, Rd.data_ptr(), Bn, C.data_ptr(), cur_stream())
-        assert (pl.query(B().MP_Q_BATCH_TILE_M), pl.query(B().MP_Q_BATCH_TILE_N),
-                pl.query(B().MP_Q_BATCH_CLUSTER)) == tile
+        assert (pl.query(B().MP_Q_BATCH_TILE_M), pl.query(B().MP_Q_BATCH_TILE_N)) == tile
         C = C.cpu().numpy().astype(np.float64)
     if prec == "bf16":
         A = bf16_round(R).astype(np.float64)
@@ -111,7 +108,6 @@ def test_tensor_core_correlations_two_block_tiles(prec, tn):
     with GpuPlan(psi, prec_mask=1 << p) as pl:
         pl.set(B().MP_OPT_BATCH_TILE_M, 256)
         pl.set(B().MP_OPT_BATCH_TILE_N, tn)
-        pl.set(B().MP_OPT_BATCH_CLUSTER, 1)
         Rd = T.from_numpy(R).cuda()
         C = T.full((Bn, M), float("nan"), dtype=T.float32, device="cuda")
         B().mp_debug_correlations(pl.plan, p, Rd.data_ptr(), Bn, C.data_ptr(), cur_stream())
@@ -143,7 +139,6 @@ def test_batched_decode_switching_tile_rows_equals_128_row_tiles():
         with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
             pl.set(B().MP_OPT_BATCH_TILE_M, tm)
             pl.set(B().MP_OPT_BATCH_TILE_N, 256)
-            pl.set(B().MP_OPT_BATCH_CLUSTER, 1)
             s, res, X, atoms, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
             assert s == 0
             out[tm] = (res, X, atoms)
@@ -175,14 +170,13 @@ def run_batched(pl, prec, Y, stops, cap=4096):
     return s, res, X.cpu().numpy(), atoms.cpu().numpy(), coefs.cpu().numpy()
 
 
-@pytest.mark.parametrize("tile", [(128, 1), (128, 4), (256, 1)], ids=lambda t: f"TM{t[0]}_CL{t[1]}")
+@pytest.mark.parametrize("tile", [128, 256], ids=lambda t: f"TM{t}")
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
 def test_batched_matches_plain_and_oracle(prec, tile):
     prob = W.make_batched(256, 1024, 300, 2, 16, seed=5, eps=1e-5, T=3000)
     p = B().MP_PREC_BF16 if prec == "bf16" else B().MP_PREC_FP8E4M3
     with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
-        pl.set(B().MP_OPT_BATCH_TILE_M, tile[0])
-        pl.set(B().MP_OPT_BATCH_CLUSTER, tile[1])
+        pl.set(B().MP_OPT_BATCH_TILE_M, tile)
         s, res, X, atoms, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
         assert s == 0
         n_same = 0
@@ -208,17 +202,16 @@ def test_autotuner_picks_a_valid_shape_and_results_do_not_depend_on_it():
     prob = W.make_batched(256, 2048, 260, 2, 12, seed=6, eps=1e-5, T=2000)
     p = B().MP_PREC_BF16
     with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
-        tn, cl, tm = B().mp_plan_autotune(pl.plan, p, prob.B)
-        assert tn in (128, 256) and cl in (1, 2, 4) and tm in (128, 256) and (tm == 128 or cl == 1)
-        assert B().mp_plan_autotune(pl.plan, p, prob.B) == (tn, cl, tm)      # cached per size bucket
+        tn, tm = B().mp_plan_autotune(pl.plan, p, prob.B)
+        assert tn in (128, 256) and tm in (128, 256)
+        assert B().mp_plan_autotune(pl.plan, p, prob.B) == (tn, tm)      # cached per size bucket
         s, res, X, _, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
         assert s == 0
-        q = (B().MP_Q_BATCH_TILE_N, B().MP_Q_BATCH_CLUSTER, B().MP_Q_BATCH_TILE_M)
-        assert tuple(pl.query(k) for k in q) == (tn, cl, tm)
-        other = (128 if tn == 256 else 256, 1, 256 if tm == 128 else 128)
+        q = (B().MP_Q_BATCH_TILE_N, B().MP_Q_BATCH_TILE_M)
+        assert tuple(pl.query(k) for k in q) == (tn, tm)
+        other = (128 if tn == 256 else 256, 256 if tm == 128 else 128)
         pl.set(B().MP_OPT_BATCH_TILE_N, other[0])
-        pl.set(B().MP_OPT_BATCH_CLUSTER, other[1])
-        pl.set(B().MP_OPT_BATCH_TILE_M, other[2])
+        pl.set(B().MP_OPT_BATCH_TILE_M, other[1])
         s2, res2, X2, _, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
         assert tuple(pl.query(k) for k in q) == other
     assert s2 == 0 and np.array_equal(X, X2)
