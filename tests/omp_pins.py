@@ -27,6 +27,21 @@ def check_worked_example(orc):
     assert np.allclose(out["coefs"], ex["coefs"], rtol=0, atol=1e-14)
     assert np.allclose(out["x"], ex["x"], rtol=0, atol=1e-14)
     assert np.linalg.norm(out["r"]) <= 1e-14
+    # top-two gaps before each selection, by hand: 1/6, then 1/4
+    assert np.allclose(out["gaps"], ex["gaps"], rtol=0, atol=1e-14)
+
+
+def check_follow_worked_example(orc):
+    """Follow mode with the imposed order 0, 2 (the reverse of OMP's):
+    ratios 5/6 and 4/5, max|c| and ||r|| before each step, the final fit."""
+    g = load_worked_example()
+    fx = g["follow"]
+    f = orc.follow(g["psi_atoms"], g["y"], fx["atoms"])
+    assert np.allclose(f["ratio"], fx["ratio"], rtol=0, atol=1e-14)
+    assert np.allclose(f["cmax"], fx["cmax"], rtol=0, atol=1e-14)
+    assert np.allclose(f["rnorm"], fx["rnorm"], rtol=0, atol=1e-14)
+    assert np.allclose(f["x"], fx["x"], rtol=0, atol=1e-14)
+    assert np.linalg.norm(f["r"]) <= 1e-14
 
 
 def check_orthonormal_equals_mp(orc):
@@ -42,6 +57,17 @@ def check_orthonormal_equals_mp(orc):
     assert out["iters"] == K and out["stop_reason"] == orc.STOP_CONVERGED
     assert list(out["atoms"]) == list(supp[np.argsort(-np.abs(x[supp]), kind="stable")])
     assert np.max(np.abs(out["x"] - x)) <= 1e-12
+    # correlations before step k are the unselected entries of x: gap
+    # (m_k - m_{k+1}) / m_k with m the sorted magnitudes, 1 at the last step;
+    # follow along OMP's own order gives ratio 1, max|c| = m_k (whatever the
+    # sign of that entry; here some are negative) and ||r|| = the norm of the
+    # unselected entries
+    m = np.sort(np.abs(x[supp]))[::-1]
+    assert np.max(np.abs(out["gaps"] - np.append((m[:-1] - m[1:]) / m[:-1], 1.0))) <= 1e-12
+    f = orc.follow(Q, x @ Q, out["atoms"])
+    assert np.all(np.abs(f["ratio"] - 1.0) <= 1e-12)
+    assert np.max(np.abs(f["cmax"] - m)) <= 1e-12
+    assert np.max(np.abs(f["rnorm"] - np.sqrt(np.cumsum((m ** 2)[::-1])[::-1]))) <= 1e-12
 
 
 def check_residual_orthogonal_to_selected(orc):
@@ -113,7 +139,11 @@ def check_tie_goes_to_smallest_index(orc):
     index is selected first."""
     out = orc.omp(np.eye(3), np.array([2.0, -2.0, 1.0]), 0.0, 3)
     assert list(out["atoms"]) == [0, 1, 2]
+    # gaps: |c| = (2, 2, 1) is a tie (0); then (0, 2, 1) gives 1/2; then
+    # (0, 0, 1) gives 1
+    assert list(out["gaps"]) == [0.0, 0.5, 1.0]
 
 
-ALL_CHECKS = [check_tie_goes_to_smallest_index, check_worked_example, check_orthonormal_equals_mp, check_residual_orthogonal_to_selected,
+ALL_CHECKS = [check_tie_goes_to_smallest_index, check_worked_example, check_follow_worked_example,
+              check_orthonormal_equals_mp, check_residual_orthogonal_to_selected,
               check_exact_recovery_in_k_steps, check_rank_stop, check_first_step_is_mp, check_stop_reasons]

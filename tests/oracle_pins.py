@@ -35,6 +35,26 @@ def check_worked_example(orc):
     # the same values follow from the closed form e_t = 3 * 4^-t
     t = np.arange(1, ex["iters"] + 1)
     assert np.array_equal(out["energies"], 3.0 * 4.0 ** (-t))
+    # top-two gaps before each update: the exact tie of step 1 gives 0, every
+    # later step 1/3 (1/3 rounded once: 1/4 over 3/4 and its power-of-two
+    # scalings are correctly rounded divisions of the same ratio)
+    assert np.array_equal(out["gaps"], np.array(ex["gaps"]))
+    assert out["gaps"][0] == 0.0 and np.all(out["gaps"][1:] == 1.0 / 3.0)
+
+
+def check_follow_worked_example(orc):
+    """Follow mode on the worked example with an imposed non-MP sequence
+    (5, 0, 5), values derived by hand: ratio |c_i| / max|c| before each
+    step, max|c| (largest magnitude, whatever its sign), ||r|| before each
+    step, and the final x~ and r."""
+    g = load_worked_example()
+    fx = g["follow"]
+    f = orc.follow(np.array(g["psi_atoms"]), np.array(g["y"]), fx["atoms"])
+    assert np.allclose(f["ratio"], fx["ratio"], rtol=1e-15, atol=0)
+    assert np.array_equal(f["cmax"], np.array(fx["cmax"]))
+    assert np.allclose(f["rnorm"] ** 2, fx["rnorm2"], rtol=1e-15, atol=0)
+    assert np.array_equal(f["x"], np.array(fx["x"]))
+    assert np.array_equal(f["r"], np.array(fx["r"]))
 
 
 def check_energy_conservation(orc):
@@ -97,6 +117,20 @@ def check_orthonormal_exact(orc):
     assert out["iters"] == K
     assert list(out["atoms"]) == list(supp[np.argsort(-mags, kind="stable")])
     assert np.max(np.abs(out["x"] - x)) <= 1e-12
+    # before step k the correlations are the not yet selected entries of x
+    # (selected ones are 0 up to rounding), so the top-two gap is
+    # (m_k - m_{k+1}) / m_k with m sorted by decreasing magnitude, and 1 at
+    # the last step
+    m = np.sort(mags)[::-1]
+    gap = np.append((m[:-1] - m[1:]) / m[:-1], 1.0)
+    assert np.max(np.abs(out["gaps"] - gap)) <= 1e-12
+    # follow mode along MP's own sequence: ratio 1, max|c| = m_k whatever
+    # the sign of that entry, ||r|| = the norm of the entries still unselected
+    f = orc.follow(Q, y, out["atoms"])
+    assert np.all(np.abs(f["ratio"] - 1.0) <= 1e-12)
+    assert np.max(np.abs(f["cmax"] - m)) <= 1e-12
+    tail = np.sqrt(np.cumsum((m ** 2)[::-1])[::-1])
+    assert np.max(np.abs(f["rnorm"] - tail)) <= 1e-12
 
 
 def check_against_loops(orc):
@@ -138,7 +172,7 @@ def check_stop_reasons(orc):
     assert loose["iters"] == 0 and loose["stop_reason"] == 0
 
 
-ALL_CHECKS = [check_worked_example, check_energy_conservation,
+ALL_CHECKS = [check_worked_example, check_follow_worked_example, check_energy_conservation,
               check_energy_identity_general, check_monotone_residual,
               check_reconstruction_identity, check_orthonormal_exact,
               check_against_loops, check_one_sparse, check_stop_reasons]

@@ -27,6 +27,24 @@ MUTATIONS = {
     "stale_energy": ("        e = float(np.dot(r, r))\n        t += 1", "        t += 1"),
     "stop_strict": ("    while e > thr2 and t < T:", "    while e >= thr2 and t < T:"),
     "x_scattered_to_wrong_atoms": ("        x[S] = xs", "        x[np.sort(S)] = xs"),
+    # the top-two gap behind the parity tests' near-tie window
+    "gap_absolute": ("gaps.append((float(a[i]) - second) / float(a[i]) if a[i] > 0 else 0.0)",
+                     "gaps.append(float(a[i]) - second)"),
+    "gap_after_update": ("second = float(np.partition(a, M - 2)[M - 2])",
+                         "a = np.abs(P @ r); second = float(np.partition(a, M - 2)[M - 2])"),
+    "gap_second_distinct_value": ("second = float(np.partition(a, M - 2)[M - 2])",
+                                  "second = float(np.max(a[a < a[i]])) if np.any(a < a[i]) else 0.0"),
+    "gap_second_is_max": ("second = float(np.partition(a, M - 2)[M - 2])",
+                          "second = float(np.partition(a, M - 1)[M - 1])"),
+    # follow mode
+    "follow_ratio_of_cmax_signed": ("        cmax = float(np.max(np.abs(c)))\n        ratio[k]",
+                                    "        cmax = float(np.max(c))\n        ratio[k]"),
+    "follow_rnorm_after_fit": ("        rnorm[k] = float(np.sqrt(np.dot(r, r)))\n        S.append(int(i))\n"
+                               "        A = P[S].T\n        xs = np.linalg.lstsq(A, y, rcond=None)[0]\n"
+                               "        r = y - A @ xs\n",
+                               "        S.append(int(i))\n        A = P[S].T\n"
+                               "        xs = np.linalg.lstsq(A, y, rcond=None)[0]\n        r = y - A @ xs\n"
+                               "        rnorm[k] = float(np.sqrt(np.dot(r, r)))\n"),
 }
 
 

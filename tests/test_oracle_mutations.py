@@ -27,6 +27,26 @@ MUTATIONS = {
     "stale_energy": ("e = float(np.dot(r, r))", "e = e"),
     "double_count_t": ("t += 1  ", "t += 2  "),
     "dropped_cap": ("while e > thr2 and t < T", "while e > thr2"),
+    # the top-two gap that sets every parity test's near-tie window
+    "gap_absolute": ("gaps.append((float(a[i]) - second) / float(a[i]) if a[i] > 0 else 0.0)",
+                     "gaps.append(float(a[i]) - second)"),
+    "gap_after_update": ("second = float(np.partition(a, M - 2)[M - 2])",
+                         "a = np.abs(P @ r); second = float(np.partition(a, M - 2)[M - 2])"),
+    "gap_second_distinct_value": ("second = float(np.partition(a, M - 2)[M - 2])",
+                                  "second = float(np.max(a[a < a[i]])) if np.any(a < a[i]) else 0.0"),
+    "gap_second_signed": ("second = float(np.partition(a, M - 2)[M - 2])",
+                          "second = float(np.max(np.delete(c, i)))"),
+    "gap_second_is_max": ("second = float(np.partition(a, M - 2)[M - 2])",
+                          "second = float(np.partition(a, M - 1)[M - 1])"),
+    # follow mode, whose max|c| and ||r|| set the tolerance of rule (iii)
+    "follow_ratio_signed": ("ratio[k] = abs(float(c[i])) / cmax if cmax > 0 else 1.0",
+                            "ratio[k] = float(c[i]) / cmax if cmax > 0 else 1.0"),
+    "follow_cmax_signed": ("cmax = float(np.max(np.abs(c)))", "cmax = float(np.max(c))"),
+    "follow_rnorm_after_update": ("        rnorm[k] = float(np.sqrt(np.dot(r, r)))\n        x[i] += float(c[i])\n"
+                                  "        r -= float(c[i]) * P[i]\n",
+                                  "        x[i] += float(c[i])\n        r -= float(c[i]) * P[i]\n"
+                                  "        rnorm[k] = float(np.sqrt(np.dot(r, r)))\n"),
+    "follow_x_overwrite": ("x[i] += float(c[i])", "x[i] = float(c[i])"),
 }
 
 
