@@ -147,30 +147,80 @@ def make_problem(n_signals, seed=0):
     return w, psi, Y, sigs
 
 
-def cpu_baseline(psi, y, eps, T, full_iters, budget_s=15.0):
-    """Time the FP64 oracle on the host cores on the first iterations of one
-    decode; extrapolate to recoveries/s with the full decode's iteration
-    count."""
+def workload_config(w, world):
+    """The ``config`` object of both arms' JSON lines (identical keys)."""
+    return {"workload": WORKLOAD, "N": w["N"], "M": w["M"], "K": w["K"], "eps": w["eps"], "T": w["T"],
+            "l2": "inputs exceed L2: the 256 MiB dictionary is streamed from HBM every iteration",
+            "parallelism": f"dp{world} (independent signals)"}
+
+
+def oracle_per_iteration(psi, y, eps, n):
+    """Seconds per FP64 oracle iteration over the first ``n`` iterations of
+    one decode.  Each oracle call widens the dictionary to a fresh FP64 copy
+    before its loop; a call with T = 0 (the copy and nothing else) is timed
+    right before and subtracted.  Returns (s per iteration, iterations,
+    seconds of the timed call)."""
     from oracle import mp_oracle as orc
-    # size the sample from a short run (21 minus 1 iterations, so the
-    # oracle's one-off FP64 copy of the dictionary cancels), then time a run
-    # of about budget_s seconds
     t0 = time.perf_counter()
-    orc.mp(psi, y, eps, 1, record=False)
+    orc.mp(psi, y, eps, 0, record=False)
     t1 = time.perf_counter()
-    orc.mp(psi, y, eps, 21, record=False)
-    t2 = time.perf_counter()
-    est = max(((t2 - t1) - (t1 - t0)) / 20.0, 1e-6)
-    n = int(max(3, min(full_iters, budget_s / est)))
-    t0 = time.perf_counter()
     out = orc.mp(psi, y, eps, n, record=False)
-    dt = time.perf_counter() - t0
-    per_iter = dt / max(out["iters"], 1)
+    t2 = time.perf_counter()
+    return max((t2 - t1) - (t1 - t0), 1e-9) / max(out["iters"], 1), out["iters"], t2 - t1
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_sample(psi, y, eps, full_iters, budget_s):
+    est, _, _ = oracle_per_iteration(psi, y, eps, 8)
+    n = int(max(4, min(full_iters, budget_s / est)))
+    per_iter, done, dt = oracle_per_iteration(psi, y, eps, n)
+    return per_iter, done, dt
+
+
+def cpu_baseline(psi, y, eps, T, full_iters, budget_s=15.0, single_budget_s=10.0):
+    """The FP64 oracle on the host cores over the first iterations of one
+    decode, extrapolated to recoveries/s with the full decode's iteration
+    count: on all cores (this process) and single-threaded (a child process
+    with the BLAS thread count set to 1 before numpy loads)."""
+    per_iter, done, dt = _oracle_sample(psi, y, eps, full_iters, budget_s)
     cores = os.cpu_count()
-    return {"value": 1.0 / (per_iter * full_iters), "unit": "recoveries/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {out['iters']} of {full_iters} iterations of one decode of {WORKLOAD} "
-                      f"(FP64 numpy, {dt:.1f} s); recoveries/s = 1/(s per iteration x {full_iters})",
-            "s_per_iteration": per_iter}
+    out = {"value": 1.0 / (per_iter * full_iters), "unit": "recoveries/s", "cores": cores, "kind": "oracle",
+           "sample": f"first {done} of {full_iters} iterations of one decode of {WORKLOAD} "
+                     f"(FP64 numpy, {dt:.1f} s, the FP64 copy of the dictionary timed apart and subtracted); "
+                     f"recoveries/s = 1/(s per iteration x {full_iters})",
+           "s_per_iteration": per_iter, "cpu_model": cpu_model()}
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        p = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", str(single_budget_s),
+                            "--cpu-worker-iters", str(full_iters)], env=env, capture_output=True, text=True,
+                           timeout=600)
+        one = json.loads(p.stdout.strip().splitlines()[-1])
+        out["single_thread"] = {"value": 1.0 / (one["s_per_iteration"] * full_iters), "unit": "recoveries/s",
+                                "cores": 1, "s_per_iteration": one["s_per_iteration"],
+                                "sample": f"first {one['iterations']} iterations, {one['seconds']:.1f} s, "
+                                          f"BLAS threads 1"}
+    except Exception as ex:
+        out["single_thread"] = {"value": None, "why": f"{type(ex).__name__}: {ex}"[:200]}
+    return out
+
+
+def cpu_worker(budget_s, full_iters):
+    """Child process of cpu_baseline: the same oracle sample with the thread
+    count the environment sets; prints one JSON line."""
+    w, psi, Y, _ = make_problem(1)
+    per_iter, done, dt = _oracle_sample(psi, Y[0], w["eps"], full_iters, budget_s)
+    print(json.dumps({"s_per_iteration": per_iter, "iterations": done, "seconds": dt}), flush=True)
 
 
 def run_reference(args):
@@ -180,25 +230,26 @@ def run_reference(args):
     w, psi, Y, sigs = make_problem(1)
     from oracle import mp_oracle as orc
     # iteration count of the full decode of this signal, from one untimed
-    # full oracle run; each timed step is a bounded prefix of it
+    # full oracle run; each timed step is a bounded prefix of it, with the
+    # oracle's one-off FP64 copy of the dictionary timed apart and subtracted
     full_iters = orc.mp(psi, Y[0], w["eps"], w["T"], record=False)["iters"]
-    sample_iters = 20
-    times = []
+    sample_iters = 100
+    per_iters, step_s = [], []
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        orc.mp(psi, Y[0], w["eps"], sample_iters, record=False)
-        dt = time.perf_counter() - t0
+        pi, done, dt = oracle_per_iteration(psi, Y[0], w["eps"], sample_iters)
         if i >= args.warmup:
-            times.append(dt)
-    per_iter = sum(times) / (len(times) * sample_iters)
+            per_iters.append(pi)
+            step_s.append(dt)
+    per_iter = sum(per_iters) / len(per_iters)
     v = 1.0 / (per_iter * full_iters)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "recoveries/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(step_s) / len(step_s),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "N": w["N"], "M": w["M"], "K": w["K"],
-                                            "eps": w["eps"], "T": w["T"]},
+            "data": "synthetic", "config": workload_config(w, args.gpus),
             "cpu_baseline": {"value": v, "unit": "recoveries/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"each step = {sample_iters} FP64 oracle iterations of one decode; "
+                             "cpu_model": cpu_model(),
+                             "sample": f"each step = {sample_iters} FP64 oracle iterations of one decode, minus "
+                                       f"the oracle's one-off FP64 copy of the dictionary (timed apart); "
                                        f"recoveries/s = 1/(s per iteration x {full_iters})"},
             "e2e": {"value": v, "unit": "recoveries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -299,10 +350,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "recoveries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N, "M": M, "K": w["K"], "eps": w["eps"], "T": w["T"],
-                   "signals": n_sig, "iterations_per_decode": iters, "plain_mode": int(mode),
-                   "l2": "inputs exceed L2: the 256 MiB dictionary is streamed from HBM every iteration",
-                   "parallelism": f"dp{world} (independent signals)"},
+        "config": workload_config(w, world),
+        "run": {"signals": n_sig, "iterations_per_decode": iters, "plain_mode": int(mode)},
         "hbm_gbs": achieved,
         "us_per_iteration": 1e3 * sum(per_launch_ms) / sum(step_iters),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -323,7 +372,7 @@ def run_ours(args):
         line["plain_small"] = plain_small_measure()
         line["variants"] = variants_measure()
         # batched low-precision form vs the plain FP32 kernel on the same signals
-        line["batched"] = [batched_measure("bf16"), batched_measure("fp8", n_plain=4)]
+        line["batched"] = [batched_measure("bf16", n_oracle=4), batched_measure("fp8", n_plain=4, n_oracle=1)]
         line["fp8_gemm_peak"] = fp8_gemm_peak()
         # tensor-core fraction of the GEMM: BF16 against the measured burst
         # peak, FP8 against the vendor library's E4M3 rate measured above
@@ -469,9 +518,11 @@ def variants_measure(n_sig=4, gram_period=32):
     return out
 
 
-def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=(256, 256)):
+def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=(256, 256), n_oracle=0):
     """Batched low-precision decode of a whole batched workload vs the plain
-    FP32 kernel on the same signals (the first ``n_plain`` of them)."""
+    FP32 kernel on the same signals (the first ``n_plain`` of them); x~ of
+    ``n_oracle`` signals spread over the batch against full FP64 oracle
+    decodes."""
     import torch
     from oracle import mp_oracle as orc
     from paper_0809_1833_gb300 import binding as B
@@ -538,6 +589,15 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
             "how": "mp_debug_time_gemm: GEMM + top-8 epilogue on the full batch of synthetic rows, CUDA events, "
                    "mean of 20 launches after 2 warm-up"}
     B.mp_plan_destroy(plan)
+    oracle_sample = []
+    for i in (np.linspace(0, prob.B - 1, n_oracle).astype(int) if n_oracle else []):
+        t0 = time.perf_counter()
+        o = orc.mp(prob.psi, prob.y[i], w["eps"], w["T"], record=False)
+        nx = np.linalg.norm(o["x"])
+        oracle_sample.append({"signal": int(i), "x_rel_err_vs_oracle":
+                              float(np.linalg.norm(Xh[i].astype(np.float64) - o["x"]) / (nx if nx > 0 else 1.0)),
+                              "iters": int(res[i].iters), "oracle_iters": int(o["iters"]),
+                              "oracle_s": time.perf_counter() - t0})
     flops = 2.0 * prob.N * prob.M * float(iters.sum())
     rec_b, rec_p = prob.B / tb, n_plain / tp
     return {"workload": name, "precision": prec_name, "signals": prob.B, "recoveries_per_s": rec_b,
@@ -546,6 +606,8 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
             "support_score_mean": float(np.mean(supp_b)), "support_score_min": float(np.min(supp_b)),
             "plain_support_score_mean": float(np.mean(supp_p)),
             "x_rel_err_vs_truth_mean": float(np.mean(xerr)), "x_rel_err_vs_truth_max": float(np.max(xerr)),
+            "x_rel_err_vs_oracle_max": max((e["x_rel_err_vs_oracle"] for e in oracle_sample), default=None),
+            "oracle_sample": oracle_sample,
             "iterations_total": int(iters.sum()), "iterations_max": int(iters.max()),
             "effective_tflops": flops / tb / 1e12, "gpu_launches_per_batch": int(launches), "gemm_shape": shape,
             "active_rows_profile": active_profile,
@@ -597,62 +659,82 @@ def gemm_sweep(prec_name, shape, rows=(64, 128, 256, 384, 512, 768, 1024)):
     return {"gemm_sweep": BATCHED[prec_name], "gemm_shape": [tm, tn], "us_by_active_rows": us}
 
 
-def served_measure(rate=2000.0, duration=10.0, pool=48, seed=0, max_slots=256, drain_s=120.0):
+def served_measure(rate=2000.0, duration=60.0, pool_s=5.0, seed=0, max_slots=256, drain_s=120.0, n_oracle=2):
     """Poisson arrivals over the four resident dictionaries of the served
     workload; every request is submitted at its arrival time through the
     server's C ABI and polled until done.  Reports offered / completed rates,
     rejections and latency percentiles (server clock: submit -> result
-    ready; client clock: submit -> successful poll)."""
+    ready; client clock: submit -> successful poll), the support score of
+    every completed request, and x~ against the FP64 oracle for the first
+    ``n_oracle`` completed requests of each dictionary.
+
+    Signals: per dictionary a pool of distinct seeded signals as large as
+    ``pool_s`` seconds of that dictionary's arrivals (K ~ U{4..N/16}); a
+    request takes the next signal of its dictionary's pool."""
     import torch
+    from oracle import mp_oracle as orc
     from paper_0809_1833_gb300 import binding as B
     from paper_0809_1833_gb300 import workloads as W
     wl = W.WORKLOADS["served_4dict_poisson2000"]
     dicts = wl["dicts"]
     prec = B.MP_PREC_BF16
     s = torch.cuda.current_stream().cuda_stream
-    plans, pools = [], []
+    pool = max(16, int(np.ceil(rate * pool_s / len(dicts))))
+    plans, pools, psis = [], [], []
+    t_gen = time.perf_counter()
     for di, (N, M) in enumerate(dicts):
         psi = W.gaussian_dictionary(N, M, seed + 10 + di)
+        psis.append(psi)
         d = torch.from_numpy(psi).cuda()
         plans.append(B.mp_plan_create(N, M, d.data_ptr(), prec_mask=1 << prec, stream=s))
         del d
         g = np.random.default_rng([seed, 50 + di])
-        ys = []
+        ys, sups = [], []
         for k in range(pool):
             K = int(g.integers(4, N // 16 + 1))
-            x, _ = W.sparse_signal(M, K, g, wl["values"])
+            x, supp = W.sparse_signal(M, K, g, wl["values"])
             ys.append(np.ascontiguousarray(W.encode(psi, x)))
-        pools.append(ys)
+            sups.append(supp)
+        pools.append((ys, sups))
+    t_gen = time.perf_counter() - t_gen
     srv = B.mp_server_create(96 << 30, max_slots, 1 << 20)
     ids = [B.mp_server_add_dictionary(srv, p, prec) for p in plans]
     slots = [B.mp_server_dictionary_slots(srv, i) for i in ids]
     arr, dsel, _ = W.served_requests(dicts, rate, duration, seed)
+    xbuf = [np.empty(M, np.float32) for (_, M) in dicts]
     # warm-up: one request per dictionary
     for di in range(len(dicts)):
-        _, t = B.mp_server_submit(srv, ids[di], pools[di][0], wl["eps"], wl["T"])
+        _, t = B.mp_server_submit(srv, ids[di], pools[di][0][0], wl["eps"], wl["T"])
         while B.mp_server_poll(srv, t)[0] == B.MP_PENDING:
             time.sleep(0.001)
     B.mp_server_reset_stats(srv)
     pending, lat, rejected, n_sub = {}, [], 0, 0
+    next_sig = [0] * len(dicts)
+    scores, sampled = [], []
     t0 = time.perf_counter()
     i, n = 0, len(arr)
     while i < n or pending:
         now = time.perf_counter() - t0
         while i < n and arr[i] <= now:
             di = int(dsel[i])
-            st, t = B.mp_server_submit(srv, ids[di], pools[di][i % pool], wl["eps"], wl["T"])
+            k = next_sig[di] % pool
+            next_sig[di] += 1
+            st, t = B.mp_server_submit(srv, ids[di], pools[di][0][k], wl["eps"], wl["T"])
             if st == 0:
-                pending[t] = now
+                pending[t] = (now, di, k)
                 n_sub += 1
             else:
                 rejected += 1
             i += 1
         done = []
-        for t, ts in pending.items():
-            st, _ = B.mp_server_poll(srv, t)
+        for t, (ts, di, k) in pending.items():
+            st, _ = B.mp_server_poll(srv, t, xbuf[di])
             if st == B.MP_OK:
                 done.append(t)
                 lat.append(time.perf_counter() - t0 - ts)
+                scores.append(orc.support_score(xbuf[di], pools[di][1][k]))
+                if sum(1 for q in sampled if q[0] == di) < n_oracle:
+                    sampled.append((di, k, xbuf[di].copy()))
             if len(done) >= 256:
                 break
         for t in done:
@@ -666,7 +748,16 @@ def served_measure(rate=2000.0, duration=10.0, pool=48, seed=0, max_slots=256, d
     B.mp_server_destroy(srv)
     for p in plans:
         B.mp_plan_destroy(p)
+    # x~ of sampled requests against the FP64 oracle's decode of the same y
+    errs = []
+    for di, k, xg in sampled:
+        o = orc.mp(psis[di], pools[di][0][k], wl["eps"], wl["T"], record=False)
+        nx = np.linalg.norm(o["x"])
+        errs.append({"dictionary": list(dicts[di]), "x_rel_err_vs_oracle":
+                     float(np.linalg.norm(xg.astype(np.float64) - o["x"]) / (nx if nx > 0 else 1.0)),
+                     "oracle_iters": int(o["iters"])})
     lat = np.array(lat)
+    scores = np.array(scores) if scores else np.zeros(0)
     return {"workload": "served_4dict_poisson2000", "dictionaries": [list(d) for d in dicts], "precision": "bf16",
             "slots_per_dictionary": slots, "offered_rps": rate, "duration_s": duration, "requests": int(n),
             "submitted_rps": float(n_sub + rejected) / max(min(wall, duration), 1e-9),
@@ -676,7 +767,64 @@ def served_measure(rate=2000.0, duration=10.0, pool=48, seed=0, max_slots=256, d
             "server_p50_ms": 1e3 * stt.latency_p50_s, "server_p99_ms": 1e3 * stt.latency_p99_s,
             "client_p50_ms": 1e3 * float(np.percentile(lat, 50)) if lat.size else None,
             "client_p99_ms": 1e3 * float(np.percentile(lat, 99)) if lat.size else None,
-            "signal_pool": f"{pool} distinct seeded signals per dictionary, K ~ U{{4..N/16}}, reused across requests"}
+            "support_score_mean": float(scores.mean()) if scores.size else None,
+            "support_score_min": float(scores.min()) if scores.size else None,
+            "support_scored_requests": int(scores.size),
+            "oracle_sample": errs,
+            "x_rel_err_vs_oracle_max": max((e["x_rel_err_vs_oracle"] for e in errs), default=None),
+            "signal_pool": f"{pool} distinct seeded signals per dictionary ({pool_s:g} s of arrivals), "
+                           f"K ~ U{{4..N/16}}, taken in turn by that dictionary's requests",
+            "signal_generation_s": t_gen}
+
+
+def step_breakdown(rows=(1, 2, 4, 8, 16), dict_index=3, reps=3):
+    """Per-step device time of the batched BF16 decode on one served
+    dictionary at a few active-row counts: the whole step (mp_recover_batched
+    on that many signals, divided by the steps the longest one needed), the
+    correlation GEMM alone (mp_debug_time_gemm at the same rows, synthetic
+    residuals) and their difference (select / rescore / update and the
+    graph's step hand-off), next to the floor of reading the BF16 dictionary
+    once from HBM.  One JSON line per row count."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0809_1833_gb300 import binding as B
+    from paper_0809_1833_gb300 import workloads as W
+    wl = W.WORKLOADS["served_4dict_poisson2000"]
+    N, M = wl["dicts"][dict_index]
+    prec = B.MP_PREC_BF16
+    psi = W.gaussian_dictionary(N, M, 10 + dict_index)
+    d = torch.from_numpy(psi).cuda()
+    plan = B.mp_plan_create(N, M, d.data_ptr(), prec_mask=1 << prec)
+    del d
+    hbm, _ = measured_peaks()
+    g = np.random.default_rng([0, 77])
+    for nrow in rows:
+        ys = []
+        for _ in range(nrow):
+            K = int(g.integers(4, N // 16 + 1))
+            x, _ = W.sparse_signal(M, K, g, wl["values"])
+            ys.append(W.encode(psi, x))
+        Y = torch.from_numpy(np.stack(ys)).cuda()
+        X = torch.empty((nrow, M), device="cuda")
+        B.mp_recover_batched(plan, prec, Y.data_ptr(), X.data_ptr(), nrow, (wl["eps"], wl["T"]))
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            _, res = B.mp_recover_batched(plan, prec, Y.data_ptr(), X.data_ptr(), nrow, (wl["eps"], wl["T"]))
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b) * 1e3)
+        steps = max(r.iters for r in res)
+        step_us = statistics.median(times) / steps
+        gemm_us = B.mp_debug_time_gemm(plan, prec, nrow, reps=50)
+        print(json.dumps({"step_breakdown": {
+            "dictionary": [N, M], "active_rows": nrow, "steps": steps, "us_per_step": step_us,
+            "gemm_us": gemm_us, "rest_us": step_us - gemm_us,
+            "gemm_shape": [B.mp_plan_query(plan, B.MP_Q_BATCH_TILE_M), B.mp_plan_query(plan, B.MP_Q_BATCH_TILE_N)],
+            "hbm_floor_us": 2.0 * N * M / (hbm * 1e3)}}), flush=True)
+    B.mp_plan_destroy(plan)
 
 
 def fp8_error(n_sample=2):
@@ -925,7 +1073,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-only", type=int, default=0, metavar="REPEATS",
                     help="print only the batched BF16 and FP8 lines, REPEATS times")
-    ap.add_argument("--served-duration", type=float, default=10.0,
+    ap.add_argument("--served-duration", type=float, default=60.0,
                     help="seconds of Poisson arrivals for the served measurement (0 = skip)")
     ap.add_argument("--served-rate", type=float, default=2000.0)
     ap.add_argument("--served-only", action="store_true", help="run only the served measurement")
@@ -940,7 +1088,18 @@ def main():
     ap.add_argument("--phase-diagram", choices=["bf16", "fp8"], default=None,
                     help="run only Sec. 3's E(sigma, rho) diagram with the batched decode in this precision")
     ap.add_argument("--trials", type=int, default=100, help="signals per phase-diagram cell")
+    ap.add_argument("--step-breakdown", action="store_true",
+                    help="run only the per-step time breakdown of the batched BF16 decode on the largest served "
+                         "dictionary at 1-16 active rows")
+    ap.add_argument("--cpu-worker", type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-worker-iters", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_worker is not None:
+        cpu_worker(args.cpu_worker, args.cpu_worker_iters)
+        return
+    if args.step_breakdown:
+        step_breakdown()
+        return
     if args.phase_diagram:
         phase_diagram(args.trials, args.phase_diagram)
         return

@@ -335,8 +335,10 @@ MPGB_API mp_status mp_recover_host(mp_plan_t plan, const float* y_host, float* x
  *  Y        : device pointer, B x N floats, row b is y_b.
  *  X        : device pointer, B x M floats, row b receives x~_b.
  *  stops    : n_stops entries, 1 (shared) or B (per signal).
- *  trace    : optional; each array holds B rows of `capacity` entries
- *             (row b records signal b's steps; `residual` is ignored).
+ *  trace    : optional; atoms, coefs and energies each hold B rows of
+ *             `capacity` entries (row b records signal b's steps);
+ *             `residual`, when set, holds B rows of N floats and row b
+ *             receives signal b's final FP32 residual.
  *  host_out : B results (required); the call synchronises `stream`.
  * The plan keeps the batch state (residuals, quantised GEMM operand, slot
  * table, candidate buffer) between calls and grows it to the largest B.

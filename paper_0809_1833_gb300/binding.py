@@ -137,7 +137,8 @@ SIGNATURES = {
     "mp_debug_correlations": (_I, [_P, _I, _P, _I, _P, _P]),
     "mp_debug_time_gemm": (_I, [_P, _I, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_double)]),
     "mp_plan_autotune": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
-    "mp_recover_noalloc": (_I, [_P, _I, _I, _I, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_result), _P]),
+    "mp_recover_noalloc": (_I, [_P, _I, _I, _I, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_trace),
+                               ctypes.POINTER(mp_result), _P]),
     "mp_shard_record_bytes": (ctypes.c_size_t, [_P]),
     "mp_shard_init": (_I, [_P, _P, _P, _P, ctypes.POINTER(mp_stop), _P, _P]),
     "mp_shard_step_local": (_I, [_P, _I, _P, _P, _P]),
@@ -318,11 +319,13 @@ def mp_plan_autotune(plan, prec, B):
     return tn.value, tm.value
 
 
-def mp_recover_noalloc(psi_ptr, N, M, ld, y_ptr, x_ptr, stop, result, stream=None):
+def mp_recover_noalloc(psi_ptr, N, M, ld, y_ptr, x_ptr, stop, result, stream=None, trace=None):
     """Allocation-free decode (include/mpgb_noalloc.h): ``stop`` is an
-    mp_stop, ``result`` an mp_result filled in place; returns the status."""
+    mp_stop, ``result`` an mp_result filled in place, ``trace`` an optional
+    mp_trace; returns the status."""
     return lib().mp_recover_noalloc(ctypes.c_void_p(int(psi_ptr)), int(N), int(M), int(ld),
                                     ctypes.c_void_p(int(y_ptr)), ctypes.c_void_p(int(x_ptr)), ctypes.byref(stop),
+                                    ctypes.byref(trace) if trace is not None else None,
                                     ctypes.byref(result), _stream(stream))
 
 

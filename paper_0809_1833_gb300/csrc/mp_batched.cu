@@ -983,6 +983,11 @@ static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, lo
             if (e->h_cnt[(k - 1) & 1] == 0) break;
         }
     }
+    // each signal's final FP32 residual (slot b = signal b), for callers that
+    // check the drift of this path's own arithmetic
+    if (trace && trace->residual)
+        MP_CUDA_TRY(cudaMemcpy2DAsync(trace->residual, sizeof(float) * p->N, e->R32, sizeof(float) * p->ldN,
+                                      sizeof(float) * p->N, B, cudaMemcpyDeviceToDevice, st));
     MP_CUDA_TRY(cudaMemcpyAsync(e->h_st, e->st, sizeof(SlotState) * B, cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaMemcpyAsync(e->h_err, e->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1039,7 +1044,7 @@ mp_status mp_recover_batched(mp_plan_t plan, int prec, const float* Y, float* X,
                 tb.atoms = trace->atoms ? trace->atoms + off : nullptr;
                 tb.coefs = trace->coefs ? trace->coefs + off : nullptr;
                 tb.energies = trace->energies ? trace->energies + off : nullptr;
-                tb.residual = nullptr;
+                tb.residual = trace->residual ? trace->residual + static_cast<size_t>(b) * p->N : nullptr;
                 tp = &tb;
             }
             mp_status s = mp_recover(plan, Y + static_cast<size_t>(b) * p->N, X + static_cast<size_t>(b) * p->M, sb, tp,

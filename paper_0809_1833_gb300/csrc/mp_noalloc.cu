@@ -10,6 +10,7 @@
 // result record) in the file-scope array below instead of in plan memory.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -27,7 +28,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 // Device address of g_noalloc_scratch per device ordinal.  In host code the
 // array's name is only a host-side stand-in, so the address is looked up
-// with cudaGetSymbolAddress, once per device, with that device current.
+// with cudaGetSymbolAddress, once per device, with that device current.  A
+// cudaDeviceReset of that device invalidates the cached address (as it does
+// every other device pointer the caller holds).
 constexpr int kMaxDevices = 64;
 static void* g_scratch_addr[kMaxDevices] = {};
 static std::mutex g_scratch_mu;
@@ -52,7 +55,7 @@ using namespace mpgb;
 extern "C" {
 
 mp_status mp_recover_noalloc(const float* psi, int N, int M, int ld, const float* y, float* x, const mp_stop* stop,
-                             mp_result* host_out, void* stream) {
+                             const mp_trace* trace, mp_result* host_out, void* stream) {
     clear_error();
     if (!psi || !y || !x || !stop || !host_out) return fail(MP_ERR_INVALID, "mp_recover_noalloc: NULL argument");
     if (N < 1 || M < 1) return fail(MP_ERR_INVALID, "mp_recover_noalloc: N and M must be >= 1");
@@ -61,8 +64,9 @@ mp_status mp_recover_noalloc(const float* psi, int N, int M, int ld, const float
     if (reinterpret_cast<uintptr_t>(psi) % 16 != 0)
         return fail(MP_ERR_INVALID, "mp_recover_noalloc: psi must be 16-byte aligned");
     if (static_cast<long long>(M) * ld > (1LL << 40)) return fail(MP_ERR_INVALID, "mp_recover_noalloc: dictionary too large");
-    if (!(stop->eps >= 0.0) || stop->max_iters < 0 || stop->reserved != 0)
-        return fail(MP_ERR_INVALID, "mp_recover_noalloc: bad stop parameters");
+    if (!(stop->eps >= 0.0) || !std::isfinite(stop->eps) || stop->max_iters < 0 || stop->reserved != 0)
+        return fail(MP_ERR_INVALID, "mp_recover_noalloc: bad stop parameters (eps must be finite and >= 0, T >= 0)");
+    if (trace && trace->capacity < 0) return fail(MP_ERR_INVALID, "mp_recover_noalloc: trace capacity < 0");
     if (sizeof(PlainWorkspace) > kNoAllocScratchBytes)
         return fail(MP_ERR_UNSUPPORTED, "mp_recover_noalloc: scratch need exceeds the 256-byte static array");
 
@@ -71,8 +75,21 @@ mp_status mp_recover_noalloc(const float* psi, int N, int M, int ld, const float
     PlanImpl p;
     cudaError_t e = cudaGetDevice(&p.device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    cudaDeviceGetAttribute(&p.sm_count, cudaDevAttrMultiProcessorCount, p.device);
-    cudaDeviceGetAttribute(&p.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (st) {
+        // the kernel runs on the current device: a stream of another device
+        // is a caller error, reported here rather than as a launch failure
+        int sdev = -1;
+        e = cudaStreamGetDevice(st, &sdev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamGetDevice");
+        if (sdev != p.device)
+            return fail(MP_ERR_INVALID, "mp_recover_noalloc: the stream belongs to device " + std::to_string(sdev) +
+                                            ", the current device is " + std::to_string(p.device));
+    }
+    e = cudaDeviceGetAttribute(&p.sm_count, cudaDevAttrMultiProcessorCount, p.device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(multiprocessor count)");
+    e = cudaDeviceGetAttribute(&p.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p.device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(shared memory per block, opt-in)");
     p.N = N;
     p.M = M;
     p.ldN = ld;
@@ -81,9 +98,8 @@ mp_status mp_recover_noalloc(const float* psi, int N, int M, int ld, const float
     mp_status s = scratch_address(p.device, &scratch);
     if (s != MP_OK) return s;
     PlainWorkspace* ws = static_cast<PlainWorkspace*>(scratch);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     // plain_launch clears the scratch on `st` before the kernel starts
-    s = plain_launch(&p, y, x, stop, nullptr, ws, st);
+    s = plain_launch(&p, y, x, stop, trace, ws, st);
     if (s != MP_OK) return s;
     PlainWorkspace h;
     std::memset(&h, 0, sizeof(h));

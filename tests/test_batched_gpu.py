@@ -10,7 +10,7 @@
 import numpy as np
 import pytest
 
-from gpu_helpers import GpuPlan, compare_to_oracle, cur_stream
+from gpu_helpers import GpuPlan, batched_decode, compare_to_oracle, cur_stream
 from oracle import mp_oracle as orc
 from paper_0809_1833_gb300 import workloads as W
 
@@ -142,12 +142,12 @@ def test_batched_decode_switching_tile_rows_equals_128_row_tiles():
             s, res, X, atoms, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
             assert s == 0
             out[tm] = (res, X, atoms)
+            Rb = run_batched.R
             if tm == 256:
                 for b in (0, 350, 699):
                     r = res[b]
                     assert r.status == 0 and r.stop_reason == B().MP_STOP_CONVERGED
-                    plain = pl.decode(prob.y[b], prob.eps, prob.T)
-                    o = dict(result=r, x=X[b], atoms=atoms[b, :r.iters], r=plain["r"])
+                    o = dict(result=r, x=X[b], atoms=atoms[b, :r.iters], r=Rb[b])
                     compare_to_oracle(prob.psi, prob.y[b], prob.eps, prob.T, o, check_follow=False)
     (r2, X2, a2), (r1, X1, a1) = out[256], out[128]
     assert [r.iters for r in r2] == [r.iters for r in r1]
@@ -155,19 +155,10 @@ def test_batched_decode_switching_tile_rows_equals_128_row_tiles():
 
 
 def run_batched(pl, prec, Y, stops, cap=4096):
-    T = torch()
-    Bn, N = Y.shape
-    Yd = T.from_numpy(np.ascontiguousarray(Y, dtype=np.float32)).cuda()
-    X = T.full((Bn, pl.M), float("nan"), dtype=T.float32, device="cuda")
-    atoms = T.full((Bn, cap), -1, dtype=T.int32, device="cuda")
-    coefs = T.zeros((Bn, cap), dtype=T.float32, device="cuda")
-    en = T.zeros((Bn, cap), dtype=T.float64, device="cuda")
-    tr = B().make_trace(atoms.data_ptr(), coefs.data_ptr(), en.data_ptr(), cap)
-    s, res = B().mp_recover_batched(pl.plan, prec, Yd.data_ptr(), X.data_ptr(), Bn, stops, tr, cur_stream(),
-                                    raise_on_error=False)
-    T.cuda.synchronize()
-    run_batched.energies = en.cpu().numpy()
-    return s, res, X.cpu().numpy(), atoms.cpu().numpy(), coefs.cpu().numpy()
+    out = batched_decode(pl, prec, Y, stops, cap)
+    run_batched.energies = out["energies"]
+    run_batched.R = out["R"]          # each signal's final residual from the batched path
+    return out["status"], out["results"], out["X"], out["atoms"], out["coefs"]
 
 
 @pytest.mark.parametrize("tile", [128, 256], ids=lambda t: f"TM{t}")
@@ -187,9 +178,10 @@ def test_batched_matches_plain_and_oracle(prec, tile):
             if (r.iters == plain["result"].iters and np.array_equal(atoms[b, :r.iters], plain["atoms"])):
                 # same atoms: the same FP32 update and the same FP64 energy order
                 assert np.array_equal(X[b], plain["x"]), b
+                assert np.array_equal(run_batched.R[b], plain["r"]), b
                 assert np.array_equal(run_batched.energies[b, :r.iters], plain["energies"]), b
                 n_same += 1
-            out = dict(result=r, x=X[b], atoms=atoms[b, :r.iters], r=plain["r"])
+            out = dict(result=r, x=X[b], atoms=atoms[b, :r.iters], r=run_batched.R[b])
             if b % 10 == 0:   # full oracle rule on a sample of the signals
                 ora = orc.mp(prob.psi, prob.y[b], prob.eps, prob.T)
                 compare_to_oracle(prob.psi, prob.y[b], prob.eps, prob.T, out, ora=ora, check_follow=False)

@@ -1,21 +1,21 @@
 """The batched and served workloads at their full sizes, in the launch
-configuration the benchmark times (autotuned GEMM shape), checked on sampled
-signals against the FP64 oracle and, where the oracle cannot finish in
-seconds, on properties that hold at any size.
+configuration the benchmark times (autotuned GEMM shape), checked against
+the full FP64 oracle on sampled signals, each compared with the batched
+path's own final residual (its drift) and atom sequence.
 
 * BF16, N=2048, M=8192, 1024 signals: every signal converges and recovers
-  its support; 6 sampled signals meet the oracle comparison rule.
+  its support; 16 sampled signals meet the oracle rule (the literal atom
+  sequence up to the first oracle gap <= 1e-5, x~ within 1e-4 relative).
 * FP8, N=8192, M=32768, 256 signals: every signal converges and recovers its
-  support; for 2 sampled signals the oracle replays the first 24 selected
-  atoms (each must be an MP choice within the FP32 bound), and x~ equals the
-  plain FP32 kernel's whenever the atom sequences agree.
+  support; 4 sampled signals meet the same rule against full FP64 oracle
+  decodes (each about half a minute on the host cores).
 * The served workload's four dictionaries: a request per dictionary through
   the server equals the same signal decoded by mp_recover_batched alone.
 """
 import numpy as np
 import pytest
 
-from gpu_helpers import GpuPlan, compare_to_oracle, cur_stream, summation_depth, U32
+from gpu_helpers import GpuPlan, batched_decode, batched_signal, compare_to_oracle
 from oracle import mp_oracle as orc
 from paper_0809_1833_gb300 import workloads as W
 
@@ -28,54 +28,35 @@ def B():
 
 
 def batched(pl, prec, prob, cap):
-    import torch
-    b = B()
-    Y = torch.from_numpy(prob.y).cuda()
-    X = torch.full((prob.B, prob.M), float("nan"), dtype=torch.float32, device="cuda")
-    atoms = torch.full((prob.B, cap), -1, dtype=torch.int32, device="cuda")
-    tr = b.make_trace(atoms.data_ptr(), 0, 0, cap)
-    s, res = b.mp_recover_batched(pl.plan, prec, Y.data_ptr(), X.data_ptr(), prob.B, (prob.eps, prob.T), tr,
-                                  cur_stream())
-    torch.cuda.synchronize()
-    return s, res, X.cpu().numpy(), atoms.cpu().numpy()
+    out = batched_decode(pl, prec, prob.y, (prob.eps, prob.T), cap)
+    return out["status"], out["results"], out["X"], out["atoms"]
+
+
+def _full_workload(name, prec, cap, sample):
+    prob = W.make_workload(name, seed=0)
+    with GpuPlan(prob.psi, prec_mask=1 << prec) as pl:
+        out = batched_decode(pl, prec, prob.y, (prob.eps, prob.T), cap)
+    assert out["status"] == 0
+    res, X = out["results"], out["X"]
+    assert all(r.status == 0 and r.stop_reason == B().MP_STOP_CONVERGED for r in res)
+    assert min(orc.support_score(X[b], prob.supports[b]) for b in range(prob.B)) == 1.0
+    diag = []
+    for b in sample:
+        ora = orc.mp(prob.psi, prob.y[b], prob.eps, prob.T)
+        d = compare_to_oracle(prob.psi, prob.y[b], prob.eps, prob.T, batched_signal(out, b), ora=ora,
+                              check_follow=False, label=f"{name}[{b}]")
+        assert d["x_rel_err"] <= 1e-4
+        diag.append(d)
+    return diag
 
 
 def test_batched_bf16_full_workload():
-    prob = W.make_workload("batched_bf16_N2048_M8192_B1024", seed=0)
-    p = B().MP_PREC_BF16
-    with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
-        s, res, X, atoms = batched(pl, p, prob, 4096)
-        assert s == 0
-        assert all(r.status == 0 and r.stop_reason == B().MP_STOP_CONVERGED for r in res)
-        assert min(orc.support_score(X[b], prob.supports[b]) for b in range(prob.B)) == 1.0
-        for b in (0, 170, 341, 512, 683, 1023):
-            plain = pl.decode(prob.y[b], prob.eps, prob.T)
-            r = res[b]
-            same = r.iters == plain["result"].iters and np.array_equal(atoms[b, :r.iters], plain["atoms"])
-            if same:
-                assert np.array_equal(X[b], plain["x"]), b
-            out = dict(result=r, x=X[b], atoms=atoms[b, :r.iters], r=plain["r"])
-            compare_to_oracle(prob.psi, prob.y[b], prob.eps, prob.T, out, check_follow=not same)
+    sample = [int(b) for b in np.linspace(0, 1023, 16)]
+    _full_workload("batched_bf16_N2048_M8192_B1024", B().MP_PREC_BF16, 4096, sample)
 
 
 def test_batched_fp8_full_workload():
-    prob = W.make_workload("batched_fp8_N8192_M32768_B256", seed=0)
-    p = B().MP_PREC_FP8E4M3
-    with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
-        s, res, X, atoms = batched(pl, p, prob, 10000)
-        assert s == 0
-        assert all(r.status == 0 and r.stop_reason == B().MP_STOP_CONVERGED for r in res)
-        assert min(orc.support_score(X[b], prob.supports[b]) for b in range(prob.B)) == 1.0
-        for b in (0, 255):
-            plain = pl.decode(prob.y[b], prob.eps, prob.T)
-            r = res[b]
-            if r.iters == plain["result"].iters and np.array_equal(atoms[b, :r.iters], plain["atoms"]):
-                assert np.array_equal(X[b], plain["x"]), b
-            # the first 24 selections are MP choices of the FP64 oracle, within
-            # the FP32 rounding bound of one correlation (no drift yet)
-            f = orc.follow(prob.psi, prob.y[b], atoms[b, :24])
-            tol = np.maximum(1e-5, 2 * summation_depth(prob.N) * U32 * f["rnorm"] / f["cmax"])
-            assert np.all(f["ratio"] >= 1 - tol), f["ratio"].min()
+    _full_workload("batched_fp8_N8192_M32768_B256", B().MP_PREC_FP8E4M3, 10000, [0, 85, 170, 255])
 
 
 def test_served_full_dictionaries_equal_lone_batched_decodes():

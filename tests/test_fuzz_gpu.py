@@ -6,7 +6,7 @@ tests."""
 import numpy as np
 import pytest
 
-from gpu_helpers import GpuPlan, compare_to_oracle, cur_stream
+from gpu_helpers import GpuPlan, batched_decode, batched_signal, compare_to_oracle
 from oracle import mp_oracle as orc
 from paper_0809_1833_gb300 import workloads as W
 
@@ -52,30 +52,21 @@ def test_plain_random_shapes_all_launch_shapes(shape):
 @pytest.mark.parametrize("case", [(150, 2100, 77), (700, 1300, 300), (33, 4100, 5)],
                          ids=lambda c: f"N{c[0]}_M{c[1]}_B{c[2]}")
 def test_batched_random_shapes(case, prec):
-    import torch
     N, M, Bn = case
     prob = W.make_batched(N, M, Bn, 1, max(2, N // 16), seed=N + M, eps=1e-5, T=3000)
     p = B().MP_PREC_BF16 if prec == "bf16" else B().MP_PREC_FP8E4M3
     with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
-        Y = torch.from_numpy(prob.y).cuda()
-        X = torch.full((Bn, M), float("nan"), dtype=torch.float32, device="cuda")
-        cap = 3000
-        atoms = torch.full((Bn, cap), -1, dtype=torch.int32, device="cuda")
-        tr = B().make_trace(atoms.data_ptr(), 0, 0, cap)
-        s, res = B().mp_recover_batched(pl.plan, p, Y.data_ptr(), X.data_ptr(), Bn, (prob.eps, prob.T), tr,
-                                        cur_stream())
-        torch.cuda.synchronize()
-        X = X.cpu().numpy()
-        atoms = atoms.cpu().numpy()
-        assert s == 0
+        out = batched_decode(pl, p, prob.y, (prob.eps, prob.T), 3000)
+        X, atoms, res = out["X"], out["atoms"], out["results"]
+        assert out["status"] == 0
         for b in sorted({0, Bn // 2, Bn - 1}):
             plain = pl.decode(prob.y[b], prob.eps, prob.T)
             r = res[b]
             same = r.iters == plain["result"].iters and np.array_equal(atoms[b, :r.iters], plain["atoms"])
             if same:
                 assert np.array_equal(X[b], plain["x"]), b
-            out = dict(result=r, x=X[b], atoms=atoms[b, :r.iters], r=plain["r"])
-            compare_to_oracle(prob.psi, prob.y[b], prob.eps, prob.T, out, check_follow=not same)
+                assert np.array_equal(out["R"][b], plain["r"]), b
+            compare_to_oracle(prob.psi, prob.y[b], prob.eps, prob.T, batched_signal(out, b), check_follow=not same)
 
 
 @pytest.mark.parametrize("shape", _shapes(8, 77), ids=lambda s: f"N{s[0]}_M{s[1]}_K{s[2]}")
