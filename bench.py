@@ -383,7 +383,7 @@ def run_ours(args):
             g["peak_tflops"] = pk
             g["frac"] = g["tflops"] / pk if pk else None
     if rank == 0 and args.served_duration > 0:
-        line["served"] = served_measure(args.served_rate, args.served_duration)
+        line["served"] = served_measure(args.served_rate, args.served_duration, gram=args.served_gram)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -659,7 +659,8 @@ def gemm_sweep(prec_name, shape, rows=(64, 128, 256, 384, 512, 768, 1024)):
     return {"gemm_sweep": BATCHED[prec_name], "gemm_shape": [tm, tn], "us_by_active_rows": us}
 
 
-def served_measure(rate=2000.0, duration=60.0, pool_s=5.0, seed=0, max_slots=256, drain_s=120.0, n_oracle=2):
+def served_measure(rate=2000.0, duration=60.0, pool_s=5.0, seed=0, max_slots=256, drain_s=120.0, n_oracle=2,
+                   gram=0):
     """Poisson arrivals over the four resident dictionaries of the served
     workload; every request is submitted at its arrival time through the
     server's C ABI and polled until done.  Reports offered / completed rates,
@@ -670,7 +671,9 @@ def served_measure(rate=2000.0, duration=60.0, pool_s=5.0, seed=0, max_slots=256
 
     Signals: per dictionary a pool of distinct seeded signals as large as
     ``pool_s`` seconds of that dictionary's arrivals (K ~ U{4..N/16}); a
-    request takes the next signal of its dictionary's pool."""
+    request takes the next signal of its dictionary's pool.  ``gram`` > 0
+    serves every dictionary in the Gram mode with that period
+    (MP_OPT_BATCH_GRAM)."""
     import torch
     from oracle import mp_oracle as orc
     from paper_0809_1833_gb300 import binding as B
@@ -687,6 +690,8 @@ def served_measure(rate=2000.0, duration=60.0, pool_s=5.0, seed=0, max_slots=256
         psis.append(psi)
         d = torch.from_numpy(psi).cuda()
         plans.append(B.mp_plan_create(N, M, d.data_ptr(), prec_mask=1 << prec, stream=s))
+        if gram:
+            B.mp_plan_set_option(plans[-1], B.MP_OPT_BATCH_GRAM, gram)
         del d
         g = np.random.default_rng([seed, 50 + di])
         ys, sups = [], []
@@ -759,6 +764,8 @@ def served_measure(rate=2000.0, duration=60.0, pool_s=5.0, seed=0, max_slots=256
     lat = np.array(lat)
     scores = np.array(scores) if scores else np.zeros(0)
     return {"workload": "served_4dict_poisson2000", "dictionaries": [list(d) for d in dicts], "precision": "bf16",
+            "correlations": f"Gram-updated, direct BF16 GEMM every {gram} steps" if gram else
+                            "direct BF16 GEMM every step",
             "slots_per_dictionary": slots, "offered_rps": rate, "duration_s": duration, "requests": int(n),
             "submitted_rps": float(n_sub + rejected) / max(min(wall, duration), 1e-9),
             "unfinished_at_stop": len(pending),
@@ -777,14 +784,16 @@ def served_measure(rate=2000.0, duration=60.0, pool_s=5.0, seed=0, max_slots=256
             "signal_generation_s": t_gen}
 
 
-def step_breakdown(rows=(1, 2, 4, 8, 16), dict_index=3, reps=3):
+def step_breakdown(rows=(1, 2, 4, 8, 16), dict_index=3, reps=3, gram=0):
     """Per-step device time of the batched BF16 decode on one served
     dictionary at a few active-row counts: the whole step (mp_recover_batched
     on that many signals, divided by the steps the longest one needed), the
     correlation GEMM alone (mp_debug_time_gemm at the same rows, synthetic
     residuals) and their difference (select / rescore / update and the
     graph's step hand-off), next to the floor of reading the BF16 dictionary
-    once from HBM.  One JSON line per row count."""
+    once from HBM.  One JSON line per row count.  ``gram`` > 0: the Gram
+    mode with that period (the GEMM column is then the direct step's GEMM,
+    which runs every ``gram``-th step)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -796,6 +805,8 @@ def step_breakdown(rows=(1, 2, 4, 8, 16), dict_index=3, reps=3):
     psi = W.gaussian_dictionary(N, M, 10 + dict_index)
     d = torch.from_numpy(psi).cuda()
     plan = B.mp_plan_create(N, M, d.data_ptr(), prec_mask=1 << prec)
+    if gram:
+        B.mp_plan_set_option(plan, B.MP_OPT_BATCH_GRAM, gram)
     del d
     hbm, _ = measured_peaks()
     g = np.random.default_rng([0, 77])
@@ -820,7 +831,7 @@ def step_breakdown(rows=(1, 2, 4, 8, 16), dict_index=3, reps=3):
         step_us = statistics.median(times) / steps
         gemm_us = B.mp_debug_time_gemm(plan, prec, nrow, reps=50)
         print(json.dumps({"step_breakdown": {
-            "dictionary": [N, M], "active_rows": nrow, "steps": steps, "us_per_step": step_us,
+            "dictionary": [N, M], "active_rows": nrow, "steps": steps, "us_per_step": step_us, "gram_period": gram,
             "gemm_us": gemm_us, "rest_us": step_us - gemm_us,
             "gemm_shape": [B.mp_plan_query(plan, B.MP_Q_BATCH_TILE_M), B.mp_plan_query(plan, B.MP_Q_BATCH_TILE_N)],
             "hbm_floor_us": 2.0 * N * M / (hbm * 1e3)}}), flush=True)
@@ -1091,6 +1102,8 @@ def main():
     ap.add_argument("--step-breakdown", action="store_true",
                     help="run only the per-step time breakdown of the batched BF16 decode on the largest served "
                          "dictionary at 1-16 active rows")
+    ap.add_argument("--served-gram", type=int, default=0,
+                    help="serve in the Gram mode with this period (2, 4, 8 or 16; 0 = direct steps)")
     ap.add_argument("--cpu-worker", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-worker-iters", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -1098,7 +1111,7 @@ def main():
         cpu_worker(args.cpu_worker, args.cpu_worker_iters)
         return
     if args.step_breakdown:
-        step_breakdown()
+        step_breakdown(gram=args.served_gram)
         return
     if args.phase_diagram:
         phase_diagram(args.trials, args.phase_diagram)
@@ -1115,7 +1128,7 @@ def main():
     if args.served_only:
         import __graft_entry__
         __graft_entry__.build()
-        print(json.dumps(served_measure(args.served_rate, args.served_duration)))
+        print(json.dumps(served_measure(args.served_rate, args.served_duration, gram=args.served_gram)))
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -172,10 +172,23 @@ typedef enum {
                                /* first atoms of every CTA's slice) loaded with an   */
                                /* evict-last L2 hint so they stay in L2 from one     */
                                /* iteration to the next; the rest streams evict-first */
-    MP_OPT_BATCH_TILE_M = 13   /* batched GEMM: signals per tile, 128 or 256 (two    */
+    MP_OPT_BATCH_TILE_M = 13,  /* batched GEMM: signals per tile, 128 or 256 (two    */
                                /* 128-row MMAs sharing each staged atom slice;       */
                                /* taken while the batch has more 128-row tiles than  */
                                /* the GPU has SMs, 128 after); 0 = auto              */
+    MP_OPT_BATCH_GRAM = 14     /* batched and served BF16 decodes with Gram-updated  */
+                               /* correlations, period R in {2, 4, 8, 16} (0 = off,  */
+                               /* the default).  Not in the paper: every R-th step   */
+                               /* is the direct step (BF16 GEMM + FP32 rescore),     */
+                               /* which also keeps each signal's correlation row;    */
+                               /* the steps between take the row's 8 largest |c|,    */
+                               /* rescore them in FP32 like the direct step, and     */
+                               /* update the row by c_j -= c G[m][j] (G = Psi^T Psi, */
+                               /* FP32, M x M, built on first use).  A step then     */
+                               /* reads one row of G per signal instead of the       */
+                               /* dictionary.  Whenever the FP32 argmax is among     */
+                               /* the 8 candidates the result equals the plain FP32  */
+                               /* decode's, as in the direct batched decode.         */
 } mp_option;
 
 /* Read-only plan properties for mp_plan_query. */
@@ -198,9 +211,10 @@ typedef enum {
     MP_Q_PLAN_N = 15,          /* N of the plan                                      */
     MP_Q_PLAN_M = 16,          /* M of the plan                                      */
     MP_Q_BATCH_TILE_M = 17,    /* signals per GEMM tile of the current batch state   */
-    MP_Q_PLAIN64_PIECES = 18   /* FP64 streaming with the 4 warps sharing every      */
+    MP_Q_PLAIN64_PIECES = 18,  /* FP64 streaming with the 4 warps sharing every      */
                                /* stage: ring stages per atom (an atom streams as    */
                                /* that many pieces); 0 when warps own whole atoms    */
+    MP_Q_BATCH_GRAM = 19       /* Gram period of the current batch state (0: off)    */
 } mp_query;
 
 /* ------------------------------------------------------------------ */

@@ -12,7 +12,7 @@ namespace mpgb {
 
 constexpr int kBM = 128;            // signals per row block = TMEM lanes = UMMA M
 constexpr int kRowBytes = 128;      // bytes of K per operand row per stage (one swizzle row)
-constexpr int kMaxStages = 8;       // GEMM shared-memory pipeline depth, upper bound
+constexpr int kMaxStages = 16;      // GEMM shared-memory pipeline depth, upper bound
 constexpr int kSmemOptin = 232448;  // shared memory a CTA may opt into on sm_103a
 
 constexpr int kTop = 8;             // low-precision candidates kept per signal and list
@@ -49,6 +49,9 @@ struct CorrArgs {
     int* zero_next;         // step: the other half's survivor count, set to 0 here (or NULL)
     int half_ok;            // tmBh holds TN/2-row boxes: a launch may take tiles of TN/2 atoms
     int* n_at_out;          // atom tiles (candidate lists per row) this launch used, or NULL
+    float* cg;              // Gram mode (BF16): row r's correlations go to cg + act_rows[r] * ldC, or NULL
+    const int* act_rows;    //   slot id of each row of this step's operand half
+    int ldC;
 };
 
 int corr_smem_bytes(int TM, int TN);
@@ -124,8 +127,17 @@ struct BatchEngine {
     int* h_err = nullptr;
     CUtensorMap tmA, tmA1, tmB, tmBh;   // operand half 0, half 1, atoms (TN-row and TN/2-row boxes)
     CUtensorMap tmA16, tmA1_16;         // operand halves with 16-row boxes
+    // Gram mode (gram_R > 0): every gram_R-th step recomputes the correlations
+    // with the GEMM and keeps them per slot (Cg, FP32, M of ldC floats); the
+    // steps between update them from one row of G = Psi^T Psi and carry each
+    // slot's 8 largest |c| (gtop, keys as in the candidate lists)
+    int gram_R = 0;
+    float* Cg = nullptr;
+    int ldC = 0;
+    unsigned long long* gtop = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
+    int graph_kernels = 0;          // kernels one replay of the graph launches
     bool graph_retire = false;
     cudaStream_t cap_stream = nullptr;
     cudaEvent_t cnt_ready[2] = {nullptr, nullptr};   // active-count reads of alternate replays
@@ -134,8 +146,10 @@ struct BatchEngine {
 
 // Bytes of device memory one slot costs (residual, operand row, candidates,
 // state, an output row of M floats when the engine owns X).
-size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x);
-mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int cap, const GemmShape& shape);
+size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x, int gram_R = 0);
+// gram_R: 0, or the Gram mode's refresh period (2, 4, 8 or 16; BF16 only;
+// the plan's Gram matrix must exist)
+mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int cap, const GemmShape& shape, int gram_R = 0);
 void engine_free(BatchEngine* e);
 // Admit n signals: rows Y (device, n x N), into slots `slots_dev` (device,
 // NULL = 0..n-1), with per-signal eps^2 and T already in e->eps2 / e->T.

@@ -37,11 +37,13 @@
 namespace mpgb {
 
 constexpr int kSelThreads = 256;
-// select/update: 8 warps per signal, one rescored candidate each.  The FP64
+// select/update: one CTA per signal (8 warps, or 4 in engines of 512 slots
+// and more; see launch_step).  The FP64
 // energy always runs in the persistent kernel's order (128 chains over
 // float4s, then warp sums in warp order), so energies and stop decisions
 // equal the plain decode's bit for bit whenever the selected atoms do.
 constexpr int kSumChains = 128;
+constexpr int kWideSelectCap = 512;   // engines with fewer slots run the 8-warp select
 constexpr int kFixThreads = 1024;
 constexpr int kStepsPerGraph = 16;   // even: every graph starts and ends on operand half 0
 
@@ -218,6 +220,12 @@ struct SelArgs {
     int ldq, fp8;
     int* fin_count;         // optional: slots that stopped this step are appended here
     int* fin_list;
+    // Gram mode
+    float* Cg;              // per-slot correlations, ldC floats apart
+    int ldC;
+    const float* G;         // Psi^T Psi, ldG floats per row
+    int ldG;
+    unsigned long long* gtop;   // per-slot 8 largest |c| of Cg (keys as cand_key), sorted
 };
 
 // Asynchronous 16-byte global -> shared copies (completed by cp_async_wait_all
@@ -307,8 +315,26 @@ MP_DEV float dot1_deep(const float* __restrict__ p, const float* __restrict__ r,
     return warp_sum_f32((ax + ay) + (az + aw));
 }
 
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a) {
+// Insert key k into the sorted (descending) top 8 t.
+MP_DEV void top8_insert(unsigned long long (&t)[kTop], unsigned long long k) {
+    if (k <= t[kTop - 1]) return;
+    t[kTop - 1] = k;
+#pragma unroll
+    for (int i = kTop - 1; i > 0; --i) {
+        const unsigned long long hi = umax64(t[i - 1], t[i]);
+        t[i] = t[i - 1] ^ t[i] ^ hi;
+        t[i - 1] = hi;
+    }
+}
+
+// Candidate sources of the select kernel: GM_LISTS, the step's GEMM lists
+// (the direct step); GM_REFRESH, the same and then the Gram update of the
+// slot's correlation row (the first step of a Gram period); GM_GRAM, the
+// slot's carried top 8 and then the Gram update (the other steps).
+constexpr int GM_LISTS = 0, GM_REFRESH = 1, GM_GRAM = 2;
+
+template <int THREADS, int GM>
+__global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : 2) select_update_kernel(const SelArgs a) {
     extern __shared__ float4 r_sh4[];
     float* r = reinterpret_cast<float*>(r_sh4);
     __shared__ double redd[THREADS / 32];
@@ -326,6 +352,14 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
     // r streams into shared memory while the candidate lists are merged
     for (int k = threadIdx.x; k < n4; k += blockDim.x) cp_async16(rs4 + k, rg4 + k);
     cp_async_commit();
+    if constexpr (GM != GM_LISTS) {
+        // the slot's correlation row heads for L2 while the step rescores
+        // (16 KiB pieces, one per thread)
+        const char* crow = reinterpret_cast<const char*>(a.Cg + static_cast<size_t>(slot) * a.ldC);
+        const uint32_t bytes = static_cast<uint32_t>(a.ldC) * 4u;
+        const uint32_t off = static_cast<uint32_t>(threadIdx.x) * 16384u;
+        if (off < bytes) prefetch_l2(crow + off, min(16384u, bytes - off));
+    }
 
     // merge the sorted per-tile lists: keys (score bits, ~atom) order by
     // score, then by the smaller atom.  Thread t folds lists t, t + THREADS,
@@ -333,7 +367,13 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
     // butterfly of the same merge gives lane 0 of every warp the warp's best
     // 8, and warp 0 merges those.  Candidate sets are disjoint at every merge,
     // so the result is the set of the 8 largest keys, whatever the split.
-    {
+    if constexpr (GM == GM_GRAM) {
+        // the 8 largest |c| of the slot's Gram-updated correlations
+        if (threadIdx.x < kTop) {
+            const unsigned long long k = a.gtop[static_cast<size_t>(slot) * kTop + threadIdx.x];
+            top[threadIdx.x] = k ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(k)) : -1;
+        }
+    } else {
         __shared__ unsigned long long wtop[THREADS / 32][kTop];
         unsigned long long lk[kTop];
 #pragma unroll
@@ -418,6 +458,13 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
     }
     const int m = key_index(kbest);
     const float c = key_coef(kbest);
+    if constexpr (GM != GM_LISTS) {
+        // and the selected atom's row of G while r and the energy are updated
+        const char* grow = reinterpret_cast<const char*>(a.G + static_cast<size_t>(m) * a.ldG);
+        const uint32_t bytes = static_cast<uint32_t>(a.ldG) * 4u;
+        const uint32_t off = static_cast<uint32_t>(threadIdx.x) * 16384u;
+        if (off < bytes) prefetch_l2(grow + off, min(16384u, bytes - off));
+    }
     // thread 0 updates x~[m] at the end: fetch the old value now
     BatchIO io;
     float xm = 0.f;
@@ -487,6 +534,72 @@ __global__ void __launch_bounds__(THREADS) select_update_kernel(const SelArgs a)
             __nv_bfloat162* q2 = reinterpret_cast<__nv_bfloat162*>(qrow) + 2 * k;
             q2[0] = __floats2bfloat162_rn(v.x, v.y);
             q2[1] = __floats2bfloat162_rn(v.z, v.w);
+        }
+    }
+    if constexpr (GM != GM_LISTS) {
+        // Gram update of the slot's correlations: after r <- r - c psi_m,
+        // <r, psi_j> moves by -c <psi_m, psi_j> = -c G[m][j] (Eqs. 9, 11), one
+        // FP32 FMA per entry with the committed c; and the 8 largest |c| of
+        // the result for the next step (keys as cand_key; ties to the
+        // smaller atom)
+        __shared__ unsigned long long gtw[THREADS / 32][kTop];
+        float4* cr4 = reinterpret_cast<float4*>(a.Cg + static_cast<size_t>(slot) * a.ldC);
+        const float4* gr4 = reinterpret_cast<const float4*>(a.G + static_cast<size_t>(m) * a.ldG);
+        unsigned long long lk[kTop];
+#pragma unroll
+        for (int k = 0; k < kTop; ++k) lk[k] = 0ull;
+        const int nq = a.ldC / 4;
+        constexpr int U = THREADS == kSumChains ? 4 : 8;   // float4s of G and of the row in flight per thread
+        for (int q0 = threadIdx.x; q0 < nq; q0 += U * THREADS) {
+            float4 g[U], v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + u * THREADS;
+                if (q < nq) {
+                    g[u] = __ldg(gr4 + q);
+                    v[u] = cr4[q];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + u * THREADS;
+                if (q >= nq) break;
+                v[u].x = fmaf(-c, g[u].x, v[u].x);
+                v[u].y = fmaf(-c, g[u].y, v[u].y);
+                v[u].z = fmaf(-c, g[u].z, v[u].z);
+                v[u].w = fmaf(-c, g[u].w, v[u].w);
+                cr4[q] = v[u];
+                const int j0 = 4 * q;
+                if (j0 + 0 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v[u].x)), j0 + 0, a.M));
+                if (j0 + 1 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v[u].y)), j0 + 1, a.M));
+                if (j0 + 2 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v[u].z)), j0 + 2, a.M));
+                if (j0 + 3 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v[u].w)), j0 + 3, a.M));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long other[kTop];
+#pragma unroll
+            for (int k = 0; k < kTop; ++k) other[k] = __shfl_xor_sync(0xffffffffu, lk[k], o);
+            merge_top8_u64(lk, other);
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < kTop; ++k) gtw[warp][k] = lk[k];
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int k = 0; k < kTop; ++k) lk[k] = lane < THREADS / 32 ? gtw[lane][k] : 0ull;
+#pragma unroll
+            for (int o = 1; o < THREADS / 32; o <<= 1) {
+                unsigned long long other[kTop];
+#pragma unroll
+                for (int k = 0; k < kTop; ++k) other[k] = __shfl_xor_sync(0xffffffffu, lk[k], o);
+                merge_top8_u64(lk, other);
+            }
+            if (lane == 0)
+#pragma unroll
+                for (int k = 0; k < kTop; ++k) a.gtop[static_cast<size_t>(slot) * kTop + k] = lk[k];
         }
     }
 }
@@ -660,7 +773,7 @@ void engine_free(BatchEngine* e) {
     for (cudaEvent_t ev : e->cnt_ready)
         if (ev) cudaEventDestroy(ev);
     void* dev[] = {e->R32, e->Rq, e->st, e->act, e->counters, e->done, e->holes, e->surv, e->cand,
-                   e->eps2, e->T, e->err, e->io, e->rscale, e->fin_list};
+                   e->eps2, e->T, e->err, e->io, e->rscale, e->fin_list, e->Cg, e->gtop};
     for (void* p : dev) cudaFree(p);
     void* host[] = {e->h_st, e->h_cnt, e->h_eps2, e->h_T, e->h_io, e->h_err};
     for (void* p : host) cudaFreeHost(p);
@@ -672,12 +785,14 @@ void batch_destroy(BatchEngine* b) {
     delete b;
 }
 
-size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x) {
+size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x, int gram_R) {
     const bool fp8 = prec == MP_PREC_FP8E4M3;
     const size_t TN = 128;   // the narrowest tile the shape choice may pick (most candidate lists)
     const size_t n_at = (p->M + TN - 1) / TN;
+    const size_t gram = gram_R > 0 ? sizeof(float) * ((p->M + 3) / 4 * 4) + sizeof(unsigned long long) * kTop : 0;
     return sizeof(float) * p->ldN + 2 * (fp8 ? p->ldK8 : 2 * p->ldK16) + sizeof(uint2) * n_at * kTop +
-           sizeof(SlotState) + 7 * sizeof(int) + sizeof(double) + sizeof(float) + (with_x ? sizeof(float) * p->M : 0);
+           sizeof(SlotState) + 7 * sizeof(int) + sizeof(double) + sizeof(float) + (with_x ? sizeof(float) * p->M : 0) +
+           gram;
 }
 
 mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_t st, GemmShape* out);
@@ -697,16 +812,19 @@ mp_status batch_shape(PlanImpl* p, int prec, int B, const float* R, cudaStream_t
     return MP_OK;
 }
 
-static mp_status engine_prepare(PlanImpl* p, int prec, int cap, const GemmShape& g) {
+static mp_status engine_prepare(PlanImpl* p, int prec, int cap, const GemmShape& g, int gram_R = 0) {
     BatchEngine* e = p->batch;
-    if (e && e->prec == prec && e->cap >= cap && e->TM == g.tm && e->TN == g.tn) return MP_OK;
+    if (e && e->prec == prec && e->cap >= cap && e->TM == g.tm && e->TN == g.tn && e->gram_R == gram_R) return MP_OK;
     if (!e) e = p->batch = new BatchEngine();
-    return engine_alloc(e, p, prec, std::max(cap, e->cap), g);
+    return engine_alloc(e, p, prec, std::max(cap, e->cap), g, gram_R);
 }
 
-mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const GemmShape& g) {
+mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const GemmShape& g, int gram_R) {
     engine_free(e);
+    if (gram_R > 0 && (prec != MP_PREC_BF16 || !p->gram))
+        return fail(MP_ERR_UNSUPPORTED, "batched Gram mode: BF16 only, after the plan's Gram matrix is built");
     const int TN = g.tn;
+    e->gram_R = gram_R;
     e->cap = newcap;
     e->cap_pad = (newcap + kBM - 1) / kBM * kBM;
     e->prec = prec;
@@ -742,6 +860,11 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     A(&e->io, sizeof(BatchIO));
     A(&e->rscale, sizeof(float) * C);
     A(&e->fin_list, sizeof(int) * C);
+    if (gram_R > 0) {
+        e->ldC = (p->M + 3) / 4 * 4;
+        A(&e->Cg, sizeof(float) * C * e->ldC);
+        A(&e->gtop, sizeof(unsigned long long) * C * kTop);
+    }
     if (r == cudaSuccess) r = cudaMallocHost(&e->h_st, sizeof(SlotState) * C);
     if (r == cudaSuccess) r = cudaMallocHost(&e->h_cnt, sizeof(int) * 8);
     if (r == cudaSuccess) r = cudaMallocHost(&e->h_eps2, sizeof(double) * C);
@@ -808,20 +931,39 @@ static cudaError_t launch_fixup(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
 }
 
 // One step on operand half `half`: GEMM + top-8, then select / rescore /
-// update, which moves the signals that run on into the other half.
-static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, cudaStream_t st) {
+// update, which moves the signals that run on into the other half.  In the
+// Gram mode, step `s` of the graph is such a direct step (which also writes
+// each slot's correlation row) when s is a multiple of the period, and
+// otherwise one select kernel that takes the slot's carried top 8 and
+// updates the row from G.  Returns the kernels launched through *kernels.
+static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, int s, cudaStream_t st, int* kernels) {
     int* fin_count = e->counters + 2;
     int* fin_list = e->fin_list;
     int* cnt[2] = {e->counters, e->counters + 3};
     const size_t qbytes = static_cast<size_t>(e->cap_pad) * e->ldq * (e->prec == MP_PREC_FP8E4M3 ? 1 : 2);
-    CorrArgs ca = corr_args(p, e);
-    ca.n_act = cnt[half];
-    ca.zero_next = cnt[1 - half];
-    ca.n_at_out = e->counters + 4;
-    cudaError_t r = launch_corr_top8(half ? e->tmA1 : e->tmA, half ? e->tmA1_16 : e->tmA16, e->tmB, e->tmBh, ca,
-                                     e->cap_pad, st);
+    const bool gram = e->gram_R > 0;
+    const bool direct = !gram || s % e->gram_R == 0;
+    cudaError_t r = cudaSuccess;
+    if (direct) {
+        CorrArgs ca = corr_args(p, e);
+        ca.n_act = cnt[half];
+        ca.zero_next = cnt[1 - half];
+        ca.n_at_out = e->counters + 4;
+        if (gram) {
+            ca.cg = e->Cg;
+            ca.ldC = e->ldC;
+            ca.act_rows = e->act + static_cast<size_t>(half) * e->cap;
+        }
+        r = launch_corr_top8(half ? e->tmA1 : e->tmA, half ? e->tmA1_16 : e->tmA16, e->tmB, e->tmBh, ca, e->cap_pad,
+                             st);
+        ++*kernels;
+    } else {
+        // no GEMM to clear the other half's count before the survivors append
+        r = cudaMemsetAsync(cnt[1 - half], 0, sizeof(int), st);
+    }
     if (r != cudaSuccess) return r;
     SelArgs sa;
+    std::memset(&sa, 0, sizeof(sa));
     sa.n_act = cnt[half];
     sa.act = e->act + static_cast<size_t>(half) * e->cap;
     sa.n_next = cnt[1 - half];
@@ -840,9 +982,28 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, cudaStream
     sa.fp8 = e->prec == MP_PREC_FP8E4M3 ? 1 : 0;
     sa.fin_count = fin_count;
     sa.fin_list = fin_list;
-    // 8 warps: each rescores one candidate with 16 loads per lane in flight
-    // (the rescore is a latency chain of L2 / HBM reads when few signals run)
-    select_update_kernel<2 * kSumChains><<<e->cap, 2 * kSumChains, p->ldN * sizeof(float), st>>>(sa);
+    sa.Cg = e->Cg;
+    sa.ldC = e->ldC;
+    sa.G = p->gram;
+    sa.ldG = p->ldG;
+    sa.gtop = e->gtop;
+    // small engines: 8 warps, each rescoring one candidate with 16 loads per
+    // lane in flight (with few signals the rescore is a latency chain of L2 /
+    // HBM reads); engines of 512 slots and more: 4 warps, two candidates
+    // each, so more signals' CTAs fit on an SM at a full batch
+    const size_t sm = p->ldN * sizeof(float);
+    if (e->cap < kWideSelectCap) {
+        constexpr int TH = 2 * kSumChains;
+        if (!gram) select_update_kernel<TH, GM_LISTS><<<e->cap, TH, sm, st>>>(sa);
+        else if (direct) select_update_kernel<TH, GM_REFRESH><<<e->cap, TH, sm, st>>>(sa);
+        else select_update_kernel<TH, GM_GRAM><<<e->cap, TH, sm, st>>>(sa);
+    } else {
+        constexpr int TH = kSumChains;
+        if (!gram) select_update_kernel<TH, GM_LISTS><<<e->cap, TH, sm, st>>>(sa);
+        else if (direct) select_update_kernel<TH, GM_REFRESH><<<e->cap, TH, sm, st>>>(sa);
+        else select_update_kernel<TH, GM_GRAM><<<e->cap, TH, sm, st>>>(sa);
+    }
+    ++*kernels;
     return cudaGetLastError();
 }
 
@@ -856,12 +1017,27 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
     }
     if (!e->cap_stream) MP_CUDA_TRY(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
     MP_CUDA_TRY(corr_prepare());
-    if (p->ldN * 4 > 48 * 1024)
-        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, p->ldN * 4));
+    if (p->ldN * 4 > 48 * 1024) {
+        const int b = p->ldN * 4;
+        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains, GM_LISTS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains, GM_REFRESH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains, GM_GRAM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<kSumChains, GM_LISTS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<kSumChains, GM_REFRESH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<kSumChains, GM_GRAM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    }
+    if (e->gram_R > 0 && (steps % e->gram_R || !p->gram))
+        return fail(MP_ERR_INVALID, "batched step graph: Gram period must divide the steps per graph");
     MP_CUDA_TRY(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t r = cudaSuccess;
-    for (int s = 0; s < steps && r == cudaSuccess; ++s) r = launch_step(p, e, s & 1, e->cap_stream);
+    int kernels = 0;
+    for (int s = 0; s < steps && r == cudaSuccess; ++s) r = launch_step(p, e, s & 1, s, e->cap_stream, &kernels);
     if (retire && r == cudaSuccess) {
         RetireArgs ra;
         ra.fin_count = e->counters + 2;
@@ -874,6 +1050,7 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
         ra.out_list = out_list;
         ra.out_count = out_count;
         retire_kernel<<<e->cap, kSelThreads, 0, e->cap_stream>>>(ra);
+        ++kernels;
         r = cudaGetLastError();
         if (r == cudaSuccess) r = cudaMemsetAsync(e->counters + 2, 0, sizeof(int), e->cap_stream);
     }
@@ -889,6 +1066,7 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
     if (r != cudaSuccess) return cuda_fail(r, "cudaGraphInstantiate");
     e->graph_steps = steps;
     e->graph_retire = retire;
+    e->graph_kernels = kernels;
     return MP_OK;
 }
 
@@ -932,7 +1110,13 @@ static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, lo
     GemmShape g;
     mp_status s = batch_shape(p, prec, B, Y, st, &g);
     if (s != MP_OK) return s;
-    s = engine_prepare(p, prec, B, g);
+    if (p->batch_gram > 0) {
+        if (prec != MP_PREC_BF16)
+            return fail(MP_ERR_UNSUPPORTED, "mp_recover_batched: the Gram mode runs with BF16 correlations");
+        s = gram_prepare(p, st);
+        if (s != MP_OK) return s;
+    }
+    s = engine_prepare(p, prec, B, g, p->batch_gram);
     if (s != MP_OK) return s;
     BatchEngine* e = p->batch;
     s = engine_build_graph(p, e, kStepsPerGraph, false, nullptr, nullptr, nullptr, nullptr);
@@ -972,7 +1156,7 @@ static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, lo
     const long long max_replays = (static_cast<long long>(maxT) + kStepsPerGraph - 1) / kStepsPerGraph + 1;
     for (long long k = 0; k < max_replays; ++k) {
         MP_CUDA_TRY(cudaGraphLaunch(e->graph, st));
-        p->launches += 2 * kStepsPerGraph;
+        p->launches += e->graph_kernels;
         MP_CUDA_TRY(cudaMemcpyAsync(e->h_cnt + (k & 1), e->counters, sizeof(int), cudaMemcpyDeviceToHost, st));
         MP_CUDA_TRY(cudaEventRecord(e->cnt_ready[k & 1], st));
         if (k > 0) {

@@ -310,6 +310,17 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmA16, const C
                                 a.dump[static_cast<size_t>(row) * a.M + m] = v[j] * (a.fp8 ? a.colscale[m] * rsc : 1.f);
                         }
                     }
+                    if (a.cg && row < n_act) {   // Gram mode: the slot's correlation row (BF16 products)
+                        float* cr = a.cg + static_cast<size_t>(a.act_rows[row]) * a.ldC + m0 + c * 32;
+                        if (m0 + c * 32 + 32 <= a.M) {
+#pragma unroll
+                            for (int j = 0; j < 32; j += 4)
+                                *reinterpret_cast<float4*>(cr + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                        } else {
+                            for (int j = 0; j < 32; ++j)
+                                if (m0 + c * 32 + j < a.M) cr[j] = v[j];
+                        }
+                    }
                     // branch-free: sort each group of 8 keys, then keep the best
                     // 8 of (list, group) -- every lane does the same work
 #pragma unroll
@@ -427,6 +438,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     // in flight per SM as with the largest one (up to kMaxStages stages).
     // Offsets stay 1024-byte aligned.
     x.as_stride = static_cast<uint32_t>(rm) * kBM * kRowBytes;
+    // all active rows in one partial block: its stages hold only the loaded
+    // 16-row boxes, so the ring holds more stages (more bytes of atoms in
+    // flight).  The MMA still reads 128 rows from a stage's start; the rows
+    // past the loaded ones fall on the next stages' bytes (inside the ring)
+    // and only feed accumulator lanes that are never read.
+    if (rm == 1 && x.n_blk == 1 && x.n_act < kBM)
+        x.as_stride = static_cast<uint32_t>((x.n_act + 15) / 16 * 16) * kRowBytes;
     x.b_stride = static_cast<uint32_t>(x.tn) * kRowBytes;
     x.stages = min(kMaxStages, static_cast<int>(ring_bytes / (x.as_stride + x.b_stride)));
     x.tilesA = smem;

@@ -155,6 +155,7 @@ struct PlanImpl {
     int evict_first = 1;            // plain streaming: L2 evict-first hint on the stream
     long long l2_keep_bytes = 0;    // plain streaming: dictionary bytes kept resident in L2
     int gram_period = 0;            // > 0: Gram-updated correlations, direct every R steps
+    int batch_gram = 0;             // batched / served BF16: Gram mode period (0 = off)
 
     long long launches = 0;
     BatchEngine* batch = nullptr;

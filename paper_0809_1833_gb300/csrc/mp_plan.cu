@@ -347,6 +347,11 @@ mp_status mp_plan_set_option(mp_plan_t plan, int option, long long value) {
                 return fail(MP_ERR_INVALID, "batch tile must be 0, 128 or 256");
             p->batch_tile_n = static_cast<int>(value);
             return MP_OK;
+        case MP_OPT_BATCH_GRAM:
+            if (value != 0 && value != 2 && value != 4 && value != 8 && value != 16)
+                return fail(MP_ERR_INVALID, "batch Gram period must be 0, 2, 4, 8 or 16");
+            p->batch_gram = static_cast<int>(value);
+            return MP_OK;
         case MP_OPT_BATCH_TILE_M:
             if (value != 0 && value != 128 && value != 256)
                 return fail(MP_ERR_INVALID, "batch tile rows must be 0, 128 or 256");
@@ -374,6 +379,7 @@ mp_status mp_plan_query(mp_plan_t plan, int what, long long* value) {
         case MP_Q_KERNEL_LAUNCHES: *value = p->launches; return MP_OK;
         case MP_Q_BATCH_TILE_N: *value = p->batch ? p->batch->TN : 0; return MP_OK;
         case MP_Q_BATCH_TILE_M: *value = p->batch ? p->batch->TM : 0; return MP_OK;
+        case MP_Q_BATCH_GRAM: *value = p->batch ? p->batch->gram_R : 0; return MP_OK;
         case MP_Q_PLAN_N: *value = p->N; return MP_OK;
         case MP_Q_PLAN_M: *value = p->M; return MP_OK;
         case MP_Q_GRAM_BYTES:

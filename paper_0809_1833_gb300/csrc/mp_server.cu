@@ -216,7 +216,7 @@ static void scheduler(mp_server_s* srv) {
                     srv->fault.store(static_cast<int>(MP_ERR_CUDA));
                     continue;
                 }
-                d->p->launches += 2 * srv->steps + 1;   // the steps' kernels and the retire kernel
+                d->p->launches += d->eng.graph_kernels;   // the steps' kernels and the retire kernel
                 srv->chunks++;
                 d->inflight = true;
                 busy = true;
@@ -266,8 +266,19 @@ mp_status mp_server_add_dictionary(mp_server_t srv, mp_plan_t plan, int prec, in
         return fail(MP_ERR_INVALID, "mp_server_add_dictionary: precision must be BF16 or FP8");
     if (!(p->prec_mask & (1u << prec)))
         return fail(MP_ERR_UNSUPPORTED, "mp_server_add_dictionary: the plan holds no copy for this precision");
+    // the Gram mode keeps the plan's Gram matrix (built here, counted in the
+    // plan's bytes) and a correlation row per slot
+    const int gram_R = p->batch_gram;
+    if (gram_R > 0) {
+        if (prec != MP_PREC_BF16)
+            return fail(MP_ERR_UNSUPPORTED, "mp_server_add_dictionary: the Gram mode runs with BF16 correlations");
+        if (srv->steps % gram_R)
+            return fail(MP_ERR_INVALID, "mp_server_add_dictionary: the Gram period must divide the chunk's steps");
+        mp_status gs = gram_prepare(p, nullptr);
+        if (gs != MP_OK) return gs;
+    }
     // HBM admission: the plan, then as many slots as the budget allows
-    const size_t slot_bytes = engine_slot_bytes(p, prec, true) + sizeof(float) * p->N;
+    const size_t slot_bytes = engine_slot_bytes(p, prec, true, gram_R) + sizeof(float) * p->N;
     const size_t fixed = p->device_bytes + (1u << 20);
     if (srv->used + fixed + slot_bytes > srv->budget)
         return fail(MP_ERR_BUSY, "mp_server_add_dictionary: HBM budget exhausted (" + std::to_string(srv->used) + " of " +
@@ -282,7 +293,7 @@ mp_status mp_server_add_dictionary(mp_server_t srv, mp_plan_t plan, int prec, in
     const int N = p->N, M = p->M;
     GemmShape g;
     mp_status st = batch_shape(p, prec, cap, nullptr, nullptr, &g);
-    if (st == MP_OK) st = engine_alloc(&d->eng, p, prec, cap, g);
+    if (st == MP_OK) st = engine_alloc(&d->eng, p, prec, cap, g, gram_R);
     cudaError_t e = cudaSuccess;
     if (st == MP_OK) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking);

@@ -1,0 +1,152 @@
+"""Batched and served BF16 decodes with Gram-updated correlations
+(MP_OPT_BATCH_GRAM, period R).
+
+Not in the paper: from Eqs. 9 and 11, after r <- r - c psi_m every
+correlation moves by -c <psi_m, psi_j> = -c G[m][j].  Every R-th step is the
+direct batched step (BF16 tensor-core GEMM, FP32 rescore of the 8 best
+candidates), which also keeps each signal's correlation row; the steps in
+between take the row's 8 largest |c|, rescore them in FP32 from the FP32
+atoms exactly as the direct step does, commit, and update the row from one
+row of G.  The selection is the FP32 rescore's, so whenever the FP32 argmax
+is among the 8 candidates the decode equals the plain FP32 kernel's bit for
+bit; the tests check that, the literal oracle rule on sampled signals, the
+server's alone-equals-in-the-mix property in this mode, and the option's
+argument checks.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from gpu_helpers import GpuPlan, batched_decode, batched_signal, compare_to_oracle, cur_stream
+from oracle import mp_oracle as orc
+from paper_0809_1833_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def B():
+    from paper_0809_1833_gb300 import binding
+    return binding
+
+
+@pytest.mark.parametrize("R", [2, 4, 16])
+def test_gram_batched_matches_plain_and_oracle(R):
+    prob = W.make_batched(256, 1024, 300, 2, 16, seed=5, eps=1e-5, T=3000)
+    p = B().MP_PREC_BF16
+    with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
+        pl.set(B().MP_OPT_BATCH_GRAM, R)
+        out = batched_decode(pl, p, prob.y, (prob.eps, prob.T), 3000)
+        assert out["status"] == 0
+        assert pl.query(B().MP_Q_BATCH_GRAM) == R
+        assert pl.query(B().MP_Q_GRAM_BYTES) == 1024 * 1024 * 4
+        n_same = 0
+        for b in range(prob.B):
+            r = out["results"][b]
+            assert r.status == 0 and r.stop_reason == B().MP_STOP_CONVERGED
+            plain = pl.decode(prob.y[b], prob.eps, prob.T)
+            if r.iters == plain["result"].iters and np.array_equal(out["atoms"][b, :r.iters], plain["atoms"]):
+                # the same atoms: the same FP32 coefficients, update and energies
+                assert np.array_equal(out["X"][b], plain["x"]), b
+                assert np.array_equal(out["R"][b], plain["r"]), b
+                assert np.array_equal(out["energies"][b, :r.iters], plain["energies"]), b
+                n_same += 1
+            if b % 15 == 0:
+                compare_to_oracle(prob.psi, prob.y[b], prob.eps, prob.T, batched_signal(out, b), check_follow=False)
+                assert orc.support_score(out["X"][b], prob.supports[b]) == 1.0
+        assert n_same >= prob.B - 3, n_same
+
+
+def test_gram_batched_largest_served_dictionary():
+    """The 4096 x 16384 dictionary of the served workload (1 GiB Gram
+    matrix), 12 signals with K ~ U{4..256}, R = 16: every signal converges,
+    recovers its support, equals the plain decode bit for bit when the atoms
+    agree, and 3 of them meet the literal oracle rule."""
+    wl = W.WORKLOADS["served_4dict_poisson2000"]
+    N, M = wl["dicts"][3]
+    psi = W.gaussian_dictionary(N, M, seed=13)
+    g = np.random.default_rng([1, 2])
+    ys, sups = [], []
+    for _ in range(12):
+        K = int(g.integers(4, N // 16 + 1))
+        x, supp = W.sparse_signal(M, K, g, wl["values"])
+        ys.append(W.encode(psi, x))
+        sups.append(supp)
+    Y = np.stack(ys)
+    p = B().MP_PREC_BF16
+    with GpuPlan(psi, prec_mask=1 << p) as pl:
+        pl.set(B().MP_OPT_BATCH_GRAM, 16)
+        out = batched_decode(pl, p, Y, (wl["eps"], wl["T"]), wl["T"])
+        assert out["status"] == 0
+        n_same = 0
+        for b in range(len(ys)):
+            r = out["results"][b]
+            assert r.status == 0 and r.stop_reason == B().MP_STOP_CONVERGED, b
+            assert orc.support_score(out["X"][b], sups[b]) == 1.0, b
+            plain = pl.decode(Y[b], wl["eps"], wl["T"])
+            if r.iters == plain["result"].iters and np.array_equal(out["atoms"][b, :r.iters], plain["atoms"]):
+                assert np.array_equal(out["X"][b], plain["x"]), b
+                n_same += 1
+        assert n_same >= len(ys) - 1, n_same
+    for b in (0, 5, 11):
+        compare_to_oracle(psi, Y[b], wl["eps"], wl["T"], batched_signal(out, b), check_follow=False)
+
+
+def test_gram_server_mixed_requests_equal_lone_decodes():
+    """Requests for two Gram-mode dictionaries (R = 8) submitted while
+    others run: each result equals the same signal decoded alone by
+    mp_recover_batched in the same mode, bit for bit."""
+    from test_server_gpu import lone, wait_all
+    prec = B().MP_PREC_BF16
+    dicts = [(256, 1024), (512, 2048)]
+    psis = [W.gaussian_dictionary(N, M, seed=30 + i) for i, (N, M) in enumerate(dicts)]
+    plans = [GpuPlan(p, prec_mask=1 << prec) for p in psis]
+    for pl in plans:
+        pl.set(B().MP_OPT_BATCH_GRAM, 8)
+    srv = B().mp_server_create(4 << 30, 64, 10000)
+    try:
+        ids = [B().mp_server_add_dictionary(srv, pl.plan, prec) for pl in plans]
+        rng = np.random.default_rng(9)
+        reqs = []
+        for k in range(120):
+            d = int(rng.integers(0, 2))
+            N, M = dicts[d]
+            K = int(rng.integers(4, N // 16 + 1))
+            reqs.append((d, W.make_plain(N, M, K, seed=3000 + k, eps=1e-5, T=4000, psi=psis[d])))
+        tickets, M_of = [], {}
+        for i, (d, prob) in enumerate(reqs):
+            s, t = B().mp_server_submit(srv, ids[d], np.ascontiguousarray(prob.y[0]), prob.eps, prob.T)
+            assert s == 0
+            tickets.append(t)
+            M_of[t] = prob.M
+            if i % 20 == 19:
+                time.sleep(0.002)
+        out = wait_all(srv, tickets, M_of)
+    finally:
+        B().mp_server_destroy(srv)
+    try:
+        for t, (d, prob) in zip(tickets, reqs):
+            res, x = out[t]
+            s, r1, x1 = lone(plans[d], prec, prob.y[0], prob.eps, prob.T)
+            assert s == 0 and res.status == 0
+            assert res.iters == r1.iters and np.array_equal(x, x1), t
+            assert orc.support_score(x, prob.supports[0]) == 1.0
+    finally:
+        for pl in plans:
+            pl.close()
+
+
+def test_gram_option_checks():
+    psi = W.gaussian_dictionary(64, 300, seed=3)
+    with GpuPlan(psi, prec_mask=(1 << B().MP_PREC_BF16) | (1 << B().MP_PREC_FP8E4M3)) as pl:
+        for bad in (1, 3, 6, 32, -2):
+            with pytest.raises(B().MpError) as ei:
+                pl.set(B().MP_OPT_BATCH_GRAM, bad)
+            assert ei.value.status == B().MP_ERR_INVALID
+        pl.set(B().MP_OPT_BATCH_GRAM, 4)
+        prob = W.make_batched(64, 300, 4, 1, 3, seed=2, psi=psi, eps=1e-5, T=500)
+        out = batched_decode(pl, B().MP_PREC_FP8E4M3, prob.y, (prob.eps, prob.T), 16)
+        assert out["status"] == B().MP_ERR_UNSUPPORTED
+        pl.set(B().MP_OPT_BATCH_GRAM, 0)
+        out = batched_decode(pl, B().MP_PREC_FP8E4M3, prob.y, (prob.eps, prob.T), 500)
+        assert out["status"] == 0
