@@ -784,7 +784,7 @@ def served_measure(rate=2000.0, duration=60.0, pool_s=5.0, seed=0, max_slots=256
             "signal_generation_s": t_gen}
 
 
-def step_breakdown(rows=(1, 2, 4, 8, 16), dict_index=3, reps=3, gram=0):
+def step_breakdown(rows=(1, 2, 4, 8, 16), dict_index=3, reps=3, gram=0, T=None):
     """Per-step device time of the batched BF16 decode on one served
     dictionary at a few active-row counts: the whole step (mp_recover_batched
     on that many signals, divided by the steps the longest one needed), the
@@ -792,8 +792,9 @@ def step_breakdown(rows=(1, 2, 4, 8, 16), dict_index=3, reps=3, gram=0):
     residuals) and their difference (select / rescore / update and the
     graph's step hand-off), next to the floor of reading the BF16 dictionary
     once from HBM.  One JSON line per row count.  ``gram`` > 0: the Gram
-    mode with that period (the GEMM column is then the direct step's GEMM,
-    which runs every ``gram``-th step)."""
+    mode with that period (no GEMM runs in that mode; the GEMM column is
+    the direct step's, for comparison).  ``T`` caps the iterations (a small
+    case for a profiler)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -818,12 +819,13 @@ def step_breakdown(rows=(1, 2, 4, 8, 16), dict_index=3, reps=3, gram=0):
             ys.append(W.encode(psi, x))
         Y = torch.from_numpy(np.stack(ys)).cuda()
         X = torch.empty((nrow, M), device="cuda")
-        B.mp_recover_batched(plan, prec, Y.data_ptr(), X.data_ptr(), nrow, (wl["eps"], wl["T"]))
+        Tcap = T or wl["T"]
+        B.mp_recover_batched(plan, prec, Y.data_ptr(), X.data_ptr(), nrow, (wl["eps"], Tcap))
         times = []
         for _ in range(reps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            _, res = B.mp_recover_batched(plan, prec, Y.data_ptr(), X.data_ptr(), nrow, (wl["eps"], wl["T"]))
+            _, res = B.mp_recover_batched(plan, prec, Y.data_ptr(), X.data_ptr(), nrow, (wl["eps"], Tcap))
             b.record()
             torch.cuda.synchronize()
             times.append(a.elapsed_time(b) * 1e3)
@@ -1103,7 +1105,10 @@ def main():
                     help="run only the per-step time breakdown of the batched BF16 decode on the largest served "
                          "dictionary at 1-16 active rows")
     ap.add_argument("--served-gram", type=int, default=0,
-                    help="serve in the Gram mode with this period (2, 4, 8 or 16; 0 = direct steps)")
+                    help="serve in the Gram mode with this refresh period (a multiple of 16; 0 = direct steps)")
+    ap.add_argument("--breakdown-rows", type=int, nargs="*", default=None,
+                    help="active-row counts of --step-breakdown (default 1 2 4 8 16)")
+    ap.add_argument("--breakdown-T", type=int, default=None, help="iteration cap of --step-breakdown")
     ap.add_argument("--cpu-worker", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-worker-iters", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -1111,7 +1116,8 @@ def main():
         cpu_worker(args.cpu_worker, args.cpu_worker_iters)
         return
     if args.step_breakdown:
-        step_breakdown(gram=args.served_gram)
+        step_breakdown(rows=tuple(args.breakdown_rows or (1, 2, 4, 8, 16)), gram=args.served_gram,
+                       T=args.breakdown_T)
         return
     if args.phase_diagram:
         phase_diagram(args.trials, args.phase_diagram)

@@ -176,19 +176,20 @@ typedef enum {
                                /* 128-row MMAs sharing each staged atom slice;       */
                                /* taken while the batch has more 128-row tiles than  */
                                /* the GPU has SMs, 128 after); 0 = auto              */
-    MP_OPT_BATCH_GRAM = 14     /* batched and served BF16 decodes with Gram-updated  */
-                               /* correlations, period R in {2, 4, 8, 16} (0 = off,  */
-                               /* the default).  Not in the paper: every R-th step   */
-                               /* is the direct step (BF16 GEMM + FP32 rescore),     */
-                               /* which also keeps each signal's correlation row;    */
-                               /* the steps between take the row's 8 largest |c|,    */
-                               /* rescore them in FP32 like the direct step, and     */
-                               /* update the row by c_j -= c G[m][j] (G = Psi^T Psi, */
-                               /* FP32, M x M, built on first use).  A step then     */
-                               /* reads one row of G per signal instead of the       */
-                               /* dictionary.  Whenever the FP32 argmax is among     */
-                               /* the 8 candidates the result equals the plain FP32  */
-                               /* decode's, as in the direct batched decode.         */
+    MP_OPT_BATCH_GRAM = 14     /* batched and served decodes (BF16 plans) with       */
+                               /* Gram-updated correlations; the value is the        */
+                               /* refresh period R, a multiple of 16 (0 = off, the   */
+                               /* default).  Not in the paper: each signal keeps its */
+                               /* FP32 correlations c = Psi^T r, computed directly   */
+                               /* from the FP32 atoms when it is admitted and again  */
+                               /* every R of its own steps; a step takes the 8       */
+                               /* largest |c|, rescores them in FP32 exactly as the  */
+                               /* direct batched step does, commits the best, and    */
+                               /* updates c_j -= c G[m][j] (G = Psi^T Psi, FP32,     */
+                               /* M x M, built on first use).  A step reads one row  */
+                               /* of G per signal and no GEMM runs.  Whenever the    */
+                               /* FP32 argmax is among the 8 candidates the result   */
+                               /* equals the plain FP32 decode's bit for bit.        */
 } mp_option;
 
 /* Read-only plan properties for mp_plan_query. */

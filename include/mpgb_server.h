@@ -48,9 +48,10 @@ MPGB_API mp_status mp_server_create(mp_server_t* out, size_t hbm_budget_bytes, i
 /* Make a plan's dictionary resident for serving at `prec` (MP_PREC_BF16 or
  * MP_PREC_FP8E4M3; the plan must hold that copy).  The plan stays owned by
  * the caller and must outlive the server.  Only before the first submit.
- * With the plan's MP_OPT_BATCH_GRAM set (BF16, a period dividing the 16
- * steps of a chunk) the dictionary is served in the Gram mode: the plan's
- * Gram matrix (4 M^2 bytes) is built here and counts against the budget.
+ * With the plan's MP_OPT_BATCH_GRAM set (BF16, a period that is a multiple
+ * of the 16 steps of a chunk) the dictionary is served in the Gram mode:
+ * the plan's Gram matrix (4 M^2 bytes) is built here and counts against
+ * the budget, and each slot keeps an FP32 correlation row (4 M bytes).
  *  dict_id : receives the id to submit against.
  * Errors: MP_ERR_INVALID, MP_ERR_UNSUPPORTED, MP_ERR_BUSY (HBM budget
  * exhausted), MP_ERR_NOMEM, MP_ERR_CUDA. */

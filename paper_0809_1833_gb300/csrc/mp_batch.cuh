@@ -49,9 +49,6 @@ struct CorrArgs {
     int* zero_next;         // step: the other half's survivor count, set to 0 here (or NULL)
     int half_ok;            // tmBh holds TN/2-row boxes: a launch may take tiles of TN/2 atoms
     int* n_at_out;          // atom tiles (candidate lists per row) this launch used, or NULL
-    float* cg;              // Gram mode (BF16): row r's correlations go to cg + act_rows[r] * ldC, or NULL
-    const int* act_rows;    //   slot id of each row of this step's operand half
-    int ldC;
 };
 
 int corr_smem_bytes(int TM, int TN);
@@ -108,7 +105,7 @@ struct BatchEngine {
     SlotState* st = nullptr;
     int* act = nullptr;        // 2 x cap slot ids by row (half 0, then half 1)
     int* counters = nullptr;   // [0] rows of half 0, [1] rows just admitted, [2] finished count, [3] rows of half 1,
-                               // [4] candidate lists per row of the last GEMM
+                               // [4] candidate lists per row of the last GEMM, [5] Gram mode: select CTAs done
     int* done = nullptr;
     int* holes = nullptr;
     int* surv = nullptr;
@@ -127,10 +124,11 @@ struct BatchEngine {
     int* h_err = nullptr;
     CUtensorMap tmA, tmA1, tmB, tmBh;   // operand half 0, half 1, atoms (TN-row and TN/2-row boxes)
     CUtensorMap tmA16, tmA1_16;         // operand halves with 16-row boxes
-    // Gram mode (gram_R > 0): every gram_R-th step recomputes the correlations
-    // with the GEMM and keeps them per slot (Cg, FP32, M of ldC floats); the
-    // steps between update them from one row of G = Psi^T Psi and carry each
-    // slot's 8 largest |c| (gtop, keys as in the candidate lists)
+    // Gram mode (gram_R > 0): each slot keeps its correlations Psi^T r in
+    // FP32 (Cg, M of ldC floats), computed directly at admission and every
+    // gram_R of its own steps, and updated from one row of G = Psi^T Psi in
+    // every step; gtop carries the row's 8 largest |c| (keys as in the
+    // candidate lists).  No GEMM runs in this mode.
     int gram_R = 0;
     float* Cg = nullptr;
     int ldC = 0;
@@ -147,8 +145,8 @@ struct BatchEngine {
 // Bytes of device memory one slot costs (residual, operand row, candidates,
 // state, an output row of M floats when the engine owns X).
 size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x, int gram_R = 0);
-// gram_R: 0, or the Gram mode's refresh period (2, 4, 8 or 16; BF16 only;
-// the plan's Gram matrix must exist)
+// gram_R: 0, or the Gram mode's refresh period (a multiple of 16; BF16 or
+// FP32 plans; the plan's Gram matrix must exist)
 mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int cap, const GemmShape& shape, int gram_R = 0);
 void engine_free(BatchEngine* e);
 // Admit n signals: rows Y (device, n x N), into slots `slots_dev` (device,

@@ -226,7 +226,21 @@ struct SelArgs {
     const float* G;         // Psi^T Psi, ldG floats per row
     int ldG;
     unsigned long long* gtop;   // per-slot 8 largest |c| of Cg (keys as cand_key), sorted
+    int* n_act_w;           // Gram mode: this half's count, cleared by the step's last CTA
+    int* done_ctr;          //   CTAs of the step that finished (NULL: not cleared here)
 };
+
+// Gram mode: the step's last CTA clears the count it read, after every CTA
+// of the step has read it, so the next step's survivors (a select kernel,
+// not a GEMM that would clear it) append from 0.
+MP_DEV void step_done(const SelArgs& a) {
+    if (threadIdx.x == 0 && a.done_ctr) {
+        if (atomicAdd(a.done_ctr, 1) == static_cast<int>(gridDim.x) - 1) {
+            *a.n_act_w = 0;
+            *a.done_ctr = 0;
+        }
+    }
+}
 
 // Asynchronous 16-byte global -> shared copies (completed by cp_async_wait_all
 // in the issuing thread, made visible to the block by a barrier after it).
@@ -327,11 +341,43 @@ MP_DEV void top8_insert(unsigned long long (&t)[kTop], unsigned long long k) {
     }
 }
 
+// Block-wide best 8 of the threads' sorted lists lk (a butterfly of the
+// bitonic top-8 merge inside each warp, then warp 0 over the warps' lists,
+// through w, a THREADS / 32 x 8 shared array); thread 0 stores them to out.
+template <int THREADS>
+MP_DEV void block_top8_store(unsigned long long (&lk)[kTop], unsigned long long (*w)[kTop], unsigned long long* out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long other[kTop];
+#pragma unroll
+        for (int k = 0; k < kTop; ++k) other[k] = __shfl_xor_sync(0xffffffffu, lk[k], o);
+        merge_top8_u64(lk, other);
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < kTop; ++k) w[warp][k] = lk[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < kTop; ++k) lk[k] = lane < THREADS / 32 ? w[lane][k] : 0ull;
+#pragma unroll
+        for (int o = 1; o < THREADS / 32; o <<= 1) {
+            unsigned long long other[kTop];
+#pragma unroll
+            for (int k = 0; k < kTop; ++k) other[k] = __shfl_xor_sync(0xffffffffu, lk[k], o);
+            merge_top8_u64(lk, other);
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < kTop; ++k) out[k] = lk[k];
+    }
+}
+
 // Candidate sources of the select kernel: GM_LISTS, the step's GEMM lists
-// (the direct step); GM_REFRESH, the same and then the Gram update of the
-// slot's correlation row (the first step of a Gram period); GM_GRAM, the
-// slot's carried top 8 and then the Gram update (the other steps).
-constexpr int GM_LISTS = 0, GM_REFRESH = 1, GM_GRAM = 2;
+// (the direct step); GM_GRAM, the slot's carried 8 largest |c| of its
+// FP32 correlation row, which the kernel then updates from G (the Gram mode).
+constexpr int GM_LISTS = 0, GM_GRAM = 1;
 
 template <int THREADS, int GM>
 __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : 2) select_update_kernel(const SelArgs a) {
@@ -342,7 +388,10 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : 2) select
     __shared__ int top[kTop];
     __shared__ unsigned long long rkey[kTop];
     const int i = blockIdx.x;
-    if (i >= *a.n_act) return;
+    if (i >= *a.n_act) {
+        step_done(a);
+        return;
+    }
     const int slot = a.act[i];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* rs4 = reinterpret_cast<float4*>(r);
@@ -352,7 +401,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : 2) select
     // r streams into shared memory while the candidate lists are merged
     for (int k = threadIdx.x; k < n4; k += blockDim.x) cp_async16(rs4 + k, rg4 + k);
     cp_async_commit();
-    if constexpr (GM != GM_LISTS) {
+    if constexpr (GM == GM_GRAM) {
         // the slot's correlation row heads for L2 while the step rescores
         // (16 KiB pieces, one per thread)
         const char* crow = reinterpret_cast<const char*>(a.Cg + static_cast<size_t>(slot) * a.ldC);
@@ -454,11 +503,12 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : 2) select
             a.st[slot] = s;
             if (a.fin_list) a.fin_list[atomicAdd(a.fin_count, 1)] = slot;
         }
+        step_done(a);
         return;
     }
     const int m = key_index(kbest);
     const float c = key_coef(kbest);
-    if constexpr (GM != GM_LISTS) {
+    if constexpr (GM == GM_GRAM) {
         // and the selected atom's row of G while r and the energy are updated
         const char* grow = reinterpret_cast<const char*>(a.G + static_cast<size_t>(m) * a.ldG);
         const uint32_t bytes = static_cast<uint32_t>(a.ldG) * 4u;
@@ -521,9 +571,14 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : 2) select
     }
     __syncthreads();
     const int row = next_row;
-    if (row < 0) return;
+    if (row < 0) {
+        step_done(a);
+        return;
+    }
     char* qrow = static_cast<char*>(a.Rq_next) + static_cast<size_t>(row) * a.ldq * (a.fp8 ? 1 : 2);
-    if (a.fp8) {
+    if constexpr (GM == GM_GRAM) {
+        // no GEMM reads the quantised operand in the Gram mode
+    } else if (a.fp8) {
         block_quantize(r, a.ldN, qrow, a.ldq, 1, redf);
     } else {
         // the first ldN elements; the row's padding up to ldq holds zeros (the
@@ -536,7 +591,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : 2) select
             q2[1] = __floats2bfloat162_rn(v.z, v.w);
         }
     }
-    if constexpr (GM != GM_LISTS) {
+    if constexpr (GM == GM_GRAM) {
         // Gram update of the slot's correlations: after r <- r - c psi_m,
         // <r, psi_j> moves by -c <psi_m, psi_j> = -c G[m][j] (Eqs. 9, 11), one
         // FP32 FMA per entry with the committed c; and the 8 largest |c| of
@@ -576,32 +631,131 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : 2) select
                 if (j0 + 3 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v[u].w)), j0 + 3, a.M));
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            unsigned long long other[kTop];
-#pragma unroll
-            for (int k = 0; k < kTop; ++k) other[k] = __shfl_xor_sync(0xffffffffu, lk[k], o);
-            merge_top8_u64(lk, other);
+        block_top8_store<THREADS>(lk, gtw, a.gtop + static_cast<size_t>(slot) * kTop);
+    }
+    step_done(a);
+}
+
+// ------------------------------------------------------------------ Gram mode: direct FP32 correlations
+// c = Psi^T r (Eq. 9) in FP32 for listed slots, written to their correlation
+// rows: at admission (r = y) and, in the graph, for the active slots whose
+// own step count reached a multiple of the refresh period (bounding the
+// recurrence's drift).  A CTA stages up to kCorrRows residual rows in shared
+// memory and its warps run over a block of kCorrAtoms atoms, each atom read
+// once from HBM for all the staged rows; float4 loads, 8 in flight per lane.
+constexpr int kCorrRows = 8;
+constexpr int kCorrAtoms = 128;
+constexpr int kCorrThreads = 256;
+constexpr int kCorrSmem = 200 * 1024;   // shared memory for the staged rows, at most
+
+static int corr_rows_per_cta(const PlanImpl* p) {
+    return std::max(1, std::min(kCorrRows, kCorrSmem / (p->ldN * static_cast<int>(sizeof(float)))));
+}
+
+struct CorrRowsArgs {
+    const float* psi32;
+    int ldN, M;
+    const float* R32;       // residual rows by slot (ldN floats)
+    const int* rows;        // slot of listed row k (NULL: slot k)
+    const int* n_ptr;       // number of listed rows on the device (NULL: n)
+    int n;
+    const SlotState* st;    // R > 0: only slots with st.t a positive multiple of R
+    int R;
+    float* Cg;
+    int ldC;
+    int rpc;                // rows staged per CTA (<= kCorrRows, by the row length)
+};
+
+MP_DEV bool corr_row_wanted(const CorrRowsArgs& a, int slot) {
+    if (a.R <= 0) return true;
+    const int t = a.st[slot].t;
+    return t > 0 && t % a.R == 0;
+}
+
+__global__ void __launch_bounds__(kCorrThreads) corr_rows_kernel(const CorrRowsArgs a) {
+    extern __shared__ float4 rsh[];           // kCorrRows rows of ldN floats
+    __shared__ int slots[kCorrRows];
+    __shared__ int want[kCorrRows];
+    const int n = a.n_ptr ? *a.n_ptr : a.n;
+    const int g0 = blockIdx.y * a.rpc;
+    if (g0 >= n) return;
+    const int nr = min(a.rpc, n - g0);
+    if (threadIdx.x < kCorrRows) {
+        int sl = -1, w = 0;
+        if (static_cast<int>(threadIdx.x) < nr) {
+            sl = a.rows ? a.rows[g0 + threadIdx.x] : g0 + static_cast<int>(threadIdx.x);
+            w = corr_row_wanted(a, sl) ? 1 : 0;
         }
-        if (lane == 0)
+        slots[threadIdx.x] = sl;
+        want[threadIdx.x] = w;
+    }
+    __syncthreads();
+    int any = 0;
 #pragma unroll
-            for (int k = 0; k < kTop; ++k) gtw[warp][k] = lk[k];
-        __syncthreads();
-        if (warp == 0) {
+    for (int j = 0; j < kCorrRows; ++j) any |= want[j];
+    if (!any) return;
+    const int n4 = a.ldN / 4;
+    for (int j = 0; j < nr; ++j) {
+        const float4* src = reinterpret_cast<const float4*>(a.R32 + static_cast<size_t>(slots[j]) * a.ldN);
+        for (int k = threadIdx.x; k < n4; k += kCorrThreads) rsh[j * n4 + k] = src[k];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m_end = min(a.M, (blockIdx.x + 1) * kCorrAtoms);
+    for (int m = blockIdx.x * kCorrAtoms + warp; m < m_end; m += kCorrThreads / 32) {
+        const float4* p = reinterpret_cast<const float4*>(a.psi32 + static_cast<size_t>(m) * a.ldN);
+        float acc[kCorrRows];
 #pragma unroll
-            for (int k = 0; k < kTop; ++k) lk[k] = lane < THREADS / 32 ? gtw[lane][k] : 0ull;
+        for (int j = 0; j < kCorrRows; ++j) acc[j] = 0.f;
+        constexpr int U = 8;
+        for (int k0 = lane; k0 < n4; k0 += 32 * U) {
+            float4 v[U];
 #pragma unroll
-            for (int o = 1; o < THREADS / 32; o <<= 1) {
-                unsigned long long other[kTop];
+            for (int u = 0; u < U; ++u)
+                if (k0 + 32 * u < n4) v[u] = __ldg(p + k0 + 32 * u);
 #pragma unroll
-                for (int k = 0; k < kTop; ++k) other[k] = __shfl_xor_sync(0xffffffffu, lk[k], o);
-                merge_top8_u64(lk, other);
+            for (int u = 0; u < U; ++u) {
+                const int k = k0 + 32 * u;
+                if (k >= n4) break;
+#pragma unroll
+                for (int j = 0; j < kCorrRows; ++j) {
+                    if (j >= nr) break;
+                    const float4 q = rsh[j * n4 + k];
+                    acc[j] = fmaf(v[u].x, q.x, fmaf(v[u].y, q.y, fmaf(v[u].z, q.z, fmaf(v[u].w, q.w, acc[j]))));
+                }
             }
-            if (lane == 0)
+        }
 #pragma unroll
-                for (int k = 0; k < kTop; ++k) a.gtop[static_cast<size_t>(slot) * kTop + k] = lk[k];
+        for (int j = 0; j < kCorrRows; ++j) {
+            if (j >= nr) break;
+            const float c = warp_sum_f32(acc[j]);
+            if (lane == 0 && want[j]) a.Cg[static_cast<size_t>(slots[j]) * a.ldC + m] = c;
         }
     }
+}
+
+// The 8 largest |c| (keys as cand_key) of each listed slot's correlation
+// row, for its next step; one CTA per listed row, the same filter as above.
+__global__ void __launch_bounds__(kCorrThreads) gram_scan_kernel(const CorrRowsArgs a, unsigned long long* gtop) {
+    __shared__ unsigned long long w[kCorrThreads / 32][kTop];
+    const int n = a.n_ptr ? *a.n_ptr : a.n;
+    const int k = blockIdx.x;
+    if (k >= n) return;
+    const int slot = a.rows ? a.rows[k] : k;
+    if (!corr_row_wanted(a, slot)) return;
+    const float4* cr4 = reinterpret_cast<const float4*>(a.Cg + static_cast<size_t>(slot) * a.ldC);
+    unsigned long long lk[kTop];
+#pragma unroll
+    for (int j = 0; j < kTop; ++j) lk[j] = 0ull;
+    for (int q = threadIdx.x; q < a.ldC / 4; q += kCorrThreads) {
+        const float4 v = cr4[q];
+        const int j0 = 4 * q;
+        if (j0 + 0 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v.x)), j0 + 0, a.M));
+        if (j0 + 1 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v.y)), j0 + 1, a.M));
+        if (j0 + 2 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v.z)), j0 + 2, a.M));
+        if (j0 + 3 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v.w)), j0 + 3, a.M));
+    }
+    block_top8_store<kCorrThreads>(lk, w, gtop + static_cast<size_t>(slot) * kTop);
 }
 
 // ------------------------------------------------------------------ fixup (one CTA)
@@ -822,7 +976,7 @@ static mp_status engine_prepare(PlanImpl* p, int prec, int cap, const GemmShape&
 mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const GemmShape& g, int gram_R) {
     engine_free(e);
     if (gram_R > 0 && (prec != MP_PREC_BF16 || !p->gram))
-        return fail(MP_ERR_UNSUPPORTED, "batched Gram mode: BF16 only, after the plan's Gram matrix is built");
+        return fail(MP_ERR_UNSUPPORTED, "batched Gram mode: BF16 plans only, after the plan's Gram matrix is built");
     const int TN = g.tn;
     e->gram_R = gram_R;
     e->cap = newcap;
@@ -864,6 +1018,9 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
         e->ldC = (p->M + 3) / 4 * 4;
         A(&e->Cg, sizeof(float) * C * e->ldC);
         A(&e->gtop, sizeof(unsigned long long) * C * kTop);
+        const int sm = corr_rows_per_cta(p) * p->ldN * static_cast<int>(sizeof(float));
+        if (r == cudaSuccess && sm > 48 * 1024)
+            r = cudaFuncSetAttribute(corr_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     }
     if (r == cudaSuccess) r = cudaMallocHost(&e->h_st, sizeof(SlotState) * C);
     if (r == cudaSuccess) r = cudaMallocHost(&e->h_cnt, sizeof(int) * 8);
@@ -932,34 +1089,24 @@ static cudaError_t launch_fixup(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
 
 // One step on operand half `half`: GEMM + top-8, then select / rescore /
 // update, which moves the signals that run on into the other half.  In the
-// Gram mode, step `s` of the graph is such a direct step (which also writes
-// each slot's correlation row) when s is a multiple of the period, and
-// otherwise one select kernel that takes the slot's carried top 8 and
-// updates the row from G.  Returns the kernels launched through *kernels.
-static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, int s, cudaStream_t st, int* kernels) {
+// Gram mode a step is the select kernel alone: its candidates are each
+// slot's carried top 8, and it updates the slot's correlation row from G.
+// Adds the kernels launched to *kernels.
+static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, cudaStream_t st, int* kernels) {
     int* fin_count = e->counters + 2;
     int* fin_list = e->fin_list;
     int* cnt[2] = {e->counters, e->counters + 3};
     const size_t qbytes = static_cast<size_t>(e->cap_pad) * e->ldq * (e->prec == MP_PREC_FP8E4M3 ? 1 : 2);
     const bool gram = e->gram_R > 0;
-    const bool direct = !gram || s % e->gram_R == 0;
     cudaError_t r = cudaSuccess;
-    if (direct) {
+    if (!gram) {
         CorrArgs ca = corr_args(p, e);
         ca.n_act = cnt[half];
         ca.zero_next = cnt[1 - half];
         ca.n_at_out = e->counters + 4;
-        if (gram) {
-            ca.cg = e->Cg;
-            ca.ldC = e->ldC;
-            ca.act_rows = e->act + static_cast<size_t>(half) * e->cap;
-        }
         r = launch_corr_top8(half ? e->tmA1 : e->tmA, half ? e->tmA1_16 : e->tmA16, e->tmB, e->tmBh, ca, e->cap_pad,
                              st);
         ++*kernels;
-    } else {
-        // no GEMM to clear the other half's count before the survivors append
-        r = cudaMemsetAsync(cnt[1 - half], 0, sizeof(int), st);
     }
     if (r != cudaSuccess) return r;
     SelArgs sa;
@@ -987,6 +1134,11 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, int s, cud
     sa.G = p->gram;
     sa.ldG = p->ldG;
     sa.gtop = e->gtop;
+    // in the Gram mode a select step follows a select step with no GEMM
+    // between them to clear the count its survivors append to: each select
+    // kernel clears the count it read once all its CTAs have read it
+    sa.n_act_w = cnt[half];
+    sa.done_ctr = gram ? e->counters + 5 : nullptr;
     // small engines: 8 warps, each rescoring one candidate with 16 loads per
     // lane in flight (with few signals the rescore is a latency chain of L2 /
     // HBM reads); engines of 512 slots and more: 4 warps, two candidates
@@ -995,15 +1147,39 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, int s, cud
     if (e->cap < kWideSelectCap) {
         constexpr int TH = 2 * kSumChains;
         if (!gram) select_update_kernel<TH, GM_LISTS><<<e->cap, TH, sm, st>>>(sa);
-        else if (direct) select_update_kernel<TH, GM_REFRESH><<<e->cap, TH, sm, st>>>(sa);
         else select_update_kernel<TH, GM_GRAM><<<e->cap, TH, sm, st>>>(sa);
     } else {
         constexpr int TH = kSumChains;
         if (!gram) select_update_kernel<TH, GM_LISTS><<<e->cap, TH, sm, st>>>(sa);
-        else if (direct) select_update_kernel<TH, GM_REFRESH><<<e->cap, TH, sm, st>>>(sa);
         else select_update_kernel<TH, GM_GRAM><<<e->cap, TH, sm, st>>>(sa);
     }
     ++*kernels;
+    return cudaGetLastError();
+}
+
+// Gram mode: direct FP32 correlations and their top 8 for listed slots
+// (rows == NULL: slots 0..n_max-1; n_ptr: the device's row count; R > 0:
+// only the slots whose step count is a positive multiple of R).
+static cudaError_t launch_gram_refresh(PlanImpl* p, BatchEngine* e, const int* rows, const int* n_ptr, int n_max, int R,
+                                       cudaStream_t st, int* kernels) {
+    if (n_max <= 0) return cudaSuccess;
+    CorrRowsArgs a;
+    a.psi32 = p->psi32;
+    a.ldN = p->ldN;
+    a.M = p->M;
+    a.R32 = e->R32;
+    a.rows = rows;
+    a.n_ptr = n_ptr;
+    a.n = n_max;
+    a.st = e->st;
+    a.R = R;
+    a.Cg = e->Cg;
+    a.ldC = e->ldC;
+    a.rpc = corr_rows_per_cta(p);
+    const dim3 grid((p->M + kCorrAtoms - 1) / kCorrAtoms, (n_max + a.rpc - 1) / a.rpc);
+    corr_rows_kernel<<<grid, kCorrThreads, static_cast<size_t>(a.rpc) * p->ldN * sizeof(float), st>>>(a);
+    gram_scan_kernel<<<n_max, kCorrThreads, 0, st>>>(a, e->gtop);
+    *kernels += 2;
     return cudaGetLastError();
 }
 
@@ -1021,23 +1197,25 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
         const int b = p->ldN * 4;
         MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains, GM_LISTS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains, GM_REFRESH>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains, GM_GRAM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<kSumChains, GM_LISTS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<kSumChains, GM_REFRESH>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<kSumChains, GM_GRAM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, b));
     }
-    if (e->gram_R > 0 && (steps % e->gram_R || !p->gram))
-        return fail(MP_ERR_INVALID, "batched step graph: Gram period must divide the steps per graph");
+    if (e->gram_R > 0 && (e->gram_R % steps || !p->gram))
+        return fail(MP_ERR_INVALID, "batched step graph: the Gram period must be a multiple of the steps per graph");
     MP_CUDA_TRY(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t r = cudaSuccess;
     int kernels = 0;
-    for (int s = 0; s < steps && r == cudaSuccess; ++s) r = launch_step(p, e, s & 1, s, e->cap_stream, &kernels);
+    // Gram mode: a replay starts with every active slot's step count a
+    // multiple of `steps` (signals join between replays and each step moves
+    // every active signal by one); the slots at a multiple of the period get
+    // their correlations recomputed directly
+    if (e->gram_R > 0)
+        r = launch_gram_refresh(p, e, e->act, e->counters, e->cap, e->gram_R, e->cap_stream, &kernels);
+    for (int s = 0; s < steps && r == cudaSuccess; ++s) r = launch_step(p, e, s & 1, e->cap_stream, &kernels);
     if (retire && r == cudaSuccess) {
         RetireArgs ra;
         ra.fin_count = e->counters + 2;
@@ -1102,6 +1280,13 @@ cudaError_t engine_admit(PlanImpl* p, BatchEngine* e, const float* Y, int n, con
     cudaError_t r = cudaGetLastError();
     if (r != cudaSuccess) return r;
     p->launches++;
+    if (e->gram_R > 0) {
+        // the Gram mode starts every signal from its direct FP32 correlations
+        int k = 0;
+        r = launch_gram_refresh(p, e, slots_dev, nullptr, n, 0, st, &k);
+        p->launches += k;
+        if (r != cudaSuccess) return r;
+    }
     return launch_fixup(p, e, st);
 }
 
@@ -1143,7 +1328,7 @@ static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, lo
     MP_CUDA_TRY(cudaMemcpyAsync(e->T, e->h_T, sizeof(int) * B, cudaMemcpyHostToDevice, st));
     MP_CUDA_TRY(cudaMemcpyAsync(e->io, e->h_io, sizeof(BatchIO), cudaMemcpyHostToDevice, st));
     MP_CUDA_TRY(cudaMemsetAsync(e->err, 0, sizeof(int), st));
-    MP_CUDA_TRY(cudaMemsetAsync(e->counters, 0, sizeof(int) * 4, st));
+    MP_CUDA_TRY(cudaMemsetAsync(e->counters, 0, sizeof(int) * 8, st));
     // signal b -> slot b, GEMM row b; then drop those that need no iteration
     MP_CUDA_TRY(engine_admit(p, e, Y, B, nullptr, st));
     // replay the captured steps until no signal is active (each step moves
@@ -1264,7 +1449,7 @@ mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B,
     MP_CUDA_TRY(cudaMemcpyAsync(e->T, e->h_T, sizeof(int) * B, cudaMemcpyHostToDevice, st));
     MP_CUDA_TRY(cudaMemcpyAsync(e->io, e->h_io, sizeof(BatchIO), cudaMemcpyHostToDevice, st));
     MP_CUDA_TRY(cudaMemsetAsync(e->err, 0, sizeof(int), st));
-    MP_CUDA_TRY(cudaMemsetAsync(e->counters, 0, sizeof(int) * 4, st));
+    MP_CUDA_TRY(cudaMemsetAsync(e->counters, 0, sizeof(int) * 8, st));
     // rows 0..B-1 hold R (quantised); the row count is set directly so that
     // zero rows are kept too
     AdmitArgs aa = admit_args(p, e, R, B, nullptr);
@@ -1326,7 +1511,7 @@ static double time_gemm(PlanImpl* p, int prec, int B, const GemmShape& g, const 
         cudaError_t r = cudaMemcpyAsync(e.eps2, e.h_eps2, sizeof(double) * B, cudaMemcpyHostToDevice, st);
         if (r == cudaSuccess) r = cudaMemcpyAsync(e.T, e.h_T, sizeof(int) * B, cudaMemcpyHostToDevice, st);
         if (r == cudaSuccess) r = cudaMemcpyAsync(e.io, e.h_io, sizeof(BatchIO), cudaMemcpyHostToDevice, st);
-        if (r == cudaSuccess) r = cudaMemsetAsync(e.counters, 0, sizeof(int) * 4, st);
+        if (r == cudaSuccess) r = cudaMemsetAsync(e.counters, 0, sizeof(int) * 8, st);
         if (r == cudaSuccess) {
             admit_kernel<<<B, kSelThreads, 0, st>>>(admit_args(p, &e, R, B, nullptr));
             r = cudaGetLastError();

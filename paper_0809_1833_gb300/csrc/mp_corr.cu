@@ -310,17 +310,6 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmA16, const C
                                 a.dump[static_cast<size_t>(row) * a.M + m] = v[j] * (a.fp8 ? a.colscale[m] * rsc : 1.f);
                         }
                     }
-                    if (a.cg && row < n_act) {   // Gram mode: the slot's correlation row (BF16 products)
-                        float* cr = a.cg + static_cast<size_t>(a.act_rows[row]) * a.ldC + m0 + c * 32;
-                        if (m0 + c * 32 + 32 <= a.M) {
-#pragma unroll
-                            for (int j = 0; j < 32; j += 4)
-                                *reinterpret_cast<float4*>(cr + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                        } else {
-                            for (int j = 0; j < 32; ++j)
-                                if (m0 + c * 32 + j < a.M) cr[j] = v[j];
-                        }
-                    }
                     // branch-free: sort each group of 8 keys, then keep the best
                     // 8 of (list, group) -- every lane does the same work
 #pragma unroll

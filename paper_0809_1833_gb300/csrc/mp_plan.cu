@@ -348,8 +348,8 @@ mp_status mp_plan_set_option(mp_plan_t plan, int option, long long value) {
             p->batch_tile_n = static_cast<int>(value);
             return MP_OK;
         case MP_OPT_BATCH_GRAM:
-            if (value != 0 && value != 2 && value != 4 && value != 8 && value != 16)
-                return fail(MP_ERR_INVALID, "batch Gram period must be 0, 2, 4, 8 or 16");
+            if (value < 0 || value > (1 << 20) || value % 16)
+                return fail(MP_ERR_INVALID, "batch Gram period must be 0 or a multiple of 16 up to 2^20");
             p->batch_gram = static_cast<int>(value);
             return MP_OK;
         case MP_OPT_BATCH_TILE_M:

@@ -272,8 +272,8 @@ mp_status mp_server_add_dictionary(mp_server_t srv, mp_plan_t plan, int prec, in
     if (gram_R > 0) {
         if (prec != MP_PREC_BF16)
             return fail(MP_ERR_UNSUPPORTED, "mp_server_add_dictionary: the Gram mode runs with BF16 correlations");
-        if (srv->steps % gram_R)
-            return fail(MP_ERR_INVALID, "mp_server_add_dictionary: the Gram period must divide the chunk's steps");
+        if (gram_R % srv->steps)
+            return fail(MP_ERR_INVALID, "mp_server_add_dictionary: the Gram period must be a multiple of 16");
         mp_status gs = gram_prepare(p, nullptr);
         if (gs != MP_OK) return gs;
     }
@@ -318,7 +318,7 @@ mp_status mp_server_add_dictionary(mp_server_t srv, mp_plan_t plan, int prec, in
             *d->eng.h_io = io;
             e = cudaMemcpy(d->eng.io, d->eng.h_io, sizeof(BatchIO), cudaMemcpyHostToDevice);
         }
-        if (e == cudaSuccess) e = cudaMemset(d->eng.counters, 0, sizeof(int) * 4);
+        if (e == cudaSuccess) e = cudaMemset(d->eng.counters, 0, sizeof(int) * 8);
         if (e == cudaSuccess) e = cudaMemset(d->eng.err, 0, sizeof(int));
         if (e == cudaSuccess) st = engine_build_graph(p, &d->eng, srv->steps, true, dx, dst, dl, dc);
     }
