@@ -515,6 +515,27 @@ def variants_measure(n_sig=4, gram_period=32):
     B.mp_recover_omp(plan, Y[0].data_ptr(), x.data_ptr(), w["eps"], 2, None, True, s)    # scratch
     out["omp"] = timed(B.mp_recover_omp)
     B.mp_plan_destroy(plan)
+    # the floor under the grid shapes' iteration: the same N on one atom per
+    # CTA, so an iteration is the grid barrier, the residual update and the
+    # FP64 energy alone (OMP adds four such barriers per step, Gram MP runs
+    # on this floor plus one row of G)
+    G = torch.cuda.get_device_properties(0).multi_processor_count
+    tiny = np.ascontiguousarray(psi_np[:G])
+    d = torch.from_numpy(tiny).cuda()
+    fp = B.mp_plan_create(w["N"], G, d.data_ptr(), stream=s)
+    floors = {}
+    for mode, label in ((2, "grid_resident"), (3, "grid_stream")):
+        B.mp_plan_set_option(fp, B.MP_OPT_PLAIN_MODE, mode)
+        B.mp_recover(fp, Y[0].data_ptr(), x.data_ptr(), 0.0, 100, None, True, s)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        B.mp_recover(fp, Y[0].data_ptr(), x.data_ptr(), 0.0, 2000, None, False, s)
+        b.record(st)
+        b.synchronize()
+        floors[label] = 1e3 * a.elapsed_time(b) / 2000
+    B.mp_plan_destroy(fp)
+    out["grid_iteration_floor_us"] = floors
+    out["floor_shape"] = f"N = {w['N']}, {G} atoms (one per CTA), 2000 iterations"
     return out
 
 
@@ -840,6 +861,70 @@ def step_breakdown(rows=(1, 2, 4, 8, 16), dict_index=3, reps=3, gram=0, T=None):
     B.mp_plan_destroy(plan)
 
 
+def shard_overhead(iters=300):
+    """Per-iteration cost of the atom-sharded decode's host loop
+    (paper_0809_1833_gb300/sharded.py) on one GPU, on the benchmark's
+    dictionary as a single shard: the persistent kernel (mp_recover) capped
+    at ``iters`` iterations; the sharded loop with no exchange (two kernel
+    launches and a Python step per iteration); and the same with the record
+    all-gathered every iteration through a one-rank NCCL group (the
+    collective's launch and synchronisation, no link transfer).  Prints one
+    JSON line."""
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0809_1833_gb300 import binding as B
+    from paper_0809_1833_gb300 import sharded as S
+    w, psi_np, Y_np, _ = make_problem(1)
+    N, M = w["N"], w["M"]
+    st = torch.cuda.current_stream()
+    d = torch.from_numpy(psi_np).cuda()
+    plan = B.mp_plan_create(N, M, d.data_ptr(), stream=st.cuda_stream)
+    del d
+    y = torch.from_numpy(Y_np[0]).cuda()
+    x = torch.empty(M, device="cuda")
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, out
+
+    t_dir, _ = timed(lambda: B.mp_recover(plan, y.data_ptr(), x.data_ptr(), 0.0, iters, None, True, st.cuda_stream))
+    ops = S.ShardOps(plan, 0, y, stream=st.cuda_stream)
+    t_loc, r_loc = timed(lambda: S.sharded_recover(ops, 0.0, iters, check_every=iters + 1))
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    os.environ.setdefault("MASTER_PORT", "29533")
+    out = {"workload": WORKLOAD, "iterations": iters,
+           "direct_us_per_iteration": 1e6 * t_dir / iters,
+           "sharded_no_exchange_us_per_iteration": 1e6 * t_loc / iters,
+           "record_bytes": B.mp_shard_record_bytes(plan)}
+    try:
+        dist.init_process_group("nccl", rank=0, world_size=1)
+        g = dist.new_group([0])
+        recs = torch.empty(B.mp_shard_record_bytes(plan), dtype=torch.uint8, device="cuda")
+
+        def with_gather():
+            ops.init(0.0, iters)
+            for _ in range(iters):
+                rec = ops.local()
+                dist.all_gather_into_tensor(recs, rec, group=g)
+                ops.apply(recs, 1)
+            return ops.result()
+        t_g, _ = timed(with_gather)
+        out["sharded_nccl_1rank_us_per_iteration"] = 1e6 * t_g / iters
+        dist.destroy_process_group()
+    except Exception as ex:   # no NCCL here
+        out["sharded_nccl_1rank_us_per_iteration"] = None
+        out["nccl"] = f"{type(ex).__name__}: {ex}"[:200]
+    out["host_loop_overhead_us"] = out["sharded_no_exchange_us_per_iteration"] - out["direct_us_per_iteration"]
+    B.mp_plan_destroy(plan)
+    print(json.dumps({"shard_overhead": out}), flush=True)
+
+
 def fp8_error(n_sample=2):
     """The FP8 batched workload (N=8192, M=32768, 256 signals) decoded in one
     batch; for the first n_sample signals the FP64 oracle's decode of the same
@@ -1109,11 +1194,16 @@ def main():
     ap.add_argument("--breakdown-rows", type=int, nargs="*", default=None,
                     help="active-row counts of --step-breakdown (default 1 2 4 8 16)")
     ap.add_argument("--breakdown-T", type=int, default=None, help="iteration cap of --step-breakdown")
+    ap.add_argument("--shard-overhead", action="store_true",
+                    help="run only the per-iteration cost of the atom-sharded host loop on one GPU")
     ap.add_argument("--cpu-worker", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-worker-iters", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_worker is not None:
         cpu_worker(args.cpu_worker, args.cpu_worker_iters)
+        return
+    if args.shard_overhead:
+        shard_overhead()
         return
     if args.step_breakdown:
         step_breakdown(rows=tuple(args.breakdown_rows or (1, 2, 4, 8, 16)), gram=args.served_gram,
