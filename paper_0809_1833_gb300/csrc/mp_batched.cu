@@ -341,6 +341,21 @@ MP_DEV void top8_insert(unsigned long long (&t)[kTop], unsigned long long k) {
     }
 }
 
+// Score of the 8th (smallest) key of a sorted top 8 as a float (0 while the
+// list is not full): an |c| below it cannot enter, so the key is not built.
+MP_DEV float top8_floor(const unsigned long long (&t)[kTop]) {
+    return __uint_as_float(static_cast<uint32_t>(t[kTop - 1] >> 32));
+}
+// Offer |c| of atom j to the sorted top 8 t (thr: top8_floor(t), kept).
+MP_DEV void top8_offer(unsigned long long (&t)[kTop], float& thr, float c, int j, int M) {
+    const float s = fabsf(c);
+    if (s >= thr && j < M) {
+        top8_insert(t, cand_key(__float_as_uint(s), static_cast<uint32_t>(j), M));
+        thr = top8_floor(t);
+    }
+}
+
+
 // Block-wide best 8 of the threads' sorted lists lk (a butterfly of the
 // bitonic top-8 merge inside each warp, then warp 0 over the warps' lists,
 // through w, a THREADS / 32 x 8 shared array); thread 0 stores them to out.
@@ -380,7 +395,8 @@ MP_DEV void block_top8_store(unsigned long long (&lk)[kTop], unsigned long long 
 constexpr int GM_LISTS = 0, GM_GRAM = 1;
 
 template <int THREADS, int GM>
-__global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : 2) select_update_kernel(const SelArgs a) {
+__global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : (THREADS == 2 * kSumChains ? 2 : 1))
+    select_update_kernel(const SelArgs a) {
     extern __shared__ float4 r_sh4[];
     float* r = reinterpret_cast<float*>(r_sh4);
     __shared__ double redd[THREADS / 32];
@@ -604,6 +620,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : 2) select
 #pragma unroll
         for (int k = 0; k < kTop; ++k) lk[k] = 0ull;
         const int nq = a.ldC / 4;
+        float thr = 0.f;
         constexpr int U = THREADS == kSumChains ? 4 : 8;   // float4s of G and of the row in flight per thread
         for (int q0 = threadIdx.x; q0 < nq; q0 += U * THREADS) {
             float4 g[U], v[U];
@@ -625,10 +642,10 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : 2) select
                 v[u].w = fmaf(-c, g[u].w, v[u].w);
                 cr4[q] = v[u];
                 const int j0 = 4 * q;
-                if (j0 + 0 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v[u].x)), j0 + 0, a.M));
-                if (j0 + 1 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v[u].y)), j0 + 1, a.M));
-                if (j0 + 2 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v[u].z)), j0 + 2, a.M));
-                if (j0 + 3 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v[u].w)), j0 + 3, a.M));
+                top8_offer(lk, thr, v[u].x, j0 + 0, a.M);
+                top8_offer(lk, thr, v[u].y, j0 + 1, a.M);
+                top8_offer(lk, thr, v[u].z, j0 + 2, a.M);
+                top8_offer(lk, thr, v[u].w, j0 + 3, a.M);
             }
         }
         block_top8_store<THREADS>(lk, gtw, a.gtop + static_cast<size_t>(slot) * kTop);
@@ -644,7 +661,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : 2) select
 // memory and its warps run over a block of kCorrAtoms atoms, each atom read
 // once from HBM for all the staged rows; float4 loads, 8 in flight per lane.
 constexpr int kCorrRows = 8;
-constexpr int kCorrAtoms = 128;
+constexpr int kCorrAtoms = 64;
 constexpr int kCorrThreads = 256;
 constexpr int kCorrSmem = 200 * 1024;   // shared memory for the staged rows, at most
 
@@ -747,13 +764,14 @@ __global__ void __launch_bounds__(kCorrThreads) gram_scan_kernel(const CorrRowsA
     unsigned long long lk[kTop];
 #pragma unroll
     for (int j = 0; j < kTop; ++j) lk[j] = 0ull;
+    float thr = 0.f;
     for (int q = threadIdx.x; q < a.ldC / 4; q += kCorrThreads) {
         const float4 v = cr4[q];
         const int j0 = 4 * q;
-        if (j0 + 0 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v.x)), j0 + 0, a.M));
-        if (j0 + 1 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v.y)), j0 + 1, a.M));
-        if (j0 + 2 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v.z)), j0 + 2, a.M));
-        if (j0 + 3 < a.M) top8_insert(lk, cand_key(__float_as_uint(fabsf(v.w)), j0 + 3, a.M));
+        top8_offer(lk, thr, v.x, j0 + 0, a.M);
+        top8_offer(lk, thr, v.y, j0 + 1, a.M);
+        top8_offer(lk, thr, v.z, j0 + 2, a.M);
+        top8_offer(lk, thr, v.w, j0 + 3, a.M);
     }
     block_top8_store<kCorrThreads>(lk, w, gtop + static_cast<size_t>(slot) * kTop);
 }
@@ -1143,11 +1161,13 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, cudaStream
     // lane in flight (with few signals the rescore is a latency chain of L2 /
     // HBM reads); engines of 512 slots and more: 4 warps, two candidates
     // each, so more signals' CTAs fit on an SM at a full batch
+    // the Gram mode's small engines: 16 warps, the row's update and top 8
+    // spread over twice the threads
     const size_t sm = p->ldN * sizeof(float);
     if (e->cap < kWideSelectCap) {
         constexpr int TH = 2 * kSumChains;
         if (!gram) select_update_kernel<TH, GM_LISTS><<<e->cap, TH, sm, st>>>(sa);
-        else select_update_kernel<TH, GM_GRAM><<<e->cap, TH, sm, st>>>(sa);
+        else select_update_kernel<2 * TH, GM_GRAM><<<e->cap, 2 * TH, sm, st>>>(sa);
     } else {
         constexpr int TH = kSumChains;
         if (!gram) select_update_kernel<TH, GM_LISTS><<<e->cap, TH, sm, st>>>(sa);
@@ -1175,7 +1195,9 @@ static cudaError_t launch_gram_refresh(PlanImpl* p, BatchEngine* e, const int* r
     a.R = R;
     a.Cg = e->Cg;
     a.ldC = e->ldC;
-    a.rpc = corr_rows_per_cta(p);
+    // a host-known row count (admission) stages no more rows than listed:
+    // less shared memory per CTA, more CTAs per SM, more loads in flight
+    a.rpc = n_ptr ? corr_rows_per_cta(p) : std::min(corr_rows_per_cta(p), n_max);
     const dim3 grid((p->M + kCorrAtoms - 1) / kCorrAtoms, (n_max + a.rpc - 1) / a.rpc);
     corr_rows_kernel<<<grid, kCorrThreads, static_cast<size_t>(a.rpc) * p->ldN * sizeof(float), st>>>(a);
     gram_scan_kernel<<<n_max, kCorrThreads, 0, st>>>(a, e->gtop);
@@ -1197,7 +1219,7 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
         const int b = p->ldN * 4;
         MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains, GM_LISTS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains, GM_GRAM>,
+        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<4 * kSumChains, GM_GRAM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<kSumChains, GM_LISTS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, b));
