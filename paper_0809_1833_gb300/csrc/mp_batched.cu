@@ -48,6 +48,10 @@ constexpr int kFixThreads = 1024;
 constexpr int kStepsPerGraph = 16;   // even: every graph starts and ends on operand half 0
 
 // ------------------------------------------------------------------ block helpers
+// The FP64 sum of the energy chains (threads 0..kSumChains-1; the other
+// threads hold zeros): warp butterflies, then the chain warps' sums in warp
+// order (adding the other warps' +0.0 would not change a bit, and FP64 adds
+// are slow on this part, so they are left out).
 MP_DEV double block_sum_f64(double v, double* red) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     v = warp_sum_f64(v);
@@ -55,7 +59,7 @@ MP_DEV double block_sum_f64(double v, double* red) {
     if (lane == 0) red[warp] = v;
     __syncthreads();
     double s = 0.0;
-    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s += red[w];
+    for (int w = 0; w < kSumChains / 32; ++w) s += red[w];
     return s;
 }
 MP_DEV float block_max_f32(float v, float* red) {
@@ -389,12 +393,7 @@ MP_DEV void block_top8_store(unsigned long long (&lk)[kTop], unsigned long long 
     }
 }
 
-// Candidate sources of the select kernel: GM_LISTS, the step's GEMM lists
-// (the direct step); GM_GRAM, the slot's carried 8 largest |c| of its
-// FP32 correlation row, which the kernel then updates from G (the Gram mode).
-constexpr int GM_LISTS = 0, GM_GRAM = 1;
-
-template <int THREADS, int GM>
+template <int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : (THREADS == 2 * kSumChains ? 2 : 1))
     select_update_kernel(const SelArgs a) {
     extern __shared__ float4 r_sh4[];
@@ -417,14 +416,6 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : (THREADS 
     // r streams into shared memory while the candidate lists are merged
     for (int k = threadIdx.x; k < n4; k += blockDim.x) cp_async16(rs4 + k, rg4 + k);
     cp_async_commit();
-    if constexpr (GM == GM_GRAM) {
-        // the slot's correlation row heads for L2 while the step rescores
-        // (16 KiB pieces, one per thread)
-        const char* crow = reinterpret_cast<const char*>(a.Cg + static_cast<size_t>(slot) * a.ldC);
-        const uint32_t bytes = static_cast<uint32_t>(a.ldC) * 4u;
-        const uint32_t off = static_cast<uint32_t>(threadIdx.x) * 16384u;
-        if (off < bytes) prefetch_l2(crow + off, min(16384u, bytes - off));
-    }
 
     // merge the sorted per-tile lists: keys (score bits, ~atom) order by
     // score, then by the smaller atom.  Thread t folds lists t, t + THREADS,
@@ -432,13 +423,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : (THREADS 
     // butterfly of the same merge gives lane 0 of every warp the warp's best
     // 8, and warp 0 merges those.  Candidate sets are disjoint at every merge,
     // so the result is the set of the 8 largest keys, whatever the split.
-    if constexpr (GM == GM_GRAM) {
-        // the 8 largest |c| of the slot's Gram-updated correlations
-        if (threadIdx.x < kTop) {
-            const unsigned long long k = a.gtop[static_cast<size_t>(slot) * kTop + threadIdx.x];
-            top[threadIdx.x] = k ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(k)) : -1;
-        }
-    } else {
+    {
         __shared__ unsigned long long wtop[THREADS / 32][kTop];
         unsigned long long lk[kTop];
 #pragma unroll
@@ -524,13 +509,6 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : (THREADS 
     }
     const int m = key_index(kbest);
     const float c = key_coef(kbest);
-    if constexpr (GM == GM_GRAM) {
-        // and the selected atom's row of G while r and the energy are updated
-        const char* grow = reinterpret_cast<const char*>(a.G + static_cast<size_t>(m) * a.ldG);
-        const uint32_t bytes = static_cast<uint32_t>(a.ldG) * 4u;
-        const uint32_t off = static_cast<uint32_t>(threadIdx.x) * 16384u;
-        if (off < bytes) prefetch_l2(grow + off, min(16384u, bytes - off));
-    }
     // thread 0 updates x~[m] at the end: fetch the old value now
     BatchIO io;
     float xm = 0.f;
@@ -592,9 +570,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : (THREADS 
         return;
     }
     char* qrow = static_cast<char*>(a.Rq_next) + static_cast<size_t>(row) * a.ldq * (a.fp8 ? 1 : 2);
-    if constexpr (GM == GM_GRAM) {
-        // no GEMM reads the quantised operand in the Gram mode
-    } else if (a.fp8) {
+    if (a.fp8) {
         block_quantize(r, a.ldN, qrow, a.ldq, 1, redf);
     } else {
         // the first ldN elements; the row's padding up to ldq holds zeros (the
@@ -607,26 +583,167 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : (THREADS 
             q2[1] = __floats2bfloat162_rn(v.z, v.w);
         }
     }
-    if constexpr (GM == GM_GRAM) {
-        // Gram update of the slot's correlations: after r <- r - c psi_m,
-        // <r, psi_j> moves by -c <psi_m, psi_j> = -c G[m][j] (Eqs. 9, 11), one
-        // FP32 FMA per entry with the committed c; and the 8 largest |c| of
-        // the result for the next step (keys as cand_key; ties to the
-        // smaller atom)
-        __shared__ unsigned long long gtw[THREADS / 32][kTop];
-        float4* cr4 = reinterpret_cast<float4*>(a.Cg + static_cast<size_t>(slot) * a.ldC);
-        const float4* gr4 = reinterpret_cast<const float4*>(a.G + static_cast<size_t>(m) * a.ldG);
-        unsigned long long lk[kTop];
+    step_done(a);
+}
+
+// ------------------------------------------------------------------ Gram-mode step (one kernel)
+// One MP step of one signal in the Gram mode.  The candidates are the slot's
+// carried 8 largest |c|; they are rescored in FP32 from the FP32 atoms in
+// the plain kernel's correlation order and the best is committed (Eq. 10),
+// r -= c psi_m in FP32 (Eq. 11).  Then two warp groups run at once:
+//   warps 0..3   the FP64 energy in the plain kernel's 128-chain order, the
+//                stop test (Eq. 8) and the slot's bookkeeping;
+//   warps 4..15  the Gram update of the slot's correlations,
+//                c_j -= c G[m][j] (one FP32 FMA per entry), and their 8
+//                largest |c| for the next step (keys as cand_key): each
+//                thread keeps the largest |c| of its entries; a warp sort of
+//                those gives, over the group's warps, a threshold that at
+//                least 8 entries reach, so the 8 largest are among the few
+//                entries at or above it, which are ranked exactly.
+// The update runs whether or not the signal stops (a stopped slot's row is
+// not read again).  The same 8 keys as a full ranking of the row, so the
+// same results bit for bit.
+constexpr int kGramThreads = 512;
+constexpr int kGramGroup0 = kSumChains;                // energy group: threads 0..127
+constexpr int kGramList = 256;                          // entries at or above the threshold kept
+
+MP_DEV float warp_kth_largest(float v, int k) {
+    // descending bitonic sort of the warp's 32 values; lane k-1 then holds
+    // the k-th largest
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-        for (int k = 0; k < kTop; ++k) lk[k] = 0ull;
-        const int nq = a.ldC / 4;
-        float thr = 0.f;
-        constexpr int U = THREADS == kSumChains ? 4 : 8;   // float4s of G and of the row in flight per thread
-        for (int q0 = threadIdx.x; q0 < nq; q0 += U * THREADS) {
+    for (int s = 2; s <= 32; s <<= 1)
+#pragma unroll
+        for (int j = s >> 1; j > 0; j >>= 1) {
+            const float o = __shfl_xor_sync(0xffffffffu, v, j);
+            const bool desc = (lane & s) == 0 || s == 32;
+            const bool low = (lane & j) == 0;
+            v = (low == desc) ? fmaxf(v, o) : fminf(v, o);
+        }
+    return __shfl_sync(0xffffffffu, v, k - 1);
+}
+
+__global__ void __launch_bounds__(kGramThreads, 1) gram_select_kernel(const SelArgs a) {
+    extern __shared__ float4 r_sh4[];
+    float* r = reinterpret_cast<float*>(r_sh4);
+    __shared__ double redd[kGramGroup0 / 32];
+    __shared__ int top[kTop];
+    __shared__ unsigned long long rkey[kTop];
+    __shared__ float wthr[kGramThreads / 32];
+    __shared__ unsigned long long list[kGramList];
+    __shared__ int list_n;
+    __shared__ unsigned long long gtw[kGramThreads / 32][kTop];
+    const int i = blockIdx.x;
+    if (i >= *a.n_act) {
+        step_done(a);
+        return;
+    }
+    const int slot = a.act[i];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* rs4 = reinterpret_cast<float4*>(r);
+    float4* rg4 = reinterpret_cast<float4*>(a.R32 + static_cast<size_t>(slot) * a.ldN);
+    const int n4 = a.ldN / 4;
+    SlotState s = a.st[slot];
+    BatchIO io;
+    if (threadIdx.x == 0) io = *a.io;
+    for (int k = threadIdx.x; k < n4; k += kGramThreads) cp_async16(rs4 + k, rg4 + k);
+    cp_async_commit();
+    float4* cr4 = reinterpret_cast<float4*>(a.Cg + static_cast<size_t>(slot) * a.ldC);
+    const int nq = a.ldC / 4;
+    for (int q = threadIdx.x * 8; q < nq; q += kGramThreads * 8) prefetch_line_l2(cr4 + q);
+    if (threadIdx.x < kTop) {
+        const unsigned long long k = a.gtop[static_cast<size_t>(slot) * kTop + threadIdx.x];
+        top[threadIdx.x] = k ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(k)) : -1;
+    }
+    if (threadIdx.x == 0) list_n = 0;
+    cp_async_wait_all();
+    __syncthreads();
+    // rescore in FP32 (Eq. 9), one candidate per warp
+    if (warp < kTop) {
+        const int m0 = top[warp];
+        unsigned long long key = 0ull;
+        if (m0 >= 0) key = pack_key(dot1_deep<16>(a.psi32 + static_cast<size_t>(m0) * a.ldN, r, a.ldN, lane), m0);
+        if (lane == 0) rkey[warp] = key;
+    }
+    __syncthreads();
+    unsigned long long kbest = 0ull;
+#pragma unroll
+    for (int w = 0; w < kTop; ++w) kbest = umax64(kbest, rkey[w]);
+    if (kbest == 0ull) {   // no candidate: nothing can be selected; the signal leaves
+        if (threadIdx.x == 0) {
+            s.status = MP_ERR_INVALID;
+            a.st[slot] = s;
+            if (a.fin_list) a.fin_list[atomicAdd(a.fin_count, 1)] = slot;
+        }
+        step_done(a);
+        return;
+    }
+    const int m = key_index(kbest);
+    const float c = key_coef(kbest);
+    const float4* gr4 = reinterpret_cast<const float4*>(a.G + static_cast<size_t>(m) * a.ldG);
+    for (int q = threadIdx.x * 8; q < nq; q += kGramThreads * 8) prefetch_line_l2(gr4 + q);
+    float xm = 0.f;
+    if (threadIdx.x == 0) xm = io.X[static_cast<size_t>(slot) * io.ldx + m];
+    // Eq. 11 in FP32
+    const float4* pm = reinterpret_cast<const float4*>(a.psi32 + static_cast<size_t>(m) * a.ldN);
+    for (int k = threadIdx.x; k < n4; k += kGramThreads) {
+        const float4 p = __ldg(pm + k);
+        float4 v = rs4[k];
+        v.x = fmaf(-c, p.x, v.x);
+        v.y = fmaf(-c, p.y, v.y);
+        v.z = fmaf(-c, p.z, v.z);
+        v.w = fmaf(-c, p.w, v.w);
+        rg4[k] = v;
+        rs4[k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kGramGroup0) {
+        // ---- energy group: e = sum r^2 in FP64 in the plain kernel's order
+        double acc = 0.0;
+        for (int k = threadIdx.x; k < n4; k += kSumChains) {
+            const float4 v = rs4[k];
+            acc = fma(static_cast<double>(v.x), static_cast<double>(v.x), acc);
+            acc = fma(static_cast<double>(v.y), static_cast<double>(v.y), acc);
+            acc = fma(static_cast<double>(v.z), static_cast<double>(v.z), acc);
+            acc = fma(static_cast<double>(v.w), static_cast<double>(v.w), acc);
+        }
+        acc = warp_sum_f64(acc);
+        if (lane == 0) redd[warp] = acc;
+        named_bar_sync(1, kGramGroup0);
+        if (threadIdx.x == 0) {
+            double e = 0.0;
+#pragma unroll
+            for (int w = 0; w < kGramGroup0 / 32; ++w) e += redd[w];
+            io.X[static_cast<size_t>(slot) * io.ldx + m] = xm + c;   // Eq. 10
+            if (io.tr_atoms && s.t < io.tr_cap) io.tr_atoms[static_cast<size_t>(slot) * io.tr_cap + s.t] = m;
+            if (io.tr_coefs && s.t < io.tr_cap) io.tr_coefs[static_cast<size_t>(slot) * io.tr_cap + s.t] = c;
+            if (io.tr_energy && s.t < io.tr_cap) io.tr_energy[static_cast<size_t>(slot) * io.tr_cap + s.t] = e;
+            const double cc = static_cast<double>(c);
+            s.audit = fmax(s.audit, fabs(e - (s.e - cc * cc)));   // divided by e0 when reported
+            s.e = e;
+            s.t += 1;   // Eq. 12
+            const bool conv = !(e > s.thr2);
+            const bool stop = conv || s.t >= s.T;
+            if (stop) s.stop_reason = conv ? MP_STOP_CONVERGED : MP_STOP_MAX_ITERS;
+            a.st[slot] = s;
+            if (!stop) {
+                const int row = atomicAdd(a.n_next, 1);
+                a.act_next[row] = slot;
+            } else if (a.fin_list) {
+                a.fin_list[atomicAdd(a.fin_count, 1)] = slot;
+            }
+        }
+    } else {
+        // ---- Gram group: c_j -= c G[m][j] and the row's 8 largest |c|
+        constexpr int GT = kGramThreads - kGramGroup0;
+        const int gt = threadIdx.x - kGramGroup0, gw = warp - kGramGroup0 / 32;
+        float mx = 0.f;
+        constexpr int U = 8;
+        for (int q0 = gt; q0 < nq; q0 += U * GT) {
             float4 g[U], v[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int q = q0 + u * THREADS;
+                const int q = q0 + u * GT;
                 if (q < nq) {
                     g[u] = __ldg(gr4 + q);
                     v[u] = cr4[q];
@@ -634,22 +751,108 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : (THREADS 
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int q = q0 + u * THREADS;
+                const int q = q0 + u * GT;
                 if (q >= nq) break;
                 v[u].x = fmaf(-c, g[u].x, v[u].x);
                 v[u].y = fmaf(-c, g[u].y, v[u].y);
                 v[u].z = fmaf(-c, g[u].z, v[u].z);
                 v[u].w = fmaf(-c, g[u].w, v[u].w);
                 cr4[q] = v[u];
+                // entries past M (the row's padding) never rank
                 const int j0 = 4 * q;
-                top8_offer(lk, thr, v[u].x, j0 + 0, a.M);
-                top8_offer(lk, thr, v[u].y, j0 + 1, a.M);
-                top8_offer(lk, thr, v[u].z, j0 + 2, a.M);
-                top8_offer(lk, thr, v[u].w, j0 + 3, a.M);
+                if (j0 + 0 < a.M) mx = fmaxf(mx, fabsf(v[u].x));
+                if (j0 + 1 < a.M) mx = fmaxf(mx, fabsf(v[u].y));
+                if (j0 + 2 < a.M) mx = fmaxf(mx, fabsf(v[u].z));
+                if (j0 + 3 < a.M) mx = fmaxf(mx, fabsf(v[u].w));
             }
         }
-        block_top8_store<THREADS>(lk, gtw, a.gtop + static_cast<size_t>(slot) * kTop);
+        // the warp's 8th largest thread maximum: 8 entries of the warp reach
+        // it, so the row's 8th largest |c| does too; the largest such value
+        // over the group's warps is the threshold
+        const float w8 = warp_kth_largest(mx, kTop);
+        if (lane == 0) wthr[gw] = w8;
+        named_bar_sync(2, GT);
+        float thr = 0.f;
+#pragma unroll
+        for (int w = 0; w < GT / 32; ++w) thr = fmaxf(thr, wthr[w]);
+        // entries at or above the threshold (only threads whose maximum
+        // reaches it re-read their entries, which they wrote themselves)
+        bool overflow = false;
+        if (mx >= thr) {
+            for (int q = gt; q < nq; q += GT) {
+                const float4 v = cr4[q];
+                const float e4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = 4 * q + u;
+                    const float sc = fabsf(e4[u]);
+                    if (j < a.M && sc >= thr) {
+                        const int at = atomicAdd(&list_n, 1);
+                        if (at < kGramList) list[at] = cand_key(__float_as_uint(sc), static_cast<uint32_t>(j), a.M);
+                    }
+                }
+            }
+        }
+        named_bar_sync(2, GT);
+        const int ln = list_n;
+        overflow = ln > kGramList;
+        unsigned long long lk[kTop];
+#pragma unroll
+        for (int k = 0; k < kTop; ++k) lk[k] = 0ull;
+        if (!overflow) {
+            // the kept entries' 8 largest keys: one warp
+            if (gw == 0) {
+                for (int t = lane; t < ln; t += 32) top8_insert(lk, list[t]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    unsigned long long other[kTop];
+#pragma unroll
+                    for (int k = 0; k < kTop; ++k) other[k] = __shfl_xor_sync(0xffffffffu, lk[k], o);
+                    merge_top8_u64(lk, other);
+                }
+                if (lane == 0)
+#pragma unroll
+                    for (int k = 0; k < kTop; ++k) a.gtop[static_cast<size_t>(slot) * kTop + k] = lk[k];
+            }
+        } else {
+            // more entries tie at the threshold than the list holds: rank
+            // the whole row (every thread its own entries, then the group)
+            float t8 = 0.f;
+            for (int q = gt; q < nq; q += GT) {
+                const float4 v = cr4[q];
+                top8_offer(lk, t8, v.x, 4 * q + 0, a.M);
+                top8_offer(lk, t8, v.y, 4 * q + 1, a.M);
+                top8_offer(lk, t8, v.z, 4 * q + 2, a.M);
+                top8_offer(lk, t8, v.w, 4 * q + 3, a.M);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                unsigned long long other[kTop];
+#pragma unroll
+                for (int k = 0; k < kTop; ++k) other[k] = __shfl_xor_sync(0xffffffffu, lk[k], o);
+                merge_top8_u64(lk, other);
+            }
+            if (lane == 0)
+#pragma unroll
+                for (int k = 0; k < kTop; ++k) gtw[gw][k] = lk[k];
+            named_bar_sync(2, GT);
+            if (gw == 0) {
+#pragma unroll
+                for (int k = 0; k < kTop; ++k) lk[k] = lane < GT / 32 ? gtw[lane][k] : 0ull;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    unsigned long long other[kTop];
+#pragma unroll
+                    for (int k = 0; k < kTop; ++k) other[k] = __shfl_xor_sync(0xffffffffu, lk[k], o);
+                    merge_top8_u64(lk, other);
+                }
+                if (lane == 0)
+#pragma unroll
+                    for (int k = 0; k < kTop; ++k) a.gtop[static_cast<size_t>(slot) * kTop + k] = lk[k];
+            }
+        }
     }
+    __syncthreads();
     step_done(a);
 }
 
@@ -1157,22 +1360,15 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, cudaStream
     // kernel clears the count it read once all its CTAs have read it
     sa.n_act_w = cnt[half];
     sa.done_ctr = gram ? e->counters + 5 : nullptr;
-    // small engines: 8 warps, each rescoring one candidate with 16 loads per
-    // lane in flight (with few signals the rescore is a latency chain of L2 /
-    // HBM reads); engines of 512 slots and more: 4 warps, two candidates
-    // each, so more signals' CTAs fit on an SM at a full batch
-    // the Gram mode's small engines: 16 warps, the row's update and top 8
-    // spread over twice the threads
+    // direct step, small engines: 8 warps, each rescoring one candidate
+    // with 16 loads per lane in flight (with few signals the rescore is a
+    // latency chain of L2 / HBM reads); engines of 512 slots and more: 4
+    // warps, two candidates each, so more signals' CTAs fit on an SM at a
+    // full batch.  Gram mode: the Gram-step kernel (16 warps).
     const size_t sm = p->ldN * sizeof(float);
-    if (e->cap < kWideSelectCap) {
-        constexpr int TH = 2 * kSumChains;
-        if (!gram) select_update_kernel<TH, GM_LISTS><<<e->cap, TH, sm, st>>>(sa);
-        else select_update_kernel<2 * TH, GM_GRAM><<<e->cap, 2 * TH, sm, st>>>(sa);
-    } else {
-        constexpr int TH = kSumChains;
-        if (!gram) select_update_kernel<TH, GM_LISTS><<<e->cap, TH, sm, st>>>(sa);
-        else select_update_kernel<TH, GM_GRAM><<<e->cap, TH, sm, st>>>(sa);
-    }
+    if (gram) gram_select_kernel<<<e->cap, kGramThreads, sm, st>>>(sa);
+    else if (e->cap < kWideSelectCap) select_update_kernel<2 * kSumChains><<<e->cap, 2 * kSumChains, sm, st>>>(sa);
+    else select_update_kernel<kSumChains><<<e->cap, kSumChains, sm, st>>>(sa);
     ++*kernels;
     return cudaGetLastError();
 }
@@ -1217,14 +1413,11 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
     MP_CUDA_TRY(corr_prepare());
     if (p->ldN * 4 > 48 * 1024) {
         const int b = p->ldN * 4;
-        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains, GM_LISTS>,
+        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<4 * kSumChains, GM_GRAM>,
+        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<kSumChains>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<kSumChains, GM_LISTS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<kSumChains, GM_GRAM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MP_CUDA_TRY(cudaFuncSetAttribute(gram_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
     }
     if (e->gram_R > 0 && (e->gram_R % steps || !p->gram))
         return fail(MP_ERR_INVALID, "batched step graph: the Gram period must be a multiple of the steps per graph");
