@@ -232,6 +232,8 @@ struct SelArgs {
     unsigned long long* gtop;   // per-slot 8 largest |c| of Cg (keys as cand_key), sorted
     int* n_act_w;           // Gram mode: this half's count, cleared by the step's last CTA
     int* done_ctr;          //   CTAs of the step that finished (NULL: not cleared here)
+    int* err;               // Gram mode: a bounded wait gave up (MP_ERR_TIMEOUT)
+    unsigned long long lim; //   the waits' limit, ns
 };
 
 // Gram mode: the step's last CTA clears the count it read, after every CTA
@@ -623,9 +625,51 @@ MP_DEV float warp_kth_largest(float v, int k) {
     return __shfl_sync(0xffffffffu, v, k - 1);
 }
 
+// The row's 8 largest keys from the kept entries (list, n entries): with at
+// most 32, one warp ranks each by counting the larger keys (keys are
+// distinct); with more, each lane folds its share into a sorted top 8 and
+// a butterfly merges them.  Lane 0's results go to out.
+MP_DEV void list_top8_store(const unsigned long long* list, int n, unsigned long long* out) {
+    const int lane = threadIdx.x & 31;
+    if (n <= 32) {
+        const unsigned long long k = lane < n ? list[lane] : 0ull;
+        int rank = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) rank += __shfl_sync(0xffffffffu, k, j) > k ? 1 : 0;
+        if (lane < n && rank < kTop) out[rank] = k;
+        if (lane >= n && lane < kTop) out[lane] = 0ull;   // fewer than 8 entries: empty keys
+        return;
+    }
+    unsigned long long lk[kTop];
+#pragma unroll
+    for (int k = 0; k < kTop; ++k) lk[k] = 0ull;
+    for (int t = lane; t < n; t += 32) top8_insert(lk, list[t]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long other[kTop];
+#pragma unroll
+        for (int k = 0; k < kTop; ++k) other[k] = __shfl_xor_sync(0xffffffffu, lk[k], o);
+        merge_top8_u64(lk, other);
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < kTop; ++k) out[k] = lk[k];
+}
+
+// SM: the slot's correlation row and the selected atom's row of G are
+// brought into shared memory by bulk copies (issued as soon as their
+// addresses are known, landing while the step rescores and updates r);
+// otherwise they are read from global memory.  The grid has at most one CTA
+// per SM; each CTA takes rows blockIdx.x, blockIdx.x + gridDim.x, ...
+template <bool SM>
 __global__ void __launch_bounds__(kGramThreads, 1) gram_select_kernel(const SelArgs a) {
-    extern __shared__ float4 r_sh4[];
-    float* r = reinterpret_cast<float*>(r_sh4);
+    extern __shared__ float4 dsm[];
+    float* r = reinterpret_cast<float*>(dsm);
+    float4* rs4 = dsm;
+    const int n4 = a.ldN / 4;
+    const int nq = a.ldC / 4;
+    float4* cs4 = dsm + n4;          // SM: the correlation row
+    float4* gs4 = dsm + n4 + nq;     //     the row of G
     __shared__ double redd[kGramGroup0 / 32];
     __shared__ int top[kTop];
     __shared__ unsigned long long rkey[kTop];
@@ -633,176 +677,240 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_select_kernel(const SelA
     __shared__ unsigned long long list[kGramList];
     __shared__ int list_n;
     __shared__ unsigned long long gtw[kGramThreads / 32][kTop];
-    const int i = blockIdx.x;
-    if (i >= *a.n_act) {
-        step_done(a);
-        return;
-    }
-    const int slot = a.act[i];
+    __shared__ uint64_t bar_c, bar_g;
+    __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* rs4 = reinterpret_cast<float4*>(r);
-    float4* rg4 = reinterpret_cast<float4*>(a.R32 + static_cast<size_t>(slot) * a.ldN);
-    const int n4 = a.ldN / 4;
-    SlotState s = a.st[slot];
-    BatchIO io;
-    if (threadIdx.x == 0) io = *a.io;
-    for (int k = threadIdx.x; k < n4; k += kGramThreads) cp_async16(rs4 + k, rg4 + k);
-    cp_async_commit();
-    float4* cr4 = reinterpret_cast<float4*>(a.Cg + static_cast<size_t>(slot) * a.ldC);
-    const int nq = a.ldC / 4;
-    for (int q = threadIdx.x * 8; q < nq; q += kGramThreads * 8) prefetch_line_l2(cr4 + q);
-    if (threadIdx.x < kTop) {
-        const unsigned long long k = a.gtop[static_cast<size_t>(slot) * kTop + threadIdx.x];
-        top[threadIdx.x] = k ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(k)) : -1;
+    // the first row's slot is fetched with the row count, not after it (the
+    // grid never exceeds the slot table, so the index is in range)
+    const int slot0 = a.act[blockIdx.x];
+    const int n_act = *a.n_act;
+    if (SM && threadIdx.x == 0) {
+        mbar_init(&bar_c, 1);
+        mbar_init(&bar_g, 1);
+        fence_mbar_init();
     }
-    if (threadIdx.x == 0) list_n = 0;
-    cp_async_wait_all();
+    if (threadIdx.x == 0) abort_flag = 0;
     __syncthreads();
-    // rescore in FP32 (Eq. 9), one candidate per warp
-    if (warp < kTop) {
-        const int m0 = top[warp];
-        unsigned long long key = 0ull;
-        if (m0 >= 0) key = pack_key(dot1_deep<16>(a.psi32 + static_cast<size_t>(m0) * a.ldN, r, a.ldN, lane), m0);
-        if (lane == 0) rkey[warp] = key;
-    }
-    __syncthreads();
-    unsigned long long kbest = 0ull;
-#pragma unroll
-    for (int w = 0; w < kTop; ++w) kbest = umax64(kbest, rkey[w]);
-    if (kbest == 0ull) {   // no candidate: nothing can be selected; the signal leaves
-        if (threadIdx.x == 0) {
-            s.status = MP_ERR_INVALID;
-            a.st[slot] = s;
-            if (a.fin_list) a.fin_list[atomicAdd(a.fin_count, 1)] = slot;
+    for (int i = blockIdx.x, it = 0; i < n_act && !abort_flag; i += gridDim.x, ++it) {
+        const uint32_t ph = static_cast<uint32_t>(it & 1);
+        const int slot = it == 0 ? slot0 : a.act[i];
+        float4* rg4 = reinterpret_cast<float4*>(a.R32 + static_cast<size_t>(slot) * a.ldN);
+        float4* cr4 = reinterpret_cast<float4*>(a.Cg + static_cast<size_t>(slot) * a.ldC);
+        if (SM && threadIdx.x == 0) {
+            mbar_arrive_expect_tx(&bar_c, static_cast<uint32_t>(a.ldC) * 4u);
+            bulk_g2s(cs4, cr4, static_cast<uint32_t>(a.ldC) * 4u, &bar_c);
         }
-        step_done(a);
-        return;
-    }
-    const int m = key_index(kbest);
-    const float c = key_coef(kbest);
-    const float4* gr4 = reinterpret_cast<const float4*>(a.G + static_cast<size_t>(m) * a.ldG);
-    for (int q = threadIdx.x * 8; q < nq; q += kGramThreads * 8) prefetch_line_l2(gr4 + q);
-    float xm = 0.f;
-    if (threadIdx.x == 0) xm = io.X[static_cast<size_t>(slot) * io.ldx + m];
-    // Eq. 11 in FP32
-    const float4* pm = reinterpret_cast<const float4*>(a.psi32 + static_cast<size_t>(m) * a.ldN);
-    for (int k = threadIdx.x; k < n4; k += kGramThreads) {
-        const float4 p = __ldg(pm + k);
-        float4 v = rs4[k];
-        v.x = fmaf(-c, p.x, v.x);
-        v.y = fmaf(-c, p.y, v.y);
-        v.z = fmaf(-c, p.z, v.z);
-        v.w = fmaf(-c, p.w, v.w);
-        rg4[k] = v;
-        rs4[k] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < kGramGroup0) {
-        // ---- energy group: e = sum r^2 in FP64 in the plain kernel's order
-        double acc = 0.0;
-        for (int k = threadIdx.x; k < n4; k += kSumChains) {
-            const float4 v = rs4[k];
-            acc = fma(static_cast<double>(v.x), static_cast<double>(v.x), acc);
-            acc = fma(static_cast<double>(v.y), static_cast<double>(v.y), acc);
-            acc = fma(static_cast<double>(v.z), static_cast<double>(v.z), acc);
-            acc = fma(static_cast<double>(v.w), static_cast<double>(v.w), acc);
+        SlotState s = a.st[slot];
+        BatchIO io;
+        if (threadIdx.x == 0) io = *a.io;
+        for (int k = threadIdx.x; k < n4; k += kGramThreads) cp_async16(rs4 + k, rg4 + k);
+        cp_async_commit();
+        if (!SM)
+            for (int q = threadIdx.x * 8; q < nq; q += kGramThreads * 8) prefetch_line_l2(cr4 + q);
+        if (threadIdx.x < kTop) {
+            const unsigned long long k = a.gtop[static_cast<size_t>(slot) * kTop + threadIdx.x];
+            top[threadIdx.x] = k ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(k)) : -1;
         }
-        acc = warp_sum_f64(acc);
-        if (lane == 0) redd[warp] = acc;
-        named_bar_sync(1, kGramGroup0);
-        if (threadIdx.x == 0) {
-            double e = 0.0;
-#pragma unroll
-            for (int w = 0; w < kGramGroup0 / 32; ++w) e += redd[w];
-            io.X[static_cast<size_t>(slot) * io.ldx + m] = xm + c;   // Eq. 10
-            if (io.tr_atoms && s.t < io.tr_cap) io.tr_atoms[static_cast<size_t>(slot) * io.tr_cap + s.t] = m;
-            if (io.tr_coefs && s.t < io.tr_cap) io.tr_coefs[static_cast<size_t>(slot) * io.tr_cap + s.t] = c;
-            if (io.tr_energy && s.t < io.tr_cap) io.tr_energy[static_cast<size_t>(slot) * io.tr_cap + s.t] = e;
-            const double cc = static_cast<double>(c);
-            s.audit = fmax(s.audit, fabs(e - (s.e - cc * cc)));   // divided by e0 when reported
-            s.e = e;
-            s.t += 1;   // Eq. 12
-            const bool conv = !(e > s.thr2);
-            const bool stop = conv || s.t >= s.T;
-            if (stop) s.stop_reason = conv ? MP_STOP_CONVERGED : MP_STOP_MAX_ITERS;
-            a.st[slot] = s;
-            if (!stop) {
-                const int row = atomicAdd(a.n_next, 1);
-                a.act_next[row] = slot;
-            } else if (a.fin_list) {
-                a.fin_list[atomicAdd(a.fin_count, 1)] = slot;
-            }
+        if (threadIdx.x == 0) list_n = 0;
+        cp_async_wait_all();
+        __syncthreads();
+        // rescore in FP32 (Eq. 9), one candidate per warp
+        if (warp < kTop) {
+            const int m0 = top[warp];
+            unsigned long long key = 0ull;
+            if (m0 >= 0) key = pack_key(dot1_deep<16>(a.psi32 + static_cast<size_t>(m0) * a.ldN, r, a.ldN, lane), m0);
+            if (lane == 0) rkey[warp] = key;
         }
-    } else {
-        // ---- Gram group: c_j -= c G[m][j] and the row's 8 largest |c|
-        constexpr int GT = kGramThreads - kGramGroup0;
-        const int gt = threadIdx.x - kGramGroup0, gw = warp - kGramGroup0 / 32;
-        float mx = 0.f;
-        constexpr int U = 8;
-        for (int q0 = gt; q0 < nq; q0 += U * GT) {
-            float4 g[U], v[U];
+        __syncthreads();
+        unsigned long long kbest = 0ull;
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int q = q0 + u * GT;
-                if (q < nq) {
-                    g[u] = __ldg(gr4 + q);
-                    v[u] = cr4[q];
+        for (int w = 0; w < kTop; ++w) kbest = umax64(kbest, rkey[w]);
+        const int m = kbest ? key_index(kbest) : 0;
+        const float c = kbest ? key_coef(kbest) : 0.f;
+        const float4* gr4 = reinterpret_cast<const float4*>(a.G + static_cast<size_t>(m) * a.ldG);
+        if (kbest && SM && threadIdx.x == 0) {
+            mbar_arrive_expect_tx(&bar_g, static_cast<uint32_t>(a.ldG) * 4u);
+            bulk_g2s(gs4, gr4, static_cast<uint32_t>(a.ldG) * 4u, &bar_g);
+        }
+        if (kbest == 0ull) {   // no candidate: nothing can be selected; the signal leaves
+            if (threadIdx.x == 0) {
+                s.status = MP_ERR_INVALID;
+                a.st[slot] = s;
+                if (a.fin_list) a.fin_list[atomicAdd(a.fin_count, 1)] = slot;
+                if (SM && !mbar_wait_bounded(&bar_c, ph, a.lim)) {
+                    atomicCAS(a.err, 0, static_cast<int>(MP_ERR_TIMEOUT));
+                    abort_flag = 1;
+                    mbar_wait_bounded(&bar_c, ph, a.lim);   // the copy in flight, once more
                 }
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int q = q0 + u * GT;
-                if (q >= nq) break;
-                v[u].x = fmaf(-c, g[u].x, v[u].x);
-                v[u].y = fmaf(-c, g[u].y, v[u].y);
-                v[u].z = fmaf(-c, g[u].z, v[u].z);
-                v[u].w = fmaf(-c, g[u].w, v[u].w);
-                cr4[q] = v[u];
-                // entries past M (the row's padding) never rank
-                const int j0 = 4 * q;
-                if (j0 + 0 < a.M) mx = fmaxf(mx, fabsf(v[u].x));
-                if (j0 + 1 < a.M) mx = fmaxf(mx, fabsf(v[u].y));
-                if (j0 + 2 < a.M) mx = fmaxf(mx, fabsf(v[u].z));
-                if (j0 + 3 < a.M) mx = fmaxf(mx, fabsf(v[u].w));
+            __syncthreads();
+            if (SM && !abort_flag && threadIdx.x == 0) {
+                // keep the G barrier's phase in step with the C barrier's
+                mbar_arrive(&bar_g);
             }
+            __syncthreads();
+            continue;
         }
-        // the warp's 8th largest thread maximum: 8 entries of the warp reach
-        // it, so the row's 8th largest |c| does too; the largest such value
-        // over the group's warps is the threshold
-        const float w8 = warp_kth_largest(mx, kTop);
-        if (lane == 0) wthr[gw] = w8;
-        named_bar_sync(2, GT);
-        float thr = 0.f;
+        if (!SM)
+            for (int q = threadIdx.x * 8; q < nq; q += kGramThreads * 8) prefetch_line_l2(gr4 + q);
+        float xm = 0.f;
+        if (threadIdx.x == 0) xm = io.X[static_cast<size_t>(slot) * io.ldx + m];
+        // Eq. 11 in FP32
+        const float4* pm = reinterpret_cast<const float4*>(a.psi32 + static_cast<size_t>(m) * a.ldN);
+        for (int k = threadIdx.x; k < n4; k += kGramThreads) {
+            const float4 p = __ldg(pm + k);
+            float4 v = rs4[k];
+            v.x = fmaf(-c, p.x, v.x);
+            v.y = fmaf(-c, p.y, v.y);
+            v.z = fmaf(-c, p.z, v.z);
+            v.w = fmaf(-c, p.w, v.w);
+            rg4[k] = v;
+            rs4[k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < kGramGroup0) {
+            // ---- energy group: e = sum r^2 in FP64 in the plain kernel's order
+            double acc = 0.0;
+            for (int k = threadIdx.x; k < n4; k += kSumChains) {
+                const float4 v = rs4[k];
+                acc = fma(static_cast<double>(v.x), static_cast<double>(v.x), acc);
+                acc = fma(static_cast<double>(v.y), static_cast<double>(v.y), acc);
+                acc = fma(static_cast<double>(v.z), static_cast<double>(v.z), acc);
+                acc = fma(static_cast<double>(v.w), static_cast<double>(v.w), acc);
+            }
+            acc = warp_sum_f64(acc);
+            if (lane == 0) redd[warp] = acc;
+            named_bar_sync(1, kGramGroup0);
+            if (threadIdx.x == 0) {
+                double e = 0.0;
 #pragma unroll
-        for (int w = 0; w < GT / 32; ++w) thr = fmaxf(thr, wthr[w]);
-        // entries at or above the threshold (only threads whose maximum
-        // reaches it re-read their entries, which they wrote themselves)
-        bool overflow = false;
-        if (mx >= thr) {
-            for (int q = gt; q < nq; q += GT) {
-                const float4 v = cr4[q];
-                const float e4[4] = {v.x, v.y, v.z, v.w};
+                for (int w = 0; w < kGramGroup0 / 32; ++w) e += redd[w];
+                io.X[static_cast<size_t>(slot) * io.ldx + m] = xm + c;   // Eq. 10
+                if (io.tr_atoms && s.t < io.tr_cap) io.tr_atoms[static_cast<size_t>(slot) * io.tr_cap + s.t] = m;
+                if (io.tr_coefs && s.t < io.tr_cap) io.tr_coefs[static_cast<size_t>(slot) * io.tr_cap + s.t] = c;
+                if (io.tr_energy && s.t < io.tr_cap) io.tr_energy[static_cast<size_t>(slot) * io.tr_cap + s.t] = e;
+                const double cc = static_cast<double>(c);
+                s.audit = fmax(s.audit, fabs(e - (s.e - cc * cc)));   // divided by e0 when reported
+                s.e = e;
+                s.t += 1;   // Eq. 12
+                const bool conv = !(e > s.thr2);
+                const bool stop = conv || s.t >= s.T;
+                if (stop) s.stop_reason = conv ? MP_STOP_CONVERGED : MP_STOP_MAX_ITERS;
+                a.st[slot] = s;
+                if (!stop) {
+                    const int row = atomicAdd(a.n_next, 1);
+                    a.act_next[row] = slot;
+                } else if (a.fin_list) {
+                    a.fin_list[atomicAdd(a.fin_count, 1)] = slot;
+                }
+            }
+        } else {
+            // ---- Gram group: c_j -= c G[m][j] and the row's 8 largest |c|
+            constexpr int GT = kGramThreads - kGramGroup0;
+            const int gt = threadIdx.x - kGramGroup0, gw = warp - kGramGroup0 / 32;
+            bool ok = true;
+            if (SM) {
+                // both rows in shared memory (bounded waits; every thread
+                // of the group sees the same outcome)
+                if (gt == 0) {
+                    const bool okc = mbar_wait_bounded(&bar_c, ph, a.lim);
+                    const bool okg = mbar_wait_bounded(&bar_g, ph, a.lim);
+                    if (!(okc && okg)) {
+                        atomicCAS(a.err, 0, static_cast<int>(MP_ERR_TIMEOUT));
+                        abort_flag = 1;
+                        // let any copy still in flight land before the
+                        // buffers are left (bounded again)
+                        if (!okc) mbar_wait_bounded(&bar_c, ph, a.lim);
+                        if (!okg) mbar_wait_bounded(&bar_g, ph, a.lim);
+                    }
+                }
+                named_bar_sync(2, GT);
+                ok = !abort_flag;
+                if (ok) {
+                    // every thread passes its own wait (the phase is complete)
+                    mbar_try_wait(&bar_c, ph);
+                    mbar_try_wait(&bar_g, ph);
+                }
+            }
+            float mx = 0.f;
+            if (ok) {
+                constexpr int U = SM ? 4 : 8;   // shared memory needs fewer loads in flight
+                for (int q0 = gt; q0 < nq; q0 += U * GT) {
+                    float4 g[U], v[U];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = 4 * q + u;
-                    const float sc = fabsf(e4[u]);
-                    if (j < a.M && sc >= thr) {
-                        const int at = atomicAdd(&list_n, 1);
-                        if (at < kGramList) list[at] = cand_key(__float_as_uint(sc), static_cast<uint32_t>(j), a.M);
+                    for (int u = 0; u < U; ++u) {
+                        const int q = q0 + u * GT;
+                        if (q < nq) {
+                            g[u] = SM ? gs4[q] : __ldg(gr4 + q);
+                            v[u] = SM ? cs4[q] : cr4[q];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int q = q0 + u * GT;
+                        if (q >= nq) break;
+                        v[u].x = fmaf(-c, g[u].x, v[u].x);
+                        v[u].y = fmaf(-c, g[u].y, v[u].y);
+                        v[u].z = fmaf(-c, g[u].z, v[u].z);
+                        v[u].w = fmaf(-c, g[u].w, v[u].w);
+                        cr4[q] = v[u];
+                        if (SM) cs4[q] = v[u];
+                        // entries past M (the row's padding) never rank
+                        const int j0 = 4 * q;
+                        if (j0 + 0 < a.M) mx = fmaxf(mx, fabsf(v[u].x));
+                        if (j0 + 1 < a.M) mx = fmaxf(mx, fabsf(v[u].y));
+                        if (j0 + 2 < a.M) mx = fmaxf(mx, fabsf(v[u].z));
+                        if (j0 + 3 < a.M) mx = fmaxf(mx, fabsf(v[u].w));
                     }
                 }
             }
-        }
-        named_bar_sync(2, GT);
-        const int ln = list_n;
-        overflow = ln > kGramList;
-        unsigned long long lk[kTop];
+            // the warp's 8th largest thread maximum: 8 entries of the warp
+            // reach it, so the row's 8th largest |c| does too; the largest
+            // such value over the group's warps is the threshold
+            const float w8 = warp_kth_largest(mx, kTop);
+            if (lane == 0) wthr[gw] = w8;
+            named_bar_sync(2, GT);
+            float thr = 0.f;
 #pragma unroll
-        for (int k = 0; k < kTop; ++k) lk[k] = 0ull;
-        if (!overflow) {
-            // the kept entries' 8 largest keys: one warp
-            if (gw == 0) {
-                for (int t = lane; t < ln; t += 32) top8_insert(lk, list[t]);
+            for (int w = 0; w < GT / 32; ++w) thr = fmaxf(thr, wthr[w]);
+            // entries at or above the threshold (only threads whose
+            // maximum reaches it look at their entries again)
+            if (ok && mx >= thr) {
+                for (int q = gt; q < nq; q += GT) {
+                    const float4 v = SM ? cs4[q] : cr4[q];
+                    const float e4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = 4 * q + u;
+                        const float sc = fabsf(e4[u]);
+                        if (j < a.M && sc >= thr) {
+                            const int at = atomicAdd(&list_n, 1);
+                            if (at < kGramList) list[at] = cand_key(__float_as_uint(sc), static_cast<uint32_t>(j), a.M);
+                        }
+                    }
+                }
+            }
+            named_bar_sync(2, GT);
+            const int ln = list_n;
+            unsigned long long* out = a.gtop + static_cast<size_t>(slot) * kTop;
+            if (!ok) {
+                // no update (a wait gave up): nothing to rank
+            } else if (ln <= kGramList) {
+                if (gw == 0) list_top8_store(list, ln, out);
+            } else {
+                // more entries tie at the threshold than the list holds: rank
+                // the whole row (every thread its own entries, then the group)
+                unsigned long long lk[kTop];
+#pragma unroll
+                for (int k = 0; k < kTop; ++k) lk[k] = 0ull;
+                float t8 = 0.f;
+                for (int q = gt; q < nq; q += GT) {
+                    const float4 v = SM ? cs4[q] : cr4[q];
+                    top8_offer(lk, t8, v.x, 4 * q + 0, a.M);
+                    top8_offer(lk, t8, v.y, 4 * q + 1, a.M);
+                    top8_offer(lk, t8, v.z, 4 * q + 2, a.M);
+                    top8_offer(lk, t8, v.w, 4 * q + 3, a.M);
+                }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     unsigned long long other[kTop];
@@ -812,47 +920,29 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_select_kernel(const SelA
                 }
                 if (lane == 0)
 #pragma unroll
-                    for (int k = 0; k < kTop; ++k) a.gtop[static_cast<size_t>(slot) * kTop + k] = lk[k];
-            }
-        } else {
-            // more entries tie at the threshold than the list holds: rank
-            // the whole row (every thread its own entries, then the group)
-            float t8 = 0.f;
-            for (int q = gt; q < nq; q += GT) {
-                const float4 v = cr4[q];
-                top8_offer(lk, t8, v.x, 4 * q + 0, a.M);
-                top8_offer(lk, t8, v.y, 4 * q + 1, a.M);
-                top8_offer(lk, t8, v.z, 4 * q + 2, a.M);
-                top8_offer(lk, t8, v.w, 4 * q + 3, a.M);
-            }
+                    for (int k = 0; k < kTop; ++k) gtw[gw][k] = lk[k];
+                named_bar_sync(2, GT);
+                if (gw == 0) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                unsigned long long other[kTop];
+                    for (int k = 0; k < kTop; ++k) lk[k] = lane < GT / 32 ? gtw[lane][k] : 0ull;
 #pragma unroll
-                for (int k = 0; k < kTop; ++k) other[k] = __shfl_xor_sync(0xffffffffu, lk[k], o);
-                merge_top8_u64(lk, other);
-            }
-            if (lane == 0)
+                    for (int o = 1; o < 32; o <<= 1) {
+                        unsigned long long other[kTop];
 #pragma unroll
-                for (int k = 0; k < kTop; ++k) gtw[gw][k] = lk[k];
-            named_bar_sync(2, GT);
-            if (gw == 0) {
+                        for (int k = 0; k < kTop; ++k) other[k] = __shfl_xor_sync(0xffffffffu, lk[k], o);
+                        merge_top8_u64(lk, other);
+                    }
+                    if (lane == 0)
 #pragma unroll
-                for (int k = 0; k < kTop; ++k) lk[k] = lane < GT / 32 ? gtw[lane][k] : 0ull;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    unsigned long long other[kTop];
-#pragma unroll
-                    for (int k = 0; k < kTop; ++k) other[k] = __shfl_xor_sync(0xffffffffu, lk[k], o);
-                    merge_top8_u64(lk, other);
+                        for (int k = 0; k < kTop; ++k) out[k] = lk[k];
                 }
-                if (lane == 0)
-#pragma unroll
-                    for (int k = 0; k < kTop; ++k) a.gtop[static_cast<size_t>(slot) * kTop + k] = lk[k];
             }
         }
+        // the next row reuses the buffers (its bulk copies write where this
+        // row's threads wrote) and the barriers
+        if (SM) fence_proxy_async_smem();
+        __syncthreads();
     }
-    __syncthreads();
     step_done(a);
 }
 
@@ -1308,6 +1398,15 @@ static cudaError_t launch_fixup(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Gram-step kernel's dynamic shared memory: r, and with `rows` the slot's
+// correlation row and a row of G.
+static size_t gram_smem_bytes(const PlanImpl* p, const BatchEngine* e, bool rows) {
+    return sizeof(float) * (static_cast<size_t>(p->ldN) + (rows ? 2 * static_cast<size_t>(e->ldC) : 0));
+}
+static bool gram_rows_in_smem(const PlanImpl* p, const BatchEngine* e) {
+    return gram_smem_bytes(p, e, true) <= 200u * 1024u;
+}
+
 // One step on operand half `half`: GEMM + top-8, then select / rescore /
 // update, which moves the signals that run on into the other half.  In the
 // Gram mode a step is the select kernel alone: its candidates are each
@@ -1365,9 +1464,16 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, cudaStream
     // latency chain of L2 / HBM reads); engines of 512 slots and more: 4
     // warps, two candidates each, so more signals' CTAs fit on an SM at a
     // full batch.  Gram mode: the Gram-step kernel (16 warps).
+    sa.err = e->err;
+    sa.lim = static_cast<unsigned long long>(p->watchdog_ns);
     const size_t sm = p->ldN * sizeof(float);
-    if (gram) gram_select_kernel<<<e->cap, kGramThreads, sm, st>>>(sa);
-    else if (e->cap < kWideSelectCap) select_update_kernel<2 * kSumChains><<<e->cap, 2 * kSumChains, sm, st>>>(sa);
+    if (gram) {
+        const int ctas = std::max(1, std::min(e->cap, p->sm_count > 0 ? p->sm_count : e->cap));
+        if (gram_rows_in_smem(p, e))
+            gram_select_kernel<true><<<ctas, kGramThreads, gram_smem_bytes(p, e, true), st>>>(sa);
+        else
+            gram_select_kernel<false><<<ctas, kGramThreads, gram_smem_bytes(p, e, false), st>>>(sa);
+    } else if (e->cap < kWideSelectCap) select_update_kernel<2 * kSumChains><<<e->cap, 2 * kSumChains, sm, st>>>(sa);
     else select_update_kernel<kSumChains><<<e->cap, kSumChains, sm, st>>>(sa);
     ++*kernels;
     return cudaGetLastError();
@@ -1417,7 +1523,13 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<kSumChains>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        MP_CUDA_TRY(cudaFuncSetAttribute(gram_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+
+    }
+    if (e->gram_R > 0) {
+        MP_CUDA_TRY(cudaFuncSetAttribute(gram_select_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         gram_smem_bytes(p, e, true)));
+        MP_CUDA_TRY(cudaFuncSetAttribute(gram_select_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         gram_smem_bytes(p, e, false)));
     }
     if (e->gram_R > 0 && (e->gram_R % steps || !p->gram))
         return fail(MP_ERR_INVALID, "batched step graph: the Gram period must be a multiple of the steps per graph");

@@ -81,6 +81,9 @@ MP_DEV void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* 
 MP_DEV void prefetch_l2(const void* src, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
+// Orders this thread's generic-proxy shared-memory accesses before later
+// async-proxy operations (bulk copies) on the same shared memory.
+MP_DEV void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 // One 128-byte line toward L2 (fire and forget).
 MP_DEV void prefetch_line_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 MP_DEV uint64_t policy_evict_first() {
