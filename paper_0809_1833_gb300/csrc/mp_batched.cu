@@ -983,63 +983,79 @@ MP_DEV bool corr_row_wanted(const CorrRowsArgs& a, int slot) {
 }
 
 __global__ void __launch_bounds__(kCorrThreads) corr_rows_kernel(const CorrRowsArgs a) {
-    extern __shared__ float4 rsh[];           // kCorrRows rows of ldN floats
+    extern __shared__ float4 rsh[];           // a.rpc rows of ldN floats
     __shared__ int slots[kCorrRows];
     __shared__ int want[kCorrRows];
     const int n = a.n_ptr ? *a.n_ptr : a.n;
-    const int g0 = blockIdx.y * a.rpc;
-    if (g0 >= n) return;
-    const int nr = min(a.rpc, n - g0);
-    if (threadIdx.x < kCorrRows) {
-        int sl = -1, w = 0;
-        if (static_cast<int>(threadIdx.x) < nr) {
-            sl = a.rows ? a.rows[g0 + threadIdx.x] : g0 + static_cast<int>(threadIdx.x);
-            w = corr_row_wanted(a, sl) ? 1 : 0;
-        }
-        slots[threadIdx.x] = sl;
-        want[threadIdx.x] = w;
-    }
-    __syncthreads();
-    int any = 0;
-#pragma unroll
-    for (int j = 0; j < kCorrRows; ++j) any |= want[j];
-    if (!any) return;
     const int n4 = a.ldN / 4;
-    for (int j = 0; j < nr; ++j) {
-        const float4* src = reinterpret_cast<const float4*>(a.R32 + static_cast<size_t>(slots[j]) * a.ldN);
-        for (int k = threadIdx.x; k < n4; k += kCorrThreads) rsh[j * n4 + k] = src[k];
-    }
-    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int W = kCorrThreads / 32;
     const int m_end = min(a.M, (blockIdx.x + 1) * kCorrAtoms);
-    for (int m = blockIdx.x * kCorrAtoms + warp; m < m_end; m += kCorrThreads / 32) {
-        const float4* p = reinterpret_cast<const float4*>(a.psi32 + static_cast<size_t>(m) * a.ldN);
-        float acc[kCorrRows];
+    // the CTA's block of atoms against every group of listed rows with a
+    // row to compute (groups without one cost a look at their flags)
+    for (int g0 = 0; g0 < n; g0 += a.rpc) {
+        const int nr = min(a.rpc, n - g0);
+        __syncthreads();   // the previous group's rows are no longer read
+        if (threadIdx.x < kCorrRows) {
+            int sl = -1, w = 0;
+            if (static_cast<int>(threadIdx.x) < nr) {
+                sl = a.rows ? a.rows[g0 + threadIdx.x] : g0 + static_cast<int>(threadIdx.x);
+                w = corr_row_wanted(a, sl) ? 1 : 0;
+            }
+            slots[threadIdx.x] = sl;
+            want[threadIdx.x] = w;
+        }
+        __syncthreads();
+        int any = 0;
 #pragma unroll
-        for (int j = 0; j < kCorrRows; ++j) acc[j] = 0.f;
-        constexpr int U = 8;
-        for (int k0 = lane; k0 < n4; k0 += 32 * U) {
-            float4 v[U];
+        for (int j = 0; j < kCorrRows; ++j) any |= want[j];
+        if (!any) continue;
+        for (int j = 0; j < nr; ++j) {
+            const float4* src = reinterpret_cast<const float4*>(a.R32 + static_cast<size_t>(slots[j]) * a.ldN);
+            for (int k = threadIdx.x; k < n4; k += kCorrThreads) rsh[j * n4 + k] = src[k];
+        }
+        __syncthreads();
+        // two atoms per warp at a time, 8 float4 loads of each in flight
+        for (int m0 = blockIdx.x * kCorrAtoms + warp; m0 < m_end; m0 += 2 * W) {
+            const int m1 = m0 + W;
+            const bool two = m1 < m_end;
+            const float4* p0 = reinterpret_cast<const float4*>(a.psi32 + static_cast<size_t>(m0) * a.ldN);
+            const float4* p1 = reinterpret_cast<const float4*>(a.psi32 + static_cast<size_t>(two ? m1 : m0) * a.ldN);
+            float acc0[kCorrRows], acc1[kCorrRows];
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (k0 + 32 * u < n4) v[u] = __ldg(p + k0 + 32 * u);
+            for (int j = 0; j < kCorrRows; ++j) acc0[j] = acc1[j] = 0.f;
+            constexpr int U = 8;
+            for (int k0 = lane; k0 < n4; k0 += 32 * U) {
+                float4 v0[U], v1[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int k = k0 + 32 * u;
-                if (k >= n4) break;
+                for (int u = 0; u < U; ++u)
+                    if (k0 + 32 * u < n4) {
+                        v0[u] = __ldg(p0 + k0 + 32 * u);
+                        v1[u] = __ldg(p1 + k0 + 32 * u);
+                    }
 #pragma unroll
-                for (int j = 0; j < kCorrRows; ++j) {
-                    if (j >= nr) break;
-                    const float4 q = rsh[j * n4 + k];
-                    acc[j] = fmaf(v[u].x, q.x, fmaf(v[u].y, q.y, fmaf(v[u].z, q.z, fmaf(v[u].w, q.w, acc[j]))));
+                for (int u = 0; u < U; ++u) {
+                    const int k = k0 + 32 * u;
+                    if (k >= n4) break;
+#pragma unroll
+                    for (int j = 0; j < kCorrRows; ++j) {
+                        if (j >= nr) break;
+                        const float4 q = rsh[j * n4 + k];
+                        acc0[j] = fmaf(v0[u].x, q.x, fmaf(v0[u].y, q.y, fmaf(v0[u].z, q.z, fmaf(v0[u].w, q.w, acc0[j]))));
+                        acc1[j] = fmaf(v1[u].x, q.x, fmaf(v1[u].y, q.y, fmaf(v1[u].z, q.z, fmaf(v1[u].w, q.w, acc1[j]))));
+                    }
                 }
             }
-        }
 #pragma unroll
-        for (int j = 0; j < kCorrRows; ++j) {
-            if (j >= nr) break;
-            const float c = warp_sum_f32(acc[j]);
-            if (lane == 0 && want[j]) a.Cg[static_cast<size_t>(slots[j]) * a.ldC + m] = c;
+            for (int j = 0; j < kCorrRows; ++j) {
+                if (j >= nr) break;
+                const float c0 = warp_sum_f32(acc0[j]);
+                const float c1 = warp_sum_f32(acc1[j]);
+                if (lane == 0 && want[j]) {
+                    a.Cg[static_cast<size_t>(slots[j]) * a.ldC + m0] = c0;
+                    if (two) a.Cg[static_cast<size_t>(slots[j]) * a.ldC + m1] = c1;
+                }
+            }
         }
     }
 }
@@ -1049,24 +1065,25 @@ __global__ void __launch_bounds__(kCorrThreads) corr_rows_kernel(const CorrRowsA
 __global__ void __launch_bounds__(kCorrThreads) gram_scan_kernel(const CorrRowsArgs a, unsigned long long* gtop) {
     __shared__ unsigned long long w[kCorrThreads / 32][kTop];
     const int n = a.n_ptr ? *a.n_ptr : a.n;
-    const int k = blockIdx.x;
-    if (k >= n) return;
-    const int slot = a.rows ? a.rows[k] : k;
-    if (!corr_row_wanted(a, slot)) return;
-    const float4* cr4 = reinterpret_cast<const float4*>(a.Cg + static_cast<size_t>(slot) * a.ldC);
-    unsigned long long lk[kTop];
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int slot = a.rows ? a.rows[k] : k;
+        if (!corr_row_wanted(a, slot)) continue;   // the same for every thread of the CTA
+        const float4* cr4 = reinterpret_cast<const float4*>(a.Cg + static_cast<size_t>(slot) * a.ldC);
+        unsigned long long lk[kTop];
 #pragma unroll
-    for (int j = 0; j < kTop; ++j) lk[j] = 0ull;
-    float thr = 0.f;
-    for (int q = threadIdx.x; q < a.ldC / 4; q += kCorrThreads) {
-        const float4 v = cr4[q];
-        const int j0 = 4 * q;
-        top8_offer(lk, thr, v.x, j0 + 0, a.M);
-        top8_offer(lk, thr, v.y, j0 + 1, a.M);
-        top8_offer(lk, thr, v.z, j0 + 2, a.M);
-        top8_offer(lk, thr, v.w, j0 + 3, a.M);
+        for (int j = 0; j < kTop; ++j) lk[j] = 0ull;
+        float thr = 0.f;
+        for (int q = threadIdx.x; q < a.ldC / 4; q += kCorrThreads) {
+            const float4 v = cr4[q];
+            const int j0 = 4 * q;
+            top8_offer(lk, thr, v.x, j0 + 0, a.M);
+            top8_offer(lk, thr, v.y, j0 + 1, a.M);
+            top8_offer(lk, thr, v.z, j0 + 2, a.M);
+            top8_offer(lk, thr, v.w, j0 + 3, a.M);
+        }
+        block_top8_store<kCorrThreads>(lk, w, gtop + static_cast<size_t>(slot) * kTop);
+        __syncthreads();   // w is reused by the next row
     }
-    block_top8_store<kCorrThreads>(lk, w, gtop + static_cast<size_t>(slot) * kTop);
 }
 
 // ------------------------------------------------------------------ fixup (one CTA)
@@ -1500,9 +1517,12 @@ static cudaError_t launch_gram_refresh(PlanImpl* p, BatchEngine* e, const int* r
     // a host-known row count (admission) stages no more rows than listed:
     // less shared memory per CTA, more CTAs per SM, more loads in flight
     a.rpc = n_ptr ? corr_rows_per_cta(p) : std::min(corr_rows_per_cta(p), n_max);
-    const dim3 grid((p->M + kCorrAtoms - 1) / kCorrAtoms, (n_max + a.rpc - 1) / a.rpc);
-    corr_rows_kernel<<<grid, kCorrThreads, static_cast<size_t>(a.rpc) * p->ldN * sizeof(float), st>>>(a);
-    gram_scan_kernel<<<n_max, kCorrThreads, 0, st>>>(a, e->gtop);
+    // one CTA per block of atoms (each runs over the row groups); the scan
+    // at most two CTAs per SM over the rows
+    const int sms = p->sm_count > 0 ? p->sm_count : 132;
+    corr_rows_kernel<<<(p->M + kCorrAtoms - 1) / kCorrAtoms, kCorrThreads,
+                       static_cast<size_t>(a.rpc) * p->ldN * sizeof(float), st>>>(a);
+    gram_scan_kernel<<<std::min(n_max, 2 * sms), kCorrThreads, 0, st>>>(a, e->gtop);
     *kernels += 2;
     return cudaGetLastError();
 }
