@@ -176,7 +176,7 @@ typedef enum {
                                /* 128-row MMAs sharing each staged atom slice;       */
                                /* taken while the batch has more 128-row tiles than  */
                                /* the GPU has SMs, 128 after); 0 = auto              */
-    MP_OPT_BATCH_GRAM = 14     /* batched and served decodes (BF16 plans) with       */
+    MP_OPT_BATCH_GRAM = 14,    /* batched and served decodes (BF16 plans) with       */
                                /* Gram-updated correlations; the value is the        */
                                /* refresh period R, a multiple of 16 (0 = off, the   */
                                /* default).  Not in the paper: each signal keeps its */
@@ -190,6 +190,15 @@ typedef enum {
                                /* of G per signal and no GEMM runs.  Whenever the    */
                                /* FP32 argmax is among the 8 candidates the result   */
                                /* equals the plain FP32 decode's bit for bit.        */
+    MP_OPT_BATCH_PAIR = 15     /* batched GEMM on two-SM tiles: a cluster of two     */
+                               /* CTAs takes 256 signals x TILE_N atoms with M = 256 */
+                               /* MMAs (tcgen05 cta_group::2), each SM holding a     */
+                               /* 128 x TILE_N accumulator twice so the top-8 of one */
+                               /* tile runs under the MMAs of the next.  0 = the     */
+                               /* autotuner decides (default), 1 = off, 2 = on; with */
+                               /* it on TILE_N may be 128..256 in steps of 32.  The  */
+                               /* candidates (and so the results) do not depend on   */
+                               /* the tile shape.                                    */
 } mp_option;
 
 /* Read-only plan properties for mp_plan_query. */
@@ -215,7 +224,8 @@ typedef enum {
     MP_Q_PLAIN64_PIECES = 18,  /* FP64 streaming with the 4 warps sharing every      */
                                /* stage: ring stages per atom (an atom streams as    */
                                /* that many pieces); 0 when warps own whole atoms    */
-    MP_Q_BATCH_GRAM = 19       /* Gram period of the current batch state (0: off)    */
+    MP_Q_BATCH_GRAM = 19,      /* Gram period of the current batch state (0: off)    */
+    MP_Q_BATCH_PAIR = 20       /* 1 if the current batch state uses two-SM tiles     */
 } mp_query;
 
 /* ------------------------------------------------------------------ */
@@ -372,6 +382,10 @@ MPGB_API mp_status mp_recover_batched(mp_plan_t plan, int prec, const float* Y, 
  * MP_OPT_BATCH_TILE_M, when set, override the result.  Synchronises the
  * legacy default stream.  tile_n, tile_m: may be NULL. */
 MPGB_API mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* tile_m);
+/* The same, also timing two-SM tiles (MP_OPT_BATCH_PAIR) for B > 128 unless
+ * that option is 1; *pair (may be NULL) receives 1 if the chosen shape is a
+ * two-SM tile (tile_m is then 256). */
+MPGB_API mp_status mp_plan_autotune_shape(mp_plan_t plan, int prec, int B, int* tile_n, int* tile_m, int* pair);
 
 /* Diagnostic: the tensor-core correlations of the batched path, written out
  * in full.  R (device, B x N floats) is quantised as the batched step does
@@ -393,6 +407,10 @@ MPGB_API mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* 
  * (precision not built), MP_ERR_CUDA. */
 MPGB_API mp_status mp_debug_time_gemm(mp_plan_t plan, int prec, int B, int tile_m, int tile_n, int reps,
                                       double* us);
+/* The same with pair = 1 for a two-SM tile (tile_m 256, tile_n 128..256 in
+ * steps of 32); pair = 0 is mp_debug_time_gemm. */
+MPGB_API mp_status mp_debug_time_gemm_pair(mp_plan_t plan, int prec, int B, int tile_m, int tile_n, int pair,
+                                           int reps, double* us);
 
 /* ------------------------------------------------------------------ */
 /* One decode with the atoms split across ranks (one GPU each)         */

@@ -43,9 +43,11 @@ MP_OPT_PLAIN_GRAM = 11
 MP_OPT_PLAIN_L2_KEEP_BYTES = 12
 MP_OPT_BATCH_TILE_M = 13
 MP_OPT_BATCH_GRAM = 14
+MP_OPT_BATCH_PAIR = 15
 MP_Q_BATCH_TILE_N = 10
 MP_Q_BATCH_TILE_M = 17
 MP_Q_BATCH_GRAM = 19
+MP_Q_BATCH_PAIR = 20
 
 MP_Q_PLAIN_MODE = 1
 MP_Q_PLAIN_CTAS = 2
@@ -138,7 +140,9 @@ SIGNATURES = {
                                 ctypes.POINTER(mp_trace), ctypes.POINTER(mp_result), _P]),
     "mp_debug_correlations": (_I, [_P, _I, _P, _I, _P, _P]),
     "mp_debug_time_gemm": (_I, [_P, _I, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_double)]),
+    "mp_debug_time_gemm_pair": (_I, [_P, _I, _I, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_double)]),
     "mp_plan_autotune": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "mp_plan_autotune_shape": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "mp_recover_noalloc": (_I, [_P, _I, _I, _I, _P, _P, ctypes.POINTER(mp_stop), ctypes.POINTER(mp_trace),
                                ctypes.POINTER(mp_result), _P]),
     "mp_shard_record_bytes": (ctypes.c_size_t, [_P]),
@@ -321,6 +325,15 @@ def mp_plan_autotune(plan, prec, B):
     return tn.value, tm.value
 
 
+def mp_plan_autotune_shape(plan, prec, B):
+    """Returns (atoms per tile, signals per tile, two-SM tile 0/1) the
+    autotuner picked, two-SM tiles included."""
+    tn, tm, pr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib().mp_plan_autotune_shape(plan, int(prec), int(B), ctypes.byref(tn), ctypes.byref(tm), ctypes.byref(pr)),
+          "mp_plan_autotune_shape")
+    return tn.value, tm.value, pr.value
+
+
 def mp_recover_noalloc(psi_ptr, N, M, ld, y_ptr, x_ptr, stop, result, stream=None, trace=None):
     """Allocation-free decode (include/mpgb_noalloc.h): ``stop`` is an
     mp_stop, ``result`` an mp_result filled in place, ``trace`` an optional
@@ -340,11 +353,12 @@ def mp_debug_correlations(plan, prec, R_ptr, B, C_ptr, stream=None):
 
 def mp_debug_time_gemm(plan, prec, B, shape=(0, 0), reps=20):
     """Microseconds per launch of the batched correlation GEMM on B
-    synthetic rows; shape = (signals per tile, atoms per tile), (0, 0) =
-    the shape a batch of B would use."""
+    synthetic rows; shape = (signals per tile, atoms per tile[, two-SM tile
+    0/1]), (0, 0) = the shape a batch of B would use."""
     us = ctypes.c_double()
-    check(lib().mp_debug_time_gemm(plan, int(prec), int(B), int(shape[0]), int(shape[1]), int(reps),
-                                   ctypes.byref(us)), "mp_debug_time_gemm")
+    pair = int(shape[2]) if len(shape) > 2 else 0
+    check(lib().mp_debug_time_gemm_pair(plan, int(prec), int(B), int(shape[0]), int(shape[1]), pair, int(reps),
+                                        ctypes.byref(us)), "mp_debug_time_gemm")
     return us.value
 
 

@@ -32,7 +32,7 @@ constexpr int kGemmThreads = 32 * (2 + 4 * kEpiGroups);   // warp 0 TMA, warp 1 
 // Arguments of the correlation GEMM.
 struct CorrArgs {
     const int* n_act;       // active rows this step (rows 0..n_act-1 of the A operand)
-    int TN;                 // atoms per tile (128 or 256)
+    int TN;                 // atoms per tile (128 or 256; two-SM tiles: 128..256, step 32)
     int RM;                 // 128-row blocks per tile (1 or 2)
     int n_at;               // atom tiles
     int M;
@@ -60,6 +60,15 @@ int corr_max_ctas();
 // any step of this launch can see (it sizes the grid).
 cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmA16, const CUtensorMap& tmB,
                              const CUtensorMap& tmBh, const CorrArgs& a, int max_rows, cudaStream_t st);
+// The same GEMM on two-SM tiles (clusters of two CTAs, tcgen05 cta_group::2):
+// 256 signal rows x a.TN atoms per cluster, a.TN a multiple of 32 in
+// [128, 256], a.RM = 2, a.stages = corr_stages(128, a.TN / 2), a.half_ok = 0;
+// tmBp's box is a.TN / 2 atom rows.
+int pair_smem_bytes(int TN);
+cudaError_t pair_prepare();
+int pair_max_clusters(int TN, bool fp8);
+cudaError_t launch_corr_pair(const CUtensorMap& tmA, const CUtensorMap& tmA16, const CUtensorMap& tmBp,
+                             const CorrArgs& a, int max_rows, cudaStream_t st);
 
 // ------------------------------------------------------------------ batch engine
 // Per-signal state of a slot.
@@ -98,6 +107,7 @@ struct BatchEngine {
     int prec = -1;
     int TM = 128;           // signal rows per GEMM tile
     int TN = 0;
+    int pair = 0;           // two-SM tiles (TM = 256 over a cluster of two CTAs)
     int n_at = 0;
     int ldq = 0;            // operand row: elements (BF16) or bytes (FP8)
     float* R32 = nullptr;
@@ -124,6 +134,7 @@ struct BatchEngine {
     int* h_err = nullptr;
     CUtensorMap tmA, tmA1, tmB, tmBh;   // operand half 0, half 1, atoms (TN-row and TN/2-row boxes)
     CUtensorMap tmA16, tmA1_16;         // operand halves with 16-row boxes
+    CUtensorMap tmBp;                   // two-SM tiles: atoms in TN/2-row boxes
     // Gram mode (gram_R > 0): each slot keeps its correlations Psi^T r in
     // FP32 (Cg, M of ldC floats), computed directly at admission and every
     // gram_R of its own steps, and updated from one row of G = Psi^T Psi in

@@ -1284,19 +1284,25 @@ mp_status batch_shape(PlanImpl* p, int prec, int B, const float* R, cudaStream_t
     GemmShape g;
     g.tn = 256;
     g.tm = rt >= 2 ? 256 : 128;
-    if (p->batch_autotune && !p->batch_tile_n && !p->batch_tile_m) {
+    g.pair = p->batch_pair == 2 ? 1 : 0;
+    if (g.pair) g.tm = 256;
+    if (p->batch_autotune && !p->batch_tile_n && !p->batch_tile_m && p->batch_pair == 0) {
         mp_status s = autotune(p, prec, B, R, st, &g);
         if (s != MP_OK) return s;
     }
     if (p->batch_tile_n) g.tn = p->batch_tile_n;
-    if (p->batch_tile_m) g.tm = p->batch_tile_m;
+    if (p->batch_tile_m && !g.pair) g.tm = p->batch_tile_m;
+    if (!g.pair && g.tn != 128 && g.tn != 256)
+        return fail(MP_ERR_INVALID, "batched GEMM: single-CTA tiles take 128 or 256 atoms");
     *shape = g;
     return MP_OK;
 }
 
 static mp_status engine_prepare(PlanImpl* p, int prec, int cap, const GemmShape& g, int gram_R = 0) {
     BatchEngine* e = p->batch;
-    if (e && e->prec == prec && e->cap >= cap && e->TM == g.tm && e->TN == g.tn && e->gram_R == gram_R) return MP_OK;
+    if (e && e->prec == prec && e->cap >= cap && e->TM == g.tm && e->TN == g.tn && e->pair == g.pair &&
+        e->gram_R == gram_R)
+        return MP_OK;
     if (!e) e = p->batch = new BatchEngine();
     return engine_alloc(e, p, prec, std::max(cap, e->cap), g, gram_R);
 }
@@ -1306,6 +1312,9 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     if (gram_R > 0 && (prec != MP_PREC_BF16 || !p->gram))
         return fail(MP_ERR_UNSUPPORTED, "batched Gram mode: BF16 plans only, after the plan's Gram matrix is built");
     const int TN = g.tn;
+    if (g.pair ? (g.tm != 256 || TN < 128 || TN > 256 || TN % 32) : ((g.tm != 128 && g.tm != 256) || (TN != 128 && TN != 256)))
+        return fail(MP_ERR_INVALID, "batched GEMM: unsupported tile shape");
+    e->pair = g.pair;
     e->gram_R = gram_R;
     e->cap = newcap;
     e->cap_pad = (newcap + kBM - 1) / kBM * kBM;
@@ -1333,7 +1342,7 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     A(&e->surv, sizeof(int) * C);
     // room for the lists of half-width tiles (taken by the GEMM when few row
     // blocks are active)
-    const bool half_ok = TN == 256;
+    const bool half_ok = TN == 256 && !g.pair;
     const size_t n_at_max = half_ok ? (p->M + TN / 2 - 1) / (TN / 2) : e->n_at;
     A(&e->cand, sizeof(uint2) * C * n_at_max * kTop);
     A(&e->eps2, sizeof(double) * C);
@@ -1368,6 +1377,7 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     if (s == MP_OK) s = make_map(&e->tmA1_16, static_cast<char*>(e->Rq) + qbytes, fp8, e->cap_pad, e->ldq, 16);
     if (s == MP_OK) s = make_map(&e->tmB, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, TN);
     if (s == MP_OK) s = make_map(&e->tmBh, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, half_ok ? TN / 2 : TN);
+    if (s == MP_OK && g.pair) s = make_map(&e->tmBp, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, TN / 2);
     if (s != MP_OK) {
         engine_free(e);
         return s;
@@ -1384,20 +1394,30 @@ static CorrArgs corr_args(PlanImpl* p, BatchEngine* e) {
     ca.RM = e->TM / kBM;
     // two accumulator buffers (the epilogue of one tile overlaps the MMAs of
     // the next) when they fit in TMEM's 512 columns, else one
-    const int nbuf = (ca.RM == 1 || 2 * ca.RM * e->TN <= 512) ? 2 : 1;
+    const int nbuf = (ca.RM == 1 || 2 * ca.RM * e->TN <= 512 || e->pair) ? 2 : 1;
     ca.n_at = e->n_at;
-    ca.half_ok = e->TN == 256 ? 1 : 0;
+    ca.half_ok = e->TN == 256 && !e->pair ? 1 : 0;
     ca.M = p->M;
     ca.nk = (fp8 ? p->ldK8 : p->ldK16 * 2) / kRowBytes;
     ca.fp8 = fp8 ? 1 : 0;
-    const int cols = nbuf * ca.RM * e->TN;   // allocations are powers of two >= 32
+    // allocations are powers of two >= 32; a two-SM tile keeps 128 rows x TN
+    // columns per SM, two buffers
+    const int cols = e->pair ? 2 * e->TN : nbuf * ca.RM * e->TN;
     ca.tmem_cols = cols > 256 ? 512 : (cols > 128 ? 256 : 128);
-    ca.stages = corr_stages(e->TM, e->TN);
+    ca.stages = e->pair ? corr_stages(kBM, e->TN / 2) : corr_stages(e->TM, e->TN);
     ca.colscale = p->scale8;
     ca.cand = e->cand;
     ca.watchdog_ns = static_cast<unsigned long long>(p->watchdog_ns);
     ca.err = e->err;
     return ca;
+}
+
+// The step's GEMM on operand half `half` (single-CTA or two-SM tiles).
+static cudaError_t launch_gemm(const BatchEngine* e, const CorrArgs& ca, int half, int max_rows, cudaStream_t st) {
+    const CUtensorMap& tA = half ? e->tmA1 : e->tmA;
+    const CUtensorMap& tA16 = half ? e->tmA1_16 : e->tmA16;
+    if (e->pair) return launch_corr_pair(tA, tA16, e->tmBp, ca, max_rows, st);
+    return launch_corr_top8(tA, tA16, e->tmB, e->tmBh, ca, max_rows, st);
 }
 
 static cudaError_t launch_fixup(PlanImpl* p, BatchEngine* e, cudaStream_t st) {
@@ -1441,8 +1461,7 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, cudaStream
         ca.n_act = cnt[half];
         ca.zero_next = cnt[1 - half];
         ca.n_at_out = e->counters + 4;
-        r = launch_corr_top8(half ? e->tmA1 : e->tmA, half ? e->tmA1_16 : e->tmA16, e->tmB, e->tmBh, ca, e->cap_pad,
-                             st);
+        r = launch_gemm(e, ca, half, e->cap_pad, st);
         ++*kernels;
     }
     if (r != cudaSuccess) return r;
@@ -1537,6 +1556,7 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
     }
     if (!e->cap_stream) MP_CUDA_TRY(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
     MP_CUDA_TRY(corr_prepare());
+    MP_CUDA_TRY(pair_prepare());
     if (p->ldN * 4 > 48 * 1024) {
         const int b = p->ldN * 4;
         MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains>,
@@ -1785,6 +1805,7 @@ mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B,
     if (s != MP_OK) return s;
     BatchEngine* e = p->batch;
     MP_CUDA_TRY(corr_prepare());
+    MP_CUDA_TRY(pair_prepare());
     for (int b = 0; b < B; ++b) {
         e->h_eps2[b] = 0.0;
         e->h_T[b] = 1;
@@ -1806,7 +1827,7 @@ mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* R, int B,
     CorrArgs ca = corr_args(p, e);
     ca.dump = C;
     ca.rscale = e->rscale;
-    MP_CUDA_TRY(launch_corr_top8(e->tmA, e->tmA16, e->tmB, e->tmBh, ca, B, st));
+    MP_CUDA_TRY(launch_gemm(e, ca, 0, B, st));
     p->launches += 2;
     MP_CUDA_TRY(cudaMemcpyAsync(e->h_err, e->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1846,7 +1867,7 @@ static double time_gemm(PlanImpl* p, int prec, int B, const GemmShape& g, const 
                         int reps = 5) {
     BatchEngine e;
     double us = -1.0;
-    if (engine_alloc(&e, p, prec, B, g) == MP_OK && corr_prepare() == cudaSuccess) {
+    if (engine_alloc(&e, p, prec, B, g) == MP_OK && corr_prepare() == cudaSuccess && pair_prepare() == cudaSuccess) {
         for (int b = 0; b < B; ++b) {
             e.h_eps2[b] = 0.0;
             e.h_T[b] = 1;
@@ -1867,9 +1888,9 @@ static double time_gemm(PlanImpl* p, int prec, int B, const GemmShape& g, const 
         if (r == cudaSuccess) r = cudaEventCreate(&e0);
         if (r == cudaSuccess) r = cudaEventCreate(&e1);
         const CorrArgs ca = corr_args(p, &e);
-        for (int it = 0; it < 2 && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmA16, e.tmB, e.tmBh, ca, B, st);
+        for (int it = 0; it < 2 && r == cudaSuccess; ++it) r = launch_gemm(&e, ca, 0, B, st);
         if (r == cudaSuccess) r = cudaEventRecord(e0, st);
-        for (int it = 0; it < reps && r == cudaSuccess; ++it) r = launch_corr_top8(e.tmA, e.tmA16, e.tmB, e.tmBh, ca, B, st);
+        for (int it = 0; it < reps && r == cudaSuccess; ++it) r = launch_gemm(&e, ca, 0, B, st);
         if (r == cudaSuccess) r = cudaEventRecord(e1, st);
         if (r == cudaSuccess) r = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -1901,19 +1922,32 @@ mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_
     double best = -1.0;
     GemmShape best_g;
     const int rt = (B + kBM - 1) / kBM;
+    auto consider = [&](const GemmShape& g) {
+        const double us = time_gemm(p, prec, B, g, R_dev ? R_dev : R, st);
+        if (us > 0.0 && (best < 0.0 || us < best)) {
+            best = us;
+            best_g = g;
+        }
+    };
     for (int tm : {128, 256}) {
         if (tm == 256 && rt < 2) continue;      // one row block: the same work as 128
         for (int tn : {256, 128}) {
             GemmShape g;
             g.tm = tm;
             g.tn = tn;
-            const double us = time_gemm(p, prec, B, g, R_dev ? R_dev : R, st);
-            if (us > 0.0 && (best < 0.0 || us < best)) {
-                best = us;
-                best_g = g;
-            }
+            consider(g);
         }
     }
+    // two-SM tiles, unless switched off: widths that spread the tiles over
+    // the clusters in whole rounds differently
+    if (rt >= 2 && p->batch_pair != 1)
+        for (int tn : {256, 224, 192}) {
+            GemmShape g;
+            g.tm = 256;
+            g.tn = tn;
+            g.pair = 1;
+            consider(g);
+        }
     if (R) cudaFreeAsync(R, st);
     if (best < 0.0) return fail(MP_ERR_CUDA, "autotune: no tile shape could be timed");
     cudaStreamSynchronize(st);
@@ -1926,7 +1960,7 @@ mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_
 
 extern "C" {
 
-mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* tile_m) {
+mp_status mp_plan_autotune_shape(mp_plan_t plan, int prec, int B, int* tile_n, int* tile_m, int* pair) {
     clear_error();
     if (!plan || B < 1) return fail(MP_ERR_INVALID, "mp_plan_autotune: bad argument");
     PlanImpl* p = &plan->impl;
@@ -1934,16 +1968,28 @@ mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* ti
         return fail(MP_ERR_INVALID, "mp_plan_autotune: precision must be BF16 or FP8");
     if (!(p->prec_mask & (1u << prec)))
         return fail(MP_ERR_UNSUPPORTED, "mp_plan_autotune: the plan holds no copy for this precision");
+    MP_CUDA_TRY(corr_prepare());
+    MP_CUDA_TRY(pair_prepare());
     GemmShape g;
     mp_status s = autotune(p, prec, B, nullptr, nullptr, &g);
     if (s != MP_OK) return s;
     if (tile_n) *tile_n = g.tn;
     if (tile_m) *tile_m = g.tm;
+    if (pair) *pair = g.pair;
     return MP_OK;
+}
+
+mp_status mp_plan_autotune(mp_plan_t plan, int prec, int B, int* tile_n, int* tile_m) {
+    return mp_plan_autotune_shape(plan, prec, B, tile_n, tile_m, nullptr);
 }
 
 mp_status mp_debug_time_gemm(mp_plan_t plan, int prec, int B, int tile_m, int tile_n, int reps,
                              double* us) {
+    return mp_debug_time_gemm_pair(plan, prec, B, tile_m, tile_n, 0, reps, us);
+}
+
+mp_status mp_debug_time_gemm_pair(mp_plan_t plan, int prec, int B, int tile_m, int tile_n, int pair, int reps,
+                                  double* us) {
     clear_error();
     if (!plan || B < 1 || reps < 1 || !us) return fail(MP_ERR_INVALID, "mp_debug_time_gemm: bad argument");
     PlanImpl* p = &plan->impl;
@@ -1952,11 +1998,13 @@ mp_status mp_debug_time_gemm(mp_plan_t plan, int prec, int B, int tile_m, int ti
     if (!(p->prec_mask & (1u << prec)))
         return fail(MP_ERR_UNSUPPORTED, "mp_debug_time_gemm: the plan holds no copy for this precision");
     GemmShape g;
-    if (tile_m || tile_n) {
-        if ((tile_m != 128 && tile_m != 256) || (tile_n != 128 && tile_n != 256))
-            return fail(MP_ERR_INVALID, "mp_debug_time_gemm: bad tile shape");
+    if (tile_m || tile_n || pair) {
+        const bool ok = pair == 1 ? (tile_m == 256 && tile_n >= 128 && tile_n <= 256 && tile_n % 32 == 0)
+                                  : (pair == 0 && (tile_m == 128 || tile_m == 256) && (tile_n == 128 || tile_n == 256));
+        if (!ok) return fail(MP_ERR_INVALID, "mp_debug_time_gemm: bad tile shape");
         g.tm = tile_m;
         g.tn = tile_n;
+        g.pair = pair;
     } else {
         mp_status s = batch_shape(p, prec, B, nullptr, nullptr, &g);
         if (s != MP_OK) return s;

@@ -12,6 +12,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "mp_batch.cuh"
 #include "mp_device.cuh"
@@ -485,6 +486,349 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------- CTA pairs
+// The same GEMM and epilogue on a two-SM tile: a cluster of two CTAs takes
+// 256 signal rows (128 per CTA) x TN atoms, and the even CTA issues M = 256
+// MMAs (cta_group::2) that read each CTA's own 128 rows and its half of the
+// TN atom rows from the same shared-memory offsets.  Each SM then holds a
+// 128 x TN accumulator, so TMEM keeps two of them: the epilogue of one tile
+// runs under the MMAs of the next, at the bytes per flop of a 256 x 256
+// single-CTA tile.  Tiles are ordered row pair fastest, so the clusters
+// running at one time share the atom tile they stream.
+
+// The running top 8 (keys tk) of one signal row over `ncols` accumulator
+// columns (a multiple of 8) at TMEM address taddr: tile columns col0..,
+// atoms m0...  Optionally dumps the correlations (diagnostic).
+template <bool FP8>
+MP_DEV void offer8(const float* v, int col, int m, const CorrArgs& a, int row, bool dump_row, uint32_t (&tk)[8]) {
+    uint32_t ck[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const bool in = m + j < a.M;
+        float sc = fabsf(v[j]);
+        if (FP8) sc *= in ? __ldg(a.colscale + m + j) : 0.f;
+        ck[j] = (in && sc <= 3.0e38f) ? score_key(sc, col + j) : 0u;
+        if (dump_row && in)
+            a.dump[static_cast<size_t>(row) * a.M + m + j] = v[j] * (FP8 ? a.colscale[m + j] * a.rscale[row] : 1.f);
+    }
+    sort8_desc(ck);
+    merge_top8(tk, ck);
+}
+template <bool FP8>
+MP_DEV void scan_top8(uint32_t taddr, int ncols, int col0, int m0, const CorrArgs& a, int row, bool dump_row,
+                      uint32_t (&tk)[8]) {
+    int c = 0;
+    for (; c + 32 <= ncols; c += 32) {
+        float v[32];
+        tmem_ld_32cols(taddr + static_cast<uint32_t>(c), v);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) offer8<FP8>(v + 8 * h, col0 + c + 8 * h, m0 + c + 8 * h, a, row, dump_row, tk);
+    }
+    if (c + 16 <= ncols) {
+        float v[16];
+        tmem_ld_16cols(taddr + static_cast<uint32_t>(c), v);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) offer8<FP8>(v + 8 * h, col0 + c + 8 * h, m0 + c + 8 * h, a, row, dump_row, tk);
+        c += 16;
+    }
+    if (c + 8 <= ncols) {
+        float v[8];
+        tmem_ld_8cols(taddr + static_cast<uint32_t>(c), v);
+        offer8<FP8>(v, col0 + c, m0 + c, a, row, dump_row, tk);
+    }
+}
+
+// Per-CTA state of the paired kernel.
+struct PairCtx {
+    uint8_t* tilesA;     // A stages (128 rows each)
+    uint8_t* tilesB;     // B stages (TN / 2 atom rows each)
+    CorrShared* sh;
+    uint32_t tmem;
+    uint32_t rank;       // 0: the CTA that issues the MMAs, 1: its peer
+    int n_act, n_rp, n_pt;   // active rows, row pairs (256-row tiles), tiles
+    int warp, lane;
+    uint64_t lim;
+};
+
+// cluster address of `p` (a shared variable of this CTA) in CTA `rank`
+MP_DEV uint32_t in_cta(const void* p, uint32_t rank) { return mapa_shared(smem_u32(p), rank); }
+
+// Bytes one CTA loads for its 128-row block of a stage: a full block as one
+// box, a partial one as 16-row boxes over its active rows, none if idle.
+MP_DEV uint32_t pair_a_bytes(int rows) {
+    return static_cast<uint32_t>(rows >= kBM ? kBM : (rows > 0 ? (rows + 15) / 16 * 16 : 0)) * kRowBytes;
+}
+
+template <bool FP8>
+MP_DEV void pair_roles(const CUtensorMap* tmA, const CUtensorMap* tmA16, const CUtensorMap* tmB, const CorrArgs& a,
+                       const PairCtx& x) {
+    const int TN = a.TN;
+    const int half = TN / 2;
+    const uint32_t as_bytes = kBM * kRowBytes;
+    const uint32_t bs_bytes = static_cast<uint32_t>(half) * kRowBytes;
+    const int stages = a.stages;
+    CorrShared* sh = x.sh;
+    const int n_act = x.n_act, n_rp = x.n_rp, n_pt = x.n_pt;
+    const int cl = static_cast<int>(blockIdx.x >> 1), n_cl = static_cast<int>(gridDim.x >> 1);
+    const int warp = x.warp, lane = x.lane;
+    const uint64_t lim = x.lim;
+    const uint32_t rank = x.rank;
+    const int kelems = FP8 ? kRowBytes : kRowBytes / 2;
+
+    if (warp == 0) {
+        // ---------------- TMA producer of this CTA (one thread).  Its loads
+        // complete on the even CTA's `full` barrier, whose expected bytes
+        // the even CTA's producer sets for both.
+        if (lane == 0) {
+            const uint32_t full0 = in_cta(&sh->full[0], 0);
+            long long g = 0;
+            int s = 0;
+            uint32_t ph = 0;
+            bool stop = false;
+            for (int pt = cl; pt < n_pt && !stop; pt += n_cl) {
+                const int rp = pt % n_rp, at = pt / n_rp;
+                const int row0 = (rp * 2 + static_cast<int>(rank)) * kBM;
+                const int rows = max(0, min(kBM, n_act - row0));
+                const uint32_t tx = pair_a_bytes(min(kBM, max(0, n_act - rp * 2 * kBM))) +
+                                    pair_a_bytes(min(kBM, max(0, n_act - (rp * 2 + 1) * kBM))) + 2u * bs_bytes;
+                for (int kb = 0; kb < a.nk; ++kb) {
+                    if (g >= stages && !mbar_wait_bounded(&sh->empty[s], ph ^ 1u, lim)) {
+                        corr_timeout(a.err, sh);
+                        stop = true;
+                        break;
+                    }
+                    if (*reinterpret_cast<volatile int*>(&sh->abort)) {
+                        stop = true;
+                        break;
+                    }
+                    if (rank == 0) mbar_arrive_expect_tx(&sh->full[s], tx);
+                    const uint32_t bar = full0 + static_cast<uint32_t>(s) * 8u;
+                    uint8_t* dst = x.tilesA + s * as_bytes;
+                    if (rows == kBM) {
+                        tma_load_2d_pair(dst, tmA, kb * kelems, row0, bar);
+                    } else {
+                        for (int r16 = 0; r16 < rows; r16 += 16)
+                            tma_load_2d_pair(dst + r16 * kRowBytes, tmA16, kb * kelems, row0 + r16, bar);
+                    }
+                    tma_load_2d_pair(x.tilesB + s * bs_bytes, tmB, kb * kelems, at * TN + static_cast<int>(rank) * half,
+                                     bar);
+                    ++g;
+                    if (++s == stages) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            // before the CTA may exit: the MMAs released every stage's last
+            // use (so this CTA's loads into it have landed and been read)
+            for (int t = 0; t < stages && t < g; ++t) {
+                const long long last = g - 1 - ((g - 1 - t) % stages);
+                mbar_wait_bounded(&sh->empty[t], static_cast<uint32_t>((last / stages) & 1), lim);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer: one thread of the even CTA
+        if (lane == 0 && rank == 0) {
+            const uint32_t idesc = make_idesc(2 * kBM, TN, FP8 ? 0u : 1u);
+            int s = 0, buf = 0, li = 0;
+            uint32_t ph = 0, bph = 0;
+            bool ok = true;
+            for (int pt = cl; pt < n_pt && ok; pt += n_cl, ++li) {
+                if (li >= 2 && !mbar_wait_bounded(&sh->tempty[buf], bph ^ 1u, lim)) {
+                    corr_timeout(a.err, sh);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = x.tmem + static_cast<uint32_t>(buf * TN);
+                for (int kb = 0; kb < a.nk; ++kb) {
+                    if (!mbar_wait_bounded(&sh->full[s], ph, lim) || *reinterpret_cast<volatile int*>(&sh->abort)) {
+                        corr_timeout(a.err, sh);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t a0 = sw128_kmajor_desc(smem_u32(x.tilesA + s * as_bytes));
+                    const uint64_t b0 = sw128_kmajor_desc(smem_u32(x.tilesB + s * bs_bytes));
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t acc = (kb == 0 && k == 0) ? 0u : 1u;
+                        if (FP8) mma_fp8_pair(d, a0 + 2 * k, b0 + 2 * k, idesc, acc);
+                        else mma_bf16_pair(d, a0 + 2 * k, b0 + 2 * k, idesc, acc);
+                    }
+                    // both CTAs' copies of the stage are free once these finish
+                    mma_commit_pair(in_cta(&sh->empty[s], 0));
+                    mma_commit_pair(in_cta(&sh->empty[s], 1));
+                    if (++s == stages) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (ok) {
+                    mma_commit_pair(in_cta(&sh->tfull[buf], 0));
+                    mma_commit_pair(in_cta(&sh->tfull[buf], 1));
+                }
+                if (++buf == 2) {
+                    buf = 0;
+                    bph ^= 1u;
+                }
+            }
+            // no MMA may still write TMEM when it is freed
+            mma_commit_pair(in_cta(&sh->drain, 0));
+            mbar_wait_bounded(&sh->drain, 0u, lim);
+        }
+    } else {
+        // ---------------- epilogue of this CTA's 128 rows (as corr_roles:
+        // warp w reads TMEM lane quadrant w % 4, column group (w - 2) / 4)
+        const int quad = warp & 3;
+        const int grp = (warp - 2) >> 2;
+        const int cols = TN / kEpiGroups;
+        const uint32_t tempty0 = in_cta(&sh->tempty[0], 0);
+        int buf = 0;
+        uint32_t bph = 0, xround = 0;
+        bool alive = true;
+        for (int pt = cl; pt < n_pt && alive; pt += n_cl) {
+            const int rp = pt % n_rp, at = pt / n_rp;
+            bool ok = mbar_wait_bounded(&sh->tfull[buf], bph, lim) && !*reinterpret_cast<volatile int*>(&sh->abort);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) corr_timeout(a.err, sh);
+                break;
+            }
+            tc_fence_after();
+            const int blk0 = (rp * 2 + static_cast<int>(rank)) * kBM;
+            const int row = blk0 + quad * 32 + lane;
+            uint32_t tk[kTop];
+#pragma unroll
+            for (int k = 0; k < kTop; ++k) tk[k] = 0u;
+            // a warp whose 32 rows are all past the active ones has nothing to rank
+            if (blk0 + quad * 32 < n_act) {
+                const uint32_t taddr = x.tmem + (static_cast<uint32_t>(quad * 32) << 16) +
+                                       static_cast<uint32_t>(buf * TN + grp * cols);
+                const bool dump_row = a.dump && row < n_act;
+                scan_top8<FP8>(taddr, cols, grp * cols, at * TN + grp * cols, a, row, dump_row, tk);
+            }
+            // the accumulator buffer is in registers: the MMAs may reuse it
+            // (one arrival per warp of each CTA on the even CTA's barrier)
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                if (rank == 0) mbar_arrive(&sh->tempty[buf]);
+                else mbar_arrive_remote(tempty0 + static_cast<uint32_t>(buf) * 8u);
+            }
+            const int rr = quad * 32 + lane;
+            if (grp != 0) {
+                bool okx = xround == 0 || mbar_wait_bounded(&sh->xempty[quad], (xround - 1u) & 1u, lim);
+                okx = __all_sync(0xffffffffu, okx);
+                if (!okx) {
+                    if (lane == 0) corr_timeout(a.err, sh);
+                    alive = false;
+                    break;
+                }
+#pragma unroll
+                for (int k = 0; k < kTop; ++k) sh->xk[((grp - 1) * kTop + k) * kBM + rr] = tk[k];
+                mbar_arrive(&sh->xfull[quad]);
+            } else {
+                bool okx = mbar_wait_bounded(&sh->xfull[quad], xround & 1u, lim);
+                okx = __all_sync(0xffffffffu, okx);
+                if (!okx) {
+                    if (lane == 0) corr_timeout(a.err, sh);
+                    alive = false;
+                    break;
+                }
+#pragma unroll
+                for (int g = 0; g < kEpiGroups - 1; ++g) {
+                    uint32_t ck[kTop];
+#pragma unroll
+                    for (int k = 0; k < kTop; ++k) ck[k] = sh->xk[(g * kTop + k) * kBM + rr];
+                    merge_top8(tk, ck);
+                }
+                mbar_arrive(&sh->xempty[quad]);
+                if (row < n_act) {
+                    uint2* o = a.cand + (static_cast<size_t>(row) * a.n_at + at) * kTop;
+#pragma unroll
+                    for (int k = 0; k < kTop; ++k) {
+                        const uint32_t m = static_cast<uint32_t>(at * TN + key_col(tk[k]));
+                        o[k] = tk[k] ? make_uint2(key_score_bits(tk[k]), m) : make_uint2(0u, 0xffffffffu);
+                    }
+                }
+            }
+            ++xround;
+            if (++buf == 2) {
+                buf = 0;
+                bph ^= 1u;
+            }
+        }
+    }
+}
+
+// Two CTAs (a cluster) per tile of 256 signal rows x a.TN atoms; a.stages
+// is corr_stages(128, a.TN / 2), a.tmem_cols 2 * a.TN rounded up to a power
+// of two.  tmB's box is a.TN / 2 atom rows.
+template <bool FP8>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
+    corr_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA16,
+                     const __grid_constant__ CUtensorMap tmB, const CorrArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t base_u32 = smem_u32(smem_raw);
+    uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
+    const uint32_t as_bytes = kBM * kRowBytes;
+    const uint32_t bs_bytes = static_cast<uint32_t>(a.TN / 2) * kRowBytes;
+    PairCtx x;
+    x.tilesA = smem;
+    x.tilesB = smem + a.stages * as_bytes;
+    CorrShared* sh = reinterpret_cast<CorrShared*>(x.tilesB + a.stages * bs_bytes);
+    x.sh = sh;
+    x.warp = static_cast<int>(threadIdx.x >> 5);
+    x.lane = static_cast<int>(threadIdx.x & 31);
+    x.rank = cluster_ctarank();
+    if (a.zero_next && blockIdx.x == 0 && threadIdx.x == 0) *a.zero_next = 0;
+    if (a.n_at_out && blockIdx.x == 0 && threadIdx.x == 0) *a.n_at_out = a.n_at;
+    x.n_act = *a.n_act;
+    const int n_blk = (x.n_act + kBM - 1) / kBM;
+    x.n_rp = (n_blk + 1) / 2;
+    x.n_pt = x.n_rp * a.n_at;
+    // both CTAs of a cluster leave together, before any barrier or TMEM use
+    if (static_cast<int>(blockIdx.x >> 1) >= x.n_pt) return;
+    x.lim = a.watchdog_ns;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(&sh->full[s], 1);
+            mbar_init(&sh->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sh->tfull[b], 1);
+            mbar_init(&sh->tempty[b], 2 * 4 * kEpiGroups);   // one arrival per epilogue warp of both CTAs
+        }
+        for (int b = 0; b < 4; ++b) {
+            mbar_init(&sh->xfull[b], 32 * (kEpiGroups - 1));
+            mbar_init(&sh->xempty[b], 32);
+        }
+        mbar_init(&sh->drain, 1);
+        sh->abort = 0;
+        fence_mbar_init();
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmA16);
+        tma_prefetch_desc(&tmB);
+    }
+    if (x.warp == 1) tmem_alloc_pair(&sh->tmem_base, static_cast<uint32_t>(a.tmem_cols));
+    tc_fence_before();
+    __syncthreads();
+    // the peer's barriers are initialised before either CTA signals them
+    cluster_sync_all();
+    tc_fence_after();
+    x.tmem = sh->tmem_base;
+    pair_roles<FP8>(&tmA, &tmA16, &tmB, a, x);
+    tc_fence_before();
+    __syncthreads();
+    // neither CTA leaves while the other may still signal its barriers or
+    // the MMAs read its shared memory
+    cluster_sync_all();
+    if (x.warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(x.tmem, static_cast<uint32_t>(a.tmem_cols));
+    }
+}
+
 int corr_smem_bytes(int TM, int TN) {
     return 1024 + corr_stages(TM, TN) * (TM * kRowBytes + TN * kRowBytes) + static_cast<int>(sizeof(CorrShared));
 }
@@ -536,6 +880,59 @@ cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmA16, c
     const int smem = corr_smem_bytes(kBM * a.RM, a.TN);
     if (a.RM == 2) corr_top8_kernel<2><<<ctas, kGemmThreads, smem, st>>>(tmA, tmA16, tmB, tmBh, a);
     else corr_top8_kernel<1><<<ctas, kGemmThreads, smem, st>>>(tmA, tmA16, tmB, tmBh, a);
+    return cudaGetLastError();
+}
+
+int pair_smem_bytes(int TN) { return corr_smem_bytes(kBM, TN / 2); }
+
+cudaError_t pair_prepare() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    int most = 0;
+    for (int tn = 128; tn <= 256; tn += 32) most = std::max(most, pair_smem_bytes(tn));
+    cudaError_t e = cudaFuncSetAttribute(corr_pair_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(corr_pair_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+// Clusters of two that can be resident at once for a tile of TN atoms
+// (at most half the SMs; fewer when the GPCs cannot all be paired).
+int pair_max_clusters(int TN, bool fp8) {
+    static int cache[2][9] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1, -1, -1, -1}};
+    const int slot = (TN - 128) / 16;
+    if (TN < 128 || TN > 256 || TN % 16) return 1;
+    int& c = cache[fp8 ? 1 : 0][slot];
+    if (c >= 0) return c;
+    const int half = std::max(1, corr_max_ctas() / 2);
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(2 * half, 1, 1);
+    cfg.blockDim = dim3(kGemmThreads, 1, 1);
+    cfg.dynamicSmemBytes = pair_smem_bytes(TN);
+    int n = 0;
+    const cudaError_t e =
+        fp8 ? cudaOccupancyMaxActiveClusters(&n, reinterpret_cast<const void*>(corr_pair_kernel<true>), &cfg)
+            : cudaOccupancyMaxActiveClusters(&n, reinterpret_cast<const void*>(corr_pair_kernel<false>), &cfg);
+    if (e != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = half;
+    }
+    c = std::min(n, half);
+    return c;
+}
+
+cudaError_t launch_corr_pair(const CUtensorMap& tmA, const CUtensorMap& tmA16, const CUtensorMap& tmBp,
+                             const CorrArgs& a, int max_rows, cudaStream_t st) {
+    if (a.TN < 128 || a.TN > 256 || a.TN % 32 || 2 * a.TN > a.tmem_cols || a.stages != corr_stages(kBM, a.TN / 2) ||
+        a.half_ok)
+        return cudaErrorInvalidValue;
+    const int max_rp = ((max_rows + kBM - 1) / kBM + 1) / 2;
+    const int clusters = std::max(1, std::min(max_rp * a.n_at, pair_max_clusters(a.TN, a.fp8 != 0)));
+    const int smem = pair_smem_bytes(a.TN);
+    if (a.fp8) corr_pair_kernel<true><<<2 * clusters, kGemmThreads, smem, st>>>(tmA, tmA16, tmBp, a);
+    else corr_pair_kernel<false><<<2 * clusters, kGemmThreads, smem, st>>>(tmA, tmA16, tmBp, a);
     return cudaGetLastError();
 }
 

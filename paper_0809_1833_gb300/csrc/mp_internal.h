@@ -99,6 +99,7 @@ struct BatchEngine;        // batched decode state (mp_batched.cu)
 struct GemmShape {
     int tm = 128;
     int tn = 256;
+    int pair = 0;   // 1: two-SM tiles of 256 rows (clusters of two CTAs), tn a multiple of 32 in [128, 256]
 };
 
 // Autotuned batched-GEMM shape for one (precision, batch-size bucket).
@@ -148,6 +149,7 @@ struct PlanImpl {
     int grid_ctas = 0;
     int batch_tile_n = 0;
     int batch_tile_m = 0;           // batched GEMM signal rows per tile (0 = auto)
+    int batch_pair = 0;             // two-SM GEMM tiles: 0 = auto, 1 = off, 2 = on
     int batch_autotune = 1;         // time the GEMM shapes on first use of a batch size
     std::vector<TuneEntry> tuned;
     int prefetch_stages = 0;        // plain streaming: L2 prefetch distance (measured slower; off)

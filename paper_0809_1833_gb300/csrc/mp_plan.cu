@@ -343,14 +343,19 @@ mp_status mp_plan_set_option(mp_plan_t plan, int option, long long value) {
             p->batch_autotune = value ? 1 : 0;
             return MP_OK;
         case MP_OPT_BATCH_TILE_N:
-            if (value != 0 && value != 128 && value != 256)
-                return fail(MP_ERR_INVALID, "batch tile must be 0, 128 or 256");
+            // 128 or 256 for single-CTA tiles; two-SM tiles also take 160, 192, 224
+            if (value != 0 && (value < 128 || value > 256 || value % 32))
+                return fail(MP_ERR_INVALID, "batch tile must be 0 or 128..256 in steps of 32");
             p->batch_tile_n = static_cast<int>(value);
             return MP_OK;
         case MP_OPT_BATCH_GRAM:
             if (value < 0 || value > (1 << 20) || value % 16)
                 return fail(MP_ERR_INVALID, "batch Gram period must be 0 or a multiple of 16 up to 2^20");
             p->batch_gram = static_cast<int>(value);
+            return MP_OK;
+        case MP_OPT_BATCH_PAIR:
+            if (value < 0 || value > 2) return fail(MP_ERR_INVALID, "batch pair option must be 0, 1 or 2");
+            p->batch_pair = static_cast<int>(value);
             return MP_OK;
         case MP_OPT_BATCH_TILE_M:
             if (value != 0 && value != 128 && value != 256)
@@ -380,6 +385,7 @@ mp_status mp_plan_query(mp_plan_t plan, int what, long long* value) {
         case MP_Q_BATCH_TILE_N: *value = p->batch ? p->batch->TN : 0; return MP_OK;
         case MP_Q_BATCH_TILE_M: *value = p->batch ? p->batch->TM : 0; return MP_OK;
         case MP_Q_BATCH_GRAM: *value = p->batch ? p->batch->gram_R : 0; return MP_OK;
+        case MP_Q_BATCH_PAIR: *value = p->batch ? p->batch->pair : 0; return MP_OK;
         case MP_Q_PLAN_N: *value = p->N; return MP_OK;
         case MP_Q_PLAN_M: *value = p->M; return MP_OK;
         case MP_Q_GRAM_BYTES:

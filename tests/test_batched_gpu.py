@@ -154,6 +154,114 @@ def test_batched_decode_switching_tile_rows_equals_128_row_tiles():
     assert np.array_equal(X2, X1) and np.array_equal(a2, a1)
 
 
+# two-SM tiles (MP_OPT_BATCH_PAIR): 256 signals x TN atoms per cluster of two CTAs
+PAIR_TN = [256, 224, 160, 128]
+
+
+def correlations(psi, R, prec, opts):
+    """mp_debug_correlations under the given plan options; returns
+    (C float64, (tile_m, tile_n, pair) the engine used)."""
+    T = torch()
+    with GpuPlan(psi, prec_mask=1 << prec) as pl:
+        for k, v in opts:
+            pl.set(k, v)
+        Rd = T.from_numpy(R).cuda()
+        C = T.full((R.shape[0], psi.shape[0]), float("nan"), dtype=T.float32, device="cuda")
+        B().mp_debug_correlations(pl.plan, prec, Rd.data_ptr(), R.shape[0], C.data_ptr(), cur_stream())
+        used = (pl.query(B().MP_Q_BATCH_TILE_M), pl.query(B().MP_Q_BATCH_TILE_N), pl.query(B().MP_Q_BATCH_PAIR))
+        return C.cpu().numpy().astype(np.float64), used
+
+
+@pytest.mark.parametrize("tn", PAIR_TN)
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("shape", [(256, 8192, 600), (100, 300, 5), (192, 777, 200), (2048, 1024, 130)],
+                         ids=lambda s: f"N{s[0]}_M{s[1]}_B{s[2]}")
+def test_pair_tile_correlations(prec, shape, tn):
+    """Two-SM tiles give the exact quantised product and the same FP32 bits
+    as single-CTA 128-row tiles: 600 rows x 8192 atoms (more tiles than
+    clusters, so clusters run several tiles through both accumulator
+    buffers), a batch of 5 (the odd CTA of the pair has no active rows), a
+    second row block of 72 rows (16-row boxes) and ragged last atom tiles."""
+    N, M, Bn = shape
+    psi = W.gaussian_dictionary(N, M, seed=5)
+    R = np.random.default_rng([N, M, Bn, 1]).standard_normal((Bn, N)).astype(np.float32)
+    p = B().MP_PREC_BF16 if prec == "bf16" else B().MP_PREC_FP8E4M3
+    C, used = correlations(psi, R, p, [(B().MP_OPT_BATCH_PAIR, 2), (B().MP_OPT_BATCH_TILE_N, tn)])
+    assert used == (256, tn, 1)
+    C1, used1 = correlations(psi, R, p, [(B().MP_OPT_BATCH_PAIR, 1), (B().MP_OPT_BATCH_TILE_M, 128),
+                                          (B().MP_OPT_BATCH_TILE_N, 128)])
+    assert used1 == (128, 128, 0)
+    if prec == "bf16":
+        A = bf16_round(R).astype(np.float64)
+        P = bf16_round(psi).astype(np.float64)
+        ref, mag = A @ P.T, np.abs(A) @ np.abs(P).T
+    else:
+        qa, sa = e4m3_rows(R)
+        qp, sp = e4m3_rows(psi)
+        ref = (qa @ qp.T) * sa[:, None] * sp[None, :]
+        mag = (np.abs(qa) @ np.abs(qp).T) * sa[:, None] * sp[None, :]
+    tol = (N + 8) * 2.0 ** -24 * mag + 1e-30
+    assert np.all(np.isfinite(C))
+    assert np.all(np.abs(C - ref) <= tol), f"max err/tol {np.max(np.abs(C - ref) / tol):.3g}"
+    assert np.array_equal(C, C1)
+
+
+@pytest.mark.parametrize("tn", [256, 224])
+def test_pair_tile_decode_equals_128_row_tiles(tn):
+    """The 700-signal decode over 8192 atoms on two-SM tiles (more tiles than
+    clusters while the batch is full, one row pair at the end): every
+    signal's atoms, x~, residual and iteration count equal the decode on
+    single-CTA 128-signal tiles bit for bit; three signals meet the oracle
+    rule."""
+    prob = W.make_batched(256, 8192, 700, 2, 16, seed=8, eps=1e-5, T=3000)
+    p = B().MP_PREC_BF16
+    out = {}
+    for key, opts in (("pair", [(B().MP_OPT_BATCH_PAIR, 2), (B().MP_OPT_BATCH_TILE_N, tn)]),
+                      ("single", [(B().MP_OPT_BATCH_PAIR, 1), (B().MP_OPT_BATCH_TILE_M, 128),
+                                  (B().MP_OPT_BATCH_TILE_N, 256)])):
+        with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
+            for k, v in opts:
+                pl.set(k, v)
+            s, res, X, atoms, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
+            assert s == 0
+            assert pl.query(B().MP_Q_BATCH_PAIR) == (1 if key == "pair" else 0)
+            out[key] = (res, X, atoms, run_batched.R.copy())
+    (r2, X2, a2, R2), (r1, X1, a1, R1) = out["pair"], out["single"]
+    assert [r.iters for r in r2] == [r.iters for r in r1]
+    assert np.array_equal(X2, X1) and np.array_equal(a2, a1) and np.array_equal(R2, R1)
+    for b in (0, 350, 699):
+        r = r2[b]
+        assert r.status == 0 and r.stop_reason == B().MP_STOP_CONVERGED
+        o = dict(result=r, x=X2[b], atoms=a2[b, :r.iters], r=R2[b])
+        compare_to_oracle(prob.psi, prob.y[b], prob.eps, prob.T, o, check_follow=False)
+
+
+def test_pair_option_checks():
+    psi = W.gaussian_dictionary(64, 300, seed=3)
+    prob = W.make_batched(64, 300, 4, 1, 3, seed=2, psi=psi, eps=1e-5, T=500)
+    p = B().MP_PREC_BF16
+    with GpuPlan(psi, prec_mask=1 << p) as pl:
+        for bad in (-1, 3):
+            with pytest.raises(B().MpError) as ei:
+                pl.set(B().MP_OPT_BATCH_PAIR, bad)
+            assert ei.value.status == B().MP_ERR_INVALID
+        for bad in (96, 100, 288):
+            with pytest.raises(B().MpError) as ei:
+                pl.set(B().MP_OPT_BATCH_TILE_N, bad)
+            assert ei.value.status == B().MP_ERR_INVALID
+        # 224 atoms per tile is a two-SM width only
+        pl.set(B().MP_OPT_BATCH_PAIR, 1)
+        pl.set(B().MP_OPT_BATCH_TILE_N, 224)
+        s, _, _, _, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
+        assert s == B().MP_ERR_INVALID
+        pl.set(B().MP_OPT_BATCH_PAIR, 2)
+        s, res, X, atoms, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
+        assert s == 0 and pl.query(B().MP_Q_BATCH_PAIR) == 1 and pl.query(B().MP_Q_BATCH_TILE_N) == 224
+        for b in range(prob.B):
+            ora = orc.mp(psi, prob.y[b], prob.eps, prob.T)
+            assert list(atoms[b, :res[b].iters]) == list(ora["atoms"])
+
+
 def run_batched(pl, prec, Y, stops, cap=4096):
     out = batched_decode(pl, prec, Y, stops, cap)
     run_batched.energies = out["energies"]
@@ -194,16 +302,23 @@ def test_autotuner_picks_a_valid_shape_and_results_do_not_depend_on_it():
     prob = W.make_batched(256, 2048, 260, 2, 12, seed=6, eps=1e-5, T=2000)
     p = B().MP_PREC_BF16
     with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
-        tn, tm = B().mp_plan_autotune(pl.plan, p, prob.B)
-        assert tn in (128, 256) and tm in (128, 256)
-        assert B().mp_plan_autotune(pl.plan, p, prob.B) == (tn, tm)      # cached per size bucket
+        tn, tm, pair = B().mp_plan_autotune_shape(pl.plan, p, prob.B)
+        if pair:
+            assert tm == 256 and tn in (192, 224, 256)
+        else:
+            assert tn in (128, 256) and tm in (128, 256)
+        assert B().mp_plan_autotune_shape(pl.plan, p, prob.B) == (tn, tm, pair)   # cached per size bucket
+        assert B().mp_plan_autotune(pl.plan, p, prob.B) == (tn, tm)
         s, res, X, _, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
         assert s == 0
-        q = (B().MP_Q_BATCH_TILE_N, B().MP_Q_BATCH_TILE_M)
-        assert tuple(pl.query(k) for k in q) == (tn, tm)
-        other = (128 if tn == 256 else 256, 256 if tm == 128 else 128)
+        q = (B().MP_Q_BATCH_TILE_N, B().MP_Q_BATCH_TILE_M, B().MP_Q_BATCH_PAIR)
+        assert tuple(pl.query(k) for k in q) == (tn, tm, pair)
+        # another shape: single-CTA if the tuner took a pair, else a pair
+        other = (256, 128, 0) if pair else (224, 256, 1)
+        pl.set(B().MP_OPT_BATCH_PAIR, 2 if other[2] else 1)
         pl.set(B().MP_OPT_BATCH_TILE_N, other[0])
-        pl.set(B().MP_OPT_BATCH_TILE_M, other[1])
+        if not other[2]:
+            pl.set(B().MP_OPT_BATCH_TILE_M, other[1])
         s2, res2, X2, _, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
         assert tuple(pl.query(k) for k in q) == other
     assert s2 == 0 and np.array_equal(X, X2)
@@ -244,10 +359,11 @@ def test_gemm_timing_diagnostic():
     psi = W.gaussian_dictionary(256, 2048, seed=9)
     p = B().MP_PREC_BF16
     with GpuPlan(psi, prec_mask=1 << p) as pl:
-        for shape in [(0, 0)] + [t for t in TILES]:
+        for shape in [(0, 0)] + [t for t in TILES] + [(256, tn, 1) for tn in PAIR_TN]:
             us = B().mp_debug_time_gemm(pl.plan, p, 300, shape, reps=3)
             assert 0.0 < us < 1e6, (shape, us)
-        for bad in [(192, 256), (128, 64), (256, 100), (64, 128), (256, 0)]:
+        for bad in [(192, 256), (128, 64), (256, 100), (64, 128), (256, 0), (256, 224), (128, 256, 1),
+                    (256, 96, 1), (256, 200, 1), (256, 288, 1), (256, 256, 2)]:
             with pytest.raises(B().MpError) as ei:
                 B().mp_debug_time_gemm(pl.plan, p, 300, bad, reps=3)
             assert ei.value.status == B().MP_ERR_INVALID, bad
