@@ -145,6 +145,9 @@ MP_DEV void red_add(float* p, float v) {
 MP_DEV void red_add(double* p, double v) {
     asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
+MP_DEV void dsmem_st_u64(uint32_t cluster_addr, uint64_t v) {
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(cluster_addr), "l"(v) : "memory");
+}
 MP_DEV uint64_t dsmem_ld_u64(uint32_t cluster_addr) {
     uint64_t v;
     asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(cluster_addr) : "memory");

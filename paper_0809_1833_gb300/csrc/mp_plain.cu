@@ -38,6 +38,9 @@ namespace mpgb {
 constexpr int kMaxWarps = 32;
 constexpr int kMaxStages = 64;
 constexpr int kResidentThreads = 256;
+constexpr int kMaxClusterCtas = 16;
+// mode 1: every warp key of the cluster, in every CTA
+constexpr int kClusterKeys = kMaxClusterCtas * (kResidentThreads / 32);
 // FP64 streaming with shared stages: a producer warp and two groups of four
 // consumer warps (two warps per SM sub-partition keep its FP64 pipe fed)
 constexpr int kCoopGroups = 2;
@@ -81,7 +84,7 @@ template <typename T>
 struct PlainShared {
     using Key = typename PlainTraits<T>::Key;
     CoopPartials<T> coop;
-    Key wkeys[2][kMaxWarps];             // mode 1: this CTA's warp keys, two-slot ring
+    Key wkeys[2][kClusterKeys];          // mode 1: the cluster's warp keys (CTA-major), two-slot ring
     Key wkey[kMaxWarps];                 // per compute warp best key
     double wsum[kMaxWarps];              // per compute warp energy partial
     Key key;                             // selected key broadcast
@@ -171,6 +174,11 @@ MP_DEV void dsmem_ld(uint32_t addr, unsigned long long* k) { *k = dsmem_ld_u64(a
 MP_DEV void dsmem_ld(uint32_t addr, Key128* k) {
     k->hi = dsmem_ld_u64(addr);
     k->lo = dsmem_ld_u64(addr + 8u);
+}
+MP_DEV void dsmem_st(uint32_t addr, unsigned long long k) { dsmem_st_u64(addr, k); }
+MP_DEV void dsmem_st(uint32_t addr, const Key128& k) {
+    dsmem_st_u64(addr, k.hi);
+    dsmem_st_u64(addr + 8u, k.lo);
 }
 
 // ------------------------------------------------------------------ dots
@@ -444,7 +452,7 @@ __global__ void __launch_bounds__(kMaxPlainThreads, 1) mp_plain_kernel(const Pla
     const Key kzero = {};
 
     if (threadIdx.x == 0) {
-        for (int w = 0; w < kMaxWarps; ++w) sh->wkeys[0][w] = sh->wkeys[1][w] = kzero;
+        for (int w = 0; w < kClusterKeys; ++w) sh->wkeys[0][w] = sh->wkeys[1][w] = kzero;
         if constexpr (FP64) sh->coop.abort[0] = sh->coop.abort[1] = 0;
         sh->abort = 0;
         sh->done = 0;
@@ -493,6 +501,9 @@ __global__ void __launch_bounds__(kMaxPlainThreads, 1) mp_plain_kernel(const Pla
     const double e0 = e;
     const double thr2 = a.eps2 * e0;
     const bool finite0 = isfinite(e0);
+    // cluster shape: every CTA of the cluster has started (and initialised
+    // its key ring) before any CTA stores into another's shared memory
+    if (CLUSTER) cluster_sync_all();
 
     int t = 0;
     double audit = 0.0;    // max |e_t - (e_{t-1} - c^2)|, divided by e0 once at the end
@@ -663,21 +674,20 @@ __global__ void __launch_bounds__(kMaxPlainThreads, 1) mp_plain_kernel(const Pla
         // ---- CTA max, then grid max
         Key key;
         if (CLUSTER) {
-            // every warp's best goes to its own slot of a two-slot ring; after
-            // the cluster barrier every warp reads all of the cluster's warp
-            // keys over DSMEM (lane l takes entries l, l + 32, ...: CTA
-            // j / ncw, warp j % ncw) and their max is the cluster's key, the
-            // same in every warp of every CTA.  A slot is rewritten only at
-            // iteration t+2, after every warp of the cluster has passed
-            // barrier t+1 and so finished its reads of iteration t
-            if (lane == 0) sh->wkeys[t & 1][cw] = best;
+            // every warp's best (the same in all its lanes) goes to entry
+            // cta * ncw + cw of a two-slot ring in every CTA of the cluster:
+            // lane q stores it into CTA q over DSMEM before the barrier,
+            // whose release / acquire makes the stores visible.  After it
+            // every warp reads the cluster's keys from its own shared memory
+            // and their max is the cluster's key, the same in every warp of
+            // every CTA.  A slot is rewritten only at iteration t+2, after
+            // every warp of the cluster has passed barrier t+1 and so
+            // finished its reads of iteration t
+            if (lane < G)
+                dsmem_st(mapa_shared(smem_u32(&sh->wkeys[t & 1][cta * ncw + cw]), static_cast<uint32_t>(lane)), best);
             cluster_sync_all();
             Key v = kzero;
-            for (int j = lane; j < G * ncw; j += 32) {
-                Key u;
-                dsmem_ld(mapa_shared(smem_u32(&sh->wkeys[t & 1][j % ncw]), static_cast<uint32_t>(j / ncw)), &u);
-                v = kmax(v, u);
-            }
+            for (int j = lane; j < G * ncw; j += 32) v = kmax(v, sh->wkeys[t & 1][j]);
             key = warp_max_key(v);
         } else {
             if (lane == 0) sh->wkey[cw] = best;
