@@ -384,6 +384,9 @@ def run_ours(args):
             g["frac"] = g["tflops"] / pk if pk else None
     if rank == 0 and args.served_duration > 0:
         line["served"] = served_measure(args.served_rate, args.served_duration, gram=args.served_gram)
+        if args.served_gram == 0 and args.served_gram_duration > 0:
+            # the same workload served with Gram-updated correlations (R = 64)
+            line["served_gram"] = served_measure(args.served_rate, args.served_gram_duration, gram=64)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -559,8 +562,11 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
     if profile:
         # under a profiler the autotuner's timings are distorted: pin the
         # shape it picks in unprofiled runs
-        B.mp_plan_set_option(plan, B.MP_OPT_BATCH_TILE_N, profile_shape[0])
-        B.mp_plan_set_option(plan, B.MP_OPT_BATCH_TILE_M, profile_shape[1] if len(profile_shape) > 1 else 128)
+        tn, tm, pair = shape_parts(profile_shape)
+        B.mp_plan_set_option(plan, B.MP_OPT_BATCH_PAIR, 2 if pair else 1)
+        B.mp_plan_set_option(plan, B.MP_OPT_BATCH_TILE_N, tn)
+        if not pair:
+            B.mp_plan_set_option(plan, B.MP_OPT_BATCH_TILE_M, tm)
     Y = torch.from_numpy(prob.y).cuda()
     X = torch.empty((prob.B, prob.M), device="cuda")
     stop = (w["eps"], w["T"])
@@ -635,6 +641,15 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
             "gemm_full_batch": gemm}
 
 
+def shape_parts(shape):
+    """--profile-shape "atoms,signals[,pair]" -> (atoms per tile, signals
+    per tile, 1 for a two-SM tile)."""
+    tn = int(shape[0])
+    tm = int(shape[1]) if len(shape) > 1 else 128
+    pair = int(shape[2]) if len(shape) > 2 else 0
+    return tn, tm, pair
+
+
 def gemm_profile_case(prec_name, shape, rows=None):
     """Three launches of the batched workload's correlation GEMM (``rows``
     active synthetic rows, default the full batch) at shape = (atoms per
@@ -651,11 +666,11 @@ def gemm_profile_case(prec_name, shape, rows=None):
     d = torch.from_numpy(psi).cuda()
     plan = B.mp_plan_create(w["N"], w["M"], d.data_ptr(), prec_mask=1 << prec)
     del d
-    tn, tm = (list(shape) + [128])[:2]
+    tn, tm, pair = shape_parts(shape)
     rows = rows or w["B"]
-    us = B.mp_debug_time_gemm(plan, prec, rows, (tm, tn), reps=1)
+    us = B.mp_debug_time_gemm(plan, prec, rows, (tm, tn, pair), reps=1)
     B.mp_plan_destroy(plan)
-    return {"profile_case": BATCHED[prec_name], "rows": rows, "gemm_shape": [tm, tn], "us": us,
+    return {"profile_case": BATCHED[prec_name], "rows": rows, "gemm_shape": [tm, tn, pair], "us": us,
             "tflops": 2.0 * w["N"] * w["M"] * rows / us / 1e6}
 
 
@@ -674,10 +689,10 @@ def gemm_sweep(prec_name, shape, rows=(64, 128, 256, 384, 512, 768, 1024)):
     d = torch.from_numpy(psi).cuda()
     plan = B.mp_plan_create(w["N"], w["M"], d.data_ptr(), prec_mask=1 << prec)
     del d
-    tn, tm = (list(shape) + [128])[:2]
-    us = {str(r): B.mp_debug_time_gemm(plan, prec, r, (tm, tn), reps=50) for r in rows if r <= w["B"]}
+    tn, tm, pair = shape_parts(shape)
+    us = {str(r): B.mp_debug_time_gemm(plan, prec, r, (tm, tn, pair), reps=50) for r in rows if r <= w["B"]}
     B.mp_plan_destroy(plan)
-    return {"gemm_sweep": BATCHED[prec_name], "gemm_shape": [tm, tn], "us_by_active_rows": us}
+    return {"gemm_sweep": BATCHED[prec_name], "gemm_shape": [tm, tn, pair], "us_by_active_rows": us}
 
 
 def served_measure(rate=2000.0, duration=60.0, pool_s=5.0, seed=0, max_slots=256, drain_s=120.0, n_oracle=2,
@@ -787,7 +802,7 @@ def served_measure(rate=2000.0, duration=60.0, pool_s=5.0, seed=0, max_slots=256
     return {"workload": "served_4dict_poisson2000", "dictionaries": [list(d) for d in dicts], "precision": "bf16",
             "correlations": f"Gram-updated, direct BF16 GEMM every {gram} steps" if gram else
                             "direct BF16 GEMM every step",
-            "slots_per_dictionary": slots, "offered_rps": rate, "duration_s": duration, "requests": int(n),
+            "slots_per_dictionary": slots, "gram_period": gram, "offered_rps": rate, "duration_s": duration, "requests": int(n),
             "submitted_rps": float(n_sub + rejected) / max(min(wall, duration), 1e-9),
             "unfinished_at_stop": len(pending),
             "submitted": int(n_sub), "rejected": int(rejected), "rejected_pct": 100.0 * rejected / max(n, 1),
@@ -1158,8 +1173,8 @@ def main():
     ap.add_argument("--profile-batched", choices=["bf16", "fp8"], default=None,
                     help="profiling case: one batched decode of that workload, then exit")
     ap.add_argument("--profile-shape", default="256,256",
-                    help="GEMM atoms per tile and signals per tile for --profile-batched "
-                         "(the autotuner's choice in unprofiled runs)")
+                    help="GEMM atoms per tile, signals per tile and (optional third value 1) a two-SM "
+                         "tile for --profile-batched / --profile-gemm / --gemm-sweep")
     ap.add_argument("--profile-rows", type=int, default=None, help="active rows of the --profile-gemm case")
     ap.add_argument("--gemm-sweep", choices=["bf16", "fp8"], default=None,
                     help="time the batched workload's GEMM alone at several active-row counts (--profile-shape)")
@@ -1189,6 +1204,9 @@ def main():
     ap.add_argument("--step-breakdown", action="store_true",
                     help="run only the per-step time breakdown of the batched BF16 decode on the largest served "
                          "dictionary at 1-16 active rows")
+    ap.add_argument("--served-gram-duration", type=float, default=30.0,
+                    help="seconds of the extra served record with Gram-updated correlations (R = 64) in the "
+                         "default line (0 = skip)")
     ap.add_argument("--served-gram", type=int, default=0,
                     help="serve in the Gram mode with this refresh period (a multiple of 16; 0 = direct steps)")
     ap.add_argument("--breakdown-rows", type=int, nargs="*", default=None,

@@ -396,7 +396,7 @@ MP_DEV void block_top8_store(unsigned long long (&lk)[kTop], unsigned long long 
 }
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : (THREADS == 2 * kSumChains ? 2 : 1))
+__global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 7 : (THREADS == 2 * kSumChains ? 2 : 1))
     select_update_kernel(const SelArgs a) {
     extern __shared__ float4 r_sh4[];
     float* r = reinterpret_cast<float*>(r_sh4);
@@ -1922,8 +1922,14 @@ mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_
     double best = -1.0;
     GemmShape best_g;
     const int rt = (B + kBM - 1) / kBM;
+    // a shape is timed on the full batch and on a quarter of it: a batch
+    // drains as its signals stop, and a shape that only wins when full can
+    // lose the decode
+    const int Bq = std::max(1, B / 4);
     auto consider = [&](const GemmShape& g) {
-        const double us = time_gemm(p, prec, B, g, R_dev ? R_dev : R, st);
+        const double u1 = time_gemm(p, prec, B, g, R_dev ? R_dev : R, st);
+        const double u2 = u1 > 0.0 ? time_gemm(p, prec, Bq, g, R_dev ? R_dev : R, st) : -1.0;
+        const double us = u2 > 0.0 ? u1 + u2 : -1.0;
         if (us > 0.0 && (best < 0.0 || us < best)) {
             best = us;
             best_g = g;
