@@ -54,12 +54,12 @@ struct CorrArgs {
 int corr_smem_bytes(int TM, int TN);
 cudaError_t corr_prepare();
 int corr_max_ctas();
-// Launch: tmA's box is 128 signal rows, tmA16's 16 rows of the same
-// operand (the active rows of a partial row block), tmB's TN atom rows,
-// tmBh's (when a.half_ok) TN/2 atom rows.  max_rows bounds the active rows
-// any step of this launch can see (it sizes the grid).
-cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmA16, const CUtensorMap& tmB,
-                             const CUtensorMap& tmBh, const CorrArgs& a, int max_rows, cudaStream_t st);
+// Launch: tmA's box is 128 signal rows (a partial row block is loaded
+// whole), tmB's TN atom rows, tmBh's (when a.half_ok) TN/2 atom rows.
+// max_rows bounds the active rows any step of this launch can see (it sizes
+// the grid).
+cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmBh,
+                             const CorrArgs& a, int max_rows, cudaStream_t st);
 // The same GEMM on two-SM tiles (clusters of two CTAs, tcgen05 cta_group::2):
 // 256 signal rows x a.TN atoms per cluster, a.TN a multiple of 32 in
 // [128, 256], a.RM = 2, a.stages = corr_stages(128, a.TN / 2), a.half_ok = 0;
@@ -67,8 +67,8 @@ cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmA16, c
 int pair_smem_bytes(int TN);
 cudaError_t pair_prepare();
 int pair_max_clusters(int TN, bool fp8);
-cudaError_t launch_corr_pair(const CUtensorMap& tmA, const CUtensorMap& tmA16, const CUtensorMap& tmBp,
-                             const CorrArgs& a, int max_rows, cudaStream_t st);
+cudaError_t launch_corr_pair(const CUtensorMap& tmA, const CUtensorMap& tmBp, const CorrArgs& a, int max_rows,
+                             cudaStream_t st);
 
 // ------------------------------------------------------------------ batch engine
 // Per-signal state of a slot.
@@ -133,7 +133,6 @@ struct BatchEngine {
     BatchIO* h_io = nullptr;
     int* h_err = nullptr;
     CUtensorMap tmA, tmA1, tmB, tmBh;   // operand half 0, half 1, atoms (TN-row and TN/2-row boxes)
-    CUtensorMap tmA16, tmA1_16;         // operand halves with 16-row boxes
     CUtensorMap tmBp;                   // two-SM tiles: atoms in TN/2-row boxes
     // Gram mode (gram_R > 0): each slot keeps its correlations Psi^T r in
     // FP32 (Cg, M of ldC floats), computed directly at admission and every

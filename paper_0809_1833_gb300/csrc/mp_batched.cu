@@ -1373,8 +1373,6 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     }
     mp_status s = make_map(&e->tmA, e->Rq, fp8, e->cap_pad, e->ldq, kBM);
     if (s == MP_OK) s = make_map(&e->tmA1, static_cast<char*>(e->Rq) + qbytes, fp8, e->cap_pad, e->ldq, kBM);
-    if (s == MP_OK) s = make_map(&e->tmA16, e->Rq, fp8, e->cap_pad, e->ldq, 16);
-    if (s == MP_OK) s = make_map(&e->tmA1_16, static_cast<char*>(e->Rq) + qbytes, fp8, e->cap_pad, e->ldq, 16);
     if (s == MP_OK) s = make_map(&e->tmB, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, TN);
     if (s == MP_OK) s = make_map(&e->tmBh, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, half_ok ? TN / 2 : TN);
     if (s == MP_OK && g.pair) s = make_map(&e->tmBp, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, TN / 2);
@@ -1415,9 +1413,8 @@ static CorrArgs corr_args(PlanImpl* p, BatchEngine* e) {
 // The step's GEMM on operand half `half` (single-CTA or two-SM tiles).
 static cudaError_t launch_gemm(const BatchEngine* e, const CorrArgs& ca, int half, int max_rows, cudaStream_t st) {
     const CUtensorMap& tA = half ? e->tmA1 : e->tmA;
-    const CUtensorMap& tA16 = half ? e->tmA1_16 : e->tmA16;
-    if (e->pair) return launch_corr_pair(tA, tA16, e->tmBp, ca, max_rows, st);
-    return launch_corr_top8(tA, tA16, e->tmB, e->tmBh, ca, max_rows, st);
+    if (e->pair) return launch_corr_pair(tA, e->tmBp, ca, max_rows, st);
+    return launch_corr_top8(tA, e->tmB, e->tmBh, ca, max_rows, st);
 }
 
 static cudaError_t launch_fixup(PlanImpl* p, BatchEngine* e, cudaStream_t st) {

@@ -123,7 +123,7 @@ struct CorrCtx {
 // The producer, MMA and epilogue roles over this CTA's tiles of RM 128-row
 // blocks x TN atoms.
 template <int RM>
-MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmA16, const CUtensorMap* tmB, const CorrArgs& a,
+MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CorrArgs& a,
                        const CorrCtx& x) {
     const int TN = a.TN;      // stage and accumulator strides
     const int tn = x.tn;      // atoms per tile in this launch: TN, or TN / 2
@@ -158,17 +158,12 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmA16, const C
                 const int rt = ct % n_rt, at = ct / n_rt;
                 // row blocks of this tile with active rows
                 const int nmb = RM == 1 ? 1 : min(RM, n_blk - rt * RM);
-                // a partial row block is loaded as 16-row boxes covering its
-                // active rows only (the MMA still runs on 128 rows; the rows
-                // past the active ones hold stale data and their
-                // accumulators are never read)
-                int rows[RM];
-                uint32_t tx = static_cast<uint32_t>(tn) * kRowBytes;
-#pragma unroll
-                for (int mb = 0; mb < RM; ++mb) {
-                    rows[mb] = mb < nmb ? min(kBM, n_act - (rt * RM + mb) * kBM) : 0;
-                    tx += static_cast<uint32_t>(rows[mb] == kBM ? kBM : (rows[mb] + 15) / 16 * 16) * kRowBytes;
-                }
+                // a partial row block is loaded whole, as one 128-row box: an
+                // SM completes TMA boxes at a fixed rate whatever their size,
+                // so one box costs less than several small ones (the rows past
+                // the active ones hold stale finite data of the operand, and
+                // their accumulators are never read)
+                const uint32_t tx = (static_cast<uint32_t>(tn) + static_cast<uint32_t>(nmb) * kBM) * kRowBytes;
                 for (int kb = 0; kb < a.nk; ++kb) {
                     // the MMAs released the stage's previous use
                     if (g >= stages && !mbar_wait_bounded(&sh->empty[s], ph ^ 1u, lim)) {
@@ -185,13 +180,7 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmA16, const C
                     for (int mb = 0; mb < RM; ++mb) {
                         if (mb >= nmb) break;
                         uint8_t* dst = tilesA + s * as_bytes + mb * a_bytes;
-                        const int row0 = (rt * RM + mb) * kBM;
-                        if (rows[mb] == kBM) {
-                            tma_load_2d(dst, tmA, kb * kelems, row0, &sh->full[s]);
-                        } else {
-                            for (int r16 = 0; r16 < rows[mb]; r16 += 16)
-                                tma_load_2d(dst + r16 * kRowBytes, tmA16, kb * kelems, row0 + r16, &sh->full[s]);
-                        }
+                        tma_load_2d(dst, tmA, kb * kelems, (rt * RM + mb) * kBM, &sh->full[s]);
                     }
                     tma_load_2d(tilesB + s * b_bytes, tmB, kb * kelems, at * tn, &sh->full[s]);
                     ++g;
@@ -386,8 +375,8 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmA16, const C
 // is made per launch from the active row count, the same in every CTA).
 template <int RM>
 __global__ void __launch_bounds__(kGemmThreads, 1)
-    corr_top8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA16,
-                     const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBh,
+    corr_top8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ CUtensorMap tmBh,
                      const CorrArgs a) {
     extern __shared__ uint8_t smem_raw[];
     // operand tiles need 1024-byte alignment for the 128-byte swizzle atoms
@@ -428,13 +417,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     // in flight per SM as with the largest one (up to kMaxStages stages).
     // Offsets stay 1024-byte aligned.
     x.as_stride = static_cast<uint32_t>(rm) * kBM * kRowBytes;
-    // all active rows in one partial block: its stages hold only the loaded
-    // 16-row boxes, so the ring holds more stages (more bytes of atoms in
-    // flight).  The MMA still reads 128 rows from a stage's start; the rows
-    // past the loaded ones fall on the next stages' bytes (inside the ring)
-    // and only feed accumulator lanes that are never read.
-    if (rm == 1 && x.n_blk == 1 && x.n_act < kBM)
-        x.as_stride = static_cast<uint32_t>((x.n_act + 15) / 16 * 16) * kRowBytes;
     x.b_stride = static_cast<uint32_t>(x.tn) * kRowBytes;
     x.stages = min(kMaxStages, static_cast<int>(ring_bytes / (x.as_stride + x.b_stride)));
     x.tilesA = smem;
@@ -460,7 +442,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         sh->abort = 0;
         fence_mbar_init();
         tma_prefetch_desc(&tmA);
-        tma_prefetch_desc(&tmA16);
         tma_prefetch_desc(x.tn == a.TN ? &tmB : &tmBh);
     }
     if (warp == 1) tmem_alloc(&sh->tmem_base, static_cast<uint32_t>(a.tmem_cols));
@@ -472,10 +453,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
     const CUtensorMap* mb = x.tn == a.TN ? &tmB : &tmBh;
     if constexpr (RM == 2) {
-        if (rm == 2) corr_roles<2>(&tmA, &tmA16, mb, a, x);
-        else corr_roles<1>(&tmA, &tmA16, mb, a, x);
+        if (rm == 2) corr_roles<2>(&tmA, mb, a, x);
+        else corr_roles<1>(&tmA, mb, a, x);
     } else {
-        corr_roles<1>(&tmA, &tmA16, mb, a, x);
+        corr_roles<1>(&tmA, mb, a, x);
     }
 
     tc_fence_before();
@@ -553,14 +534,12 @@ struct PairCtx {
 // cluster address of `p` (a shared variable of this CTA) in CTA `rank`
 MP_DEV uint32_t in_cta(const void* p, uint32_t rank) { return mapa_shared(smem_u32(p), rank); }
 
-// Bytes one CTA loads for its 128-row block of a stage: a full block as one
-// box, a partial one as 16-row boxes over its active rows, none if idle.
-MP_DEV uint32_t pair_a_bytes(int rows) {
-    return static_cast<uint32_t>(rows >= kBM ? kBM : (rows > 0 ? (rows + 15) / 16 * 16 : 0)) * kRowBytes;
-}
+// Bytes one CTA loads for its 128-row block of a stage (rows: its active
+// rows): the whole block as one box if any row is active, else nothing.
+MP_DEV uint32_t pair_a_bytes(int rows) { return rows > 0 ? static_cast<uint32_t>(kBM) * kRowBytes : 0u; }
 
 template <bool FP8>
-MP_DEV void pair_roles(const CUtensorMap* tmA, const CUtensorMap* tmA16, const CUtensorMap* tmB, const CorrArgs& a,
+MP_DEV void pair_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CorrArgs& a,
                        const PairCtx& x) {
     const int TN = a.TN;
     const int half = TN / 2;
@@ -588,9 +567,9 @@ MP_DEV void pair_roles(const CUtensorMap* tmA, const CUtensorMap* tmA16, const C
             for (int pt = cl; pt < n_pt && !stop; pt += n_cl) {
                 const int rp = pt % n_rp, at = pt / n_rp;
                 const int row0 = (rp * 2 + static_cast<int>(rank)) * kBM;
-                const int rows = max(0, min(kBM, n_act - row0));
-                const uint32_t tx = pair_a_bytes(min(kBM, max(0, n_act - rp * 2 * kBM))) +
-                                    pair_a_bytes(min(kBM, max(0, n_act - (rp * 2 + 1) * kBM))) + 2u * bs_bytes;
+                const bool rows = n_act > row0;   // this CTA's block has active rows
+                const uint32_t tx = pair_a_bytes(n_act - rp * 2 * kBM) + pair_a_bytes(n_act - (rp * 2 + 1) * kBM) +
+                                    2u * bs_bytes;
                 for (int kb = 0; kb < a.nk; ++kb) {
                     if (g >= stages && !mbar_wait_bounded(&sh->empty[s], ph ^ 1u, lim)) {
                         corr_timeout(a.err, sh);
@@ -604,12 +583,7 @@ MP_DEV void pair_roles(const CUtensorMap* tmA, const CUtensorMap* tmA16, const C
                     if (rank == 0) mbar_arrive_expect_tx(&sh->full[s], tx);
                     const uint32_t bar = full0 + static_cast<uint32_t>(s) * 8u;
                     uint8_t* dst = x.tilesA + s * as_bytes;
-                    if (rows == kBM) {
-                        tma_load_2d_pair(dst, tmA, kb * kelems, row0, bar);
-                    } else {
-                        for (int r16 = 0; r16 < rows; r16 += 16)
-                            tma_load_2d_pair(dst + r16 * kRowBytes, tmA16, kb * kelems, row0 + r16, bar);
-                    }
+                    if (rows) tma_load_2d_pair(dst, tmA, kb * kelems, row0, bar);
                     tma_load_2d_pair(x.tilesB + s * bs_bytes, tmB, kb * kelems, at * TN + static_cast<int>(rank) * half,
                                      bar);
                     ++g;
@@ -766,8 +740,8 @@ MP_DEV void pair_roles(const CUtensorMap* tmA, const CUtensorMap* tmA16, const C
 // of two.  tmB's box is a.TN / 2 atom rows.
 template <bool FP8>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
-    corr_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA16,
-                     const __grid_constant__ CUtensorMap tmB, const CorrArgs a) {
+    corr_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const CorrArgs a) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t base_u32 = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
@@ -807,7 +781,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
         sh->abort = 0;
         fence_mbar_init();
         tma_prefetch_desc(&tmA);
-        tma_prefetch_desc(&tmA16);
         tma_prefetch_desc(&tmB);
     }
     if (x.warp == 1) tmem_alloc_pair(&sh->tmem_base, static_cast<uint32_t>(a.tmem_cols));
@@ -817,7 +790,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
     cluster_sync_all();
     tc_fence_after();
     x.tmem = sh->tmem_base;
-    pair_roles<FP8>(&tmA, &tmA16, &tmB, a, x);
+    pair_roles<FP8>(&tmA, &tmB, a, x);
     tc_fence_before();
     __syncthreads();
     // neither CTA leaves while the other may still signal its barriers or
@@ -863,7 +836,7 @@ int corr_max_ctas() {
     return cache;
 }
 
-cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmA16, const CUtensorMap& tmB,
+cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB,
                              const CUtensorMap& tmBh, const CorrArgs& a, int max_rows, cudaStream_t st) {
     const int nbuf = (a.RM == 1 || a.RM * a.TN * 2 <= 512) ? 2 : 1;   // as the kernel computes it
     if ((a.RM != 1 && a.RM != 2) || nbuf * a.RM * a.TN > a.tmem_cols ||
@@ -878,8 +851,8 @@ cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmA16, c
         max_ct = std::max(max_ct, std::min(max_rt, 2) * ((a.M + a.TN / 2 - 1) / (a.TN / 2)));
     const int ctas = std::max(1, std::min(max_ct, corr_max_ctas()));
     const int smem = corr_smem_bytes(kBM * a.RM, a.TN);
-    if (a.RM == 2) corr_top8_kernel<2><<<ctas, kGemmThreads, smem, st>>>(tmA, tmA16, tmB, tmBh, a);
-    else corr_top8_kernel<1><<<ctas, kGemmThreads, smem, st>>>(tmA, tmA16, tmB, tmBh, a);
+    if (a.RM == 2) corr_top8_kernel<2><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, a);
+    else corr_top8_kernel<1><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, a);
     return cudaGetLastError();
 }
 
@@ -923,7 +896,7 @@ int pair_max_clusters(int TN, bool fp8) {
     return c;
 }
 
-cudaError_t launch_corr_pair(const CUtensorMap& tmA, const CUtensorMap& tmA16, const CUtensorMap& tmBp,
+cudaError_t launch_corr_pair(const CUtensorMap& tmA, const CUtensorMap& tmBp,
                              const CorrArgs& a, int max_rows, cudaStream_t st) {
     if (a.TN < 128 || a.TN > 256 || a.TN % 32 || 2 * a.TN > a.tmem_cols || a.stages != corr_stages(kBM, a.TN / 2) ||
         a.half_ok)
@@ -931,8 +904,8 @@ cudaError_t launch_corr_pair(const CUtensorMap& tmA, const CUtensorMap& tmA16, c
     const int max_rp = ((max_rows + kBM - 1) / kBM + 1) / 2;
     const int clusters = std::max(1, std::min(max_rp * a.n_at, pair_max_clusters(a.TN, a.fp8 != 0)));
     const int smem = pair_smem_bytes(a.TN);
-    if (a.fp8) corr_pair_kernel<true><<<2 * clusters, kGemmThreads, smem, st>>>(tmA, tmA16, tmBp, a);
-    else corr_pair_kernel<false><<<2 * clusters, kGemmThreads, smem, st>>>(tmA, tmA16, tmBp, a);
+    if (a.fp8) corr_pair_kernel<true><<<2 * clusters, kGemmThreads, smem, st>>>(tmA, tmBp, a);
+    else corr_pair_kernel<false><<<2 * clusters, kGemmThreads, smem, st>>>(tmA, tmBp, a);
     return cudaGetLastError();
 }
 

@@ -181,7 +181,7 @@ def test_pair_tile_correlations(prec, shape, tn):
     as single-CTA 128-row tiles: 600 rows x 8192 atoms (more tiles than
     clusters, so clusters run several tiles through both accumulator
     buffers), a batch of 5 (the odd CTA of the pair has no active rows), a
-    second row block of 72 rows (16-row boxes) and ragged last atom tiles."""
+    second row block of 72 rows (loaded as a whole block) and ragged last atom tiles."""
     N, M, Bn = shape
     psi = W.gaussian_dictionary(N, M, seed=5)
     R = np.random.default_rng([N, M, Bn, 1]).standard_normal((Bn, N)).astype(np.float32)
