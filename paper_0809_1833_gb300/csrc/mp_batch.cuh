@@ -49,17 +49,21 @@ struct CorrArgs {
     int* zero_next;         // step: the other half's survivor count, set to 0 here (or NULL)
     int half_ok;            // tmBh holds TN/2-row boxes: a launch may take tiles of TN/2 atoms
     int* n_at_out;          // atom tiles (candidate lists per row) this launch used, or NULL
+    int ks2_ok;             // tmA3 / tmB3 are set: 128-atom one-block tiles may stage two K slices
 };
 
 int corr_smem_bytes(int TM, int TN);
 cudaError_t corr_prepare();
 int corr_max_ctas();
 // Launch: tmA's box is 128 signal rows (a partial row block is loaded
-// whole), tmB's TN atom rows, tmBh's (when a.half_ok) TN/2 atom rows.
-// max_rows bounds the active rows any step of this launch can see (it sizes
-// the grid).
+// whole), tmB's TN atom rows, tmBh's (when a.half_ok) TN/2 atom rows; with
+// a.ks2_ok, tmA3 / tmB3 are the same operands as 3-D views (128-byte K
+// slice, rows, slice index) with boxes of 128 rows x 2 slices, used by
+// launches whose tile is one row block by 128 atoms.  max_rows bounds the
+// active rows any step of this launch can see (it sizes the grid).
 cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmBh,
-                             const CorrArgs& a, int max_rows, cudaStream_t st);
+                             const CUtensorMap& tmA3, const CUtensorMap& tmB3, const CorrArgs& a, int max_rows,
+                             cudaStream_t st);
 // The same GEMM on two-SM tiles (clusters of two CTAs, tcgen05 cta_group::2):
 // 256 signal rows x a.TN atoms per cluster, a.TN a multiple of 32 in
 // [128, 256], a.RM = 2, a.stages = corr_stages(128, a.TN / 2), a.half_ok = 0;
@@ -134,6 +138,7 @@ struct BatchEngine {
     int* h_err = nullptr;
     CUtensorMap tmA, tmA1, tmB, tmBh;   // operand half 0, half 1, atoms (TN-row and TN/2-row boxes)
     CUtensorMap tmBp;                   // two-SM tiles: atoms in TN/2-row boxes
+    CUtensorMap tmA3, tmA1_3, tmB3;     // 3-D views (slice, rows, slice index): 128 rows x 2 K slices
     // Gram mode (gram_R > 0): each slot keeps its correlations Psi^T r in
     // FP32 (Cg, M of ldC floats), computed directly at admission and every
     // gram_R of its own steps, and updated from one row of G = Psi^T Psi in

@@ -1248,6 +1248,27 @@ static mp_status make_map(CUtensorMap* map, void* base, bool fp8, long long rows
     return MP_OK;
 }
 
+// The same matrix as a 3-D view: K slices of 128 bytes (x), rows (y), slice
+// index (z, stride 128 bytes); box = 128 rows x 2 slices, 128-byte swizzle.
+// The box lands in shared memory as two slices of 128 rows one after the
+// other, each in the layout of a 2-D box of make_map.
+static mp_status make_map3(CUtensorMap* map, void* base, bool fp8, long long rows, long long row_elems) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(MP_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    const int esize = fp8 ? 1 : 2;
+    const long long ke = kRowBytes / esize;
+    cuuint64_t dims[3] = {static_cast<cuuint64_t>(ke), static_cast<cuuint64_t>(rows),
+                          static_cast<cuuint64_t>(row_elems / ke)};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(row_elems * esize), static_cast<cuuint64_t>(kRowBytes)};
+    cuuint32_t box[3] = {static_cast<cuuint32_t>(ke), static_cast<cuuint32_t>(kBM), 2u};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides,
+                     box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(MP_ERR_CUDA, "cuTensorMapEncodeTiled (3-D) failed (" + std::to_string(r) + ")");
+    return MP_OK;
+}
+
 void engine_free(BatchEngine* e) {
     if (!e) return;
     if (e->graph) cudaGraphExecDestroy(e->graph);
@@ -1376,6 +1397,9 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     if (s == MP_OK) s = make_map(&e->tmB, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, TN);
     if (s == MP_OK) s = make_map(&e->tmBh, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, half_ok ? TN / 2 : TN);
     if (s == MP_OK && g.pair) s = make_map(&e->tmBp, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq, TN / 2);
+    if (s == MP_OK) s = make_map3(&e->tmA3, e->Rq, fp8, e->cap_pad, e->ldq);
+    if (s == MP_OK) s = make_map3(&e->tmA1_3, static_cast<char*>(e->Rq) + qbytes, fp8, e->cap_pad, e->ldq);
+    if (s == MP_OK) s = make_map3(&e->tmB3, fp8 ? p->psi8 : p->psi16, fp8, p->M, e->ldq);
     if (s != MP_OK) {
         engine_free(e);
         return s;
@@ -1404,6 +1428,7 @@ static CorrArgs corr_args(PlanImpl* p, BatchEngine* e) {
     ca.tmem_cols = cols > 256 ? 512 : (cols > 128 ? 256 : 128);
     ca.stages = e->pair ? corr_stages(kBM, e->TN / 2) : corr_stages(e->TM, e->TN);
     ca.colscale = p->scale8;
+    ca.ks2_ok = e->pair ? 0 : 1;
     ca.cand = e->cand;
     ca.watchdog_ns = static_cast<unsigned long long>(p->watchdog_ns);
     ca.err = e->err;
@@ -1414,7 +1439,7 @@ static CorrArgs corr_args(PlanImpl* p, BatchEngine* e) {
 static cudaError_t launch_gemm(const BatchEngine* e, const CorrArgs& ca, int half, int max_rows, cudaStream_t st) {
     const CUtensorMap& tA = half ? e->tmA1 : e->tmA;
     if (e->pair) return launch_corr_pair(tA, e->tmBp, ca, max_rows, st);
-    return launch_corr_top8(tA, e->tmB, e->tmBh, ca, max_rows, st);
+    return launch_corr_top8(tA, e->tmB, e->tmBh, half ? e->tmA1_3 : e->tmA3, e->tmB3, ca, max_rows, st);
 }
 
 static cudaError_t launch_fixup(PlanImpl* p, BatchEngine* e, cudaStream_t st) {

@@ -85,6 +85,16 @@ MP_DEV void issue_kblock(uint32_t d, uint64_t a0, uint64_t b0, uint32_t idesc, i
     }
 }
 
+// 3-D tiled load: box {x.., y.., z..} at (x, y, z) (the operands' 3-D view:
+// 128-byte K slice, rows, slice index), completion counted on `bar`.
+MP_DEV void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
 struct CorrShared {
     uint64_t full[kMaxStages];
     uint64_t empty[kMaxStages];
@@ -110,12 +120,13 @@ struct CorrCtx {
     uint8_t* tilesB;       // B stages
     CorrShared* sh;
     uint32_t tmem;
-    uint32_t as_stride;    // bytes of one stage's A region (room for the largest tile)
+    uint32_t as_stride;    // bytes of one K slice's A region (room for the launch's tile)
     int n_act, n_blk;      // active rows, 128-row blocks holding them
     int n_rt, n_ct;        // row tiles and tiles (for this launch's RM)
     int tn, n_at;          // atoms per tile and atom tiles of this launch
     int stages;            // ring depth for this launch's tile
-    uint32_t b_stride;     // bytes of one stage's B region
+    int ks;                // K slices per stage: 1, or 2 (one 3-D box per operand)
+    uint32_t b_stride;     // bytes of one K slice's B region
     int warp, lane;
     uint64_t lim;          // watchdog, ns
 };
@@ -123,8 +134,8 @@ struct CorrCtx {
 // The producer, MMA and epilogue roles over this CTA's tiles of RM 128-row
 // blocks x TN atoms.
 template <int RM>
-MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CorrArgs& a,
-                       const CorrCtx& x) {
+MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmA3,
+                       const CUtensorMap* tmB3, const CorrArgs& a, const CorrCtx& x) {
     const int TN = a.TN;      // stage and accumulator strides
     const int tn = x.tn;      // atoms per tile in this launch: TN, or TN / 2
     // TMEM accumulator buffers: two unless one tile fills the 512 columns
@@ -133,6 +144,11 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
     const uint32_t as_bytes = x.as_stride;
     const uint32_t b_bytes = x.b_stride;         // one stage's B region (tn atom rows)
     const int stages = x.stages;
+    // a stage holds ks K slices (slice-major: [slice][rows]); with ks = 2
+    // each operand's two slices come in one 3-D box
+    const int ks = x.ks;
+    const int n_st = (a.nk + ks - 1) / ks;     // stages per tile
+    const uint32_t ast_bytes = static_cast<uint32_t>(ks) * as_bytes, bst_bytes = static_cast<uint32_t>(ks) * b_bytes;
     uint8_t* tilesA = x.tilesA;
     uint8_t* tilesB = x.tilesB;
     CorrShared* sh = x.sh;
@@ -163,8 +179,9 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
                 // so one box costs less than several small ones (the rows past
                 // the active ones hold stale finite data of the operand, and
                 // their accumulators are never read)
-                const uint32_t tx = (static_cast<uint32_t>(tn) + static_cast<uint32_t>(nmb) * kBM) * kRowBytes;
-                for (int kb = 0; kb < a.nk; ++kb) {
+                const uint32_t tx =
+                    static_cast<uint32_t>(ks) * (static_cast<uint32_t>(tn) + static_cast<uint32_t>(nmb) * kBM) * kRowBytes;
+                for (int kb = 0; kb < n_st; ++kb) {
                     // the MMAs released the stage's previous use
                     if (g >= stages && !mbar_wait_bounded(&sh->empty[s], ph ^ 1u, lim)) {
                         corr_timeout(a.err, sh);
@@ -176,13 +193,20 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
                         break;
                     }
                     mbar_arrive_expect_tx(&sh->full[s], tx);
+                    if (ks == 2) {
+                        // one row block (RM = 1 launches only), slices 2kb and
+                        // 2kb + 1 (past the last one: zero fill, not multiplied)
+                        tma_load_3d(tilesA + s * ast_bytes, tmA3, 0, rt * kBM, 2 * kb, &sh->full[s]);
+                        tma_load_3d(tilesB + s * bst_bytes, tmB3, 0, at * tn, 2 * kb, &sh->full[s]);
+                    } else {
 #pragma unroll
-                    for (int mb = 0; mb < RM; ++mb) {
-                        if (mb >= nmb) break;
-                        uint8_t* dst = tilesA + s * as_bytes + mb * a_bytes;
-                        tma_load_2d(dst, tmA, kb * kelems, (rt * RM + mb) * kBM, &sh->full[s]);
+                        for (int mb = 0; mb < RM; ++mb) {
+                            if (mb >= nmb) break;
+                            uint8_t* dst = tilesA + s * as_bytes + mb * a_bytes;
+                            tma_load_2d(dst, tmA, kb * kelems, (rt * RM + mb) * kBM, &sh->full[s]);
+                        }
+                        tma_load_2d(tilesB + s * b_bytes, tmB, kb * kelems, at * tn, &sh->full[s]);
                     }
-                    tma_load_2d(tilesB + s * b_bytes, tmB, kb * kelems, at * tn, &sh->full[s]);
                     ++g;
                     if (++s == stages) {
                         s = 0;
@@ -218,19 +242,26 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
                 tc_fence_after();
                 // row block mb accumulates in columns [mb * TN, (mb + 1) * TN) of the buffer
                 const uint32_t d = tmem + static_cast<uint32_t>(buf * RM * TN);
-                for (int kb = 0; kb < a.nk; ++kb) {
+                for (int kb = 0; kb < n_st; ++kb) {
                     if (!mbar_wait_bounded(&sh->full[s], ph, lim) || *reinterpret_cast<volatile int*>(&sh->abort)) {
                         corr_timeout(a.err, sh);
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    // descriptors of the stage's tiles; a step of 32 bytes
+                    // descriptors of the stage's slices; a step of 32 bytes
                     // along K adds 2 to the start-address field (address >> 4)
-                    const uint64_t a0 = sw128_kmajor_desc(smem_u32(tilesA + s * as_bytes));
-                    const uint64_t b0 = sw128_kmajor_desc(smem_u32(tilesB + s * b_bytes));
+                    const uint64_t a0 = sw128_kmajor_desc(smem_u32(tilesA + s * ast_bytes));
+                    const uint64_t b0 = sw128_kmajor_desc(smem_u32(tilesB + s * bst_bytes));
                     if (a.fp8) issue_kblock<RM, true>(d, a0, b0, idesc, nmb, TN, kb == 0);
                     else issue_kblock<RM, false>(d, a0, b0, idesc, nmb, TN, kb == 0);
+                    if (ks == 2 && 2 * kb + 1 < a.nk) {
+                        // the stage's second slice: as_bytes / b_bytes further
+                        // (address >> 4 in the descriptors' start field)
+                        const uint64_t a1 = a0 + (as_bytes >> 4), b1 = b0 + (b_bytes >> 4);
+                        if (a.fp8) issue_kblock<RM, true>(d, a1, b1, idesc, nmb, TN, false);
+                        else issue_kblock<RM, false>(d, a1, b1, idesc, nmb, TN, false);
+                    }
                     // stage reusable once these MMAs finish
                     mma_commit(&sh->empty[s]);
                     if (++s == stages) {
@@ -376,7 +407,8 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const Cor
 template <int RM>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     corr_top8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     const __grid_constant__ CUtensorMap tmBh,
+                     const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmA3,
+                     const __grid_constant__ CUtensorMap tmB3,
                      const CorrArgs a) {
     extern __shared__ uint8_t smem_raw[];
     // operand tiles need 1024-byte alignment for the 128-byte swizzle atoms
@@ -418,9 +450,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     // Offsets stay 1024-byte aligned.
     x.as_stride = static_cast<uint32_t>(rm) * kBM * kRowBytes;
     x.b_stride = static_cast<uint32_t>(x.tn) * kRowBytes;
-    x.stages = min(kMaxStages, static_cast<int>(ring_bytes / (x.as_stride + x.b_stride)));
+    // two K slices per stage (one 3-D box per operand) when the tile is one
+    // row block by 128 atoms and the ring still holds 3 such stages: an SM
+    // completes TMA boxes at a fixed rate, so bigger boxes feed it faster
+    x.ks = (a.ks2_ok && rm == 1 && x.tn == 128 && ring_bytes / (2u * (x.as_stride + x.b_stride)) >= 3u) ? 2 : 1;
+    x.stages = min(kMaxStages, static_cast<int>(ring_bytes / (static_cast<uint32_t>(x.ks) * (x.as_stride + x.b_stride))));
     x.tilesA = smem;
-    x.tilesB = smem + x.stages * x.as_stride;
+    x.tilesB = smem + x.stages * x.ks * x.as_stride;
     x.n_ct = x.n_rt * x.n_at;                       // tiles
     if (static_cast<int>(blockIdx.x) >= x.n_ct) return;   // a CTA with no tile
     x.lim = a.watchdog_ns;
@@ -443,6 +479,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         fence_mbar_init();
         tma_prefetch_desc(&tmA);
         tma_prefetch_desc(x.tn == a.TN ? &tmB : &tmBh);
+        if (x.ks == 2) {
+            tma_prefetch_desc(&tmA3);
+            tma_prefetch_desc(&tmB3);
+        }
     }
     if (warp == 1) tmem_alloc(&sh->tmem_base, static_cast<uint32_t>(a.tmem_cols));
     tc_fence_before();
@@ -453,10 +493,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
     const CUtensorMap* mb = x.tn == a.TN ? &tmB : &tmBh;
     if constexpr (RM == 2) {
-        if (rm == 2) corr_roles<2>(&tmA, mb, a, x);
-        else corr_roles<1>(&tmA, mb, a, x);
+        if (rm == 2) corr_roles<2>(&tmA, mb, &tmA3, &tmB3, a, x);
+        else corr_roles<1>(&tmA, mb, &tmA3, &tmB3, a, x);
     } else {
-        corr_roles<1>(&tmA, mb, a, x);
+        corr_roles<1>(&tmA, mb, &tmA3, &tmB3, a, x);
     }
 
     tc_fence_before();
@@ -836,8 +876,9 @@ int corr_max_ctas() {
     return cache;
 }
 
-cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB,
-                             const CUtensorMap& tmBh, const CorrArgs& a, int max_rows, cudaStream_t st) {
+cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmBh,
+                             const CUtensorMap& tmA3, const CUtensorMap& tmB3, const CorrArgs& a, int max_rows,
+                             cudaStream_t st) {
     const int nbuf = (a.RM == 1 || a.RM * a.TN * 2 <= 512) ? 2 : 1;   // as the kernel computes it
     if ((a.RM != 1 && a.RM != 2) || nbuf * a.RM * a.TN > a.tmem_cols ||
         a.stages != corr_stages(kBM * a.RM, a.TN) || (a.half_ok && a.TN != 256))
@@ -851,8 +892,8 @@ cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB,
         max_ct = std::max(max_ct, std::min(max_rt, 2) * ((a.M + a.TN / 2 - 1) / (a.TN / 2)));
     const int ctas = std::max(1, std::min(max_ct, corr_max_ctas()));
     const int smem = corr_smem_bytes(kBM * a.RM, a.TN);
-    if (a.RM == 2) corr_top8_kernel<2><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, a);
-    else corr_top8_kernel<1><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, a);
+    if (a.RM == 2) corr_top8_kernel<2><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, tmA3, tmB3, a);
+    else corr_top8_kernel<1><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, tmA3, tmB3, a);
     return cudaGetLastError();
 }
 
