@@ -133,7 +133,7 @@ struct CorrCtx {
 
 // The producer, MMA and epilogue roles over this CTA's tiles of RM 128-row
 // blocks x TN atoms.
-template <int RM>
+template <int RM, int KS>
 MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmA3,
                        const CUtensorMap* tmB3, const CorrArgs& a, const CorrCtx& x) {
     const int TN = a.TN;      // stage and accumulator strides
@@ -146,7 +146,7 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUt
     const int stages = x.stages;
     // a stage holds ks K slices (slice-major: [slice][rows]); with ks = 2
     // each operand's two slices come in one 3-D box
-    const int ks = x.ks;
+    constexpr int ks = KS;   // the launch's x.ks
     const int n_st = (a.nk + ks - 1) / ks;     // stages per tile
     const uint32_t ast_bytes = static_cast<uint32_t>(ks) * as_bytes, bst_bytes = static_cast<uint32_t>(ks) * b_bytes;
     uint8_t* tilesA = x.tilesA;
@@ -193,7 +193,7 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUt
                         break;
                     }
                     mbar_arrive_expect_tx(&sh->full[s], tx);
-                    if (ks == 2) {
+                    if constexpr (KS == 2) {
                         // one row block (RM = 1 launches only), slices 2kb and
                         // 2kb + 1 (past the last one: zero fill, not multiplied)
                         tma_load_3d(tilesA + s * ast_bytes, tmA3, 0, rt * kBM, 2 * kb, &sh->full[s]);
@@ -255,7 +255,7 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUt
                     const uint64_t b0 = sw128_kmajor_desc(smem_u32(tilesB + s * bst_bytes));
                     if (a.fp8) issue_kblock<RM, true>(d, a0, b0, idesc, nmb, TN, kb == 0);
                     else issue_kblock<RM, false>(d, a0, b0, idesc, nmb, TN, kb == 0);
-                    if (ks == 2 && 2 * kb + 1 < a.nk) {
+                    if (KS == 2 && 2 * kb + 1 < a.nk) {
                         // the stage's second slice: as_bytes / b_bytes further
                         // (address >> 4 in the descriptors' start field)
                         const uint64_t a1 = a0 + (as_bytes >> 4), b1 = b0 + (b_bytes >> 4);
@@ -493,10 +493,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
     const CUtensorMap* mb = x.tn == a.TN ? &tmB : &tmBh;
     if constexpr (RM == 2) {
-        if (rm == 2) corr_roles<2>(&tmA, mb, &tmA3, &tmB3, a, x);
-        else corr_roles<1>(&tmA, mb, &tmA3, &tmB3, a, x);
+        if (rm == 2) corr_roles<2, 1>(&tmA, mb, &tmA3, &tmB3, a, x);
+        else if (x.ks == 2) corr_roles<1, 2>(&tmA, mb, &tmA3, &tmB3, a, x);
+        else corr_roles<1, 1>(&tmA, mb, &tmA3, &tmB3, a, x);
     } else {
-        corr_roles<1>(&tmA, mb, &tmA3, &tmB3, a, x);
+        if (x.ks == 2) corr_roles<1, 2>(&tmA, mb, &tmA3, &tmB3, a, x);
+        else corr_roles<1, 1>(&tmA, mb, &tmA3, &tmB3, a, x);
     }
 
     tc_fence_before();
