@@ -396,7 +396,7 @@ MP_DEV void block_top8_store(unsigned long long (&lk)[kTop], unsigned long long 
 }
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 7 : (THREADS == 2 * kSumChains ? 2 : 1))
+__global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : (THREADS == 2 * kSumChains ? 2 : 1))
     select_update_kernel(const SelArgs a) {
     extern __shared__ float4 r_sh4[];
     float* r = reinterpret_cast<float*>(r_sh4);
@@ -521,15 +521,39 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 7 : (THREADS 
     // Eq. 11 in FP32, the FP64 energy, then the requantised row of a signal
     // that runs on
     const float4* pm = reinterpret_cast<const float4*>(a.psi32 + static_cast<size_t>(m) * a.ldN);
-    for (int k = threadIdx.x; k < n4; k += THREADS) {
-        const float4 p = __ldg(pm + k);
-        float4 v = rs4[k];
-        v.x = fmaf(-c, p.x, v.x);
-        v.y = fmaf(-c, p.y, v.y);
-        v.z = fmaf(-c, p.z, v.z);
-        v.w = fmaf(-c, p.w, v.w);
-        rg4[k] = v;
-        rs4[k] = v;
+    {
+        // the thread's first kUpd vectors of psi_m are loaded together, so
+        // their latencies overlap, then applied; any rest in a plain loop
+        constexpr int kUpd = 4;
+        float4 p[kUpd];
+#pragma unroll
+        for (int u = 0; u < kUpd; ++u) {
+            const int k = threadIdx.x + u * THREADS;
+            if (k < n4) p[u] = __ldg(pm + k);
+        }
+#pragma unroll
+        for (int u = 0; u < kUpd; ++u) {
+            const int k = threadIdx.x + u * THREADS;
+            if (k < n4) {
+                float4 v = rs4[k];
+                v.x = fmaf(-c, p[u].x, v.x);
+                v.y = fmaf(-c, p[u].y, v.y);
+                v.z = fmaf(-c, p[u].z, v.z);
+                v.w = fmaf(-c, p[u].w, v.w);
+                rg4[k] = v;
+                rs4[k] = v;
+            }
+        }
+        for (int k = threadIdx.x + kUpd * THREADS; k < n4; k += THREADS) {
+            const float4 q = __ldg(pm + k);
+            float4 v = rs4[k];
+            v.x = fmaf(-c, q.x, v.x);
+            v.y = fmaf(-c, q.y, v.y);
+            v.z = fmaf(-c, q.z, v.z);
+            v.w = fmaf(-c, q.w, v.w);
+            rg4[k] = v;
+            rs4[k] = v;
+        }
     }
     if (THREADS != kSumChains) __syncthreads();   // the chains read other threads' updates
     double acc = 0.0;
