@@ -95,6 +95,21 @@ MP_DEV void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, 
         : "memory");
 }
 
+// FP8: the per-atom scales of atoms m .. m+7 (0 for atoms past M), as two
+// 16-byte loads where all 8 exist (m is a multiple of 8, so they are
+// aligned), else one by one.
+MP_DEV void colscale8(const float* __restrict__ cs, int m, int M, float (&out)[8]) {
+    if (m + 8 <= M) {
+        const float4 c0 = __ldg(reinterpret_cast<const float4*>(cs + m));
+        const float4 c1 = __ldg(reinterpret_cast<const float4*>(cs + m + 4));
+        out[0] = c0.x; out[1] = c0.y; out[2] = c0.z; out[3] = c0.w;
+        out[4] = c1.x; out[5] = c1.y; out[6] = c1.z; out[7] = c1.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) out[j] = m + j < M ? __ldg(cs + m + j) : 0.f;
+    }
+}
+
 struct CorrShared {
     uint64_t full[kMaxStages];
     uint64_t empty[kMaxStages];
@@ -336,12 +351,14 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUt
 #pragma unroll
                     for (int h = 0; h < 4; ++h) {
                         uint32_t ck[8];
+                        float cs8[8];
+                        if (a.fp8) colscale8(a.colscale, m0 + c * 32 + h * 8, a.M, cs8);
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
                             const int col = grp * cols + c * 32 + h * 8 + j;   // column in the tile
                             const int m = m0 + c * 32 + h * 8 + j;
                             float sc = fabsf(v[h * 8 + j]);
-                            if (a.fp8) sc *= m < a.M ? __ldg(a.colscale + m) : 0.f;
+                            if (a.fp8) sc *= cs8[j];
                             ck[j] = (m < a.M && sc <= 3.0e38f) ? score_key(sc, col) : 0u;
                         }
                         sort8_desc(ck);
@@ -525,11 +542,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 template <bool FP8>
 MP_DEV void offer8(const float* v, int col, int m, const CorrArgs& a, int row, bool dump_row, uint32_t (&tk)[8]) {
     uint32_t ck[8];
+    float cs8[8];
+    if (FP8) colscale8(a.colscale, m, a.M, cs8);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const bool in = m + j < a.M;
         float sc = fabsf(v[j]);
-        if (FP8) sc *= in ? __ldg(a.colscale + m + j) : 0.f;
+        if (FP8) sc *= cs8[j];
         ck[j] = (in && sc <= 3.0e38f) ? score_key(sc, col + j) : 0u;
         if (dump_row && in)
             a.dump[static_cast<size_t>(row) * a.M + m + j] = v[j] * (FP8 ? a.colscale[m + j] * a.rscale[row] : 1.f);
