@@ -149,7 +149,8 @@ typedef enum {
     MP_OPT_DEBUG_SKIP_ARRIVE = 3, /* grid modes: this CTA never arrives at the first */
                                /* grid barrier (watchdog test), -1 = off             */
     MP_OPT_GRID_CTAS = 4,      /* grid modes: CTA count (0 = one per SM)             */
-    MP_OPT_BATCH_TILE_N = 5,   /* batched: atoms per GEMM tile (0 = autotuned)       */
+    MP_OPT_BATCH_TILE_N = 5,   /* batched: atoms per GEMM tile, 128..256 in steps of */
+                               /* 32 (0 = autotuned)                                 */
     MP_OPT_PLAIN_PREFETCH = 6, /* grid streaming: stages pulled into L2 ahead of the */
                                /* shared-memory ring (0 = off, the default)          */
                                /* (7: no longer used)                                */
@@ -195,8 +196,7 @@ typedef enum {
                                /* MMAs (tcgen05 cta_group::2), each SM holding a     */
                                /* 128 x TILE_N accumulator twice so the top-8 of one */
                                /* tile runs under the MMAs of the next.  0 = the     */
-                               /* autotuner decides (default), 1 = off, 2 = on; with */
-                               /* it on TILE_N may be 128..256 in steps of 32.  The  */
+                               /* autotuner decides (default), 1 = off, 2 = on.  The */
                                /* candidates (and so the results) do not depend on   */
                                /* the tile shape.                                    */
 } mp_option;
@@ -374,8 +374,9 @@ MPGB_API mp_status mp_recover_batched(mp_plan_t plan, int prec, const float* Y, 
                              mp_result* host_out, void* stream);
 
 /* Autotuner of the batched correlation GEMM: times each tile shape (128 or
- * 256 signals per tile; 128 or 256 atoms per tile) on B synthetic rows at
- * precision `prec`, keeps the fastest for B's size bucket (the next power
+ * 256 signals per tile; 128, 224 or 256 atoms per tile) on B synthetic rows
+ * and on B/4 (a batch drains as its signals stop) at precision `prec`, keeps
+ * the fastest sum for B's size bucket (the next power
  * of two, at least 128) and returns it.  With the default
  * MP_OPT_BATCH_AUTOTUNE = 1, mp_recover_batched runs the same timing on its
  * own first batch of a new bucket.  Options MP_OPT_BATCH_TILE_N /
@@ -400,7 +401,7 @@ MPGB_API mp_status mp_debug_correlations(mp_plan_t plan, int prec, const float* 
  * epilogue, one launch per step) on B synthetic rows at precision `prec`:
  * the autotuner's timing routine, mean of `reps` launches after 2 warm-up
  * launches, written to *us in microseconds per launch.  Tile shape
- * (tile_m signals x tile_n atoms): 128 or 256 each; both 0 = the shape
+ * (tile_m signals x tile_n atoms): tile_m 128 or 256, tile_n 128..256 in steps of 32; both 0 = the shape
  * mp_recover_batched would use for B signals (options, else autotuned).
  * Allocates its own buffers; synchronises the legacy default stream.
  * Errors: MP_ERR_INVALID (bad shape or argument), MP_ERR_UNSUPPORTED

@@ -1337,8 +1337,6 @@ mp_status batch_shape(PlanImpl* p, int prec, int B, const float* R, cudaStream_t
     }
     if (p->batch_tile_n) g.tn = p->batch_tile_n;
     if (p->batch_tile_m && !g.pair) g.tm = p->batch_tile_m;
-    if (!g.pair && g.tn != 128 && g.tn != 256)
-        return fail(MP_ERR_INVALID, "batched GEMM: single-CTA tiles take 128 or 256 atoms");
     *shape = g;
     return MP_OK;
 }
@@ -1357,7 +1355,8 @@ mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const 
     if (gram_R > 0 && (prec != MP_PREC_BF16 || !p->gram))
         return fail(MP_ERR_UNSUPPORTED, "batched Gram mode: BF16 plans only, after the plan's Gram matrix is built");
     const int TN = g.tn;
-    if (g.pair ? (g.tm != 256 || TN < 128 || TN > 256 || TN % 32) : ((g.tm != 128 && g.tm != 256) || (TN != 128 && TN != 256)))
+    if (g.pair ? g.tm != 256 : (g.tm != 128 && g.tm != 256)) return fail(MP_ERR_INVALID, "batched GEMM: unsupported tile shape");
+    if (TN < 128 || TN > 256 || TN % 32)
         return fail(MP_ERR_INVALID, "batched GEMM: unsupported tile shape");
     e->pair = g.pair;
     e->gram_R = gram_R;
@@ -1983,7 +1982,7 @@ mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_
     };
     for (int tm : {128, 256}) {
         if (tm == 256 && rt < 2) continue;      // one row block: the same work as 128
-        for (int tn : {256, 128}) {
+        for (int tn : {256, 224, 128}) {
             GemmShape g;
             g.tm = tm;
             g.tn = tn;
@@ -2051,8 +2050,8 @@ mp_status mp_debug_time_gemm_pair(mp_plan_t plan, int prec, int B, int tile_m, i
         return fail(MP_ERR_UNSUPPORTED, "mp_debug_time_gemm: the plan holds no copy for this precision");
     GemmShape g;
     if (tile_m || tile_n || pair) {
-        const bool ok = pair == 1 ? (tile_m == 256 && tile_n >= 128 && tile_n <= 256 && tile_n % 32 == 0)
-                                  : (pair == 0 && (tile_m == 128 || tile_m == 256) && (tile_n == 128 || tile_n == 256));
+        const bool tn_ok = tile_n >= 128 && tile_n <= 256 && tile_n % 32 == 0;
+        const bool ok = tn_ok && (pair == 1 ? tile_m == 256 : (pair == 0 && (tile_m == 128 || tile_m == 256)));
         if (!ok) return fail(MP_ERR_INVALID, "mp_debug_time_gemm: bad tile shape");
         g.tm = tile_m;
         g.tn = tile_n;

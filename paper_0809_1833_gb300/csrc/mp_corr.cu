@@ -110,6 +110,50 @@ MP_DEV void colscale8(const float* __restrict__ cs, int m, int M, float (&out)[8
     }
 }
 
+// The running top 8 (keys tk) of one signal row over `ncols` accumulator
+// columns (a multiple of 8) at TMEM address taddr: tile columns col0..,
+// atoms m0...  Optionally dumps the correlations (diagnostic).
+template <bool FP8>
+MP_DEV void offer8(const float* v, int col, int m, const CorrArgs& a, int row, bool dump_row, uint32_t (&tk)[8]) {
+    uint32_t ck[8];
+    float cs8[8];
+    if (FP8) colscale8(a.colscale, m, a.M, cs8);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const bool in = m + j < a.M;
+        float sc = fabsf(v[j]);
+        if (FP8) sc *= cs8[j];
+        ck[j] = (in && sc <= 3.0e38f) ? score_key(sc, col + j) : 0u;
+        if (dump_row && in)
+            a.dump[static_cast<size_t>(row) * a.M + m + j] = v[j] * (FP8 ? a.colscale[m + j] * a.rscale[row] : 1.f);
+    }
+    sort8_desc(ck);
+    merge_top8(tk, ck);
+}
+template <bool FP8>
+MP_DEV void scan_top8(uint32_t taddr, int ncols, int col0, int m0, const CorrArgs& a, int row, bool dump_row,
+                      uint32_t (&tk)[8]) {
+    int c = 0;
+    for (; c + 32 <= ncols; c += 32) {
+        float v[32];
+        tmem_ld_32cols(taddr + static_cast<uint32_t>(c), v);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) offer8<FP8>(v + 8 * h, col0 + c + 8 * h, m0 + c + 8 * h, a, row, dump_row, tk);
+    }
+    if (c + 16 <= ncols) {
+        float v[16];
+        tmem_ld_16cols(taddr + static_cast<uint32_t>(c), v);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) offer8<FP8>(v + 8 * h, col0 + c + 8 * h, m0 + c + 8 * h, a, row, dump_row, tk);
+        c += 16;
+    }
+    if (c + 8 <= ncols) {
+        float v[8];
+        tmem_ld_8cols(taddr + static_cast<uint32_t>(c), v);
+        offer8<FP8>(v, col0 + c, m0 + c, a, row, dump_row, tk);
+    }
+}
+
 struct CorrShared {
     uint64_t full[kMaxStages];
     uint64_t empty[kMaxStages];
@@ -148,7 +192,7 @@ struct CorrCtx {
 
 // The producer, MMA and epilogue roles over this CTA's tiles of RM 128-row
 // blocks x TN atoms.
-template <int RM, int KS>
+template <int RM, int KS, bool TAIL>
 MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmA3,
                        const CUtensorMap* tmB3, const CorrArgs& a, const CorrCtx& x) {
     const int TN = a.TN;      // stage and accumulator strides
@@ -365,6 +409,17 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUt
                         merge_top8(tk, ck);
                     }
                 }
+                // column groups that are not whole 32-column chunks (TN = 160
+                // or 224, the TAIL instantiation): their last 16 and / or 8
+                // columns
+                if (TAIL && c_end > 0 && (cols & 31)) {
+                    const int c0 = (cols / 32) * 32;
+                    const uint32_t taddr = tmem + (static_cast<uint32_t>(quad * 32) << 16) +
+                                           static_cast<uint32_t>((buf * RM + mb) * TN + grp * cols + c0);
+                    const bool dump_row = a.dump && row < n_act;
+                    if (a.fp8) scan_top8<true>(taddr, cols - c0, grp * cols + c0, m0 + c0, a, row, dump_row, tk);
+                    else scan_top8<false>(taddr, cols - c0, grp * cols + c0, m0 + c0, a, row, dump_row, tk);
+                }
                 if (mb == nmb - 1) {
                     // the buffer's last columns are in registers: the MMAs may reuse it
                     tc_fence_before();
@@ -421,7 +476,7 @@ MP_DEV void corr_roles(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUt
 // RM = 2: 256-row tiles while the batch has more 128-row tiles than the
 // grid has CTAs, 128-row tiles once it has drained below that (the choice
 // is made per launch from the active row count, the same in every CTA).
-template <int RM>
+template <int RM, bool TAIL>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     corr_top8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmA3,
@@ -510,12 +565,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
     const CUtensorMap* mb = x.tn == a.TN ? &tmB : &tmBh;
     if constexpr (RM == 2) {
-        if (rm == 2) corr_roles<2, 1>(&tmA, mb, &tmA3, &tmB3, a, x);
-        else if (x.ks == 2) corr_roles<1, 2>(&tmA, mb, &tmA3, &tmB3, a, x);
-        else corr_roles<1, 1>(&tmA, mb, &tmA3, &tmB3, a, x);
+        if (rm == 2) corr_roles<2, 1, TAIL>(&tmA, mb, &tmA3, &tmB3, a, x);
+        else if (x.ks == 2) corr_roles<1, 2, false>(&tmA, mb, &tmA3, &tmB3, a, x);
+        else corr_roles<1, 1, TAIL>(&tmA, mb, &tmA3, &tmB3, a, x);
     } else {
-        if (x.ks == 2) corr_roles<1, 2>(&tmA, mb, &tmA3, &tmB3, a, x);
-        else corr_roles<1, 1>(&tmA, mb, &tmA3, &tmB3, a, x);
+        if (x.ks == 2) corr_roles<1, 2, false>(&tmA, mb, &tmA3, &tmB3, a, x);
+        else corr_roles<1, 1, TAIL>(&tmA, mb, &tmA3, &tmB3, a, x);
     }
 
     tc_fence_before();
@@ -535,50 +590,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 // runs under the MMAs of the next, at the bytes per flop of a 256 x 256
 // single-CTA tile.  Tiles are ordered row pair fastest, so the clusters
 // running at one time share the atom tile they stream.
-
-// The running top 8 (keys tk) of one signal row over `ncols` accumulator
-// columns (a multiple of 8) at TMEM address taddr: tile columns col0..,
-// atoms m0...  Optionally dumps the correlations (diagnostic).
-template <bool FP8>
-MP_DEV void offer8(const float* v, int col, int m, const CorrArgs& a, int row, bool dump_row, uint32_t (&tk)[8]) {
-    uint32_t ck[8];
-    float cs8[8];
-    if (FP8) colscale8(a.colscale, m, a.M, cs8);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const bool in = m + j < a.M;
-        float sc = fabsf(v[j]);
-        if (FP8) sc *= cs8[j];
-        ck[j] = (in && sc <= 3.0e38f) ? score_key(sc, col + j) : 0u;
-        if (dump_row && in)
-            a.dump[static_cast<size_t>(row) * a.M + m + j] = v[j] * (FP8 ? a.colscale[m + j] * a.rscale[row] : 1.f);
-    }
-    sort8_desc(ck);
-    merge_top8(tk, ck);
-}
-template <bool FP8>
-MP_DEV void scan_top8(uint32_t taddr, int ncols, int col0, int m0, const CorrArgs& a, int row, bool dump_row,
-                      uint32_t (&tk)[8]) {
-    int c = 0;
-    for (; c + 32 <= ncols; c += 32) {
-        float v[32];
-        tmem_ld_32cols(taddr + static_cast<uint32_t>(c), v);
-#pragma unroll
-        for (int h = 0; h < 4; ++h) offer8<FP8>(v + 8 * h, col0 + c + 8 * h, m0 + c + 8 * h, a, row, dump_row, tk);
-    }
-    if (c + 16 <= ncols) {
-        float v[16];
-        tmem_ld_16cols(taddr + static_cast<uint32_t>(c), v);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) offer8<FP8>(v + 8 * h, col0 + c + 8 * h, m0 + c + 8 * h, a, row, dump_row, tk);
-        c += 16;
-    }
-    if (c + 8 <= ncols) {
-        float v[8];
-        tmem_ld_8cols(taddr + static_cast<uint32_t>(c), v);
-        offer8<FP8>(v, col0 + c, m0 + c, a, row, dump_row, tk);
-    }
-}
 
 // Per-CTA state of the paired kernel.
 struct PairCtx {
@@ -867,17 +878,20 @@ int corr_smem_bytes(int TM, int TN) {
     return 1024 + corr_stages(TM, TN) * (TM * kRowBytes + TN * kRowBytes) + static_cast<int>(sizeof(CorrShared));
 }
 
-template <int RM>
+template <int RM, bool TAIL>
 static cudaError_t set_attrs() {
-    const int most = std::max(corr_smem_bytes(kBM * RM, 128), corr_smem_bytes(kBM * RM, 256));
-    return cudaFuncSetAttribute(corr_top8_kernel<RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    int most = 0;
+    for (int tn = 128; tn <= 256; tn += 32) most = std::max(most, corr_smem_bytes(kBM * RM, tn));
+    return cudaFuncSetAttribute(corr_top8_kernel<RM, TAIL>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
 }
 
 cudaError_t corr_prepare() {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = set_attrs<1>();
-    if (e == cudaSuccess) e = set_attrs<2>();
+    cudaError_t e = set_attrs<1, false>();
+    if (e == cudaSuccess) e = set_attrs<2, false>();
+    if (e == cudaSuccess) e = set_attrs<1, true>();
+    if (e == cudaSuccess) e = set_attrs<2, true>();
     if (e == cudaSuccess) done = true;
     return e;
 }
@@ -901,7 +915,7 @@ cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, con
                              const CUtensorMap& tmA3, const CUtensorMap& tmB3, const CorrArgs& a, int max_rows,
                              cudaStream_t st) {
     const int nbuf = (a.RM == 1 || a.RM * a.TN * 2 <= 512) ? 2 : 1;   // as the kernel computes it
-    if ((a.RM != 1 && a.RM != 2) || nbuf * a.RM * a.TN > a.tmem_cols ||
+    if ((a.RM != 1 && a.RM != 2) || a.TN < 128 || a.TN > 256 || a.TN % 32 || nbuf * a.RM * a.TN > a.tmem_cols ||
         a.stages != corr_stages(kBM * a.RM, a.TN) || (a.half_ok && a.TN != 256))
         return cudaErrorInvalidValue;
     // enough CTAs for the largest tile count this launch can see (with
@@ -913,8 +927,16 @@ cudaError_t launch_corr_top8(const CUtensorMap& tmA, const CUtensorMap& tmB, con
         max_ct = std::max(max_ct, std::min(max_rt, 2) * ((a.M + a.TN / 2 - 1) / (a.TN / 2)));
     const int ctas = std::max(1, std::min(max_ct, corr_max_ctas()));
     const int smem = corr_smem_bytes(kBM * a.RM, a.TN);
-    if (a.RM == 2) corr_top8_kernel<2><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, tmA3, tmB3, a);
-    else corr_top8_kernel<1><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, tmA3, tmB3, a);
+    // column groups of TN / 4 that are not whole 32-column chunks need the
+    // tail scan (TN = 160, 224)
+    const bool tail = (a.TN / kEpiGroups) % 32 != 0;
+    if (a.RM == 2) {
+        if (tail) corr_top8_kernel<2, true><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, tmA3, tmB3, a);
+        else corr_top8_kernel<2, false><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, tmA3, tmB3, a);
+    } else {
+        if (tail) corr_top8_kernel<1, true><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, tmA3, tmB3, a);
+        else corr_top8_kernel<1, false><<<ctas, kGemmThreads, smem, st>>>(tmA, tmB, tmBh, tmA3, tmB3, a);
+    }
     return cudaGetLastError();
 }
 

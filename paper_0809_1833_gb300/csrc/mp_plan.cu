@@ -343,7 +343,7 @@ mp_status mp_plan_set_option(mp_plan_t plan, int option, long long value) {
             p->batch_autotune = value ? 1 : 0;
             return MP_OK;
         case MP_OPT_BATCH_TILE_N:
-            // 128 or 256 for single-CTA tiles; two-SM tiles also take 160, 192, 224
+            // 128, 160, 192, 224 or 256 atoms per tile
             if (value != 0 && (value < 128 || value > 256 || value % 32))
                 return fail(MP_ERR_INVALID, "batch tile must be 0 or 128..256 in steps of 32");
             p->batch_tile_n = static_cast<int>(value);

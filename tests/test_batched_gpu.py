@@ -45,7 +45,7 @@ def e4m3_rows(a):
 
 
 # (signals per tile, atoms per tile)
-TILES = [(128, 256), (128, 128), (256, 256), (256, 128)]
+TILES = [(128, 256), (128, 128), (256, 256), (256, 128), (256, 224), (128, 160)]
 
 
 @pytest.mark.parametrize("tile", TILES, ids=lambda t: f"TM{t[0]}_TN{t[1]}")
@@ -249,14 +249,15 @@ def test_pair_option_checks():
             with pytest.raises(B().MpError) as ei:
                 pl.set(B().MP_OPT_BATCH_TILE_N, bad)
             assert ei.value.status == B().MP_ERR_INVALID
-        # 224 atoms per tile is a two-SM width only
+        # 224 atoms per tile on single-CTA tiles, then on two-SM tiles
         pl.set(B().MP_OPT_BATCH_PAIR, 1)
         pl.set(B().MP_OPT_BATCH_TILE_N, 224)
-        s, _, _, _, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
-        assert s == B().MP_ERR_INVALID
+        s, res1, X1, _, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
+        assert s == 0 and pl.query(B().MP_Q_BATCH_PAIR) == 0 and pl.query(B().MP_Q_BATCH_TILE_N) == 224
         pl.set(B().MP_OPT_BATCH_PAIR, 2)
         s, res, X, atoms, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
         assert s == 0 and pl.query(B().MP_Q_BATCH_PAIR) == 1 and pl.query(B().MP_Q_BATCH_TILE_N) == 224
+        assert np.array_equal(X, X1)
         for b in range(prob.B):
             ora = orc.mp(psi, prob.y[b], prob.eps, prob.T)
             assert list(atoms[b, :res[b].iters]) == list(ora["atoms"])
@@ -306,7 +307,7 @@ def test_autotuner_picks_a_valid_shape_and_results_do_not_depend_on_it():
         if pair:
             assert tm == 256 and tn in (192, 224, 256)
         else:
-            assert tn in (128, 256) and tm in (128, 256)
+            assert tn in (128, 224, 256) and tm in (128, 256)
         assert B().mp_plan_autotune_shape(pl.plan, p, prob.B) == (tn, tm, pair)   # cached per size bucket
         assert B().mp_plan_autotune(pl.plan, p, prob.B) == (tn, tm)
         s, res, X, _, _ = run_batched(pl, p, prob.y, (prob.eps, prob.T))
@@ -362,7 +363,7 @@ def test_gemm_timing_diagnostic():
         for shape in [(0, 0)] + [t for t in TILES] + [(256, tn, 1) for tn in PAIR_TN]:
             us = B().mp_debug_time_gemm(pl.plan, p, 300, shape, reps=3)
             assert 0.0 < us < 1e6, (shape, us)
-        for bad in [(192, 256), (128, 64), (256, 100), (64, 128), (256, 0), (256, 224), (128, 256, 1),
+        for bad in [(192, 256), (128, 64), (256, 100), (64, 128), (256, 0), (256, 200), (128, 256, 1),
                     (256, 96, 1), (256, 200, 1), (256, 288, 1), (256, 256, 2)]:
             with pytest.raises(B().MpError) as ei:
                 B().mp_debug_time_gemm(pl.plan, p, 300, bad, reps=3)
