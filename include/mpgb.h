@@ -191,7 +191,7 @@ typedef enum {
                                /* of G per signal and no GEMM runs.  Whenever the    */
                                /* FP32 argmax is among the 8 candidates the result   */
                                /* equals the plain FP32 decode's bit for bit.        */
-    MP_OPT_BATCH_PAIR = 15     /* batched GEMM on two-SM tiles: a cluster of two     */
+    MP_OPT_BATCH_PAIR = 15,    /* batched GEMM on two-SM tiles: a cluster of two     */
                                /* CTAs takes 256 signals x TILE_N atoms with M = 256 */
                                /* MMAs (tcgen05 cta_group::2), each SM holding a     */
                                /* 128 x TILE_N accumulator twice so the top-8 of one */
@@ -199,6 +199,26 @@ typedef enum {
                                /* autotuner decides (default), 1 = off, 2 = on.  The */
                                /* candidates (and so the results) do not depend on   */
                                /* the tile shape.                                    */
+    MP_OPT_BATCH_GRAM_BELOW = 16 /* mp_recover_batched with MP_OPT_BATCH_GRAM = R > 0: */
+                               /* a threshold S >= 1 switches the decode from direct */
+                               /* steps (BF16 tcgen05 GEMM + FP32 rescore) to        */
+                               /* Gram-updated steps once at most S signals are      */
+                               /* still active (0 = off, the default: every step is  */
+                               /* a Gram step).  Not in the paper: a direct step     */
+                               /* costs a GEMM whose time barely falls as the batch  */
+                               /* drains (every tile reads the whole K extent of its */
+                               /* atoms and signals), a Gram step one row of G per   */
+                               /* active signal.  At the switch the correlations of  */
+                               /* every active signal are computed directly from the */
+                               /* FP32 atoms; after it they are refreshed every R of */
+                               /* the signal's own steps.  The switch comes between  */
+                               /* graph replays (16 steps), the first replay after   */
+                               /* the count is seen at or below S; a batch of at     */
+                               /* most S signals starts with Gram steps.  Selections */
+                               /* are the FP32 rescore's in both kinds of step, so   */
+                               /* whenever the FP32 argmax is among the 8 candidates */
+                               /* the result equals the direct decode's bit for bit. */
+                               /* The server ignores this option.                    */
 } mp_option;
 
 /* Read-only plan properties for mp_plan_query. */
@@ -225,7 +245,9 @@ typedef enum {
                                /* stage: ring stages per atom (an atom streams as    */
                                /* that many pieces); 0 when warps own whole atoms    */
     MP_Q_BATCH_GRAM = 19,      /* Gram period of the current batch state (0: off)    */
-    MP_Q_BATCH_PAIR = 20       /* 1 if the current batch state uses two-SM tiles     */
+    MP_Q_BATCH_PAIR = 20,      /* 1 if the current batch state uses two-SM tiles     */
+    MP_Q_BATCH_GRAM_BELOW = 21 /* switch threshold of the current batch state (0:   */
+                               /* no switch)                                          */
 } mp_query;
 
 /* ------------------------------------------------------------------ */

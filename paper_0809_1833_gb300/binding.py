@@ -44,10 +44,12 @@ MP_OPT_PLAIN_L2_KEEP_BYTES = 12
 MP_OPT_BATCH_TILE_M = 13
 MP_OPT_BATCH_GRAM = 14
 MP_OPT_BATCH_PAIR = 15
+MP_OPT_BATCH_GRAM_BELOW = 16
 MP_Q_BATCH_TILE_N = 10
 MP_Q_BATCH_TILE_M = 17
 MP_Q_BATCH_GRAM = 19
 MP_Q_BATCH_PAIR = 20
+MP_Q_BATCH_GRAM_BELOW = 21
 
 MP_Q_PLAIN_MODE = 1
 MP_Q_PLAIN_CTAS = 2

@@ -148,9 +148,17 @@ struct BatchEngine {
     float* Cg = nullptr;
     int ldC = 0;
     unsigned long long* gtop = nullptr;
+    // Switched mode (gram_below > 0, with gram_R > 0): the decode runs direct
+    // GEMM steps (`graph`) while more than gram_below signals are active,
+    // then computes every active signal's correlations directly once and
+    // runs Gram-updated steps (`graph_g`) to the end.  Admission computes no
+    // correlation rows in this mode.
+    int gram_below = 0;
     cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph_g = nullptr;
     int graph_steps = 0;
     int graph_kernels = 0;          // kernels one replay of the graph launches
+    int graph_g_kernels = 0;        // the same for graph_g
     bool graph_retire = false;
     cudaStream_t cap_stream = nullptr;
     cudaEvent_t cnt_ready[2] = {nullptr, nullptr};   // active-count reads of alternate replays
@@ -161,8 +169,10 @@ struct BatchEngine {
 // state, an output row of M floats when the engine owns X).
 size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x, int gram_R = 0);
 // gram_R: 0, or the Gram mode's refresh period (a multiple of 16; BF16 or
-// FP32 plans; the plan's Gram matrix must exist)
-mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int cap, const GemmShape& shape, int gram_R = 0);
+// FP32 plans; the plan's Gram matrix must exist); gram_below > 0 (with
+// gram_R > 0): the switched mode
+mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int cap, const GemmShape& shape, int gram_R = 0,
+                       int gram_below = 0);
 void engine_free(BatchEngine* e);
 // Admit n signals: rows Y (device, n x N), into slots `slots_dev` (device,
 // NULL = 0..n-1), with per-signal eps^2 and T already in e->eps2 / e->T.

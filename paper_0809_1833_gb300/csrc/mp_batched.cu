@@ -1296,6 +1296,7 @@ static mp_status make_map3(CUtensorMap* map, void* base, bool fp8, long long row
 void engine_free(BatchEngine* e) {
     if (!e) return;
     if (e->graph) cudaGraphExecDestroy(e->graph);
+    if (e->graph_g) cudaGraphExecDestroy(e->graph_g);
     if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
     for (cudaEvent_t ev : e->cnt_ready)
         if (ev) cudaEventDestroy(ev);
@@ -1341,25 +1342,30 @@ mp_status batch_shape(PlanImpl* p, int prec, int B, const float* R, cudaStream_t
     return MP_OK;
 }
 
-static mp_status engine_prepare(PlanImpl* p, int prec, int cap, const GemmShape& g, int gram_R = 0) {
+static mp_status engine_prepare(PlanImpl* p, int prec, int cap, const GemmShape& g, int gram_R = 0,
+                                int gram_below = 0) {
     BatchEngine* e = p->batch;
     if (e && e->prec == prec && e->cap >= cap && e->TM == g.tm && e->TN == g.tn && e->pair == g.pair &&
-        e->gram_R == gram_R)
+        e->gram_R == gram_R && e->gram_below == gram_below)
         return MP_OK;
     if (!e) e = p->batch = new BatchEngine();
-    return engine_alloc(e, p, prec, std::max(cap, e->cap), g, gram_R);
+    return engine_alloc(e, p, prec, std::max(cap, e->cap), g, gram_R, gram_below);
 }
 
-mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const GemmShape& g, int gram_R) {
+mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const GemmShape& g, int gram_R,
+                       int gram_below) {
     engine_free(e);
     if (gram_R > 0 && (prec != MP_PREC_BF16 || !p->gram))
         return fail(MP_ERR_UNSUPPORTED, "batched Gram mode: BF16 plans only, after the plan's Gram matrix is built");
+    if (gram_below < 0 || (gram_below > 0 && gram_R <= 0))
+        return fail(MP_ERR_INVALID, "batched switched mode: needs a Gram period");
     const int TN = g.tn;
     if (g.pair ? g.tm != 256 : (g.tm != 128 && g.tm != 256)) return fail(MP_ERR_INVALID, "batched GEMM: unsupported tile shape");
     if (TN < 128 || TN > 256 || TN % 32)
         return fail(MP_ERR_INVALID, "batched GEMM: unsupported tile shape");
     e->pair = g.pair;
     e->gram_R = gram_R;
+    e->gram_below = gram_below;
     e->cap = newcap;
     e->cap_pad = (newcap + kBM - 1) / kBM * kBM;
     e->prec = prec;
@@ -1494,12 +1500,13 @@ static bool gram_rows_in_smem(const PlanImpl* p, const BatchEngine* e) {
 // Gram mode a step is the select kernel alone: its candidates are each
 // slot's carried top 8, and it updates the slot's correlation row from G.
 // Adds the kernels launched to *kernels.
-static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, cudaStream_t st, int* kernels) {
+// gram: a Gram-updated step (select kernel only) instead of a direct one
+// (GEMM, then select)
+static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, bool gram, cudaStream_t st, int* kernels) {
     int* fin_count = e->counters + 2;
     int* fin_list = e->fin_list;
     int* cnt[2] = {e->counters, e->counters + 3};
     const size_t qbytes = static_cast<size_t>(e->cap_pad) * e->ldq * (e->prec == MP_PREC_FP8E4M3 ? 1 : 2);
-    const bool gram = e->gram_R > 0;
     cudaError_t r = cudaSuccess;
     if (!gram) {
         CorrArgs ca = corr_args(p, e);
@@ -1591,43 +1598,20 @@ static cudaError_t launch_gram_refresh(PlanImpl* p, BatchEngine* e, const int* r
     return cudaGetLastError();
 }
 
-mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire, float* out_x, SlotState* out_state,
-                             int* out_list, int* out_count) {
-    if (steps <= 0 || steps % 2) return fail(MP_ERR_INVALID, "batched step graph: an even number of steps");
-    if (e->graph && e->graph_steps == steps && e->graph_retire == retire) return MP_OK;
-    if (e->graph) {
-        cudaGraphExecDestroy(e->graph);
-        e->graph = nullptr;
-    }
-    if (!e->cap_stream) MP_CUDA_TRY(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
-    MP_CUDA_TRY(corr_prepare());
-    MP_CUDA_TRY(pair_prepare());
-    if (p->ldN * 4 > 48 * 1024) {
-        const int b = p->ldN * 4;
-        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<kSumChains>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-
-    }
-    if (e->gram_R > 0) {
-        MP_CUDA_TRY(cudaFuncSetAttribute(gram_select_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         gram_smem_bytes(p, e, true)));
-        MP_CUDA_TRY(cudaFuncSetAttribute(gram_select_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         gram_smem_bytes(p, e, false)));
-    }
-    if (e->gram_R > 0 && (e->gram_R % steps || !p->gram))
-        return fail(MP_ERR_INVALID, "batched step graph: the Gram period must be a multiple of the steps per graph");
+// Capture `steps` steps of one kind (direct or Gram-updated), optionally
+// followed by the retire copy, and instantiate them into *out.
+static mp_status capture_steps(PlanImpl* p, BatchEngine* e, int steps, bool gram, bool retire, float* out_x,
+                               SlotState* out_state, int* out_list, int* out_count, cudaGraphExec_t* out,
+                               int* out_kernels) {
     MP_CUDA_TRY(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t r = cudaSuccess;
     int kernels = 0;
-    // Gram mode: a replay starts with every active slot's step count a
+    // Gram steps: a replay starts with every active slot's step count a
     // multiple of `steps` (signals join between replays and each step moves
     // every active signal by one); the slots at a multiple of the period get
     // their correlations recomputed directly
-    if (e->gram_R > 0)
-        r = launch_gram_refresh(p, e, e->act, e->counters, e->cap, e->gram_R, e->cap_stream, &kernels);
-    for (int s = 0; s < steps && r == cudaSuccess; ++s) r = launch_step(p, e, s & 1, e->cap_stream, &kernels);
+    if (gram) r = launch_gram_refresh(p, e, e->act, e->counters, e->cap, e->gram_R, e->cap_stream, &kernels);
+    for (int s = 0; s < steps && r == cudaSuccess; ++s) r = launch_step(p, e, s & 1, gram, e->cap_stream, &kernels);
     if (retire && r == cudaSuccess) {
         RetireArgs ra;
         ra.fin_count = e->counters + 2;
@@ -1651,12 +1635,62 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
         return cuda_fail(r, "batched step capture");
     }
     if (r2 != cudaSuccess) return cuda_fail(r2, "cudaStreamEndCapture");
-    r = cudaGraphInstantiate(&e->graph, g, 0);
+    r = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (r != cudaSuccess) return cuda_fail(r, "cudaGraphInstantiate");
+    *out_kernels = kernels;
+    return MP_OK;
+}
+
+mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire, float* out_x, SlotState* out_state,
+                             int* out_list, int* out_count) {
+    if (steps <= 0 || steps % 2) return fail(MP_ERR_INVALID, "batched step graph: an even number of steps");
+    if (e->graph && e->graph_steps == steps && e->graph_retire == retire) return MP_OK;
+    if (e->graph) {
+        cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+    }
+    if (e->graph_g) {
+        cudaGraphExecDestroy(e->graph_g);
+        e->graph_g = nullptr;
+    }
+    if (e->gram_below > 0 && retire)
+        return fail(MP_ERR_UNSUPPORTED, "batched step graph: the switched mode has no retiring graph");
+    if (!e->cap_stream) MP_CUDA_TRY(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
+    MP_CUDA_TRY(corr_prepare());
+    MP_CUDA_TRY(pair_prepare());
+    if (p->ldN * 4 > 48 * 1024) {
+        const int b = p->ldN * 4;
+        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<2 * kSumChains>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MP_CUDA_TRY(cudaFuncSetAttribute(select_update_kernel<kSumChains>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+
+    }
+    if (e->gram_R > 0) {
+        MP_CUDA_TRY(cudaFuncSetAttribute(gram_select_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         gram_smem_bytes(p, e, true)));
+        MP_CUDA_TRY(cudaFuncSetAttribute(gram_select_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         gram_smem_bytes(p, e, false)));
+    }
+    if (e->gram_R > 0 && (e->gram_R % steps || !p->gram))
+        return fail(MP_ERR_INVALID, "batched step graph: the Gram period must be a multiple of the steps per graph");
+    // the main graph: Gram steps in the Gram mode, direct steps otherwise
+    // (the switched mode starts direct); the switched mode's Gram steps in
+    // a second graph
+    const bool gram_main = e->gram_R > 0 && e->gram_below == 0;
+    mp_status s = capture_steps(p, e, steps, gram_main, retire, out_x, out_state, out_list, out_count, &e->graph,
+                                &e->graph_kernels);
+    if (s == MP_OK && e->gram_below > 0)
+        s = capture_steps(p, e, steps, true, false, nullptr, nullptr, nullptr, nullptr, &e->graph_g,
+                          &e->graph_g_kernels);
+    if (s != MP_OK) {
+        if (e->graph) cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+        return s;
+    }
     e->graph_steps = steps;
     e->graph_retire = retire;
-    e->graph_kernels = kernels;
     return MP_OK;
 }
 
@@ -1692,8 +1726,9 @@ cudaError_t engine_admit(PlanImpl* p, BatchEngine* e, const float* Y, int n, con
     cudaError_t r = cudaGetLastError();
     if (r != cudaSuccess) return r;
     p->launches++;
-    if (e->gram_R > 0) {
+    if (e->gram_R > 0 && e->gram_below == 0) {
         // the Gram mode starts every signal from its direct FP32 correlations
+        // (the switched mode computes them when it switches)
         int k = 0;
         r = launch_gram_refresh(p, e, slots_dev, nullptr, n, 0, st, &k);
         p->launches += k;
@@ -1713,7 +1748,8 @@ static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, lo
         s = gram_prepare(p, st);
         if (s != MP_OK) return s;
     }
-    s = engine_prepare(p, prec, B, g, p->batch_gram);
+    const int gram_below = p->batch_gram > 0 ? p->batch_gram_below : 0;
+    s = engine_prepare(p, prec, B, g, p->batch_gram, gram_below);
     if (s != MP_OK) return s;
     BatchEngine* e = p->batch;
     s = engine_build_graph(p, e, kStepsPerGraph, false, nullptr, nullptr, nullptr, nullptr);
@@ -1743,6 +1779,26 @@ static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, lo
     MP_CUDA_TRY(cudaMemsetAsync(e->counters, 0, sizeof(int) * 8, st));
     // signal b -> slot b, GEMM row b; then drop those that need no iteration
     MP_CUDA_TRY(engine_admit(p, e, Y, B, nullptr, st));
+    // Switched mode: from direct steps to Gram-updated ones.  Between
+    // replays the active rows are half 0's (count counters[0]); every active
+    // signal gets its correlations computed directly from the FP32 atoms
+    // (and its 8 largest), and the count the first Gram step's survivors
+    // append to (half 1's, left over from the last direct step, which a GEMM
+    // would have cleared) is cleared.
+    bool gram_steps = false;
+    auto switch_to_gram = [&]() -> mp_status {
+        MP_CUDA_TRY(cudaMemsetAsync(e->counters + 3, 0, sizeof(int), st));
+        int k = 0;
+        MP_CUDA_TRY(launch_gram_refresh(p, e, e->act, e->counters, e->cap, 0, st, &k));
+        p->launches += k;
+        gram_steps = true;
+        return MP_OK;
+    };
+    // a batch no larger than the threshold starts with Gram steps
+    if (gram_below > 0 && B <= gram_below) {
+        s = switch_to_gram();
+        if (s != MP_OK) return s;
+    }
     // replay the captured steps until no signal is active (each step moves
     // every active signal by one iteration, so maxT steps always suffice).
     // Replay k is queued before the active count after replay k - 1 is
@@ -1752,13 +1808,20 @@ static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, lo
         if (!e->cnt_ready[j]) MP_CUDA_TRY(cudaEventCreateWithFlags(&e->cnt_ready[j], cudaEventDisableTiming));
     const long long max_replays = (static_cast<long long>(maxT) + kStepsPerGraph - 1) / kStepsPerGraph + 1;
     for (long long k = 0; k < max_replays; ++k) {
-        MP_CUDA_TRY(cudaGraphLaunch(e->graph, st));
-        p->launches += e->graph_kernels;
+        MP_CUDA_TRY(cudaGraphLaunch(gram_steps ? e->graph_g : e->graph, st));
+        p->launches += gram_steps ? e->graph_g_kernels : e->graph_kernels;
         MP_CUDA_TRY(cudaMemcpyAsync(e->h_cnt + (k & 1), e->counters, sizeof(int), cudaMemcpyDeviceToHost, st));
         MP_CUDA_TRY(cudaEventRecord(e->cnt_ready[k & 1], st));
         if (k > 0) {
             MP_CUDA_TRY(cudaEventSynchronize(e->cnt_ready[(k - 1) & 1]));
-            if (e->h_cnt[(k - 1) & 1] == 0) break;
+            const int n_left = e->h_cnt[(k - 1) & 1];
+            if (n_left == 0) break;
+            // the count after replay k - 1 reached the threshold: switch
+            // after replay k (already queued; it holds at most that many)
+            if (gram_below > 0 && !gram_steps && n_left <= gram_below) {
+                s = switch_to_gram();
+                if (s != MP_OK) return s;
+            }
         }
     }
     // each signal's final FP32 residual (slot b = signal b), for callers that

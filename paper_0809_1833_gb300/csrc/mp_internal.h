@@ -158,6 +158,8 @@ struct PlanImpl {
     long long l2_keep_bytes = 0;    // plain streaming: dictionary bytes kept resident in L2
     int gram_period = 0;            // > 0: Gram-updated correlations, direct every R steps
     int batch_gram = 0;             // batched / served BF16: Gram mode period (0 = off)
+    int batch_gram_below = 0;       // batched BF16 with batch_gram > 0: direct steps while more
+                                    // signals than this are active, Gram steps after (0 = off)
 
     long long launches = 0;
     BatchEngine* batch = nullptr;

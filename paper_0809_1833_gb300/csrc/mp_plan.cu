@@ -353,6 +353,11 @@ mp_status mp_plan_set_option(mp_plan_t plan, int option, long long value) {
                 return fail(MP_ERR_INVALID, "batch Gram period must be 0 or a multiple of 16 up to 2^20");
             p->batch_gram = static_cast<int>(value);
             return MP_OK;
+        case MP_OPT_BATCH_GRAM_BELOW:
+            if (value < 0 || value > (1 << 30))
+                return fail(MP_ERR_INVALID, "batch Gram switch threshold must be 0..2^30 signals");
+            p->batch_gram_below = static_cast<int>(value);
+            return MP_OK;
         case MP_OPT_BATCH_PAIR:
             if (value < 0 || value > 2) return fail(MP_ERR_INVALID, "batch pair option must be 0, 1 or 2");
             p->batch_pair = static_cast<int>(value);
@@ -386,6 +391,7 @@ mp_status mp_plan_query(mp_plan_t plan, int what, long long* value) {
         case MP_Q_BATCH_TILE_M: *value = p->batch ? p->batch->TM : 0; return MP_OK;
         case MP_Q_BATCH_GRAM: *value = p->batch ? p->batch->gram_R : 0; return MP_OK;
         case MP_Q_BATCH_PAIR: *value = p->batch ? p->batch->pair : 0; return MP_OK;
+        case MP_Q_BATCH_GRAM_BELOW: *value = p->batch ? p->batch->gram_below : 0; return MP_OK;
         case MP_Q_PLAN_N: *value = p->N; return MP_OK;
         case MP_Q_PLAN_M: *value = p->M; return MP_OK;
         case MP_Q_GRAM_BYTES:

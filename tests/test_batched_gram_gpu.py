@@ -12,6 +12,13 @@ equals the plain FP32 kernel's bit for bit; the tests check that (for every
 signal here), the literal oracle rule on sampled signals, the server's
 alone-equals-in-the-mix property in this mode, and the option's argument
 checks.
+
+The switched mode (MP_OPT_BATCH_GRAM_BELOW = S) runs direct steps while more
+than S signals are active and Gram steps after, with every active signal's
+correlations computed directly at the switch; since both kinds of step
+select by the same FP32 rescore, its decodes must equal the direct decode's
+bit for bit here too, on a small batch at several thresholds and on the full
+1024-signal BF16 workload at the threshold the benchmark uses.
 """
 import time
 
@@ -150,3 +157,78 @@ def test_gram_option_checks():
         pl.set(B().MP_OPT_BATCH_GRAM, 0)
         out = batched_decode(pl, B().MP_PREC_FP8E4M3, prob.y, (prob.eps, prob.T), 500)
         assert out["status"] == 0
+
+
+def _same_decodes(out, ref, n):
+    for b in range(n):
+        r, r0 = out["results"][b], ref["results"][b]
+        assert (r.status, r.stop_reason, r.iters) == (r0.status, r0.stop_reason, r0.iters), b
+        assert r.rel_residual == r0.rel_residual and r.energy_audit_max == r0.energy_audit_max, b
+    for k in ("X", "atoms", "coefs", "energies", "R"):
+        assert np.array_equal(out[k], ref[k], equal_nan=True), k
+
+
+@pytest.mark.parametrize("S", [1, 64, 299, 300])
+def test_switched_batched_equals_direct(S):
+    """300 signals, R = 64: S = 300 (the whole batch) starts with Gram steps,
+    S = 299 switches after the first replay, S = 64 part-way, S = 1 at the
+    tail.  Every signal equals the direct decode bit for bit; sampled
+    signals meet the oracle rule on their own atoms and residual."""
+    prob = W.make_batched(256, 1024, 300, 2, 16, seed=5, eps=1e-5, T=3000)
+    p = B().MP_PREC_BF16
+    with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
+        l0 = pl.query(B().MP_Q_KERNEL_LAUNCHES)
+        ref = batched_decode(pl, p, prob.y, (prob.eps, prob.T), 3000)
+        l1 = pl.query(B().MP_Q_KERNEL_LAUNCHES)
+        assert ref["status"] == 0
+        pl.set(B().MP_OPT_BATCH_GRAM, 64)
+        pl.set(B().MP_OPT_BATCH_GRAM_BELOW, S)
+        out = batched_decode(pl, p, prob.y, (prob.eps, prob.T), 3000)
+        l2 = pl.query(B().MP_Q_KERNEL_LAUNCHES)
+        assert out["status"] == 0
+        assert pl.query(B().MP_Q_BATCH_GRAM_BELOW) == S and pl.query(B().MP_Q_BATCH_GRAM) == 64
+        _same_decodes(out, ref, prob.B)
+        if S >= 64:
+            # Gram steps are one launch, direct steps two: the switch happened
+            assert l2 - l1 < l1 - l0, (l1 - l0, l2 - l1)
+        for b in range(0, prob.B, 60):
+            compare_to_oracle(prob.psi, prob.y[b], prob.eps, prob.T, batched_signal(out, b), check_follow=False,
+                              gram_period=64)
+            assert orc.support_score(out["X"][b], prob.supports[b]) == 1.0
+
+
+def test_switched_full_bf16_workload_equals_direct():
+    """The 1024-signal BF16 workload (N = 2048, M = 8192) with the
+    benchmark's switched setting (S = 512, R = 256): all 1024 decodes equal
+    the direct decodes bit for bit, and 4 sampled signals meet the oracle
+    rule."""
+    name = "batched_bf16_N2048_M8192_B1024"
+    prob = W.make_workload(name, seed=0)
+    p = B().MP_PREC_BF16
+    with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
+        ref = batched_decode(pl, p, prob.y, (prob.eps, prob.T), 1024)
+        assert ref["status"] == 0
+        pl.set(B().MP_OPT_BATCH_GRAM, 256)
+        pl.set(B().MP_OPT_BATCH_GRAM_BELOW, 512)
+        out = batched_decode(pl, p, prob.y, (prob.eps, prob.T), 1024)
+        assert out["status"] == 0
+    _same_decodes(out, ref, prob.B)
+    for b in (0, 341, 682, 1023):
+        d = compare_to_oracle(prob.psi, prob.y[b], prob.eps, prob.T, batched_signal(out, b), check_follow=False,
+                              gram_period=256, label=f"{name}[{b}] switched")
+        assert d["x_rel_err"] <= 1e-4
+
+
+def test_switched_option_checks():
+    psi = W.gaussian_dictionary(64, 300, seed=3)
+    p = B().MP_PREC_BF16
+    with GpuPlan(psi, prec_mask=1 << p) as pl:
+        with pytest.raises(B().MpError) as ei:
+            pl.set(B().MP_OPT_BATCH_GRAM_BELOW, -1)
+        assert ei.value.status == B().MP_ERR_INVALID
+        # without a Gram period the threshold has no effect: direct steps
+        pl.set(B().MP_OPT_BATCH_GRAM_BELOW, 8)
+        prob = W.make_batched(64, 300, 4, 1, 3, seed=2, psi=psi, eps=1e-5, T=500)
+        out = batched_decode(pl, p, prob.y, (prob.eps, prob.T), 500)
+        assert out["status"] == 0
+        assert pl.query(B().MP_Q_BATCH_GRAM_BELOW) == 0 and pl.query(B().MP_Q_BATCH_GRAM) == 0
