@@ -372,7 +372,7 @@ def run_ours(args):
         line["plain_small"] = plain_small_measure()
         line["variants"] = variants_measure()
         # batched low-precision form vs the plain FP32 kernel on the same signals
-        line["batched"] = [batched_measure("bf16", n_oracle=4, switched=(512, 640)),
+        line["batched"] = [batched_measure("bf16", n_oracle=4, variants=((256, 0), (512, 896))),
                            batched_measure("fp8", n_plain=4, n_oracle=1)]
         line["fp8_gemm_peak"] = fp8_gemm_peak()
         # tensor-core fraction of the GEMM: BF16 against the measured burst
@@ -544,14 +544,14 @@ def variants_measure(n_sig=4, gram_period=32):
 
 
 def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=(256, 256), n_oracle=0,
-                    switched=None):
+                    variants=()):
     """Batched low-precision decode of a whole batched workload vs the plain
     FP32 kernel on the same signals (the first ``n_plain`` of them); x~ of
     ``n_oracle`` signals spread over the batch against full FP64 oracle
-    decodes.  ``switched`` = (R, S): also time the same batch in the
-    switched mode (direct GEMM steps while more than S signals are active,
-    Gram-updated steps with refresh period R after) and compare its x~ with
-    the direct decode's bit for bit."""
+    decodes.  ``variants``: (R, S) pairs; each also times the same batch
+    with Gram-updated correlations, refresh period R (S = 0: every step;
+    S > 0: direct GEMM steps while more than S signals are active, Gram
+    steps after), and compares its x~ with the direct decode's bit for bit."""
     import torch
     from oracle import mp_oracle as orc
     from paper_0809_1833_gb300 import binding as B
@@ -617,9 +617,8 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
         supp_p.append(orc.support_score(xs.cpu().numpy(), prob.supports[i]))
     # the correlation GEMM alone at the batch's shape, full batch (first step)
     g_us = B.mp_debug_time_gemm(plan, prec, prob.B, reps=20)
-    sw = None
-    if switched:
-        R_sw, S_sw = switched
+    var_out = []
+    for R_sw, S_sw in variants:
         B.mp_plan_set_option(plan, B.MP_OPT_BATCH_GRAM, R_sw)
         B.mp_plan_set_option(plan, B.MP_OPT_BATCH_GRAM_BELOW, S_sw)
         Xs = torch.empty_like(X)
@@ -643,15 +642,18 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
         tsw = statistics.median(ts)
         Xsh = Xs.cpu().numpy()
         same = np.all(Xsh == Xh, axis=1) & np.array([r.iters == q.iters for r, q in zip(res_s, res)])
-        sw = {"mode": f"direct BF16 GEMM steps while more than {S_sw} signals are active, then Gram-updated "
-                      f"steps (correlations computed directly at the switch and every {R_sw} of a signal's steps)",
-              "gram_period": R_sw, "switch_below": S_sw, "recoveries_per_s": prob.B / tsw, "ms_per_batch": 1e3 * tsw,
-              "speedup_vs_direct": tb / tsw, "signals_equal_to_direct_bitwise": int(same.sum()),
-              "support_score_min": float(min(orc.support_score(Xsh[i], prob.supports[i]) for i in range(prob.B))),
-              "effective_tflops": 2.0 * prob.N * prob.M * float(iters.sum()) / tsw / 1e12,
-              "effective_tflops_note": "direct-step-equivalent correlation work (2 N M per signal-step) per second",
-              "gpu_launches_per_batch": int(ls), "gram_bytes": B.mp_plan_query(plan, B.MP_Q_GRAM_BYTES),
-              "first_call_s_with_gram_build": first_s}
+        mode = (f"direct BF16 GEMM steps while more than {S_sw} signals are active, then Gram-updated steps"
+                if S_sw else "Gram-updated steps throughout (no GEMM)")
+        var_out.append({
+            "mode": mode + f"; correlations computed directly in FP32 at admission or switch and every {R_sw} "
+                           "of a signal's steps",
+            "gram_period": R_sw, "switch_below": S_sw, "recoveries_per_s": prob.B / tsw, "ms_per_batch": 1e3 * tsw,
+            "speedup_vs_direct": tb / tsw, "signals_equal_to_direct_bitwise": int(same.sum()),
+            "support_score_min": float(min(orc.support_score(Xsh[i], prob.supports[i]) for i in range(prob.B))),
+            "effective_tflops": 2.0 * prob.N * prob.M * float(iters.sum()) / tsw / 1e12,
+            "effective_tflops_note": "direct-step-equivalent correlation work (2 N M per signal-step) per second",
+            "gpu_launches_per_batch": int(ls), "gram_bytes": B.mp_plan_query(plan, B.MP_Q_GRAM_BYTES),
+            "first_call_s_with_gram_build": first_s})
     gemm = {"rows": prob.B, "us_per_launch": g_us, "tflops": 2.0 * prob.N * prob.M * prob.B / g_us / 1e6,
             "how": "mp_debug_time_gemm: GEMM + top-8 epilogue on the full batch of synthetic rows, CUDA events, "
                    "mean of 20 launches after 2 warm-up"}
@@ -678,7 +680,7 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
             "iterations_total": int(iters.sum()), "iterations_max": int(iters.max()),
             "effective_tflops": flops / tb / 1e12, "gpu_launches_per_batch": int(launches), "gemm_shape": shape,
             "active_rows_profile": active_profile,
-            "gemm_full_batch": gemm, "switched": sw}
+            "gemm_full_batch": gemm, "gram_variants": var_out}
 
 
 def shape_parts(shape):

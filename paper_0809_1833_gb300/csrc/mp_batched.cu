@@ -629,7 +629,8 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : (THREADS 
 // The update runs whether or not the signal stops (a stopped slot's row is
 // not read again).  The same 8 keys as a full ranking of the row, so the
 // same results bit for bit.
-constexpr int kGramThreads = 512;
+constexpr int kGramThreads = 512;                       // threads of an SM's Gram-step CTAs together
+constexpr int kGramCta = 256;                           // threads per CTA (kGramThreads / kGramCta per SM)
 constexpr int kGramGroup0 = kSumChains;                // energy group: threads 0..127
 constexpr int kGramList = 256;                          // entries at or above the threshold kept
 
@@ -683,10 +684,11 @@ MP_DEV void list_top8_store(const unsigned long long* list, int n, unsigned long
 // SM: the slot's correlation row and the selected atom's row of G are
 // brought into shared memory by bulk copies (issued as soon as their
 // addresses are known, landing while the step rescores and updates r);
-// otherwise they are read from global memory.  The grid has at most one CTA
-// per SM; each CTA takes rows blockIdx.x, blockIdx.x + gridDim.x, ...
+// otherwise they are read from global memory.  The grid has at most
+// kGramThreads / kGramCta CTAs per SM; each CTA takes rows blockIdx.x,
+// blockIdx.x + gridDim.x, ...
 template <bool SM>
-__global__ void __launch_bounds__(kGramThreads, 1) gram_select_kernel(const SelArgs a) {
+__global__ void __launch_bounds__(kGramCta, kGramThreads / kGramCta) gram_select_kernel(const SelArgs a) {
     extern __shared__ float4 dsm[];
     float* r = reinterpret_cast<float*>(dsm);
     float4* rs4 = dsm;
@@ -697,10 +699,10 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_select_kernel(const SelA
     __shared__ double redd[kGramGroup0 / 32];
     __shared__ int top[kTop];
     __shared__ unsigned long long rkey[kTop];
-    __shared__ float wthr[kGramThreads / 32];
+    __shared__ float wthr[kGramCta / 32];
     __shared__ unsigned long long list[kGramList];
     __shared__ int list_n;
-    __shared__ unsigned long long gtw[kGramThreads / 32][kTop];
+    __shared__ unsigned long long gtw[kGramCta / 32][kTop];
     __shared__ uint64_t bar_c, bar_g;
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -727,10 +729,10 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_select_kernel(const SelA
         SlotState s = a.st[slot];
         BatchIO io;
         if (threadIdx.x == 0) io = *a.io;
-        for (int k = threadIdx.x; k < n4; k += kGramThreads) cp_async16(rs4 + k, rg4 + k);
+        for (int k = threadIdx.x; k < n4; k += kGramCta) cp_async16(rs4 + k, rg4 + k);
         cp_async_commit();
         if (!SM)
-            for (int q = threadIdx.x * 8; q < nq; q += kGramThreads * 8) prefetch_line_l2(cr4 + q);
+            for (int q = threadIdx.x * 8; q < nq; q += kGramCta * 8) prefetch_line_l2(cr4 + q);
         if (threadIdx.x < kTop) {
             const unsigned long long k = a.gtop[static_cast<size_t>(slot) * kTop + threadIdx.x];
             top[threadIdx.x] = k ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(k)) : -1;
@@ -776,12 +778,12 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_select_kernel(const SelA
             continue;
         }
         if (!SM)
-            for (int q = threadIdx.x * 8; q < nq; q += kGramThreads * 8) prefetch_line_l2(gr4 + q);
+            for (int q = threadIdx.x * 8; q < nq; q += kGramCta * 8) prefetch_line_l2(gr4 + q);
         float xm = 0.f;
         if (threadIdx.x == 0) xm = io.X[static_cast<size_t>(slot) * io.ldx + m];
         // Eq. 11 in FP32
         const float4* pm = reinterpret_cast<const float4*>(a.psi32 + static_cast<size_t>(m) * a.ldN);
-        for (int k = threadIdx.x; k < n4; k += kGramThreads) {
+        for (int k = threadIdx.x; k < n4; k += kGramCta) {
             const float4 p = __ldg(pm + k);
             float4 v = rs4[k];
             v.x = fmaf(-c, p.x, v.x);
@@ -830,7 +832,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_select_kernel(const SelA
             }
         } else {
             // ---- Gram group: c_j -= c G[m][j] and the row's 8 largest |c|
-            constexpr int GT = kGramThreads - kGramGroup0;
+            constexpr int GT = kGramCta - kGramGroup0;
             const int gt = threadIdx.x - kGramGroup0, gw = warp - kGramGroup0 / 32;
             bool ok = true;
             if (SM) {
@@ -1084,6 +1086,100 @@ __global__ void __launch_bounds__(kCorrThreads) corr_rows_kernel(const CorrRowsA
     }
 }
 
+// The same correlations as a register-tiled FP32 GEMM, for refreshes whose
+// listed rows are all due together (every row, or rows that share one step
+// count, as in a batched decode where every active signal has taken the same
+// number of steps): C[i][j] = sum_n r_slot(i)[n] psi_j[n], a 128-row x
+// 128-atom output tile per CTA, 8 x 8 per thread, 16-deep slices of both
+// operands staged transposed in shared memory; each entry is one FP32 FMA
+// chain in increasing n.  A CTA whose tile holds no due row (or lies past
+// the device's row count) leaves at once.
+constexpr int kTileC = 128;
+constexpr int kTileK = 16;
+// below this many listed rows a 128-row tile computes mostly padding: the
+// row-group kernel (one pass over the atoms per 8 rows) is cheaper
+constexpr int kTiledMinRows = 64;
+
+__global__ void __launch_bounds__(256) corr_tile_kernel(const CorrRowsArgs a) {
+    __shared__ __align__(16) float As[kTileK][kTileC + 4];
+    __shared__ __align__(16) float Bs[kTileK][kTileC + 4];
+    __shared__ int slots[kTileC];
+    __shared__ int any_due;
+    const int n = a.n_ptr ? *a.n_ptr : a.n;
+    const int i0 = blockIdx.y * kTileC, j0 = blockIdx.x * kTileC;
+    if (i0 >= n) return;   // the same for every thread of the CTA
+    const int tid = threadIdx.x;
+    if (tid == 0) any_due = 0;
+    __syncthreads();
+    if (tid < kTileC) {
+        int sl = -1;
+        if (i0 + tid < n) {
+            sl = a.rows ? a.rows[i0 + tid] : i0 + tid;
+            if (corr_row_wanted(a, sl)) any_due = 1;
+            else sl = -1;
+        }
+        slots[tid] = sl;
+    }
+    __syncthreads();
+    if (!any_due) return;
+    const int tx = tid & 15, ty = tid >> 4;
+    float acc[8][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+    // each thread stages 2 float4 of each operand per slice: tile row
+    // q >> 2, K offset 4 (q & 3), for q = tid and tid + 256
+    for (int k0 = 0; k0 < a.ldN; k0 += kTileK) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = tid + 256 * h;
+            const int row = q >> 2, kk = 4 * (q & 3);
+            const int sl = slots[row], jb = j0 + row;
+            float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va;
+            if (sl >= 0) va = *reinterpret_cast<const float4*>(a.R32 + static_cast<size_t>(sl) * a.ldN + k0 + kk);
+            if (jb < a.M) vb = __ldg(reinterpret_cast<const float4*>(a.psi32 + static_cast<size_t>(jb) * a.ldN + k0 + kk));
+            As[kk + 0][row] = va.x;
+            As[kk + 1][row] = va.y;
+            As[kk + 2][row] = va.z;
+            As[kk + 3][row] = va.w;
+            Bs[kk + 0][row] = vb.x;
+            Bs[kk + 1][row] = vb.y;
+            Bs[kk + 2][row] = vb.z;
+            Bs[kk + 3][row] = vb.w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kTileK; ++k) {
+            float x[8], w[8];
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[k][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[k][ty * 8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[k][tx * 8]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[k][tx * 8 + 4]);
+            x[0] = a0.x; x[1] = a0.y; x[2] = a0.z; x[3] = a0.w;
+            x[4] = a1.x; x[5] = a1.y; x[6] = a1.z; x[7] = a1.w;
+            w[0] = b0.x; w[1] = b0.y; w[2] = b0.z; w[3] = b0.w;
+            w[4] = b1.x; w[5] = b1.y; w[6] = b1.z; w[7] = b1.w;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(x[u], w[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int sl = slots[ty * 8 + u];
+        if (sl < 0) continue;
+        float* crow = a.Cg + static_cast<size_t>(sl) * a.ldC;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const int j = j0 + tx * 8 + v;
+            if (j < a.M) crow[j] = acc[u][v];
+        }
+    }
+}
+
 // The 8 largest |c| (keys as cand_key) of each listed slot's correlation
 // row, for its next step; one CTA per listed row, the same filter as above.
 __global__ void __launch_bounds__(kCorrThreads) gram_scan_kernel(const CorrRowsArgs a, unsigned long long* gtop) {
@@ -1323,9 +1419,9 @@ size_t engine_slot_bytes(const PlanImpl* p, int prec, bool with_x, int gram_R) {
            gram;
 }
 
-mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_t st, GemmShape* out);
+mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_t st, GemmShape* out, int lo_rows = 0);
 
-mp_status batch_shape(PlanImpl* p, int prec, int B, const float* R, cudaStream_t st, GemmShape* shape) {
+mp_status batch_shape(PlanImpl* p, int prec, int B, const float* R, cudaStream_t st, GemmShape* shape, int lo_rows) {
     const int rt = (B + kBM - 1) / kBM;
     GemmShape g;
     g.tn = 256;
@@ -1333,7 +1429,7 @@ mp_status batch_shape(PlanImpl* p, int prec, int B, const float* R, cudaStream_t
     g.pair = p->batch_pair == 2 ? 1 : 0;
     if (g.pair) g.tm = 256;
     if (p->batch_autotune && !p->batch_tile_n && !p->batch_tile_m && p->batch_pair == 0) {
-        mp_status s = autotune(p, prec, B, R, st, &g);
+        mp_status s = autotune(p, prec, B, R, st, &g, lo_rows);
         if (s != MP_OK) return s;
     }
     if (p->batch_tile_n) g.tn = p->batch_tile_n;
@@ -1556,11 +1652,12 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, bool gram,
     sa.lim = static_cast<unsigned long long>(p->watchdog_ns);
     const size_t sm = p->ldN * sizeof(float);
     if (gram) {
-        const int ctas = std::max(1, std::min(e->cap, p->sm_count > 0 ? p->sm_count : e->cap));
+        const int per_sm = kGramThreads / kGramCta;
+        const int ctas = std::max(1, std::min(e->cap, p->sm_count > 0 ? per_sm * p->sm_count : e->cap));
         if (gram_rows_in_smem(p, e))
-            gram_select_kernel<true><<<ctas, kGramThreads, gram_smem_bytes(p, e, true), st>>>(sa);
+            gram_select_kernel<true><<<ctas, kGramCta, gram_smem_bytes(p, e, true), st>>>(sa);
         else
-            gram_select_kernel<false><<<ctas, kGramThreads, gram_smem_bytes(p, e, false), st>>>(sa);
+            gram_select_kernel<false><<<ctas, kGramCta, gram_smem_bytes(p, e, false), st>>>(sa);
     } else if (e->cap < kWideSelectCap) select_update_kernel<2 * kSumChains><<<e->cap, 2 * kSumChains, sm, st>>>(sa);
     else select_update_kernel<kSumChains><<<e->cap, kSumChains, sm, st>>>(sa);
     ++*kernels;
@@ -1569,9 +1666,12 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, bool gram,
 
 // Gram mode: direct FP32 correlations and their top 8 for listed slots
 // (rows == NULL: slots 0..n_max-1; n_ptr: the device's row count; R > 0:
-// only the slots whose step count is a positive multiple of R).
+// only the slots whose step count is a positive multiple of R).  `tiled`:
+// the listed rows are all due together (R = 0, or one shared step count),
+// so the register-tiled GEMM computes them; otherwise (a server's slots at
+// different steps) the row-group kernel looks at each row's own count.
 static cudaError_t launch_gram_refresh(PlanImpl* p, BatchEngine* e, const int* rows, const int* n_ptr, int n_max, int R,
-                                       cudaStream_t st, int* kernels) {
+                                       bool tiled, cudaStream_t st, int* kernels) {
     if (n_max <= 0) return cudaSuccess;
     CorrRowsArgs a;
     a.psi32 = p->psi32;
@@ -1591,8 +1691,11 @@ static cudaError_t launch_gram_refresh(PlanImpl* p, BatchEngine* e, const int* r
     // one CTA per block of atoms (each runs over the row groups); the scan
     // at most two CTAs per SM over the rows
     const int sms = p->sm_count > 0 ? p->sm_count : 132;
-    corr_rows_kernel<<<(p->M + kCorrAtoms - 1) / kCorrAtoms, kCorrThreads,
-                       static_cast<size_t>(a.rpc) * p->ldN * sizeof(float), st>>>(a);
+    if (tiled)
+        corr_tile_kernel<<<dim3((p->M + kTileC - 1) / kTileC, (n_max + kTileC - 1) / kTileC), 256, 0, st>>>(a);
+    else
+        corr_rows_kernel<<<(p->M + kCorrAtoms - 1) / kCorrAtoms, kCorrThreads,
+                           static_cast<size_t>(a.rpc) * p->ldN * sizeof(float), st>>>(a);
     gram_scan_kernel<<<std::min(n_max, 2 * sms), kCorrThreads, 0, st>>>(a, e->gtop);
     *kernels += 2;
     return cudaGetLastError();
@@ -1610,7 +1713,10 @@ static mp_status capture_steps(PlanImpl* p, BatchEngine* e, int steps, bool gram
     // multiple of `steps` (signals join between replays and each step moves
     // every active signal by one); the slots at a multiple of the period get
     // their correlations recomputed directly
-    if (gram) r = launch_gram_refresh(p, e, e->act, e->counters, e->cap, e->gram_R, e->cap_stream, &kernels);
+    // a batched decode's active signals have all taken the same number of
+    // steps (they start together); a server's (retire) have not
+    if (gram)
+        r = launch_gram_refresh(p, e, e->act, e->counters, e->cap, e->gram_R, !retire, e->cap_stream, &kernels);
     for (int s = 0; s < steps && r == cudaSuccess; ++s) r = launch_step(p, e, s & 1, gram, e->cap_stream, &kernels);
     if (retire && r == cudaSuccess) {
         RetireArgs ra;
@@ -1730,7 +1836,7 @@ cudaError_t engine_admit(PlanImpl* p, BatchEngine* e, const float* Y, int n, con
         // the Gram mode starts every signal from its direct FP32 correlations
         // (the switched mode computes them when it switches)
         int k = 0;
-        r = launch_gram_refresh(p, e, slots_dev, nullptr, n, 0, st, &k);
+        r = launch_gram_refresh(p, e, slots_dev, nullptr, n, 0, n >= kTiledMinRows, st, &k);
         p->launches += k;
         if (r != cudaSuccess) return r;
     }
@@ -1740,7 +1846,9 @@ cudaError_t engine_admit(PlanImpl* p, BatchEngine* e, const float* Y, int n, con
 static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, long long ldx, int B, const mp_stop* stops,
                              int n_stops, const mp_trace* trace, mp_result* out, cudaStream_t st) {
     GemmShape g;
-    mp_status s = batch_shape(p, prec, B, Y, st, &g);
+    // the switched mode's GEMMs see more than the threshold's active rows
+    const int sw = p->batch_gram > 0 ? p->batch_gram_below : 0;
+    mp_status s = batch_shape(p, prec, B, Y, st, &g, sw > 0 && B > sw ? sw + 1 : 0);
     if (s != MP_OK) return s;
     if (p->batch_gram > 0) {
         if (prec != MP_PREC_BF16)
@@ -1786,17 +1894,18 @@ static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, lo
     // append to (half 1's, left over from the last direct step, which a GEMM
     // would have cleared) is cleared.
     bool gram_steps = false;
-    auto switch_to_gram = [&]() -> mp_status {
+    // n_rows: the active count last seen (at least the count at the switch)
+    auto switch_to_gram = [&](int n_rows) -> mp_status {
         MP_CUDA_TRY(cudaMemsetAsync(e->counters + 3, 0, sizeof(int), st));
         int k = 0;
-        MP_CUDA_TRY(launch_gram_refresh(p, e, e->act, e->counters, e->cap, 0, st, &k));
+        MP_CUDA_TRY(launch_gram_refresh(p, e, e->act, e->counters, e->cap, 0, n_rows >= kTiledMinRows, st, &k));
         p->launches += k;
         gram_steps = true;
         return MP_OK;
     };
     // a batch no larger than the threshold starts with Gram steps
     if (gram_below > 0 && B <= gram_below) {
-        s = switch_to_gram();
+        s = switch_to_gram(B);
         if (s != MP_OK) return s;
     }
     // replay the captured steps until no signal is active (each step moves
@@ -1819,7 +1928,7 @@ static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, lo
             // the count after replay k - 1 reached the threshold: switch
             // after replay k (already queued; it holds at most that many)
             if (gram_below > 0 && !gram_steps && n_left <= gram_below) {
-                s = switch_to_gram();
+                s = switch_to_gram(n_left);
                 if (s != MP_OK) return s;
             }
         }
@@ -2013,10 +2122,11 @@ static double time_gemm(PlanImpl* p, int prec, int B, const GemmShape& g, const 
     return us;
 }
 
-mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_t st, GemmShape* out) {
+mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_t st, GemmShape* out, int lo_rows) {
     const int bucket = batch_bucket(B);
+    const int lo = lo_rows > 0 ? std::min(lo_rows, B) : 0;
     for (const TuneEntry& t : p->tuned)
-        if (t.prec == prec && t.bucket == bucket) {
+        if (t.prec == prec && t.bucket == bucket && t.lo == lo) {
             *out = t.shape;
             return MP_OK;
         }
@@ -2032,8 +2142,9 @@ mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_
     const int rt = (B + kBM - 1) / kBM;
     // a shape is timed on the full batch and on a quarter of it: a batch
     // drains as its signals stop, and a shape that only wins when full can
-    // lose the decode
-    const int Bq = std::max(1, B / 4);
+    // lose the decode (a decode that switches to Gram steps below a count
+    // runs no GEMM under it: the shapes are timed at that count instead)
+    const int Bq = lo > 0 ? lo : std::max(1, B / 4);
     auto consider = [&](const GemmShape& g) {
         const double u1 = time_gemm(p, prec, B, g, R_dev ? R_dev : R, st);
         const double u2 = u1 > 0.0 ? time_gemm(p, prec, Bq, g, R_dev ? R_dev : R, st) : -1.0;
@@ -2065,7 +2176,7 @@ mp_status autotune(PlanImpl* p, int prec, int B, const float* R_dev, cudaStream_
     if (R) cudaFreeAsync(R, st);
     if (best < 0.0) return fail(MP_ERR_CUDA, "autotune: no tile shape could be timed");
     cudaStreamSynchronize(st);
-    p->tuned.push_back(TuneEntry{prec, bucket, best_g, best});
+    p->tuned.push_back(TuneEntry{prec, bucket, best_g, best, lo});
     *out = best_g;
     return MP_OK;
 }

@@ -108,6 +108,7 @@ struct TuneEntry {
     int bucket;
     GemmShape shape;
     double us;             // measured GEMM time per launch
+    int lo = 0;            // the smaller batch the shapes were also timed on (0: a quarter)
 };
 
 struct PlanImpl {
@@ -183,7 +184,11 @@ void batch_destroy(BatchEngine* b);
 // GEMM shape (signals and atoms per tile) for a batch of B signals: the
 // plan's options if set, else the autotuned choice (timed now on first use
 // of the batch-size bucket, on rows R when given), else a fixed rule.
-mp_status batch_shape(PlanImpl* p, int prec, int B, const float* R, cudaStream_t st, GemmShape* shape);
+// lo_rows > 0: the fewest active rows a GEMM of this decode will see (the
+// autotuner times each shape on the full batch and on that many rows; by
+// default on a quarter of the batch).
+mp_status batch_shape(PlanImpl* p, int prec, int B, const float* R, cudaStream_t st, GemmShape* shape,
+                      int lo_rows = 0);
 
 }  // namespace mpgb
 

@@ -197,25 +197,27 @@ def test_switched_batched_equals_direct(S):
             assert orc.support_score(out["X"][b], prob.supports[b]) == 1.0
 
 
-def test_switched_full_bf16_workload_equals_direct():
-    """The 1024-signal BF16 workload (N = 2048, M = 8192) with the
-    benchmark's switched setting (S = 512, R = 256): all 1024 decodes equal
-    the direct decodes bit for bit, and 4 sampled signals meet the oracle
-    rule."""
+@pytest.mark.parametrize("R,S", [(256, 0), (512, 896), (256, 512)], ids=["gram_R256", "switch896_R512", "switch512_R256"])
+def test_gram_full_bf16_workload_equals_direct(R, S):
+    """The 1024-signal BF16 workload (N = 2048, M = 8192) in the benchmark's
+    Gram settings (every step a Gram step with R = 256; direct steps down to
+    896 active signals, then Gram steps with R = 512) and one more switch
+    point: all 1024 decodes equal the direct decodes bit for bit, and 4
+    sampled signals meet the oracle rule."""
     name = "batched_bf16_N2048_M8192_B1024"
     prob = W.make_workload(name, seed=0)
     p = B().MP_PREC_BF16
     with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
         ref = batched_decode(pl, p, prob.y, (prob.eps, prob.T), 1024)
         assert ref["status"] == 0
-        pl.set(B().MP_OPT_BATCH_GRAM, 256)
-        pl.set(B().MP_OPT_BATCH_GRAM_BELOW, 512)
+        pl.set(B().MP_OPT_BATCH_GRAM, R)
+        pl.set(B().MP_OPT_BATCH_GRAM_BELOW, S)
         out = batched_decode(pl, p, prob.y, (prob.eps, prob.T), 1024)
         assert out["status"] == 0
     _same_decodes(out, ref, prob.B)
     for b in (0, 341, 682, 1023):
         d = compare_to_oracle(prob.psi, prob.y[b], prob.eps, prob.T, batched_signal(out, b), check_follow=False,
-                              gram_period=256, label=f"{name}[{b}] switched")
+                              gram_period=R, label=f"{name}[{b}] R={R} S={S}")
         assert d["x_rel_err"] <= 1e-4
 
 
