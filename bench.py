@@ -373,7 +373,7 @@ def run_ours(args):
         line["variants"] = variants_measure()
         # batched low-precision form vs the plain FP32 kernel on the same signals
         line["batched"] = [batched_measure("bf16", n_oracle=4, variants=((256, 0), (512, 896))),
-                           batched_measure("fp8", n_plain=4, n_oracle=1)]
+                           batched_measure("fp8", n_plain=4, n_oracle=1, variants=((512, 0),))]
         line["fp8_gemm_peak"] = fp8_gemm_peak()
         # tensor-core fraction of the GEMM: BF16 against the measured burst
         # peak, FP8 against the vendor library's E4M3 rate measured above
@@ -862,6 +862,72 @@ def served_measure(rate=2000.0, duration=60.0, pool_s=5.0, seed=0, max_slots=256
             "signal_generation_s": t_gen}
 
 
+def gram_steps(prec_name="bf16", rows=(1024, 768, 512, 256, 64), settings=((256, 0), (320, 0), (512, 896)),
+               reps=5):
+    """Direct against Gram-updated steps on a batched workload.  Per-step
+    device time at several active-signal counts: the first n signals decoded
+    with the iteration cap at 16 and at 48 (nearly all of them still active
+    at 48), (t48 - t16) / 32 steps, direct and with Gram steps from
+    admission (R = 1024: no refresh inside the window).  Then the whole
+    batch in each (R, S) setting (S = 0: Gram steps from admission; S > 0:
+    direct steps while more than S signals are active), with the count of
+    signals whose x~ equals the direct decode's bit for bit.  One JSON line
+    per measurement."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0809_1833_gb300 import binding as B
+    from paper_0809_1833_gb300 import workloads as W
+    name = BATCHED[prec_name]
+    w = W.WORKLOADS[name]
+    prob = W.make_workload(name, seed=0)
+    prec = B.MP_PREC_BF16 if prec_name == "bf16" else B.MP_PREC_FP8E4M3
+    d = torch.from_numpy(prob.psi).cuda()
+    plan = B.mp_plan_create(prob.N, prob.M, d.data_ptr(), prec_mask=1 << prec)
+    del d
+    Yall = torch.from_numpy(prob.y).cuda()
+    X = torch.empty((prob.B, prob.M), device="cuda")
+
+    def t_ms(n, T):
+        Y = Yall[:n]
+        B.mp_recover_batched(plan, prec, Y.data_ptr(), X.data_ptr(), n, (w["eps"], T))
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            _, res = B.mp_recover_batched(plan, prec, Y.data_ptr(), X.data_ptr(), n, (w["eps"], T))
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts), res
+
+    for gram in (0, 1024):
+        B.mp_plan_set_option(plan, B.MP_OPT_BATCH_GRAM, gram)
+        B.mp_plan_set_option(plan, B.MP_OPT_BATCH_GRAM_BELOW, 0)
+        for n in rows:
+            n = min(n, prob.B)
+            t1, _ = t_ms(n, 16)
+            t2, res = t_ms(n, 48)
+            print(json.dumps({"gram_steps": name, "step": "gram" if gram else "direct", "signals": n,
+                              "active_at_step_48": int(sum(r.iters >= 48 for r in res)),
+                              "us_per_step": (t2 - t1) * 1e3 / 32}), flush=True)
+    B.mp_plan_set_option(plan, B.MP_OPT_BATCH_GRAM, 0)
+    t0, _ = t_ms(prob.B, w["T"])
+    x0 = X.cpu().numpy()
+    print(json.dumps({"gram_steps": name, "decode": "direct", "ms": t0, "recoveries_per_s": prob.B / t0 * 1e3}),
+          flush=True)
+    for R, S in settings:
+        B.mp_plan_set_option(plan, B.MP_OPT_BATCH_GRAM, R)
+        B.mp_plan_set_option(plan, B.MP_OPT_BATCH_GRAM_BELOW, S)
+        t, _ = t_ms(prob.B, w["T"])
+        x = X.cpu().numpy()
+        print(json.dumps({"gram_steps": name, "decode": "gram", "gram_period": R, "switch_below": S, "ms": t,
+                          "recoveries_per_s": prob.B / t * 1e3,
+                          "signals_equal_to_direct_bitwise": int(np.all(x == x0, axis=1).sum())}), flush=True)
+    B.mp_plan_destroy(plan)
+
+
 def step_breakdown(rows=(1, 2, 4, 8, 16), dict_index=3, reps=3, gram=0, T=None):
     """Per-step device time of the batched BF16 decode on one served
     dictionary at a few active-row counts: the whole step (mp_recover_batched
@@ -1254,6 +1320,8 @@ def main():
     ap.add_argument("--breakdown-rows", type=int, nargs="*", default=None,
                     help="active-row counts of --step-breakdown (default 1 2 4 8 16)")
     ap.add_argument("--breakdown-T", type=int, default=None, help="iteration cap of --step-breakdown")
+    ap.add_argument("--gram-steps", choices=["bf16", "fp8"], default=None,
+                    help="per-step time of direct and Gram-updated steps, and whole decodes in the Gram settings")
     ap.add_argument("--shard-overhead", action="store_true",
                     help="run only the per-iteration cost of the atom-sharded host loop on one GPU")
     ap.add_argument("--cpu-worker", type=float, default=None, help=argparse.SUPPRESS)
@@ -1264,6 +1332,12 @@ def main():
         return
     if args.shard_overhead:
         shard_overhead()
+        return
+    if args.gram_steps:
+        if args.gram_steps == "fp8":
+            gram_steps("fp8", rows=(256, 128, 64), settings=((512, 0), (1024, 0)), reps=2)
+        else:
+            gram_steps("bf16")
         return
     if args.step_breakdown:
         step_breakdown(rows=tuple(args.breakdown_rows or (1, 2, 4, 8, 16)), gram=args.served_gram,

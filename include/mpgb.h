@@ -177,7 +177,9 @@ typedef enum {
                                /* 128-row MMAs sharing each staged atom slice;       */
                                /* taken while the batch has more 128-row tiles than  */
                                /* the GPU has SMs, 128 after); 0 = auto              */
-    MP_OPT_BATCH_GRAM = 14,    /* batched and served decodes (BF16 plans) with       */
+    MP_OPT_BATCH_GRAM = 14,    /* batched decodes (either precision: Gram steps use  */
+                               /* the FP32 atoms only) and served decodes (BF16      */
+                               /* dictionaries) with                                 */
                                /* Gram-updated correlations; the value is the        */
                                /* refresh period R, a multiple of 16 (0 = off, the   */
                                /* default).  Not in the paper: each signal keeps its */

@@ -1451,8 +1451,8 @@ static mp_status engine_prepare(PlanImpl* p, int prec, int cap, const GemmShape&
 mp_status engine_alloc(BatchEngine* e, PlanImpl* p, int prec, int newcap, const GemmShape& g, int gram_R,
                        int gram_below) {
     engine_free(e);
-    if (gram_R > 0 && (prec != MP_PREC_BF16 || !p->gram))
-        return fail(MP_ERR_UNSUPPORTED, "batched Gram mode: BF16 plans only, after the plan's Gram matrix is built");
+    if (gram_R > 0 && !p->gram)
+        return fail(MP_ERR_UNSUPPORTED, "batched Gram mode: the plan's Gram matrix is not built");
     if (gram_below < 0 || (gram_below > 0 && gram_R <= 0))
         return fail(MP_ERR_INVALID, "batched switched mode: needs a Gram period");
     const int TN = g.tn;
@@ -1774,10 +1774,14 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
 
     }
     if (e->gram_R > 0) {
-        MP_CUDA_TRY(cudaFuncSetAttribute(gram_select_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         gram_smem_bytes(p, e, true)));
-        MP_CUDA_TRY(cudaFuncSetAttribute(gram_select_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         gram_smem_bytes(p, e, false)));
+        // only the variant launch_step will take (rows in shared memory
+        // when they fit; a long row may not fit any CTA's shared memory)
+        if (gram_rows_in_smem(p, e))
+            MP_CUDA_TRY(cudaFuncSetAttribute(gram_select_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             gram_smem_bytes(p, e, true)));
+        else
+            MP_CUDA_TRY(cudaFuncSetAttribute(gram_select_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             gram_smem_bytes(p, e, false)));
     }
     if (e->gram_R > 0 && (e->gram_R % steps || !p->gram))
         return fail(MP_ERR_INVALID, "batched step graph: the Gram period must be a multiple of the steps per graph");
@@ -1851,8 +1855,8 @@ static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, lo
     mp_status s = batch_shape(p, prec, B, Y, st, &g, sw > 0 && B > sw ? sw + 1 : 0);
     if (s != MP_OK) return s;
     if (p->batch_gram > 0) {
-        if (prec != MP_PREC_BF16)
-            return fail(MP_ERR_UNSUPPORTED, "mp_recover_batched: the Gram mode runs with BF16 correlations");
+        // Gram steps use the FP32 atoms only (the precision's copy serves the
+        // switched mode's direct steps and the operand rows)
         s = gram_prepare(p, st);
         if (s != MP_OK) return s;
     }

@@ -150,10 +150,15 @@ def test_gram_option_checks():
             with pytest.raises(B().MpError) as ei:
                 pl.set(B().MP_OPT_BATCH_GRAM, bad)
             assert ei.value.status == B().MP_ERR_INVALID
+        # Gram steps read the FP32 atoms only: an FP8 plan runs them too, and
+        # each signal equals its plain FP32 decode
         pl.set(B().MP_OPT_BATCH_GRAM, 32)
         prob = W.make_batched(64, 300, 4, 1, 3, seed=2, psi=psi, eps=1e-5, T=500)
-        out = batched_decode(pl, B().MP_PREC_FP8E4M3, prob.y, (prob.eps, prob.T), 16)
-        assert out["status"] == B().MP_ERR_UNSUPPORTED
+        out = batched_decode(pl, B().MP_PREC_FP8E4M3, prob.y, (prob.eps, prob.T), 500)
+        assert out["status"] == 0
+        for b in range(prob.B):
+            plain = pl.decode(prob.y[b], prob.eps, prob.T)
+            assert np.array_equal(out["X"][b], plain["x"]), b
         pl.set(B().MP_OPT_BATCH_GRAM, 0)
         out = batched_decode(pl, B().MP_PREC_FP8E4M3, prob.y, (prob.eps, prob.T), 500)
         assert out["status"] == 0
@@ -234,3 +239,29 @@ def test_switched_option_checks():
         out = batched_decode(pl, p, prob.y, (prob.eps, prob.T), 500)
         assert out["status"] == 0
         assert pl.query(B().MP_Q_BATCH_GRAM_BELOW) == 0 and pl.query(B().MP_Q_BATCH_GRAM) == 0
+
+
+def test_gram_fp8_full_workload():
+    """The FP8 workload's dictionary (N = 8192, M = 32768, 4 GiB Gram
+    matrix), its 256 signals decoded with Gram steps (R = 512) on an FP8
+    plan: every signal converges and recovers its support, 8 sampled signals
+    equal the plain FP32 decode bit for bit, and one meets the oracle rule
+    against a full FP64 oracle decode."""
+    name = "batched_fp8_N8192_M32768_B256"
+    prob = W.make_workload(name, seed=0)
+    p = B().MP_PREC_FP8E4M3
+    with GpuPlan(prob.psi, prec_mask=1 << p) as pl:
+        pl.set(B().MP_OPT_BATCH_GRAM, 512)
+        out = batched_decode(pl, p, prob.y, (prob.eps, prob.T), 4096)
+        assert out["status"] == 0
+        assert pl.query(B().MP_Q_GRAM_BYTES) == prob.M * prob.M * 4
+        res = out["results"]
+        assert all(r.status == 0 and r.stop_reason == B().MP_STOP_CONVERGED for r in res)
+        assert min(orc.support_score(out["X"][b], prob.supports[b]) for b in range(prob.B)) == 1.0
+        for b in range(0, prob.B, 32):
+            plain = pl.decode(prob.y[b], prob.eps, prob.T)
+            assert res[b].iters == plain["result"].iters, b
+            assert np.array_equal(out["X"][b], plain["x"]), b
+    d = compare_to_oracle(prob.psi, prob.y[128], prob.eps, prob.T, batched_signal(out, 128), check_follow=False,
+                          gram_period=512, label=f"{name}[128] Gram R=512")
+    assert d["x_rel_err"] <= 1e-4
