@@ -1654,10 +1654,10 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, bool gram,
     if (gram) {
         const int per_sm = kGramThreads / kGramCta;
         const int ctas = std::max(1, std::min(e->cap, p->sm_count > 0 ? per_sm * p->sm_count : e->cap));
-        if (gram_rows_in_smem(p, e))
-            gram_select_kernel<true><<<ctas, kGramCta, gram_smem_bytes(p, e, true), st>>>(sa);
-        else
-            gram_select_kernel<false><<<ctas, kGramCta, gram_smem_bytes(p, e, false), st>>>(sa);
+        const bool rows_sm = gram_rows_in_smem(p, e);
+        const size_t gsm = gram_smem_bytes(p, e, rows_sm);
+        if (rows_sm) gram_select_kernel<true><<<ctas, kGramCta, gsm, st>>>(sa);
+        else gram_select_kernel<false><<<ctas, kGramCta, gsm, st>>>(sa);
     } else if (e->cap < kWideSelectCap) select_update_kernel<2 * kSumChains><<<e->cap, 2 * kSumChains, sm, st>>>(sa);
     else select_update_kernel<kSumChains><<<e->cap, kSumChains, sm, st>>>(sa);
     ++*kernels;
@@ -1776,12 +1776,10 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
     if (e->gram_R > 0) {
         // only the variant launch_step will take (rows in shared memory
         // when they fit; a long row may not fit any CTA's shared memory)
-        if (gram_rows_in_smem(p, e))
-            MP_CUDA_TRY(cudaFuncSetAttribute(gram_select_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             gram_smem_bytes(p, e, true)));
-        else
-            MP_CUDA_TRY(cudaFuncSetAttribute(gram_select_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             gram_smem_bytes(p, e, false)));
+        const bool rows_sm = gram_rows_in_smem(p, e);
+        const int gsm = static_cast<int>(gram_smem_bytes(p, e, rows_sm));
+        MP_CUDA_TRY(cudaFuncSetAttribute(rows_sm ? gram_select_kernel<true> : gram_select_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, gsm));
     }
     if (e->gram_R > 0 && (e->gram_R % steps || !p->gram))
         return fail(MP_ERR_INVALID, "batched step graph: the Gram period must be a multiple of the steps per graph");
