@@ -630,7 +630,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : (THREADS 
 // not read again).  The same 8 keys as a full ranking of the row, so the
 // same results bit for bit.
 constexpr int kGramThreads = 512;                       // threads of an SM's Gram-step CTAs together
-constexpr int kGramCta = 256;                           // threads per CTA (kGramThreads / kGramCta per SM)
+constexpr int kSmemPerSM = 233472;                      // shared memory of one SM (228 KB on sm_103a)
 constexpr int kGramGroup0 = kSumChains;                // energy group: threads 0..127
 constexpr int kGramList = 256;                          // entries at or above the threshold kept
 
@@ -684,11 +684,13 @@ MP_DEV void list_top8_store(const unsigned long long* list, int n, unsigned long
 // SM: the slot's correlation row and the selected atom's row of G are
 // brought into shared memory by bulk copies (issued as soon as their
 // addresses are known, landing while the step rescores and updates r);
-// otherwise they are read from global memory.  The grid has at most
-// kGramThreads / kGramCta CTAs per SM; each CTA takes rows blockIdx.x,
+// otherwise they are read from global memory.  CTA = 256 (two CTAs per SM:
+// two signals' chains of dependent phases at once) when two fit in an SM's
+// shared memory, else 512 (one CTA per SM, 12 warps on each long row); the
+// grid has kGramThreads / CTA CTAs per SM; each CTA takes rows blockIdx.x,
 // blockIdx.x + gridDim.x, ...
-template <bool SM>
-__global__ void __launch_bounds__(kGramCta, kGramThreads / kGramCta) gram_select_kernel(const SelArgs a) {
+template <bool SM, int CTA>
+__global__ void __launch_bounds__(CTA, kGramThreads / CTA) gram_select_kernel(const SelArgs a) {
     extern __shared__ float4 dsm[];
     float* r = reinterpret_cast<float*>(dsm);
     float4* rs4 = dsm;
@@ -699,12 +701,13 @@ __global__ void __launch_bounds__(kGramCta, kGramThreads / kGramCta) gram_select
     __shared__ double redd[kGramGroup0 / 32];
     __shared__ int top[kTop];
     __shared__ unsigned long long rkey[kTop];
-    __shared__ float wthr[kGramCta / 32];
+    __shared__ float wthr[CTA / 32];
     __shared__ unsigned long long list[kGramList];
     __shared__ int list_n;
-    __shared__ unsigned long long gtw[kGramCta / 32][kTop];
+    __shared__ unsigned long long gtw[CTA / 32][kTop];
     __shared__ uint64_t bar_c, bar_g;
     __shared__ int abort_flag;
+    __shared__ int spec_m;   // SM: the row of G whose copy started with the signal (-1: none)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // the first row's slot is fetched with the row count, not after it (the
     // grid never exceeds the slot table, so the index is in range)
@@ -717,6 +720,9 @@ __global__ void __launch_bounds__(kGramCta, kGramThreads / kGramCta) gram_select
     }
     if (threadIdx.x == 0) abort_flag = 0;
     __syncthreads();
+    // parity of bar_g's next phase: it completes once per signal, or twice
+    // when the speculative row of G was not the selected one
+    uint32_t gph = 0;
     for (int i = blockIdx.x, it = 0; i < n_act && !abort_flag; i += gridDim.x, ++it) {
         const uint32_t ph = static_cast<uint32_t>(it & 1);
         const int slot = it == 0 ? slot0 : a.act[i];
@@ -725,14 +731,23 @@ __global__ void __launch_bounds__(kGramCta, kGramThreads / kGramCta) gram_select
         if (SM && threadIdx.x == 0) {
             mbar_arrive_expect_tx(&bar_c, static_cast<uint32_t>(a.ldC) * 4u);
             bulk_g2s(cs4, cr4, static_cast<uint32_t>(a.ldC) * 4u, &bar_c);
+            // the carried best candidate is nearly always the one the rescore
+            // selects: its row of G starts coming in with the correlations
+            const unsigned long long k0 = a.gtop[static_cast<size_t>(slot) * kTop];
+            const int mg = k0 ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(k0)) : -1;
+            spec_m = mg;
+            if (mg >= 0) {
+                mbar_arrive_expect_tx(&bar_g, static_cast<uint32_t>(a.ldG) * 4u);
+                bulk_g2s(gs4, a.G + static_cast<size_t>(mg) * a.ldG, static_cast<uint32_t>(a.ldG) * 4u, &bar_g);
+            }
         }
         SlotState s = a.st[slot];
         BatchIO io;
         if (threadIdx.x == 0) io = *a.io;
-        for (int k = threadIdx.x; k < n4; k += kGramCta) cp_async16(rs4 + k, rg4 + k);
+        for (int k = threadIdx.x; k < n4; k += CTA) cp_async16(rs4 + k, rg4 + k);
         cp_async_commit();
         if (!SM)
-            for (int q = threadIdx.x * 8; q < nq; q += kGramCta * 8) prefetch_line_l2(cr4 + q);
+            for (int q = threadIdx.x * 8; q < nq; q += CTA * 8) prefetch_line_l2(cr4 + q);
         if (threadIdx.x < kTop) {
             const unsigned long long k = a.gtop[static_cast<size_t>(slot) * kTop + threadIdx.x];
             top[threadIdx.x] = k ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(k)) : -1;
@@ -754,10 +769,29 @@ __global__ void __launch_bounds__(kGramCta, kGramThreads / kGramCta) gram_select
         const int m = kbest ? key_index(kbest) : 0;
         const float c = kbest ? key_coef(kbest) : 0.f;
         const float4* gr4 = reinterpret_cast<const float4*>(a.G + static_cast<size_t>(m) * a.ldG);
+        const int mg = SM ? spec_m : -1;
+        const bool g_miss = SM && kbest && mg >= 0 && mg != m;   // the same in every thread
         if (kbest && SM && threadIdx.x == 0) {
-            mbar_arrive_expect_tx(&bar_g, static_cast<uint32_t>(a.ldG) * 4u);
-            bulk_g2s(gs4, gr4, static_cast<uint32_t>(a.ldG) * 4u, &bar_g);
+            bool issue = mg < 0;
+            if (g_miss) {
+                // the guessed row lands first (the buffer is not written twice
+                // at once), then the selected row comes in
+                issue = mbar_wait_bounded(&bar_g, gph, a.lim);
+                if (!issue) {
+                    atomicCAS(a.err, 0, static_cast<int>(MP_ERR_TIMEOUT));
+                    abort_flag = 1;
+                    mbar_wait_bounded(&bar_g, gph, a.lim);   // the copy in flight, once more
+                }
+            }
+            if (issue) {
+                mbar_arrive_expect_tx(&bar_g, static_cast<uint32_t>(a.ldG) * 4u);
+                bulk_g2s(gs4, gr4, static_cast<uint32_t>(a.ldG) * 4u, &bar_g);
+            }
         }
+        // the phase the row update waits for; bar_g completes one phase for
+        // this signal, two after a missed guess
+        const uint32_t gwait = g_miss ? (gph ^ 1u) : gph;
+        if (!g_miss) gph ^= 1u;
         if (kbest == 0ull) {   // no candidate: nothing can be selected; the signal leaves
             if (threadIdx.x == 0) {
                 s.status = MP_ERR_INVALID;
@@ -768,22 +802,28 @@ __global__ void __launch_bounds__(kGramCta, kGramThreads / kGramCta) gram_select
                     abort_flag = 1;
                     mbar_wait_bounded(&bar_c, ph, a.lim);   // the copy in flight, once more
                 }
+                // a speculative row of G lands before its buffer is reused
+                if (SM && mg >= 0 && !mbar_wait_bounded(&bar_g, gwait, a.lim)) {
+                    atomicCAS(a.err, 0, static_cast<int>(MP_ERR_TIMEOUT));
+                    abort_flag = 1;
+                    mbar_wait_bounded(&bar_g, gwait, a.lim);
+                }
             }
             __syncthreads();
-            if (SM && !abort_flag && threadIdx.x == 0) {
-                // keep the G barrier's phase in step with the C barrier's
+            if (SM && mg < 0 && !abort_flag && threadIdx.x == 0) {
+                // no row of G was copied: complete its phase by hand
                 mbar_arrive(&bar_g);
             }
             __syncthreads();
             continue;
         }
         if (!SM)
-            for (int q = threadIdx.x * 8; q < nq; q += kGramCta * 8) prefetch_line_l2(gr4 + q);
+            for (int q = threadIdx.x * 8; q < nq; q += CTA * 8) prefetch_line_l2(gr4 + q);
         float xm = 0.f;
         if (threadIdx.x == 0) xm = io.X[static_cast<size_t>(slot) * io.ldx + m];
         // Eq. 11 in FP32
         const float4* pm = reinterpret_cast<const float4*>(a.psi32 + static_cast<size_t>(m) * a.ldN);
-        for (int k = threadIdx.x; k < n4; k += kGramCta) {
+        for (int k = threadIdx.x; k < n4; k += CTA) {
             const float4 p = __ldg(pm + k);
             float4 v = rs4[k];
             v.x = fmaf(-c, p.x, v.x);
@@ -832,7 +872,7 @@ __global__ void __launch_bounds__(kGramCta, kGramThreads / kGramCta) gram_select
             }
         } else {
             // ---- Gram group: c_j -= c G[m][j] and the row's 8 largest |c|
-            constexpr int GT = kGramCta - kGramGroup0;
+            constexpr int GT = CTA - kGramGroup0;
             const int gt = threadIdx.x - kGramGroup0, gw = warp - kGramGroup0 / 32;
             bool ok = true;
             if (SM) {
@@ -840,14 +880,14 @@ __global__ void __launch_bounds__(kGramCta, kGramThreads / kGramCta) gram_select
                 // of the group sees the same outcome)
                 if (gt == 0) {
                     const bool okc = mbar_wait_bounded(&bar_c, ph, a.lim);
-                    const bool okg = mbar_wait_bounded(&bar_g, ph, a.lim);
+                    const bool okg = mbar_wait_bounded(&bar_g, gwait, a.lim);
                     if (!(okc && okg)) {
                         atomicCAS(a.err, 0, static_cast<int>(MP_ERR_TIMEOUT));
                         abort_flag = 1;
                         // let any copy still in flight land before the
                         // buffers are left (bounded again)
                         if (!okc) mbar_wait_bounded(&bar_c, ph, a.lim);
-                        if (!okg) mbar_wait_bounded(&bar_g, ph, a.lim);
+                        if (!okg) mbar_wait_bounded(&bar_g, gwait, a.lim);
                     }
                 }
                 named_bar_sync(2, GT);
@@ -855,7 +895,7 @@ __global__ void __launch_bounds__(kGramCta, kGramThreads / kGramCta) gram_select
                 if (ok) {
                     // every thread passes its own wait (the phase is complete)
                     mbar_try_wait(&bar_c, ph);
-                    mbar_try_wait(&bar_g, ph);
+                    mbar_try_wait(&bar_g, gwait);
                 }
             }
             float mx = 0.f;
@@ -1590,6 +1630,15 @@ static size_t gram_smem_bytes(const PlanImpl* p, const BatchEngine* e, bool rows
 static bool gram_rows_in_smem(const PlanImpl* p, const BatchEngine* e) {
     return gram_smem_bytes(p, e, true) <= 200u * 1024u;
 }
+// threads per Gram-step CTA: 256 when the rows are staged in shared memory
+// and two such CTAs fit in an SM's (with the static part and the per-CTA
+// reserve), else 512: rows read from global memory are long, and 12 warps
+// on each row's update beat a second CTA (measured on M = 32768)
+static int gram_cta(const PlanImpl* p, const BatchEngine* e) {
+    if (!gram_rows_in_smem(p, e)) return 512;
+    const size_t per_cta = gram_smem_bytes(p, e, true) + 4096u;
+    return 2u * per_cta <= static_cast<size_t>(kSmemPerSM) ? 256 : 512;
+}
 
 // One step on operand half `half`: GEMM + top-8, then select / rescore /
 // update, which moves the signals that run on into the other half.  In the
@@ -1652,12 +1701,18 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, bool gram,
     sa.lim = static_cast<unsigned long long>(p->watchdog_ns);
     const size_t sm = p->ldN * sizeof(float);
     if (gram) {
-        const int per_sm = kGramThreads / kGramCta;
+        const int cta = gram_cta(p, e);
+        const int per_sm = kGramThreads / cta;
         const int ctas = std::max(1, std::min(e->cap, p->sm_count > 0 ? per_sm * p->sm_count : e->cap));
         const bool rows_sm = gram_rows_in_smem(p, e);
         const size_t gsm = gram_smem_bytes(p, e, rows_sm);
-        if (rows_sm) gram_select_kernel<true><<<ctas, kGramCta, gsm, st>>>(sa);
-        else gram_select_kernel<false><<<ctas, kGramCta, gsm, st>>>(sa);
+        if (cta == 256) {
+            if (rows_sm) gram_select_kernel<true, 256><<<ctas, 256, gsm, st>>>(sa);
+            else gram_select_kernel<false, 256><<<ctas, 256, gsm, st>>>(sa);
+        } else {
+            if (rows_sm) gram_select_kernel<true, 512><<<ctas, 512, gsm, st>>>(sa);
+            else gram_select_kernel<false, 512><<<ctas, 512, gsm, st>>>(sa);
+        }
     } else if (e->cap < kWideSelectCap) select_update_kernel<2 * kSumChains><<<e->cap, 2 * kSumChains, sm, st>>>(sa);
     else select_update_kernel<kSumChains><<<e->cap, kSumChains, sm, st>>>(sa);
     ++*kernels;
@@ -1714,9 +1769,12 @@ static mp_status capture_steps(PlanImpl* p, BatchEngine* e, int steps, bool gram
     // every active signal by one); the slots at a multiple of the period get
     // their correlations recomputed directly
     // a batched decode's active signals have all taken the same number of
-    // steps (they start together); a server's (retire) have not
+    // steps (they start together); a server's (retire) have not.  A small
+    // batch's refreshes stay with the row-group kernel (a 128-row tile would
+    // compute mostly padding)
     if (gram)
-        r = launch_gram_refresh(p, e, e->act, e->counters, e->cap, e->gram_R, !retire, e->cap_stream, &kernels);
+        r = launch_gram_refresh(p, e, e->act, e->counters, e->cap, e->gram_R, !retire && e->cap >= kTiledMinRows,
+                                e->cap_stream, &kernels);
     for (int s = 0; s < steps && r == cudaSuccess; ++s) r = launch_step(p, e, s & 1, gram, e->cap_stream, &kernels);
     if (retire && r == cudaSuccess) {
         RetireArgs ra;
@@ -1778,7 +1836,9 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
         // when they fit; a long row may not fit any CTA's shared memory)
         const bool rows_sm = gram_rows_in_smem(p, e);
         const int gsm = static_cast<int>(gram_smem_bytes(p, e, rows_sm));
-        MP_CUDA_TRY(cudaFuncSetAttribute(rows_sm ? gram_select_kernel<true> : gram_select_kernel<false>,
+        const bool two = gram_cta(p, e) == 256;
+        MP_CUDA_TRY(cudaFuncSetAttribute(rows_sm ? (two ? gram_select_kernel<true, 256> : gram_select_kernel<true, 512>)
+                                                 : (two ? gram_select_kernel<false, 256> : gram_select_kernel<false, 512>),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, gsm));
     }
     if (e->gram_R > 0 && (e->gram_R % steps || !p->gram))
