@@ -165,7 +165,7 @@ def log_parity(rec):
 
 
 def compare_to_oracle(psi, y, eps, T, gpu, ora=None, x_tol=1e-4, check_follow=True, fp64=False, gram_period=0,
-                      strict=True, label=None):
+                      strict=True, label=None, gram_rescored=False):
     """Apply rules (i)-(iii); returns a dict of diagnostics, asserts on failure.
     ``gpu`` holds the path's own result, atoms, x~ and final residual ``r``.
     ``check_follow=False`` skips the FP64 replay when the whole sequence and
@@ -174,8 +174,13 @@ def compare_to_oracle(psi, y, eps, T, gpu, ora=None, x_tol=1e-4, check_follow=Tr
     ``gram_period`` R > 0: the correlations were updated through the Gram
     matrix for up to R - 1 steps after each direct computation; each update
     adds at most |c_prev| |G - Psi^T Psi| + 2^-24 |c_m| <= (N + 2) 2^-24 ||r||
-    of error (G entries are N-term FP32 FMA chains of unit atoms), so d grows
-    by 2 R (N + 2) (a factor 2 for ||r|| at the refresh vs now).
+    of error (G entries are N-term FP32 FMA chains of unit atoms), so the
+    depth of the correlations that rank the candidates grows by 2 R (N + 2)
+    (a factor 2 for ||r|| at the refresh vs now).  ``gram_rescored``: the
+    path rescored its candidates in FP32 and updated r with that exact
+    coefficient (the batched Gram mode), so the residual's drift bound keeps
+    the plain depth; otherwise (the plain Gram decode commits the
+    recurrence's coefficient) the drift bound takes the widened depth too.
     ``strict=False``: rule (i) up to the FP32-bound cut-off instead of the
     literal one (see the module docstring for when a test may ask)."""
     from oracle import mp_oracle as orc
@@ -192,7 +197,9 @@ def compare_to_oracle(psi, y, eps, T, gpu, ora=None, x_tol=1e-4, check_follow=Tr
     if label is not None:
         out["label"] = label
     u = U64 if fp64 else U32
-    d = (summation_depth64(N) if fp64 else summation_depth(N)) + (2 * gram_period * (N + 2) if gram_period > 0 else 0)
+    d_plain = summation_depth64(N) if fp64 else summation_depth(N)
+    d = d_plain + (2 * gram_period * (N + 2) if gram_period > 0 else 0)  # the correlations that rank
+    d_r = d_plain if gram_rescored else d                                # the residual's arithmetic
     gamma = d * u
     floor = GAP_TIE64 if fp64 else GAP_TIE
     r_all = np.sqrt(np.concatenate([[ora["e0"]], ora["energies"]]))   # oracle ||r|| before each step and at the end
@@ -223,7 +230,7 @@ def compare_to_oracle(psi, y, eps, T, gpu, ora=None, x_tol=1e-4, check_follow=Tr
             assert np.array_equal(ga[:n], oa[:n]), f"atom sequence diverges at {div} before the FP32-bound cut-off {tie}"
         if f is not None:
             n_t = min(len(ga), len(r_all))
-            D_T = u * np.sqrt(d + 1) * np.sqrt(np.sum(r_all[:n_t] ** 2))
+            D_T = u * np.sqrt(d_r + 1) * np.sqrt(np.sum(r_all[:n_t] ** 2))
             out["drift_over_estimate"] = Delta / D_T if D_T > 0 else 0.0
             assert Delta <= 16 * D_T + 1e-300, f"drift {Delta:.3e} exceeds 16x the rounding estimate {D_T:.3e}"
         cut = lit if strict else tie

@@ -198,7 +198,7 @@ def test_switched_batched_equals_direct(S):
             assert l2 - l1 < l1 - l0, (l1 - l0, l2 - l1)
         for b in range(0, prob.B, 60):
             compare_to_oracle(prob.psi, prob.y[b], prob.eps, prob.T, batched_signal(out, b), check_follow=False,
-                              gram_period=64)
+                              gram_period=64, gram_rescored=True)
             assert orc.support_score(out["X"][b], prob.supports[b]) == 1.0
 
 
@@ -222,7 +222,8 @@ def test_gram_full_bf16_workload_equals_direct(R, S):
     _same_decodes(out, ref, prob.B)
     for b in (0, 341, 682, 1023):
         d = compare_to_oracle(prob.psi, prob.y[b], prob.eps, prob.T, batched_signal(out, b), check_follow=False,
-                              gram_period=R, label=f"{name}[{b}] R={R} S={S}")
+                              gram_period=R, gram_rescored=True,
+                              label=f"{name}[{b}] R={R} S={S}")
         assert d["x_rel_err"] <= 1e-4
 
 
@@ -263,5 +264,6 @@ def test_gram_fp8_full_workload():
             assert res[b].iters == plain["result"].iters, b
             assert np.array_equal(out["X"][b], plain["x"]), b
     d = compare_to_oracle(prob.psi, prob.y[128], prob.eps, prob.T, batched_signal(out, 128), check_follow=False,
-                          gram_period=512, label=f"{name}[128] Gram R=512")
+                          gram_period=512, gram_rescored=True,
+                          label=f"{name}[128] Gram R=512")
     assert d["x_rel_err"] <= 1e-4
