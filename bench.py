@@ -544,14 +544,16 @@ def variants_measure(n_sig=4, gram_period=32):
 
 
 def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=(256, 256), n_oracle=0,
-                    variants=()):
+                    variants=(), profile_gram=0):
     """Batched low-precision decode of a whole batched workload vs the plain
     FP32 kernel on the same signals (the first ``n_plain`` of them); x~ of
     ``n_oracle`` signals spread over the batch against full FP64 oracle
     decodes.  ``variants``: (R, S) pairs; each also times the same batch
     with Gram-updated correlations, refresh period R (S = 0: every step;
     S > 0: direct GEMM steps while more than S signals are active, Gram
-    steps after), and compares its x~ with the direct decode's bit for bit."""
+    steps after), and compares its x~ with the direct decode's bit for bit.
+    ``profile_gram`` R > 0 with ``profile``: the profiling case decodes with
+    Gram-updated steps of period R instead of GEMM steps."""
     import torch
     from oracle import mp_oracle as orc
     from paper_0809_1833_gb300 import binding as B
@@ -572,6 +574,8 @@ def batched_measure(prec_name, reps=3, n_plain=16, profile=False, profile_shape=
         B.mp_plan_set_option(plan, B.MP_OPT_BATCH_TILE_N, tn)
         if not pair:
             B.mp_plan_set_option(plan, B.MP_OPT_BATCH_TILE_M, tm)
+        if profile_gram:
+            B.mp_plan_set_option(plan, B.MP_OPT_BATCH_GRAM, profile_gram)
     Y = torch.from_numpy(prob.y).cuda()
     X = torch.empty((prob.B, prob.M), device="cuda")
     stop = (w["eps"], w["T"])
@@ -1320,6 +1324,8 @@ def main():
     ap.add_argument("--breakdown-rows", type=int, nargs="*", default=None,
                     help="active-row counts of --step-breakdown (default 1 2 4 8 16)")
     ap.add_argument("--breakdown-T", type=int, default=None, help="iteration cap of --step-breakdown")
+    ap.add_argument("--profile-gram", type=int, default=0, metavar="R",
+                    help="with --profile-batched: the decode takes Gram-updated steps of period R")
     ap.add_argument("--gram-steps", choices=["bf16", "fp8"], default=None,
                     help="per-step time of direct and Gram-updated steps, and whole decodes in the Gram settings")
     ap.add_argument("--shard-overhead", action="store_true",
@@ -1384,7 +1390,8 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         shape = tuple(int(v) for v in args.profile_shape.split(","))
-        print(json.dumps(batched_measure(args.profile_batched, profile=True, profile_shape=shape)))
+        print(json.dumps(batched_measure(args.profile_batched, profile=True, profile_shape=shape,
+                                         profile_gram=args.profile_gram)))
     elif args.profile:
         run_profile_case(args.profile)
     elif args.impl == "reference":
