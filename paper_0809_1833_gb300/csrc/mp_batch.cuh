@@ -156,9 +156,14 @@ struct BatchEngine {
     int gram_below = 0;
     cudaGraphExec_t graph = nullptr;
     cudaGraphExec_t graph_g = nullptr;
+    // Gram steps without the refresh at the start of the replay: a batched
+    // decode's signals all start together, so the host knows which replays
+    // begin at a multiple of the period and runs this graph for the others
+    cudaGraphExec_t graph_gn = nullptr;
     int graph_steps = 0;
     int graph_kernels = 0;          // kernels one replay of the graph launches
     int graph_g_kernels = 0;        // the same for graph_g
+    int graph_gn_kernels = 0;       // the same for graph_gn
     bool graph_retire = false;
     cudaStream_t cap_stream = nullptr;
     cudaEvent_t cnt_ready[2] = {nullptr, nullptr};   // active-count reads of alternate replays

@@ -1433,6 +1433,7 @@ void engine_free(BatchEngine* e) {
     if (!e) return;
     if (e->graph) cudaGraphExecDestroy(e->graph);
     if (e->graph_g) cudaGraphExecDestroy(e->graph_g);
+    if (e->graph_gn) cudaGraphExecDestroy(e->graph_gn);
     if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
     for (cudaEvent_t ev : e->cnt_ready)
         if (ev) cudaEventDestroy(ev);
@@ -1760,7 +1761,7 @@ static cudaError_t launch_gram_refresh(PlanImpl* p, BatchEngine* e, const int* r
 // followed by the retire copy, and instantiate them into *out.
 static mp_status capture_steps(PlanImpl* p, BatchEngine* e, int steps, bool gram, bool retire, float* out_x,
                                SlotState* out_state, int* out_list, int* out_count, cudaGraphExec_t* out,
-                               int* out_kernels) {
+                               int* out_kernels, bool refresh = true) {
     MP_CUDA_TRY(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t r = cudaSuccess;
     int kernels = 0;
@@ -1772,7 +1773,7 @@ static mp_status capture_steps(PlanImpl* p, BatchEngine* e, int steps, bool gram
     // steps (they start together); a server's (retire) have not.  A small
     // batch's refreshes stay with the row-group kernel (a 128-row tile would
     // compute mostly padding)
-    if (gram)
+    if (gram && refresh)
         r = launch_gram_refresh(p, e, e->act, e->counters, e->cap, e->gram_R, !retire && e->cap >= kTiledMinRows,
                                 e->cap_stream, &kernels);
     for (int s = 0; s < steps && r == cudaSuccess; ++s) r = launch_step(p, e, s & 1, gram, e->cap_stream, &kernels);
@@ -1818,6 +1819,10 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
         cudaGraphExecDestroy(e->graph_g);
         e->graph_g = nullptr;
     }
+    if (e->graph_gn) {
+        cudaGraphExecDestroy(e->graph_gn);
+        e->graph_gn = nullptr;
+    }
     if (e->gram_below > 0 && retire)
         return fail(MP_ERR_UNSUPPORTED, "batched step graph: the switched mode has no retiring graph");
     if (!e->cap_stream) MP_CUDA_TRY(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
@@ -1852,9 +1857,17 @@ mp_status engine_build_graph(PlanImpl* p, BatchEngine* e, int steps, bool retire
     if (s == MP_OK && e->gram_below > 0)
         s = capture_steps(p, e, steps, true, false, nullptr, nullptr, nullptr, nullptr, &e->graph_g,
                           &e->graph_g_kernels);
+    // a batched decode's Gram steps without the refresh (replays that do not
+    // start at a multiple of the period)
+    if (s == MP_OK && e->gram_R > 0 && !retire)
+        s = capture_steps(p, e, steps, true, false, nullptr, nullptr, nullptr, nullptr, &e->graph_gn,
+                          &e->graph_gn_kernels, false);
     if (s != MP_OK) {
-        if (e->graph) cudaGraphExecDestroy(e->graph);
-        e->graph = nullptr;
+        for (cudaGraphExec_t* gp : {&e->graph, &e->graph_g, &e->graph_gn})
+            if (*gp) {
+                cudaGraphExecDestroy(*gp);
+                *gp = nullptr;
+            }
         return s;
     }
     e->graph_steps = steps;
@@ -1978,9 +1991,27 @@ static mp_status batched_run(PlanImpl* p, int prec, const float* Y, float* X, lo
     for (int j = 0; j < 2; ++j)
         if (!e->cnt_ready[j]) MP_CUDA_TRY(cudaEventCreateWithFlags(&e->cnt_ready[j], cudaEventDisableTiming));
     const long long max_replays = (static_cast<long long>(maxT) + kStepsPerGraph - 1) / kStepsPerGraph + 1;
+    // every active signal has taken kStepsPerGraph * k steps when replay k
+    // starts; a Gram replay refreshes them only when that is a positive
+    // multiple of the period, and runs without the refresh launches otherwise
+    const bool pure_gram = e->gram_R > 0 && gram_below == 0;
     for (long long k = 0; k < max_replays; ++k) {
-        MP_CUDA_TRY(cudaGraphLaunch(gram_steps ? e->graph_g : e->graph, st));
-        p->launches += gram_steps ? e->graph_g_kernels : e->graph_kernels;
+        cudaGraphExec_t g = e->graph;
+        int gk = e->graph_kernels;
+        if (pure_gram || gram_steps) {
+            const long long t0 = static_cast<long long>(kStepsPerGraph) * k;
+            if (t0 > 0 && t0 % e->gram_R == 0) {
+                if (gram_steps) {
+                    g = e->graph_g;
+                    gk = e->graph_g_kernels;
+                }
+            } else {
+                g = e->graph_gn;
+                gk = e->graph_gn_kernels;
+            }
+        }
+        MP_CUDA_TRY(cudaGraphLaunch(g, st));
+        p->launches += gk;
         MP_CUDA_TRY(cudaMemcpyAsync(e->h_cnt + (k & 1), e->counters, sizeof(int), cudaMemcpyDeviceToHost, st));
         MP_CUDA_TRY(cudaEventRecord(e->cnt_ready[k & 1], st));
         if (k > 0) {

@@ -267,3 +267,35 @@ def test_gram_fp8_full_workload():
                           gram_period=512, gram_rescored=True,
                           label=f"{name}[128] Gram R=512")
     assert d["x_rel_err"] <= 1e-4
+
+
+@pytest.mark.parametrize("R,S", [(32, 0), (32, 4), (16, 1)], ids=["gram", "switch4", "switch1"])
+def test_gram_edge_cases(R, S):
+    """The edge cases of the direct batched decode in the Gram and switched
+    modes: y = 0, T = 0, a non-finite signal, eps above 1 and eps = 0 beside a
+    normal signal; every signal's result equals the direct decode's, and a
+    second call with one signal on the same plan equals its first decode."""
+    psi = W.gaussian_dictionary(64, 300, seed=2)
+    prob = W.make_batched(64, 300, 6, 1, 3, seed=2, psi=psi, eps=1e-5, T=500)
+    Y = prob.y.copy()
+    Y[1] = 0.0                  # y = 0
+    Y[3, 7] = np.nan            # non-finite signal
+    stops = [(1e-5, 500), (1e-5, 500), (1e-5, 0), (1e-5, 500), (2.0, 500), (0.0, 9)]
+    p = B().MP_PREC_BF16
+    with GpuPlan(psi, prec_mask=1 << p) as pl:
+        ref = batched_decode(pl, p, Y, stops, 500)
+        pl.set(B().MP_OPT_BATCH_GRAM, R)
+        pl.set(B().MP_OPT_BATCH_GRAM_BELOW, S)
+        out = batched_decode(pl, p, Y, stops, 500)
+        assert ref["status"] == out["status"] == B().MP_ERR_NONFINITE
+        for b in range(6):
+            r, r0 = out["results"][b], ref["results"][b]
+            assert (r.status, r.stop_reason, r.iters) == (r0.status, r0.stop_reason, r0.iters), b
+        for b in (0, 1, 2, 4, 5):
+            assert np.array_equal(out["X"][b], ref["X"][b]), b
+            n = out["results"][b].iters
+            assert np.array_equal(out["atoms"][b, :n], ref["atoms"][b, :n]), b
+        assert out["results"][5].iters == 9 and out["results"][1].stop_reason == B().MP_STOP_ZERO_Y
+        one = batched_decode(pl, p, prob.y[:1], (1e-5, 500), 500)
+        assert one["status"] == 0 and one["results"][0].iters == out["results"][0].iters
+        assert np.array_equal(one["X"][0], out["X"][0])
