@@ -1768,11 +1768,10 @@ static mp_status capture_steps(PlanImpl* p, BatchEngine* e, int steps, bool gram
     // Gram steps: a replay starts with every active slot's step count a
     // multiple of `steps` (signals join between replays and each step moves
     // every active signal by one); the slots at a multiple of the period get
-    // their correlations recomputed directly
-    // a batched decode's active signals have all taken the same number of
-    // steps (they start together); a server's (retire) have not.  A small
-    // batch's refreshes stay with the row-group kernel (a 128-row tile would
-    // compute mostly padding)
+    // their correlations recomputed directly.  A batched decode's active
+    // signals have all taken the same number of steps (they start together),
+    // a server's (retire) have not; a small batch's refreshes stay with the
+    // row-group kernel (a 128-row tile would compute mostly padding).
     if (gram && refresh)
         r = launch_gram_refresh(p, e, e->act, e->counters, e->cap, e->gram_R, !retire && e->cap >= kTiledMinRows,
                                 e->cap_stream, &kernels);
