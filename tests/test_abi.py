@@ -79,3 +79,31 @@ def test_header_compiles_as_c(tmp_path):
     p = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
                         "-c", str(c), "-o", str(tmp_path / "t.o")], capture_output=True, text=True)
     assert p.returncode == 0, p.stderr
+
+
+def header_enum_values():
+    """Every `MP_NAME = value` enumerator the headers declare."""
+    vals = {}
+    for h in sorted(os.listdir(INCLUDE)):
+        if h.endswith(".h"):
+            src = open(os.path.join(INCLUDE, h)).read()
+            src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)   # comments mention values in prose
+            src = re.sub(r"//[^\n]*", " ", src)
+            for name, v in re.findall(r"\b(MP_[A-Z0-9_]+)\s*=\s*(-?\d+)", src):
+                vals[name] = int(v)
+    return vals
+
+
+def test_binding_constants_match_header():
+    """The binding's option, query, precision, stop-reason and status
+    numbers are the header's (a renumbered or added enumerator must reach
+    both sides)."""
+    from paper_0809_1833_gb300 import binding as B
+    hdr = header_enum_values()
+    assert {"MP_OPT_BATCH_GRAM", "MP_OPT_BATCH_GRAM_BELOW", "MP_Q_BATCH_GRAM_BELOW", "MP_PREC_BF16"} <= set(hdr)
+    checked = 0
+    for name, v in hdr.items():
+        if hasattr(B, name):
+            assert getattr(B, name) == v, (name, getattr(B, name), v)
+            checked += 1
+    assert checked >= 40, checked
