@@ -630,7 +630,6 @@ __global__ void __launch_bounds__(THREADS, THREADS == kSumChains ? 6 : (THREADS 
 // not read again).  The same 8 keys as a full ranking of the row, so the
 // same results bit for bit.
 constexpr int kGramThreads = 512;                       // threads of an SM's Gram-step CTAs together
-constexpr int kSmemPerSM = 233472;                      // shared memory of one SM (228 KB on sm_103a)
 constexpr int kGramGroup0 = kSumChains;                // energy group: threads 0..127
 constexpr int kGramList = 256;                          // entries at or above the threshold kept
 
@@ -1638,7 +1637,7 @@ static bool gram_rows_in_smem(const PlanImpl* p, const BatchEngine* e) {
 static int gram_cta(const PlanImpl* p, const BatchEngine* e) {
     if (!gram_rows_in_smem(p, e)) return 512;
     const size_t per_cta = gram_smem_bytes(p, e, true) + 4096u;
-    return 2u * per_cta <= static_cast<size_t>(kSmemPerSM) ? 256 : 512;
+    return 2u * per_cta <= static_cast<size_t>(p->smem_per_sm) ? 256 : 512;
 }
 
 // One step on operand half `half`: GEMM + top-8, then select / rescore /

@@ -120,6 +120,7 @@ struct PlanImpl {
     int device = 0;
     int sm_count = 0;
     int max_smem_optin = 0;
+    int smem_per_sm = 0;            // shared memory of one SM (all its CTAs together)
     size_t device_bytes = 0;
 
     float* psi32 = nullptr;

@@ -212,8 +212,14 @@ static mp_status plan_create_t(mp_plan_t* out, const mp_plan_desc* desc, const T
     p->prec_mask = desc->prec_mask | 1u;
     cudaError_t e;
     if ((e = cudaGetDevice(&p->device)) != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
-    cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
-    cudaDeviceGetAttribute(&p->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    if ((e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaDeviceGetAttribute(multiprocessor count)"));
+    if ((e = cudaDeviceGetAttribute(&p->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device)) !=
+        cudaSuccess)
+        return bail(cuda_fail(e, "cudaDeviceGetAttribute(shared memory per block, opt-in)"));
+    if ((e = cudaDeviceGetAttribute(&p->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device)) !=
+        cudaSuccess)
+        return bail(cuda_fail(e, "cudaDeviceGetAttribute(shared memory per multiprocessor)"));
 
     const size_t n32 = static_cast<size_t>(p->M) * p->ldN;
     if ((e = cudaMalloc(&p->psi32, n32 * sizeof(float))) != cudaSuccess)
