@@ -1696,7 +1696,8 @@ static cudaError_t launch_step(PlanImpl* p, BatchEngine* e, int half, bool gram,
     // with 16 loads per lane in flight (with few signals the rescore is a
     // latency chain of L2 / HBM reads); engines of 512 slots and more: 4
     // warps, two candidates each, so more signals' CTAs fit on an SM at a
-    // full batch.  Gram mode: the Gram-step kernel (16 warps).
+    // full batch.  Gram mode: the Gram-step kernel (8 or 16 warps per CTA,
+    // gram_cta).
     sa.err = e->err;
     sa.lim = static_cast<unsigned long long>(p->watchdog_ns);
     const size_t sm = p->ldN * sizeof(float);
